@@ -1,0 +1,33 @@
+"""Interpolative and CUR decompositions from chosen skeletons (Sec. 2.2).
+
+Column ID (Eq. (2.1)):   CID(A; J_s) = C C^+ A,  C = A(:, J_s),  so Z = C^+ A.
+CUR (Eq. (2.4)):         CUR(A; I_s, J_s) = C (C^+ A R^+) R,  R = A(I_s, :),  U = C^+ A R^+.
+Stable CUR (Remark 3):   with C = Q_C R_C and R^T = Q_R R_R (unpivoted QR),
+                         CUR = Q_C (Q_C^T A Q_R) Q_R^T,  hence U = R_C^{-1} (Q_C^T A Q_R) R_R^{-T}.
+
+LAPACK Householder QR (numpy.linalg.qr) and triangular solves serve as single steps.
+"""
+
+import numpy as np
+from scipy.linalg import solve_triangular
+
+
+def column_id(A, Js):
+    """Z (s x n, FP64) of the column ID A ~ A(:, Js) Z, computed as R_C^{-1} (Q_C^T A)."""
+    A = np.asarray(A, dtype=np.float64)
+    C = A[:, np.asarray(Js)]
+    Q, R = np.linalg.qr(C, mode="reduced")
+    return solve_triangular(R, Q.T @ A, lower=False)
+
+
+def cur(A, Js, Is):
+    """U (s x s, FP64) of the CUR A ~ A(:, Js) U A(Is, :) via the stable form (Remark 3)."""
+    A = np.asarray(A, dtype=np.float64)
+    C = A[:, np.asarray(Js)]
+    Rm = A[np.asarray(Is), :]
+    Qc, Rc = np.linalg.qr(C, mode="reduced")
+    Qr, Rr = np.linalg.qr(Rm.T, mode="reduced")
+    M = Qc.T @ A @ Qr
+    U = solve_triangular(Rc, M, lower=False)                # R_C^{-1} M
+    U = solve_triangular(Rr, U.T, lower=False).T            # (R_R^{-1} U^T)^T = U R_R^{-T}
+    return U

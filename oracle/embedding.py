@@ -1,0 +1,123 @@
+"""Randomized linear embeddings Gamma (l x m) of Sec. 2.3, drawn from Philox-4x32-10.
+
+Gaussian embedding (Sec. 2.3, item 1): i.i.d. entries N(0, 1/l).  Reading: the printed mean
+"mu" is taken as 0, as in every cited construction.  The scale 1/sqrt(l) does not change
+any pivot (argmax is invariant under positive scaling) and is applied to the sketch.
+
+    counter = (j >> 2, i, TAG_GAUSSIAN, 0), key = seed split in two 32-bit words.
+    The four output words (x0, x1, x2, x3) give two Box-Muller pairs, i.e. the four
+    standard normals G[i, 4*(j>>2) + q], q = 0..3:
+        u_a = (2*(x_a >> 9) + 1) * 2^-24   in [2^-24, 1 - 2^-24] (exact in FP32)
+        (G0, G1) = sqrt(-2 ln u_0) * (cos 2 pi u_1, sin 2 pi u_1)
+        (G2, G3) = sqrt(-2 ln u_2) * (cos 2 pi u_3, sin 2 pi u_3)
+    Gamma = G / sqrt(l).
+
+Sparse sign embedding (Sec. 2.3, item 3): every column s_j of Gamma holds zeta Rademacher
+values at uniformly random distinct coordinates.  Readings: coordinates are drawn without
+replacement; the printed scale sqrt(m/zeta) is taken as 1/sqrt(zeta), which makes
+E[Gamma^T Gamma] = I like the Gaussian embedding (the scale never changes a pivot).
+
+    words w_0, w_1, ... of column j come from counters (j, 0, TAG_SPARSE, c) for
+    c = 0, 1, ...; word w_0 holds the signs (bit q set -> the q-th coordinate is -1);
+    the coordinates come from Floyd's sampling algorithm (Bentley & Floyd, CACM 1987):
+        for q in 0..zeta-1:  J = l - zeta + q;  t = (w_{1+q} * (J + 1)) >> 32
+                             take t unless already taken, else take J.
+"""
+
+import numpy as np
+
+from .philox import philox4x32, seed_key
+
+TAG_GAUSSIAN = 0
+TAG_SPARSE = 1
+
+
+def _unit_open(x):
+    """u = (2*(x >> 9) + 1) * 2^-24: 23 random bits, symmetric about 1/2, never 0 or 1."""
+    return (2.0 * (x.astype(np.uint64) >> np.uint64(9)).astype(np.float64) + 1.0) * 2.0 ** -24
+
+
+def gaussian_normals(l, m, seed):
+    """Standard normal matrix G (l x m, FP64) with Gamma = G / sqrt(l)."""
+    m4 = (m + 3) // 4
+    i_idx, j4_idx = np.meshgrid(np.arange(l, dtype=np.uint64),
+                                np.arange(m4, dtype=np.uint64), indexing="ij")
+    ctr = np.zeros((l * m4, 4), dtype=np.uint64)
+    ctr[:, 0] = j4_idx.ravel()
+    ctr[:, 1] = i_idx.ravel()
+    ctr[:, 2] = TAG_GAUSSIAN
+    words = philox4x32(ctr, seed_key(seed)).reshape(l, m4, 4)
+    G = np.empty((l, m4, 4), dtype=np.float64)
+    for a in (0, 2):
+        u1 = _unit_open(words[:, :, a])
+        u2 = _unit_open(words[:, :, a + 1])
+        r = np.sqrt(-2.0 * np.log(u1))
+        G[:, :, a] = r * np.cos(2.0 * np.pi * u2)
+        G[:, :, a + 1] = r * np.sin(2.0 * np.pi * u2)
+    return G.reshape(l, 4 * m4)[:, :m]
+
+
+def gaussian_embedding(l, m, seed):
+    """Gamma (l x m, FP64) with i.i.d. N(0, 1/l) entries (Sec. 2.3, item 1)."""
+    return gaussian_normals(l, m, seed) / np.sqrt(l)
+
+
+def sparse_sign_pattern(l, m, zeta, seed):
+    """Coordinates and signs of the sparse sign embedding (Sec. 2.3, item 3).
+
+    returns rows (m x zeta, int64) and signs (m x zeta, +-1.0); column j of Gamma is
+    sum_q signs[j, q] / sqrt(zeta) * e_{rows[j, q]}.
+    """
+    if not (1 <= zeta <= l and zeta <= 31):
+        raise ValueError("sparse sign embedding needs 1 <= zeta <= min(l, 31)")
+    nw = 1 + zeta
+    ncalls = (nw + 3) // 4
+    j_idx, c_idx = np.meshgrid(np.arange(m, dtype=np.uint64),
+                               np.arange(ncalls, dtype=np.uint64), indexing="ij")
+    ctr = np.zeros((m * ncalls, 4), dtype=np.uint64)
+    ctr[:, 0] = j_idx.ravel()
+    ctr[:, 2] = TAG_SPARSE
+    ctr[:, 3] = c_idx.ravel()
+    words = philox4x32(ctr, seed_key(seed)).reshape(m, ncalls * 4).astype(np.uint64)
+    rows = np.empty((m, zeta), dtype=np.int64)
+    for q in range(zeta):                      # Floyd's algorithm, all columns at once
+        J = l - zeta + q
+        t = ((words[:, 1 + q] * np.uint64(J + 1)) >> np.uint64(32)).astype(np.int64)
+        seen = (rows[:, :q] == t[:, None]).any(axis=1) if q else np.zeros(m, dtype=bool)
+        rows[:, q] = np.where(seen, J, t)
+    sign_bits = words[:, 0]
+    signs = np.empty((m, zeta), dtype=np.float64)
+    for q in range(zeta):
+        signs[:, q] = np.where((sign_bits >> np.uint64(q)) & np.uint64(1), -1.0, 1.0)
+    return rows, signs
+
+
+def sparse_sign_embedding(l, m, zeta, seed):
+    """Dense copy of the sparse sign Gamma (l x m, FP64); small sizes only."""
+    rows, signs = sparse_sign_pattern(l, m, zeta, seed)
+    Gam = np.zeros((l, m), dtype=np.float64)
+    cols = np.repeat(np.arange(m), zeta)
+    Gam[rows.ravel(), cols] = signs.ravel() / np.sqrt(zeta)
+    return Gam
+
+
+# ---------------------------------------------------------------------------------------
+# Operand rounding, for emulating what a reduced-precision sketch multiplies.
+# ---------------------------------------------------------------------------------------
+
+def round_fp32(x):
+    """Round to the nearest FP32 value (ties to even), returned as FP64."""
+    return np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def round_bf16(x):
+    """Round to the nearest bfloat16 value (ties to even) via FP32, returned as FP64.
+
+    bfloat16 keeps the upper 16 bits of an IEEE binary32 word; rounding to nearest even
+    adds 0x7FFF plus the lowest kept bit before truncating (finite inputs only).
+    """
+    f = np.asarray(x, dtype=np.float64).astype(np.float32)
+    bits = f.view(np.uint32).astype(np.uint64)
+    bits = (bits + np.uint64(0x7FFF) + ((bits >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)
+    out = (bits << np.uint64(16)).astype(np.uint32).view(np.float32)
+    return out.astype(np.float64)

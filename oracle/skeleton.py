@@ -1,0 +1,44 @@
+"""Algorithm 2 (randomized LUPP skeleton selection) end to end, and its CPQR variant
+(Algorithm 1 with CPQR on the sketch), followed by the column ID and the stable CUR.
+
+Readings: the algorithms return |J_s| = l pivots; with a target rank k and oversampling p
+(l = k + p, Sec. 2.3), the first s = k greedy pivots form the skeleton.  For LUPP the first
+k steps read only rows 0..k-1 of X, so the extra p rows never change LUPP's k pivots; they
+do enter CPQR's norms.  Row skeletons I_s come from row-wise LUPP on C = A(:, J_s)
+(Algorithm 2 line 4).
+"""
+
+import numpy as np
+
+from . import sketch, pivoting, decomp, errors
+
+
+def skeletonize(A, k, p, seed, kind="gaussian", pivot="lupp", zeta=8,
+                operand_rounding=None, want_cur=True):
+    A = np.asarray(A, dtype=np.float64)
+    l = k + p
+    if kind == "gaussian":
+        X = sketch.gaussian_sketch(A, l, seed, operand_rounding)
+    elif kind == "sparse_sign":
+        X = sketch.sparse_sign_sketch(A, l, zeta, seed)
+    else:
+        raise ValueError(kind)
+    if pivot == "lupp":
+        piv = pivoting.lupp_columns(X, k)
+    elif pivot == "cpqr":
+        piv = pivoting.cpqr_columns(X, k)
+    else:
+        raise ValueError(pivot)
+    Js = piv["Js"]
+    out = dict(X=X, Js=Js, pivot=piv, Rfac=piv["R"], gaps=piv["gaps"], status=piv["status"])
+    if piv["status"] != "ok":
+        return out
+    Z = decomp.column_id(A, Js)
+    out.update(Z=Z, err_id=errors.rel_id_error(A, Js, Z), eta=errors.eta(piv["R"], Js))
+    if want_cur:
+        C = A[:, Js]
+        rp = pivoting.lupp_rows(C, k)
+        Is = rp["Js"]
+        U = decomp.cur(A, Js, Is)
+        out.update(Is=Is, row_pivot=rp, U=U, err_cur=errors.rel_cur_error(A, Js, U, Is))
+    return out

@@ -1,0 +1,40 @@
+"""Row sketch X = Gamma A (Algorithm 1 line 2; Algorithm 2 line 2; Table 1).
+
+The sketch is a plain product; the only choices are the embedding and, when emulating a
+reduced-precision sketch, the rounding applied to each operand before the exact (FP64)
+product.
+"""
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import embedding
+
+
+def gaussian_sketch(A, l, seed, operand_rounding=None):
+    """X = Gamma A with the Gaussian Gamma (l x m) of ``embedding.gaussian_embedding``.
+
+    operand_rounding: None (exact FP64), "fp32" or "bf16".  When given, the standard normals
+    G and A are each rounded to that format, X = (round(G) @ round(A)) / sqrt(l) in FP64 --
+    which is what a kernel multiplying such operands with exact products computes, up to
+    its own summation order.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    G = embedding.gaussian_normals(l, A.shape[0], seed)
+    if operand_rounding == "fp32":
+        G, A = embedding.round_fp32(G), embedding.round_fp32(A)
+    elif operand_rounding == "bf16":
+        G, A = embedding.round_bf16(G), embedding.round_bf16(A)
+    elif operand_rounding is not None:
+        raise ValueError(operand_rounding)
+    return (G @ A) / np.sqrt(l)
+
+
+def sparse_sign_sketch(A, l, zeta, seed):
+    """X = Gamma A with the sparse sign Gamma; A dense (ndarray) or scipy.sparse."""
+    m = A.shape[0]
+    rows, signs = embedding.sparse_sign_pattern(l, m, zeta, seed)
+    cols = np.repeat(np.arange(m), zeta)
+    Gam = sp.csr_matrix((signs.ravel() / np.sqrt(zeta), (rows.ravel(), cols)), shape=(l, m))
+    X = Gam @ A
+    return np.asarray(X.todense() if sp.issparse(X) else X, dtype=np.float64)

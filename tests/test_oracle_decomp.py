@@ -1,0 +1,129 @@
+"""Pins for the oracle's column ID, CUR, errors and Theorem 1 (Secs. 2.2, 2.4, 4)."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import decomp, errors, pivoting, sketch, skeleton
+import workloads
+
+
+def test_id_interpolates_skeleton_columns():
+    """Z(:, Js) = I for linearly independent skeleton columns (Eq. (2.1))."""
+    A = workloads.config1(200, 150, seed=3)
+    Js = np.array([5, 17, 3, 100, 42])
+    Z = decomp.column_id(A, Js)
+    assert np.allclose(Z[:, Js], np.eye(5), atol=1e-10)
+
+
+def test_id_is_least_squares_optimal():
+    """C^T (A - C Z) = 0 (normal equations), and Z equals numpy's lstsq solution."""
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((80, 60))
+    Js = rng.choice(60, 12, replace=False)
+    Z = decomp.column_id(A, Js)
+    C = A[:, Js]
+    assert np.max(np.abs(C.T @ (A - C @ Z))) < 1e-11
+    Zl = np.linalg.lstsq(C, A, rcond=None)[0]
+    assert np.allclose(Z, Zl, atol=1e-11)
+
+
+def test_exact_rank_reconstruction():
+    """Lemma 1 + Algorithm 2: an exactly rank-r input, l = s = r, is reconstructed exactly
+    by both the column ID and the CUR (two-sided ID equals column ID, Sec. 3.3)."""
+    A = workloads.exact_rank(300, 200, 15, seed=7)
+    out = skeleton.skeletonize(A, k=15, p=0, seed=11)
+    assert out["err_id"] < 1e-12
+    assert out["err_cur"] < 1e-11
+    C = A[:, out["Js"]]
+    S = C[out["Is"], :]
+    assert np.linalg.cond(S) < 1e8
+
+
+def test_remark1_sandwich():
+    """Remark 1: ||A - CC^+A|| <= ||A - CUR|| <= sqrt(||A - CC^+A||^2 + ||A - AR^+R||^2),
+    Frobenius and spectral norms."""
+    A = workloads.config1(120, 90, seed=4)
+    out = skeleton.skeletonize(A, k=20, p=5, seed=2)
+    Js, Is, Z, U = out["Js"], out["Is"], out["Z"], out["U"]
+    C, Rm = A[:, Js], A[Is, :]
+    E_id = A - C @ Z
+    E_cur = A - C @ U @ Rm
+    E_row = A - A @ np.linalg.pinv(Rm) @ Rm
+    for nrm in ("fro", 2):
+        a, b, c = (np.linalg.norm(E, nrm) for E in (E_id, E_cur, E_row))
+        assert a <= b * (1 + 1e-10)
+        assert b <= np.sqrt(a ** 2 + c ** 2) * (1 + 1e-10)
+
+
+def test_stable_cur_equals_definition():
+    """U = R_C^{-1} (Q_C^T A Q_R) R_R^{-T} equals C^+ A R^+ (Eq. (2.4), Remark 3)."""
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((50, 40))
+    Js, Is = rng.choice(40, 7, replace=False), rng.choice(50, 7, replace=False)
+    U = decomp.cur(A, Js, Is)
+    want = np.linalg.pinv(A[:, Js]) @ A @ np.linalg.pinv(A[Is, :])
+    assert np.allclose(U, want, atol=1e-10)
+
+
+def test_theorem1_bound_and_eta_formula():
+    """Theorem 1: ||A - CC^+A||_F <= eta ||A - A Xt^+ Xt||_F with Xt = R^LU(0:s, :), and
+    eta = ||I - P_X||_2 for the oblique projector P_X = Pi_1 Xt_1^{-1} Xt (brute force)."""
+    for seed in range(5):
+        A = workloads.dense_config2(150, 120, seed=seed, dtype=np.float64)
+        X = sketch.gaussian_sketch(A, 26, seed=100 + seed)
+        piv = pivoting.lupp_columns(X, 20)
+        Js, R = piv["Js"], piv["R"]
+        Z = decomp.column_id(A, Js)
+        err = errors.fro(A - A[:, Js] @ Z)
+        eta = errors.eta(R, Js)
+        assert err <= eta * errors.rangefinder_error(A, R) * (1 + 1e-10)
+        n = A.shape[1]
+        Pi1 = np.zeros((n, len(Js)))
+        Pi1[Js, np.arange(len(Js))] = 1.0
+        P = Pi1 @ np.linalg.solve(R[:, Js], R)
+        assert eta == pytest.approx(np.linalg.norm(np.eye(n) - P, 2), rel=1e-9)
+        # the same bound holds for the row space of the first s rows of X
+        assert errors.rangefinder_error(A, R) == pytest.approx(errors.rangefinder_error(A, X[:20]), rel=1e-8)
+
+
+def test_theorem1_bound_cpqr():
+    """Theorem 1 with CPQR pivots, Xt = R^QR(0:s, :)."""
+    A = workloads.dense_config2(140, 100, seed=9, dtype=np.float64)
+    X = sketch.gaussian_sketch(A, 30, seed=1)
+    piv = pivoting.cpqr_columns(X, 24)
+    Z = decomp.column_id(A, piv["Js"])
+    err = errors.fro(A - A[:, piv["Js"]] @ Z)
+    assert err <= errors.eta(piv["R"], piv["Js"]) * errors.rangefinder_error(A, piv["R"]) * (1 + 1e-10)
+
+
+def test_volume_sampling_existence_brute_force():
+    """Sec. 2.2.3: some k-subset achieves ||A - CC^+A||_F <= sqrt(1+k) ||A - A_k||_F.
+    Brute force over all subsets of a tiny matrix; the algorithm's error is >= that minimum
+    and its ID error uses the least-squares optimal Z."""
+    rng = np.random.default_rng(5)
+    for trial in range(3):
+        A = rng.standard_normal((9, 11)) @ np.diag(0.6 ** np.arange(11))
+        k = 3
+        best = min(errors.fro(A - A[:, list(S)] @ np.linalg.lstsq(A[:, list(S)], A, rcond=None)[0])
+                   for S in itertools.combinations(range(11), k))
+        assert best <= np.sqrt(1 + k) * errors.best_rank_k_error(A, k) * (1 + 1e-12)
+        out = skeleton.skeletonize(A, k=k, p=2, seed=trial, want_cur=False)
+        assert out["err_id"] * errors.fro(A) >= best * (1 - 1e-12)
+
+
+def test_rangefinder_expectation_bound():
+    """Eq. (2.7): E||A - A X^+ X||_F^2 <= (l-1)/(l-k-1) ||A - A_k||_F^2 for Gaussian
+    sketches (mean over 200 seeds, 10% slack for sampling error)."""
+    A = workloads.dense_config2(60, 50, seed=1, dtype=np.float64)
+    k, l = 6, 12
+    vals = [errors.rangefinder_error(A, sketch.gaussian_sketch(A, l, seed=s)) ** 2 for s in range(200)]
+    bound = (l - 1) / (l - k - 1) * errors.best_rank_k_error(A, k) ** 2
+    assert np.mean(vals) <= 1.1 * bound
+
+
+def test_sparse_sign_skeleton_runs_and_is_close_to_optimal():
+    A = workloads.dense_config2(400, 200, seed=2, dtype=np.float64)
+    out = skeleton.skeletonize(A, k=20, p=20, seed=4, kind="sparse_sign", zeta=8)
+    opt = errors.best_rank_k_error(A, 20) / errors.fro(A)
+    assert opt <= out["err_id"] < 3 * opt

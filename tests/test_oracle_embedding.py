@@ -1,0 +1,118 @@
+"""Pins for the embeddings of Sec. 2.3 (Gaussian and sparse sign) and operand rounding."""
+import numpy as np
+import pytest
+import torch
+from scipy import stats
+
+from oracle import embedding, sketch
+
+
+def test_gaussian_normals_are_standard_normal():
+    """KS test against N(0,1) and the first four moments over 4e5 draws."""
+    G = embedding.gaussian_normals(100, 4000, seed=123).ravel()
+    assert abs(G.mean()) < 5 / np.sqrt(G.size)
+    assert abs(G.var() - 1.0) < 5 * np.sqrt(2.0 / G.size)
+    assert abs(stats.skew(G)) < 0.03
+    assert abs(stats.kurtosis(G)) < 0.06
+    assert stats.kstest(G, "norm").pvalue > 1e-3
+
+
+def test_gaussian_entries_independent_across_rows_and_columns():
+    """Sample correlations between neighbouring entries (within a Box-Muller pair, across
+    pairs, across rows) vanish: a reused word or a dropped sin/cos would correlate them."""
+    G = embedding.gaussian_normals(64, 4096, seed=5)
+    n = G.size / 2
+    for a, b in [(G[:, 0::4], G[:, 1::4]), (G[:, 1::4], G[:, 2::4]), (G[:-1], G[1:])]:
+        r = np.corrcoef(a.ravel(), b.ravel())[0, 1]
+        assert abs(r) < 6 / np.sqrt(min(a.size, n))
+
+
+def test_gaussian_embedding_is_isometric_in_expectation():
+    """E[Gamma^T Gamma] = I_m for i.i.d. N(0, 1/l) entries (Sec. 2.3, item 1): the
+    average over seeds of Gamma^T Gamma approaches the identity."""
+    l, m, S = 20, 12, 400
+    acc = np.zeros((m, m))
+    for s in range(S):
+        Gam = embedding.gaussian_embedding(l, m, seed=1000 + s)
+        acc += Gam.T @ Gam
+    acc /= S
+    assert np.max(np.abs(acc - np.eye(m))) < 6 * np.sqrt(2.0 / (l * S))
+
+
+def test_gaussian_is_a_function_of_seed_row_column():
+    """Regenerating a sub-block gives the same values (counter-based definition)."""
+    G = embedding.gaussian_normals(10, 37, seed=9)
+    G2 = embedding.gaussian_normals(10, 40, seed=9)
+    assert np.array_equal(G, G2[:, :37])
+    G3 = embedding.gaussian_normals(10, 37, seed=10)
+    assert not np.any(G == G3)
+
+
+def test_sparse_sign_columns():
+    """Every column has zeta distinct coordinates and values +-1/sqrt(zeta) (Sec. 2.3 item 3)."""
+    l, m, zeta = 40, 3000, 8
+    rows, signs = embedding.sparse_sign_pattern(l, m, zeta, seed=77)
+    assert rows.min() >= 0 and rows.max() < l
+    for j in range(m):
+        assert len(set(rows[j])) == zeta
+    Gam = embedding.sparse_sign_embedding(l, m, zeta, seed=77)
+    assert np.allclose(np.count_nonzero(Gam, axis=0), zeta)
+    assert np.allclose(np.abs(Gam[Gam != 0]), 1 / np.sqrt(zeta))
+    assert np.allclose(np.sum(Gam ** 2, axis=0), 1.0)
+
+
+def test_sparse_sign_coordinates_uniform_and_signs_balanced():
+    """Floyd's algorithm draws a uniform zeta-subset: every coordinate appears with
+    frequency zeta/l (chi-square), pairs are uniform too, and signs are fair."""
+    l, m, zeta = 16, 40000, 5
+    rows, signs = embedding.sparse_sign_pattern(l, m, zeta, seed=3)
+    counts = np.bincount(rows.ravel(), minlength=l)
+    assert stats.chisquare(counts).pvalue > 1e-4
+    pair = np.zeros((l, l))
+    for q1 in range(zeta):
+        for q2 in range(zeta):
+            if q1 != q2:
+                np.add.at(pair, (rows[:, q1], rows[:, q2]), 1)
+    off = pair[~np.eye(l, dtype=bool)]
+    assert stats.chisquare(off).pvalue > 1e-4
+    assert abs(signs.mean()) < 6 / np.sqrt(signs.size)
+
+
+def test_sparse_sign_full_column():
+    """zeta = l: every coordinate is taken exactly once."""
+    rows, _ = embedding.sparse_sign_pattern(8, 500, 8, seed=1)
+    assert np.all(np.sort(rows, axis=1) == np.arange(8)[None, :])
+
+
+def test_round_bf16_matches_torch():
+    """The oracle's bfloat16 rounding equals torch's (an independent routine)."""
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(100000) * 10.0 ** rng.integers(-20, 20, 100000),
+                        [0.0, -0.0, 1.0, 1.00390625, 1.005859375, 65504.0]])
+    want = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(embedding.round_bf16(x), want)
+
+
+def test_integer_sketch_is_exact_in_every_rounding():
+    """Small integers survive FP32 and BF16 rounding, so the sketch of an integer matrix by
+    a Rademacher-valued embedding is the exact integer product in every mode."""
+    rng = np.random.default_rng(4)
+    A = rng.integers(-8, 9, size=(50, 30)).astype(np.float64)
+    for mode in (None, "fp32", "bf16"):
+        Ar = A if mode is None else (embedding.round_fp32(A) if mode == "fp32" else embedding.round_bf16(A))
+        assert np.array_equal(Ar, A)
+    X = sketch.sparse_sign_sketch(A, l=16, zeta=16, seed=2) * 4.0     # entries +-1
+    assert np.array_equal(X, np.round(X))
+
+
+def test_sketch_scale_preserves_norms_in_expectation():
+    """E||Gamma A||_F^2 = ||A||_F^2 for both embeddings."""
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((200, 10))
+    vals_g, vals_s = [], []
+    for s in range(100):
+        vals_g.append(np.sum(sketch.gaussian_sketch(A, 30, seed=s) ** 2))
+        vals_s.append(np.sum(sketch.sparse_sign_sketch(A, 30, 8, seed=s) ** 2))
+    nA = np.sum(A ** 2)
+    assert abs(np.mean(vals_g) / nA - 1) < 0.05
+    assert abs(np.mean(vals_s) / nA - 1) < 0.05
