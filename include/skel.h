@@ -1,0 +1,211 @@
+/*
+ * skel.h -- C ABI of libskel, a GB300 (sm_103a) library for randomized-pivoting
+ * skeletonization: column interpolative decomposition (ID) and CUR decomposition by
+ * pivoting on a random sketch (Dong & Martinsson, "Simpler is better: a comparative study of
+ * randomized pivoting algorithms for CUR and interpolative decompositions", arXiv 2104.05877).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every matrix pointer is a DEVICE pointer owned by the caller; the library never frees
+ *    or retains it.  The library never allocates memory: each call that needs scratch memory
+ *    takes a caller-provided device workspace `ws` of `*ws_bytes` bytes.  Calling with
+ *    ws == NULL writes the required size to *ws_bytes and returns SKEL_OK without launching
+ *    anything.  A workspace smaller than required returns SKEL_ERR_WORKSPACE.  Workspace
+ *    must be 256-byte aligned.
+ *  - Tall matrices (A, C, Q: m rows) are COLUMN-MAJOR: element (i, j) at p[i + j*ld], ld >= m.
+ *    Wide matrices (the sketch X, pivot factors R, the ID matrix Z: l or s rows, n columns)
+ *    are ROW-MAJOR: element (r, j) at p[r*ld + j], ld >= n.  (So X^T is column-major n x l.)
+ *  - Indices are 0-based int32 (the paper's MATLAB indices are 1-based), in selection order.
+ *  - All work is enqueued on `stream` in stream order; no call synchronizes the host.
+ *    Argument errors are detected on the host and returned synchronously with nothing
+ *    launched.  Errors found on the device (non-finite data, a zero pivot, a timed-out grid
+ *    wait) are written to `dev_status` (device int32[2]: {code, step}; may be NULL), first
+ *    error wins; the caller reads it after synchronizing.  Device errors never trap.
+ *  - Random numbers: every entry of an embedding is a function of (seed, row, column) through
+ *    Philox-4x32-10 (Salmon et al., SC'11), so the same seed gives the same embedding in any
+ *    launch shape.
+ */
+#ifndef SKEL_H
+#define SKEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SKEL_OK = 0,
+  SKEL_ERR_INVALID_ARG = 1,    /* host-side argument check failed; nothing launched        */
+  SKEL_ERR_WORKSPACE = 2,      /* *ws_bytes smaller than required, or ws misaligned        */
+  SKEL_ERR_NONFINITE = 3,      /* device: NaN/Inf met in the data                          */
+  SKEL_ERR_RANK_DEFICIENT = 4, /* device: an exactly zero pivot; dev_status[1] = its step  */
+  SKEL_ERR_TIMEOUT = 5,        /* device: a grid-wide wait exceeded its limit              */
+  SKEL_ERR_CUDA = 6,           /* a CUDA runtime call failed (launch, attribute, memset)   */
+  SKEL_ERR_UNSUPPORTED = 7     /* valid request this build does not implement              */
+} skel_status;
+
+/* storage type of a matrix */
+typedef enum { SKEL_F64 = 0, SKEL_F32 = 1 } skel_dtype;
+
+/* arithmetic of the sketch product: operands rounded to this format, products accumulated
+ * in FP32 (FP64 for SKEL_PREC_F64). */
+typedef enum {
+  SKEL_PREC_F64 = 0,  /* plain: FP64 operands and accumulation (SIMT DFMA)                */
+  SKEL_PREC_F32 = 1,  /* FP32 operands and accumulation (SIMT FFMA)                       */
+  SKEL_PREC_TF32 = 2, /* tensor cores (tcgen05 kind::tf32), FP32 accumulate in TMEM       */
+  SKEL_PREC_BF16 = 3  /* tensor cores (tcgen05 kind::f16, bf16 operands), FP32 accumulate */
+} skel_prec;
+
+/* embedding Gamma (Sec. 2.3) */
+typedef enum {
+  SKEL_SKETCH_GAUSSIAN = 0,   /* i.i.d. N(0, 1/l) (Sec. 2.3, item 1)                        */
+  SKEL_SKETCH_SPARSE_SIGN = 1 /* zeta +-1/sqrt(zeta) per column at distinct rows (item 3)   */
+} skel_sketch_kind;
+
+const char* skel_status_string(int status);
+int skel_version(void);
+
+/*
+ * skel_sketch -- row sketch X = Gamma A of a dense A (Algorithm 1 line 2; Algorithm 2
+ * line 2; Table 1).
+ *   m, n      : A is m x n, column-major, leading dimension lda >= m, storage a_dtype.
+ *   l         : number of sketch rows (l = k + p, Sec. 2.3), 1 <= l <= 4096.
+ *   kind      : Gaussian (Gamma(i,j) = G(i,j)/sqrt(l), G from Philox + Box-Muller with
+ *               counter (j/4, i, 0, 0)) or sparse sign (zeta nonzeros per column, Floyd's
+ *               sampling from counters (j, 0, 1, c)); zeta is ignored for Gaussian.
+ *   prec      : arithmetic of the product (skel_prec).  SKEL_PREC_F64 requires
+ *               a_dtype = SKEL_F64 and writes X as FP64; every other precision reads A as
+ *               stored and writes X as FP32.  Sparse sign supports F64 and F32 only.
+ *   X, ldx    : output, l x n row-major (ldx >= n).
+ * The Gaussian entries are generated inside the kernel and never stored.  Non-finite
+ * entries of X set SKEL_ERR_NONFINITE in dev_status.
+ */
+skel_status skel_sketch(int64_t m, int64_t n, skel_dtype a_dtype, const void* A, int64_t lda,
+                        int32_t l, skel_sketch_kind kind, int32_t zeta, skel_prec prec,
+                        uint64_t seed, void* X, int64_t ldx, void* ws, size_t* ws_bytes,
+                        int32_t* dev_status, cudaStream_t stream);
+
+/*
+ * skel_sketch_csc -- X = Gamma A for a sparse A in compressed sparse column form (Table 1,
+ * T_s = O(nnz(A) zeta) for the sparse sign embedding).
+ *   col_ptr[n+1] (int64), row_idx[nnz] (int32, any order within a column), val[nnz] (FP32).
+ *   kind must be SKEL_SKETCH_SPARSE_SIGN or SKEL_SKETCH_GAUSSIAN.  X is FP32, l x n
+ *   row-major.
+ */
+skel_status skel_sketch_csc(int64_t m, int64_t n, int64_t nnz, const int64_t* col_ptr,
+                            const int32_t* row_idx, const float* val, int32_t l,
+                            skel_sketch_kind kind, int32_t zeta, uint64_t seed, float* X,
+                            int64_t ldx, void* ws, size_t* ws_bytes, int32_t* dev_status,
+                            cudaStream_t stream);
+
+/*
+ * skel_pivot_lupp -- column-wise LU with partial pivoting on X (Sec. 2.5.2, Eq. (LUPP);
+ * Algorithm 2 line 3), first s steps.  Step t picks j_t = argmax over unselected j of
+ * |S(t, j)| for the current Schur complement S (ties: lowest column index), then
+ * R(t, :) = S(t, :)/S(t, j_t) and S(t+1:, :) -= S(t+1:, j_t) R(t, :).  Only rows 0..s-1 of X
+ * are read.  Row pivoting of a tall C (Algorithm 2 line 4) is this call on C^T: pass the
+ * column-major m x s C as X with l = s, n = m, ldx = ldc.
+ *   dtype     : storage and arithmetic of X and of the factors (F64 or F32).
+ *   X, ldx    : l x n row-major input (not modified).  1 <= s <= min(l, n), s <= 1024.
+ *   Js        : out, int32[s], pivots in selection order.
+ *   L, ldl    : optional out (may be NULL), s x s lower triangular, row-major, L(r, t) =
+ *               S(r, j_t) at step t; X(0:s, :) = L R.
+ *   R, ldr    : optional out (may be NULL), s x n row-major, R(t, j_t) = 1, |R| <= 1.
+ * A zero pivot at step t sets SKEL_ERR_RANK_DEFICIENT with step t and writes Js[t..] = -1.
+ */
+skel_status skel_pivot_lupp(skel_dtype dtype, const void* X, int64_t l, int64_t n, int64_t ldx,
+                            int32_t s, int32_t* Js, void* L, int64_t ldl, void* R, int64_t ldr,
+                            void* ws, size_t* ws_bytes, int32_t* dev_status,
+                            cudaStream_t stream);
+
+/*
+ * skel_pivot_cpqr -- column pivoted Householder QR on X (Sec. 2.5.1, Eq. (QRCP)), first s
+ * steps: j_t = argmax of the remaining column norm over rows t..l-1 (kept by downdating,
+ * recomputed when cancellation exceeds sqrt(unit roundoff)), then a Householder reflector
+ * with beta = -sign(S(t, j_t)) ||S(t:, j_t)||.
+ *   X, ldx    : l x n row-major (all l rows are read).  1 <= s <= min(l, n), l <= 1024.
+ *   Js        : out int32[s].   R, ldr: optional s x n row-major, R(t, j_t) = beta_t.
+ */
+skel_status skel_pivot_cpqr(skel_dtype dtype, const void* X, int64_t l, int64_t n, int64_t ldx,
+                            int32_t s, int32_t* Js, void* R, int64_t ldr, void* ws,
+                            size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream);
+
+/*
+ * skel_id -- column ID A ~ C Z with C = A(:, Js) (Eq. (2.1)): Z = C^+ A = R_C^{-1} Q_C^T A,
+ * where C = Q_C R_C is a Householder QR (FP64 for dtype F64; FP32 for F32) and the s x s
+ * triangular solve is FP64.  Z(:, Js) = I.
+ *   A, lda    : m x n column-major, dtype F64 or F32.  Js: int32[s] device, distinct.
+ *   Z, ldz    : out, s x n row-major FP64 (ldz >= n).
+ *   sq_norms  : optional out (may be NULL), device double[2] = {||A||_F^2, ||Q_C^T A||_F^2};
+ *               their difference is ||A - C Z||_F^2 (orthogonal projection).
+ */
+skel_status skel_id(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
+                    int32_t s, const int32_t* Js, double* Z, int64_t ldz, double* sq_norms,
+                    void* ws, size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream);
+
+/*
+ * skel_cur -- CUR A ~ C U R (Eq. (2.4)) with rows Is from row-wise LUPP on C = A(:, Js)
+ * (Algorithm 2 line 4) and U from the stable form of Remark 3:
+ * U = R_C^{-1} (Q_C^T A Q_R) R_R^{-T}, where C = Q_C R_C and R^T = A(Is, :)^T = Q_R R_R.
+ *   Is        : out int32[s] row skeletons.   U, ldu: out s x s row-major FP64.
+ */
+skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
+                     int32_t s, const int32_t* Js, int32_t* Is, double* U, int64_t ldu,
+                     void* ws, size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream);
+
+/*
+ * skel_error -- Frobenius errors formed directly from the residuals, and Theorem 1's
+ * a-posteriori factor.
+ *   out[0] = ||A||_F
+ *   out[1] = ||A - A(:, Js) Z||_F                (if Z != NULL, else NaN)
+ *   out[2] = ||A - A(:, Js) U A(Is, :)||_F        (if U != NULL and Is != NULL, else NaN)
+ *   out[3] = eta = sqrt(1 + ||R_1^{-1} R_2||_2^2) (if Rf != NULL, else NaN), R_1 = Rf(:, Js),
+ *            R_2 = the other columns of the s x n pivot factor Rf (LUPP's R or CPQR's R).
+ *   out       : device double[4].
+ * Products use the storage precision of A (FP32 products, FP64 sums for F32 data).
+ */
+skel_status skel_error(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
+                       int32_t s, const int32_t* Js, const double* Z, int64_t ldz,
+                       const int32_t* Is, const double* U, int64_t ldu, skel_dtype rf_dtype,
+                       const void* Rf, int64_t ldrf, double* out, void* ws, size_t* ws_bytes,
+                       int32_t* dev_status, cudaStream_t stream);
+
+/*
+ * skel_debug_gaussian -- writes the standard normals G (l x m, row-major, ld = m) that the
+ * Gaussian sketch kernels generate, in FP32 (as_fp64 = 0) or FP64 (as_fp64 = 1).  For tests
+ * of the generator; the sketch kernels themselves never store G.
+ */
+skel_status skel_debug_gaussian(int32_t l, int64_t m, uint64_t seed, int as_fp64, void* G,
+                                cudaStream_t stream);
+
+/*
+ * skel_debug_philox -- raw Philox-4x32-10 words for `count` counters (uint32[count*4] in,
+ * uint32[count*4] out, device), key (k0, k1).  For tests of the generator.
+ */
+skel_status skel_debug_philox(const uint32_t* counters, int64_t count, uint32_t k0, uint32_t k1,
+                              uint32_t* out, cudaStream_t stream);
+
+/*
+ * skel_debug_curand_philox -- cuRAND's own device Philox4_32_10 stream (curand_init(seed,
+ * subsequence = i, offset 0), then per_seq calls of curand4) for i < nseq, written as
+ * uint32[nseq * per_seq * 4].  Lets tests compare this library's generator with cuRAND's.
+ */
+skel_status skel_debug_curand_philox(uint64_t seed, int64_t nseq, int per_seq, uint32_t* out,
+                                     cudaStream_t stream);
+
+/*
+ * skel_debug_grid_timeout -- launches `grid` co-resident CTAs on the grid-wide wait used by
+ * the persistent pivot and QR kernels, with CTA 0 never arriving, so every other CTA gives up
+ * after wait_ns nanoseconds (<= 5e9) and SKEL_ERR_TIMEOUT is written to dev_status.  Tests
+ * the failure path without hanging the device.  Workspace handshake as elsewhere.
+ */
+skel_status skel_debug_grid_timeout(int grid, uint64_t wait_ns, void* ws, size_t* ws_bytes,
+                                    int32_t* dev_status, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SKEL_H */

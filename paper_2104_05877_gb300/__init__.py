@@ -1,0 +1,288 @@
+"""Python binding of libskel (include/skel.h): randomized-pivoting skeletonization on GB300.
+
+Thin argument marshalling over the C ABI: torch tensors supply device memory and the current
+CUDA stream; every step of the computation runs in libskel's CUDA kernels.  There is no CPU
+path: without the built library (``python -m paper_2104_05877_gb300.build``) or without a
+CUDA device every call raises.
+
+Layouts (as in the C header): tall matrices (A, C, Q) are column-major (``t.stride(0) == 1``);
+wide matrices (the sketch X, pivot factors, Z) are row-major.  Indices are 0-based int32.
+"""
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libskel.so")
+
+F64, F32 = 0, 1
+PREC = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3}
+KIND = {"gaussian": 0, "sparse_sign": 1}
+STATUS = {0: "ok", 1: "invalid argument", 2: "workspace", 3: "non-finite", 4: "rank deficient",
+          5: "timeout", 6: "cuda error", 7: "unsupported"}
+
+_lib = None
+
+
+class SkelError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = int(code)
+        super().__init__(f"{where}: skel status {self.code} ({STATUS.get(self.code, '?')})")
+
+
+def lib():
+    """Load libskel.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libskel.so not built at {LIB_PATH}; run python -m paper_2104_05877_gb300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    i64, i32, u64, u32, vp, szp = (ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32,
+                                   ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t))
+    sig = {
+        "skel_sketch": [i64, i64, i32, vp, i64, i32, i32, i32, i32, u64, vp, i64, vp, szp, vp, vp],
+        "skel_sketch_csc": [i64, i64, i64, vp, vp, vp, i32, i32, i32, u64, vp, i64, vp, szp, vp, vp],
+        "skel_pivot_lupp": [i32, vp, i64, i64, i64, i32, vp, vp, i64, vp, i64, vp, szp, vp, vp],
+        "skel_pivot_cpqr": [i32, vp, i64, i64, i64, i32, vp, vp, i64, vp, szp, vp, vp],
+        "skel_id": [i64, i64, i32, vp, i64, i32, vp, vp, i64, vp, vp, szp, vp, vp],
+        "skel_cur": [i64, i64, i32, vp, i64, i32, vp, vp, vp, i64, vp, szp, vp, vp],
+        "skel_error": [i64, i64, i32, vp, i64, i32, vp, vp, i64, vp, vp, i64, i32, vp, i64, vp, vp,
+                       szp, vp, vp],
+        "skel_debug_gaussian": [i32, i64, u64, ctypes.c_int, vp, vp],
+        "skel_debug_philox": [vp, i64, u32, u32, vp, vp],
+        "skel_debug_curand_philox": [u64, i64, ctypes.c_int, vp, vp],
+        "skel_debug_grid_timeout": [ctypes.c_int, u64, vp, szp, vp, vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.skel_status_string.argtypes = [ctypes.c_int]
+    L.skel_status_string.restype = ctypes.c_char_p
+    L.skel_version.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+# ------------------------------------------------------------------------------------------
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dt(t):
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _colmajor(A):
+    """(tensor, ld) with A column-major; copies only when A is not already column-major."""
+    if A.dim() != 2:
+        raise ValueError("expected a matrix")
+    if A.stride(0) == 1 and (A.stride(1) >= max(1, A.shape[0]) or A.shape[1] <= 1):
+        return A, max(A.stride(1), A.shape[0], 1)
+    At = A.t().contiguous().t()
+    return At, max(At.shape[0], 1)
+
+
+def _rowmajor(X):
+    if X.dim() != 2:
+        raise ValueError("expected a matrix")
+    if X.stride(1) == 1 and (X.stride(0) >= max(1, X.shape[1]) or X.shape[0] <= 1):
+        return X, max(X.stride(0), X.shape[1], 1)
+    Xc = X.contiguous()
+    return Xc, max(Xc.shape[1], 1)
+
+
+def new_status(device=None):
+    return torch.zeros(2, dtype=torch.int32, device=device or "cuda")
+
+
+def check_status(dev_status, where=""):
+    """Synchronize and raise SkelError if a kernel recorded an error."""
+    code, step = (int(x) for x in dev_status.cpu())
+    if code != 0:
+        raise SkelError(code, f"{where} (step {step})")
+
+
+def _call(name, build_args, device):
+    """Two-phase call: workspace query, allocate, run.  build_args(ws_ptr, ws_size_ptr)."""
+    fn = getattr(lib(), name)
+    sz = ctypes.c_size_t(0)
+    rc = fn(*build_args(None, ctypes.byref(sz)))
+    if rc != 0:
+        raise SkelError(rc, name)
+    ws = torch.empty(max(int(sz.value), 1), dtype=torch.uint8, device=device)
+    rc = fn(*build_args(_ptr(ws), ctypes.byref(sz)))
+    if rc != 0:
+        raise SkelError(rc, name)
+    return ws
+
+
+# ------------------------------------------------------------------------------------------
+def sketch(A, l, kind="gaussian", prec="f32", seed=0, zeta=8, X=None, status=None):
+    """X = Gamma A (l x n, row-major): FP64 for prec='f64', FP32 otherwise."""
+    A, lda = _colmajor(A)
+    m, n = A.shape
+    xdt = torch.float64 if prec == "f64" else torch.float32
+    if X is None:
+        X = torch.empty(l, n, dtype=xdt, device=A.device)
+    X, ldx = _rowmajor(X)
+    st = status if status is not None else new_status(A.device)
+    _call("skel_sketch", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, l, KIND[kind], zeta, PREC[prec],
+                                        seed, _ptr(X), ldx, w, sz, _ptr(st), _stream()], A.device)
+    return X, st
+
+
+def sketch_csc(col_ptr, row_idx, val, m, n, l, kind="sparse_sign", seed=0, zeta=8, status=None):
+    X = torch.empty(l, n, dtype=torch.float32, device=val.device)
+    st = status if status is not None else new_status(val.device)
+    nnz = val.numel()
+    _call("skel_sketch_csc", lambda w, sz: [m, n, nnz, _ptr(col_ptr), _ptr(row_idx), _ptr(val), l,
+                                            KIND[kind], zeta, seed, _ptr(X), n, w, sz, _ptr(st),
+                                            _stream()], val.device)
+    return X, st
+
+
+def pivot_lupp(X, s, factors=True, status=None):
+    """Column-wise LUPP on X (l x n row-major): Js (s,), and optionally L (s x s), R (s x n)."""
+    X, ldx = _rowmajor(X)
+    l, n = X.shape
+    Js = torch.empty(s, dtype=torch.int32, device=X.device)
+    Lf = torch.empty(s, s, dtype=X.dtype, device=X.device) if factors else None
+    Rf = torch.empty(s, n, dtype=X.dtype, device=X.device) if factors else None
+    st = status if status is not None else new_status(X.device)
+    _call("skel_pivot_lupp", lambda w, sz: [_dt(X), _ptr(X), l, n, ldx, s, _ptr(Js), _ptr(Lf), s,
+                                            _ptr(Rf), n, w, sz, _ptr(st), _stream()], X.device)
+    return Js, Lf, Rf, st
+
+
+def pivot_lupp_rows(C, s, status=None):
+    """Row-wise LUPP on a tall C (m x s', column-major): the row skeletons Is."""
+    C, ldc = _colmajor(C)
+    m, sc = C.shape
+    Is = torch.empty(s, dtype=torch.int32, device=C.device)
+    st = status if status is not None else new_status(C.device)
+    _call("skel_pivot_lupp", lambda w, sz: [_dt(C), _ptr(C), sc, m, ldc, s, _ptr(Is), None, 0, None,
+                                            0, w, sz, _ptr(st), _stream()], C.device)
+    return Is, st
+
+
+def pivot_cpqr(X, s, factors=True, status=None):
+    X, ldx = _rowmajor(X)
+    l, n = X.shape
+    Js = torch.empty(s, dtype=torch.int32, device=X.device)
+    Rf = torch.empty(s, n, dtype=X.dtype, device=X.device) if factors else None
+    st = status if status is not None else new_status(X.device)
+    _call("skel_pivot_cpqr", lambda w, sz: [_dt(X), _ptr(X), l, n, ldx, s, _ptr(Js), _ptr(Rf), n, w,
+                                            sz, _ptr(st), _stream()], X.device)
+    return Js, Rf, st
+
+
+def column_id(A, Js, status=None):
+    """Z (s x n, FP64, row-major) with A ~ A(:, Js) Z, and [||A||_F^2, ||Q_C^T A||_F^2]."""
+    A, lda = _colmajor(A)
+    m, n = A.shape
+    s = Js.numel()
+    Z = torch.empty(s, n, dtype=torch.float64, device=A.device)
+    sq = torch.empty(2, dtype=torch.float64, device=A.device)
+    st = status if status is not None else new_status(A.device)
+    _call("skel_id", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, s, _ptr(Js), _ptr(Z), n, _ptr(sq), w,
+                                    sz, _ptr(st), _stream()], A.device)
+    return Z, sq, st
+
+
+def cur(A, Js, status=None):
+    """Is (row skeletons by LUPP on C) and U (s x s FP64) with A ~ A(:, Js) U A(Is, :)."""
+    A, lda = _colmajor(A)
+    m, n = A.shape
+    s = Js.numel()
+    Is = torch.empty(s, dtype=torch.int32, device=A.device)
+    U = torch.empty(s, s, dtype=torch.float64, device=A.device)
+    st = status if status is not None else new_status(A.device)
+    _call("skel_cur", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, s, _ptr(Js), _ptr(Is), _ptr(U), s, w,
+                                     sz, _ptr(st), _stream()], A.device)
+    return Is, U, st
+
+
+def error(A, Js=None, Z=None, Is=None, U=None, Rf=None, status=None):
+    """Device double[4] = [||A||_F, ||A - CZ||_F, ||A - CUR||_F, eta] (NaN where not asked)."""
+    A, lda = _colmajor(A)
+    m, n = A.shape
+    s = 0 if Js is None else Js.numel()
+    out = torch.empty(4, dtype=torch.float64, device=A.device)
+    st = status if status is not None else new_status(A.device)
+    if Rf is not None:
+        Rf, ldrf = _rowmajor(Rf)
+        rdt = _dt(Rf)
+    else:
+        ldrf, rdt = 0, F64
+    ldz = 0 if Z is None else _rowmajor(Z)[1]
+    _call("skel_error", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, s, _ptr(Js), _ptr(Z), ldz, _ptr(Is),
+                                       _ptr(U), s, rdt, _ptr(Rf), ldrf, _ptr(out), w, sz, _ptr(st),
+                                       _stream()], A.device)
+    return out, st
+
+
+def debug_gaussian(l, m, seed, fp64=False, device="cuda"):
+    G = torch.empty(l, m, dtype=torch.float64 if fp64 else torch.float32, device=device)
+    rc = lib().skel_debug_gaussian(l, m, seed, int(fp64), _ptr(G), _stream())
+    if rc != 0:
+        raise SkelError(rc, "skel_debug_gaussian")
+    return G
+
+
+def debug_philox(counters, k0, k1):
+    """counters: int64/uint32-valued tensor (N, 4) on the device -> (N, 4) int64 words."""
+    c = counters.to(torch.int64).to(torch.int32)   # two's complement bit patterns
+    out = torch.empty_like(c)
+    rc = lib().skel_debug_philox(_ptr(c), c.shape[0], k0, k1, _ptr(out), _stream())
+    if rc != 0:
+        raise SkelError(rc, "skel_debug_philox")
+    return out.to(torch.int64) & 0xFFFFFFFF
+
+
+def debug_curand_philox(seed, nseq, per_seq, device="cuda"):
+    out = torch.empty(nseq * per_seq * 4, dtype=torch.int32, device=device)
+    rc = lib().skel_debug_curand_philox(seed, nseq, per_seq, _ptr(out), _stream())
+    if rc != 0:
+        raise SkelError(rc, "skel_debug_curand_philox")
+    return (out.to(torch.int64) & 0xFFFFFFFF).reshape(nseq, per_seq, 4)
+
+
+def debug_grid_timeout(grid, wait_ns, device="cuda"):
+    """Runs a grid-wide wait that cannot complete; returns the device status tensor."""
+    st = new_status(device)
+    _call("skel_debug_grid_timeout", lambda w, sz: [grid, wait_ns, w, sz, _ptr(st), _stream()], device)
+    return st
+
+
+def skeletonize(A, k, p=10, seed=0, prec="f32", pivot="lupp", kind="gaussian", zeta=8,
+                want_cur=True, want_error=True):
+    """Algorithm 2 end to end on the device: sketch -> pivots on X -> column ID (-> rows by
+    LUPP on C, CUR) (-> errors and eta).  Returns a dict of device tensors."""
+    st = new_status(A.device)
+    l = k + p
+    X, _ = sketch(A, l, kind=kind, prec=prec, seed=seed, zeta=zeta, status=st)
+    if pivot == "lupp":
+        Js, _, Rf, _ = pivot_lupp(X, k, status=st)
+    else:
+        Js, Rf, _ = pivot_cpqr(X, k, status=st)
+    Z, sq, _ = column_id(A, Js, status=st)
+    out = dict(X=X, Js=Js, Rf=Rf, Z=Z, sq_norms=sq, status=st)
+    if want_cur:
+        Is, U, _ = cur(A, Js, status=st)
+        out.update(Is=Is, U=U)
+    if want_error:
+        e, _ = error(A, Js, Z, out.get("Is"), out.get("U"), Rf, status=st)
+        out["errors"] = e
+    return out

@@ -1,0 +1,390 @@
+// C ABI entry points of libskel (include/skel.h): argument checks, workspace planning and
+// stream-ordered launches.  No entry point allocates memory or synchronizes the host.
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace skel;
+
+namespace {
+
+// Carves 256-byte aligned regions out of the caller's workspace.  The same sequence of
+// take() calls runs once to size the workspace (base == nullptr) and once to use it.
+struct Arena {
+  char* base;
+  size_t off = 0;
+  explicit Arena(void* b) : base(static_cast<char*>(b)) {}
+  void* take(size_t bytes) {
+    void* p = base ? base + off : nullptr;
+    off += align_up(bytes);
+    return p;
+  }
+};
+
+#define SK_CUDA(x)                                 \
+  do {                                             \
+    if ((x) != cudaSuccess) return SKEL_ERR_CUDA;  \
+  } while (0)
+#define SK_TRY(x)                      \
+  do {                                 \
+    skel_status _s = (x);              \
+    if (_s != SKEL_OK) return _s;      \
+  } while (0)
+
+size_t esize(skel_dtype dt) { return dt == SKEL_F64 ? 8 : 4; }
+bool valid_dtype(skel_dtype dt) { return dt == SKEL_F64 || dt == SKEL_F32; }
+
+// Common workspace handshake: returns true when the call should stop here (size query or
+// error); *st receives the status to return.
+bool ws_handshake(size_t need, void* ws, size_t* ws_bytes, skel_status* st) {
+  if (ws_bytes == nullptr) { *st = SKEL_ERR_INVALID_ARG; return true; }
+  if (ws == nullptr) {
+    *ws_bytes = need;
+    *st = SKEL_OK;
+    return true;
+  }
+  if (*ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0) {
+    *st = SKEL_ERR_WORKSPACE;
+    return true;
+  }
+  return false;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* skel_status_string(int status) {
+  switch (status) {
+    case SKEL_OK: return "ok";
+    case SKEL_ERR_INVALID_ARG: return "invalid argument";
+    case SKEL_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case SKEL_ERR_NONFINITE: return "non-finite value in the data";
+    case SKEL_ERR_RANK_DEFICIENT: return "zero pivot (rank deficient)";
+    case SKEL_ERR_TIMEOUT: return "grid-wide wait timed out";
+    case SKEL_ERR_CUDA: return "CUDA runtime error";
+    case SKEL_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+int skel_version(void) { return 100; }
+
+// ------------------------------------------------------------------------------------
+skel_status skel_sketch(int64_t m, int64_t n, skel_dtype a_dtype, const void* A, int64_t lda,
+                        int32_t l, skel_sketch_kind kind, int32_t zeta, skel_prec prec,
+                        uint64_t seed, void* X, int64_t ldx, void* ws, size_t* ws_bytes,
+                        int32_t* dev_status, cudaStream_t stream) {
+  if (m < 0 || n < 0 || l < 1 || l > 4096 || !valid_dtype(a_dtype)) return SKEL_ERR_INVALID_ARG;
+  if (lda < std::max<int64_t>(1, m) || ldx < std::max<int64_t>(1, n)) return SKEL_ERR_INVALID_ARG;
+  if ((m > 0 && n > 0 && A == nullptr) || (n > 0 && X == nullptr)) return SKEL_ERR_INVALID_ARG;
+  if (m > 0xFFFFFFFFll || n > 0xFFFFFFFFll) return SKEL_ERR_INVALID_ARG;
+  if (prec < SKEL_PREC_F64 || prec > SKEL_PREC_BF16) return SKEL_ERR_INVALID_ARG;
+  if (prec == SKEL_PREC_F64 && a_dtype != SKEL_F64) return SKEL_ERR_INVALID_ARG;
+  if (kind != SKEL_SKETCH_GAUSSIAN && kind != SKEL_SKETCH_SPARSE_SIGN) return SKEL_ERR_INVALID_ARG;
+  const skel_dtype x_dt = prec == SKEL_PREC_F64 ? SKEL_F64 : SKEL_F32;
+  Arena ar(ws);
+  int32_t* table = nullptr;
+  if (kind == SKEL_SKETCH_SPARSE_SIGN) {
+    if (zeta < 1 || zeta > 31 || zeta > l) return SKEL_ERR_INVALID_ARG;
+    if (prec == SKEL_PREC_TF32 || prec == SKEL_PREC_BF16) return SKEL_ERR_UNSUPPORTED;
+    if (esize(x_dt) * (size_t)l * 32 + 4 * 256 * (size_t)zeta > 220 * 1024) return SKEL_ERR_UNSUPPORTED;
+    if (prec == SKEL_PREC_F32 && a_dtype != SKEL_F32) return SKEL_ERR_UNSUPPORTED;
+    table = static_cast<int32_t*>(ar.take(sparse_pattern_bytes(m, zeta)));
+  }
+  skel_status st;
+  if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+  if (n == 0) return SKEL_OK;
+  if (kind == SKEL_SKETCH_SPARSE_SIGN) {
+    if (m == 0) {
+      for (int32_t r = 0; r < l; ++r)
+        SK_CUDA(cudaMemsetAsync(static_cast<char*>(X) + esize(x_dt) * r * ldx, 0, esize(x_dt) * n, stream));
+      return SKEL_OK;
+    }
+    SK_CUDA(launch_sparse_pattern(m, l, zeta, seed, table, stream));
+    SK_CUDA(launch_sparse_sketch_dense(m, n, a_dtype, A, lda, l, zeta, table, X, ldx, dev_status, stream));
+    return SKEL_OK;
+  }
+  if (prec == SKEL_PREC_BF16 || prec == SKEL_PREC_TF32) {
+    if (a_dtype != SKEL_F32) return SKEL_ERR_UNSUPPORTED;
+    const cudaError_t e = launch_sketch_tc(m, n, static_cast<const float*>(A), lda, l, prec, seed,
+                                           static_cast<float*>(X), ldx, dev_status, stream);
+    if (e == cudaErrorNotSupported) return SKEL_ERR_UNSUPPORTED;
+    SK_CUDA(e);
+    return SKEL_OK;
+  }
+  GemmArgs a{};
+  a.M = l; a.N = n; a.K = m;
+  a.B = View{A, 1, lda}; a.b_dt = a_dtype;
+  a.out = X; a.out_sr = ldx; a.out_sc = 1; a.out_dt = x_dt;
+  a.alpha = 1.0 / std::sqrt((double)l);
+  a.seed = seed;
+  a.dev_status = dev_status;
+  SK_CUDA(launch_gemm(a, prec == SKEL_PREC_F64, LEFT_GAUSSIAN, EPI_SKETCH, stream));
+  return SKEL_OK;
+}
+
+skel_status skel_sketch_csc(int64_t m, int64_t n, int64_t nnz, const int64_t* col_ptr,
+                            const int32_t* row_idx, const float* val, int32_t l,
+                            skel_sketch_kind kind, int32_t zeta, uint64_t seed, float* X,
+                            int64_t ldx, void* ws, size_t* ws_bytes, int32_t* dev_status,
+                            cudaStream_t stream) {
+  if (m < 0 || n < 0 || nnz < 0 || l < 1 || l > 4096) return SKEL_ERR_INVALID_ARG;
+  if (m > 0x7FFFFFFFll || n > 0xFFFFFFFFll) return SKEL_ERR_INVALID_ARG;
+  if (ldx < std::max<int64_t>(1, n) || (n > 0 && (X == nullptr || col_ptr == nullptr)))
+    return SKEL_ERR_INVALID_ARG;
+  if (nnz > 0 && (row_idx == nullptr || val == nullptr)) return SKEL_ERR_INVALID_ARG;
+  Arena ar(ws);
+  int32_t* table = nullptr;
+  if (kind == SKEL_SKETCH_SPARSE_SIGN) {
+    if (zeta < 1 || zeta > 31 || zeta > l) return SKEL_ERR_INVALID_ARG;
+    if (sizeof(float) * (size_t)l * 32 > 220 * 1024) return SKEL_ERR_UNSUPPORTED;
+    table = static_cast<int32_t*>(ar.take(sparse_pattern_bytes(m, zeta)));
+  } else if (kind != SKEL_SKETCH_GAUSSIAN) {
+    return SKEL_ERR_INVALID_ARG;
+  }
+  skel_status st;
+  if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+  if (n == 0) return SKEL_OK;
+  if (kind == SKEL_SKETCH_SPARSE_SIGN) {
+    SK_CUDA(launch_sparse_pattern(m, l, zeta, seed, table, stream));
+    SK_CUDA(launch_sparse_sketch_csc(m, n, col_ptr, row_idx, val, l, zeta, table, X, ldx, dev_status, stream));
+  } else {
+    SK_CUDA(launch_gauss_sketch_csc(m, n, col_ptr, row_idx, val, l, seed, X, ldx, dev_status, stream));
+  }
+  return SKEL_OK;
+}
+
+// ------------------------------------------------------------------------------------
+skel_status skel_pivot_lupp(skel_dtype dtype, const void* X, int64_t l, int64_t n, int64_t ldx,
+                            int32_t s, int32_t* Js, void* L, int64_t ldl, void* R, int64_t ldr,
+                            void* ws, size_t* ws_bytes, int32_t* dev_status,
+                            cudaStream_t stream) {
+  if (!valid_dtype(dtype) || X == nullptr || Js == nullptr) return SKEL_ERR_INVALID_ARG;
+  if (s < 1 || s > kMaxS || s > l || s > n || n > 0x7FFFFFFFll) return SKEL_ERR_INVALID_ARG;
+  if (ldx < n || (L && ldl < s) || (R && ldr < n)) return SKEL_ERR_INVALID_ARG;
+  const size_t need = lupp_workspace(dtype, n, s, nullptr);
+  skel_status st;
+  if (ws_handshake(need, ws, ws_bytes, &st)) return st;
+  return run_lupp(dtype, X, n, ldx, s, Js, L, ldl, R, ldr, ws, *ws_bytes, dev_status, stream);
+}
+
+skel_status skel_pivot_cpqr(skel_dtype dtype, const void* X, int64_t l, int64_t n, int64_t ldx,
+                            int32_t s, int32_t* Js, void* R, int64_t ldr, void* ws,
+                            size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  if (!valid_dtype(dtype) || X == nullptr || Js == nullptr) return SKEL_ERR_INVALID_ARG;
+  if (s < 1 || l > kMaxS || s > l || s > n || n > 0x7FFFFFFFll) return SKEL_ERR_INVALID_ARG;
+  if (ldx < n || (R && ldr < n)) return SKEL_ERR_INVALID_ARG;
+  const size_t need = cpqr_workspace(dtype, l, n, s, nullptr);
+  skel_status st;
+  if (ws_handshake(need, ws, ws_bytes, &st)) return st;
+  return run_cpqr(dtype, X, l, n, ldx, s, Js, R, ldr, ws, *ws_bytes, dev_status, stream);
+}
+
+// ------------------------------------------------------------------------------------
+namespace {
+
+bool id_args_ok(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda, int32_t s,
+                const int32_t* Js) {
+  return valid_dtype(dtype) && A && Js && m >= 1 && n >= 1 && s >= 1 && s <= kMaxS && s <= m &&
+         s <= n && lda >= m;
+}
+
+// C = A(:, Js); C = Q R.  Returns device pointers through the arena.
+skel_status skeleton_qr(Arena& ar, bool run, int64_t m, skel_dtype dt, const void* A, int64_t lda,
+                        int32_t s, const int32_t* idx, void** C, void** Q, double** R,
+                        int32_t* dev_status, cudaStream_t st) {
+  *C = ar.take(esize(dt) * (size_t)m * s);
+  *Q = ar.take(esize(dt) * (size_t)m * s);
+  *R = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
+  const size_t qn = qr_workspace(dt, m, s);
+  void* qws = ar.take(qn);
+  if (!run) return SKEL_OK;
+  SK_CUDA(launch_gather_cols(m, s, dt, A, lda, idx, *C, m, st));
+  return run_qr(dt, *C, m, m, s, *Q, m, *R, s, qws, qn, dev_status, st);
+}
+
+}  // namespace
+
+skel_status skel_id(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
+                    int32_t s, const int32_t* Js, double* Z, int64_t ldz, double* sq_norms,
+                    void* ws, size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  if (!id_args_ok(m, n, dtype, A, lda, s, Js) || Z == nullptr || ldz < n) return SKEL_ERR_INVALID_ARG;
+  const bool f64 = dtype == SKEL_F64;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool run = pass == 1;
+    Arena ar(run ? ws : nullptr);
+    void *C, *Q;
+    double* R;
+    SK_TRY(skeleton_qr(ar, run, m, dtype, A, lda, s, Js, &C, &Q, &R, dev_status, stream));
+    void* W = ar.take(esize(dtype) * (size_t)s * n);
+    const int64_t nbw = gemm_num_blocks(s, n);
+    double* pw = static_cast<double*>(ar.take(sizeof(double) * nbw));
+    const int64_t nba = sqnorm_num_blocks(m, n);
+    double* pa = static_cast<double*>(ar.take(sizeof(double) * nba));
+    if (!run) {
+      skel_status st;
+      if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+      continue;
+    }
+    GemmArgs g{};
+    g.M = s; g.N = n; g.K = m;
+    g.L = View{Q, m, 1}; g.l_dt = dtype;          // Q^T(r, i) = Q(i, r)
+    g.B = View{A, 1, lda}; g.b_dt = dtype;
+    g.out = W; g.out_sr = n; g.out_sc = 1; g.out_dt = dtype;
+    g.alpha = 1.0;
+    g.partials = pw;
+    SK_CUDA(launch_gemm(g, f64, LEFT_LOAD, EPI_STORE_SQ, stream));
+    SK_CUDA(launch_trsm_upper(s, n, R, s, 0, dtype, W, n, Z, ldz, stream));
+    if (sq_norms) {
+      SK_CUDA(launch_sqnorm(m, n, dtype, A, lda, pa, stream));
+      SK_CUDA(launch_reduce_sum(pa, nba, sq_norms, 0, stream));
+      SK_CUDA(launch_reduce_sum(pw, nbw, sq_norms + 1, 0, stream));
+    }
+  }
+  return SKEL_OK;
+}
+
+skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
+                     int32_t s, const int32_t* Js, int32_t* Is, double* U, int64_t ldu,
+                     void* ws, size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  if (!id_args_ok(m, n, dtype, A, lda, s, Js) || Is == nullptr || U == nullptr || ldu < s)
+    return SKEL_ERR_INVALID_ARG;
+  const bool f64 = dtype == SKEL_F64;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool run = pass == 1;
+    Arena ar(run ? ws : nullptr);
+    void *C, *Qc, *Rt, *Qr;
+    double *Rc, *Rr;
+    SK_TRY(skeleton_qr(ar, run, m, dtype, A, lda, s, Js, &C, &Qc, &Rc, dev_status, stream));
+    const size_t lw = lupp_workspace(dtype, m, s, nullptr);
+    void* lws = ar.take(lw);
+    Rt = ar.take(esize(dtype) * (size_t)n * s);
+    Qr = ar.take(esize(dtype) * (size_t)n * s);
+    Rr = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
+    const size_t qn = qr_workspace(dtype, n, s);
+    void* qws = ar.take(qn);
+    void* W = ar.take(esize(dtype) * (size_t)s * n);
+    double* M = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
+    double* T1 = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
+    double* T2 = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
+    if (!run) {
+      skel_status st;
+      if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+      continue;
+    }
+    // rows by LUPP on C (Algorithm 2 line 4): C column-major m x s is C^T row-major s x m
+    SK_TRY(run_lupp(dtype, C, m, m, s, Is, nullptr, 0, nullptr, 0, lws, lw, dev_status, stream));
+    SK_CUDA(launch_gather_rows_t(n, s, dtype, A, lda, Is, Rt, n, stream));
+    SK_TRY(run_qr(dtype, Rt, n, n, s, Qr, n, Rr, s, qws, qn, dev_status, stream));
+    GemmArgs g{};
+    g.M = s; g.N = n; g.K = m;
+    g.L = View{Qc, m, 1}; g.l_dt = dtype;
+    g.B = View{A, 1, lda}; g.b_dt = dtype;
+    g.out = W; g.out_sr = n; g.out_sc = 1; g.out_dt = dtype;
+    g.alpha = 1.0;
+    SK_CUDA(launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, stream));
+    GemmArgs h{};
+    h.M = s; h.N = s; h.K = n;
+    h.L = View{W, n, 1}; h.l_dt = dtype;
+    h.B = View{Qr, 1, n}; h.b_dt = dtype;
+    h.out = M; h.out_sr = s; h.out_sc = 1; h.out_dt = SKEL_F64;
+    h.alpha = 1.0;
+    SK_CUDA(launch_gemm(h, f64, LEFT_LOAD, EPI_STORE, stream));
+    // U = R_C^{-1} M R_R^{-T} = (R_R^{-1} (R_C^{-1} M)^T)^T
+    SK_CUDA(launch_trsm_upper(s, s, Rc, s, 0, SKEL_F64, M, s, T1, s, stream));
+    SK_CUDA(launch_transpose_f64(s, T1, s, T2, s, stream));
+    SK_CUDA(launch_trsm_upper(s, s, Rr, s, 0, SKEL_F64, T2, s, T1, s, stream));
+    SK_CUDA(launch_transpose_f64(s, T1, s, U, ldu, stream));
+  }
+  return SKEL_OK;
+}
+
+skel_status skel_error(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
+                       int32_t s, const int32_t* Js, const double* Z, int64_t ldz,
+                       const int32_t* Is, const double* U, int64_t ldu, skel_dtype rf_dtype,
+                       const void* Rf, int64_t ldrf, double* out, void* ws, size_t* ws_bytes,
+                       int32_t* dev_status, cudaStream_t stream) {
+  if (!valid_dtype(dtype) || A == nullptr || out == nullptr || m < 1 || n < 1 || lda < m)
+    return SKEL_ERR_INVALID_ARG;
+  const bool need_js = Z || U || Rf;
+  if (need_js && (Js == nullptr || s < 1 || s > kMaxS || s > m || s > n)) return SKEL_ERR_INVALID_ARG;
+  if ((Z && ldz < n) || (U && (ldu < s || Is == nullptr)) || (Rf && (!valid_dtype(rf_dtype) || ldrf < n)))
+    return SKEL_ERR_INVALID_ARG;
+  const bool f64 = dtype == SKEL_F64;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool run = pass == 1;
+    Arena ar(run ? ws : nullptr);
+    const int64_t nba = sqnorm_num_blocks(m, n);
+    double* pa = static_cast<double*>(ar.take(sizeof(double) * nba));
+    void* C = need_js ? ar.take(esize(dtype) * (size_t)m * s) : nullptr;
+    const int64_t nbr = gemm_num_blocks(m, n);
+    double* pr = static_cast<double*>(ar.take(sizeof(double) * nbr));
+    void* P = U ? ar.take(esize(dtype) * (size_t)m * s) : nullptr;
+    void* Rt = U ? ar.take(esize(dtype) * (size_t)n * s) : nullptr;
+    double* H = Rf ? static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s)) : nullptr;
+    double* R1 = Rf ? static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s)) : nullptr;
+    double* M1 = Rf ? static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s)) : nullptr;
+    double* M2 = Rf ? static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s)) : nullptr;
+    double* pscr = Rf ? static_cast<double*>(ar.take(sizeof(double) * (16 + 2 * (size_t)s * s))) : nullptr;
+    if (!run) {
+      skel_status st;
+      if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+      continue;
+    }
+    SK_CUDA(launch_fill_f64(out, 4, NAN, stream));
+    SK_CUDA(launch_sqnorm(m, n, dtype, A, lda, pa, stream));
+    SK_CUDA(launch_reduce_sum(pa, nba, out + 0, 1, stream));
+    if (need_js) SK_CUDA(launch_gather_cols(m, s, dtype, A, lda, Js, C, m, stream));
+    if (Z) {
+      GemmArgs g{};
+      g.M = m; g.N = n; g.K = s;
+      g.L = View{C, 1, m}; g.l_dt = dtype;
+      g.B = View{Z, ldz, 1}; g.b_dt = SKEL_F64;
+      g.ref = View{A, 1, lda}; g.ref_dt = dtype;
+      g.alpha = 1.0;
+      g.partials = pr;
+      SK_CUDA(launch_gemm(g, f64, LEFT_LOAD, EPI_RESID, stream));
+      SK_CUDA(launch_reduce_sum(pr, nbr, out + 1, 1, stream));
+    }
+    if (U) {
+      GemmArgs g{};
+      g.M = m; g.N = s; g.K = s;
+      g.L = View{C, 1, m}; g.l_dt = dtype;
+      g.B = View{U, ldu, 1}; g.b_dt = SKEL_F64;
+      g.out = P; g.out_sr = 1; g.out_sc = m; g.out_dt = dtype;
+      g.alpha = 1.0;
+      SK_CUDA(launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, stream));
+      SK_CUDA(launch_gather_rows_t(n, s, dtype, A, lda, Is, Rt, n, stream));
+      GemmArgs h{};
+      h.M = m; h.N = n; h.K = s;
+      h.L = View{P, 1, m}; h.l_dt = dtype;
+      h.B = View{Rt, n, 1}; h.b_dt = dtype;          // R(r, c) = Rt[c + r*n]
+      h.ref = View{A, 1, lda}; h.ref_dt = dtype;
+      h.alpha = 1.0;
+      h.partials = pr;
+      SK_CUDA(launch_gemm(h, f64, LEFT_LOAD, EPI_RESID, stream));
+      SK_CUDA(launch_reduce_sum(pr, nbr, out + 2, 1, stream));
+    }
+    if (Rf) {
+      // eta^2 = lambda_max(R_1^{-1} (R R^T) R_1^{-T}) = 1 + ||R_1^{-1} R_2||_2^2
+      GemmArgs g{};
+      g.M = s; g.N = s; g.K = n;
+      g.L = View{Rf, ldrf, 1}; g.l_dt = rf_dtype;
+      g.B = View{Rf, 1, ldrf}; g.b_dt = rf_dtype;
+      g.out = H; g.out_sr = s; g.out_sc = 1; g.out_dt = SKEL_F64;
+      g.alpha = 1.0;
+      SK_CUDA(launch_gemm(g, true, LEFT_LOAD, EPI_STORE, stream));
+      SK_CUDA(launch_gather_cols_rowmajor_f64(s, rf_dtype, Rf, ldrf, Js, R1, s, stream));
+      SK_CUDA(launch_trsm_upper(s, s, R1, s, 0, SKEL_F64, H, s, M1, s, stream));
+      SK_CUDA(launch_transpose_f64(s, M1, s, M2, s, stream));
+      SK_CUDA(launch_trsm_upper(s, s, R1, s, 0, SKEL_F64, M2, s, M1, s, stream));
+      SK_CUDA(launch_power_sqrt_lmax(s, M1, s, out + 3, pscr, stream));
+    }
+  }
+  return SKEL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,244 @@
+// Shared device utilities of libskel: the counter-based generator, Box-Muller transform,
+// device error recording and a bounded grid-wide all-gather for persistent kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/skel.h"
+
+namespace skel {
+
+constexpr int kMaxS = 1024;            // largest pivot count / panel width handled
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;   // grid-wide wait limit: 2 s
+
+// ------------------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of
+//   (hi0,lo0) = M0*c0, (hi1,lo1) = M1*c2, c' = (hi1^c1^k0, lo1, hi0^c3^k1, lo0),
+// with the key bumped by the Weyl constants between rounds.
+// ------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = mulhi32(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = mulhi32(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+constexpr uint32_t kTagGaussian = 0;
+constexpr uint32_t kTagSparse = 1;
+
+// u = (2*(x >> 9) + 1) * 2^-24: exact in FP32, in [2^-24, 1 - 2^-24].
+__device__ __forceinline__ float unit_open_f32(uint32_t x) {
+  return __uint2float_rn(((x >> 9) << 1) | 1u) * 5.9604644775390625e-8f;
+}
+__device__ __forceinline__ double unit_open_f64(uint32_t x) {
+  return (double)(((x >> 9) << 1) | 1u) * 5.9604644775390625e-8;
+}
+
+// Box-Muller: (sqrt(-2 ln u1) cos 2 pi u2, sqrt(-2 ln u1) sin 2 pi u2).
+__device__ __forceinline__ float2 box_muller_f32(uint32_t a, uint32_t b) {
+  const float r = sqrtf(-2.0f * logf(unit_open_f32(a)));
+  float s, c;
+  sincospif(2.0f * unit_open_f32(b), &s, &c);
+  return make_float2(r * c, r * s);
+}
+__device__ __forceinline__ double2 box_muller_f64(uint32_t a, uint32_t b) {
+  const double r = sqrt(-2.0 * log(unit_open_f64(a)));
+  double s, c;
+  sincospi(2.0 * unit_open_f64(b), &s, &c);
+  return make_double2(r * c, r * s);
+}
+
+// Standard normals G(i, 4*j4 .. 4*j4+3) of the Gaussian embedding (Gamma = G / sqrt(l)).
+__device__ __forceinline__ float4 gaussian4_f32(uint32_t k0, uint32_t k1, uint32_t i, uint32_t j4) {
+  const uint4 w = philox4x32_10(make_uint4(j4, i, kTagGaussian, 0u), k0, k1);
+  const float2 p = box_muller_f32(w.x, w.y), q = box_muller_f32(w.z, w.w);
+  return make_float4(p.x, p.y, q.x, q.y);
+}
+__device__ __forceinline__ void gaussian4_f64(uint32_t k0, uint32_t k1, uint32_t i, uint32_t j4,
+                                              double out[4]) {
+  const uint4 w = philox4x32_10(make_uint4(j4, i, kTagGaussian, 0u), k0, k1);
+  const double2 p = box_muller_f64(w.x, w.y), q = box_muller_f64(w.z, w.w);
+  out[0] = p.x; out[1] = p.y; out[2] = q.x; out[3] = q.y;
+}
+
+// ------------------------------------------------------------------------------------
+// Device status: int32[2] = {first error code, step}.  Never traps.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void record_error(int32_t* st, int code, int step) {
+  if (st == nullptr) return;
+  if (atomicCAS(st, 0, code) == 0) atomicExch(st + 1, step);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int32_t* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed_gpu(const int32_t* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// ------------------------------------------------------------------------------------
+// Grid all-gather for persistent cooperative kernels.  Every CTA b owns slot b of two
+// parity buffers; step t publishes into buffer t&1 with tag t+1 (tags start at 0 because
+// the host clears them before each launch).  A CTA publishes step t+1 only after it has
+// read step t, so two buffers suffice.  Payloads must be read with L2-only loads (__ldcg).
+// ------------------------------------------------------------------------------------
+struct GridComm {
+  int32_t* tags;       // [2 * G]
+  int32_t* abort;      // one word: set when any CTA gives up
+  char* payload;       // [2 * G * slot_bytes]
+  int64_t slot_bytes;
+  int G;
+  uint64_t wait_ns;
+  __device__ __forceinline__ char* slot(int step, int b) const {
+    return payload + ((int64_t)(step & 1) * G + b) * slot_bytes;
+  }
+};
+
+// Publish this CTA's slot for `step` (call after all threads wrote the payload; contains a
+// __syncthreads).
+__device__ __forceinline__ void comm_publish(const GridComm& gc, int step) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release_gpu(gc.tags + (step & 1) * gc.G + blockIdx.x, step + 1);
+  }
+}
+
+// Wait until every CTA published `step`.  Returns false (uniformly over the CTA) on timeout
+// or abort; the caller then records its error and leaves.  Needs blockDim.x >= G.
+__device__ __forceinline__ bool comm_wait_all(const GridComm& gc, int step, int32_t* dev_status) {
+  __shared__ int s_fail;
+  if (threadIdx.x == 0) s_fail = 0;
+  __syncthreads();
+  if (threadIdx.x < gc.G) {
+    const int32_t* tag = gc.tags + (step & 1) * gc.G + threadIdx.x;
+    const uint64_t t0 = global_ns();
+    uint32_t it = 0;
+    while (ld_acquire_gpu(tag) < step + 1) {
+      if ((++it & 63u) == 0) {
+        if (ld_relaxed_gpu(gc.abort) != 0) { s_fail = 1; break; }
+        if (global_ns() - t0 > gc.wait_ns) {
+          s_fail = 2;
+          atomicExch(gc.abort, 1);
+          break;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int f = s_fail;
+  if (f == 2 && threadIdx.x == 0) record_error(dev_status, SKEL_ERR_TIMEOUT, step);
+  __threadfence();
+  return f == 0;
+}
+
+// Block-wide argmax of (key, index): larger key wins; equal keys -> smaller index.
+template <typename T>
+struct KeyIdx {
+  T key;
+  int64_t idx;
+};
+
+template <typename T>
+__device__ __forceinline__ bool better(T ka, int64_t ia, T kb, int64_t ib) {
+  return (ka > kb) || (ka == kb && ia < ib);
+}
+
+template <typename T>
+__device__ __forceinline__ KeyIdx<T> block_argmax(T key, int64_t idx) {
+  __shared__ T sk[32];
+  __shared__ int64_t si[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T k2 = __shfl_xor_sync(0xffffffffu, key, o);
+    const int64_t i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (better(k2, i2, key, idx)) { key = k2; idx = i2; }
+  }
+  __syncthreads();
+  if (lane == 0) { sk[warp] = key; si[warp] = idx; }
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (warp == 0) {
+    key = lane < nw ? sk[lane] : sk[0];
+    idx = lane < nw ? si[lane] : si[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T k2 = __shfl_xor_sync(0xffffffffu, key, o);
+      const int64_t i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (better(k2, i2, key, idx)) { key = k2; idx = i2; }
+    }
+    if (lane == 0) { sk[0] = key; si[0] = idx; }
+  }
+  __syncthreads();
+  KeyIdx<T> r{sk[0], si[0]};
+  __syncthreads();
+  return r;
+}
+
+// Block-wide sum (deterministic order for a fixed block size).
+template <typename T>
+__device__ __forceinline__ T block_sum(T v) {
+  __shared__ T sv[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) sv[warp] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (warp == 0) {
+    v = lane < nw ? sv[lane] : T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sv[0] = v;
+  }
+  __syncthreads();
+  const T r = sv[0];
+  __syncthreads();
+  return r;
+}
+
+// Magnitude key for pivot searches: NaN and Inf rank above every finite value so that a
+// non-finite entry in a pivot row is always selected and then reported.
+template <typename T>
+__device__ __forceinline__ T pivot_key(T v) {
+  const T a = fabs(v);
+  return isfinite(a) ? a : T(INFINITY);
+}
+
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float dmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float dsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float ddiv(float a, float b) { return __fdiv_rn(a, b); }
+
+}  // namespace skel

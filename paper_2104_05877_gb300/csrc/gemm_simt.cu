@@ -1,0 +1,281 @@
+// SIMT tiled GEMM with pluggable left operand (loaded, or Gaussian generated in-kernel from
+// Philox) and fused epilogues; plus gathers, transposes and deterministic reductions.
+//
+// Used for: the FP64/FP32 Gaussian sketch X = Gamma A (Algorithm 2 line 2) with Gamma never
+// stored; W = Q_C^T A (Eq. (2.1) via Q_C R_C = C); W Q_R (Remark 3); T T^T for Theorem 1's
+// eta; and the residual norms ||A - C Z||_F, ||A - C U R||_F.
+#include "common.cuh"
+#include "internal.h"
+
+namespace skel {
+
+namespace {
+
+constexpr int BM = 64, BN = 128, BK = 16, NT = 256;
+constexpr int TM = 4, TN = 8;   // per-thread micro tile: rows ty*4+i, cols tx+16*j
+
+template <typename T>
+__device__ __forceinline__ T load_as(const void* p, int64_t off, skel_dtype dt) {
+  return dt == SKEL_F64 ? (T)__ldg(static_cast<const double*>(p) + off)
+                        : (T)__ldg(static_cast<const float*>(p) + off);
+}
+
+template <typename T, int LEFT, int EPI>
+__global__ void __launch_bounds__(NT) gemm_kernel(const GemmArgs a) {
+  __shared__ T Ls[BK][BM + 4];
+  __shared__ T Bs[BK][BN + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t r0 = (int64_t)blockIdx.y * BM, c0 = (int64_t)blockIdx.x * BN;
+  const uint32_t k0s = (uint32_t)(a.seed & 0xffffffffu), k1s = (uint32_t)(a.seed >> 32);
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+  const bool l_kcontig = (a.L.sc == 1);
+  const bool b_kcontig = (a.B.sr == 1);
+  for (int64_t kb = 0; kb < a.K; kb += BK) {
+    // ---- left tile (BM x BK) ----
+    if (LEFT == LEFT_GAUSSIAN) {
+      const int r = tid >> 2, k4 = tid & 3;       // 64 rows x 4 groups of 4 columns
+      const int64_t gr = r0 + r;
+      const int64_t gk = kb + 4 * k4;
+      T g[4] = {T(0), T(0), T(0), T(0)};
+      if (gr < a.M && gk < a.K) {
+        if constexpr (sizeof(T) == 8) {
+          double d[4];
+          gaussian4_f64(k0s, k1s, (uint32_t)gr, (uint32_t)(gk >> 2), d);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) g[q] = (T)d[q];
+        } else {
+          const float4 f = gaussian4_f32(k0s, k1s, (uint32_t)gr, (uint32_t)(gk >> 2));
+          g[0] = f.x; g[1] = f.y; g[2] = f.z; g[3] = f.w;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Ls[4 * k4 + q][r] = (gk + q < a.K) ? g[q] : T(0);
+    } else {
+#pragma unroll
+      for (int e0 = 0; e0 < BM * BK; e0 += NT) {
+        const int e = e0 + tid;
+        int r, k;
+        if (l_kcontig) { r = e / BK; k = e % BK; } else { r = e % BM; k = e / BM; }
+        const int64_t gr = r0 + r, gk = kb + k;
+        Ls[k][r] = (gr < a.M && gk < a.K) ? load_as<T>(a.L.p, gr * a.L.sr + gk * a.L.sc, a.l_dt) : T(0);
+      }
+    }
+    // ---- right tile (BK x BN) ----
+#pragma unroll
+    for (int e0 = 0; e0 < BK * BN; e0 += NT) {
+      const int e = e0 + tid;
+      int k, c;
+      if (b_kcontig) { k = e % BK; c = e / BK; } else { c = e % BN; k = e / BN; }
+      const int64_t gk = kb + k, gc = c0 + c;
+      Bs[k][c] = (gk < a.K && gc < a.N) ? load_as<T>(a.B.p, gk * a.B.sr + gc * a.B.sc, a.b_dt) : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      T lv[TM], bv[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) lv[i] = Ls[k][ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) bv[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(lv[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+
+  // ---- epilogue ----
+  const T alpha = (T)a.alpha;
+  double part = 0.0;
+  bool bad = false;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int64_t gr = r0 + ty * TM + i;
+    if (gr >= a.M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int64_t gc = c0 + tx + 16 * j;
+      if (gc >= a.N) continue;
+      const T v = alpha * acc[i][j];
+      if (EPI == EPI_RESID) {
+        const double d = load_as<double>(a.ref.p, gr * a.ref.sr + gc * a.ref.sc, a.ref_dt) - (double)v;
+        part += d * d;
+      } else {
+        const int64_t off = gr * a.out_sr + gc * a.out_sc;
+        if (a.out_dt == SKEL_F64) static_cast<double*>(a.out)[off] = (double)v;
+        else static_cast<float*>(a.out)[off] = (float)v;
+        if (EPI == EPI_STORE_SQ) part += (double)v * (double)v;
+        if (EPI == EPI_SKETCH && !isfinite(v)) bad = true;
+      }
+    }
+  }
+  if (EPI == EPI_SKETCH && bad) record_error(a.dev_status, SKEL_ERR_NONFINITE, -1);
+  if (EPI == EPI_RESID || EPI == EPI_STORE_SQ) {
+    const double tot = block_sum<double>(part);
+    if (tid == 0) a.partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+  }
+}
+
+template <typename T, int LEFT, int EPI>
+cudaError_t launch_t(const GemmArgs& a, cudaStream_t st) {
+  dim3 grid((unsigned)((a.N + BN - 1) / BN), (unsigned)((a.M + BM - 1) / BM));
+  gemm_kernel<T, LEFT, EPI><<<grid, NT, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t dispatch_epi(const GemmArgs& a, GemmLeft left, GemmEpi epi, cudaStream_t st) {
+  if (left == LEFT_GAUSSIAN) {
+    if (epi == EPI_SKETCH) return launch_t<T, LEFT_GAUSSIAN, EPI_SKETCH>(a, st);
+    return cudaErrorInvalidValue;
+  }
+  switch (epi) {
+    case EPI_STORE: return launch_t<T, LEFT_LOAD, EPI_STORE>(a, st);
+    case EPI_STORE_SQ: return launch_t<T, LEFT_LOAD, EPI_STORE_SQ>(a, st);
+    case EPI_RESID: return launch_t<T, LEFT_LOAD, EPI_RESID>(a, st);
+    case EPI_SKETCH: return launch_t<T, LEFT_LOAD, EPI_SKETCH>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------------------------
+__global__ void reduce_sum_kernel(const double* p, int64_t count, double* out, int take_sqrt) {
+  double v = 0.0;
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) v += p[i];
+  v = block_sum<double>(v);
+  if (threadIdx.x == 0) *out = take_sqrt ? sqrt(v) : v;
+}
+
+constexpr int SQ_COLS = 8;
+__global__ void sqnorm_kernel(int64_t m, int64_t n, skel_dtype dt, const void* A, int64_t lda,
+                              double* partials) {
+  double v = 0.0;
+  const int64_t c0 = (int64_t)blockIdx.x * SQ_COLS;
+  for (int cc = 0; cc < SQ_COLS; ++cc) {
+    const int64_t c = c0 + cc;
+    if (c >= n) break;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+      const double x = load_as<double>(A, i + c * lda, dt);
+      v += x * x;
+    }
+  }
+  v = block_sum<double>(v);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v;
+}
+
+template <typename T>
+__global__ void gather_cols_kernel(int64_t m, const T* A, int64_t lda, const int32_t* idx,
+                                   T* C, int64_t ldc) {
+  const int r = blockIdx.y;
+  const int64_t src = (int64_t)idx[r];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    C[i + r * ldc] = A[i + src * lda];
+}
+
+template <typename T>
+__global__ void gather_rows_t_kernel(int64_t n, int32_t s, const T* A, int64_t lda,
+                                     const int32_t* idx, T* Rt, int64_t ldr) {
+  const int r = blockIdx.y;
+  const int64_t row = (int64_t)idx[r];
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x)
+    Rt[c + r * ldr] = A[row + c * lda];
+}
+
+__global__ void gather_cols_rm_kernel(int32_t s, skel_dtype dt, const void* F, int64_t ldf,
+                                      const int32_t* idx, double* out, int64_t ldo) {
+  const int r = blockIdx.x;
+  for (int t = threadIdx.x; t < s; t += blockDim.x)
+    out[(int64_t)r * ldo + t] = load_as<double>(F, (int64_t)r * ldf + idx[t], dt);
+}
+
+__global__ void transpose_kernel(int32_t s, const double* in, int64_t ldi, double* out, int64_t ldo) {
+  const int r = blockIdx.x;
+  for (int c = threadIdx.x; c < s; c += blockDim.x) out[(int64_t)c * ldo + r] = in[(int64_t)r * ldi + c];
+}
+
+__global__ void fill_kernel(double* d, int64_t count, double v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = v;
+}
+
+}  // namespace
+
+int64_t gemm_num_blocks(int64_t M, int64_t N) { return ((N + BN - 1) / BN) * ((M + BM - 1) / BM); }
+
+cudaError_t launch_gemm(const GemmArgs& a, bool f64, GemmLeft left, GemmEpi epi, cudaStream_t st) {
+  if (a.M <= 0 || a.N <= 0) return cudaSuccess;
+  if ((a.M + BM - 1) / BM > 65535) return cudaErrorInvalidValue;
+  return f64 ? dispatch_epi<double>(a, left, epi, st) : dispatch_epi<float>(a, left, epi, st);
+}
+
+cudaError_t launch_reduce_sum(const double* partials, int64_t count, double* out, int take_sqrt,
+                              cudaStream_t st) {
+  reduce_sum_kernel<<<1, 1024, 0, st>>>(partials, count, out, take_sqrt);
+  return cudaGetLastError();
+}
+
+int64_t sqnorm_num_blocks(int64_t m, int64_t n) { return (n + SQ_COLS - 1) / SQ_COLS; }
+
+cudaError_t launch_sqnorm(int64_t m, int64_t n, skel_dtype dt, const void* A, int64_t lda,
+                          double* partials, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  sqnorm_kernel<<<(unsigned)sqnorm_num_blocks(m, n), 256, 0, st>>>(m, n, dt, A, lda, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_cols(int64_t m, int32_t s, skel_dtype dt, const void* A, int64_t lda,
+                               const int32_t* idx, void* C, int64_t ldc, cudaStream_t st) {
+  dim3 grid((unsigned)std::min<int64_t>((m + 255) / 256, 64), (unsigned)s);
+  if (dt == SKEL_F64)
+    gather_cols_kernel<double><<<grid, 256, 0, st>>>(m, (const double*)A, lda, idx, (double*)C, ldc);
+  else
+    gather_cols_kernel<float><<<grid, 256, 0, st>>>(m, (const float*)A, lda, idx, (float*)C, ldc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows_t(int64_t n, int32_t s, skel_dtype dt, const void* A, int64_t lda,
+                                 const int32_t* idx, void* Rt, int64_t ldr, cudaStream_t st) {
+  dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)s);
+  if (dt == SKEL_F64)
+    gather_rows_t_kernel<double><<<grid, 256, 0, st>>>(n, s, (const double*)A, lda, idx, (double*)Rt, ldr);
+  else
+    gather_rows_t_kernel<float><<<grid, 256, 0, st>>>(n, s, (const float*)A, lda, idx, (float*)Rt, ldr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_cols_rowmajor_f64(int32_t s, skel_dtype dt, const void* F, int64_t ldf,
+                                            const int32_t* idx, double* out, int64_t ldo,
+                                            cudaStream_t st) {
+  gather_cols_rm_kernel<<<s, 256, 0, st>>>(s, dt, F, ldf, idx, out, ldo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_f64(int32_t s, const double* in, int64_t ldi, double* out,
+                                 int64_t ldo, cudaStream_t st) {
+  transpose_kernel<<<s, 256, 0, st>>>(s, in, ldi, out, ldo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_f64(double* d, int64_t count, double value, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  fill_kernel<<<(unsigned)std::min<int64_t>((count + 255) / 256, 1024), 256, 0, st>>>(d, count, value);
+  return cudaGetLastError();
+}
+
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+}  // namespace skel

@@ -1,0 +1,120 @@
+// Host-side launchers shared between the translation units of libskel.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/skel.h"
+
+namespace skel {
+
+// Strided view of an operand: element (r, c) at p[r*sr + c*sc].
+struct View {
+  const void* p;
+  int64_t sr, sc;
+};
+
+enum GemmLeft { LEFT_LOAD = 0, LEFT_GAUSSIAN = 1 };
+enum GemmEpi {
+  EPI_STORE = 0,       // out(r,c) = alpha*acc
+  EPI_STORE_SQ = 1,    // store, and partial[block] = sum (alpha*acc)^2
+  EPI_RESID = 2,       // partial[block] = sum (ref(r,c) - alpha*acc)^2
+  EPI_SKETCH = 3       // store, flag non-finite outputs
+};
+
+// out(M x N) = alpha * L(M x K) * B(K x N).  `f64` selects FP64 storage+arithmetic for the
+// operands (true) or FP32 (false); L/B/ref are converted on load from their own dtypes.
+struct GemmArgs {
+  int64_t M, N, K;
+  View L;  skel_dtype l_dt;   // ignored for LEFT_GAUSSIAN
+  View B;  skel_dtype b_dt;
+  void* out; int64_t out_sr, out_sc; skel_dtype out_dt;
+  View ref; skel_dtype ref_dt;     // EPI_RESID
+  double alpha;
+  double* partials;                // EPI_STORE_SQ / EPI_RESID: one double per CTA
+  uint64_t seed;                   // LEFT_GAUSSIAN
+  int32_t* dev_status;
+};
+int64_t gemm_num_blocks(int64_t M, int64_t N);
+cudaError_t launch_gemm(const GemmArgs& a, bool f64, GemmLeft left, GemmEpi epi, cudaStream_t st);
+
+// Sum `count` doubles in `partials` (deterministic) into *out (device), optionally sqrt.
+cudaError_t launch_reduce_sum(const double* partials, int64_t count, double* out, int take_sqrt,
+                              cudaStream_t st);
+// ||A||_F^2 of an m x n column-major matrix -> partials (one per block), returns #blocks.
+int64_t sqnorm_num_blocks(int64_t m, int64_t n);
+cudaError_t launch_sqnorm(int64_t m, int64_t n, skel_dtype dt, const void* A, int64_t lda,
+                          double* partials, cudaStream_t st);
+
+// C(:, r) = A(:, idx[r]) (m x s column-major out, ld = ldc), dtype preserved.
+cudaError_t launch_gather_cols(int64_t m, int32_t s, skel_dtype dt, const void* A, int64_t lda,
+                               const int32_t* idx, void* C, int64_t ldc, cudaStream_t st);
+// Rt(c, r) = A(idx[r], c): the transpose of the row gather, n x s column-major (ld = ldr).
+cudaError_t launch_gather_rows_t(int64_t n, int32_t s, skel_dtype dt, const void* A, int64_t lda,
+                                 const int32_t* idx, void* Rt, int64_t ldr, cudaStream_t st);
+// out(r, t) = F(r, idx[t]) for an s x ? row-major F: s x s row-major FP64 out.
+cudaError_t launch_gather_cols_rowmajor_f64(int32_t s, skel_dtype dt, const void* F, int64_t ldf,
+                                            const int32_t* idx, double* out, int64_t ldo,
+                                            cudaStream_t st);
+// out = in^T for an s x s row-major FP64 matrix.
+cudaError_t launch_transpose_f64(int32_t s, const double* in, int64_t ldi, double* out,
+                                 int64_t ldo, cudaStream_t st);
+// Set d[0..count) = value.
+cudaError_t launch_fill_f64(double* d, int64_t count, double value, cudaStream_t st);
+
+// Y = R^{-1} B for an s x s upper triangular FP64 R (row-major), B s x N row-major of dtype
+// b_dt, Y s x N row-major FP64 (may alias B only when b_dt == SKEL_F64 and ldb == ldy).
+cudaError_t launch_trsm_upper(int32_t s, int64_t N, const double* R, int64_t ldr, int unit_diag,
+                              skel_dtype b_dt, const void* B, int64_t ldb, double* Y, int64_t ldy,
+                              cudaStream_t st);
+
+// eta = sqrt(lambda_max(G)) for a symmetric positive definite s x s FP64 G (row-major),
+// by power iteration in one CTA.  Writes *out.
+cudaError_t launch_power_sqrt_lmax(int32_t s, const double* G, int64_t ldg, double* out,
+                                   double* scratch /* 2*s doubles */, cudaStream_t st);
+
+// Persistent pivoting kernels (pivot.cu).
+size_t lupp_workspace(skel_dtype dt, int64_t n, int32_t s, int* grid_out);
+skel_status run_lupp(skel_dtype dt, const void* X, int64_t n, int64_t ldx, int32_t s, int32_t* Js,
+                     void* L, int64_t ldl, void* R, int64_t ldr, void* ws, size_t ws_bytes,
+                     int32_t* dev_status, cudaStream_t st);
+size_t cpqr_workspace(skel_dtype dt, int64_t l, int64_t n, int32_t s, int* grid_out);
+skel_status run_cpqr(skel_dtype dt, const void* X, int64_t l, int64_t n, int64_t ldx, int32_t s,
+                     int32_t* Js, void* R, int64_t ldr, void* ws, size_t ws_bytes,
+                     int32_t* dev_status, cudaStream_t st);
+
+// Householder QR of a tall m x s column-major C (qr.cu): explicit Q (m x s col-major, same
+// dtype, ld = ldq) and R (s x s row-major FP64).
+size_t qr_workspace(skel_dtype dt, int64_t m, int32_t s);
+skel_status run_qr(skel_dtype dt, const void* C, int64_t m, int64_t ldc, int32_t s, void* Q,
+                   int64_t ldq, double* R, int64_t ldr, void* ws, size_t ws_bytes,
+                   int32_t* dev_status, cudaStream_t st);
+
+// Sparse sign / CSC sketches (sparse.cu).
+size_t sparse_pattern_bytes(int64_t m, int32_t zeta);
+cudaError_t launch_sparse_pattern(int64_t m, int32_t l, int32_t zeta, uint64_t seed,
+                                  int32_t* table, cudaStream_t st);
+cudaError_t launch_sparse_sketch_dense(int64_t m, int64_t n, skel_dtype dt, const void* A,
+                                       int64_t lda, int32_t l, int32_t zeta,
+                                       const int32_t* table, void* X, int64_t ldx,
+                                       int32_t* dev_status, cudaStream_t st);
+cudaError_t launch_sparse_sketch_csc(int64_t m, int64_t n, const int64_t* col_ptr,
+                                     const int32_t* row_idx, const float* val, int32_t l,
+                                     int32_t zeta, const int32_t* table, float* X, int64_t ldx,
+                                     int32_t* dev_status, cudaStream_t st);
+cudaError_t launch_gauss_sketch_csc(int64_t m, int64_t n, const int64_t* col_ptr,
+                                    const int32_t* row_idx, const float* val, int32_t l,
+                                    uint64_t seed, float* X, int64_t ldx, int32_t* dev_status,
+                                    cudaStream_t st);
+
+// Tensor-core Gaussian sketch (sketch_tc.cu).  Returns cudaErrorNotSupported when the
+// shape is outside what the kernel handles.
+cudaError_t launch_sketch_tc(int64_t m, int64_t n, const float* A, int64_t lda, int32_t l,
+                             skel_prec prec, uint64_t seed, float* X, int64_t ldx,
+                             int32_t* dev_status, cudaStream_t st);
+
+int device_sm_count();
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+}  // namespace skel

@@ -15,3 +15,23 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="session")
+def skel():
+    """The CUDA library binding, built if needed; GPU tests only."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2104_05877_gb300 as sk
+    if not os.path.exists(sk.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    sk.lib()
+    return sk
+
+
+@pytest.fixture(scope="session")
+def dev():
+    import torch
+    return torch.device("cuda:0")

@@ -1,0 +1,128 @@
+"""GPU: column ID (Eq. (2.1)), stable CUR (Remark 3), errors and Theorem 1's eta."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import decomp, errors, pivoting, sketch
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _js(A, k, p, seed):
+    X = sketch.gaussian_sketch(A, k + p, seed)
+    return pivoting.lupp_columns(X, k)
+
+
+@pytest.mark.parametrize("m,n,k", [(1000, 800, 50), (300, 200, 20), (257, 129, 1), (640, 130, 128)])
+def test_id_fp64_matches_oracle(skel, dev, m, n, k):
+    """FP64 mode, same J_s: ||Z_gpu - Z_or||_F <= 1e-10 ||Z_or||_F, Z(:, Js) = I."""
+    A = workloads.config1(m, n, seed=m) if k > 1 else np.asfortranarray(np.random.default_rng(0).standard_normal((m, n)))
+    Js = _js(A, k, 10 if k + 10 <= n else 0, 1)["Js"]
+    C = A[:, Js]
+    kappa = np.linalg.cond(C)
+    assert kappa * 2.0 ** -52 < 1e-11, f"cond(C) = {kappa:.2e} makes the 1e-10 bound unattainable"
+    Z, sq, st = skel.column_id(torch.from_numpy(A).to(dev), torch.from_numpy(Js.astype(np.int32)).to(dev))
+    skel.check_status(st)
+    Zr = decomp.column_id(A, Js)
+    Zg = Z.cpu().numpy()
+    assert np.linalg.norm(Zg - Zr) <= 1e-10 * np.linalg.norm(Zr)
+    assert np.max(np.abs(Zg[:, Js] - np.eye(k))) < 1e-11
+    nA2, nW2 = sq.cpu().numpy()
+    e2 = np.linalg.norm(A - C @ Zr) ** 2
+    assert nA2 == pytest.approx(np.linalg.norm(A) ** 2, rel=1e-12)
+    assert nA2 - nW2 == pytest.approx(e2, rel=1e-6, abs=1e-12 * nA2)
+
+
+def test_id_fp32_error_within_gate(skel, dev):
+    """FP32 QR / FP32 Q^T A / FP64 solve: the ID error stays within 1.05x of the oracle's."""
+    A = workloads.dense_config2(2048, 1536, seed=4)
+    Ad = A.astype(np.float64)
+    Js = _js(Ad, 128, 16, 2)["Js"]
+    Z, _, st = skel.column_id(torch.from_numpy(A).to(dev), torch.from_numpy(Js.astype(np.int32)).to(dev))
+    skel.check_status(st)
+    e_gpu = errors.rel_id_error(Ad, Js, Z.cpu().numpy())
+    e_or = errors.rel_id_error(Ad, Js, decomp.column_id(Ad, Js))
+    assert e_gpu <= 1.05 * e_or
+    print(f"FP32 ID: e_gpu/e_or - 1 = {e_gpu / e_or - 1:.2e}")
+
+
+def test_exact_rank_reconstruction_fp64(skel, dev):
+    """Exactly rank-r input, s = r: the GPU column ID and CUR reproduce A (Lemma 1)."""
+    A = workloads.exact_rank(400, 300, 12, seed=3)
+    Js = _js(A, 12, 0, 5)["Js"]
+    Jt = torch.from_numpy(Js.astype(np.int32)).to(dev)
+    At = torch.from_numpy(A).to(dev)
+    Z, _, st = skel.column_id(At, Jt)
+    Is, U, _ = skel.cur(At, Jt, status=st)
+    out, _ = skel.error(At, Jt, Z, Is, U, status=st)
+    skel.check_status(st)
+    e = out.cpu().numpy()
+    assert e[1] / e[0] < 1e-12
+    assert e[2] / e[0] < 1e-10
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_cur_matches_oracle(skel, dev, dt):
+    A = workloads.config1(600, 500, seed=8).astype(dt)
+    Ad = A.astype(np.float64)
+    k = 30
+    Js = _js(Ad, k, 10, 3)["Js"]
+    Jt = torch.from_numpy(Js.astype(np.int32)).to(dev)
+    Is, U, st = skel.cur(torch.from_numpy(np.asfortranarray(A)).to(dev), Jt)
+    skel.check_status(st)
+    Isg = Is.cpu().numpy()
+    rp = pivoting.lupp_rows(Ad[:, Js], k)
+    kk = int(np.argmax(rp["gaps"] < (1e-9 if dt == np.float64 else 1e-3))) if np.any(rp["gaps"] < (1e-9 if dt == np.float64 else 1e-3)) else k
+    assert np.array_equal(Isg[:kk], rp["Js"][:kk])
+    Ur = decomp.cur(Ad, Js, Isg)
+    e_gpu = errors.rel_cur_error(Ad, Js, U.cpu().numpy(), Isg)
+    e_or = errors.rel_cur_error(Ad, Js, Ur, Isg)
+    assert e_gpu <= 1.05 * e_or
+    if dt == np.float64:
+        assert np.linalg.norm(U.cpu().numpy() - Ur) <= 1e-8 * np.linalg.norm(Ur)
+
+
+@pytest.mark.parametrize("pivot", ["lupp", "cpqr"])
+def test_error_and_eta_match_oracle(skel, dev, pivot):
+    A = workloads.dense_config2(700, 500, seed=6, dtype=np.float64)
+    k, l = 40, 50
+    X = sketch.gaussian_sketch(A, l, 9)
+    piv = pivoting.lupp_columns(X, k) if pivot == "lupp" else pivoting.cpqr_columns(X, k)
+    Js = piv["Js"]
+    Z = decomp.column_id(A, Js)
+    Is = pivoting.lupp_rows(A[:, Js], k)["Js"]
+    U = decomp.cur(A, Js, Is)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    out, st = skel.error(t(np.asfortranarray(A)).t().contiguous().t(), t(Js.astype(np.int32)), t(Z),
+                         t(Is.astype(np.int32)), t(U), t(piv["R"]))
+    skel.check_status(st)
+    e = out.cpu().numpy()
+    assert e[0] == pytest.approx(np.linalg.norm(A), rel=1e-13)
+    assert e[1] == pytest.approx(np.linalg.norm(A - A[:, Js] @ Z), rel=1e-10)
+    assert e[2] == pytest.approx(np.linalg.norm(A - A[:, Js] @ U @ A[Is, :]), rel=1e-8)
+    assert e[3] == pytest.approx(errors.eta(piv["R"], Js), rel=1e-8)
+    # Theorem 1 holds with the device's numbers
+    assert e[1] <= e[3] * errors.rangefinder_error(A, piv["R"]) * (1 + 1e-10)
+
+
+def test_end_to_end_fp64_config1(skel, dev):
+    """Config 1 (1000 x 800, k = 50, p = 10): the whole FP64 device pipeline equals the
+    oracle's skeleton, Z within 1e-10, errors within 1.05x."""
+    A = workloads.config1()
+    k, p, seed = 50, 10, workloads.seed_for(1, "gamma")
+    out = skel.skeletonize(torch.from_numpy(A).to(dev), k, p, seed=seed, prec="f64")
+    torch.cuda.synchronize()
+    skel.check_status(out["status"])
+    ref = oracle.skeleton.skeletonize(A, k, p, seed)
+    Js = out["Js"].cpu().numpy()
+    small = np.flatnonzero(ref["gaps"] < 1e-9)
+    kk = int(small[0]) if small.size else k
+    assert np.array_equal(Js[:kk], ref["Js"][:kk])
+    e = out["errors"].cpu().numpy()
+    assert e[1] / e[0] <= 1.05 * ref["err_id"]
+    assert e[2] / e[0] <= 1.05 * ref["err_cur"]
+    if kk == k:
+        assert np.linalg.norm(out["Z"].cpu().numpy() - ref["Z"]) <= 1e-10 * np.linalg.norm(ref["Z"])
+        assert e[3] == pytest.approx(ref["eta"], rel=1e-8)

@@ -1,0 +1,142 @@
+"""GPU: LUPP and CPQR on the sketch (Sec. 2.5) against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import pivoting, errors, sketch
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _prefix(gaps, delta):
+    """Number of leading steps whose oracle gap is at least delta."""
+    small = np.flatnonzero(gaps < delta)
+    return int(small[0]) if small.size else len(gaps)
+
+
+@pytest.mark.parametrize("l,n,s", [(20, 100, 20), (60, 800, 50), (8, 8, 8), (30, 5000, 1),
+                                   (128, 3001, 100), (256, 8192, 256)])
+def test_lupp_fp64_bit_exact(skel, dev, l, n, s):
+    """Same FP64 X in, same operation order: pivots and factors are bit-identical."""
+    X = np.random.default_rng(l * n + s).standard_normal((l, n))
+    Js, Lf, Rf, st = skel.pivot_lupp(torch.from_numpy(X).to(dev), s)
+    skel.check_status(st)
+    ref = pivoting.lupp_columns(X, s)
+    assert np.array_equal(Js.cpu().numpy(), ref["Js"])
+    assert np.array_equal(Rf.cpu().numpy(), ref["R"])
+    assert np.array_equal(Lf.cpu().numpy(), ref["L"][:s, :s])
+
+
+def test_lupp_fp64_global_slab_path(skel, dev):
+    """s x (n / G) too large for shared memory: the slab lives in the global workspace."""
+    l, n, s = 520, 8192, 512
+    X = np.random.default_rng(3).standard_normal((l, n))
+    Js, _, Rf, st = skel.pivot_lupp(torch.from_numpy(X).to(dev), s)
+    skel.check_status(st)
+    ref = pivoting.lupp_columns(X, s)
+    assert np.array_equal(Js.cpu().numpy(), ref["Js"])
+    assert np.array_equal(Rf.cpu().numpy(), ref["R"])
+
+
+@pytest.mark.parametrize("l,n,s", [(40, 1000, 32), (300, 4096, 256)])
+def test_lupp_fp32_prefix(skel, dev, l, n, s):
+    """FP32 arithmetic: pivots equal the FP64 oracle's up to the first step whose relative
+    gap is below 1e-3 (1e4 x the FP32 unit roundoff)."""
+    X = np.random.default_rng(n).standard_normal((l, n)).astype(np.float32)
+    Js, _, Rf, st = skel.pivot_lupp(torch.from_numpy(X).to(dev), s)
+    skel.check_status(st)
+    ref = pivoting.lupp_columns(X.astype(np.float64), s)
+    k = _prefix(ref["gaps"], 1e-3)
+    assert k >= min(s, 10)
+    assert np.array_equal(Js.cpu().numpy()[:k], ref["Js"][:k])
+    R = Rf.cpu().numpy()
+    assert np.max(np.abs(R)) <= 1.0 + 1e-6
+    assert np.allclose(R[np.arange(s), Js.cpu().numpy()], 1.0)
+
+
+def test_lupp_kahan_ties(skel, dev):
+    """Lemma 2's Kahan-type X: ties at every step resolve to the lowest index."""
+    for dt in (torch.float64, torch.float32):
+        X = workloads.kahan_type(12, 40)
+        Js, _, Rf, st = skel.pivot_lupp(torch.from_numpy(X).to(dev, dt), 12)
+        skel.check_status(st)
+        assert np.array_equal(Js.cpu().numpy(), np.arange(12))
+        assert np.array_equal(Rf.cpu().numpy().astype(np.float64), X)
+
+
+def test_lupp_rank_deficient(skel, dev):
+    X = np.zeros((4, 50))
+    X[0, 7] = 2.0
+    X[1, 9] = -1.0
+    Js, _, _, st = skel.pivot_lupp(torch.from_numpy(X).to(dev), 4)
+    with pytest.raises(skel.SkelError) as e:
+        skel.check_status(st)
+    assert e.value.code == 4
+    assert list(Js.cpu().numpy()) == [7, 9, -1, -1]
+
+
+def test_lupp_nonfinite(skel, dev):
+    X = np.random.default_rng(0).standard_normal((6, 30))
+    X[0, 4] = np.inf
+    _, _, _, st = skel.pivot_lupp(torch.from_numpy(X).to(dev), 3)
+    with pytest.raises(skel.SkelError) as e:
+        skel.check_status(st)
+    assert e.value.code == 3
+
+
+@pytest.mark.parametrize("m,s", [(500, 20), (8192, 64), (20000, 129)])
+def test_row_lupp_on_tall_C(skel, dev, m, s):
+    """Algorithm 2 line 4: row pivots of C (column-major) via LUPP on C^T."""
+    C = np.asfortranarray(np.random.default_rng(m).standard_normal((m, s)))
+    Is, st = skel.pivot_lupp_rows(torch.from_numpy(C).to(dev), s)
+    skel.check_status(st)
+    assert np.array_equal(Is.cpu().numpy(), pivoting.lupp_rows(C, s)["Js"])
+
+
+@pytest.mark.parametrize("l,n,s,dt", [(20, 300, 20, np.float64), (64, 2000, 48, np.float64),
+                                      (80, 8192, 64, np.float32), (40, 777, 30, np.float32)])
+def test_cpqr_prefix(skel, dev, l, n, s, dt):
+    X = np.random.default_rng(l + n).standard_normal((l, n)).astype(dt)
+    Js, Rf, st = skel.pivot_cpqr(torch.from_numpy(X).to(dev), s)
+    skel.check_status(st)
+    ref = pivoting.cpqr_columns(X.astype(np.float64), s)
+    delta = 1e-9 if dt == np.float64 else 1e-3
+    k = _prefix(ref["gaps"], delta)
+    assert k >= min(s, 8)
+    Jg = Js.cpu().numpy()
+    assert np.array_equal(Jg[:k], ref["Js"][:k])
+    R = Rf.cpu().numpy().astype(np.float64)
+    tol = 1e-10 if dt == np.float64 else 2e-4
+    assert np.allclose(np.abs(R[np.arange(k), Jg[:k]]), np.abs(ref["R"][np.arange(k), ref["Js"][:k]]), rtol=tol)
+    # R^T R on the selected columns reproduces the Gram matrix of X on the first k pivots
+    if k == s:
+        R1 = R[:, Jg]
+        XJ = X.astype(np.float64)[:, Jg]
+        assert np.allclose(np.triu(R1), R1, atol=0)
+
+
+def test_cpqr_kahan_like_separated(skel, dev):
+    """Columns of strictly decreasing norm, orthogonal: CPQR picks them in norm order."""
+    l, n = 16, 64
+    rng = np.random.default_rng(1)
+    Q, _ = np.linalg.qr(rng.standard_normal((l, l)))
+    X = np.zeros((l, n))
+    perm = rng.permutation(n)
+    for r in range(l):
+        X[:, perm[r]] = Q[:, r] * 2.0 ** (-r)
+    Js, Rf, st = skel.pivot_cpqr(torch.from_numpy(X).to(dev), l)
+    skel.check_status(st)
+    assert np.array_equal(Js.cpu().numpy(), perm[:l])
+
+
+def test_grid_wait_times_out(skel, dev):
+    """A grid-wide wait that can never complete returns SKEL_ERR_TIMEOUT after its limit and
+    leaves the context usable."""
+    st = skel.debug_grid_timeout(8, 200_000_000, device=dev)
+    with pytest.raises(skel.SkelError) as e:
+        skel.check_status(st)
+    assert e.value.code == 5
+    X = torch.randn(4, 40, dtype=torch.float64, device=dev)
+    Js, _, _, st2 = skel.pivot_lupp(X, 4)
+    skel.check_status(st2)

@@ -1,0 +1,111 @@
+"""GPU: the sketch X = Gamma A against the oracle (Algorithm 2 line 2)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import torch
+
+from oracle import embedding, sketch
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _bound(l, m, seed, A, u):
+    """Elementwise bound m*u*(|G| |A|)/sqrt(l) on the summation-order difference."""
+    G = embedding.gaussian_normals(l, m, seed)
+    return (m * u + 1e-15) * (np.abs(G) @ np.abs(A)) / np.sqrt(l) + 1e-300
+
+
+@pytest.mark.parametrize("m,n,l", [(300, 200, 30), (1000, 777, 61), (129, 1, 5), (64, 300, 1)])
+def test_sketch_fp64(skel, dev, m, n, l):
+    A = workloads.config1(m, n, seed=m + n) if m >= n else np.random.default_rng(1).standard_normal((m, n))
+    A = np.asfortranarray(A)
+    X, st = skel.sketch(torch.from_numpy(A).to(dev), l, prec="f64", seed=42)
+    skel.check_status(st)
+    want = sketch.gaussian_sketch(A, l, 42)
+    assert np.all(np.abs(X.cpu().numpy() - want) <= _bound(l, m, 42, A, 2.0 ** -52))
+
+
+@pytest.mark.parametrize("m,n,l", [(512, 300, 40), (1000, 130, 80)])
+def test_sketch_fp32(skel, dev, m, n, l):
+    A = workloads.dense_config2(m, n, seed=3)                 # FP32 storage
+    X, st = skel.sketch(torch.from_numpy(A).to(dev), l, prec="f32", seed=5)
+    skel.check_status(st)
+    want = sketch.gaussian_sketch(A.astype(np.float64), l, 5, operand_rounding="fp32")
+    bound = _bound(l, m, 5, A.astype(np.float64), 2.0 ** -23) + 8 * 2.0 ** -24 * _bound(l, m, 5, A, 1.0) / m
+    assert np.all(np.abs(X.cpu().numpy() - want) <= bound)
+
+
+def test_sketch_empty_and_zero_m(skel, dev):
+    A = torch.zeros(0, 5, dtype=torch.float64, device=dev)
+    X, st = skel.sketch(A, 3, prec="f64")
+    skel.check_status(st)
+    assert torch.all(X == 0)
+
+
+def test_sketch_nonfinite_reported(skel, dev):
+    A = np.random.default_rng(0).standard_normal((50, 40))
+    A[7, 3] = np.nan
+    _, st = skel.sketch(torch.from_numpy(np.asfortranarray(A)).to(dev), 8, prec="f64")
+    with pytest.raises(skel.SkelError) as e:
+        skel.check_status(st)
+    assert e.value.code == 3
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_sparse_sign_dense_input(skel, dev, dtype):
+    m, n, l, zeta = 700, 150, 48, 8
+    A = np.asfortranarray(np.random.default_rng(2).standard_normal((m, n)).astype(dtype))
+    prec = "f64" if dtype == np.float64 else "f32"
+    X, st = skel.sketch(torch.from_numpy(A).to(dev), l, kind="sparse_sign", prec=prec, seed=11, zeta=zeta)
+    skel.check_status(st)
+    want = sketch.sparse_sign_sketch(A.astype(np.float64), l, zeta, 11)
+    u = 2.0 ** -52 if dtype == np.float64 else 2.0 ** -23
+    Gam = embedding.sparse_sign_embedding(l, m, zeta, 11)
+    bound = m * u * (np.abs(Gam) @ np.abs(A.astype(np.float64))) + 1e-300
+    assert np.all(np.abs(X.cpu().numpy() - want) <= bound)
+
+
+def test_sparse_sign_pattern_is_exact(skel, dev):
+    """Integer A with zeta = l: X = sum of signed entries, exact in FP64; checks every
+    (row, sign) of the device pattern against the oracle's."""
+    m, n, l = 300, 64, 8
+    A = np.asfortranarray(np.random.default_rng(5).integers(-4, 5, size=(m, n)).astype(np.float64))
+    X, st = skel.sketch(torch.from_numpy(A).to(dev), l, kind="sparse_sign", prec="f64", seed=3, zeta=l)
+    skel.check_status(st)
+    want = sketch.sparse_sign_sketch(A, l, l, 3)
+    assert np.array_equal(X.cpu().numpy() * np.sqrt(l), np.round(want * np.sqrt(l)))
+    # zeta < l: single column of A with one nonzero per row isolates each Gamma column
+    m2, l2, z2 = 40, 16, 5
+    A2 = np.asfortranarray(np.eye(m2))
+    X2, st = skel.sketch(torch.from_numpy(A2).to(dev), l2, kind="sparse_sign", prec="f64", seed=9, zeta=z2)
+    skel.check_status(st)
+    assert np.array_equal(X2.cpu().numpy(), embedding.sparse_sign_embedding(l2, m2, z2, 9))
+
+
+def test_sparse_sign_csc(skel, dev):
+    A = workloads.snn_csc(3000, 400, 30, seed=4, density=0.08)
+    l, zeta = 64, 8
+    Ad = A.astype(np.float64)
+    col_ptr = torch.from_numpy(A.indptr.astype(np.int64)).to(dev)
+    row_idx = torch.from_numpy(A.indices.astype(np.int32)).to(dev)
+    val = torch.from_numpy(A.data.astype(np.float32)).to(dev)
+    X, st = skel.sketch_csc(col_ptr, row_idx, val, A.shape[0], A.shape[1], l, seed=21, zeta=zeta)
+    skel.check_status(st)
+    want = sketch.sparse_sign_sketch(Ad, l, zeta, 21)
+    Gam = embedding.sparse_sign_embedding(l, A.shape[0], zeta, 21)
+    bound = A.shape[0] * 2.0 ** -23 * (np.abs(Gam) @ np.abs(Ad.toarray())) + 1e-300
+    assert np.all(np.abs(X.cpu().numpy() - want) <= bound)
+
+
+def test_gaussian_csc(skel, dev):
+    A = workloads.snn_csc(500, 120, 10, seed=8, density=0.2)
+    l = 24
+    col_ptr = torch.from_numpy(A.indptr.astype(np.int64)).to(dev)
+    row_idx = torch.from_numpy(A.indices.astype(np.int32)).to(dev)
+    val = torch.from_numpy(A.data.astype(np.float32)).to(dev)
+    X, st = skel.sketch_csc(col_ptr, row_idx, val, A.shape[0], A.shape[1], l, kind="gaussian", seed=2)
+    skel.check_status(st)
+    Ad = A.toarray().astype(np.float64)
+    want = sketch.gaussian_sketch(Ad, l, 2)
+    assert np.all(np.abs(X.cpu().numpy() - want) <= _bound(l, 500, 2, Ad, 2.0 ** -22) + 1e-6 * _bound(l, 500, 2, Ad, 1.0) / 500)
