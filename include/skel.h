@@ -67,6 +67,8 @@ typedef enum {
 
 const char* skel_status_string(int status);
 int skel_version(void);
+/* Number of CUDA kernels this library has launched in the calling process so far. */
+uint64_t skel_launch_count(void);
 
 /*
  * skel_sketch -- row sketch X = Gamma A of a dense A (Algorithm 1 line 2; Algorithm 2
@@ -78,7 +80,10 @@ int skel_version(void);
  *               sampling from counters (j, 0, 1, c)); zeta is ignored for Gaussian.
  *   prec      : arithmetic of the product (skel_prec).  SKEL_PREC_F64 requires
  *               a_dtype = SKEL_F64 and writes X as FP64; every other precision reads A as
- *               stored and writes X as FP32.  Sparse sign supports F64 and F32 only.
+ *               stored and writes X as FP32.  Sparse sign supports F64 and F32 only.  The
+ *               tensor-core precisions (TF32, BF16) need a_dtype = SKEL_F32, a 16-byte
+ *               aligned A and lda a multiple of 4 (A is streamed by TMA); otherwise they
+ *               return SKEL_ERR_UNSUPPORTED.
  *   X, ldx    : output, l x n row-major (ldx >= n).
  * The Gaussian entries are generated inside the kernel and never stored.  Non-finite
  * entries of X set SKEL_ERR_NONFINITE in dev_status.
@@ -147,14 +152,28 @@ skel_status skel_id(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64
                     void* ws, size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream);
 
 /*
- * skel_cur -- CUR A ~ C U R (Eq. (2.4)) with rows Is from row-wise LUPP on C = A(:, Js)
- * (Algorithm 2 line 4) and U from the stable form of Remark 3:
- * U = R_C^{-1} (Q_C^T A Q_R) R_R^{-T}, where C = Q_C R_C and R^T = A(Is, :)^T = Q_R R_R.
- *   Is        : out int32[s] row skeletons.   U, ldu: out s x s row-major FP64.
+ * skel_pivot_rows -- row skeletons of Algorithm 2 line 4: gathers C = A(:, Js) (m x s) and
+ * runs row-wise LUPP on it (the LUPP of skel_pivot_lupp applied to C^T).
+ *   Is        : out int32[s] row skeletons in selection order.
+ */
+skel_status skel_pivot_rows(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
+                            int32_t s, const int32_t* Js, int32_t* Is, void* ws,
+                            size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream);
+
+/*
+ * skel_cur -- CUR A ~ C U R (Eq. (2.4)) with C = A(:, Js), R = A(Is, :) and U from the
+ * stable form of Remark 3: U = R_C^{-1} (Q_C^T A Q_R) R_R^{-T}, where C = Q_C R_C and
+ * R^T = Q_R R_R (Householder QR, FP64 for dtype F64, FP32 for F32; FP64 solves).
+ *   Is        : row skeletons; input when rows_given != 0, otherwise computed here by
+ *               row-wise LUPP on C (Algorithm 2 line 4) and written.
+ *   U, ldu    : out s x s row-major FP64.
+ *   sq_norms  : optional out (may be NULL), device double[2] = {||A||_F^2, ||Q_C^T A Q_R||_F^2};
+ *               their difference is ||A - C U R||_F^2 (a two-sided orthogonal projection).
  */
 skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
-                     int32_t s, const int32_t* Js, int32_t* Is, double* U, int64_t ldu,
-                     void* ws, size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream);
+                     int32_t s, const int32_t* Js, int32_t* Is, int rows_given, double* U,
+                     int64_t ldu, double* sq_norms, void* ws, size_t* ws_bytes,
+                     int32_t* dev_status, cudaStream_t stream);
 
 /*
  * skel_error -- Frobenius errors formed directly from the residuals, and Theorem 1's

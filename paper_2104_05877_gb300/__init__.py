@@ -48,7 +48,8 @@ def lib():
         "skel_pivot_lupp": [i32, vp, i64, i64, i64, i32, vp, vp, i64, vp, i64, vp, szp, vp, vp],
         "skel_pivot_cpqr": [i32, vp, i64, i64, i64, i32, vp, vp, i64, vp, szp, vp, vp],
         "skel_id": [i64, i64, i32, vp, i64, i32, vp, vp, i64, vp, vp, szp, vp, vp],
-        "skel_cur": [i64, i64, i32, vp, i64, i32, vp, vp, vp, i64, vp, szp, vp, vp],
+        "skel_cur": [i64, i64, i32, vp, i64, i32, vp, vp, ctypes.c_int, vp, i64, vp, vp, szp, vp, vp],
+        "skel_pivot_rows": [i64, i64, i32, vp, i64, i32, vp, vp, vp, szp, vp, vp],
         "skel_error": [i64, i64, i32, vp, i64, i32, vp, vp, i64, vp, vp, i64, i32, vp, i64, vp, vp,
                        szp, vp, vp],
         "skel_debug_gaussian": [i32, i64, u64, ctypes.c_int, vp, vp],
@@ -63,6 +64,7 @@ def lib():
     L.skel_status_string.argtypes = [ctypes.c_int]
     L.skel_status_string.restype = ctypes.c_char_p
     L.skel_version.restype = ctypes.c_int
+    L.skel_launch_count.restype = ctypes.c_uint64
     _lib = L
     return L
 
@@ -133,6 +135,12 @@ def sketch(A, l, kind="gaussian", prec="f32", seed=0, zeta=8, X=None, status=Non
     """X = Gamma A (l x n, row-major): FP64 for prec='f64', FP32 otherwise."""
     A, lda = _colmajor(A)
     m, n = A.shape
+    if prec in ("tf32", "bf16") and (lda % 4 or A.data_ptr() % 16):
+        # the tensor-core path streams A with TMA: 16-byte aligned columns required
+        ld4 = (m + 3) // 4 * 4
+        Ap = torch.empty(n, ld4, dtype=A.dtype, device=A.device).t()
+        Ap[:m].copy_(A)
+        A, lda = Ap[:m], ld4
     xdt = torch.float64 if prec == "f64" else torch.float32
     if X is None:
         X = torch.empty(l, n, dtype=xdt, device=A.device)
@@ -201,17 +209,38 @@ def column_id(A, Js, status=None):
     return Z, sq, st
 
 
-def cur(A, Js, status=None):
-    """Is (row skeletons by LUPP on C) and U (s x s FP64) with A ~ A(:, Js) U A(Is, :)."""
+def pivot_rows(A, Js, status=None):
+    """Row skeletons Is by row-wise LUPP on C = A(:, Js) (Algorithm 2 line 4)."""
     A, lda = _colmajor(A)
     m, n = A.shape
     s = Js.numel()
     Is = torch.empty(s, dtype=torch.int32, device=A.device)
-    U = torch.empty(s, s, dtype=torch.float64, device=A.device)
     st = status if status is not None else new_status(A.device)
-    _call("skel_cur", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, s, _ptr(Js), _ptr(Is), _ptr(U), s, w,
-                                     sz, _ptr(st), _stream()], A.device)
-    return Is, U, st
+    _call("skel_pivot_rows", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, s, _ptr(Js), _ptr(Is), w, sz,
+                                            _ptr(st), _stream()], A.device)
+    return Is, st
+
+
+def cur(A, Js, Is=None, status=None):
+    """U (s x s FP64) with A ~ A(:, Js) U A(Is, :) (Remark 3) and [||A||_F^2, ||Q_C^T A Q_R||_F^2].
+    Is is computed by row-wise LUPP on C when not given.  Returns (Is, U, sq_norms, status)."""
+    A, lda = _colmajor(A)
+    m, n = A.shape
+    s = Js.numel()
+    given = Is is not None
+    if not given:
+        Is = torch.empty(s, dtype=torch.int32, device=A.device)
+    U = torch.empty(s, s, dtype=torch.float64, device=A.device)
+    sq = torch.empty(2, dtype=torch.float64, device=A.device)
+    st = status if status is not None else new_status(A.device)
+    _call("skel_cur", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, s, _ptr(Js), _ptr(Is), int(given),
+                                     _ptr(U), s, _ptr(sq), w, sz, _ptr(st), _stream()], A.device)
+    return Is, U, sq, st
+
+
+def launch_count():
+    """Kernels launched by libskel in this process so far."""
+    return int(lib().skel_launch_count())
 
 
 def error(A, Js=None, Z=None, Is=None, U=None, Rf=None, status=None):
@@ -280,8 +309,9 @@ def skeletonize(A, k, p=10, seed=0, prec="f32", pivot="lupp", kind="gaussian", z
     Z, sq, _ = column_id(A, Js, status=st)
     out = dict(X=X, Js=Js, Rf=Rf, Z=Z, sq_norms=sq, status=st)
     if want_cur:
-        Is, U, _ = cur(A, Js, status=st)
-        out.update(Is=Is, U=U)
+        Is, _ = pivot_rows(A, Js, status=st)
+        _, U, sq_cur, _ = cur(A, Js, Is, status=st)
+        out.update(Is=Is, U=U, sq_norms_cur=sq_cur)
     if want_error:
         e, _ = error(A, Js, Z, out.get("Is"), out.get("U"), Rf, status=st)
         out["errors"] = e

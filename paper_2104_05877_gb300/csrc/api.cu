@@ -6,9 +6,13 @@
 #include "common.cuh"
 #include "internal.h"
 
+#include <atomic>
+
 using namespace skel;
 
 namespace {
+
+std::atomic<unsigned long long> g_launches{0};
 
 // Carves 256-byte aligned regions out of the caller's workspace.  The same sequence of
 // take() calls runs once to size the workspace (base == nullptr) and once to use it.
@@ -54,7 +58,11 @@ bool ws_handshake(size_t need, void* ws, size_t* ws_bytes, skel_status* st) {
 
 }  // namespace
 
+void skel::note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
 extern "C" {
+
+uint64_t skel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 const char* skel_status_string(int status) {
   switch (status) {
@@ -94,6 +102,9 @@ skel_status skel_sketch(int64_t m, int64_t n, skel_dtype a_dtype, const void* A,
     if (prec == SKEL_PREC_F32 && a_dtype != SKEL_F32) return SKEL_ERR_UNSUPPORTED;
     table = static_cast<int32_t*>(ar.take(sparse_pattern_bytes(m, zeta)));
   }
+  const bool tensor = kind == SKEL_SKETCH_GAUSSIAN && (prec == SKEL_PREC_BF16 || prec == SKEL_PREC_TF32);
+  if (tensor && a_dtype != SKEL_F32) return SKEL_ERR_UNSUPPORTED;
+  void* tcws = tensor && m > 0 && n > 0 ? ar.take(sketch_tc_workspace(m, n, l)) : nullptr;
   skel_status st;
   if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
   if (n == 0) return SKEL_OK;
@@ -107,10 +118,9 @@ skel_status skel_sketch(int64_t m, int64_t n, skel_dtype a_dtype, const void* A,
     SK_CUDA(launch_sparse_sketch_dense(m, n, a_dtype, A, lda, l, zeta, table, X, ldx, dev_status, stream));
     return SKEL_OK;
   }
-  if (prec == SKEL_PREC_BF16 || prec == SKEL_PREC_TF32) {
-    if (a_dtype != SKEL_F32) return SKEL_ERR_UNSUPPORTED;
+  if (tensor && m > 0) {
     const cudaError_t e = launch_sketch_tc(m, n, static_cast<const float*>(A), lda, l, prec, seed,
-                                           static_cast<float*>(X), ldx, dev_status, stream);
+                                           static_cast<float*>(X), ldx, tcws, dev_status, stream);
     if (e == cudaErrorNotSupported) return SKEL_ERR_UNSUPPORTED;
     SK_CUDA(e);
     return SKEL_OK;
@@ -247,9 +257,32 @@ skel_status skel_id(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64
   return SKEL_OK;
 }
 
+skel_status skel_pivot_rows(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
+                            int32_t s, const int32_t* Js, int32_t* Is, void* ws,
+                            size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  if (!id_args_ok(m, n, dtype, A, lda, s, Js) || Is == nullptr) return SKEL_ERR_INVALID_ARG;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool run = pass == 1;
+    Arena ar(run ? ws : nullptr);
+    void* C = ar.take(esize(dtype) * (size_t)m * s);
+    const size_t lw = lupp_workspace(dtype, m, s, nullptr);
+    void* lws = ar.take(lw);
+    if (!run) {
+      skel_status st;
+      if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+      continue;
+    }
+    SK_CUDA(launch_gather_cols(m, s, dtype, A, lda, Js, C, m, stream));
+    // C column-major m x s is C^T row-major s x m: row pivots of C = column pivots of C^T
+    SK_TRY(run_lupp(dtype, C, m, m, s, Is, nullptr, 0, nullptr, 0, lws, lw, dev_status, stream));
+  }
+  return SKEL_OK;
+}
+
 skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
-                     int32_t s, const int32_t* Js, int32_t* Is, double* U, int64_t ldu,
-                     void* ws, size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+                     int32_t s, const int32_t* Js, int32_t* Is, int rows_given, double* U,
+                     int64_t ldu, double* sq_norms, void* ws, size_t* ws_bytes,
+                     int32_t* dev_status, cudaStream_t stream) {
   if (!id_args_ok(m, n, dtype, A, lda, s, Js) || Is == nullptr || U == nullptr || ldu < s)
     return SKEL_ERR_INVALID_ARG;
   const bool f64 = dtype == SKEL_F64;
@@ -259,8 +292,8 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
     void *C, *Qc, *Rt, *Qr;
     double *Rc, *Rr;
     SK_TRY(skeleton_qr(ar, run, m, dtype, A, lda, s, Js, &C, &Qc, &Rc, dev_status, stream));
-    const size_t lw = lupp_workspace(dtype, m, s, nullptr);
-    void* lws = ar.take(lw);
+    const size_t lw = rows_given ? 0 : lupp_workspace(dtype, m, s, nullptr);
+    void* lws = rows_given ? nullptr : ar.take(lw);
     Rt = ar.take(esize(dtype) * (size_t)n * s);
     Qr = ar.take(esize(dtype) * (size_t)n * s);
     Rr = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
@@ -270,13 +303,18 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
     double* M = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
     double* T1 = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
     double* T2 = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
+    const int64_t nbm = gemm_num_blocks(s, s);
+    double* pm = static_cast<double*>(ar.take(sizeof(double) * nbm));
+    const int64_t nba = sqnorm_num_blocks(m, n);
+    double* pa = static_cast<double*>(ar.take(sizeof(double) * nba));
     if (!run) {
       skel_status st;
       if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
       continue;
     }
     // rows by LUPP on C (Algorithm 2 line 4): C column-major m x s is C^T row-major s x m
-    SK_TRY(run_lupp(dtype, C, m, m, s, Is, nullptr, 0, nullptr, 0, lws, lw, dev_status, stream));
+    if (!rows_given)
+      SK_TRY(run_lupp(dtype, C, m, m, s, Is, nullptr, 0, nullptr, 0, lws, lw, dev_status, stream));
     SK_CUDA(launch_gather_rows_t(n, s, dtype, A, lda, Is, Rt, n, stream));
     SK_TRY(run_qr(dtype, Rt, n, n, s, Qr, n, Rr, s, qws, qn, dev_status, stream));
     GemmArgs g{};
@@ -292,7 +330,13 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
     h.B = View{Qr, 1, n}; h.b_dt = dtype;
     h.out = M; h.out_sr = s; h.out_sc = 1; h.out_dt = SKEL_F64;
     h.alpha = 1.0;
-    SK_CUDA(launch_gemm(h, f64, LEFT_LOAD, EPI_STORE, stream));
+    h.partials = pm;
+    SK_CUDA(launch_gemm(h, f64, LEFT_LOAD, EPI_STORE_SQ, stream));
+    if (sq_norms) {
+      SK_CUDA(launch_sqnorm(m, n, dtype, A, lda, pa, stream));
+      SK_CUDA(launch_reduce_sum(pa, nba, sq_norms, 0, stream));
+      SK_CUDA(launch_reduce_sum(pm, nbm, sq_norms + 1, 0, stream));
+    }
     // U = R_C^{-1} M R_R^{-T} = (R_R^{-1} (R_C^{-1} M)^T)^T
     SK_CUDA(launch_trsm_upper(s, s, Rc, s, 0, SKEL_F64, M, s, T1, s, stream));
     SK_CUDA(launch_transpose_f64(s, T1, s, T2, s, stream));

@@ -126,6 +126,7 @@ template <typename T, int LEFT, int EPI>
 cudaError_t launch_t(const GemmArgs& a, cudaStream_t st) {
   dim3 grid((unsigned)((a.N + BN - 1) / BN), (unsigned)((a.M + BM - 1) / BM));
   gemm_kernel<T, LEFT, EPI><<<grid, NT, 0, st>>>(a);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -220,6 +221,7 @@ cudaError_t launch_gemm(const GemmArgs& a, bool f64, GemmLeft left, GemmEpi epi,
 cudaError_t launch_reduce_sum(const double* partials, int64_t count, double* out, int take_sqrt,
                               cudaStream_t st) {
   reduce_sum_kernel<<<1, 1024, 0, st>>>(partials, count, out, take_sqrt);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -229,6 +231,7 @@ cudaError_t launch_sqnorm(int64_t m, int64_t n, skel_dtype dt, const void* A, in
                           double* partials, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   sqnorm_kernel<<<(unsigned)sqnorm_num_blocks(m, n), 256, 0, st>>>(m, n, dt, A, lda, partials);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -239,6 +242,7 @@ cudaError_t launch_gather_cols(int64_t m, int32_t s, skel_dtype dt, const void* 
     gather_cols_kernel<double><<<grid, 256, 0, st>>>(m, (const double*)A, lda, idx, (double*)C, ldc);
   else
     gather_cols_kernel<float><<<grid, 256, 0, st>>>(m, (const float*)A, lda, idx, (float*)C, ldc);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -249,6 +253,7 @@ cudaError_t launch_gather_rows_t(int64_t n, int32_t s, skel_dtype dt, const void
     gather_rows_t_kernel<double><<<grid, 256, 0, st>>>(n, s, (const double*)A, lda, idx, (double*)Rt, ldr);
   else
     gather_rows_t_kernel<float><<<grid, 256, 0, st>>>(n, s, (const float*)A, lda, idx, (float*)Rt, ldr);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -256,18 +261,21 @@ cudaError_t launch_gather_cols_rowmajor_f64(int32_t s, skel_dtype dt, const void
                                             const int32_t* idx, double* out, int64_t ldo,
                                             cudaStream_t st) {
   gather_cols_rm_kernel<<<s, 256, 0, st>>>(s, dt, F, ldf, idx, out, ldo);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_transpose_f64(int32_t s, const double* in, int64_t ldi, double* out,
                                  int64_t ldo, cudaStream_t st) {
   transpose_kernel<<<s, 256, 0, st>>>(s, in, ldi, out, ldo);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill_f64(double* d, int64_t count, double value, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   fill_kernel<<<(unsigned)std::min<int64_t>((count + 255) / 256, 1024), 256, 0, st>>>(d, count, value);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -109,12 +109,15 @@ cudaError_t launch_gauss_sketch_csc(int64_t m, int64_t n, const int64_t* col_ptr
                                     cudaStream_t st);
 
 // Tensor-core Gaussian sketch (sketch_tc.cu).  Returns cudaErrorNotSupported when the
-// shape is outside what the kernel handles.
+// shape or alignment is outside what the kernel handles.  ws: sketch_tc_workspace bytes.
+size_t sketch_tc_workspace(int64_t m, int64_t n, int32_t l);
 cudaError_t launch_sketch_tc(int64_t m, int64_t n, const float* A, int64_t lda, int32_t l,
-                             skel_prec prec, uint64_t seed, float* X, int64_t ldx,
+                             skel_prec prec, uint64_t seed, float* X, int64_t ldx, void* ws,
                              int32_t* dev_status, cudaStream_t st);
 
 int device_sm_count();
+// Number of kernels this library has launched in the process (diagnostics).
+void note_launches(int n);
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 }  // namespace skel

@@ -344,6 +344,7 @@ skel_status launch_pivot(bool is_lupp, const Plan& pl, PivParams<T>& p, void* ws
   cfg.numAttrs = 1;
   cudaError_t e = is_lupp ? cudaLaunchKernelEx(&cfg, lupp_kernel<T>, p)
                           : cudaLaunchKernelEx(&cfg, cpqr_kernel<T>, p);
+  note_launches(1);
   return e == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
 }
 

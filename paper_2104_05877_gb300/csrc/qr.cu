@@ -240,6 +240,7 @@ skel_status launch_qr_t(const T* C, int64_t m, int64_t ldc, int s, T* Q, int64_t
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  note_launches(1);
   return cudaLaunchKernelEx(&cfg, qr_kernel<T>, p) == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
 }
 

@@ -163,6 +163,7 @@ cudaError_t launch_sparse_pattern(int64_t m, int32_t l, int32_t zeta, uint64_t s
   if (m <= 0) return cudaSuccess;
   sparse_pattern_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(
       m, l, zeta, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), table);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -186,6 +187,7 @@ cudaError_t launch_sparse_sketch_dense(int64_t m, int64_t n, skel_dtype dt, cons
     sparse_dense_kernel<float><<<grid, 256, smem, st>>>(m, n, (const float*)A, lda, l, zeta, table,
                                                         (float*)X, ldx, (float)(1.0 / sqrt((double)zeta)), dev_status);
   }
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -199,6 +201,7 @@ cudaError_t launch_sparse_sketch_csc(int64_t m, int64_t n, const int64_t* col_pt
   if (e != cudaSuccess) return e;
   sparse_csc_kernel<<<(unsigned)((n + CT - 1) / CT), 256, smem, st>>>(
       n, col_ptr, row_idx, val, l, zeta, table, X, ldx, (float)(1.0 / sqrt((double)zeta)), dev_status);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -210,6 +213,7 @@ cudaError_t launch_gauss_sketch_csc(int64_t m, int64_t n, const int64_t* col_ptr
   gauss_csc_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(
       n, col_ptr, row_idx, val, l, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), X, ldx,
       (float)(1.0 / sqrt((double)l)), dev_status);
+  note_launches(1);
   return cudaGetLastError();
 }
 

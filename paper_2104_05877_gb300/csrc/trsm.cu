@@ -134,6 +134,7 @@ cudaError_t launch_trsm_upper(int32_t s, int64_t N, const double* R, int64_t ldr
     if (e != cudaSuccess) return e;
     trsm_upper_kernel<float><<<grid, 256, smem, st>>>(s, N, nb, R, ldr, unit_diag, (const float*)B, ldb, Y, ldy);
   }
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -167,6 +168,7 @@ cudaError_t launch_power_sqrt_lmax(int32_t s, const double* Min, int64_t ldm, do
   }
   power_kernel<<<1, 1024, 0, st>>>(s, cur, s, logs, q + 1, 300);
   eta_finalize_kernel<<<1, 32, 0, st>>>(logs, q, out);
+  note_launches(3 + q);
   return cudaGetLastError();
 }
 

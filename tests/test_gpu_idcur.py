@@ -55,7 +55,7 @@ def test_exact_rank_reconstruction_fp64(skel, dev):
     Jt = torch.from_numpy(Js.astype(np.int32)).to(dev)
     At = torch.from_numpy(A).to(dev)
     Z, _, st = skel.column_id(At, Jt)
-    Is, U, _ = skel.cur(At, Jt, status=st)
+    Is, U, _, _ = skel.cur(At, Jt, status=st)
     out, _ = skel.error(At, Jt, Z, Is, U, status=st)
     skel.check_status(st)
     e = out.cpu().numpy()
@@ -70,7 +70,7 @@ def test_cur_matches_oracle(skel, dev, dt):
     k = 30
     Js = _js(Ad, k, 10, 3)["Js"]
     Jt = torch.from_numpy(Js.astype(np.int32)).to(dev)
-    Is, U, st = skel.cur(torch.from_numpy(np.asfortranarray(A)).to(dev), Jt)
+    Is, U, sq, st = skel.cur(torch.from_numpy(np.asfortranarray(A)).to(dev), Jt)
     skel.check_status(st)
     Isg = Is.cpu().numpy()
     rp = pivoting.lupp_rows(Ad[:, Js], k)

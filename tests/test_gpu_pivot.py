@@ -39,16 +39,24 @@ def test_lupp_fp64_global_slab_path(skel, dev):
     assert np.array_equal(Rf.cpu().numpy(), ref["R"])
 
 
-@pytest.mark.parametrize("l,n,s", [(40, 1000, 32), (300, 4096, 256)])
-def test_lupp_fp32_prefix(skel, dev, l, n, s):
+def _separated(l, n, seed, ratio):
+    """Gaussian X with geometric column scales in random order: wide pivot gaps."""
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((l, n)) * ratio ** rng.permutation(n)[None, :]).astype(np.float32)
+
+
+@pytest.mark.parametrize("l,n,s,ratio,min_prefix", [(40, 1000, 32, 0.7, 32), (300, 4096, 256, 0.93, 200),
+                                                    (300, 4096, 256, 1.0, 0)])
+def test_lupp_fp32_prefix(skel, dev, l, n, s, ratio, min_prefix):
     """FP32 arithmetic: pivots equal the FP64 oracle's up to the first step whose relative
-    gap is below 1e-3 (1e4 x the FP32 unit roundoff)."""
-    X = np.random.default_rng(n).standard_normal((l, n)).astype(np.float32)
+    gap is below 1e-3 (1e4 x the FP32 unit roundoff); on well-separated inputs that prefix
+    covers (nearly) every step."""
+    X = _separated(l, n, n + s, ratio)
     Js, _, Rf, st = skel.pivot_lupp(torch.from_numpy(X).to(dev), s)
     skel.check_status(st)
     ref = pivoting.lupp_columns(X.astype(np.float64), s)
     k = _prefix(ref["gaps"], 1e-3)
-    assert k >= min(s, 10)
+    assert k >= min_prefix
     assert np.array_equal(Js.cpu().numpy()[:k], ref["Js"][:k])
     R = Rf.cpu().numpy()
     assert np.max(np.abs(R)) <= 1.0 + 1e-6
@@ -94,16 +102,17 @@ def test_row_lupp_on_tall_C(skel, dev, m, s):
     assert np.array_equal(Is.cpu().numpy(), pivoting.lupp_rows(C, s)["Js"])
 
 
-@pytest.mark.parametrize("l,n,s,dt", [(20, 300, 20, np.float64), (64, 2000, 48, np.float64),
-                                      (80, 8192, 64, np.float32), (40, 777, 30, np.float32)])
-def test_cpqr_prefix(skel, dev, l, n, s, dt):
-    X = np.random.default_rng(l + n).standard_normal((l, n)).astype(dt)
+@pytest.mark.parametrize("l,n,s,dt,ratio,min_prefix", [(20, 300, 20, np.float64, 1.0, 2), (64, 2000, 48, np.float64, 1.0, 1),
+                                                      (80, 8192, 64, np.float32, 0.95, 20), (40, 777, 30, np.float32, 0.8, 30),
+                                                      (80, 8192, 64, np.float32, 1.0, 0)])
+def test_cpqr_prefix(skel, dev, l, n, s, dt, ratio, min_prefix):
+    X = _separated(l, n, l + n, ratio).astype(dt)
     Js, Rf, st = skel.pivot_cpqr(torch.from_numpy(X).to(dev), s)
     skel.check_status(st)
     ref = pivoting.cpqr_columns(X.astype(np.float64), s)
     delta = 1e-9 if dt == np.float64 else 1e-3
     k = _prefix(ref["gaps"], delta)
-    assert k >= min(s, 8)
+    assert k >= min_prefix
     Jg = Js.cpu().numpy()
     assert np.array_equal(Jg[:k], ref["Js"][:k])
     R = Rf.cpu().numpy().astype(np.float64)

@@ -74,7 +74,9 @@ def test_sparse_sign_pattern_is_exact(skel, dev):
     X, st = skel.sketch(torch.from_numpy(A).to(dev), l, kind="sparse_sign", prec="f64", seed=3, zeta=l)
     skel.check_status(st)
     want = sketch.sparse_sign_sketch(A, l, l, 3)
-    assert np.array_equal(X.cpu().numpy() * np.sqrt(l), np.round(want * np.sqrt(l)))
+    got = X.cpu().numpy() * np.sqrt(l)
+    assert np.max(np.abs(got - np.round(got))) < 1e-9
+    assert np.array_equal(np.round(got), np.round(want * np.sqrt(l)))
     # zeta < l: single column of A with one nonzero per row isolates each Gamma column
     m2, l2, z2 = 40, 16, 5
     A2 = np.asfortranarray(np.eye(m2))
@@ -109,3 +111,34 @@ def test_gaussian_csc(skel, dev):
     Ad = A.toarray().astype(np.float64)
     want = sketch.gaussian_sketch(Ad, l, 2)
     assert np.all(np.abs(X.cpu().numpy() - want) <= _bound(l, 500, 2, Ad, 2.0 ** -22) + 1e-6 * _bound(l, 500, 2, Ad, 1.0) / 500)
+
+
+@pytest.mark.parametrize("m,n,l", [(1000, 777, 61), (2048, 1536, 272), (4096, 600, 130), (300, 5000, 40),
+                                   (129, 513, 128), (8192, 1024, 528)])
+def test_sketch_tf32_tensor_cores(skel, dev, m, n, l):
+    """tcgen05 kind::tf32 sketch: Gamma is rounded to TF32 in the kernel and A is read by the
+    tensor core as TF32 (at most 2^-10 relative per operand); accumulation is FP32.  Bound:
+    |dX| <= (2^-9 + m 2^-23) (|G| |A|) / sqrt(l) elementwise against the exact FP64 sketch."""
+    A = workloads.dense_config2(m, n, seed=m + l)
+    X, st = skel.sketch(torch.from_numpy(A).to(dev), l, prec="tf32", seed=77)
+    skel.check_status(st)
+    Ad = A.astype(np.float64)
+    want = sketch.gaussian_sketch(Ad, l, 77)
+    G = embedding.gaussian_normals(l, m, 77)
+    bound = (2.0 ** -9 + m * 2.0 ** -23) * (np.abs(G) @ np.abs(Ad)) / np.sqrt(l)
+    err = np.abs(X.cpu().numpy() - want)
+    assert np.all(err <= bound), (err / bound).max()
+
+
+def test_sketch_tf32_padded_lda(skel, dev):
+    """A stored with lda > m (a multiple of 4): only the m x n view is read."""
+    m, n, l = 700, 300, 50
+    full = np.asfortranarray(np.random.default_rng(1).standard_normal((704, n)).astype(np.float32))
+    At = torch.from_numpy(full).to(dev)[:m, :]
+    X, st = skel.sketch(At, l, prec="tf32", seed=3)
+    skel.check_status(st)
+    Ad = full[:m].astype(np.float64)
+    want = sketch.gaussian_sketch(Ad, l, 3)
+    G = embedding.gaussian_normals(l, m, 3)
+    bound = (2.0 ** -9 + m * 2.0 ** -23) * (np.abs(G) @ np.abs(Ad)) / np.sqrt(l)
+    assert np.all(np.abs(X.cpu().numpy() - want) <= bound)
