@@ -234,12 +234,14 @@ skel_status skel_id(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64
     double* pw = static_cast<double*>(ar.take(sizeof(double) * nbw));
     const int64_t nba = sqnorm_num_blocks(m, n);
     double* pa = static_cast<double*>(ar.take(sizeof(double) * nba));
+    void* kws = ar.take(gemm_workspace(s, n, m, f64));
     if (!run) {
       skel_status st;
       if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
       continue;
     }
     GemmArgs g{};
+    g.splitk_ws = kws;
     g.M = s; g.N = n; g.K = m;
     g.L = View{Q, m, 1}; g.l_dt = dtype;          // Q^T(r, i) = Q(i, r)
     g.B = View{A, 1, lda}; g.b_dt = dtype;
@@ -307,6 +309,8 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
     double* pm = static_cast<double*>(ar.take(sizeof(double) * nbm));
     const int64_t nba = sqnorm_num_blocks(m, n);
     double* pa = static_cast<double*>(ar.take(sizeof(double) * nba));
+    void* kws1 = ar.take(gemm_workspace(s, n, m, f64));
+    void* kws2 = ar.take(gemm_workspace(s, s, n, f64));
     if (!run) {
       skel_status st;
       if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
@@ -318,6 +322,7 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
     SK_CUDA(launch_gather_rows_t(n, s, dtype, A, lda, Is, Rt, n, stream));
     SK_TRY(run_qr(dtype, Rt, n, n, s, Qr, n, Rr, s, qws, qn, dev_status, stream));
     GemmArgs g{};
+    g.splitk_ws = kws1;
     g.M = s; g.N = n; g.K = m;
     g.L = View{Qc, m, 1}; g.l_dt = dtype;
     g.B = View{A, 1, lda}; g.b_dt = dtype;
@@ -325,6 +330,7 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
     g.alpha = 1.0;
     SK_CUDA(launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, stream));
     GemmArgs h{};
+    h.splitk_ws = kws2;
     h.M = s; h.N = s; h.K = n;
     h.L = View{W, n, 1}; h.l_dt = dtype;
     h.B = View{Qr, 1, n}; h.b_dt = dtype;
@@ -372,7 +378,8 @@ skel_status skel_error(int64_t m, int64_t n, skel_dtype dtype, const void* A, in
     double* R1 = Rf ? static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s)) : nullptr;
     double* M1 = Rf ? static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s)) : nullptr;
     double* M2 = Rf ? static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s)) : nullptr;
-    double* pscr = Rf ? static_cast<double*>(ar.take(sizeof(double) * (16 + 2 * (size_t)s * s))) : nullptr;
+    double* pscr = Rf ? static_cast<double*>(ar.take(power_scratch_bytes(s))) : nullptr;
+    void* kwsh = Rf ? ar.take(gemm_workspace(s, s, n, true)) : nullptr;
     if (!run) {
       skel_status st;
       if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
@@ -415,6 +422,7 @@ skel_status skel_error(int64_t m, int64_t n, skel_dtype dtype, const void* A, in
     if (Rf) {
       // eta^2 = lambda_max(R_1^{-1} (R R^T) R_1^{-T}) = 1 + ||R_1^{-1} R_2||_2^2
       GemmArgs g{};
+      g.splitk_ws = kwsh;
       g.M = s; g.N = s; g.K = n;
       g.L = View{Rf, ldrf, 1}; g.l_dt = rf_dtype;
       g.B = View{Rf, 1, ldrf}; g.b_dt = rf_dtype;

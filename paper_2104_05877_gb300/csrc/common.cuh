@@ -104,15 +104,25 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int32_t* p) {
 }
 
 // ------------------------------------------------------------------------------------
-// Grid all-gather for persistent cooperative kernels.  Every CTA b owns slot b of two
-// parity buffers; step t publishes into buffer t&1 with tag t+1 (tags start at 0 because
-// the host clears them before each launch).  A CTA publishes step t+1 only after it has
-// read step t, so two buffers suffice.  Payloads must be read with L2-only loads (__ldcg).
+// Grid-wide step synchronisation for persistent cooperative kernels.
+//   * arrival: one release-ordered atomicAdd per CTA on a monotonic counter (zeroed by the
+//     host before the launch); step t is complete when the counter reaches G*(t+1);
+//   * waiting: a single thread per CTA polls the counter (acquire), so polling traffic is G
+//     loads per round on one line instead of one per thread;
+//   * payload: every CTA owns slot b of two parity buffers; a CTA arrives at step t+1 only
+//     after it has read step t, so two buffers suffice.  Payloads are read with L2-only
+//     loads (__ldcg) because the same addresses are rewritten two steps later;
+//   * keys: one packed 64-bit word per step for argmax reductions by atomicMax (zeroed by
+//     the host), (order-preserving magnitude bits << 32) | (0xFFFFFFFF - index), so the
+//     largest magnitude wins and equal magnitudes go to the lowest index.
+// Every wait is bounded (wait_ns); a CTA that gives up sets `abort`, which makes the others
+// give up at their next poll.
 // ------------------------------------------------------------------------------------
 struct GridComm {
-  int32_t* tags;       // [2 * G]
-  int32_t* abort;      // one word: set when any CTA gives up
-  char* payload;       // [2 * G * slot_bytes]
+  unsigned int* counter;
+  int32_t* abort;
+  unsigned long long* keys;
+  char* payload;
   int64_t slot_bytes;
   int G;
   uint64_t wait_ns;
@@ -121,42 +131,61 @@ struct GridComm {
   }
 };
 
-// Publish this CTA's slot for `step` (call after all threads wrote the payload; contains a
-// __syncthreads).
-__device__ __forceinline__ void comm_publish(const GridComm& gc, int step) {
+// Bytes of the header region of a GridComm workspace: counter, abort, keys[nsteps].
+__host__ __device__ inline size_t comm_header_bytes(int nsteps) {
+  return 256 + (((size_t)8 * (nsteps > 0 ? nsteps : 1) + 255) / 256) * 256;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Arrive at `step` (after this CTA's payload writes; contains a __syncthreads).
+__device__ __forceinline__ void comm_arrive(const GridComm& gc, int step) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    st_release_gpu(gc.tags + (step & 1) * gc.G + blockIdx.x, step + 1);
+    atomicAdd(gc.counter, 1u);
   }
 }
 
-// Wait until every CTA published `step`.  Returns false (uniformly over the CTA) on timeout
-// or abort; the caller then records its error and leaves.  Needs blockDim.x >= G.
-__device__ __forceinline__ bool comm_wait_all(const GridComm& gc, int step, int32_t* dev_status) {
+// Wait until every CTA arrived at `step`.  Returns false (uniformly over the CTA) on timeout
+// or abort; the caller then leaves.
+__device__ __forceinline__ bool comm_wait(const GridComm& gc, int step, int32_t* dev_status) {
   __shared__ int s_fail;
-  if (threadIdx.x == 0) s_fail = 0;
-  __syncthreads();
-  if (threadIdx.x < gc.G) {
-    const int32_t* tag = gc.tags + (step & 1) * gc.G + threadIdx.x;
-    const uint64_t t0 = global_ns();
-    uint32_t it = 0;
-    while (ld_acquire_gpu(tag) < step + 1) {
-      if ((++it & 63u) == 0) {
-        if (ld_relaxed_gpu(gc.abort) != 0) { s_fail = 1; break; }
-        if (global_ns() - t0 > gc.wait_ns) {
-          s_fail = 2;
-          atomicExch(gc.abort, 1);
-          break;
+  if (threadIdx.x == 0) {
+    const unsigned int target = (unsigned int)gc.G * (unsigned int)(step + 1);
+    int fail = 0;
+    if ((int)(ld_acquire_u32(gc.counter) - target) < 0) {
+      const uint64_t t0 = global_ns();
+      uint32_t it = 0;
+      while ((int)(ld_acquire_u32(gc.counter) - target) < 0) {
+        if ((++it & 15u) == 0) {
+          if (ld_relaxed_gpu(gc.abort) != 0) { fail = 1; break; }
+          if (global_ns() - t0 > gc.wait_ns) {
+            fail = 2;
+            atomicExch(gc.abort, 1);
+            record_error(dev_status, SKEL_ERR_TIMEOUT, step);
+            break;
+          }
         }
       }
     }
+    s_fail = fail;
   }
   __syncthreads();
   const int f = s_fail;
-  if (f == 2 && threadIdx.x == 0) record_error(dev_status, SKEL_ERR_TIMEOUT, step);
-  __threadfence();
+  __syncthreads();
   return f == 0;
+}
+
+__device__ __forceinline__ unsigned long long pack_key(float mag, int64_t idx) {
+  return ((unsigned long long)__float_as_uint(mag) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)idx);
+}
+__device__ __forceinline__ int64_t key_index(unsigned long long key) {
+  return (int64_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
 }
 
 // Block-wide argmax of (key, index): larger key wins; equal keys -> smaller index.

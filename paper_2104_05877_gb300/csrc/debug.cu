@@ -52,8 +52,8 @@ __global__ void curand_philox_kernel(uint64_t seed, int64_t nseq, int per_seq, u
 // other CTA waits at most wait_ns and then reports SKEL_ERR_TIMEOUT.
 __global__ void grid_wait_kernel(GridComm gc, int absent, int32_t* dev_status) {
   if ((int)blockIdx.x == absent) return;
-  comm_publish(gc, 0);
-  comm_wait_all(gc, 0, dev_status);
+  comm_arrive(gc, 0);
+  comm_wait(gc, 0, dev_status);
 }
 
 }  // namespace
@@ -70,15 +70,16 @@ skel_status skel_debug_curand_philox(uint64_t seed, int64_t nseq, int per_seq, u
 skel_status skel_debug_grid_timeout(int grid, uint64_t wait_ns, void* ws, size_t* ws_bytes,
                                     int32_t* dev_status, cudaStream_t stream) {
   if (grid < 2 || grid > 256 || ws_bytes == nullptr || wait_ns > 5000000000ull) return SKEL_ERR_INVALID_ARG;
-  const size_t need = align_up(sizeof(int32_t) * (2 * grid + 1)) + align_up(2 * (size_t)grid * 16);
+  const size_t need = comm_header_bytes(1);
   if (ws == nullptr) { *ws_bytes = need; return SKEL_OK; }
   if (*ws_bytes < need) return SKEL_ERR_WORKSPACE;
   char* base = static_cast<char*>(ws);
   GridComm gc{};
-  gc.tags = reinterpret_cast<int32_t*>(base);
-  gc.abort = gc.tags + 2 * grid;
-  gc.payload = base + align_up(sizeof(int32_t) * (2 * grid + 1));
-  gc.slot_bytes = 16;
+  gc.counter = reinterpret_cast<unsigned int*>(base);
+  gc.abort = reinterpret_cast<int32_t*>(base + 4);
+  gc.keys = nullptr;
+  gc.payload = nullptr;
+  gc.slot_bytes = 0;
   gc.G = grid;
   gc.wait_ns = wait_ns;
   if (cudaMemsetAsync(base, 0, need, stream) != cudaSuccess) return SKEL_ERR_CUDA;

@@ -20,7 +20,7 @@ __device__ __forceinline__ T load_as(const void* p, int64_t off, skel_dtype dt) 
                         : (T)__ldg(static_cast<const float*>(p) + off);
 }
 
-template <typename T, int LEFT, int EPI>
+template <typename T, int LEFT, int EPI, bool SPLIT>
 __global__ void __launch_bounds__(NT) gemm_kernel(const GemmArgs a) {
   __shared__ T Ls[BK][BM + 4];
   __shared__ T Bs[BK][BN + 4];
@@ -35,7 +35,9 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmArgs a) {
 
   const bool l_kcontig = (a.L.sc == 1);
   const bool b_kcontig = (a.B.sr == 1);
-  for (int64_t kb = 0; kb < a.K; kb += BK) {
+  const int64_t kz0 = (int64_t)blockIdx.z * a.kchunk;
+  const int64_t kz1 = kz0 + a.kchunk < a.K ? kz0 + a.kchunk : a.K;
+  for (int64_t kb = kz0; kb < kz1; kb += BK) {
     // ---- left tile (BM x BK) ----
     if (LEFT == LEFT_GAUSSIAN) {
       const int r = tid >> 2, k4 = tid & 3;       // 64 rows x 4 groups of 4 columns
@@ -91,6 +93,20 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmArgs a) {
   }
 
   // ---- epilogue ----
+  if (SPLIT) {        // raw partial sums of this K-chunk: ws[z][r][c]
+    T* ws = static_cast<T*>(a.splitk_ws) + (int64_t)blockIdx.z * a.M * a.N;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int64_t gr = r0 + ty * TM + i;
+      if (gr >= a.M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int64_t gc = c0 + tx + 16 * j;
+        if (gc < a.N) ws[gr * a.N + gc] = acc[i][j];
+      }
+    }
+    return;
+  }
   const T alpha = (T)a.alpha;
   double part = 0.0;
   bool bad = false;
@@ -122,25 +138,58 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmArgs a) {
   }
 }
 
+// Sum the K-chunk partials in chunk order, then apply the STORE / STORE_SQ epilogue.  The
+// grid has gemm_num_blocks(M, N) CTAs so that STORE_SQ writes as many partials as the
+// unsplit kernel.
+template <typename T, int EPI>
+__global__ void __launch_bounds__(NT) splitk_reduce_kernel(const GemmArgs a, int nz) {
+  const T* ws = static_cast<const T*>(a.splitk_ws);
+  const int64_t total = a.M * a.N;
+  double part = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    T acc = T(0);
+    for (int z = 0; z < nz; ++z) acc += ws[(int64_t)z * total + e];
+    const T v = (T)a.alpha * acc;
+    const int64_t r = e / a.N, c = e % a.N;
+    const int64_t off = r * a.out_sr + c * a.out_sc;
+    if (a.out_dt == SKEL_F64) static_cast<double*>(a.out)[off] = (double)v;
+    else static_cast<float*>(a.out)[off] = (float)v;
+    if (EPI == EPI_STORE_SQ) part += (double)v * (double)v;
+  }
+  if (EPI == EPI_STORE_SQ) {
+    const double tot = block_sum<double>(part);
+    if (threadIdx.x == 0) a.partials[blockIdx.x] = tot;
+  }
+}
+
 template <typename T, int LEFT, int EPI>
-cudaError_t launch_t(const GemmArgs& a, cudaStream_t st) {
-  dim3 grid((unsigned)((a.N + BN - 1) / BN), (unsigned)((a.M + BM - 1) / BM));
-  gemm_kernel<T, LEFT, EPI><<<grid, NT, 0, st>>>(a);
-  note_launches(1);
+cudaError_t launch_t(const GemmArgs& a0, int nz, cudaStream_t st) {
+  GemmArgs a = a0;
+  const unsigned gx = (unsigned)((a.N + BN - 1) / BN), gy = (unsigned)((a.M + BM - 1) / BM);
+  if (nz > 1 && (EPI == EPI_STORE || EPI == EPI_STORE_SQ) && LEFT == LEFT_LOAD) {
+    gemm_kernel<T, LEFT, EPI, true><<<dim3(gx, gy, nz), NT, 0, st>>>(a);
+    splitk_reduce_kernel<T, EPI><<<gx * gy, NT, 0, st>>>(a, nz);
+    note_launches(2);
+  } else {
+    a.kchunk = a.K;
+    gemm_kernel<T, LEFT, EPI, false><<<dim3(gx, gy, 1), NT, 0, st>>>(a);
+    note_launches(1);
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t dispatch_epi(const GemmArgs& a, GemmLeft left, GemmEpi epi, cudaStream_t st) {
+cudaError_t dispatch_epi(const GemmArgs& a, int nz, GemmLeft left, GemmEpi epi, cudaStream_t st) {
   if (left == LEFT_GAUSSIAN) {
-    if (epi == EPI_SKETCH) return launch_t<T, LEFT_GAUSSIAN, EPI_SKETCH>(a, st);
+    if (epi == EPI_SKETCH) return launch_t<T, LEFT_GAUSSIAN, EPI_SKETCH>(a, 1, st);
     return cudaErrorInvalidValue;
   }
   switch (epi) {
-    case EPI_STORE: return launch_t<T, LEFT_LOAD, EPI_STORE>(a, st);
-    case EPI_STORE_SQ: return launch_t<T, LEFT_LOAD, EPI_STORE_SQ>(a, st);
-    case EPI_RESID: return launch_t<T, LEFT_LOAD, EPI_RESID>(a, st);
-    case EPI_SKETCH: return launch_t<T, LEFT_LOAD, EPI_SKETCH>(a, st);
+    case EPI_STORE: return launch_t<T, LEFT_LOAD, EPI_STORE>(a, nz, st);
+    case EPI_STORE_SQ: return launch_t<T, LEFT_LOAD, EPI_STORE_SQ>(a, nz, st);
+    case EPI_RESID: return launch_t<T, LEFT_LOAD, EPI_RESID>(a, 1, st);
+    case EPI_SKETCH: return launch_t<T, LEFT_LOAD, EPI_SKETCH>(a, 1, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -212,10 +261,33 @@ __global__ void fill_kernel(double* d, int64_t count, double v) {
 
 int64_t gemm_num_blocks(int64_t M, int64_t N) { return ((N + BN - 1) / BN) * ((M + BM - 1) / BM); }
 
-cudaError_t launch_gemm(const GemmArgs& a, bool f64, GemmLeft left, GemmEpi epi, cudaStream_t st) {
-  if (a.M <= 0 || a.N <= 0) return cudaSuccess;
-  if ((a.M + BM - 1) / BM > 65535) return cudaErrorInvalidValue;
-  return f64 ? dispatch_epi<double>(a, left, epi, st) : dispatch_epi<float>(a, left, epi, st);
+// K-split factor: enough CTAs for two waves, chunks of at least 256 along K.
+static int splitk_factor(int64_t M, int64_t N, int64_t K) {
+  const int64_t tiles = gemm_num_blocks(M, N);
+  const int64_t want = 2 * (int64_t)device_sm_count();
+  if (tiles >= want || K < 512) return 1;
+  int64_t z = (want + tiles - 1) / tiles;
+  z = std::min<int64_t>(z, K / 256);
+  z = std::min<int64_t>(z, 64);
+  return (int)std::max<int64_t>(z, 1);
+}
+
+size_t gemm_workspace(int64_t M, int64_t N, int64_t K, bool f64) {
+  const int z = splitk_factor(M, N, K);
+  return z > 1 ? align_up((size_t)z * M * N * (f64 ? 8 : 4)) : 0;
+}
+
+cudaError_t launch_gemm(const GemmArgs& a0, bool f64, GemmLeft left, GemmEpi epi, cudaStream_t st) {
+  if (a0.M <= 0 || a0.N <= 0) return cudaSuccess;
+  if ((a0.M + BM - 1) / BM > 65535) return cudaErrorInvalidValue;
+  GemmArgs a = a0;
+  int nz = a.splitk_ws ? splitk_factor(a.M, a.N, a.K) : 1;
+  if (nz > 1) {
+    const int64_t per = (a.K + nz - 1) / nz;
+    a.kchunk = (per + BK - 1) / BK * BK;
+    nz = (int)((a.K + a.kchunk - 1) / a.kchunk);
+  }
+  return f64 ? dispatch_epi<double>(a, nz, left, epi, st) : dispatch_epi<float>(a, nz, left, epi, st);
 }
 
 cudaError_t launch_reduce_sum(const double* partials, int64_t count, double* out, int take_sqrt,

@@ -32,11 +32,16 @@ struct GemmArgs {
   void* out; int64_t out_sr, out_sc; skel_dtype out_dt;
   View ref; skel_dtype ref_dt;     // EPI_RESID
   double alpha;
-  double* partials;                // EPI_STORE_SQ / EPI_RESID: one double per CTA
+  double* partials;                // EPI_STORE_SQ / EPI_RESID: gemm_num_blocks(M, N) doubles
   uint64_t seed;                   // LEFT_GAUSSIAN
   int32_t* dev_status;
+  void* splitk_ws;                 // optional: gemm_workspace() bytes enable a K-split
+  int64_t kchunk;                  // set by launch_gemm
 };
 int64_t gemm_num_blocks(int64_t M, int64_t N);
+// Scratch for splitting K across CTAs when the M x N tiles cannot fill the GPU (STORE and
+// STORE_SQ epilogues with a loaded left operand); 0 when no split is used.
+size_t gemm_workspace(int64_t M, int64_t N, int64_t K, bool f64);
 cudaError_t launch_gemm(const GemmArgs& a, bool f64, GemmLeft left, GemmEpi epi, cudaStream_t st);
 
 // Sum `count` doubles in `partials` (deterministic) into *out (device), optionally sqrt.
@@ -69,10 +74,11 @@ cudaError_t launch_trsm_upper(int32_t s, int64_t N, const double* R, int64_t ldr
                               skel_dtype b_dt, const void* B, int64_t ldb, double* Y, int64_t ldy,
                               cudaStream_t st);
 
-// eta = sqrt(lambda_max(G)) for a symmetric positive definite s x s FP64 G (row-major),
-// by power iteration in one CTA.  Writes *out.
+// sqrt(lambda_max(G)) for a symmetric positive definite s x s FP64 G (row-major): trace
+// normalisation and repeated squaring, then power iteration in one CTA.  Writes *out.
+size_t power_scratch_bytes(int32_t s);
 cudaError_t launch_power_sqrt_lmax(int32_t s, const double* G, int64_t ldg, double* out,
-                                   double* scratch /* 2*s doubles */, cudaStream_t st);
+                                   double* scratch /* power_scratch_bytes(s) */, cudaStream_t st);
 
 // Persistent pivoting kernels (pivot.cu).
 size_t lupp_workspace(skel_dtype dt, int64_t n, int32_t s, int* grid_out);

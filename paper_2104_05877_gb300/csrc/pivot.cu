@@ -7,13 +7,16 @@
 //
 // Design: one persistent cooperative grid.  CTA b owns a contiguous slab of columns and
 // keeps rows 0..s-1 (LUPP) or 0..l-1 (CPQR) of its slab resident in shared memory (global
-// workspace when the slab does not fit).  Each step costs one grid-wide all-gather: every
-// CTA publishes its best local candidate together with that candidate's column; after the
-// wait every CTA reduces the G candidates in the same order (lowest index wins ties), reads
-// the winner's column and updates its own slab.  The winner's column is frozen once
-// selected, so its published copy stays valid.  The LUPP update uses separately rounded
-// multiply and subtract (no FMA contraction), the operation order of the textbook
-// algorithm, so FP64 runs reproduce a plain FP64 restatement bit for bit.
+// workspace when the slab does not fit).  Each step costs one grid-wide barrier: every CTA
+// publishes its best local candidate and that candidate's column, then arrives; the argmax
+// is a single packed 64-bit atomicMax per CTA for FP32 data, or a fixed-order scan of the G
+// published candidates for FP64 data.  The winner's column is frozen once selected, so its
+// published copy stays valid.  LUPP looks one step ahead: after the pivot of step t arrives,
+// a CTA first updates row t+1 (and its own next candidate column), publishes its candidate
+// for step t+1, and only then applies the rest of the Schur update while the barrier
+// completes.  The LUPP update uses separately rounded multiply and subtract (no FMA
+// contraction), the operation order of the textbook algorithm, so FP64 runs reproduce a
+// plain FP64 restatement bit for bit.
 #include <algorithm>
 
 #include "common.cuh"
@@ -58,19 +61,60 @@ __device__ void fail_tail(const PivParams<T>& p, int t, int code) {
   if (threadIdx.x == 0) atomicExch(p.gc.abort, 1);
 }
 
-// Reduce the G published candidates (header only) to the winner: returns (key, index).
-template <typename T, bool KEY_IS_MAG>
-__device__ KeyIdx<T> reduce_candidates(const GridComm& gc, int t) {
+// Publish this CTA's candidate (index, value, column rows r0..r1-1) for `step`.
+template <typename T>
+__device__ __forceinline__ void publish(const GridComm& gc, int step, int64_t idx, T val, T key,
+                                        const T* W, int64_t ldw, int jb, int r0, int r1) {
+  char* sl = gc.slot(step, blockIdx.x);
+  T* col = reinterpret_cast<T*>(sl + kHeader);
+  for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) col[r] = W[(int64_t)r * ldw + jb];
+  if (threadIdx.x == 0) {
+    *reinterpret_cast<long long*>(sl) = idx;
+    *reinterpret_cast<T*>(sl + 8) = val;
+    if constexpr (sizeof(T) == 4) atomicMax(gc.keys + step, pack_key((float)key, idx));
+  }
+}
+
+// Winner of `step` (call after comm_wait): its global index, or -1 if nobody published.
+template <typename T>
+__device__ int64_t winner(const GridComm& gc, int step, bool key_is_mag) {
+  if constexpr (sizeof(T) == 4) {
+    __shared__ long long s_w;
+    if (threadIdx.x == 0) {
+      const unsigned long long k = __ldcg(gc.keys + step);
+      s_w = k == 0ull ? -1 : key_index(k);
+    }
+    __syncthreads();
+    const long long w = s_w;
+    __syncthreads();
+    return w;
+  } else {
+    T key = T(-1);
+    int64_t idx = INT64_MAX;
+    for (int q = threadIdx.x; q < gc.G; q += blockDim.x) {
+      const char* sl = gc.slot(step, q);
+      const long long ci = __ldcg(reinterpret_cast<const long long*>(sl));
+      if (ci >= 0) {
+        const T v = __ldcg(reinterpret_cast<const T*>(sl + 8));
+        const T kq = key_is_mag ? pivot_key(v) : (isfinite(v) ? v : T(INFINITY));
+        if (better(kq, (int64_t)ci, key, idx)) { key = kq; idx = ci; }
+      }
+    }
+    const KeyIdx<T> r = block_argmax<T>(key, idx);
+    return r.idx == INT64_MAX ? -1 : r.idx;
+  }
+}
+
+// Local argmax of |W(row, jj)| over unselected local columns.
+template <typename T>
+__device__ __forceinline__ KeyIdx<T> local_best(const T* W, int64_t ldw, int row, int nl, int64_t c0,
+                                                const unsigned char* sel) {
   T key = T(-1);
   int64_t idx = INT64_MAX;
-  if ((int)threadIdx.x < gc.G) {
-    const char* sl = gc.slot(t, threadIdx.x);
-    const long long ci = __ldcg(reinterpret_cast<const long long*>(sl));
-    if (ci >= 0) {
-      const T v = __ldcg(reinterpret_cast<const T*>(sl + 8));
-      key = KEY_IS_MAG ? pivot_key(v) : (isfinite(v) ? v : T(INFINITY));
-      idx = ci;
-    }
+  for (int jj = threadIdx.x; jj < nl; jj += blockDim.x) {
+    if (sel[jj]) continue;
+    const T k = pivot_key(W[(int64_t)row * ldw + jj]);
+    if (better(k, c0 + jj, key, idx)) { key = k; idx = c0 + jj; }
   }
   return block_argmax<T>(key, idx);
 }
@@ -100,46 +144,31 @@ __global__ void __launch_bounds__(kThreads) lupp_kernel(const PivParams<T> p) {
     for (int64_t e = tid; e < (int64_t)s * s; e += bd) p.L[(e / s) * p.ldl + (e % s)] = T(0);
   __syncthreads();
 
-  for (int t = 0; t < s; ++t) {
-    // local candidate: largest |S(t, j)| among unselected local columns
-    T key = T(-1);
-    int64_t idx = INT64_MAX;
-    for (int jj = tid; jj < nl; jj += bd) {
-      if (sel[jj]) continue;
-      const T k = pivot_key(W[(int64_t)t * nloc + jj]);
-      if (better(k, c0 + jj, key, idx)) { key = k; idx = c0 + jj; }
-    }
-    const KeyIdx<T> mine = block_argmax<T>(key, idx);
-    char* sl = p.gc.slot(t, b);
-    if (mine.key >= T(0)) {
-      const int jb = (int)(mine.idx - c0);
-      T* col = reinterpret_cast<T*>(sl + kHeader);
-      for (int r = t + tid; r < s; r += bd) col[r] = W[(int64_t)r * nloc + jb];
-      if (tid == 0) {
-        *reinterpret_cast<long long*>(sl) = mine.idx;
-        *reinterpret_cast<T*>(sl + 8) = W[(int64_t)t * nloc + jb];
-      }
+  // step 0 candidate
+  {
+    const KeyIdx<T> c = local_best<T>(W, nloc, 0, nl, c0, sel);
+    if (c.key >= T(0)) {
+      const int jb = (int)(c.idx - c0);
+      publish<T>(p.gc, 0, c.idx, W[jb], c.key, W, nloc, jb, 0, s);
     } else if (tid == 0) {
-      *reinterpret_cast<long long*>(sl) = -1;
+      *reinterpret_cast<long long*>(p.gc.slot(0, b)) = -1;
     }
-    comm_publish(p.gc, t);
-    if (!comm_wait_all(p.gc, t, p.dev_status)) return;
+    comm_arrive(p.gc, 0);
+  }
 
-    const KeyIdx<T> win = reduce_candidates<T, true>(p.gc, t);
-    if (win.idx == INT64_MAX) { fail_tail(p, t, SKEL_ERR_INVALID_ARG); return; }
-    const int wb = (int)(win.idx / nloc);
-    const char* wsl = p.gc.slot(t, wb);
+  for (int t = 0; t < s; ++t) {
+    if (!comm_wait(p.gc, t, p.dev_status)) return;
+    const int64_t w = winner<T>(p.gc, t, true);
+    if (w < 0) { fail_tail(p, t, SKEL_ERR_INVALID_ARG); return; }
+    const char* wsl = p.gc.slot(t, (int)(w / nloc));
     const T piv = __ldcg(reinterpret_cast<const T*>(wsl + 8));
     if (!isfinite(piv)) { fail_tail(p, t, SKEL_ERR_NONFINITE); return; }
     if (piv == T(0)) { fail_tail(p, t, SKEL_ERR_RANK_DEFICIENT); return; }
     const T* wcol = reinterpret_cast<const T*>(wsl + kHeader);
     for (int r = t + tid; r < s; r += bd) pivcol[r] = __ldcg(wcol + r);
-    if (b == 0 && tid == 0) p.Js[t] = (int32_t)win.idx;
-    __syncthreads();
-    if (b == 0 && p.L)
-      for (int r = t + tid; r < s; r += bd) p.L[(int64_t)r * p.ldl + t] = pivcol[r];
-
-    const int jw = (win.idx >= c0 && win.idx < c0 + nl) ? (int)(win.idx - c0) : -1;
+    if (b == 0 && tid == 0) p.Js[t] = (int32_t)w;
+    const int jw = (w >= c0 && w < c0 + nl) ? (int)(w - c0) : -1;
+    // R(t, :) for the local slab: row t is final at step t
     for (int jj = tid; jj < nl; jj += bd) {
       T rv;
       if (jj == jw) rv = T(1);
@@ -149,14 +178,41 @@ __global__ void __launch_bounds__(kThreads) lupp_kernel(const PivParams<T> p) {
       if (p.R) p.R[(int64_t)t * p.ldr + c0 + jj] = rv;
     }
     __syncthreads();
+    if (b == 0 && p.L)
+      for (int r = t + tid; r < s; r += bd) p.L[(int64_t)r * p.ldl + t] = pivcol[r];
     if (jw >= 0 && tid == 0) sel[jw] = 1;
     __syncthreads();
-    const int nr = s - t - 1;
-    for (int64_t e = tid; e < (int64_t)nr * nl; e += bd) {
-      const int r = t + 1 + (int)(e / nl), jj = (int)(e % nl);
+    if (t + 1 == s) break;
+
+    // lookahead: row t+1, then this CTA's candidate for step t+1, then publish + arrive
+    const int r1 = t + 1;
+    for (int jj = tid; jj < nl; jj += bd) {
       if (sel[jj]) continue;
-      T* w = &W[(int64_t)r * nloc + jj];
-      *w = dsub(*w, dmul(pivcol[r], rowt[jj]));
+      T* x = &W[(int64_t)r1 * nloc + jj];
+      *x = dsub(*x, dmul(pivcol[r1], rowt[jj]));
+    }
+    __syncthreads();
+    const KeyIdx<T> c = local_best<T>(W, nloc, r1, nl, c0, sel);
+    int jb = -1;
+    if (c.key >= T(0)) {
+      jb = (int)(c.idx - c0);
+      for (int r = t + 2 + tid; r < s; r += bd) {
+        T* x = &W[(int64_t)r * nloc + jb];
+        *x = dsub(*x, dmul(pivcol[r], rowt[jb]));
+      }
+      __syncthreads();
+      publish<T>(p.gc, r1, c.idx, W[(int64_t)r1 * nloc + jb], c.key, W, nloc, jb, r1, s);
+    } else if (tid == 0) {
+      *reinterpret_cast<long long*>(p.gc.slot(r1, b)) = -1;
+    }
+    comm_arrive(p.gc, r1);
+    // rest of the Schur update (rows t+2..s-1), overlapping the barrier
+    const int nr = s - t - 2;
+    for (int64_t e = tid; e < (int64_t)nr * nl; e += bd) {
+      const int r = t + 2 + (int)(e / nl), jj = (int)(e % nl);
+      if (sel[jj] || jj == jb) continue;     // jb's rows > t+1 were updated before publishing
+      T* x = &W[(int64_t)r * nloc + jj];
+      *x = dsub(*x, dmul(pivcol[r], rowt[jj]));
     }
     __syncthreads();
   }
@@ -205,25 +261,18 @@ __global__ void __launch_bounds__(kThreads) cpqr_kernel(const PivParams<T> p) {
       if (better(k, c0 + jj, key, idx)) { key = k; idx = c0 + jj; }
     }
     const KeyIdx<T> mine = block_argmax<T>(key, idx);
-    char* sl = p.gc.slot(t, b);
     if (mine.key >= T(0)) {
       const int jb = (int)(mine.idx - c0);
-      T* col = reinterpret_cast<T*>(sl + kHeader);
-      for (int r = t + tid; r < l; r += bd) col[r] = W[(int64_t)r * nloc + jb];
-      if (tid == 0) {
-        *reinterpret_cast<long long*>(sl) = mine.idx;
-        *reinterpret_cast<T*>(sl + 8) = nu[jb];
-      }
+      publish<T>(p.gc, t, mine.idx, nu[jb], mine.key, W, nloc, jb, t, l);
     } else if (tid == 0) {
-      *reinterpret_cast<long long*>(sl) = -1;
+      *reinterpret_cast<long long*>(p.gc.slot(t, b)) = -1;
     }
-    comm_publish(p.gc, t);
-    if (!comm_wait_all(p.gc, t, p.dev_status)) return;
+    comm_arrive(p.gc, t);
+    if (!comm_wait(p.gc, t, p.dev_status)) return;
 
-    const KeyIdx<T> win = reduce_candidates<T, false>(p.gc, t);
-    if (win.idx == INT64_MAX) { fail_tail(p, t, SKEL_ERR_INVALID_ARG); return; }
-    const int wb = (int)(win.idx / nloc);
-    const T* wcol = reinterpret_cast<const T*>(p.gc.slot(t, wb) + kHeader);
+    const int64_t w = winner<T>(p.gc, t, false);
+    if (w < 0) { fail_tail(p, t, SKEL_ERR_INVALID_ARG); return; }
+    const T* wcol = reinterpret_cast<const T*>(p.gc.slot(t, (int)(w / nloc)) + kHeader);
     T part = T(0);
     for (int r = t + tid; r < l; r += bd) {
       const T x = __ldcg(wcol + r);
@@ -241,8 +290,8 @@ __global__ void __launch_bounds__(kThreads) cpqr_kernel(const PivParams<T> p) {
     __syncthreads();
     for (int r = t + 1 + tid; r < l; r += bd) v[r] = v[r] / den;
     if (tid == 0) v[t] = T(1);
-    if (b == 0 && tid == 0) p.Js[t] = (int32_t)win.idx;
-    const int jw = (win.idx >= c0 && win.idx < c0 + nl) ? (int)(win.idx - c0) : -1;
+    if (b == 0 && tid == 0) p.Js[t] = (int32_t)w;
+    const int jw = (w >= c0 && w < c0 + nl) ? (int)(w - c0) : -1;
     __syncthreads();
     if (jw >= 0 && tid == 0) {
       sel[jw] = 1;
@@ -261,9 +310,9 @@ __global__ void __launch_bounds__(kThreads) cpqr_kernel(const PivParams<T> p) {
       const T f = tau * d;
       T tail = T(0);
       for (int r = t + lane; r < l; r += 32) {
-        T* w = &W[(int64_t)r * nloc + jj];
-        *w -= f * v[r];
-        if (r > t) tail += (*w) * (*w);
+        T* x = &W[(int64_t)r * nloc + jj];
+        *x -= f * v[r];
+        if (r > t) tail += (*x) * (*x);
       }
       for (int o = 16; o > 0; o >>= 1) tail += __shfl_xor_sync(0xffffffffu, tail, o);
       if (lane == 0) {
@@ -278,7 +327,6 @@ __global__ void __launch_bounds__(kThreads) cpqr_kernel(const PivParams<T> p) {
   }
 }
 
-template <typename T>
 int choose_grid(int64_t n, int min_cols) {
   const int sms = device_sm_count();
   int64_t g = (n + min_cols - 1) / min_cols;
@@ -295,20 +343,21 @@ size_t smem_bytes(int rows, int nloc, int s_or_l, bool slab) {
 }
 
 struct Plan {
-  int G, nloc, in_smem;
+  int G, nloc, in_smem, nsteps;
   size_t smem, slot_bytes, comm_bytes, block_bytes, total;
 };
 
 template <typename T>
-Plan plan_pivot(int64_t n, int rows, int s_or_l_vec, int slot_rows) {
+Plan plan_pivot(int64_t n, int rows, int s_or_l_vec, int slot_rows, int nsteps) {
   Plan pl{};
-  pl.G = choose_grid<T>(n, 32);
+  pl.G = choose_grid(n, 32);
   pl.nloc = (int)((n + pl.G - 1) / pl.G);
+  pl.nsteps = nsteps;
   const size_t with = smem_bytes<T>(rows, pl.nloc, s_or_l_vec, true);
   pl.in_smem = with <= kSmemBudget;
   pl.smem = pl.in_smem ? with : smem_bytes<T>(rows, pl.nloc, s_or_l_vec, false);
   pl.slot_bytes = align_up(kHeader + sizeof(T) * slot_rows, 16);
-  pl.comm_bytes = align_up(sizeof(int32_t) * (2 * pl.G + 1)) + align_up(2 * pl.G * pl.slot_bytes);
+  pl.comm_bytes = comm_header_bytes(nsteps) + align_up(2 * pl.G * pl.slot_bytes);
   pl.block_bytes = pl.in_smem ? 0 : align_up(sizeof(T) * (size_t)pl.G * rows * pl.nloc);
   pl.total = pl.comm_bytes + pl.block_bytes;
   return pl;
@@ -318,17 +367,17 @@ template <typename T>
 skel_status launch_pivot(bool is_lupp, const Plan& pl, PivParams<T>& p, void* ws,
                          cudaStream_t st) {
   char* base = static_cast<char*>(ws);
-  p.gc.tags = reinterpret_cast<int32_t*>(base);
-  p.gc.abort = p.gc.tags + 2 * pl.G;
-  p.gc.payload = base + align_up(sizeof(int32_t) * (2 * pl.G + 1));
+  p.gc.counter = reinterpret_cast<unsigned int*>(base);
+  p.gc.abort = reinterpret_cast<int32_t*>(base + 4);
+  p.gc.keys = reinterpret_cast<unsigned long long*>(base + 256);
+  p.gc.payload = base + comm_header_bytes(pl.nsteps);
   p.gc.slot_bytes = (int64_t)pl.slot_bytes;
   p.gc.G = pl.G;
   p.gc.wait_ns = kDefaultWaitNs;
   p.gblock = pl.in_smem ? nullptr : reinterpret_cast<T*>(base + pl.comm_bytes);
   p.nloc = pl.nloc;
   p.in_smem = pl.in_smem;
-  if (cudaMemsetAsync(base, 0, sizeof(int32_t) * (2 * pl.G + 1), st) != cudaSuccess)
-    return SKEL_ERR_CUDA;
+  if (cudaMemsetAsync(base, 0, comm_header_bytes(pl.nsteps), st) != cudaSuccess) return SKEL_ERR_CUDA;
   const void* fn = is_lupp ? (const void*)lupp_kernel<T> : (const void*)cpqr_kernel<T>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem) != cudaSuccess)
     return SKEL_ERR_CUDA;
@@ -351,7 +400,7 @@ skel_status launch_pivot(bool is_lupp, const Plan& pl, PivParams<T>& p, void* ws
 }  // namespace
 
 size_t lupp_workspace(skel_dtype dt, int64_t n, int32_t s, int* grid_out) {
-  const Plan pl = dt == SKEL_F64 ? plan_pivot<double>(n, s, s, s) : plan_pivot<float>(n, s, s, s);
+  const Plan pl = dt == SKEL_F64 ? plan_pivot<double>(n, s, s, s, s) : plan_pivot<float>(n, s, s, s, s);
   if (grid_out) *grid_out = pl.G;
   return pl.total;
 }
@@ -360,14 +409,14 @@ skel_status run_lupp(skel_dtype dt, const void* X, int64_t n, int64_t ldx, int32
                      void* L, int64_t ldl, void* R, int64_t ldr, void* ws, size_t ws_bytes,
                      int32_t* dev_status, cudaStream_t st) {
   if (dt == SKEL_F64) {
-    const Plan pl = plan_pivot<double>(n, s, s, s);
+    const Plan pl = plan_pivot<double>(n, s, s, s, s);
     if (ws_bytes < pl.total) return SKEL_ERR_WORKSPACE;
     PivParams<double> p{};
     p.X = (const double*)X; p.l = s; p.n = n; p.ldx = ldx; p.s = s; p.Js = Js;
     p.L = (double*)L; p.ldl = ldl; p.R = (double*)R; p.ldr = ldr; p.rows = s; p.dev_status = dev_status;
     return launch_pivot<double>(true, pl, p, ws, st);
   }
-  const Plan pl = plan_pivot<float>(n, s, s, s);
+  const Plan pl = plan_pivot<float>(n, s, s, s, s);
   if (ws_bytes < pl.total) return SKEL_ERR_WORKSPACE;
   PivParams<float> p{};
   p.X = (const float*)X; p.l = s; p.n = n; p.ldx = ldx; p.s = s; p.Js = Js;
@@ -376,8 +425,8 @@ skel_status run_lupp(skel_dtype dt, const void* X, int64_t n, int64_t ldx, int32
 }
 
 size_t cpqr_workspace(skel_dtype dt, int64_t l, int64_t n, int32_t s, int* grid_out) {
-  const Plan pl = dt == SKEL_F64 ? plan_pivot<double>(n, (int)l, (int)l, (int)l)
-                                 : plan_pivot<float>(n, (int)l, (int)l, (int)l);
+  const Plan pl = dt == SKEL_F64 ? plan_pivot<double>(n, (int)l, (int)l, (int)l, s)
+                                 : plan_pivot<float>(n, (int)l, (int)l, (int)l, s);
   if (grid_out) *grid_out = pl.G;
   return pl.total;
 }
@@ -386,14 +435,14 @@ skel_status run_cpqr(skel_dtype dt, const void* X, int64_t l, int64_t n, int64_t
                      int32_t* Js, void* R, int64_t ldr, void* ws, size_t ws_bytes,
                      int32_t* dev_status, cudaStream_t st) {
   if (dt == SKEL_F64) {
-    const Plan pl = plan_pivot<double>(n, (int)l, (int)l, (int)l);
+    const Plan pl = plan_pivot<double>(n, (int)l, (int)l, (int)l, s);
     if (ws_bytes < pl.total) return SKEL_ERR_WORKSPACE;
     PivParams<double> p{};
     p.X = (const double*)X; p.l = l; p.n = n; p.ldx = ldx; p.s = s; p.Js = Js;
     p.R = (double*)R; p.ldr = ldr; p.rows = (int)l; p.dev_status = dev_status;
     return launch_pivot<double>(false, pl, p, ws, st);
   }
-  const Plan pl = plan_pivot<float>(n, (int)l, (int)l, (int)l);
+  const Plan pl = plan_pivot<float>(n, (int)l, (int)l, (int)l, s);
   if (ws_bytes < pl.total) return SKEL_ERR_WORKSPACE;
   PivParams<float> p{};
   p.X = (const float*)X; p.l = l; p.n = n; p.ldx = ldx; p.s = s; p.Js = Js;

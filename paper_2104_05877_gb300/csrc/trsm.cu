@@ -141,13 +141,18 @@ cudaError_t launch_trsm_upper(int32_t s, int64_t N, const double* R, int64_t ldr
 // sqrt(lambda_max(M)) for a symmetric positive definite s x s M (overwritten).  M is
 // normalised by its trace and squared q times (N_i = N_{i-1}^2 / tr(N_{i-1}^2)), so that the
 // power iteration sees the eigenvalue ratio raised to the 2^q-th power.
+size_t power_scratch_bytes(int32_t s) {
+  return align_up(sizeof(double) * (16 + 2 * (size_t)s * s)) + gemm_workspace(s, s, s, true);
+}
+
 cudaError_t launch_power_sqrt_lmax(int32_t s, const double* Min, int64_t ldm, double* out,
                                    double* scratch, cudaStream_t st) {
-  // scratch layout: [logs: 16 doubles][two s x s buffers]
+  // scratch layout: [logs: 16 doubles][two s x s buffers][split-K scratch]
   constexpr int q = 4;
   double* logs = scratch;
   double* bufA = scratch + 16;
   double* bufB = bufA + (int64_t)s * s;
+  void* kws = reinterpret_cast<char*>(scratch) + align_up(sizeof(double) * (16 + 2 * (size_t)s * s));
   cudaError_t e = cudaMemcpy2DAsync(bufA, sizeof(double) * s, Min, sizeof(double) * ldm,
                                     sizeof(double) * s, s, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
@@ -161,6 +166,7 @@ cudaError_t launch_power_sqrt_lmax(int32_t s, const double* Min, int64_t ldm, do
     a.B = View{cur, s, 1}; a.b_dt = SKEL_F64;      // symmetric: B(k, c) = cur(k, c)
     a.out = nxt; a.out_sr = s; a.out_sc = 1; a.out_dt = SKEL_F64;
     a.alpha = 1.0;
+    a.splitk_ws = gemm_workspace(s, s, s, true) ? kws : nullptr;
     e = launch_gemm(a, true, LEFT_LOAD, EPI_STORE, st);
     if (e != cudaSuccess) return e;
     trace_normalize_kernel<<<1, 1024, 0, st>>>(s, nxt, s, logs, i);
