@@ -127,6 +127,30 @@ skel_status skel_pivot_lupp(skel_dtype dtype, const void* X, int64_t l, int64_t 
                             cudaStream_t stream);
 
 /*
+ * skel_pivot_lupp_static -- the same computation and outputs as skel_pivot_lupp, for callers
+ * that cannot allocate device memory.  Some programs must not allocate: a host that hands out
+ * all device memory from its own fixed pool and forbids allocations after start-up, or a loop
+ * with a hard latency budget where cudaMalloc's implicit synchronisation of the whole device
+ * is not acceptable.  Such a caller passes only X and the outputs; this entry point allocates
+ * nothing.  (The paper has no counterpart; this is an interface choice of this library.)
+ *   Scratch: a fixed 8 MiB array in the library's device image, held by every device that
+ *   loads the library until the process exits.  A problem whose scratch need (the workspace
+ *   skel_pivot_lupp would ask for) exceeds 8 MiB returns SKEL_ERR_WORKSPACE with nothing
+ *   launched.
+ *   Set-up: the first call on a device, with that device current, looks up the array's device
+ *   address (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ *   capture.  Later calls do no set-up.
+ *   Sharing: every call on a device uses the same array and each call leaves its contents
+ *   behind; a call clears what must start at zero itself.  Calls that overlap on the GPU
+ *   (different streams, or host threads, without ordering between them) race on the array
+ *   and give wrong results: order them.
+ */
+skel_status skel_pivot_lupp_static(skel_dtype dtype, const void* X, int64_t l, int64_t n,
+                                   int64_t ldx, int32_t s, int32_t* Js, void* L, int64_t ldl,
+                                   void* R, int64_t ldr, int32_t* dev_status,
+                                   cudaStream_t stream);
+
+/*
  * skel_pivot_cpqr -- column pivoted Householder QR on X (Sec. 2.5.1, Eq. (QRCP)), first s
  * steps: j_t = argmax of the remaining column norm over rows t..l-1 (kept by downdating,
  * recomputed when cancellation exceeds sqrt(unit roundoff)), then a Householder reflector
