@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--prec", default="tf32", choices=["tf32", "bf16", "f32"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-GPU comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    ap.add_argument("--only", default=None, choices=["sketch", "lupp", "rows", "id", "cur", "eta"],
+                    help="run only this call (warm-up + steps, no extras): a small command for profilers")
     return ap.parse_args()
 
 
@@ -207,6 +209,31 @@ def run_ours(args, rank, world):
         e, _ = skel.error(A, Js, Rf=Rf, status=st)
         evs[6].record()
         return Js, Is, sq_id, sq_cur, e
+
+    if args.only:
+        X, _ = skel.sketch(A, l, prec=args.prec, seed=seed_G, status=st)
+        Js, _, Rf, _ = skel.pivot_lupp(X, k, status=st)
+        Is, _ = skel.pivot_rows(A, Js, status=st)
+        call = {"sketch": lambda: skel.sketch(A, l, prec=args.prec, seed=seed_G, X=X, status=st),
+                "lupp": lambda: skel.pivot_lupp(X, k, status=st),
+                "rows": lambda: skel.pivot_rows(A, Js, status=st),
+                "id": lambda: skel.column_id(A, Js, status=st),
+                "cur": lambda: skel.cur(A, Js, Is, status=st),
+                "eta": lambda: skel.error(A, Js, Rf=Rf, status=st)}[args.only]
+        for _ in range(args.warmup):
+            call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            call()
+        e1.record()
+        torch.cuda.synchronize()
+        skel.check_status(st, args.only)
+        if rank == 0:
+            print(json.dumps({"only": args.only, "ms": e0.elapsed_time(e1) / args.steps,
+                              "config": workload_config(k, p, args.prec)}), flush=True)
+        return
 
     mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(7)]
     for _ in range(args.warmup):

@@ -175,10 +175,10 @@ skel_status skel_pivot_lupp(skel_dtype dtype, const void* X, int64_t l, int64_t 
   if (!valid_dtype(dtype) || X == nullptr || Js == nullptr) return SKEL_ERR_INVALID_ARG;
   if (s < 1 || s > kMaxS || s > l || s > n || n > 0x7FFFFFFFll) return SKEL_ERR_INVALID_ARG;
   if (ldx < n || (L && ldl < s) || (R && ldr < n)) return SKEL_ERR_INVALID_ARG;
-  const size_t need = lupp_workspace(dtype, n, s, nullptr);
+  const size_t need = lupp_auto_workspace(dtype, n, s);
   skel_status st;
   if (ws_handshake(need, ws, ws_bytes, &st)) return st;
-  return run_lupp(dtype, X, n, ldx, s, Js, L, ldl, R, ldr, ws, *ws_bytes, dev_status, stream);
+  return run_lupp_auto(dtype, X, n, ldx, s, Js, L, ldl, R, ldr, ws, *ws_bytes, dev_status, stream);
 }
 
 skel_status skel_pivot_cpqr(skel_dtype dtype, const void* X, int64_t l, int64_t n, int64_t ldx,
@@ -267,7 +267,7 @@ skel_status skel_pivot_rows(int64_t m, int64_t n, skel_dtype dtype, const void* 
     const bool run = pass == 1;
     Arena ar(run ? ws : nullptr);
     void* C = ar.take(esize(dtype) * (size_t)m * s);
-    const size_t lw = lupp_workspace(dtype, m, s, nullptr);
+    const size_t lw = lupp_auto_workspace(dtype, m, s);
     void* lws = ar.take(lw);
     if (!run) {
       skel_status st;
@@ -276,7 +276,7 @@ skel_status skel_pivot_rows(int64_t m, int64_t n, skel_dtype dtype, const void* 
     }
     SK_CUDA(launch_gather_cols(m, s, dtype, A, lda, Js, C, m, stream));
     // C column-major m x s is C^T row-major s x m: row pivots of C = column pivots of C^T
-    SK_TRY(run_lupp(dtype, C, m, m, s, Is, nullptr, 0, nullptr, 0, lws, lw, dev_status, stream));
+    SK_TRY(run_lupp_auto(dtype, C, m, m, s, Is, nullptr, 0, nullptr, 0, lws, lw, dev_status, stream));
   }
   return SKEL_OK;
 }
@@ -294,7 +294,7 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
     void *C, *Qc, *Rt, *Qr;
     double *Rc, *Rr;
     SK_TRY(skeleton_qr(ar, run, m, dtype, A, lda, s, Js, &C, &Qc, &Rc, dev_status, stream));
-    const size_t lw = rows_given ? 0 : lupp_workspace(dtype, m, s, nullptr);
+    const size_t lw = rows_given ? 0 : lupp_auto_workspace(dtype, m, s);
     void* lws = rows_given ? nullptr : ar.take(lw);
     Rt = ar.take(esize(dtype) * (size_t)n * s);
     Qr = ar.take(esize(dtype) * (size_t)n * s);
@@ -318,7 +318,7 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
     }
     // rows by LUPP on C (Algorithm 2 line 4): C column-major m x s is C^T row-major s x m
     if (!rows_given)
-      SK_TRY(run_lupp(dtype, C, m, m, s, Is, nullptr, 0, nullptr, 0, lws, lw, dev_status, stream));
+      SK_TRY(run_lupp_auto(dtype, C, m, m, s, Is, nullptr, 0, nullptr, 0, lws, lw, dev_status, stream));
     SK_CUDA(launch_gather_rows_t(n, s, dtype, A, lda, Is, Rt, n, stream));
     SK_TRY(run_qr(dtype, Rt, n, n, s, Qr, n, Rr, s, qws, qn, dev_status, stream));
     GemmArgs g{};

@@ -4,6 +4,8 @@
 // Used for: the FP64/FP32 Gaussian sketch X = Gamma A (Algorithm 2 line 2) with Gamma never
 // stored; W = Q_C^T A (Eq. (2.1) via Q_C R_C = C); W Q_R (Remark 3); T T^T for Theorem 1's
 // eta; and the residual norms ||A - C Z||_F, ||A - C U R||_F.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -146,17 +148,18 @@ __global__ void __launch_bounds__(NT) splitk_reduce_kernel(const GemmArgs a, int
   const T* ws = static_cast<const T*>(a.splitk_ws);
   const int64_t total = a.M * a.N;
   double part = 0.0;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    T acc = T(0);
-    for (int z = 0; z < nz; ++z) acc += ws[(int64_t)z * total + e];
-    const T v = (T)a.alpha * acc;
-    const int64_t r = e / a.N, c = e % a.N;
-    const int64_t off = r * a.out_sr + c * a.out_sc;
-    if (a.out_dt == SKEL_F64) static_cast<double*>(a.out)[off] = (double)v;
-    else static_cast<float*>(a.out)[off] = (float)v;
-    if (EPI == EPI_STORE_SQ) part += (double)v * (double)v;
-  }
+  // rows of the output are dealt to CTAs, columns to threads
+  for (int64_t r = blockIdx.x; r < a.M; r += gridDim.x)
+    for (int64_t c = threadIdx.x; c < a.N; c += blockDim.x) {
+      const int64_t e = r * a.N + c;
+      T acc = T(0);
+      for (int z = 0; z < nz; ++z) acc += ws[(int64_t)z * total + e];
+      const T v = (T)a.alpha * acc;
+      const int64_t off = r * a.out_sr + c * a.out_sc;
+      if (a.out_dt == SKEL_F64) static_cast<double*>(a.out)[off] = (double)v;
+      else static_cast<float*>(a.out)[off] = (float)v;
+      if (EPI == EPI_STORE_SQ) part += (double)v * (double)v;
+    }
   if (EPI == EPI_STORE_SQ) {
     const double tot = block_sum<double>(part);
     if (threadIdx.x == 0) a.partials[blockIdx.x] = tot;
@@ -169,7 +172,11 @@ cudaError_t launch_t(const GemmArgs& a0, int nz, cudaStream_t st) {
   const unsigned gx = (unsigned)((a.N + BN - 1) / BN), gy = (unsigned)((a.M + BM - 1) / BM);
   if (nz > 1 && (EPI == EPI_STORE || EPI == EPI_STORE_SQ) && LEFT == LEFT_LOAD) {
     gemm_kernel<T, LEFT, EPI, true><<<dim3(gx, gy, nz), NT, 0, st>>>(a);
-    splitk_reduce_kernel<T, EPI><<<gx * gy, NT, 0, st>>>(a, nz);
+    // STORE_SQ writes one partial per reduce CTA, so it keeps the tile count as its grid
+    const int64_t total = a.M * a.N;
+    const unsigned rg = EPI == EPI_STORE_SQ ? gx * gy
+                        : (unsigned)std::max<int64_t>(gx * gy, std::min<int64_t>((total + NT - 1) / NT, 1024));
+    splitk_reduce_kernel<T, EPI><<<rg, NT, 0, st>>>(a, nz);
     note_launches(2);
   } else {
     a.kchunk = a.K;

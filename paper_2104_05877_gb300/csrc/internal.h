@@ -85,6 +85,12 @@ size_t lupp_workspace(skel_dtype dt, int64_t n, int32_t s, int* grid_out);
 skel_status run_lupp(skel_dtype dt, const void* X, int64_t n, int64_t ldx, int32_t s, int32_t* Js,
                      void* L, int64_t ldl, void* R, int64_t ldr, void* ws, size_t ws_bytes,
                      int32_t* dev_status, cudaStream_t st);
+// LUPP through the panel-blocked cluster kernels when a panel fits one cluster's shared
+// memory (lupp_panel.cu), else through the grid-barrier kernel above.
+size_t lupp_auto_workspace(skel_dtype dt, int64_t n, int32_t s);
+skel_status run_lupp_auto(skel_dtype dt, const void* X, int64_t n, int64_t ldx, int32_t s,
+                          int32_t* Js, void* L, int64_t ldl, void* R, int64_t ldr, void* ws,
+                          size_t ws_bytes, int32_t* dev_status, cudaStream_t st);
 size_t cpqr_workspace(skel_dtype dt, int64_t l, int64_t n, int32_t s, int* grid_out);
 skel_status run_cpqr(skel_dtype dt, const void* X, int64_t l, int64_t n, int64_t ldx, int32_t s,
                      int32_t* Js, void* R, int64_t ldr, void* ws, size_t ws_bytes,

@@ -135,13 +135,12 @@ __global__ void __launch_bounds__(kThreads) lupp_kernel(const PivParams<T> p) {
   unsigned char* sel = carve(cur, nloc);
   T* W = p.in_smem ? (T*)carve(cur, sizeof(T) * (size_t)s * nloc) : p.gblock + (int64_t)b * s * nloc;
 
-  for (int64_t e = tid; e < (int64_t)s * nl; e += bd) {
-    const int r = (int)(e / nl), jj = (int)(e % nl);
-    W[(int64_t)r * nloc + jj] = p.X[(int64_t)r * p.ldx + c0 + jj];
-  }
+  for (int r = 0; r < s; ++r)
+    for (int jj = tid; jj < nl; jj += bd) W[(int64_t)r * nloc + jj] = p.X[(int64_t)r * p.ldx + c0 + jj];
   for (int jj = tid; jj < nloc; jj += bd) sel[jj] = 0;
   if (b == 0 && p.L)
-    for (int64_t e = tid; e < (int64_t)s * s; e += bd) p.L[(e / s) * p.ldl + (e % s)] = T(0);
+    for (int r = 0; r < s; ++r)
+      for (int c = tid; c < s; c += bd) p.L[(int64_t)r * p.ldl + c] = T(0);
   __syncthreads();
 
   // step 0 candidate
@@ -207,12 +206,13 @@ __global__ void __launch_bounds__(kThreads) lupp_kernel(const PivParams<T> p) {
     }
     comm_arrive(p.gc, r1);
     // rest of the Schur update (rows t+2..s-1), overlapping the barrier
-    const int nr = s - t - 2;
-    for (int64_t e = tid; e < (int64_t)nr * nl; e += bd) {
-      const int r = t + 2 + (int)(e / nl), jj = (int)(e % nl);
+    for (int jj = tid; jj < nl; jj += bd) {
       if (sel[jj] || jj == jb) continue;     // jb's rows > t+1 were updated before publishing
-      T* x = &W[(int64_t)r * nloc + jj];
-      *x = dsub(*x, dmul(pivcol[r], rowt[jj]));
+      const T rv = rowt[jj];
+      for (int r = t + 2; r < s; ++r) {
+        T* x = &W[(int64_t)r * nloc + jj];
+        *x = dsub(*x, dmul(pivcol[r], rv));
+      }
     }
     __syncthreads();
   }
@@ -238,10 +238,8 @@ __global__ void __launch_bounds__(kThreads) cpqr_kernel(const PivParams<T> p) {
   // downdating guard: recompute a norm when it fell below sqrt(u) of its last exact value
   const T guard = sizeof(T) == 8 ? T(1.4901161193847656e-08) : T(2.44140625e-04);
 
-  for (int64_t e = tid; e < (int64_t)l * nl; e += bd) {
-    const int r = (int)(e / nl), jj = (int)(e % nl);
-    W[(int64_t)r * nloc + jj] = p.X[(int64_t)r * p.ldx + c0 + jj];
-  }
+  for (int r = 0; r < l; ++r)
+    for (int jj = tid; jj < nl; jj += bd) W[(int64_t)r * nloc + jj] = p.X[(int64_t)r * p.ldx + c0 + jj];
   for (int jj = tid; jj < nloc; jj += bd) sel[jj] = 0;
   __syncthreads();
   for (int jj = warp; jj < nl; jj += nwarps) {

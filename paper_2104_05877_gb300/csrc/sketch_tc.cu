@@ -33,14 +33,14 @@ namespace {
 constexpr int TC_M = 128;
 constexpr int TC_BK = 32;             // FP32 elements per 128-byte swizzle row
 constexpr int TC_N = 512;             // columns of A per CTA (TMEM columns)
-constexpr int TC_STAGES = 2;
+constexpr int TC_ASTAGES = 3;          // TMA stages of A (latency hiding)
+constexpr int TC_GSTAGES = 2;          // generated Gamma stages
 constexpr int TC_THREADS = 384;
 constexpr int TC_GEN_WARP0 = 4;
 constexpr int TC_GEN_WARPS = 8;
 constexpr uint32_t G_BYTES = TC_M * 128;        // 16 KB per stage
 constexpr uint32_t A_BYTES = TC_N * 128;        // 64 KB per stage
-constexpr uint32_t STAGE_BYTES = G_BYTES + A_BYTES;
-constexpr size_t TC_SMEM = 1024 + TC_STAGES * STAGE_BYTES + 256;
+constexpr size_t TC_SMEM = 1024 + TC_GSTAGES * G_BYTES + TC_ASTAGES * A_BYTES + 256;
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -142,11 +142,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 sketch_tc_tf32_kernel(const __grid_constant__ CUtensorMap tmapA, const TcParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* gbuf = smem;                                  // [S][G_BYTES]
-  unsigned char* abuf = smem + TC_STAGES * G_BYTES;            // [S][A_BYTES]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * STAGE_BYTES);
-  // bars: full_a[S], full_g[S], empty[S], done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * TC_STAGES + 1);
+  unsigned char* gbuf = smem;                                  // [GS][G_BYTES]
+  unsigned char* abuf = smem + TC_GSTAGES * G_BYTES;           // [AS][A_BYTES]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(abuf + TC_ASTAGES * A_BYTES);
+  // bars: full_a[AS], empty_a[AS], full_g[GS], empty_g[GS], done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_ASTAGES + 2 * TC_GSTAGES + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -157,15 +157,19 @@ sketch_tc_tf32_kernel(const __grid_constant__ CUtensorMap tmapA, const TcParams 
   const int nk = (int)((ke - kb + TC_BK - 1) / TC_BK);
 
   auto full_a = [&](int s) { return smem_u32(&bars[s]); };
-  auto full_g = [&](int s) { return smem_u32(&bars[TC_STAGES + s]); };
-  auto empty = [&](int s) { return smem_u32(&bars[2 * TC_STAGES + s]); };
-  const uint32_t done = smem_u32(&bars[3 * TC_STAGES]);
+  auto empty_a = [&](int s) { return smem_u32(&bars[TC_ASTAGES + s]); };
+  auto full_g = [&](int s) { return smem_u32(&bars[2 * TC_ASTAGES + s]); };
+  auto empty_g = [&](int s) { return smem_u32(&bars[2 * TC_ASTAGES + TC_GSTAGES + s]); };
+  const uint32_t done = smem_u32(&bars[2 * TC_ASTAGES + 2 * TC_GSTAGES]);
 
   if (tid == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < TC_ASTAGES; ++s) {
       mbar_init(full_a(s), 1);
+      mbar_init(empty_a(s), 1);
+    }
+    for (int s = 0; s < TC_GSTAGES; ++s) {
       mbar_init(full_g(s), TC_GEN_WARPS);
-      mbar_init(empty(s), 1);
+      mbar_init(empty_g(s), 1);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -190,10 +194,10 @@ sketch_tc_tf32_kernel(const __grid_constant__ CUtensorMap tmapA, const TcParams 
     int issued = 0;
     if (lane == 0) {
       for (int it = 0; it < nk; ++it) {
-        const int s = it % TC_STAGES;
-        const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+        const int s = it % TC_ASTAGES;
+        const uint32_t ph = (uint32_t)(it / TC_ASTAGES) & 1u;
         if (*(volatile int*)abort_flag) break;
-        if (it >= TC_STAGES && !mbar_wait(empty(s), ph ^ 1u, TC_WAIT_NS)) { fail(); break; }
+        if (it >= TC_ASTAGES && !mbar_wait(empty_a(s), ph ^ 1u, TC_WAIT_NS)) { fail(); break; }
         mbar_expect_tx(full_a(s), A_BYTES);
         const int x = (int)(kb + (int64_t)it * TC_BK);
         const uint32_t dst = smem_u32(abuf + s * A_BYTES);
@@ -202,9 +206,9 @@ sketch_tc_tf32_kernel(const __grid_constant__ CUtensorMap tmapA, const TcParams 
         ++issued;
       }
       // drain: every issued load must have landed before the CTA may exit
-      for (int it = std::max(0, issued - TC_STAGES); it < issued; ++it) {
-        const int s = it % TC_STAGES;
-        if (!mbar_wait(full_a(s), (uint32_t)(it / TC_STAGES) & 1u, TC_WAIT_NS)) fail();
+      for (int it = std::max(0, issued - TC_ASTAGES); it < issued; ++it) {
+        const int s = it % TC_ASTAGES;
+        if (!mbar_wait(full_a(s), (uint32_t)(it / TC_ASTAGES) & 1u, TC_WAIT_NS)) fail();
       }
     }
   } else if (warp == 1) {
@@ -212,13 +216,13 @@ sketch_tc_tf32_kernel(const __grid_constant__ CUtensorMap tmapA, const TcParams 
     if (lane == 0) {
       const uint32_t idesc = idesc_tf32(TC_M, TC_N / 2);
       for (int it = 0; it < nk; ++it) {
-        const int s = it % TC_STAGES;
-        const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+        const int sa = it % TC_ASTAGES, sg = it % TC_GSTAGES;
+        const uint32_t pa = (uint32_t)(it / TC_ASTAGES) & 1u, pg = (uint32_t)(it / TC_GSTAGES) & 1u;
         if (*(volatile int*)abort_flag) break;
-        if (!mbar_wait(full_a(s), ph, TC_WAIT_NS) || !mbar_wait(full_g(s), ph, TC_WAIT_NS)) { fail(); break; }
+        if (!mbar_wait(full_a(sa), pa, TC_WAIT_NS) || !mbar_wait(full_g(sg), pg, TC_WAIT_NS)) { fail(); break; }
         tc_fence_after();
-        const uint32_t ga = smem_u32(gbuf + s * G_BYTES);
-        const uint32_t aa = smem_u32(abuf + s * A_BYTES);
+        const uint32_t ga = smem_u32(gbuf + sg * G_BYTES);
+        const uint32_t aa = smem_u32(abuf + sa * A_BYTES);
 #pragma unroll
         for (int kk = 0; kk < TC_BK / 8; ++kk) {
           const uint64_t adesc = sw128_desc(ga + kk * 32);
@@ -226,7 +230,8 @@ sketch_tc_tf32_kernel(const __grid_constant__ CUtensorMap tmapA, const TcParams 
           mma_tf32(tmem, adesc, sw128_desc(aa + kk * 32), idesc, acc);
           mma_tf32(tmem + TC_N / 2, adesc, sw128_desc(aa + A_BYTES / 2 + kk * 32), idesc, acc);
         }
-        mma_commit(empty(s));
+        mma_commit(empty_a(sa));
+        mma_commit(empty_g(sg));
       }
       mma_commit(done);
     }
@@ -234,10 +239,10 @@ sketch_tc_tf32_kernel(const __grid_constant__ CUtensorMap tmapA, const TcParams 
     // ---------------- Gamma generators ----------------
     const int gt = tid - TC_GEN_WARP0 * 32;            // 0..255
     for (int it = 0; it < nk; ++it) {
-      const int s = it % TC_STAGES;
-      const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+      const int s = it % TC_GSTAGES;
+      const uint32_t ph = (uint32_t)(it / TC_GSTAGES) & 1u;
       if (*(volatile int*)abort_flag) break;
-      if (it >= TC_STAGES && !mbar_wait(empty(s), ph ^ 1u, TC_WAIT_NS)) { fail(); break; }
+      if (it >= TC_GSTAGES && !mbar_wait(empty_g(s), ph ^ 1u, TC_WAIT_NS)) { fail(); break; }
       unsigned char* g = gbuf + s * G_BYTES;
       const int64_t kt = kb + (int64_t)it * TC_BK;
 #pragma unroll
@@ -311,16 +316,16 @@ sketch_tc_tf32_kernel(const __grid_constant__ CUtensorMap tmapA, const TcParams 
 // X = scale * sum_p part[p]; flags non-finite results.
 __global__ void tc_reduce_kernel(const float* part, int P, int64_t pstride, int l, int64_t n,
                                  float* X, int64_t ldx, float scale, int32_t* dev_status) {
-  const int64_t total = (int64_t)l * n;
   bool bad = false;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    float acc = 0.f;
-    for (int q = 0; q < P; ++q) acc += part[q * pstride + e];
-    const float v = acc * scale;
-    bad |= !isfinite(v);
-    X[(e / n) * ldx + e % n] = v;
-  }
+  for (int r = blockIdx.y; r < l; r += gridDim.y)
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t e = (int64_t)r * n + c;
+      float acc = 0.f;
+      for (int q = 0; q < P; ++q) acc += part[q * pstride + e];
+      const float v = acc * scale;
+      bad |= !isfinite(v);
+      X[(int64_t)r * ldx + c] = v;
+    }
   if (bad) record_error(dev_status, SKEL_ERR_NONFINITE, -1);
 }
 
@@ -404,8 +409,7 @@ cudaError_t launch_sketch_tc(int64_t m, int64_t n, const float* A, int64_t lda, 
   note_launches(1);
   e = cudaGetLastError();
   if (e != cudaSuccess || p.direct) return e;
-  const int64_t total = (int64_t)l * n;
-  tc_reduce_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 4 * 1024), 256, 0, st>>>(
+  tc_reduce_kernel<<<dim3((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)std::min(l, 128)), 256, 0, st>>>(
       static_cast<const float*>(ws), pl.P, p.part_stride, l, n, X, ldx, p.scale, dev_status);
   note_launches(1);
   return cudaGetLastError();

@@ -16,43 +16,39 @@ __global__ void __launch_bounds__(256) trsm_upper_kernel(int s, int64_t N, int n
                                                          int64_t ldr, int unit, const TB* B,
                                                          int64_t ldb, double* Y, int64_t ldy) {
   extern __shared__ double Ys[];     // [s][nb]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int tid = threadIdx.x, bd = blockDim.x;
   const int64_t c0 = (int64_t)blockIdx.x * nb;
   const int nc = (int)std::min<int64_t>(nb, N - c0);
-  for (int64_t e = tid; e < (int64_t)s * nb; e += blockDim.x) {
+  for (int64_t e = tid; e < (int64_t)s * nb; e += bd) {
     const int r = (int)(e / nb), cc = (int)(e % nb);
     Ys[e] = cc < nc ? (double)B[(int64_t)r * ldb + c0 + cc] : 0.0;
   }
   __syncthreads();
   for (int hi = s; hi > 0; hi -= RB) {
     const int lo = std::max(0, hi - RB);
-    // off-diagonal update from the solved rows q >= hi: one warp per row, lanes over columns
+    // off-diagonal update from the solved rows q >= hi: one thread per (row, column) pair
     if (hi < s) {
-      for (int r = lo + warp; r < hi; r += nwarps) {
+      for (int e = tid; e < (hi - lo) * nb; e += bd) {
+        const int r = lo + e / nb, cc = e % nb;
         const double* Rr = R + (int64_t)r * ldr;
-        for (int cc = lane; cc < nb; cc += 32) {
-          double acc = 0.0;
-          for (int q = hi; q < s; ++q) acc = fma(__ldg(Rr + q), Ys[q * nb + cc], acc);
-          Ys[r * nb + cc] -= acc;
-        }
+        double acc = 0.0;
+        for (int q = hi; q < s; ++q) acc = fma(__ldg(Rr + q), Ys[q * nb + cc], acc);
+        Ys[r * nb + cc] -= acc;
       }
       __syncthreads();
     }
-    // diagonal block, sequential rows, lanes over columns (warp 0)
-    if (warp == 0) {
-      for (int r = hi - 1; r >= lo; --r) {
-        const double* Rr = R + (int64_t)r * ldr;
-        for (int cc = lane; cc < nb; cc += 32) {
-          double acc = Ys[r * nb + cc];
-          for (int q = r + 1; q < hi; ++q) acc -= __ldg(Rr + q) * Ys[q * nb + cc];
-          Ys[r * nb + cc] = unit ? acc : acc / __ldg(Rr + r);
-        }
-        __syncwarp();
+    // diagonal block: rows hi-1 .. lo in order, threads over columns
+    for (int r = hi - 1; r >= lo; --r) {
+      const double* Rr = R + (int64_t)r * ldr;
+      for (int cc = tid; cc < nb; cc += bd) {
+        double acc = Ys[r * nb + cc];
+        for (int q = r + 1; q < hi; ++q) acc -= __ldg(Rr + q) * Ys[q * nb + cc];
+        Ys[r * nb + cc] = unit ? acc : acc / __ldg(Rr + r);
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
-  for (int64_t e = tid; e < (int64_t)s * nb; e += blockDim.x) {
+  for (int64_t e = tid; e < (int64_t)s * nb; e += bd) {
     const int r = (int)(e / nb), cc = (int)(e % nb);
     if (cc < nc) Y[(int64_t)r * ldy + c0 + cc] = Ys[e];
   }
@@ -120,7 +116,7 @@ cudaError_t launch_trsm_upper(int32_t s, int64_t N, const double* R, int64_t ldr
   if (N <= 0 || s <= 0) return cudaSuccess;
   const int sms = device_sm_count();
   int nb = 32;
-  while (nb > 4 && (N + nb - 1) / nb < 2 * sms) nb >>= 1;
+  while (nb > 2 && (N + nb - 1) / nb < 2 * sms) nb >>= 1;
   while ((size_t)s * nb * sizeof(double) > 160 * 1024 && nb > 1) nb >>= 1;
   const size_t smem = (size_t)s * nb * sizeof(double);
   const unsigned grid = (unsigned)((N + nb - 1) / nb);

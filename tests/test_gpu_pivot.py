@@ -149,3 +149,16 @@ def test_grid_wait_times_out(skel, dev):
     X = torch.randn(4, 40, dtype=torch.float64, device=dev)
     Js, _, _, st2 = skel.pivot_lupp(X, 4)
     skel.check_status(st2)
+
+
+def test_lupp_very_wide_uses_grid_kernel(skel, dev):
+    """400000 columns: a panel of even 8 rows does not fit one cluster's shared memory, so
+    the grid-barrier kernel runs, with its column slab in the global workspace (FP64);
+    factors stay bit-identical to the oracle."""
+    l, n, s = 64, 400_000, 48
+    X = np.random.default_rng(11).standard_normal((l, n))
+    Js, _, Rf, st = skel.pivot_lupp(torch.from_numpy(X).to(dev), s)
+    skel.check_status(st)
+    ref = pivoting.lupp_columns(X, s)
+    assert np.array_equal(Js.cpu().numpy(), ref["Js"])
+    assert np.array_equal(Rf.cpu().numpy(), ref["R"])
