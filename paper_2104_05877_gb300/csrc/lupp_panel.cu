@@ -46,120 +46,263 @@ struct PanelParams {
   T* M;                // (s - t0 - b) x b multipliers of the trailing rows (row-major)
 };
 
-// One published candidate: magnitude key, global column index, and the candidate's column
-// rows 0..b-1 (only rows q.. are meaningful at step q).
+// Per-step exchange.  Every CTA sends every CTA of the cluster (itself included) its step-q
+// candidate: a header {key, column index} and the candidate's column rows 4*floor(q/4) .. b-1
+// in 16-byte groups.  The stores are st.async into the receiver's inbox buffer q % 3, each
+// completing its byte count on the receiver's mbarrier of that buffer, so a sender never waits
+// for its stores and a receiver waits only for its own barrier phase.  A sender without
+// candidates still sends the full byte count (key -1, index INT_MAX).
 constexpr int kMaxPanel = 64;
+constexpr int kInbox = 3;
 template <typename T>
-struct Cand {
-  T key;
-  long long idx;
+struct __align__(16) CandCol {
   T col[kMaxPanel];
+};
+template <typename T>
+struct __align__(16) CandHdr {
+  T key;
+  int idx;
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kPanelThreads) lupp_panel_kernel(const PanelParams<T> p) {
+__host__ __device__ constexpr uint32_t hdr_bytes() { return sizeof(T) + 4; }
+// bytes one sender delivers to one receiver for step q of a b-row panel
+template <typename T>
+__host__ __device__ constexpr uint32_t push_bytes(int q, int b) {
+  return hdr_bytes<T>() + (uint32_t)((b + 3) / 4 - q / 4) * 4u * (uint32_t)sizeof(T);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+  return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ uint32_t map_cluster_u32(uint32_t local, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_async_b32(uint32_t addr, uint32_t v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
+               :: "r"(addr), "r"(v), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void st_async_b64(uint32_t addr, uint64_t v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];"
+               :: "r"(addr), "l"(v), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void st_async_v4_b32(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                                uint32_t d, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
+               :: "r"(addr), "r"(a), "r"(b), "r"(c), "r"(d), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void st_async_v2_b64(uint32_t addr, uint64_t a, uint64_t b, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b64 [%0], {%1, %2}, [%3];"
+               :: "r"(addr), "l"(a), "l"(b), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+               " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+// Bounded wait for a barrier phase: false after ~wait_ns without completion.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t wait_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    for (int k = 0; k < 64; ++k)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > wait_ns) return false;
+  }
+}
+
+// Pivot order: larger magnitude key, ties to the lower column index.
+template <typename T>
+__device__ __forceinline__ bool cand_better(T ka, int ia, T kb, int ib) {
+  return ka > kb || (ka == kb && ia < ib);
+}
+
+template <typename T>
+__device__ __forceinline__ void warp_argmax(T& k, int& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T k2 = __shfl_xor_sync(0xffffffffu, k, o);
+    const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+    if (cand_better(k2, i2, k, i)) { k = k2; i = i2; }
+  }
+}
+
+template <typename T> __device__ __forceinline__ uint32_t bits32(T v) { return __float_as_uint((float)v); }
+template <typename T> __device__ __forceinline__ uint64_t bits64(T v) { return (uint64_t)__double_as_longlong((double)v); }
+
+// Warp 0 sends this CTA's candidate (key k, index i, local column jb) for step qn to every
+// CTA of the cluster.  With lprev (qn > 0) rows qn+1.. of column jb still lack step qn-1's
+// update (multipliers lprev, R(qn-1, jb) in row qn-1 of P): it is applied here and written
+// back to P, so the owner thread skips that column in its own update.  Lane l covers rows
+// 4(l%16) .. 4(l%16)+3 for the receivers of parity l/16.
+template <typename T>
+__device__ __forceinline__ void push_candidate(uint32_t col_base, uint32_t hdr_base, uint32_t bar_local,
+                                               int crank, int CL, T* P, int ncl, int b, int qn, T k,
+                                               int i, int jb, const T* lprev) {
+  const int lane = threadIdx.x & 31;
+  const bool have = i != INT_MAX;
+  const int g = lane & 15;
+  const int f0 = 4 * g;
+  const bool active = f0 < b && f0 + 3 >= qn;      // groups floor(qn/4) .. ceil(b/4)-1
+  T v[4] = {T(0), T(0), T(0), T(0)};
+  if (have && active) {
+    const T rq = lprev ? P[(int64_t)(qn - 1) * ncl + jb] : T(0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int f = f0 + u;
+      if (f < b) {
+        v[u] = P[(int64_t)f * ncl + jb];           // rows < qn: R(f, jb), final
+        if (lprev && f > qn) v[u] = dsub(v[u], dmul(lprev[f], rq));
+      }
+    }
+  }
+  __syncwarp();                          // every lane has read column jb before it is rewritten
+  if (have && active && lprev && lane < 16)
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (f0 + u < b && f0 + u > qn) P[(int64_t)(f0 + u) * ncl + jb] = v[u];
+  const uint32_t col_off = (uint32_t)(crank * sizeof(CandCol<T>) + f0 * sizeof(T));
+  if (active)
+    for (int d = lane >> 4; d < CL; d += 2) {
+      const uint32_t dst = map_cluster_u32(col_base + col_off, d);
+      const uint32_t bar = map_cluster_u32(bar_local, d);
+      if constexpr (sizeof(T) == 4) {
+        st_async_v4_b32(dst, bits32(v[0]), bits32(v[1]), bits32(v[2]), bits32(v[3]), bar);
+      } else {
+        st_async_v2_b64(dst, bits64(v[0]), bits64(v[1]), bar);
+        st_async_v2_b64(dst + 16, bits64(v[2]), bits64(v[3]), bar);
+      }
+    }
+  if (lane < CL) {
+    const uint32_t dst = map_cluster_u32(hdr_base + (uint32_t)(crank * sizeof(CandHdr<T>)), lane);
+    const uint32_t bar = map_cluster_u32(bar_local, lane);
+    if constexpr (sizeof(T) == 4) st_async_b32(dst, bits32(k), bar);
+    else st_async_b64(dst, bits64(k), bar);
+    st_async_b32(dst + sizeof(T), (uint32_t)i, bar);
+  }
+}
+
+// Step q of the panel (one-step lookahead; one CTA barrier, no cluster barrier):
+//   wait    the mbarrier phase of inbox q % 3: every CTA's step-q candidate has landed
+//   select  every warp reduces the CL headers (same result everywhere); the winner's column
+//           holds the multipliers of step q
+//   row q   R(t, :) = P(q, :) / pivot over row q of P, the update of row q+1, and this
+//           thread's step-(q+1) candidates over row q+1, in one pass over its columns
+//   push    CTA argmax (one __syncthreads); warp 0 sends the winner with its column
+//   rest    the update of rows q+2.. (skipping the sent column) overlaps the exchange
+// Inbox q % 3 is rewritten for step q+3 only after its sender has received step q+2 from
+// this CTA, which this CTA sends after every warp is done with step q's multipliers.  The
+// byte count of step q+3 is armed right after step q's phase completes.
+template <typename T>
+__global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const PanelParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
   const int CL = (int)cluster.num_blocks();
-  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31;
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
   const int b = p.b, ncl = p.ncl;
-  const int64_t c0 = (int64_t)crank * ncl;
+  const int c0 = crank * ncl;
   const int nl = (int)(p.n - c0 < 0 ? 0 : (p.n - c0 < ncl ? p.n - c0 : ncl));
 
-  // inbox[parity][sender]: every CTA pushes its candidate into every peer's inbox before the
-  // cluster barrier, so after the barrier all reads are local.  A slot is rewritten two
-  // steps later, after every reader has passed the intervening barrier.
-  __shared__ Cand<T> inbox[2][16];
-  __shared__ long long s_w;
-  __shared__ int s_owner;
+  __shared__ CandCol<T> icol[kInbox][16];    // icol[step % 3][sender]
+  __shared__ CandHdr<T> ihdr[kInbox][16];
+  __shared__ __align__(8) uint64_t ibar[kInbox];
   __shared__ T wkey[2][32];
-  __shared__ int64_t widx[2][32];
+  __shared__ int widx[2][32];
   __shared__ int s_J[kMaxPanel];           // pivots of this panel, written out at the end
   __shared__ T s_L[kMaxPanel][kMaxPanel];  // L(t0+r, t0+q) = pivot column q, row r >= q
-  T* P = reinterpret_cast<T*>(smem);                       // [b][ncl]
-  T* rowq = P + ((size_t)b * ncl > (size_t)b * b + b ? (size_t)b * ncl : (size_t)b * b + b);   // [ncl]
-  T* pivc = rowq + ncl;                                    // [b]
-  unsigned char* sl = reinterpret_cast<unsigned char*>(pivc + b);   // [ncl]
+  __shared__ int s_timeout;
+  T* P = reinterpret_cast<T*>(smem);                        // [b][ncl]
+  T* RJ = P + (size_t)b * ncl;                              // [b][b]: R(t0+qq, j_q)
+  unsigned char* sl = reinterpret_cast<unsigned char*>(RJ + (size_t)b * b);   // [ncl]
 
   if (*(volatile int32_t*)p.fail) return;   // an earlier panel stopped (uniform over the cluster)
-  for (int q = 0; q < b; ++q)
-    for (int jj = tid; jj < nl; jj += bd) P[(int64_t)q * ncl + jj] = p.Xg[(int64_t)(p.t0 + q) * p.n + c0 + jj];
+  if (tid == 0) {
+    for (int k = 0; k < kInbox; ++k) mbar_init(smem_u32(&ibar[k]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_timeout = 0;
+  }
+  for (int q0 = 0; q0 < b; q0 += 8)         // eight independent loads in flight per thread
+    for (int jj = tid; jj < nl; jj += bd) {
+      T v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (q0 + u < b) v[u] = p.Xg[(int64_t)(p.t0 + q0 + u) * p.n + c0 + jj];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (q0 + u < b) P[(int64_t)(q0 + u) * ncl + jj] = v[u];
+    }
   for (int jj = tid; jj < nl; jj += bd) sl[jj] = p.sel[c0 + jj];
-  cluster.sync();     // every peer has started before anyone writes into its shared memory
+  const uint32_t col0 = smem_u32(&icol[0][0]), hdr0 = smem_u32(&ihdr[0][0]), bar0 = smem_u32(&ibar[0]);
+  auto col_base = [&](int k) { return col0 + (uint32_t)(k * sizeof(icol[0])); };
+  auto hdr_base = [&](int k) { return hdr0 + (uint32_t)(k * sizeof(ihdr[0])); };
+  auto bar_base = [&](int k) { return bar0 + (uint32_t)(k * sizeof(uint64_t)); };
+  __syncthreads();
+
+  // CTA argmax of the per-thread candidates (key, idx) for step qn: one __syncthreads, after
+  // which every warp holds the result.
+  auto cta_argmax = [&](int qn, T& key, int& idx) {
+    warp_argmax(key, idx);
+    if (lane == 0) { wkey[qn & 1][warp] = key; widx[qn & 1][warp] = idx; }
+    __syncthreads();
+    key = lane < nw ? wkey[qn & 1][lane] : T(-1);
+    idx = lane < nw ? widx[qn & 1][lane] : INT_MAX;
+    warp_argmax(key, idx);
+  };
+
+  {
+    T key = T(-1);
+    int idx = INT_MAX;
+    for (int jj = tid; jj < nl; jj += bd) {
+      if (sl[jj]) continue;
+      const T k = pivot_key(P[jj]);
+      if (cand_better(k, c0 + jj, key, idx)) { key = k; idx = c0 + jj; }
+    }
+    cta_argmax(0, key, idx);
+    if (tid == 0)
+      for (int k = 0; k < kInbox && k < b; ++k) mbar_expect_tx(bar_base(k), (uint32_t)CL * push_bytes<T>(k, b));
+    cluster.sync();     // barriers initialised and armed everywhere before the first send
+    if (warp == 0)
+      push_candidate<T>(col_base(0), hdr_base(0), bar_base(0), crank, CL, P, ncl, b, 0, key, idx, idx - c0, nullptr);
+  }
 
   bool stopped = false;
   int done = 0;                       // completed steps of this panel
   for (int q = 0; q < b; ++q) {
     const int t = p.t0 + q;
-    const int par = q & 1;
-    // local candidate
-    T key = T(-1);
-    int64_t idx = INT64_MAX;
-    for (int jj = tid; jj < nl; jj += bd) {
-      if (sl[jj]) continue;
-      const T k = pivot_key(P[(int64_t)q * ncl + jj]);
-      if (better(k, c0 + jj, key, idx)) { key = k; idx = c0 + jj; }
-    }
-    // CTA argmax with one barrier: warp winners go to wbest[par], then every warp reduces them
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const T k2 = __shfl_xor_sync(0xffffffffu, key, o);
-      const int64_t i2 = __shfl_xor_sync(0xffffffffu, idx, o);
-      if (better(k2, i2, key, idx)) { key = k2; idx = i2; }
-    }
-    if (lane == 0) { wkey[par][tid >> 5] = key; widx[par][tid >> 5] = idx; }
+    const int buf = q % kInbox;
+    if (!mbar_wait(bar_base(buf), (uint32_t)((q / kInbox) & 1), 2000000000ull))
+      if (atomicExch(&s_timeout, 1) == 0) {
+        record_error(p.dev_status, SKEL_ERR_TIMEOUT, t);
+        atomicExch(p.fail, 1);            // later panels and trailing updates skip their work
+      }
     __syncthreads();
-    KeyIdx<T> mine;
+    if (s_timeout) {                       // uniform in the CTA; the peers time out in turn
+      stopped = true;
+      break;
+    }
+    if (tid == 0 && q + kInbox < b) mbar_expect_tx(bar_base(buf), (uint32_t)CL * push_bytes<T>(q + kInbox, b));
+    int w;
     {
-      const int nw = bd >> 5;
-      T k = lane < nw ? wkey[par][lane] : T(-1);
-      int64_t i = lane < nw ? widx[par][lane] : INT64_MAX;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const T k2 = __shfl_xor_sync(0xffffffffu, k, o);
-        const int64_t i2 = __shfl_xor_sync(0xffffffffu, i, o);
-        if (better(k2, i2, k, i)) { k = k2; i = i2; }
-      }
-      mine.key = k;
-      mine.idx = i;
+      T k = lane < CL ? ihdr[buf][lane].key : T(-1);
+      int i = lane < CL ? ihdr[buf][lane].idx : INT_MAX;
+      warp_argmax(k, i);
+      w = i;
     }
-    const bool have = mine.idx != INT64_MAX;
-    const int jb = have ? (int)(mine.idx - c0) : 0;
-    // push: thread tid serves peer (tid % CL), column rows f = q + tid / CL, step bd / CL
-    {
-      const int dest = tid % CL;
-      Cand<T>* slot = &cluster.map_shared_rank(&inbox[0][0], dest)[par * 16 + crank];
-      if (tid < CL) {
-        slot->key = have ? mine.key : T(-1);
-        slot->idx = have ? (long long)mine.idx : (long long)INT64_MAX;
-      }
-      if (have)
-        for (int f = q + tid / CL; f < b; f += bd / CL) slot->col[f] = P[(int64_t)f * ncl + jb];
-    }
-    cluster.sync();
-    if (tid < 32) {
-      T k = T(-1);
-      int64_t i = INT64_MAX;
-      int who = lane;
-      if (lane < CL) { k = inbox[par][lane].key; i = inbox[par][lane].idx; }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const T k2 = __shfl_xor_sync(0xffffffffu, k, o);
-        const int64_t i2 = __shfl_xor_sync(0xffffffffu, i, o);
-        const int w2 = __shfl_xor_sync(0xffffffffu, who, o);
-        if (better(k2, i2, k, i)) { k = k2; i = i2; who = w2; }
-      }
-      if (lane == 0) { s_w = i; s_owner = who; }
-    }
-    __syncthreads();
-    const int64_t w = s_w;
-    const int owner = s_owner;
-    if (w != INT64_MAX)
-      for (int r = q + tid; r < b; r += bd) pivc[r] = inbox[par][owner].col[r];
-    __syncthreads();
-    const T piv = w != INT64_MAX ? pivc[q] : T(0);
-    const int code = w == INT64_MAX ? SKEL_ERR_INVALID_ARG
+    int owner = w != INT_MAX ? w / ncl : 0;
+    owner = owner < 0 ? 0 : (owner >= CL ? CL - 1 : owner);
+    const T* lcol = icol[buf][owner].col;        // pivot column: multipliers of step q
+    const T piv = w != INT_MAX ? lcol[q] : T(0);
+    const int code = w == INT_MAX ? SKEL_ERR_INVALID_ARG
                    : !isfinite(piv) ? SKEL_ERR_NONFINITE
                    : piv == T(0) ? SKEL_ERR_RANK_DEFICIENT : 0;
     if (code != 0) {                       // uniform over the cluster
@@ -170,41 +313,65 @@ __global__ void __launch_bounds__(kPanelThreads) lupp_panel_kernel(const PanelPa
       stopped = true;
       break;
     }
-    if (tid == 0) s_J[q] = (int)w;
+    if (tid == 0) s_J[q] = w;
     if (crank == 0 && p.L)
-      for (int r = q + tid; r < b; r += bd) s_L[r][q] = pivc[r];
-    const int mine_w = owner == crank ? (int)(w - c0) : -1;
-    // R(t, :) replaces row q of P (row q is final at step q); the update of rows q+1.. uses it
+      for (int r = q + tid; r < b; r += bd) s_L[r][q] = lcol[r];
+    const int mine_w = owner == crank ? w - c0 : -1;
+    const bool more = q + 1 < b;
+    const T lnext = more ? lcol[q + 1] : T(0);
+    T key = T(-1);
+    int idx = INT_MAX;
+    // R(t, :) replaces row q of P (row q is final at step q); row q+1 is updated and scanned
     for (int jj = tid; jj < nl; jj += bd) {
       T* pq = &P[(int64_t)q * ncl + jj];
       T rv;
-      if (jj == mine_w) rv = T(1);
-      else if (sl[jj]) rv = T(0);
-      else rv = ddiv(*pq, piv);
-      *pq = rv;
-      if (jj != mine_w && !sl[jj]) {
-        int r = q + 1;
-        for (; r + 4 <= b; r += 4) {       // loads of four rows first, then their updates
-          const T l0 = pivc[r], l1 = pivc[r + 1], l2 = pivc[r + 2], l3 = pivc[r + 3];
-          T* x = &P[(int64_t)r * ncl + jj];
-          T x0 = x[0], x1 = x[ncl], x2 = x[2 * ncl], x3 = x[3 * ncl];
-          x0 = dsub(x0, dmul(l0, rv));
-          x1 = dsub(x1, dmul(l1, rv));
-          x2 = dsub(x2, dmul(l2, rv));
-          x3 = dsub(x3, dmul(l3, rv));
-          x[0] = x0; x[ncl] = x1; x[2 * ncl] = x2; x[3 * ncl] = x3;
-        }
-        for (; r < b; ++r) {
-          T* x = &P[(int64_t)r * ncl + jj];
-          *x = dsub(*x, dmul(pivc[r], rv));
+      if (jj == mine_w) {
+        rv = T(1);
+        sl[jj] = 1;
+      } else if (sl[jj]) {
+        rv = T(0);
+      } else {
+        rv = ddiv(*pq, piv);
+        if (more) {
+          const T x = dsub(pq[ncl], dmul(lnext, rv));
+          pq[ncl] = x;
+          const T kx = pivot_key(x);
+          if (cand_better(kx, c0 + jj, key, idx)) { key = kx; idx = c0 + jj; }
         }
       }
+      *pq = rv;
     }
-    __syncthreads();
-    if (mine_w >= 0 && tid == 0) sl[mine_w] = 1;
+    int jb = -1;                          // the sent column: warp 0 updates it
+    if (more) {
+      cta_argmax(q + 1, key, idx);
+      if (idx != INT_MAX) jb = idx - c0;
+      if (warp == 0) {
+        const int nb = (q + 1) % kInbox;
+        push_candidate<T>(col_base(nb), hdr_base(nb), bar_base(nb), crank, CL, P, ncl, b, q + 1, key, idx, jb, lcol);
+      }
+    }
+    for (int jj = tid; jj < nl; jj += bd) {
+      if (sl[jj] || jj == jb) continue;
+      const T rv = P[(int64_t)q * ncl + jj];
+      int r = q + 2;
+      for (; r + 4 <= b; r += 4) {         // loads of four rows first, then their updates
+        const T l0 = lcol[r], l1 = lcol[r + 1], l2 = lcol[r + 2], l3 = lcol[r + 3];
+        T* x = &P[(int64_t)r * ncl + jj];
+        T x0 = x[0], x1 = x[ncl], x2 = x[2 * ncl], x3 = x[3 * ncl];
+        x0 = dsub(x0, dmul(l0, rv));
+        x1 = dsub(x1, dmul(l1, rv));
+        x2 = dsub(x2, dmul(l2, rv));
+        x3 = dsub(x3, dmul(l3, rv));
+        x[0] = x0; x[ncl] = x1; x[2 * ncl] = x2; x[3 * ncl] = x3;
+      }
+      for (; r < b; ++r) {
+        T* x = &P[(int64_t)r * ncl + jj];
+        *x = dsub(*x, dmul(lcol[r], rv));
+      }
+    }
     done = q + 1;
-    __syncthreads();
   }
+  __syncthreads();
   // write out what the completed steps produced: R rows, selected flags, pivots, L
   for (int q = 0; q < done; ++q)
     for (int jj = tid; jj < nl; jj += bd) p.R[(int64_t)(p.t0 + q) * p.ldr + c0 + jj] = P[(int64_t)q * ncl + jj];
@@ -220,24 +387,25 @@ __global__ void __launch_bounds__(kPanelThreads) lupp_panel_kernel(const PanelPa
   // Multipliers of the trailing rows, M(r, q) = S^{(q)}(r, j_q): one warp per row, lane i
   // owns q = i and q = i + 32; after M(r, qq) is final it is broadcast and every later q
   // subtracts M(r, qq) R(t0+qq, j_q) -- the same operations in the same order as
-  // step-by-step elimination.  R(panel, J_panel) is staged in shared memory (reusing P).
-  __threadfence();
-  cluster.sync();
-  if (!stopped && p.s - p.t0 - b > 0) {
-    T* RJ = P;                                             // [b][b], b <= 64
-    int* J = reinterpret_cast<int*>(RJ + (size_t)b * b);
-    for (int q = tid; q < b; q += bd) J[q] = s_J[q];
-    __syncthreads();
-    for (int qq = 0; qq < b; ++qq)
-      for (int q = tid; q < b; q += bd) RJ[qq * b + q] = __ldcg(p.R + (int64_t)(p.t0 + qq) * p.ldr + J[q]);
-    __syncthreads();
+  // step-by-step elimination.  R(panel, J_panel) is read from the owners' shared memory.
+  cluster.sync();     // every CTA's R rows are final in its shared memory
+  const bool trail = !stopped && done == b && p.s - p.t0 - b > 0;
+  if (trail) {
+    for (int e = tid; e < b * b; e += bd) {
+      const int qq = e / b, q = e % b;
+      const int j = s_J[q];
+      const int o = j / ncl;
+      RJ[e] = cluster.map_shared_rank(P, o)[(int64_t)qq * ncl + (j - o * ncl)];
+    }
+  }
+  cluster.sync();     // no CTA leaves or reuses its shared memory while others read it
+  if (trail) {
     const int rows = p.s - p.t0 - b;
-    const int warp = tid >> 5, nwarps = bd >> 5;
-    for (int ri = crank * nwarps + warp; ri < rows; ri += CL * nwarps) {
+    for (int ri = crank * nw + warp; ri < rows; ri += CL * nw) {
       const int64_t r = p.t0 + b + ri;
       const int q0 = lane, q1 = lane + 32;
-      T a0 = q0 < b ? p.Xg[r * p.n + J[q0]] : T(0);
-      T a1 = q1 < b ? p.Xg[r * p.n + J[q1]] : T(0);
+      T a0 = q0 < b ? p.Xg[r * p.n + s_J[q0]] : T(0);
+      T a1 = q1 < b ? p.Xg[r * p.n + s_J[q1]] : T(0);
       for (int qq = 0; qq < b; ++qq) {
         const T mq = __shfl_sync(0xffffffffu, qq < 32 ? a0 : a1, qq & 31);   // final M(r, qq)
         if (q0 > qq && q0 < b) a0 = dsub(a0, dmul(mq, RJ[qq * b + q0]));
@@ -252,60 +420,45 @@ __global__ void __launch_bounds__(kPanelThreads) lupp_panel_kernel(const PanelPa
       }
     }
   }
-  cluster.sync();     // no CTA leaves while others may still read its shared memory
 }
 
-// Trailing update: rows t0+b .. s-1 of Xg, a block of RB rows x CW columns per CTA, with the
-// panel rows R(t0.., j0..j0+CW) staged in shared memory.
-constexpr int RB = 16;
-template <typename T> constexpr int trail_cw() { return sizeof(T) == 8 ? 256 : 512; }
+// Trailing update: rows t0+b .. s-1 of Xg.  A CTA covers kTrailRows rows x kTrailThreads
+// columns; each thread owns one column and keeps its kTrailRows entries in registers, so the
+// elimination chains of the rows are independent.  R(t0+q, j) is read from L2 once per q and
+// applied to every row; the multipliers sit transposed in shared memory (a broadcast row per
+// q).  Each entry sees the same operations in the same order as step-by-step elimination.
+constexpr int kTrailRows = 16;
+constexpr int kTrailThreads = 256;
 
 template <typename T>
-size_t trail_smem(int b) {
-  return sizeof(T) * ((size_t)RB * b + (size_t)b * trail_cw<T>());
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) lupp_trail_kernel(const PanelParams<T> p) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int CW = trail_cw<T>();
-  const int b = p.b, tid = threadIdx.x;
-  const int r0 = blockIdx.y * RB;                         // index among the trailing rows
+__global__ void __launch_bounds__(kTrailThreads) lupp_trail_kernel(const PanelParams<T> p) {
+  __shared__ __align__(16) T Mt[kMaxPanel][kTrailRows];   // Mt[q][u] = M(r0 + u, q)
+  const int b = p.b;
+  const int r0 = blockIdx.y * kTrailRows;                // index among the trailing rows
   const int rows = p.s - p.t0 - b;
-  const int nrows = rows - r0 < RB ? rows - r0 : RB;
+  const int nrows = rows - r0 < kTrailRows ? rows - r0 : kTrailRows;
   if (nrows <= 0) return;
   if (*(volatile int32_t*)p.fail) return;
-  T* M = reinterpret_cast<T*>(smem);                      // [RB][b]
-  T* Rt = M + (size_t)RB * b;                             // [b][CW]: R(t0+q, j0+c)
-  const int64_t j0 = (int64_t)blockIdx.x * CW;
-  const int nc = (int)std::min<int64_t>(CW, p.n - j0);
-  for (int q = 0; q < b; ++q)
-    for (int c = tid; c < nc; c += blockDim.x) Rt[q * CW + c] = p.R[(int64_t)(p.t0 + q) * p.ldr + j0 + c];
-  for (int e = tid; e < nrows * b; e += blockDim.x) M[e] = p.M[(int64_t)r0 * b + e];
-  __syncthreads();
-  for (int c = tid; c < nc; c += blockDim.x) {
-    const int64_t j = j0 + c;
-    if (p.sel[j]) continue;
-    // four independent elimination chains per thread (rows ri..ri+3), each in step order
-    for (int ri = 0; ri < nrows; ri += 4) {
-      const int nr4 = nrows - ri < 4 ? nrows - ri : 4;
-      T v[4];
-      T* x[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        x[u] = &p.Xg[(int64_t)(p.t0 + b + r0 + ri + (u < nr4 ? u : 0)) * p.n + j];
-        v[u] = *x[u];
-      }
-      for (int q = 0; q < b; ++q) {
-        const T rq = Rt[q * CW + c];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = dsub(v[u], dmul(M[(ri + (u < nr4 ? u : 0)) * b + q], rq));
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (u < nr4) *x[u] = v[u];
-    }
+  for (int e = threadIdx.x; e < b * kTrailRows; e += blockDim.x) {
+    const int q = e / kTrailRows, u = e % kTrailRows;
+    Mt[q][u] = u < nrows ? p.M[(int64_t)(r0 + u) * b + q] : T(0);
   }
+  __syncthreads();
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= p.n || p.sel[j]) return;
+  T* x = p.Xg + (int64_t)(p.t0 + b + r0) * p.n + j;
+  T v[kTrailRows];
+#pragma unroll
+  for (int u = 0; u < kTrailRows; ++u) v[u] = u < nrows ? x[(int64_t)u * p.n] : T(0);
+  const T* Rj = p.R + (int64_t)p.t0 * p.ldr + j;
+  for (int q = 0; q < b; ++q) {
+    const T rq = Rj[(int64_t)q * p.ldr];
+#pragma unroll
+    for (int u = 0; u < kTrailRows; ++u) v[u] = dsub(v[u], dmul(Mt[q][u], rq));
+  }
+#pragma unroll
+  for (int u = 0; u < kTrailRows; ++u)
+    if (u < nrows) x[(int64_t)u * p.n] = v[u];
 }
 
 template <typename T>
@@ -330,9 +483,8 @@ struct PanelPlan {
 
 template <typename T>
 size_t panel_smem(int b, int ncl) {
-  // P (b x ncl) is reused after the steps for R(panel, J_panel) (b x b) and J (b ints)
-  const size_t pbuf = std::max((size_t)b * ncl, (size_t)b * b + (size_t)b);
-  return sizeof(T) * (pbuf + ncl + b) + ncl + 64;
+  // P (b x ncl), R(panel, J_panel) (b x b), selected flags (ncl bytes)
+  return sizeof(T) * ((size_t)b * ncl + (size_t)b * b) + ncl + 64;
 }
 
 // Largest cluster the device accepts for the panel kernel (16 non-portable, else 8), and the
@@ -340,6 +492,7 @@ size_t panel_smem(int b, int ncl) {
 template <typename T>
 PanelPlan plan_panel(int64_t n, int s) {
   PanelPlan pl;
+  if (n >= (int64_t)1 << 30) return pl;   // column indices are 32-bit inside the panel kernel
   static int max_cluster = -1;
   static size_t kPanelSmem = 0;       // dynamic budget = opt-in maximum - static shared memory
   if (max_cluster < 0) {
@@ -437,13 +590,8 @@ skel_status run_panel_t(const PanelPlan& pl, const T* X, int64_t n, int64_t ldx,
     note_launches(1);
     const int rows = s - t0 - p.b;
     if (rows > 0) {
-      constexpr int CW = trail_cw<T>();
-      dim3 grid((unsigned)((n + CW - 1) / CW), (unsigned)((rows + RB - 1) / RB));
-      const size_t tsm = trail_smem<T>(p.b);
-      if (tsm > 48 * 1024 &&
-          cudaFuncSetAttribute(lupp_trail_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm) != cudaSuccess)
-        return SKEL_ERR_CUDA;
-      lupp_trail_kernel<T><<<grid, 256, tsm, st>>>(p);
+      dim3 grid((unsigned)((n + kTrailThreads - 1) / kTrailThreads), (unsigned)((rows + kTrailRows - 1) / kTrailRows));
+      lupp_trail_kernel<T><<<grid, kTrailThreads, 0, st>>>(p);
       note_launches(1);
     }
   }
