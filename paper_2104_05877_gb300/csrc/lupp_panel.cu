@@ -47,13 +47,15 @@ struct PanelParams {
 };
 
 // Per-step exchange.  Every CTA sends every CTA of the cluster (itself included) its step-q
-// candidate: a header {key, column index} and the candidate's column rows 4*floor(q/4) .. b-1
-// in 16-byte groups.  The stores are st.async into the receiver's inbox buffer q % 3, each
-// completing its byte count on the receiver's mbarrier of that buffer, so a sender never waits
-// for its stores and a receiver waits only for its own barrier phase.  A sender without
-// candidates still sends the full byte count (key -1, index INT_MAX).
+// candidate: a header {key, column index} and the candidate's column, rows q0 .. b-1 of the
+// sending step's sub-block [q0, q1), in 16-byte groups.  The stores are st.async into the
+// receiver's inbox buffer q % 3, each completing its byte count on the receiver's mbarrier of
+// that buffer, so a sender never waits for its stores and a receiver waits only for its own
+// barrier phase.  A sender without candidates still sends the full byte count (key -1, index
+// INT_MAX).
 constexpr int kMaxPanel = 64;
 constexpr int kInbox = 3;
+constexpr int kPanelKB = 8;    // sub-block of steps whose updates of the rows below are deferred
 template <typename T>
 struct __align__(16) CandCol {
   T col[kMaxPanel];
@@ -66,11 +68,14 @@ struct __align__(16) CandHdr {
 
 template <typename T>
 __host__ __device__ constexpr uint32_t hdr_bytes() { return sizeof(T) + 4; }
-// bytes one sender delivers to one receiver for step q of a b-row panel
+// bytes one sender delivers to one receiver when its sub-block starts at row q0s (a multiple
+// of 4) in a b-row panel
 template <typename T>
-__host__ __device__ constexpr uint32_t push_bytes(int q, int b) {
-  return hdr_bytes<T>() + (uint32_t)((b + 3) / 4 - q / 4) * 4u * (uint32_t)sizeof(T);
+__host__ __device__ constexpr uint32_t push_bytes(int q0s, int b) {
+  return hdr_bytes<T>() + (uint32_t)((b + 3) / 4 - q0s / 4) * 4u * (uint32_t)sizeof(T);
 }
+// sub-block start of the step that sends the candidates of step qn
+__host__ __device__ constexpr int send_q0(int qn) { return qn == 0 ? 0 : (qn - 1) / kPanelKB * kPanelKB; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
   return (uint32_t)__cvta_generic_to_shared(ptr);
@@ -126,50 +131,63 @@ __device__ __forceinline__ bool cand_better(T ka, int ia, T kb, int ib) {
   return ka > kb || (ka == kb && ia < ib);
 }
 
-template <typename T>
-__device__ __forceinline__ void warp_argmax(T& k, int& i) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const T k2 = __shfl_xor_sync(0xffffffffu, k, o);
-    const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-    if (cand_better(k2, i2, k, i)) { k = k2; i = i2; }
-  }
+// Warp argmax in the pivot order with warp reductions: keys are >= 0 (magnitudes, +inf for
+// non-finite entries) or -1 (no candidate), so their bit patterns order like the values.
+__device__ __forceinline__ void warp_argmax(float& k, int& i) {
+  const unsigned kbits = k >= 0.f ? __float_as_uint(k) : 0u;
+  const unsigned m = __reduce_max_sync(0xffffffffu, kbits);
+  const unsigned im = __reduce_min_sync(0xffffffffu, kbits == m ? (unsigned)i : 0x7fffffffu);
+  i = (int)im;
+  k = im == 0x7fffffffu ? -1.f : __uint_as_float(m);
+}
+__device__ __forceinline__ void warp_argmax(double& k, int& i) {
+  const unsigned long long bits = k >= 0.0 ? (unsigned long long)__double_as_longlong(k) : 0ull;
+  const unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
+  const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+  const unsigned im = __reduce_min_sync(0xffffffffu, hi == mh && lo == ml ? (unsigned)i : 0x7fffffffu);
+  i = (int)im;
+  k = im == 0x7fffffffu ? -1.0 : __longlong_as_double((long long)(((unsigned long long)mh << 32) | ml));
 }
 
 template <typename T> __device__ __forceinline__ uint32_t bits32(T v) { return __float_as_uint((float)v); }
 template <typename T> __device__ __forceinline__ uint64_t bits64(T v) { return (uint64_t)__double_as_longlong((double)v); }
 
-// Warp 0 sends this CTA's candidate (key k, index i, local column jb) for step qn to every
-// CTA of the cluster.  With lprev (qn > 0) rows qn+1.. of column jb still lack step qn-1's
-// update (multipliers lprev, R(qn-1, jb) in row qn-1 of P): it is applied here and written
-// back to P, so the owner thread skips that column in its own update.  Lane l covers rows
-// 4(l%16) .. 4(l%16)+3 for the receivers of parity l/16.
+// Warp 0 sends this CTA's candidate (key k, index i, local column jb) for step qn = q+1 to
+// every CTA of the cluster; step q lies in the sub-block [q0, q1).  Rows qn+1 .. q1-1 of
+// column jb take step q's update here (multipliers lcol, R(q, jb) in row q of P) and are
+// written back, so the owner thread skips the column; rows from q1 on are sent as they are
+// (updated through step q0-1) and the receivers apply the sub-block's steps themselves.  When
+// qn = q1 starts the next sub-block, the sub-block's deferred update of the column's rows
+// q1+1 .. b-1 (resolved multipliers LkT) is applied here after the send, again in place of the
+// owner.  Lane l covers rows 4(l%16) .. 4(l%16)+3 for the receivers of parity l/16.  For the
+// first candidate (qn = 0) lcol is null.
 template <typename T>
 __device__ __forceinline__ void push_candidate(uint32_t col_base, uint32_t hdr_base, uint32_t bar_local,
-                                               int crank, int CL, T* P, int ncl, int b, int qn, T k,
-                                               int i, int jb, const T* lprev) {
+                                               int crank, int CL, T* P, int ldp, int b, int qn, int q0,
+                                               int q1, T k, int i, int jb, const T* lcol,
+                                               const T (*LkT)[kPanelKB]) {
   const int lane = threadIdx.x & 31;
   const bool have = i != INT_MAX;
-  const int g = lane & 15;
-  const int f0 = 4 * g;
-  const bool active = f0 < b && f0 + 3 >= qn;      // groups floor(qn/4) .. ceil(b/4)-1
+  const int f0 = 4 * (lane & 15);
+  const bool active = f0 < b && f0 >= q0;          // groups q0/4 .. ceil(b/4)-1
   T v[4] = {T(0), T(0), T(0), T(0)};
   if (have && active) {
-    const T rq = lprev ? P[(int64_t)(qn - 1) * ncl + jb] : T(0);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int f = f0 + u;
-      if (f < b) {
-        v[u] = P[(int64_t)f * ncl + jb];           // rows < qn: R(f, jb), final
-        if (lprev && f > qn) v[u] = dsub(v[u], dmul(lprev[f], rq));
-      }
+    for (int u = 0; u < 4; ++u)
+      if (f0 + u < b) v[u] = P[(f0 + u) * ldp + jb];
+    if (lcol) {
+      const T rq = P[(qn - 1) * ldp + jb];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (f0 + u > qn && f0 + u < q1) v[u] = dsub(v[u], dmul(lcol[f0 + u], rq));
     }
   }
   __syncwarp();                          // every lane has read column jb before it is rewritten
-  if (have && active && lprev && lane < 16)
+  if (have && active && lcol && lane < 16)
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      if (f0 + u < b && f0 + u > qn) P[(int64_t)(f0 + u) * ncl + jb] = v[u];
+      if (f0 + u > qn && f0 + u < q1) P[(f0 + u) * ldp + jb] = v[u];
   const uint32_t col_off = (uint32_t)(crank * sizeof(CandCol<T>) + f0 * sizeof(T));
   if (active)
     for (int d = lane >> 4; d < CL; d += 2) {
@@ -189,16 +207,33 @@ __device__ __forceinline__ void push_candidate(uint32_t col_base, uint32_t hdr_b
     else st_async_b64(dst, bits64(k), bar);
     st_async_b32(dst + sizeof(T), (uint32_t)i, bar);
   }
+  if (have && lcol && qn == q1 && q1 < b)
+    for (int f = q1 + 1 + lane; f < b; f += 32) {
+      T x = P[f * ldp + jb];
+#pragma unroll
+      for (int kk = 0; kk < kPanelKB; ++kk) x = dsub(x, dmul(LkT[f][kk], P[(q0 + kk) * ldp + jb]));
+      P[f * ldp + jb] = x;
+    }
 }
 
-// Step q of the panel (one-step lookahead; one CTA barrier, no cluster barrier):
-//   wait    the mbarrier phase of inbox q % 3: every CTA's step-q candidate has landed
+// Step q of the panel (one-step lookahead; no cluster barrier).  Steps are grouped in
+// sub-blocks [q0, q1) of kPanelKB.  Rows inside the current sub-block are updated at every
+// step; rows below it once per sub-block with all of its steps (each entry read once, updated
+// kPanelKB times in step order, written once), which divides the shared memory traffic of the
+// rank-1 updates by kPanelKB.  The multipliers of those deferred rows arrive as the pivot
+// columns were stored (updated through step q0-1) and are completed once per sub-block:
+//   L(f, k) = raw(f, k) - sum_{q0 <= k' < k} L(f, k') R(k', j_k),  k' in order,
+// which is the tail of the textbook sequence for S^(k)(f, j_k).
+//   wait    the mbarrier phase of inbox q % 3 (bounded), then a CTA barrier
 //   select  every warp reduces the CL headers (same result everywhere); the winner's column
-//           holds the multipliers of step q
-//   row q   R(t, :) = P(q, :) / pivot over row q of P, the update of row q+1, and this
-//           thread's step-(q+1) candidates over row q+1, in one pass over its columns
-//   push    CTA argmax (one __syncthreads); warp 0 sends the winner with its column
-//   rest    the update of rows q+2.. (skipping the sent column) overlaps the exchange
+//           holds the multipliers of step q (at a sub-block's first step its rows still lack
+//           the previous sub-block and are completed first)
+//   row q   R(t, :) = P(q, :) / pivot over row q of P, the update of row q+1 (all steps of
+//           the sub-block when row q+1 starts the next one), and this thread's step-(q+1)
+//           candidates over row q+1, in one pass over its columns
+//   push    CTA argmax (one CTA barrier); warp 0 sends the winner with its column
+//   rest    the update of rows q+2 .. q1-1, or at the end of a sub-block the deferred update
+//           of rows q1+1 .. b-1 (skipping the sent column), overlaps the exchange
 // Inbox q % 3 is rewritten for step q+3 only after its sender has received step q+2 from
 // this CTA, which this CTA sends after every warp is done with step q's multipliers.  The
 // byte count of step q+3 is armed right after step q's phase completes.
@@ -210,6 +245,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
   const int CL = (int)cluster.num_blocks();
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
   const int b = p.b, ncl = p.ncl;
+  const int ldp = ncl + 1;            // odd row stride: a column read across rows is conflict-free
   const int c0 = crank * ncl;
   const int nl = (int)(p.n - c0 < 0 ? 0 : (p.n - c0 < ncl ? p.n - c0 : ncl));
 
@@ -219,10 +255,13 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
   __shared__ T wkey[2][32];
   __shared__ int widx[2][32];
   __shared__ int s_J[kMaxPanel];           // pivots of this panel, written out at the end
-  __shared__ T s_L[kMaxPanel][kMaxPanel];  // L(t0+r, t0+q) = pivot column q, row r >= q
   __shared__ int s_timeout;
-  T* P = reinterpret_cast<T*>(smem);                        // [b][ncl]
-  T* RJ = P + (size_t)b * ncl;                              // [b][b]: R(t0+qq, j_q)
+  __shared__ T Lk[2][kPanelKB][kMaxPanel];                 // deferred-row multipliers, step-major
+  __shared__ __align__(16) T LkT[2][kMaxPanel][kPanelKB];  // completed ones, row-major
+  __shared__ T Rsub[kPanelKB][kPanelKB];                   // Rsub[k][k'] = R(q0+k', j_{q0+k})
+  __shared__ T lfix[kMaxPanel];                            // completed pivot column
+  T* P = reinterpret_cast<T*>(smem);                        // [b][ldp]
+  T* RJ = P + (size_t)b * ldp;                              // [b][b]: R(t0+qq, j_q)
   unsigned char* sl = reinterpret_cast<unsigned char*>(RJ + (size_t)b * b);   // [ncl]
 
   if (*(volatile int32_t*)p.fail) return;   // an earlier panel stopped (uniform over the cluster)
@@ -239,7 +278,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
         if (q0 + u < b) v[u] = p.Xg[(int64_t)(p.t0 + q0 + u) * p.n + c0 + jj];
 #pragma unroll
       for (int u = 0; u < 8; ++u)
-        if (q0 + u < b) P[(int64_t)(q0 + u) * ncl + jj] = v[u];
+        if (q0 + u < b) P[(q0 + u) * ldp + jj] = v[u];
     }
   for (int jj = tid; jj < nl; jj += bd) sl[jj] = p.sel[c0 + jj];
   const uint32_t col0 = smem_u32(&icol[0][0]), hdr0 = smem_u32(&ihdr[0][0]), bar0 = smem_u32(&ibar[0]);
@@ -269,10 +308,12 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
     }
     cta_argmax(0, key, idx);
     if (tid == 0)
-      for (int k = 0; k < kInbox && k < b; ++k) mbar_expect_tx(bar_base(k), (uint32_t)CL * push_bytes<T>(k, b));
+      for (int k = 0; k < kInbox && k < b; ++k)
+        mbar_expect_tx(bar_base(k), (uint32_t)CL * push_bytes<T>(send_q0(k), b));
     cluster.sync();     // barriers initialised and armed everywhere before the first send
     if (warp == 0)
-      push_candidate<T>(col_base(0), hdr_base(0), bar_base(0), crank, CL, P, ncl, b, 0, key, idx, idx - c0, nullptr);
+      push_candidate<T>(col_base(0), hdr_base(0), bar_base(0), crank, CL, P, ldp, b, 0, 0, 0, key, idx,
+                        idx - c0, nullptr, LkT[0]);
   }
 
   bool stopped = false;
@@ -290,18 +331,23 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
       stopped = true;
       break;
     }
-    if (tid == 0 && q + kInbox < b) mbar_expect_tx(bar_base(buf), (uint32_t)CL * push_bytes<T>(q + kInbox, b));
-    int w;
+    if (tid == bd - 1 && q + kInbox < b)
+      mbar_expect_tx(bar_base(buf), (uint32_t)CL * push_bytes<T>(send_q0(q + kInbox), b));
+    const int q0 = q - q % kPanelKB;
+    const int q1 = q0 + kPanelKB < b ? q0 + kPanelKB : b;
+    const int sb = (q / kPanelKB) & 1;
+    int w, owner;
     {
+      const int i0 = lane < CL ? ihdr[buf][lane].idx : INT_MAX;
       T k = lane < CL ? ihdr[buf][lane].key : T(-1);
-      int i = lane < CL ? ihdr[buf][lane].idx : INT_MAX;
+      int i = i0;
       warp_argmax(k, i);
       w = i;
+      owner = __ffs(__ballot_sync(0xffffffffu, i0 == w && w != INT_MAX)) - 1;
+      owner = owner < 0 ? 0 : owner;
     }
-    int owner = w != INT_MAX ? w / ncl : 0;
-    owner = owner < 0 ? 0 : (owner >= CL ? CL - 1 : owner);
-    const T* lcol = icol[buf][owner].col;        // pivot column: multipliers of step q
-    const T piv = w != INT_MAX ? lcol[q] : T(0);
+    const T* lc = icol[buf][owner].col;          // pivot column as sent
+    const T piv = w != INT_MAX ? lc[q] : T(0);
     const int code = w == INT_MAX ? SKEL_ERR_INVALID_ARG
                    : !isfinite(piv) ? SKEL_ERR_NONFINITE
                    : piv == T(0) ? SKEL_ERR_RANK_DEFICIENT : 0;
@@ -313,17 +359,54 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
       stopped = true;
       break;
     }
+    const T* lcol = lc;                          // multipliers of step q, rows q+1 ..
+    if (q == q0 && q > 0) {                // rows below q still lack the previous sub-block
+      const int p0 = q0 - kPanelKB;
+      for (int f = q + 1 + tid; f < b; f += bd) {
+        T x = lc[f];
+#pragma unroll
+        for (int kk = 0; kk < kPanelKB; ++kk) x = dsub(x, dmul(Lk[sb ^ 1][kk][f], lc[p0 + kk]));
+        lfix[f] = x;
+      }
+      __syncthreads();
+      lcol = lfix;
+    }
     if (tid == 0) s_J[q] = w;
+    if (tid >= q1 && tid < b) Lk[sb][q - q0][tid] = lcol[tid];        // deferred rows, incomplete
+    if (tid < q - q0) Rsub[q - q0][tid] = lc[q0 + tid];               // R(q0+tid, j_q)
     if (crank == 0 && p.L)
-      for (int r = q + tid; r < b; r += bd) s_L[r][q] = lcol[r];
-    const int mine_w = owner == crank ? w - c0 : -1;
+      for (int r = q + tid; r < q1; r += bd) p.L[(int64_t)(p.t0 + r) * p.ldl + t] = r == q ? piv : lcol[r];
     const bool more = q + 1 < b;
-    const T lnext = more ? lcol[q + 1] : T(0);
+    const bool blk_end = more && q + 1 == q1;    // row q+1 starts the next sub-block
+    if (blk_end) {                         // complete the deferred rows' multipliers, in order
+      if (tid >= q1 && tid < b) {
+        T xs[kPanelKB];
+#pragma unroll
+        for (int kk = 0; kk < kPanelKB; ++kk) {
+          T x = Lk[sb][kk][tid];
+#pragma unroll
+          for (int k2 = 0; k2 < kk; ++k2)
+            x = dsub(x, dmul(xs[k2], kk == kPanelKB - 1 ? lc[q0 + k2] : Rsub[kk][k2]));
+          xs[kk] = x;
+        }
+#pragma unroll
+        for (int kk = 0; kk < kPanelKB; ++kk) {
+          Lk[sb][kk][tid] = xs[kk];
+          LkT[sb][tid][kk] = xs[kk];
+        }
+        if (crank == 0 && p.L)
+#pragma unroll
+          for (int kk = 0; kk < kPanelKB; ++kk) p.L[(int64_t)(p.t0 + tid) * p.ldl + p.t0 + q0 + kk] = xs[kk];
+      }
+      __syncthreads();
+    }
+    const int mine_w = owner == crank ? w - c0 : -1;
+    const T lnext = more && !blk_end ? lcol[q + 1] : T(0);
     T key = T(-1);
     int idx = INT_MAX;
     // R(t, :) replaces row q of P (row q is final at step q); row q+1 is updated and scanned
     for (int jj = tid; jj < nl; jj += bd) {
-      T* pq = &P[(int64_t)q * ncl + jj];
+      T* pq = &P[q * ldp + jj];
       T rv;
       if (jj == mine_w) {
         rv = T(1);
@@ -333,8 +416,16 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
       } else {
         rv = ddiv(*pq, piv);
         if (more) {
-          const T x = dsub(pq[ncl], dmul(lnext, rv));
-          pq[ncl] = x;
+          T x = pq[ldp];
+          if (!blk_end) {
+            x = dsub(x, dmul(lnext, rv));
+          } else {                         // all steps of the sub-block for row q1
+            const T* Lq1 = LkT[sb][q1];
+#pragma unroll
+            for (int kk = 0; kk < kPanelKB - 1; ++kk) x = dsub(x, dmul(Lq1[kk], P[(q0 + kk) * ldp + jj]));
+            x = dsub(x, dmul(Lq1[kPanelKB - 1], rv));
+          }
+          pq[ldp] = x;
           const T kx = pivot_key(x);
           if (cand_better(kx, c0 + jj, key, idx)) { key = kx; idx = c0 + jj; }
         }
@@ -347,43 +438,43 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
       if (idx != INT_MAX) jb = idx - c0;
       if (warp == 0) {
         const int nb = (q + 1) % kInbox;
-        push_candidate<T>(col_base(nb), hdr_base(nb), bar_base(nb), crank, CL, P, ncl, b, q + 1, key, idx, jb, lcol);
+        push_candidate<T>(col_base(nb), hdr_base(nb), bar_base(nb), crank, CL, P, ldp, b, q + 1, q0, q1, key,
+                          idx, jb, lcol, LkT[sb]);
       }
     }
-    for (int jj = tid; jj < nl; jj += bd) {
-      if (sl[jj] || jj == jb) continue;
-      const T rv = P[(int64_t)q * ncl + jj];
-      int r = q + 2;
-      for (; r + 4 <= b; r += 4) {         // loads of four rows first, then their updates
-        const T l0 = lcol[r], l1 = lcol[r + 1], l2 = lcol[r + 2], l3 = lcol[r + 3];
-        T* x = &P[(int64_t)r * ncl + jj];
-        T x0 = x[0], x1 = x[ncl], x2 = x[2 * ncl], x3 = x[3 * ncl];
-        x0 = dsub(x0, dmul(l0, rv));
-        x1 = dsub(x1, dmul(l1, rv));
-        x2 = dsub(x2, dmul(l2, rv));
-        x3 = dsub(x3, dmul(l3, rv));
-        x[0] = x0; x[ncl] = x1; x[2 * ncl] = x2; x[3 * ncl] = x3;
+    if (more && !blk_end) {                // rows q+2 .. q1-1: step q
+      for (int jj = tid; jj < nl; jj += bd) {
+        if (sl[jj] || jj == jb) continue;
+        const T rv = P[q * ldp + jj];
+        for (int r = q + 2; r < q1; ++r) {
+          T* x = &P[r * ldp + jj];
+          *x = dsub(*x, dmul(lcol[r], rv));
+        }
       }
-      for (; r < b; ++r) {
-        T* x = &P[(int64_t)r * ncl + jj];
-        *x = dsub(*x, dmul(lcol[r], rv));
+    } else if (blk_end) {                  // rows q1+1 .. b-1: steps q0 .. q (a full sub-block)
+      for (int jj = tid; jj < nl; jj += bd) {
+        if (sl[jj] || jj == jb) continue;
+        T rk[kPanelKB];
+#pragma unroll
+        for (int kk = 0; kk < kPanelKB; ++kk) rk[kk] = P[(q0 + kk) * ldp + jj];
+        for (int r = q1 + 1; r < b; ++r) {
+          T* x = &P[r * ldp + jj];
+          T xv = *x;
+#pragma unroll
+          for (int kk = 0; kk < kPanelKB; ++kk) xv = dsub(xv, dmul(LkT[sb][r][kk], rk[kk]));
+          *x = xv;
+        }
       }
     }
     done = q + 1;
   }
   __syncthreads();
-  // write out what the completed steps produced: R rows, selected flags, pivots, L
+  // write out what the completed steps produced: R rows, selected flags, pivots
   for (int q = 0; q < done; ++q)
-    for (int jj = tid; jj < nl; jj += bd) p.R[(int64_t)(p.t0 + q) * p.ldr + c0 + jj] = P[(int64_t)q * ncl + jj];
+    for (int jj = tid; jj < nl; jj += bd) p.R[(int64_t)(p.t0 + q) * p.ldr + c0 + jj] = P[q * ldp + jj];
   for (int jj = tid; jj < nl; jj += bd) p.sel[c0 + jj] = sl[jj];
-  if (crank == 0) {
+  if (crank == 0)
     for (int q = tid; q < done; q += bd) p.Js[p.t0 + q] = s_J[q];
-    if (p.L)
-      for (int e = tid; e < b * done; e += bd) {
-        const int r = e / done, q = e % done;
-        if (r >= q) p.L[(int64_t)(p.t0 + r) * p.ldl + p.t0 + q] = s_L[r][q];
-      }
-  }
   // Multipliers of the trailing rows, M(r, q) = S^{(q)}(r, j_q): one warp per row, lane i
   // owns q = i and q = i + 32; after M(r, qq) is final it is broadcast and every later q
   // subtracts M(r, qq) R(t0+qq, j_q) -- the same operations in the same order as
@@ -395,7 +486,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
       const int qq = e / b, q = e % b;
       const int j = s_J[q];
       const int o = j / ncl;
-      RJ[e] = cluster.map_shared_rank(P, o)[(int64_t)qq * ncl + (j - o * ncl)];
+      RJ[e] = cluster.map_shared_rank(P, o)[qq * ldp + (j - o * ncl)];
     }
   }
   cluster.sync();     // no CTA leaves or reuses its shared memory while others read it
@@ -483,8 +574,8 @@ struct PanelPlan {
 
 template <typename T>
 size_t panel_smem(int b, int ncl) {
-  // P (b x ncl), R(panel, J_panel) (b x b), selected flags (ncl bytes)
-  return sizeof(T) * ((size_t)b * ncl + (size_t)b * b) + ncl + 64;
+  // P (b x (ncl+1)), R(panel, J_panel) (b x b), selected flags (ncl bytes)
+  return sizeof(T) * ((size_t)b * (ncl + 1) + (size_t)b * b) + ncl + 64;
 }
 
 // Largest cluster the device accepts for the panel kernel (16 non-portable, else 8), and the
