@@ -124,6 +124,10 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmArgs a) {
       if (EPI == EPI_RESID) {
         const double d = load_as<double>(a.ref.p, gr * a.ref.sr + gc * a.ref.sc, a.ref_dt) - (double)v;
         part += d * d;
+      } else if (EPI == EPI_ACCUM) {
+        const int64_t off = gr * a.out_sr + gc * a.out_sc;
+        if (a.out_dt == SKEL_F64) static_cast<double*>(a.out)[off] += (double)v;
+        else static_cast<float*>(a.out)[off] += (float)v;
       } else {
         const int64_t off = gr * a.out_sr + gc * a.out_sc;
         if (a.out_dt == SKEL_F64) static_cast<double*>(a.out)[off] = (double)v;
@@ -197,6 +201,7 @@ cudaError_t dispatch_epi(const GemmArgs& a, int nz, GemmLeft left, GemmEpi epi, 
     case EPI_STORE_SQ: return launch_t<T, LEFT_LOAD, EPI_STORE_SQ>(a, nz, st);
     case EPI_RESID: return launch_t<T, LEFT_LOAD, EPI_RESID>(a, 1, st);
     case EPI_SKETCH: return launch_t<T, LEFT_LOAD, EPI_SKETCH>(a, 1, st);
+    case EPI_ACCUM: return launch_t<T, LEFT_LOAD, EPI_ACCUM>(a, 1, st);
   }
   return cudaErrorInvalidValue;
 }

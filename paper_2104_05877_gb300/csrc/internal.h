@@ -20,7 +20,8 @@ enum GemmEpi {
   EPI_STORE = 0,       // out(r,c) = alpha*acc
   EPI_STORE_SQ = 1,    // store, and partial[block] = sum (alpha*acc)^2
   EPI_RESID = 2,       // partial[block] = sum (ref(r,c) - alpha*acc)^2
-  EPI_SKETCH = 3       // store, flag non-finite outputs
+  EPI_SKETCH = 3,      // store, flag non-finite outputs
+  EPI_ACCUM = 4        // out(r,c) += alpha*acc (no K split)
 };
 
 // out(M x N) = alpha * L(M x K) * B(K x N).  `f64` selects FP64 storage+arithmetic for the
@@ -98,6 +99,13 @@ skel_status run_cpqr(skel_dtype dt, const void* X, int64_t l, int64_t n, int64_t
 
 // Householder QR of a tall m x s column-major C (qr.cu): explicit Q (m x s col-major, same
 // dtype, ld = ldq) and R (s x s row-major FP64).
+// Panel-blocked Householder QR on thread-block clusters: reflectors V (m x s, unit lower
+// trapezoidal, column-major) and R (s x s row-major FP64).  qr_panels_workspace returns 0 and
+// run_qr_panels SKEL_ERR_UNSUPPORTED when a panel of at least 8 columns does not fit a cluster.
+size_t qr_panels_workspace(skel_dtype dt, int64_t m, int32_t s);
+skel_status run_qr_panels(skel_dtype dt, const void* C, int64_t m, int64_t ldc, int32_t s, void* V,
+                          int64_t ldv, double* R, int64_t ldr, void* ws, size_t ws_bytes,
+                          int32_t* dev_status, cudaStream_t st);
 size_t qr_workspace(skel_dtype dt, int64_t m, int32_t s);
 skel_status run_qr(skel_dtype dt, const void* C, int64_t m, int64_t ldc, int32_t s, void* Q,
                    int64_t ldq, double* R, int64_t ldr, void* ws, size_t ws_bytes,

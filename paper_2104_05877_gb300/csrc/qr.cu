@@ -1,7 +1,9 @@
 // Householder QR of the tall skeleton C = A(:, Js) (m x s), for the column ID
 // Z = R_C^{-1} Q_C^T A (Eq. (2.1)) and the stable CUR of Remark 3 (also applied to R^T).
 //
-// Factorisation: one persistent cooperative grid; CTA b owns a contiguous block of rows,
+// Factorisation: panels of columns on thread-block clusters (qr_panel.cu) when a panel of at
+// least 8 columns fits the cluster's shared memory; otherwise the kernel below.
+// Fallback factorisation: one persistent cooperative grid; CTA b owns a contiguous block of rows,
 // resident in shared memory (global workspace when too large).  Step t needs the dot
 // products of column t with columns t..s-1 over rows >= t (a "Gram row"): every CTA adds its
 // partial Gram row into a per-step accumulator with atomics, the owner of row t publishes
@@ -187,9 +189,11 @@ skel_status launch_qr_t(const T* C, int64_t m, int64_t ldc, int s, T* Q, int64_t
                         int64_t ldr, void* ws, size_t ws_bytes, int32_t* dev_status,
                         cudaStream_t st) {
   const QrPlan pl = plan_qr<T>(m, s);
-  if (ws_bytes < pl.factor_total + q_extra_bytes<T>(m, s)) return SKEL_ERR_WORKSPACE;
   const bool f64 = sizeof(T) == 8;
   const skel_dtype dt = f64 ? SKEL_F64 : SKEL_F32;
+  const size_t pws = qr_panels_workspace(dt, m, s);     // 0: panels do not fit a cluster
+  const size_t factor = pws > 0 ? pws : pl.factor_total;
+  if (ws_bytes < factor + q_extra_bytes<T>(m, s)) return SKEL_ERR_WORKSPACE;
   char* base = static_cast<char*>(ws);
   QrParams<T> p{};
   p.C = C; p.m = m; p.ldc = ldc; p.s = s; p.R = R; p.ldr = ldr;
@@ -206,7 +210,7 @@ skel_status launch_qr_t(const T* C, int64_t m, int64_t ldc, int s, T* Q, int64_t
   p.mloc = pl.mloc;
   p.in_smem = pl.in_smem;
   p.dev_status = dev_status;
-  char* extra = base + pl.factor_total;
+  char* extra = base + factor;
   T* V = reinterpret_cast<T*>(extra);
   extra += align_up(sizeof(T) * (size_t)m * s);
   double* Gm = reinterpret_cast<double*>(extra);
@@ -220,6 +224,10 @@ skel_status launch_qr_t(const T* C, int64_t m, int64_t ldc, int s, T* Q, int64_t
   void* kws2 = extra;
   p.V = V; p.ldv = m;
 
+  if (pws > 0) {
+    const skel_status r = run_qr_panels(dt, C, m, ldc, s, V, m, R, ldr, base, pws, dev_status, st);
+    if (r != SKEL_OK) return r;
+  } else {
   if (cudaMemsetAsync(base, 0, pl.comm_bytes + pl.acc_bytes, st) != cudaSuccess) return SKEL_ERR_CUDA;
   if (cudaFuncSetAttribute((const void*)qr_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)pl.smem) != cudaSuccess)
@@ -236,6 +244,7 @@ skel_status launch_qr_t(const T* C, int64_t m, int64_t ldc, int s, T* Q, int64_t
   cfg.numAttrs = 1;
   note_launches(1);
   if (cudaLaunchKernelEx(&cfg, qr_factor_kernel<T>, p) != cudaSuccess) return SKEL_ERR_CUDA;
+  }
 
   // G = V^T V (s x s, FP64 out)
   GemmArgs g{};
@@ -267,8 +276,9 @@ skel_status launch_qr_t(const T* C, int64_t m, int64_t ldc, int s, T* Q, int64_t
 }  // namespace
 
 size_t qr_workspace(skel_dtype dt, int64_t m, int32_t s) {
-  if (dt == SKEL_F64) return plan_qr<double>(m, s).factor_total + q_extra_bytes<double>(m, s);
-  return plan_qr<float>(m, s).factor_total + q_extra_bytes<float>(m, s);
+  const size_t pws = qr_panels_workspace(dt, m, s);
+  if (dt == SKEL_F64) return (pws > 0 ? pws : plan_qr<double>(m, s).factor_total) + q_extra_bytes<double>(m, s);
+  return (pws > 0 ? pws : plan_qr<float>(m, s).factor_total) + q_extra_bytes<float>(m, s);
 }
 
 skel_status run_qr(skel_dtype dt, const void* C, int64_t m, int64_t ldc, int32_t s, void* Q,

@@ -1,0 +1,649 @@
+// Panel-blocked Householder QR of the tall skeleton C = A(:, Js) (m x s) on thread-block
+// clusters, for the column ID Z = R_C^{-1} Q_C^T A (Eq. (2.1)) and the stable CUR of Remark 3.
+//
+// The s columns are factored in panels of b.  For a panel [t0, t0+b):
+//   * PANEL (one cluster of CL CTAs; CTA k holds rows [k*mloc, (k+1)*mloc) of the panel
+//     columns in shared memory, column-major).  Column c (global t = t0+c) is one step:
+//       - every CTA holds the dot products of column c with the panel columns j >= c over its
+//         rows >= t, and sends them (and the owner of row t sends row t) to every CTA with
+//         st.async stores that complete on the receiver's mbarrier; each CTA sums the CL
+//         partials in CTA order, so every CTA forms the same values:
+//             D_j = x^T C(:, j),  sigma^2 = D_c,  alpha = C(t, c),  beta = -sign(alpha) sigma,
+//             v = (x - beta e_t)/(alpha - beta),  tau = (beta - alpha)/beta,
+//             w_j = v^T C(:, j) = (D_j - beta C(t, j))/(alpha - beta)       (j > c),
+//             R(t, t0+j) = C(t, j) - tau w_j,  R(t, t) = beta;
+//       - the CTA stores v, updates column c+1, then applies C(:, j) -= tau w_j v to the
+//         columns j > c+1 while forming the next step's dot products in the same pass.
+//     At the end of the panel the cluster forms G = V_p^T V_p (register-tiled partial Grams,
+//     summed across the cluster through distributed shared memory).  With the compact WY
+//     form Q_p = H_t0 .. H_t0+b-1 = I - V T V^T, T^{-1} = S = diag(G)/2 + strictly_upper(G),
+//     so each row of V T^T solves (V T^T)(i, :) S^T = V(i, :) by forward substitution; every
+//     CTA writes V (explicit unit diagonal) and V T^T for its rows.
+//   * TRAIL (two grid-wide GEMMs): W = V^T C(t0:, t0+b:), C(t0:, t0+b:) -= (V T^T) W, which
+//     applies Q_p^T to the columns to the right.
+// R entries above a panel (rows < t0 of its columns) are final when the panel is loaded and
+// are written out from there.
+#include <algorithm>
+
+#include <cooperative_groups.h>
+
+#include "cluster.cuh"
+#include "common.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace skel {
+
+namespace {
+
+constexpr int kQrThreads = 512;
+constexpr int kQrMaxB = 64;
+constexpr int kQrInbox = 3;
+constexpr size_t kQrSmemOptin = 227 * 1024;
+
+template <typename T>
+struct QrPanelParams {
+  T* Cw; int64_t m, ldw;       // working copy of C (m x s, column-major)
+  int s, t0, b, mloc;          // mloc: a multiple of 4
+  T* V; int64_t ldv;           // out: reflectors, unit lower trapezoidal, m x s column-major
+  T* VT;                       // out: V_p T_p^T, m x b column-major (ld = m)
+  double* R; int64_t ldr;      // out: s x s row-major
+  int32_t* fail;
+  int32_t* dev_status;
+};
+
+__host__ __device__ constexpr int qr_b4(int b) { return (b + 3) / 4 * 4; }
+// bytes one receiver takes in for step c: CL partial rows and the pivot row, columns
+// 4*floor(c/4) .. b4-1 of each
+template <typename T>
+__host__ __device__ constexpr uint32_t qr_step_bytes(int CL, int b, int c) {
+  return (uint32_t)(CL + 1) * (uint32_t)(qr_b4(b) - c / 4 * 4) * (uint32_t)sizeof(T);
+}
+
+template <typename T> __device__ __forceinline__ uint32_t qbits32(T v) { return __float_as_uint((float)v); }
+template <typename T> __device__ __forceinline__ uint64_t qbits64(T v) { return (uint64_t)__double_as_longlong((double)v); }
+
+// Send columns g0*4 .. b4-1 of src (shared memory) to dst_local (the same offset in every CTA
+// of the cluster), 16 bytes per st.async; thread `slot` of `nslots` handles (receiver, group)
+// pairs.
+template <typename T>
+__device__ __forceinline__ void qr_send(const T* src, uint32_t dst_local, uint32_t bar_local, int CL,
+                                        int g0, int b4, int slot, int nslots) {
+  const int groups = b4 / 4 - g0;
+  for (int e = slot; e < CL * groups; e += nslots) {
+    const int d = e / groups, g = g0 + e % groups;
+    const uint32_t dst = map_cluster_u32(dst_local + (uint32_t)(g * 4 * sizeof(T)), d);
+    const uint32_t bar = map_cluster_u32(bar_local, d);
+    const T* v = src + 4 * g;
+    if constexpr (sizeof(T) == 4) {
+      st_async_v4_b32(dst, qbits32(v[0]), qbits32(v[1]), qbits32(v[2]), qbits32(v[3]), bar);
+    } else {
+      st_async_v2_b64(dst, qbits64(v[0]), qbits64(v[1]), bar);
+      st_async_v2_b64(dst + 16, qbits64(v[2]), qbits64(v[3]), bar);
+    }
+  }
+}
+
+// The first n (<= 16) of 16 consecutive shared-memory elements into registers (zeros after
+// them): 16-byte loads when aligned and n == 16.
+template <typename T>
+__device__ __forceinline__ void load16(const T* p, bool aligned, int n, T (&v)[16]) {
+  if (aligned && n == 16) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 f = reinterpret_cast<const float4*>(p)[q];
+        v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const double2 f = reinterpret_cast<const double2*>(p)[q];
+        v[2 * q] = f.x; v[2 * q + 1] = f.y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = k < n ? p[k] : T(0);
+  }
+}
+
+// Transposed butterfly reduction of NV per-lane values over the 32 lanes of a warp: halving
+// levels (xor 16, 8, ...) each keep half of the values, so that afterwards lane l holds the
+// warp totals of entries xr_index<NV>(l) + k, k < max(NV/32, 1); remaining levels sum fully.
+template <int NV, typename T>
+__device__ __forceinline__ void xreduce(T (&a)[NV], int lane) {
+#pragma unroll
+  for (int L = 0; L < 5; ++L) {
+    const int m = 16 >> L;
+    const int h = NV >> (L + 1);
+    const bool up = (lane & m) != 0;
+    if (h >= 1) {
+#pragma unroll
+      for (int k = 0; k < (NV >> (L + 1) > 0 ? NV >> (L + 1) : 1); ++k) {
+        const T keep = up ? a[k + h] : a[k];
+        const T send = up ? a[k] : a[k + h];
+        a[k] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+      }
+    } else {
+      a[0] += __shfl_xor_sync(0xffffffffu, a[0], m);
+    }
+  }
+}
+template <int NV>
+__device__ __forceinline__ int xr_index(int lane) {
+  int idx = 0;
+#pragma unroll
+  for (int L = 0; L < 5; ++L) {
+    const int h = NV >> (L + 1);
+    if (h >= 1 && (lane & (16 >> L))) idx += h;
+  }
+  return idx;
+}
+
+constexpr int kQrMaxChunks = 8;       // rows per CTA <= 8 chunks of 512
+
+template <typename T>
+__global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(const QrPanelParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const int CL = (int)cluster.num_blocks();
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+  const int b = p.b, b4 = qr_b4(b), mloc = p.mloc, t0 = p.t0;
+  const int64_t r0 = (int64_t)crank * mloc;
+  const int ml = (int)(p.m - r0 < 0 ? 0 : (p.m - r0 < mloc ? p.m - r0 : mloc));
+
+  __shared__ __align__(16) T part[kQrInbox][16][kQrMaxB];   // partial dot products per sender
+  __shared__ __align__(16) T rowt[kQrInbox][kQrMaxB];       // row t of the panel
+  __shared__ __align__(8) uint64_t qbar[kQrInbox];
+  __shared__ __align__(16) T wloc[kQrMaxB];                 // this CTA's partials for the next step
+  __shared__ __align__(16) T rownext[kQrMaxB];              // row t+1 (owner)
+  __shared__ T wv[kQrMaxB];                                 // tau * w_j of the current step
+  __shared__ T wpart[4][kQrMaxB];                           // per-row-group partial dot products
+  __shared__ int s_timeout, s_stop;
+  T* P = reinterpret_cast<T*>(smem);                        // [b][mloc]
+  T* G = P + (size_t)b * mloc;                              // [b][b]: partial, then summed V^T V
+  T* GT = G + (size_t)b * b;                                // [b][b]: its transpose
+
+  if (*(volatile int32_t*)p.fail) return;
+  if (tid == 0) {
+    for (int k = 0; k < kQrInbox; ++k) mbar_init(smem_u32(&qbar[k]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_timeout = 0;
+    s_stop = 0;
+  }
+  // load the panel (rows past m are zero); rows above the panel hold final R entries
+  for (int j0 = 0; j0 < b; j0 += 8)         // eight independent loads in flight per thread
+    for (int i = tid; i < mloc; i += bd) {
+      T v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        v[u] = (j0 + u < b && i < ml) ? p.Cw[r0 + i + (int64_t)(t0 + j0 + u) * p.ldw] : T(0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < b) {
+          P[(size_t)(j0 + u) * mloc + i] = v[u];
+          if (i < ml && r0 + i < t0) p.R[(r0 + i) * p.ldr + t0 + j0 + u] = (double)v[u];
+        }
+    }
+  const uint32_t part0 = smem_u32(&part[0][0][0]), rowt0 = smem_u32(&rowt[0][0]), bar0 = smem_u32(&qbar[0]);
+  auto part_dst = [&](int k) { return part0 + (uint32_t)(k * sizeof(part[0]) + crank * sizeof(part[0][0])); };
+  auto rowt_dst = [&](int k) { return rowt0 + (uint32_t)(k * sizeof(rowt[0])); };
+  auto bar_at = [&](int k) { return bar0 + (uint32_t)(k * sizeof(uint64_t)); };
+  __syncthreads();
+
+  // step 0's dot products: column 0 with every panel column over rows >= t0
+  for (int j = warp; j < b4; j += nw) {
+    T d = T(0);
+    if (j < b)
+      for (int i = lane; i < ml; i += 32)
+        if (r0 + i >= t0) d = fma(P[i], P[(size_t)j * mloc + i], d);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (lane == 0) wloc[j] = d;
+  }
+  const int owner0 = (int)(t0 / mloc);
+  if (crank == owner0)
+    for (int j = tid; j < b4; j += bd) rownext[j] = j < b ? P[(size_t)j * mloc + (t0 - r0)] : T(0);
+  __syncthreads();
+  if (tid == 0)
+    for (int k = 0; k < kQrInbox && k < b; ++k) mbar_expect_tx(bar_at(k), qr_step_bytes<T>(CL, b, k));
+  cluster.sync();     // barriers initialised and armed everywhere before the first send
+  qr_send<T>(wloc, part_dst(0), bar_at(0), CL, 0, b4, tid, bd / 2);
+  if (crank == owner0) qr_send<T>(rownext, rowt_dst(0), bar_at(0), CL, 0, b4, tid - bd / 2 >= 0 ? tid - bd / 2 : bd, bd / 2);
+
+  bool stopped = false;
+  for (int c = 0; c < b; ++c) {
+    const int64_t t = t0 + c;
+    const int buf = c % kQrInbox;
+    if (!mbar_wait(bar_at(buf), (uint32_t)((c / kQrInbox) & 1), kDefaultWaitNs))
+      if (atomicExch(&s_timeout, 1) == 0) {
+        record_error(p.dev_status, SKEL_ERR_TIMEOUT, (int)t);
+        atomicExch(p.fail, 1);
+      }
+    __syncthreads();
+    if (s_timeout) {
+      stopped = true;
+      break;
+    }
+    if (tid == bd - 1 && c + kQrInbox < b) mbar_expect_tx(bar_at(buf), qr_step_bytes<T>(CL, b, c + kQrInbox));
+    // scalars of the reflector (every thread, same order)
+    T sig2 = T(0);
+    for (int k = 0; k < CL; ++k) sig2 += part[buf][k][c];
+    const T alpha = rowt[buf][c];
+    if (!isfinite(sig2) || sig2 == T(0)) {           // uniform over the cluster
+      if (crank == 0 && tid == 0) {
+        record_error(p.dev_status, isfinite(sig2) ? SKEL_ERR_RANK_DEFICIENT : SKEL_ERR_NONFINITE, (int)t);
+        atomicExch(p.fail, 1);
+      }
+      stopped = true;
+      break;
+    }
+    const T nrm = sqrt(sig2);
+    const T beta = alpha != T(0) ? -copysign(nrm, alpha) : -nrm;
+    const T den = alpha - beta;
+    const T tau = (beta - alpha) / beta;
+    // tau w_j and R(t, :) (threads over panel columns)
+    if (tid < b) {
+      const int j = tid;
+      double rv = 0.0;
+      if (j == c) {
+        rv = (double)beta;
+      } else if (j > c) {
+        T D = T(0);
+        for (int k = 0; k < CL; ++k) D += part[buf][k][j];
+        const T wj = (D - beta * rowt[buf][j]) / den;
+        wv[j] = tau * wj;
+        rv = (double)(rowt[buf][j] - tau * wj);
+      }
+      if (crank == 0) p.R[t * p.ldr + t0 + j] = rv;
+    }
+    __syncthreads();
+    const bool more = c + 1 < b;
+    // reflector v (column c) and the update of column c+1 (x); threads over rows
+    const T twn = more ? wv[c + 1] : T(0);
+    const T rden = T(1) / den;
+    for (int i = tid; i < ml; i += bd) {
+      const int64_t gi = r0 + i;
+      if (gi < t) continue;
+      const T v = gi == t ? T(1) : P[(size_t)c * mloc + i] * rden;
+      P[(size_t)c * mloc + i] = v;
+      if (more) {
+        const T x = fma(-twn, v, P[(size_t)(c + 1) * mloc + i]);
+        P[(size_t)(c + 1) * mloc + i] = x;
+        if (gi == t + 1) rownext[c + 1] = x;
+      }
+    }
+    __syncthreads();
+    if (!more) break;
+    // columns j > c+1: C(:, j) -= tau w_j v; dot products of x with the columns j >= c+1 over
+    // rows > t.  Warp (wr, wc): rows wr*128 .. +127 of every 512-row chunk (16 bytes per lane
+    // per column), columns c+1+wc, c+1+wc+4, ...; eight columns at a time are reduced over
+    // the lanes by a transposed butterfly into wpart[wr][j].  v and x are zero outside their
+    // rows, so the update leaves the other rows unchanged.
+    {
+      constexpr int VN = 16 / (int)sizeof(T);        // elements per 16-byte access
+      constexpr int NV = 4 / VN;                     // accesses per lane per column (4 rows)
+      const int wr = warp & 3, wc = warp >> 2;
+      const int ncol = (b - (c + 1) - wc + 3) / 4;   // columns of this warp
+      for (int q0 = 0; q0 < ncol; q0 += 8) {
+        T pr[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) pr[u] = T(0);
+        for (int i0 = 0; i0 < mloc; i0 += 512) {
+          const int ib = i0 + wr * 128 + 4 * lane;   // this lane's 4 rows
+          if (ib >= mloc) continue;
+          T vr[4], xr[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int64_t gi = r0 + ib + e;
+            const T a = P[(size_t)c * mloc + ib + e], x = P[(size_t)(c + 1) * mloc + ib + e];
+            vr[e] = gi >= t ? a : T(0);
+            xr[e] = gi > t ? x : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u;
+            if (q >= ncol) continue;
+            const int j = c + 1 + wc + 4 * q;
+            T* col = P + (size_t)j * mloc + ib;
+            T y[4];
+#pragma unroll
+            for (int h = 0; h < NV; ++h) {
+              if constexpr (sizeof(T) == 4) {
+                const float4 f = *reinterpret_cast<const float4*>(col);
+                y[0] = f.x; y[1] = f.y; y[2] = f.z; y[3] = f.w;
+              } else {
+                const double2 f = reinterpret_cast<const double2*>(col)[h];
+                y[2 * h] = f.x; y[2 * h + 1] = f.y;
+              }
+            }
+            if (j > c + 1) {
+              const T f = -wv[j];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                y[e] = fma(f, vr[e], y[e]);
+                if (r0 + ib + e == t + 1) rownext[j] = y[e];
+              }
+              if constexpr (sizeof(T) == 4) {
+                *reinterpret_cast<float4*>(col) = make_float4(y[0], y[1], y[2], y[3]);
+              } else {
+                reinterpret_cast<double2*>(col)[0] = make_double2(y[0], y[1]);
+                reinterpret_cast<double2*>(col)[1] = make_double2(y[2], y[3]);
+              }
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) pr[u] = fma(xr[e], y[e], pr[u]);
+          }
+        }
+        xreduce<8>(pr, lane);
+        const int q = q0 + xr_index<8>(lane);
+        if ((lane & 3) == 0 && q < ncol) wpart[wr][c + 1 + wc + 4 * q] = pr[0];
+      }
+    }
+    __syncthreads();
+    if (tid < b4) {
+      const int j = tid;
+      T d = T(0);
+      if (j >= c + 1 && j < b)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) d += wpart[w][j];
+      wloc[j] = d;
+    }
+    if (crank == (int)((t + 1) / mloc) && tid >= b && tid < b4) rownext[tid] = T(0);
+    __syncthreads();
+    const int own = (int)((t + 1) / mloc);
+    const int nb = (c + 1) % kQrInbox;
+    const int g0 = (c + 1) / 4;
+    qr_send<T>(wloc, part_dst(nb), bar_at(nb), CL, g0, b4, tid, bd / 2);
+    if (crank == own) qr_send<T>(rownext, rowt_dst(nb), bar_at(nb), CL, g0, b4, tid - bd / 2 >= 0 ? tid - bd / 2 : bd, bd / 2);
+  }
+  if (stopped && tid == 0) s_stop = 1;
+  __syncthreads();
+  const bool ok = !s_stop;              // uniform over the cluster (timeouts aside)
+  // V_p (explicit unit diagonal, zeros above) back into P and out
+  if (ok)
+    for (int k = 0; k < b; ++k)
+      for (int i = tid; i < mloc; i += bd) {
+        const int64_t gi = r0 + i, tk = t0 + k;
+        const T v = i >= ml ? T(0) : gi > tk ? P[(size_t)k * mloc + i] : (gi == tk ? T(1) : T(0));
+        P[(size_t)k * mloc + i] = v;
+        if (i < ml) p.V[gi + tk * p.ldv] = v;
+      }
+  __syncthreads();
+  // this CTA's V_p^T V_p: warps over TB x TB block pairs (jt <= kt), lanes over rows
+  if (ok) {
+    constexpr int TB = sizeof(T) == 4 ? 8 : 4;
+    const int nbk = (b + TB - 1) / TB;
+    for (int pq = warp; pq < nbk * nbk; pq += nw) {
+      const int jt = pq / nbk, kt = pq % nbk;
+      if (jt > kt) continue;
+      T acc[TB * TB];
+#pragma unroll
+      for (int e = 0; e < TB * TB; ++e) acc[e] = T(0);
+      for (int i = lane; i < mloc; i += 32) {
+        T x[TB], y[TB];
+#pragma unroll
+        for (int a = 0; a < TB; ++a) {
+          x[a] = TB * jt + a < b ? P[(size_t)(TB * jt + a) * mloc + i] : T(0);
+          y[a] = TB * kt + a < b ? P[(size_t)(TB * kt + a) * mloc + i] : T(0);
+        }
+#pragma unroll
+        for (int a = 0; a < TB; ++a)
+#pragma unroll
+          for (int q = 0; q < TB; ++q) acc[a * TB + q] = fma(x[a], y[q], acc[a * TB + q]);
+      }
+      xreduce<TB * TB>(acc, lane);
+      constexpr int per = TB * TB / 32 > 0 ? TB * TB / 32 : 1;
+      const int base = xr_index<TB * TB>(lane);
+      if (TB * TB >= 32 || (lane & (32 / (TB * TB) - 1)) == 0)
+#pragma unroll
+        for (int k = 0; k < per; ++k) {
+          const int e = base + k, a = e / TB, q = e % TB;
+          if (TB * jt + a < b && TB * kt + q < b) G[(TB * jt + a) * b + TB * kt + q] = acc[k];
+        }
+    }
+  }
+  cluster.sync();     // partial Grams complete in every CTA
+  // rows r = crank + CL*q of G: sum the CL partials in CTA order (upper triangle)
+  T gsum[kQrMaxB / 8] = {};
+  if (ok && tid < b)
+#pragma unroll
+    for (int q = 0; q < kQrMaxB / 8; ++q) {
+      const int r = crank + CL * q;
+      if (r < b && tid >= r) {
+        T v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = k < CL ? cluster.map_shared_rank(G, k)[r * b + tid] : T(0);
+        T a = T(0);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) a += v[k];
+        gsum[q] = a;
+      }
+    }
+  cluster.sync();     // every CTA has read the partials
+  if (ok && tid < b)
+#pragma unroll
+    for (int q = 0; q < kQrMaxB / 8; ++q) {
+      const int r = crank + CL * q;
+      if (r < b && tid >= r) G[r * b + tid] = gsum[q];
+    }
+  cluster.sync();     // summed rows in place
+  if (ok) {
+    T g[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + bd * u;
+      const int r = e / b, j = e % b;
+      g[u] = e < b * b && j >= r ? cluster.map_shared_rank(G, r % CL)[e] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + bd * u;
+      if (e < b * b) {
+        const int r = e / b, j = e % b;
+        if (j >= r && r % CL != crank) G[e] = g[u];
+        GT[j * b + r] = g[u];
+      }
+    }
+  }
+  cluster.sync();     // G = V_p^T V_p (upper triangle) and its transpose everywhere
+  if (ok) {
+    // (V T^T)(i, :) S^T = V(i, :) with S = diag(G)/2 + strictly_upper(G) upper triangular:
+    //   (V T^T)(i, j) = (V(i, j) - sum_{k>j} S(j, k) (V T^T)(i, k)) / S(j, j),
+    // back substitution in chunks of 16 columns from the last; a solved chunk is removed from
+    // the earlier columns in place
+    constexpr int CH = 16;
+    const bool al = b % (16 / (int)sizeof(T)) == 0;   // 16-byte aligned rows of G and GT
+    for (int i = tid; i < ml; i += bd) {
+      for (int h = (b - 1) / CH * CH; h >= 0; h -= CH) {
+        T z[CH];
+#pragma unroll
+        for (int k = 0; k < CH; ++k) z[k] = h + k < b ? P[(size_t)(h + k) * mloc + i] : T(0);
+#pragma unroll
+        for (int j = CH - 1; j >= 0; --j) {
+          if (h + j < b) {
+            T col[16];                                       // S(h+k, h+j), k < j; G(h+j, h+j)
+            load16(GT + (size_t)(h + j) * b + h, al, b - h < CH ? b - h : CH, col);
+            z[j] = z[j] * (T(2) / col[j]);
+#pragma unroll
+            for (int k = 0; k < j; ++k) z[k] = fma(-col[k], z[j], z[k]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < CH; ++k)
+          if (h + k < b) p.VT[r0 + i + (int64_t)(h + k) * p.m] = z[k];
+        for (int j = 0; j < h; ++j) {
+          T row[16];                                         // S(j, h+k)
+          load16(G + (size_t)j * b + h, al, b - h < CH ? b - h : CH, row);
+          T y = P[(size_t)j * mloc + i];
+#pragma unroll
+          for (int k = 0; k < CH; ++k)
+            if (h + k < b) y = fma(-row[k], z[k], y);
+          P[(size_t)j * mloc + i] = y;
+        }
+      }
+    }
+  }
+}
+
+struct QrPanelPlan {
+  int CL = 0, b = 0, mloc = 0;
+  size_t smem = 0;
+};
+
+template <typename T>
+size_t qr_panel_smem(int b, int mloc) {
+  return sizeof(T) * ((size_t)b * mloc + 2 * (size_t)b * b);
+}
+
+template <typename T>
+QrPanelPlan plan_qr_panels(int64_t m, int s) {
+  QrPanelPlan pl;
+  static int max_cluster = -1;
+  static size_t budget = 0;
+  if (max_cluster < 0) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, qr_panel_kernel<T>) != cudaSuccess) {
+      cudaGetLastError();
+      return pl;
+    }
+    budget = kQrSmemOptin - fa.sharedSizeBytes - 1024;
+    max_cluster = 8;
+    if (cudaFuncSetAttribute(qr_panel_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+        cudaFuncSetAttribute(qr_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(16);
+      cfg.blockDim = dim3(kQrThreads);
+      cfg.dynamicSmemBytes = budget;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 16;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, qr_panel_kernel<T>, &cfg) == cudaSuccess && nclusters > 0)
+        max_cluster = 16;
+    }
+    cudaGetLastError();
+  }
+  if (s < 1 || m < s) return pl;
+  const int CL = max_cluster;
+  const int64_t mloc = ((m + CL - 1) / CL + 3) / 4 * 4;
+  if (mloc > kQrMaxChunks * 512) return pl;                // keep the row loops short
+  int b = std::min(kQrMaxB, s);
+  while (b >= 8 && qr_panel_smem<T>(b, (int)mloc) > budget) b -= 4;
+  if (b < std::min(8, s) || qr_panel_smem<T>(b, (int)mloc) > budget) return pl;
+  pl.CL = CL;
+  pl.b = b;
+  pl.mloc = (int)mloc;
+  pl.smem = qr_panel_smem<T>(b, (int)mloc);
+  return pl;
+}
+
+// workspace: fail word, Cw (m x s), VT (m x kQrMaxB), W (kQrMaxB x s), split-K scratch
+template <typename T>
+size_t qr_panels_ws(int64_t m, int s) {
+  const bool f64 = sizeof(T) == 8;
+  size_t kws = 0;                     // split-K scratch of W = V_p^T C(t0:, t0+b:), any width
+  for (int ntr = 1; ntr <= s; ++ntr) kws = std::max(kws, gemm_workspace(kQrMaxB, ntr, m, f64));
+  return 256 + align_up(sizeof(T) * (size_t)m * s) + align_up(sizeof(T) * (size_t)m * kQrMaxB) +
+         align_up(sizeof(T) * (size_t)kQrMaxB * s) + kws;
+}
+
+template <typename T>
+skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_t ldc, int s, T* V,
+                            int64_t ldv, double* R, int64_t ldr, void* ws, int32_t* dev_status,
+                            cudaStream_t st) {
+  const bool f64 = sizeof(T) == 8;
+  char* base = static_cast<char*>(ws);
+  int32_t* fail = reinterpret_cast<int32_t*>(base);
+  base += 256;
+  T* Cw = reinterpret_cast<T*>(base);
+  base += align_up(sizeof(T) * (size_t)m * s);
+  T* VT = reinterpret_cast<T*>(base);
+  base += align_up(sizeof(T) * (size_t)m * kQrMaxB);
+  T* Wt = reinterpret_cast<T*>(base);
+  base += align_up(sizeof(T) * (size_t)kQrMaxB * s);
+  void* kws = base;
+  if (cudaMemsetAsync(fail, 0, 4, st) != cudaSuccess) return SKEL_ERR_CUDA;
+  if (cudaMemset2DAsync(R, sizeof(double) * ldr, 0, sizeof(double) * s, s, st) != cudaSuccess) return SKEL_ERR_CUDA;
+  if (cudaMemcpy2DAsync(Cw, sizeof(T) * m, C, sizeof(T) * ldc, sizeof(T) * m, s, cudaMemcpyDeviceToDevice, st) !=
+      cudaSuccess)
+    return SKEL_ERR_CUDA;
+  if (cudaFuncSetAttribute(qr_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem) != cudaSuccess)
+    return SKEL_ERR_CUDA;
+  if (pl.CL > 8 &&
+      cudaFuncSetAttribute(qr_panel_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return SKEL_ERR_CUDA;
+  const skel_dtype dt = f64 ? SKEL_F64 : SKEL_F32;
+  QrPanelParams<T> p{};
+  p.Cw = Cw; p.m = m; p.ldw = m; p.s = s; p.mloc = pl.mloc;
+  p.V = V; p.ldv = ldv; p.VT = VT; p.R = R; p.ldr = ldr; p.fail = fail; p.dev_status = dev_status;
+  for (int t0 = 0; t0 < s; t0 += pl.b) {
+    p.t0 = t0;
+    p.b = std::min(pl.b, s - t0);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(pl.CL);
+    cfg.blockDim = dim3(kQrThreads);
+    cfg.dynamicSmemBytes = qr_panel_smem<T>(p.b, pl.mloc);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = pl.CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, qr_panel_kernel<T>, p) != cudaSuccess) return SKEL_ERR_CUDA;
+    note_launches(1);
+    const int ntr = s - t0 - p.b;
+    if (ntr <= 0) continue;
+    // W = V_p^T C(t0:, t0+b:)  (b x ntr, row-major)
+    GemmArgs g{};
+    g.M = p.b; g.N = ntr; g.K = m - t0;
+    g.L = View{V + t0 + (int64_t)t0 * ldv, ldv, 1}; g.l_dt = dt;      // V_p^T(r, k) = V(t0+k, t0+r)
+    g.B = View{Cw + t0 + (int64_t)(t0 + p.b) * m, 1, m}; g.b_dt = dt;
+    g.out = Wt; g.out_sr = ntr; g.out_sc = 1; g.out_dt = dt;
+    g.alpha = 1.0;
+    g.splitk_ws = kws;
+    if (launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, st) != cudaSuccess) return SKEL_ERR_CUDA;
+    // C(t0:, t0+b:) -= (V_p T_p^T) W
+    GemmArgs h{};
+    h.M = m - t0; h.N = ntr; h.K = p.b;
+    h.L = View{VT + t0, 1, m}; h.l_dt = dt;
+    h.B = View{Wt, ntr, 1}; h.b_dt = dt;
+    h.out = Cw + t0 + (int64_t)(t0 + p.b) * m; h.out_sr = 1; h.out_sc = m; h.out_dt = dt;
+    h.alpha = -1.0;
+    if (launch_gemm(h, f64, LEFT_LOAD, EPI_ACCUM, st) != cudaSuccess) return SKEL_ERR_CUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
+}
+
+}  // namespace
+
+size_t qr_panels_workspace(skel_dtype dt, int64_t m, int32_t s) {
+  if (dt == SKEL_F64) return plan_qr_panels<double>(m, s).b > 0 ? qr_panels_ws<double>(m, s) : 0;
+  return plan_qr_panels<float>(m, s).b > 0 ? qr_panels_ws<float>(m, s) : 0;
+}
+
+skel_status run_qr_panels(skel_dtype dt, const void* C, int64_t m, int64_t ldc, int32_t s, void* V,
+                          int64_t ldv, double* R, int64_t ldr, void* ws, size_t ws_bytes,
+                          int32_t* dev_status, cudaStream_t st) {
+  if (dt == SKEL_F64) {
+    const QrPanelPlan pl = plan_qr_panels<double>(m, s);
+    if (pl.b == 0) return SKEL_ERR_UNSUPPORTED;
+    if (ws_bytes < qr_panels_ws<double>(m, s)) return SKEL_ERR_WORKSPACE;
+    return run_qr_panels_t<double>(pl, (const double*)C, m, ldc, s, (double*)V, ldv, R, ldr, ws, dev_status, st);
+  }
+  const QrPanelPlan pl = plan_qr_panels<float>(m, s);
+  if (pl.b == 0) return SKEL_ERR_UNSUPPORTED;
+  if (ws_bytes < qr_panels_ws<float>(m, s)) return SKEL_ERR_WORKSPACE;
+  return run_qr_panels_t<float>(pl, (const float*)C, m, ldc, s, (float*)V, ldv, R, ldr, ws, dev_status, st);
+}
+
+}  // namespace skel
