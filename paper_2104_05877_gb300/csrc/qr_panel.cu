@@ -109,6 +109,38 @@ __device__ __forceinline__ void load16(const T* p, bool aligned, int n, T (&v)[1
   }
 }
 
+// Four consecutive shared-memory elements (16-byte aligned for FP32, 8-byte for FP64).
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 f = *reinterpret_cast<const float4*>(p);
+    v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+  } else {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void ld2(const T* p, T (&v)[2]) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 f = *reinterpret_cast<const float2*>(p);
+    v[0] = f.x; v[1] = f.y;
+  } else {
+    const double2 f = *reinterpret_cast<const double2*>(p);
+    v[0] = f.x; v[1] = f.y;
+  }
+}
+
 // Transposed butterfly reduction of NV per-lane values over the 32 lanes of a warp: halving
 // levels (xor 16, 8, ...) each keep half of the values, so that afterwards lane l holds the
 // warp totals of entries xr_index<NV>(l) + k, k < max(NV/32, 1); remaining levels sum fully.
@@ -218,16 +250,20 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(const QrPanelPa
   for (int c = 0; c < b; ++c) {
     const int64_t t = t0 + c;
     const int buf = c % kQrInbox;
-    if (!mbar_wait(bar_at(buf), (uint32_t)((c / kQrInbox) & 1), kDefaultWaitNs))
-      if (atomicExch(&s_timeout, 1) == 0) {
+    const uint32_t par = (uint32_t)((c / kQrInbox) & 1);
+    if (warp == 0) {                     // one warp polls; the others wait at the CTA barrier
+      const bool okw = mbar_wait(bar_at(buf), par, kDefaultWaitNs);
+      if (!__all_sync(0xffffffffu, okw) && lane == 0 && atomicExch(&s_timeout, 1) == 0) {
         record_error(p.dev_status, SKEL_ERR_TIMEOUT, (int)t);
         atomicExch(p.fail, 1);
       }
+    }
     __syncthreads();
     if (s_timeout) {
       stopped = true;
       break;
     }
+    if (warp != 0) mbar_try_wait(bar_at(buf), par);   // acquire of the completed phase
     if (tid == bd - 1 && c + kQrInbox < b) mbar_expect_tx(bar_at(buf), qr_step_bytes<T>(CL, b, c + kQrInbox));
     // scalars of the reflector (every thread, same order)
     T sig2 = T(0);
@@ -284,10 +320,9 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(const QrPanelPa
     // the lanes by a transposed butterfly into wpart[wr][j].  v and x are zero outside their
     // rows, so the update leaves the other rows unchanged.
     {
-      constexpr int VN = 16 / (int)sizeof(T);        // elements per 16-byte access
-      constexpr int NV = 4 / VN;                     // accesses per lane per column (4 rows)
       const int wr = warp & 3, wc = warp >> 2;
       const int ncol = (b - (c + 1) - wc + 3) / 4;   // columns of this warp
+      const int trel = (int)(t - r0);                // local index of row t (may be out of range)
       for (int q0 = 0; q0 < ncol; q0 += 8) {
         T pr[8];
 #pragma unroll
@@ -296,46 +331,33 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(const QrPanelPa
           const int ib = i0 + wr * 128 + 4 * lane;   // this lane's 4 rows
           if (ib >= mloc) continue;
           T vr[4], xr[4];
+          ld4(P + c * mloc + ib, vr);
+          ld4(P + (c + 1) * mloc + ib, xr);
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const int64_t gi = r0 + ib + e;
-            const T a = P[(size_t)c * mloc + ib + e], x = P[(size_t)(c + 1) * mloc + ib + e];
-            vr[e] = gi >= t ? a : T(0);
-            xr[e] = gi > t ? x : T(0);
+            if (ib + e < trel) vr[e] = T(0);
+            if (ib + e <= trel) xr[e] = T(0);
           }
+          const int hit = trel + 1 - ib;             // 0..3: this lane holds row t+1
+          int j = c + 1 + wc + 4 * q0;
+          T* col = P + j * mloc + ib;
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            const int q = q0 + u;
-            if (q >= ncol) continue;
-            const int j = c + 1 + wc + 4 * q;
-            T* col = P + (size_t)j * mloc + ib;
-            T y[4];
+            if (q0 + u < ncol) {
+              T y[4];
+              ld4(col, y);
+              if (j > c + 1) {
+                const T f = -wv[j];
 #pragma unroll
-            for (int h = 0; h < NV; ++h) {
-              if constexpr (sizeof(T) == 4) {
-                const float4 f = *reinterpret_cast<const float4*>(col);
-                y[0] = f.x; y[1] = f.y; y[2] = f.z; y[3] = f.w;
-              } else {
-                const double2 f = reinterpret_cast<const double2*>(col)[h];
-                y[2 * h] = f.x; y[2 * h + 1] = f.y;
+                for (int e = 0; e < 4; ++e) y[e] = fma(f, vr[e], y[e]);
+                st4(col, y);
+                if ((unsigned)hit < 4u) rownext[j] = hit == 0 ? y[0] : hit == 1 ? y[1] : hit == 2 ? y[2] : y[3];
               }
+#pragma unroll
+              for (int e = 0; e < 4; ++e) pr[u] = fma(xr[e], y[e], pr[u]);
             }
-            if (j > c + 1) {
-              const T f = -wv[j];
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                y[e] = fma(f, vr[e], y[e]);
-                if (r0 + ib + e == t + 1) rownext[j] = y[e];
-              }
-              if constexpr (sizeof(T) == 4) {
-                *reinterpret_cast<float4*>(col) = make_float4(y[0], y[1], y[2], y[3]);
-              } else {
-                reinterpret_cast<double2*>(col)[0] = make_double2(y[0], y[1]);
-                reinterpret_cast<double2*>(col)[1] = make_double2(y[2], y[3]);
-              }
-            }
-#pragma unroll
-            for (int e = 0; e < 4; ++e) pr[u] = fma(xr[e], y[e], pr[u]);
+            j += 4;
+            col += 4 * mloc;
           }
         }
         xreduce<8>(pr, lane);
@@ -364,16 +386,27 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(const QrPanelPa
   __syncthreads();
   const bool ok = !s_stop;              // uniform over the cluster (timeouts aside)
   // V_p (explicit unit diagonal, zeros above) back into P and out
-  if (ok)
-    for (int k = 0; k < b; ++k)
-      for (int i = tid; i < mloc; i += bd) {
-        const int64_t gi = r0 + i, tk = t0 + k;
-        const T v = i >= ml ? T(0) : gi > tk ? P[(size_t)k * mloc + i] : (gi == tk ? T(1) : T(0));
-        P[(size_t)k * mloc + i] = v;
-        if (i < ml) p.V[gi + tk * p.ldv] = v;
+  if (ok) {
+    const int nq = mloc / 4;
+    for (int e = tid; e < b * nq; e += bd) {
+      const int k = e / nq, ib = 4 * (e % nq);
+      const int kt = (int)(t0 + k - r0);             // local row of the diagonal of column k
+      T v[4];
+      ld4(P + k * mloc + ib, v);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = ib + u;
+        v[u] = i >= ml ? T(0) : i > kt ? v[u] : (i == kt ? T(1) : T(0));
       }
+      st4(P + k * mloc + ib, v);
+      T* vout = p.V + r0 + ib + (int64_t)(t0 + k) * p.ldv;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (ib + u < ml) vout[u] = v[u];
+    }
+  }
   __syncthreads();
-  // this CTA's V_p^T V_p: warps over TB x TB block pairs (jt <= kt), lanes over rows
+  // this CTA's V_p^T V_p: warps over TB x TB block pairs (jt <= kt), lanes over 4-row groups
   if (ok) {
     constexpr int TB = sizeof(T) == 4 ? 8 : 4;
     const int nbk = (b + TB - 1) / TB;
@@ -383,17 +416,21 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(const QrPanelPa
       T acc[TB * TB];
 #pragma unroll
       for (int e = 0; e < TB * TB; ++e) acc[e] = T(0);
-      for (int i = lane; i < mloc; i += 32) {
-        T x[TB], y[TB];
+      for (int ib = 2 * lane; ib < mloc; ib += 64) {   // two rows per lane per pass
+        T x[TB][2], y[TB][2];
 #pragma unroll
         for (int a = 0; a < TB; ++a) {
-          x[a] = TB * jt + a < b ? P[(size_t)(TB * jt + a) * mloc + i] : T(0);
-          y[a] = TB * kt + a < b ? P[(size_t)(TB * kt + a) * mloc + i] : T(0);
+          const int ja = TB * jt + a, ka = TB * kt + a;
+          x[a][0] = x[a][1] = y[a][0] = y[a][1] = T(0);
+          if (ja < b) ld2(P + ja * mloc + ib, x[a]);
+          if (ka < b) ld2(P + ka * mloc + ib, y[a]);
         }
 #pragma unroll
         for (int a = 0; a < TB; ++a)
 #pragma unroll
-          for (int q = 0; q < TB; ++q) acc[a * TB + q] = fma(x[a], y[q], acc[a * TB + q]);
+          for (int q = 0; q < TB; ++q)
+#pragma unroll
+            for (int u = 0; u < 2; ++u) acc[a * TB + q] = fma(x[a][u], y[q][u], acc[a * TB + q]);
       }
       xreduce<TB * TB>(acc, lane);
       constexpr int per = TB * TB / 32 > 0 ? TB * TB / 32 : 1;
