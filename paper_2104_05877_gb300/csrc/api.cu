@@ -230,11 +230,12 @@ skel_status skel_id(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64
     double* R;
     SK_TRY(skeleton_qr(ar, run, m, dtype, A, lda, s, Js, &C, &Q, &R, dev_status, stream));
     void* W = ar.take(esize(dtype) * (size_t)s * n);
-    const int64_t nbw = gemm_num_blocks(s, n);
+    const bool tcw = !f64 && gemm_tc_usable(m, n, s, nullptr, m, A, lda);   // tensor-core W
+    const int64_t nbw = tcw ? gemm_tc_num_partials(m, n, s) : gemm_num_blocks(s, n);
     double* pw = static_cast<double*>(ar.take(sizeof(double) * nbw));
     const int64_t nba = sqnorm_num_blocks(m, n);
     double* pa = static_cast<double*>(ar.take(sizeof(double) * nba));
-    void* kws = ar.take(gemm_workspace(s, n, m, f64));
+    void* kws = ar.take(tcw ? gemm_tc_workspace(m, n, s) : gemm_workspace(s, n, m, f64));
     if (!run) {
       skel_status st;
       if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
@@ -248,7 +249,11 @@ skel_status skel_id(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64
     g.out = W; g.out_sr = n; g.out_sc = 1; g.out_dt = dtype;
     g.alpha = 1.0;
     g.partials = pw;
-    SK_CUDA(launch_gemm(g, f64, LEFT_LOAD, EPI_STORE_SQ, stream));
+    if (tcw)
+      SK_CUDA(launch_gemm_tc_tn(m, n, s, static_cast<const float*>(Q), m, static_cast<const float*>(A), lda,
+                                static_cast<float*>(W), n, pw, kws, dev_status, stream));
+    else
+      SK_CUDA(launch_gemm(g, f64, LEFT_LOAD, EPI_STORE_SQ, stream));
     SK_CUDA(launch_trsm_upper(s, n, R, s, 0, dtype, W, n, Z, ldz, stream));
     if (sq_norms) {
       SK_CUDA(launch_sqnorm(m, n, dtype, A, lda, pa, stream));
@@ -309,7 +314,8 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
     double* pm = static_cast<double*>(ar.take(sizeof(double) * nbm));
     const int64_t nba = sqnorm_num_blocks(m, n);
     double* pa = static_cast<double*>(ar.take(sizeof(double) * nba));
-    void* kws1 = ar.take(gemm_workspace(s, n, m, f64));
+    const bool tcw = !f64 && gemm_tc_usable(m, n, s, nullptr, m, A, lda);   // tensor-core W
+    void* kws1 = ar.take(tcw ? gemm_tc_workspace(m, n, s) : gemm_workspace(s, n, m, f64));
     void* kws2 = ar.take(gemm_workspace(s, s, n, f64));
     if (!run) {
       skel_status st;
@@ -328,7 +334,11 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
     g.B = View{A, 1, lda}; g.b_dt = dtype;
     g.out = W; g.out_sr = n; g.out_sc = 1; g.out_dt = dtype;
     g.alpha = 1.0;
-    SK_CUDA(launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, stream));
+    if (tcw)
+      SK_CUDA(launch_gemm_tc_tn(m, n, s, static_cast<const float*>(Qc), m, static_cast<const float*>(A), lda,
+                                static_cast<float*>(W), n, nullptr, kws1, dev_status, stream));
+    else
+      SK_CUDA(launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, stream));
     GemmArgs h{};
     h.splitk_ws = kws2;
     h.M = s; h.N = s; h.K = n;

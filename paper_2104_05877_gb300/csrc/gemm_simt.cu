@@ -215,15 +215,43 @@ __global__ void reduce_sum_kernel(const double* p, int64_t count, double* out, i
 }
 
 constexpr int SQ_COLS = 8;
-__global__ void sqnorm_kernel(int64_t m, int64_t n, skel_dtype dt, const void* A, int64_t lda,
-                              double* partials) {
+// ||A||_F^2 partials, one per CTA (8 columns, fixed order).  FP32 data: 16-byte loads and
+// squares summed in FP32 over 16 elements, then in FP64 (the FP32 roundings are unbiased and
+// far below what the Gram-identity errors need); FP64 data: plain FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) sqnorm_kernel(int64_t m, int64_t n, const T* A, int64_t lda,
+                                                     double* partials) {
   double v = 0.0;
   const int64_t c0 = (int64_t)blockIdx.x * SQ_COLS;
+  const bool vec = sizeof(T) == 4 && (lda & 3) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
   for (int cc = 0; cc < SQ_COLS; ++cc) {
     const int64_t c = c0 + cc;
     if (c >= n) break;
+    const T* col = A + c * lda;
+    if constexpr (sizeof(T) == 4) {
+      if (vec) {
+        const int64_t m4 = m / 4;
+        const float4* c4 = reinterpret_cast<const float4*>(col);
+        int64_t i = threadIdx.x;
+        for (; i + 3 * 256 < m4; i += 4 * 256) {      // 16 elements per thread per pass
+          float a = 0.f;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 x = c4[i + u * 256];
+            a = fmaf(x.x, x.x, a); a = fmaf(x.y, x.y, a); a = fmaf(x.z, x.z, a); a = fmaf(x.w, x.w, a);
+          }
+          v += (double)a;
+        }
+        for (; i < m4; i += 256) {
+          const float4 x = c4[i];
+          v += (double)(x.x * x.x + x.y * x.y) + (double)(x.z * x.z + x.w * x.w);
+        }
+        for (int64_t r = 4 * m4 + threadIdx.x; r < m; r += 256) v += (double)col[r] * col[r];
+        continue;
+      }
+    }
     for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
-      const double x = load_as<double>(A, i + c * lda, dt);
+      const double x = (double)col[i];
       v += x * x;
     }
   }
@@ -314,7 +342,10 @@ int64_t sqnorm_num_blocks(int64_t m, int64_t n) { return (n + SQ_COLS - 1) / SQ_
 cudaError_t launch_sqnorm(int64_t m, int64_t n, skel_dtype dt, const void* A, int64_t lda,
                           double* partials, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  sqnorm_kernel<<<(unsigned)sqnorm_num_blocks(m, n), 256, 0, st>>>(m, n, dt, A, lda, partials);
+  if (dt == SKEL_F64)
+    sqnorm_kernel<double><<<(unsigned)sqnorm_num_blocks(m, n), 256, 0, st>>>(m, n, (const double*)A, lda, partials);
+  else
+    sqnorm_kernel<float><<<(unsigned)sqnorm_num_blocks(m, n), 256, 0, st>>>(m, n, (const float*)A, lda, partials);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -106,6 +106,15 @@ size_t qr_panels_workspace(skel_dtype dt, int64_t m, int32_t s);
 skel_status run_qr_panels(skel_dtype dt, const void* C, int64_t m, int64_t ldc, int32_t s, void* V,
                           int64_t ldv, double* R, int64_t ldr, void* ws, size_t ws_bytes,
                           int32_t* dev_status, cudaStream_t st);
+// W = Q^T A (s x n row-major FP32) on the tensor cores, 3xTF32 (FP32-level accuracy), for FP32
+// Q (m x s) and A (m x n) column-major; sq_partials (optional) receives gemm_tc_num_partials
+// partial sums of W^2 in a fixed order.
+bool gemm_tc_usable(int64_t m, int64_t n, int32_t s, const void* Q, int64_t ldq, const void* A, int64_t lda);
+size_t gemm_tc_workspace(int64_t m, int64_t n, int32_t s);
+int64_t gemm_tc_num_partials(int64_t m, int64_t n, int32_t s);
+cudaError_t launch_gemm_tc_tn(int64_t m, int64_t n, int32_t s, const float* Q, int64_t ldq, const float* A,
+                              int64_t lda, float* W, int64_t ldw, double* sq_partials, void* ws,
+                              int32_t* dev_status, cudaStream_t st);
 size_t qr_workspace(skel_dtype dt, int64_t m, int32_t s);
 skel_status run_qr(skel_dtype dt, const void* C, int64_t m, int64_t ldc, int32_t s, void* Q,
                    int64_t ldq, double* R, int64_t ldr, void* ws, size_t ws_bytes,
