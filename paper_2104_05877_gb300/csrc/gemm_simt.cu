@@ -39,6 +39,32 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmArgs a) {
   const bool b_kcontig = (a.B.sr == 1);
   const int64_t kz0 = (int64_t)blockIdx.z * a.kchunk;
   const int64_t kz1 = kz0 + a.kchunk < a.K ? kz0 + a.kchunk : a.K;
+  // Loaded operands: the next K-tile is fetched into registers while the current one is used
+  // (one tile of global-load latency hidden per step); the Gaussian left operand is generated
+  // straight into shared memory.
+  constexpr int LPT = BM * BK / NT, BPT = BK * BN / NT;   // elements per thread: 4, 8
+  T lreg[LPT], breg[BPT];
+  auto fetch = [&](int64_t kb) {
+    if (LEFT != LEFT_GAUSSIAN) {
+#pragma unroll
+      for (int q = 0; q < LPT; ++q) {
+        const int e = q * NT + tid;
+        int r, k;
+        if (l_kcontig) { r = e / BK; k = e % BK; } else { r = e % BM; k = e / BM; }
+        const int64_t gr = r0 + r, gk = kb + k;
+        lreg[q] = (gr < a.M && gk < kz1) ? load_as<T>(a.L.p, gr * a.L.sr + gk * a.L.sc, a.l_dt) : T(0);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < BPT; ++q) {
+      const int e = q * NT + tid;
+      int k, c;
+      if (b_kcontig) { k = e % BK; c = e / BK; } else { c = e % BN; k = e / BN; }
+      const int64_t gk = kb + k, gc = c0 + c;
+      breg[q] = (gk < kz1 && gc < a.N) ? load_as<T>(a.B.p, gk * a.B.sr + gc * a.B.sc, a.b_dt) : T(0);
+    }
+  };
+  if (kz0 < kz1) fetch(kz0);
   for (int64_t kb = kz0; kb < kz1; kb += BK) {
     // ---- left tile (BM x BK) ----
     if (LEFT == LEFT_GAUSSIAN) {
@@ -61,24 +87,23 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmArgs a) {
       for (int q = 0; q < 4; ++q) Ls[4 * k4 + q][r] = (gk + q < a.K) ? g[q] : T(0);
     } else {
 #pragma unroll
-      for (int e0 = 0; e0 < BM * BK; e0 += NT) {
-        const int e = e0 + tid;
+      for (int q = 0; q < LPT; ++q) {
+        const int e = q * NT + tid;
         int r, k;
         if (l_kcontig) { r = e / BK; k = e % BK; } else { r = e % BM; k = e / BM; }
-        const int64_t gr = r0 + r, gk = kb + k;
-        Ls[k][r] = (gr < a.M && gk < a.K) ? load_as<T>(a.L.p, gr * a.L.sr + gk * a.L.sc, a.l_dt) : T(0);
+        Ls[k][r] = lreg[q];
       }
     }
     // ---- right tile (BK x BN) ----
 #pragma unroll
-    for (int e0 = 0; e0 < BK * BN; e0 += NT) {
-      const int e = e0 + tid;
+    for (int q = 0; q < BPT; ++q) {
+      const int e = q * NT + tid;
       int k, c;
       if (b_kcontig) { k = e % BK; c = e / BK; } else { c = e % BN; k = e / BN; }
-      const int64_t gk = kb + k, gc = c0 + c;
-      Bs[k][c] = (gk < a.K && gc < a.N) ? load_as<T>(a.B.p, gk * a.B.sr + gc * a.B.sc, a.b_dt) : T(0);
+      Bs[k][c] = breg[q];
     }
     __syncthreads();
+    if (kb + BK < kz1) fetch(kb + BK);
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
       T lv[TM], bv[TN];

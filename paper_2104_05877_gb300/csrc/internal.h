@@ -100,11 +100,12 @@ skel_status run_cpqr(skel_dtype dt, const void* X, int64_t l, int64_t n, int64_t
 // Householder QR of a tall m x s column-major C (qr.cu): explicit Q (m x s col-major, same
 // dtype, ld = ldq) and R (s x s row-major FP64).
 // Panel-blocked Householder QR on thread-block clusters: reflectors V (m x s, unit lower
-// trapezoidal, column-major) and R (s x s row-major FP64).  qr_panels_workspace returns 0 and
+// trapezoidal, column-major), R (s x s row-major FP64) and, when Q is given, the explicit
+// Q_C = H_0 .. H_{s-1} [I; 0] (m x s column-major).  qr_panels_workspace returns 0 and
 // run_qr_panels SKEL_ERR_UNSUPPORTED when a panel of at least 8 columns does not fit a cluster.
 size_t qr_panels_workspace(skel_dtype dt, int64_t m, int32_t s);
 skel_status run_qr_panels(skel_dtype dt, const void* C, int64_t m, int64_t ldc, int32_t s, void* V,
-                          int64_t ldv, double* R, int64_t ldr, void* ws, size_t ws_bytes,
+                          int64_t ldv, double* R, int64_t ldr, void* Q, int64_t ldq, void* ws, size_t ws_bytes,
                           int32_t* dev_status, cudaStream_t st);
 // W = Q^T A (s x n row-major FP32) on the tensor cores, 3xTF32 (FP32-level accuracy), for FP32
 // Q (m x s) and A (m x n) column-major; sq_partials (optional) receives gemm_tc_num_partials

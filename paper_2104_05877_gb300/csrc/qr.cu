@@ -224,10 +224,9 @@ skel_status launch_qr_t(const T* C, int64_t m, int64_t ldc, int s, T* Q, int64_t
   void* kws2 = extra;
   p.V = V; p.ldv = m;
 
-  if (pws > 0) {
-    const skel_status r = run_qr_panels(dt, C, m, ldc, s, V, m, R, ldr, base, pws, dev_status, st);
-    if (r != SKEL_OK) return r;
-  } else {
+  if (pws > 0)        // factorisation and Q_C from the panels' WY blocks
+    return run_qr_panels(dt, C, m, ldc, s, V, m, R, ldr, Q, ldq, base, pws, dev_status, st);
+  {
   if (cudaMemsetAsync(base, 0, pl.comm_bytes + pl.acc_bytes, st) != cudaSuccess) return SKEL_ERR_CUDA;
   if (cudaFuncSetAttribute((const void*)qr_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)pl.smem) != cudaSuccess)

@@ -48,6 +48,7 @@ struct QrPanelParams {
   int s, t0, b, mloc;          // mloc: a multiple of 4
   T* V; int64_t ldv;           // out: reflectors, unit lower trapezoidal, m x s column-major
   T* VT;                       // out: V_p T_p^T, m x b column-major (ld = m)
+  T* VTN;                      // out: V_p T_p in columns t0.. of an m x s column-major array
   double* R; int64_t ldr;      // out: s x s row-major
   int32_t* fail;
   int32_t* dev_status;
@@ -523,6 +524,41 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(const QrPanelPa
         }
       }
     }
+    // V T for the formation of Q: (V T)(i, :) S = V(i, :), forward substitution in chunks of 16
+    // columns from the first, on V reloaded from its global copy (P now holds V T^T's
+    // intermediate values)
+    __syncthreads();
+    for (int k = 0; k < b; ++k)
+      for (int i = tid; i < ml; i += bd) P[(size_t)k * mloc + i] = p.V[r0 + i + (int64_t)(t0 + k) * p.ldv];
+    __syncthreads();
+    for (int i = tid; i < ml; i += bd) {
+      for (int h = 0; h < b; h += CH) {
+        T z[CH];
+#pragma unroll
+        for (int k = 0; k < CH; ++k) z[k] = h + k < b ? P[(size_t)(h + k) * mloc + i] : T(0);
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          if (h + j < b) {
+            T row[16];                                       // S(h+j, h+k), k > j; G(h+j, h+j)
+            load16(G + (size_t)(h + j) * b + h, al, b - h < CH ? b - h : CH, row);
+            z[j] = z[j] * (T(2) / row[j]);
+#pragma unroll
+            for (int k = j + 1; k < CH; ++k) z[k] = fma(-row[k], z[j], z[k]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < CH; ++k)
+          if (h + k < b) p.VTN[r0 + i + (int64_t)(t0 + h + k) * p.m] = z[k];
+        for (int j = h + CH; j < b; ++j) {
+          T col[16];                                         // S(h+k, j)
+          load16(GT + (size_t)j * b + h, al, CH, col);
+          T y = P[(size_t)j * mloc + i];
+#pragma unroll
+          for (int k = 0; k < CH; ++k) y = fma(-col[k], z[k], y);
+          P[(size_t)j * mloc + i] = y;
+        }
+      }
+    }
   }
 }
 
@@ -582,25 +618,35 @@ QrPanelPlan plan_qr_panels(int64_t m, int s) {
   return pl;
 }
 
-// workspace: fail word, Cw (m x s), VT (m x kQrMaxB), W (kQrMaxB x s), split-K scratch
+// workspace: fail word, Cw (m x s), VTN (m x s), VT (m x kQrMaxB), W (kQrMaxB x s), split-K scratch
 template <typename T>
 size_t qr_panels_ws(int64_t m, int s) {
   const bool f64 = sizeof(T) == 8;
   size_t kws = 0;                     // split-K scratch of W = V_p^T C(t0:, t0+b:), any width
   for (int ntr = 1; ntr <= s; ++ntr) kws = std::max(kws, gemm_workspace(kQrMaxB, ntr, m, f64));
-  return 256 + align_up(sizeof(T) * (size_t)m * s) + align_up(sizeof(T) * (size_t)m * kQrMaxB) +
+  return 256 + 2 * align_up(sizeof(T) * (size_t)m * s) + align_up(sizeof(T) * (size_t)m * kQrMaxB) +
          align_up(sizeof(T) * (size_t)kQrMaxB * s) + kws;
+}
+
+// Q = [I_s; 0] before the panels are applied (m x s, leading dimension ldq)
+template <typename T>
+__global__ void eye_kernel(int64_t m, int s, T* Q, int64_t ldq) {
+  for (int c = blockIdx.y; c < s; c += gridDim.y)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+      Q[i + (int64_t)c * ldq] = i == c ? T(1) : T(0);
 }
 
 template <typename T>
 skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_t ldc, int s, T* V,
-                            int64_t ldv, double* R, int64_t ldr, void* ws, int32_t* dev_status,
-                            cudaStream_t st) {
+                            int64_t ldv, double* R, int64_t ldr, T* Q, int64_t ldq, void* ws,
+                            int32_t* dev_status, cudaStream_t st) {
   const bool f64 = sizeof(T) == 8;
   char* base = static_cast<char*>(ws);
   int32_t* fail = reinterpret_cast<int32_t*>(base);
   base += 256;
   T* Cw = reinterpret_cast<T*>(base);
+  base += align_up(sizeof(T) * (size_t)m * s);
+  T* VTN = reinterpret_cast<T*>(base);
   base += align_up(sizeof(T) * (size_t)m * s);
   T* VT = reinterpret_cast<T*>(base);
   base += align_up(sizeof(T) * (size_t)m * kQrMaxB);
@@ -620,7 +666,7 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
   const skel_dtype dt = f64 ? SKEL_F64 : SKEL_F32;
   QrPanelParams<T> p{};
   p.Cw = Cw; p.m = m; p.ldw = m; p.s = s; p.mloc = pl.mloc;
-  p.V = V; p.ldv = ldv; p.VT = VT; p.R = R; p.ldr = ldr; p.fail = fail; p.dev_status = dev_status;
+  p.V = V; p.ldv = ldv; p.VT = VT; p.VTN = VTN; p.R = R; p.ldr = ldr; p.fail = fail; p.dev_status = dev_status;
   for (int t0 = 0; t0 < s; t0 += pl.b) {
     p.t0 = t0;
     p.b = std::min(pl.b, s - t0);
@@ -658,6 +704,31 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
     h.alpha = -1.0;
     if (launch_gemm(h, f64, LEFT_LOAD, EPI_ACCUM, st) != cudaSuccess) return SKEL_ERR_CUDA;
   }
+  if (Q == nullptr) return cudaGetLastError() == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
+  // Q_C = Q_0 Q_1 .. [I; 0] with Q_p = I - V_p T_p V_p^T, applied from the last panel:
+  // Y = V_p^T E(t0:, :), E(t0:, :) -= (V_p T_p) Y
+  eye_kernel<T><<<dim3((unsigned)std::min<int64_t>((m + 255) / 256, 64), (unsigned)std::min(s, 1024)), 256, 0, st>>>(
+      m, s, Q, ldq);
+  note_launches(1);
+  const int np = (s + pl.b - 1) / pl.b;
+  for (int pi = np - 1; pi >= 0; --pi) {
+    const int t0 = pi * pl.b, b = std::min(pl.b, s - t0);
+    GemmArgs g{};
+    g.M = b; g.N = s; g.K = m - t0;
+    g.L = View{V + t0 + (int64_t)t0 * ldv, ldv, 1}; g.l_dt = dt;       // V_p^T(r, k) = V(t0+k, t0+r)
+    g.B = View{Q + t0, 1, ldq}; g.b_dt = dt;
+    g.out = Wt; g.out_sr = s; g.out_sc = 1; g.out_dt = dt;
+    g.alpha = 1.0;
+    g.splitk_ws = kws;
+    if (launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, st) != cudaSuccess) return SKEL_ERR_CUDA;
+    GemmArgs h{};
+    h.M = m - t0; h.N = s; h.K = b;
+    h.L = View{VTN + t0 + (int64_t)t0 * m, 1, m}; h.l_dt = dt;
+    h.B = View{Wt, s, 1}; h.b_dt = dt;
+    h.out = Q + t0; h.out_sr = 1; h.out_sc = ldq; h.out_dt = dt;
+    h.alpha = -1.0;
+    if (launch_gemm(h, f64, LEFT_LOAD, EPI_ACCUM, st) != cudaSuccess) return SKEL_ERR_CUDA;
+  }
   return cudaGetLastError() == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
 }
 
@@ -669,18 +740,20 @@ size_t qr_panels_workspace(skel_dtype dt, int64_t m, int32_t s) {
 }
 
 skel_status run_qr_panels(skel_dtype dt, const void* C, int64_t m, int64_t ldc, int32_t s, void* V,
-                          int64_t ldv, double* R, int64_t ldr, void* ws, size_t ws_bytes,
+                          int64_t ldv, double* R, int64_t ldr, void* Q, int64_t ldq, void* ws, size_t ws_bytes,
                           int32_t* dev_status, cudaStream_t st) {
   if (dt == SKEL_F64) {
     const QrPanelPlan pl = plan_qr_panels<double>(m, s);
     if (pl.b == 0) return SKEL_ERR_UNSUPPORTED;
     if (ws_bytes < qr_panels_ws<double>(m, s)) return SKEL_ERR_WORKSPACE;
-    return run_qr_panels_t<double>(pl, (const double*)C, m, ldc, s, (double*)V, ldv, R, ldr, ws, dev_status, st);
+    return run_qr_panels_t<double>(pl, (const double*)C, m, ldc, s, (double*)V, ldv, R, ldr, (double*)Q, ldq, ws,
+                                   dev_status, st);
   }
   const QrPanelPlan pl = plan_qr_panels<float>(m, s);
   if (pl.b == 0) return SKEL_ERR_UNSUPPORTED;
   if (ws_bytes < qr_panels_ws<float>(m, s)) return SKEL_ERR_WORKSPACE;
-  return run_qr_panels_t<float>(pl, (const float*)C, m, ldc, s, (float*)V, ldv, R, ldr, ws, dev_status, st);
+  return run_qr_panels_t<float>(pl, (const float*)C, m, ldc, s, (float*)V, ldv, R, ldr, (float*)Q, ldq, ws,
+                                 dev_status, st);
 }
 
 }  // namespace skel
