@@ -38,7 +38,7 @@ M_DIM = N_DIM = 8192
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--k", type=int, default=256)
@@ -70,7 +70,8 @@ def make_A(device, seed):
 
 # ------------------------------------------------------------------------------------------
 class ClockSampler:
-    """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks/throttle reasons sampled every 50 ms while running (entering waits,
+    up to 3 s, for the first sample so that the sampler is live when the timed region starts)."""
 
     def __init__(self, index):
         self.index = index
@@ -83,10 +84,13 @@ class ClockSampler:
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
                  "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
                  "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
@@ -120,6 +124,14 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# kernels timed with CUDA events during the timed region
+TIMED_KERNELS = ("sketch_tc", "gemm_tc", "lupp_panel", "lupp_trail", "qr_panel", "trsm", "gemm_qr",
+                 "gemm_cur", "gemm_eta_h", "gemm_eta_sq", "gemm_simt")
+# DRAM bytes (read + write) per launch from one ncu capture of the current kernel at this
+# workload (None where no capture of the current code exists)
+TRAFFIC_PER_LAUNCH = {"sketch_tc": 488.7e6, "gemm_tc": 332.4e6, "lupp_panel": 3.09e6, "qr_panel": 2.22e6}
 
 
 def load_peaks():
@@ -253,6 +265,19 @@ def run_ours(args, rank, world):
             out = step(all_evs[i])
         t_end.record()
         torch.cuda.synchronize()
+    # second timed region, same steps, with CUDA events around the hot kernels' launches (kept
+    # apart so that the recorded events do not touch the headline numbers)
+    skel.kernel_timing(True)
+    kev = [mk() for _ in range(args.steps)]
+    k_begin, k_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k_begin.record()
+    for i in range(args.steps):
+        step(kev[i])
+    k_end.record()
+    torch.cuda.synchronize()
+    ktimes = {nm: skel.kernel_time(nm) for nm in TIMED_KERNELS}
+    skel.kernel_timing(False)
+    k_total_ms = k_begin.elapsed_time(k_end)
     if world > 1:
         torch.distributed.barrier()
     launches = skel.launch_count() - launches0
@@ -281,28 +306,47 @@ def run_ours(args, rank, world):
     sketch_tflops = 2.0 * l * m * n / (per["sketch"] * 1e-3) / 1e12
     fp32_alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12        # TFLOP/s, FFMA
     fp64_alu_peak = 1.25                                  # TFLOP/s, nominal FP64
+    # Algorithmic work of each timed kernel over one step (bound, work, peak, unit):
+    #   sketch_tc   X = Gamma A: 2 l m n TF32 flop (or 4 m n bytes of A if HBM-bound)
+    #   gemm_tc     W = Q^T A in the ID and the CUR: 2 x 3 (2 k m n) TF32 flop (3 products)
+    #   lupp_panel  s greedy steps over n (LUPP on X) and over m (row LUPP on C): the panel
+    #               rank-1 updates, sum over panels of b^2 cols (mul + sub)
+    #   qr_panel    three Householder QRs (C twice, R^T once): ~4 rows k^2 flop each
+    #               (factorisation + the panel WY factors)
+    #   trsm        Z = R_C^{-1} W (k^2 n) and four k x k solves (CUR, eta): FP64
+    #   gemm_eta_h  R R^T, 2 k^2 n FP64 flop
+    b_pan = 64
+    lupp_flops = sum(min(b_pan, k - t0) ** 2 for t0 in range(0, k, b_pan)) * (n + m)
     models = {
-        "sketch": ("tensor", 2.0 * l * m * n / 1e12, tf32_peak, "TFLOP/s") if 2.0 * l * m * n / (tf32_peak * 1e12)
-        > a_bytes / (hbm * 1e9) else ("hbm", a_bytes / 1e9, hbm, "GB/s"),
-        "lupp": ("hbm", 4.0 * l * n * 2 / 1e9, hbm, "GB/s"),
-        "rows": ("hbm", (8.0 * m * k + 4.0 * m * k) / 1e9, hbm, "GB/s"),
-        "id": ("alu", (2.0 * k * m * n + 4.0 * m * k * k) / 1e12, fp32_alu_peak, "TFLOP/s"),
-        "cur": ("alu", (2.0 * k * m * n + 2.0 * k * k * n + 8.0 * m * k * k) / 1e12, fp32_alu_peak, "TFLOP/s"),
-        "eta": ("alu", 2.0 * k * k * n / 1e12, fp64_alu_peak, "TFLOP/s"),
+        "sketch_tc": ("tensor", 2.0 * l * m * n / 1e12, tf32_peak, "TFLOP/s")
+        if 2.0 * l * m * n / (tf32_peak * 1e12) > a_bytes / (hbm * 1e9) else ("hbm", a_bytes / 1e9, hbm, "GB/s"),
+        "gemm_tc": ("tensor", 2 * 3 * 2.0 * k * m * n / 1e12, tf32_peak, "TFLOP/s"),
+        "lupp_panel": ("alu", lupp_flops / 1e12, fp32_alu_peak, "TFLOP/s"),
+        "qr_panel": ("alu", (4.0 * m * k * k * 2 + 4.0 * n * k * k) / 1e12, fp32_alu_peak, "TFLOP/s"),
+        "trsm": ("alu", (1.0 * k * k * n + 4.0 * k ** 3) / 1e12, fp64_alu_peak, "TFLOP/s"),
+        "gemm_eta_h": ("alu", 2.0 * k * k * n / 1e12, fp64_alu_peak, "TFLOP/s"),
     }
-    dom = max(per, key=per.get)
-    bound, work, peak, unit = models[dom]
-    achieved = work / (per[dom] * 1e-3)
-    roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": f"{peak_src} MEASURED_PEAKS.json" if peak_src == "measured" else "fallback",
-                "work_per_launch": work}
     kernels = {}
-    for nm in names:
-        b, w, pk, u = models[nm]
-        a = w / (per[nm] * 1e-3)
-        kernels[nm] = {"ms": per[nm], "share": per[nm] / sum(per.values()), "bound": b, "achieved": a,
-                       "peak": pk, "unit": u, "frac": a / pk}
+    for nm, (tot, cnt) in ktimes.items():
+        if cnt == 0:
+            continue
+        ent = {"ms_per_step": tot / args.steps, "launches_per_step": cnt / args.steps,
+               "avg_us": 1e3 * tot / cnt, "share_of_step": tot / k_total_ms}
+        if nm in models:
+            b, w, pk, u = models[nm]
+            a = w / (tot / args.steps * 1e-3)          # work per step / device time per step
+            ent.update({"bound": b, "achieved": a, "peak": pk, "unit": u, "frac": a / pk})
+        kernels[nm] = ent
+    modeled = [nm for nm in kernels if "bound" in kernels[nm]]
+    dom = max(modeled, key=lambda nm: kernels[nm]["ms_per_step"])
+    kd = kernels[dom]
+    roofline = {"kernel": dom, "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
+                "unit": kd["unit"], "frac": kd["frac"], "traffic": TRAFFIC_PER_LAUNCH.get(dom),
+                "peak_source": f"{peak_src} MEASURED_PEAKS.json" if peak_src == "measured" else "fallback",
+                "launches_per_step": kd["launches_per_step"], "avg_launch_us": kd["avg_us"],
+                "timing": "CUDA events on the launching stream around every launch, in a second timed "
+                          "region of the same steps"}
+    calls = {nm: {"ms": per[nm], "share": per[nm] / sum(per.values())} for nm in names}
 
     # FP64 plain-GPU form of the skeleton stage on the same matrix
     fp64 = None
@@ -379,7 +423,7 @@ def run_ours(args, rank, world):
         "oracle_rel_id_error": oracle_err,
         "id_error_ratio_vs_oracle": (rel_id / oracle_err) if oracle_err else None,
         "fp64_gpu": fp64,
-        "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu,
+        "roofline": roofline, "kernels": kernels, "calls": calls, "cpu_baseline": cpu,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(4 * m * n),
                 "d2h_bytes_per_step": int(8 * k)},
         "gpu_launches": launches, "clocks": clk.summary(),

@@ -248,6 +248,21 @@ skel_status skel_debug_curand_philox(uint64_t seed, int64_t nseq, int per_seq, u
 skel_status skel_debug_grid_timeout(int grid, uint64_t wait_ns, void* ws, size_t* ws_bytes,
                                     int32_t* dev_status, cudaStream_t stream);
 
+/*
+ * skel_debug_kernel_timing -- measurement aid (no counterpart in the paper): enable != 0 makes
+ * the launch sites of the hot kernels record a CUDA event on the launching stream before and
+ * after each launch, from now on; enable == 0 stops recording.  Either call discards earlier
+ * records.  Costs one branch per launch while disabled (the default).
+ * skel_debug_kernel_time -- total device time (ms) and launch count of the recorded launches
+ * of one kernel since the last skel_debug_kernel_timing call; waits for those launches.
+ * Names: "sketch_tc", "gemm_tc" (W = Q^T A), "lupp_panel", "lupp_trail", "qr_panel", "trsm",
+ * "gemm_qr" (QR trailing updates and Q formation), "gemm_cur" (W Q_R), "gemm_eta_h" (R R^T),
+ * "gemm_eta_sq" (eta's squarings), "gemm_simt" (other SIMT GEMMs).
+ * Host-side state, process-wide; not for concurrent use from several threads.
+ */
+skel_status skel_debug_kernel_timing(int enable);
+skel_status skel_debug_kernel_time(const char* kernel, double* total_ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

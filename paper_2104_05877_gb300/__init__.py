@@ -65,6 +65,11 @@ def lib():
     L.skel_status_string.restype = ctypes.c_char_p
     L.skel_version.restype = ctypes.c_int
     L.skel_launch_count.restype = ctypes.c_uint64
+    L.skel_debug_kernel_timing.argtypes = [ctypes.c_int]
+    L.skel_debug_kernel_timing.restype = ctypes.c_int
+    L.skel_debug_kernel_time.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int64)]
+    L.skel_debug_kernel_time.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -241,6 +246,24 @@ def cur(A, Js, Is=None, status=None):
 def launch_count():
     """Kernels launched by libskel in this process so far."""
     return int(lib().skel_launch_count())
+
+
+def kernel_timing(enable):
+    """Start (True) or stop (False) per-kernel CUDA-event timing of the hot kernels; either
+    discards earlier records."""
+    rc = lib().skel_debug_kernel_timing(1 if enable else 0)
+    if rc != 0:
+        raise SkelError(rc, "skel_debug_kernel_timing")
+
+
+def kernel_time(name):
+    """(total ms, launches) of the recorded launches of one kernel ("sketch_tc", "gemm_tc",
+    "lupp_panel", "lupp_trail", "qr_panel", "gemm_simt", "trsm")."""
+    ms, n = ctypes.c_double(0.0), ctypes.c_int64(0)
+    rc = lib().skel_debug_kernel_time(name.encode(), ctypes.byref(ms), ctypes.byref(n))
+    if rc != 0:
+        raise SkelError(rc, "skel_debug_kernel_time")
+    return ms.value, n.value
 
 
 def error(A, Js=None, Z=None, Is=None, U=None, Rf=None, status=None):

@@ -347,6 +347,7 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
     h.out = M; h.out_sr = s; h.out_sc = 1; h.out_dt = SKEL_F64;
     h.alpha = 1.0;
     h.partials = pm;
+    h.timer = "gemm_cur";
     SK_CUDA(launch_gemm(h, f64, LEFT_LOAD, EPI_STORE_SQ, stream));
     if (sq_norms) {
       SK_CUDA(launch_sqnorm(m, n, dtype, A, lda, pa, stream));
@@ -438,6 +439,7 @@ skel_status skel_error(int64_t m, int64_t n, skel_dtype dtype, const void* A, in
       g.B = View{Rf, 1, ldrf}; g.b_dt = rf_dtype;
       g.out = H; g.out_sr = s; g.out_sc = 1; g.out_dt = SKEL_F64;
       g.alpha = 1.0;
+      g.timer = "gemm_eta_h";
       SK_CUDA(launch_gemm(g, true, LEFT_LOAD, EPI_STORE, stream));
       SK_CUDA(launch_gather_cols_rowmajor_f64(s, rf_dtype, Rf, ldrf, Js, R1, s, stream));
       SK_CUDA(launch_trsm_upper(s, s, R1, s, 0, SKEL_F64, H, s, M1, s, stream));

@@ -200,7 +200,10 @@ cudaError_t launch_t(const GemmArgs& a0, int nz, cudaStream_t st) {
   GemmArgs a = a0;
   const unsigned gx = (unsigned)((a.N + BN - 1) / BN), gy = (unsigned)((a.M + BM - 1) / BM);
   if (nz > 1 && (EPI == EPI_STORE || EPI == EPI_STORE_SQ) && LEFT == LEFT_LOAD) {
-    gemm_kernel<T, LEFT, EPI, true><<<dim3(gx, gy, nz), NT, 0, st>>>(a);
+    {
+      KernelTimer kt(a.timer ? a.timer : "gemm_simt", st);
+      gemm_kernel<T, LEFT, EPI, true><<<dim3(gx, gy, nz), NT, 0, st>>>(a);
+    }
     // STORE_SQ writes one partial per reduce CTA, so it keeps the tile count as its grid
     const int64_t total = a.M * a.N;
     const unsigned rg = EPI == EPI_STORE_SQ ? gx * gy
@@ -209,7 +212,10 @@ cudaError_t launch_t(const GemmArgs& a0, int nz, cudaStream_t st) {
     note_launches(2);
   } else {
     a.kchunk = a.K;
-    gemm_kernel<T, LEFT, EPI, false><<<dim3(gx, gy, 1), NT, 0, st>>>(a);
+    {
+      KernelTimer kt(a.timer ? a.timer : "gemm_simt", st);
+      gemm_kernel<T, LEFT, EPI, false><<<dim3(gx, gy, 1), NT, 0, st>>>(a);
+    }
     note_launches(1);
   }
   return cudaGetLastError();
@@ -326,13 +332,16 @@ __global__ void fill_kernel(double* d, int64_t count, double v) {
 
 int64_t gemm_num_blocks(int64_t M, int64_t N) { return ((N + BN - 1) / BN) * ((M + BM - 1) / BM); }
 
-// K-split factor: enough CTAs for two waves, chunks of at least 256 along K.
+// K-split factor: enough CTAs for two waves, chunks of at least 256 along K (16 when the
+// output has fewer tiles than an eighth of the SMs, e.g. an FP64 s x s x s product, whose
+// few tiles would otherwise leave most of the machine's FP64 units idle).
 static int splitk_factor(int64_t M, int64_t N, int64_t K) {
   const int64_t tiles = gemm_num_blocks(M, N);
   const int64_t want = 2 * (int64_t)device_sm_count();
-  if (tiles >= want || K < 512) return 1;
+  const int64_t min_chunk = tiles * 8 < device_sm_count() ? 16 : 256;
+  if (tiles >= want || K < 2 * min_chunk) return 1;
   int64_t z = (want + tiles - 1) / tiles;
-  z = std::min<int64_t>(z, K / 256);
+  z = std::min<int64_t>(z, K / min_chunk);
   z = std::min<int64_t>(z, 64);
   return (int)std::max<int64_t>(z, 1);
 }

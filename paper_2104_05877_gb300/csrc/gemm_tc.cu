@@ -393,7 +393,10 @@ cudaError_t launch_gemm_tc_tn(int64_t m, int64_t n, int32_t s, const float* Q, i
   cudaError_t e = cudaFuncSetAttribute(gemm_tn_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GT_SMEM);
   if (e != cudaSuccess) return e;
   dim3 grid(pl.mblocks, pl.jtiles, pl.P);
-  gemm_tn_tf32x3_kernel<<<grid, GT_THREADS, GT_SMEM, st>>>(tA, tQh, tQl, p);
+  {
+    KernelTimer kt("gemm_tc", st);
+    gemm_tn_tf32x3_kernel<<<grid, GT_THREADS, GT_SMEM, st>>>(tA, tQh, tQl, p);
+  }
   note_launches(1);
   e = cudaGetLastError();
   if (e != cudaSuccess || p.direct) return e;

@@ -38,6 +38,7 @@ struct GemmArgs {
   int32_t* dev_status;
   void* splitk_ws;                 // optional: gemm_workspace() bytes enable a K-split
   int64_t kchunk;                  // set by launch_gemm
+  const char* timer = nullptr;     // kernel-timing name ("gemm_simt" when null)
 };
 int64_t gemm_num_blocks(int64_t M, int64_t N);
 // Scratch for splitting K across CTAs when the M x N tiles cannot fill the GPU (STORE and
@@ -148,6 +149,22 @@ cudaError_t launch_sketch_tc(int64_t m, int64_t n, const float* A, int64_t lda, 
 int device_sm_count();
 // Number of kernels this library has launched in the process (diagnostics).
 void note_launches(int n);
+
+// CUDA events around one kernel launch (scope), recorded only while skel_debug_kernel_timing
+// is enabled: construct immediately before the launch, destroy immediately after it.
+class KernelTimer {
+ public:
+  KernelTimer(const char* name, cudaStream_t st);
+  ~KernelTimer();
+  KernelTimer(const KernelTimer&) = delete;
+  KernelTimer& operator=(const KernelTimer&) = delete;
+
+ private:
+  const char* name_;
+  cudaStream_t st_;
+  void* start_ = nullptr;
+  void* stop_ = nullptr;
+};
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 }  // namespace skel

@@ -630,12 +630,18 @@ skel_status run_panel_t(const PanelPlan& pl, const T* X, int64_t n, int64_t ldx,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, lupp_panel_kernel<T>, p) != cudaSuccess) return SKEL_ERR_CUDA;
+    {
+      KernelTimer kt("lupp_panel", st);
+      if (cudaLaunchKernelEx(&cfg, lupp_panel_kernel<T>, p) != cudaSuccess) return SKEL_ERR_CUDA;
+    }
     note_launches(1);
     const int rows = s - t0 - p.b;
     if (rows > 0) {
       dim3 grid((unsigned)((n + kTrailThreads - 1) / kTrailThreads), (unsigned)((rows + kTrailRows - 1) / kTrailRows));
-      lupp_trail_kernel<T><<<grid, kTrailThreads, 0, st>>>(p);
+      {
+        KernelTimer kt("lupp_trail", st);
+        lupp_trail_kernel<T><<<grid, kTrailThreads, 0, st>>>(p);
+      }
       note_launches(1);
     }
   }

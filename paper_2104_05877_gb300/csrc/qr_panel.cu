@@ -682,7 +682,10 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, qr_panel_kernel<T>, p) != cudaSuccess) return SKEL_ERR_CUDA;
+    {
+      KernelTimer kt("qr_panel", st);
+      if (cudaLaunchKernelEx(&cfg, qr_panel_kernel<T>, p) != cudaSuccess) return SKEL_ERR_CUDA;
+    }
     note_launches(1);
     const int ntr = s - t0 - p.b;
     if (ntr <= 0) continue;
@@ -694,6 +697,7 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
     g.out = Wt; g.out_sr = ntr; g.out_sc = 1; g.out_dt = dt;
     g.alpha = 1.0;
     g.splitk_ws = kws;
+    g.timer = "gemm_qr";
     if (launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, st) != cudaSuccess) return SKEL_ERR_CUDA;
     // C(t0:, t0+b:) -= (V_p T_p^T) W
     GemmArgs h{};
@@ -702,6 +706,7 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
     h.B = View{Wt, ntr, 1}; h.b_dt = dt;
     h.out = Cw + t0 + (int64_t)(t0 + p.b) * m; h.out_sr = 1; h.out_sc = m; h.out_dt = dt;
     h.alpha = -1.0;
+    h.timer = "gemm_qr";
     if (launch_gemm(h, f64, LEFT_LOAD, EPI_ACCUM, st) != cudaSuccess) return SKEL_ERR_CUDA;
   }
   if (Q == nullptr) return cudaGetLastError() == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
@@ -720,6 +725,7 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
     g.out = Wt; g.out_sr = s; g.out_sc = 1; g.out_dt = dt;
     g.alpha = 1.0;
     g.splitk_ws = kws;
+    g.timer = "gemm_qr";
     if (launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, st) != cudaSuccess) return SKEL_ERR_CUDA;
     GemmArgs h{};
     h.M = m - t0; h.N = s; h.K = b;
@@ -727,6 +733,7 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
     h.B = View{Wt, s, 1}; h.b_dt = dt;
     h.out = Q + t0; h.out_sr = 1; h.out_sc = ldq; h.out_dt = dt;
     h.alpha = -1.0;
+    h.timer = "gemm_qr";
     if (launch_gemm(h, f64, LEFT_LOAD, EPI_ACCUM, st) != cudaSuccess) return SKEL_ERR_CUDA;
   }
   return cudaGetLastError() == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;

@@ -310,7 +310,10 @@ cudaError_t launch_sketch_tc(int64_t m, int64_t n, const float* A, int64_t lda, 
   cudaError_t e = cudaFuncSetAttribute(sketch_tc_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
   if (e != cudaSuccess) return e;
   dim3 grid(pl.lblocks, pl.jtiles, pl.P);
-  sketch_tc_tf32_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(tmap, p);
+  {
+    KernelTimer kt("sketch_tc", st);
+    sketch_tc_tf32_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(tmap, p);
+  }
   note_launches(1);
   e = cudaGetLastError();
   if (e != cudaSuccess || p.direct) return e;

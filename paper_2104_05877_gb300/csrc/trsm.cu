@@ -54,6 +54,121 @@ __global__ void __launch_bounds__(256) trsm_upper_kernel(int s, int64_t N, int n
   }
 }
 
+// Few right-hand sides (N small against the GPU): a CTA solves nbs = 4 columns.  The 32 x 32
+// diagonal blocks of R are inverted first (warp k inverts block k by back substitution on the
+// identity), so that the back substitution over the s/32 row blocks is, per block, one
+// off-diagonal update (each warp owns 4 rows, its lanes split the dot products, a transposed
+// shuffle reduction combines them) and one 32 x 32 upper triangular product.  Sequential depth
+// s/32 instead of s.
+constexpr int TS_NB = 4;
+constexpr int TS_THREADS = 256;
+
+template <int NV>
+__device__ __forceinline__ void xreduce_d(double (&a)[NV], int lane) {
+#pragma unroll
+  for (int L = 0; L < 5; ++L) {
+    const int m = 16 >> L;
+    const int h = NV >> (L + 1);
+    const bool up = (lane & m) != 0;
+    if (h >= 1) {
+#pragma unroll
+      for (int k = 0; k < (NV >> (L + 1) > 0 ? NV >> (L + 1) : 1); ++k) {
+        const double keep = up ? a[k + h] : a[k];
+        const double send = up ? a[k] : a[k + h];
+        a[k] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+      }
+    } else {
+      a[0] += __shfl_xor_sync(0xffffffffu, a[0], m);
+    }
+  }
+}
+
+template <typename TB>
+__global__ void __launch_bounds__(TS_THREADS) trsm_small_kernel(int s, int64_t N, const double* R, int64_t ldr,
+                                                                int unit, const TB* B, int64_t ldb, double* Y,
+                                                                int64_t ldy) {
+  extern __shared__ double sm[];
+  const int nbk = (s + 31) / 32;
+  double* Dinv = sm;                                   // [nbk][32][32], row-major blocks
+  double* Ys = Dinv + (size_t)nbk * 1024;              // [s][TS_NB]
+  double* Tmp = Ys + (size_t)s * TS_NB;                // [32][TS_NB]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t c0 = (int64_t)blockIdx.x * TS_NB;
+  const int nc = (int)std::min<int64_t>(TS_NB, N - c0);
+  for (int e = tid; e < s * TS_NB; e += TS_THREADS) {
+    const int r = e / TS_NB, cc = e % TS_NB;
+    Ys[e] = cc < nc ? (double)B[(int64_t)r * ldb + c0 + cc] : 0.0;
+  }
+  // inverse of each diagonal block: lane j solves R_kk x = e_j (rows beyond s: identity)
+  for (int k = warp; k < nbk; k += TS_THREADS / 32) {
+    const int b0 = 32 * k;
+    double* D = Dinv + (size_t)k * 1024;
+    const int j = lane;
+    for (int i = 31; i >= 0; --i) {
+      double x;
+      if (b0 + i >= s) {
+        x = i == j ? 1.0 : 0.0;
+      } else {
+        double acc = i == j ? 1.0 : 0.0;
+        for (int q = i + 1; q < 32 && b0 + q < s; ++q) acc -= __ldg(R + (int64_t)(b0 + i) * ldr + b0 + q) * D[q * 32 + j];
+        x = unit ? acc : acc / __ldg(R + (int64_t)(b0 + i) * ldr + b0 + i);
+      }
+      D[i * 32 + j] = x;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int k = nbk - 1; k >= 0; --k) {
+    const int b0 = 32 * k;
+    const int qlo = b0 + 32;
+    if (qlo < s) {
+      // Y_k -= R(k-block, qlo:) Y(qlo:, :): warp w owns rows b0+4w .. +3; lanes split q
+      double a[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) a[e] = 0.0;
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        const int r = b0 + 4 * warp + rr;
+        if (r >= s) continue;
+        const double* Rr = R + (int64_t)r * ldr;
+        for (int q = qlo + lane; q < s; q += 32) {
+          const double rq = __ldg(Rr + q);
+#pragma unroll
+          for (int cc = 0; cc < TS_NB; ++cc) a[rr * TS_NB + cc] = fma(rq, Ys[q * TS_NB + cc], a[rr * TS_NB + cc]);
+        }
+      }
+      xreduce_d<16>(a, lane);
+      if ((lane & 1) == 0) {
+        int idx = 0;
+#pragma unroll
+        for (int L = 0; L < 4; ++L)
+          if (lane & (16 >> L)) idx += 16 >> (L + 1);
+        const int r = b0 + 4 * warp + idx / TS_NB, cc = idx % TS_NB;
+        if (r < s) Ys[r * TS_NB + cc] -= a[0];
+      }
+      __syncthreads();
+    }
+    // Y_k = inv(R_kk) Y_k
+    if (tid < 32 * TS_NB) {
+      const int i = tid / TS_NB, cc = tid % TS_NB;
+      const double* D = Dinv + (size_t)k * 1024 + i * 32;
+      double acc = 0.0;
+      for (int q = i; q < 32 && b0 + q < s; ++q) acc = fma(D[q], Ys[(b0 + q) * TS_NB + cc], acc);
+      Tmp[tid] = acc;
+    }
+    __syncthreads();
+    if (tid < 32 * TS_NB) {
+      const int i = tid / TS_NB;
+      if (b0 + i < s) Ys[(b0 + i) * TS_NB + tid % TS_NB] = Tmp[tid];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < s * TS_NB; e += TS_THREADS) {
+    const int r = e / TS_NB, cc = e % TS_NB;
+    if (cc < nc) Y[(int64_t)r * ldy + c0 + cc] = Ys[e];
+  }
+}
+
 // Normalise an s x s matrix by its trace: M /= tr(M); logs[slot] = log(tr(M)).
 __global__ void trace_normalize_kernel(int s, double* M, int64_t ldm, double* logs, int slot) {
   double v = 0.0;
@@ -115,12 +230,30 @@ cudaError_t launch_trsm_upper(int32_t s, int64_t N, const double* R, int64_t ldr
                               cudaStream_t st) {
   if (N <= 0 || s <= 0) return cudaSuccess;
   const int sms = device_sm_count();
+  const size_t small_smem = sizeof(double) * ((size_t)((s + 31) / 32) * 1024 + (size_t)s * TS_NB + 32 * TS_NB);
+  if ((N + TS_NB - 1) / TS_NB <= 4 * sms && small_smem <= 200 * 1024) {
+    KernelTimer kt("trsm", st);
+    cudaError_t e;
+    const unsigned grid = (unsigned)((N + TS_NB - 1) / TS_NB);
+    if (b_dt == SKEL_F64) {
+      e = cudaFuncSetAttribute(trsm_small_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem);
+      if (e != cudaSuccess) return e;
+      trsm_small_kernel<double><<<grid, TS_THREADS, small_smem, st>>>(s, N, R, ldr, unit_diag, (const double*)B, ldb, Y, ldy);
+    } else {
+      e = cudaFuncSetAttribute(trsm_small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem);
+      if (e != cudaSuccess) return e;
+      trsm_small_kernel<float><<<grid, TS_THREADS, small_smem, st>>>(s, N, R, ldr, unit_diag, (const float*)B, ldb, Y, ldy);
+    }
+    note_launches(1);
+    return cudaGetLastError();
+  }
   int nb = 32;
   while (nb > 2 && (N + nb - 1) / nb < 2 * sms) nb >>= 1;
   while ((size_t)s * nb * sizeof(double) > 160 * 1024 && nb > 1) nb >>= 1;
   const size_t smem = (size_t)s * nb * sizeof(double);
   const unsigned grid = (unsigned)((N + nb - 1) / nb);
   cudaError_t e;
+  KernelTimer kt("trsm", st);
   if (b_dt == SKEL_F64) {
     e = cudaFuncSetAttribute(trsm_upper_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -163,6 +296,7 @@ cudaError_t launch_power_sqrt_lmax(int32_t s, const double* Min, int64_t ldm, do
     a.out = nxt; a.out_sr = s; a.out_sc = 1; a.out_dt = SKEL_F64;
     a.alpha = 1.0;
     a.splitk_ws = gemm_workspace(s, s, s, true) ? kws : nullptr;
+    a.timer = "gemm_eta_sq";
     e = launch_gemm(a, true, LEFT_LOAD, EPI_STORE, st);
     if (e != cudaSuccess) return e;
     trace_normalize_kernel<<<1, 1024, 0, st>>>(s, nxt, s, logs, i);
