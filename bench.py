@@ -127,11 +127,11 @@ class ClockSampler:
 
 
 # kernels timed with CUDA events during the timed region
-TIMED_KERNELS = ("sketch_tc", "gemm_tc", "lupp_panel", "lupp_trail", "qr_panel", "trsm", "gemm_qr",
+TIMED_KERNELS = ("sketch_tc", "gemm_tc", "lupp_panel", "lupp_trail", "qr_panel", "qr_wy", "trsm", "gemm_qr",
                  "gemm_cur", "gemm_eta_h", "gemm_eta_sq", "gemm_simt")
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel at this
 # workload (None where no capture of the current code exists)
-TRAFFIC_PER_LAUNCH = {"sketch_tc": 488.7e6, "gemm_tc": 332.4e6, "lupp_panel": 3.09e6, "qr_panel": 2.22e6}
+TRAFFIC_PER_LAUNCH = {"sketch_tc": 488.7e6, "gemm_tc": 332.4e6, "lupp_panel": 3.09e6}
 
 
 def load_peaks():
@@ -311,8 +311,8 @@ def run_ours(args, rank, world):
     #   gemm_tc     W = Q^T A in the ID and the CUR: 2 x 3 (2 k m n) TF32 flop (3 products)
     #   lupp_panel  s greedy steps over n (LUPP on X) and over m (row LUPP on C): the panel
     #               rank-1 updates, sum over panels of b^2 cols (mul + sub)
-    #   qr_panel    three Householder QRs (C twice, R^T once): ~4 rows k^2 flop each
-    #               (factorisation + the panel WY factors)
+    #   qr_panel    the column steps of three Householder QRs (C twice, R^T once): 2 rows k^2
+    #               flop each (the panels' WY factors are formed by other kernels)
     #   trsm        Z = R_C^{-1} W (k^2 n) and four k x k solves (CUR, eta): FP64
     #   gemm_eta_h  R R^T, 2 k^2 n FP64 flop
     b_pan = 64
@@ -322,7 +322,7 @@ def run_ours(args, rank, world):
         if 2.0 * l * m * n / (tf32_peak * 1e12) > a_bytes / (hbm * 1e9) else ("hbm", a_bytes / 1e9, hbm, "GB/s"),
         "gemm_tc": ("tensor", 2 * 3 * 2.0 * k * m * n / 1e12, tf32_peak, "TFLOP/s"),
         "lupp_panel": ("alu", lupp_flops / 1e12, fp32_alu_peak, "TFLOP/s"),
-        "qr_panel": ("alu", (4.0 * m * k * k * 2 + 4.0 * n * k * k) / 1e12, fp32_alu_peak, "TFLOP/s"),
+        "qr_panel": ("alu", 2.0 * (2 * m + n) * k * k / 1e12, fp32_alu_peak, "TFLOP/s"),
         "trsm": ("alu", (1.0 * k * k * n + 4.0 * k ** 3) / 1e12, fp64_alu_peak, "TFLOP/s"),
         "gemm_eta_h": ("alu", 2.0 * k * k * n / 1e12, fp64_alu_peak, "TFLOP/s"),
     }

@@ -255,7 +255,7 @@ skel_status skel_debug_grid_timeout(int grid, uint64_t wait_ns, void* ws, size_t
  * records.  Costs one branch per launch while disabled (the default).
  * skel_debug_kernel_time -- total device time (ms) and launch count of the recorded launches
  * of one kernel since the last skel_debug_kernel_timing call; waits for those launches.
- * Names: "sketch_tc", "gemm_tc" (W = Q^T A), "lupp_panel", "lupp_trail", "qr_panel", "trsm",
+ * Names: "sketch_tc", "gemm_tc" (W = Q^T A), "lupp_panel", "lupp_trail", "qr_panel", "qr_wy", "trsm",
  * "gemm_qr" (QR trailing updates and Q formation), "gemm_cur" (W Q_R), "gemm_eta_h" (R R^T),
  * "gemm_eta_sq" (eta's squarings), "gemm_simt" (other SIMT GEMMs).
  * Host-side state, process-wide; not for concurrent use from several threads.

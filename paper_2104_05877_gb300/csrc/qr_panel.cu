@@ -14,13 +14,13 @@
 //             R(t, t0+j) = C(t, j) - tau w_j,  R(t, t) = beta;
 //       - the CTA stores v, updates column c+1, then applies C(:, j) -= tau w_j v to the
 //         columns j > c+1 while forming the next step's dot products in the same pass.
-//     At the end of the panel the cluster forms G = V_p^T V_p (register-tiled partial Grams,
-//     summed across the cluster through distributed shared memory).  With the compact WY
-//     form Q_p = H_t0 .. H_t0+b-1 = I - V T V^T, T^{-1} = S = diag(G)/2 + strictly_upper(G),
-//     so each row of V T^T solves (V T^T)(i, :) S^T = V(i, :) by forward substitution; every
-//     CTA writes V (explicit unit diagonal) and V T^T for its rows.
+//     The panel kernel ends by writing V (explicit unit diagonal, zeros above).
+//   * WY (grid-wide): G = V_p^T V_p by a split-K GEMM; with the compact WY form
+//     Q_p = H_t0 .. H_t0+b-1 = I - V T V^T, T^{-1} = S = diag(G)/2 + strictly_upper(G), so
+//     qr_wy_kernel forms V T^T and V T one row per thread by substitution with S.
 //   * TRAIL (two grid-wide GEMMs): W = V^T C(t0:, t0+b:), C(t0:, t0+b:) -= (V T^T) W, which
-//     applies Q_p^T to the columns to the right.
+//     applies Q_p^T to the columns to the right.  After the last panel, Q_C = Q_0 .. [I; 0]
+//     from the panels' V T blocks, two GEMMs per panel.
 // R entries above a panel (rows < t0 of its columns) are final when the panel is loaded and
 // are written out from there.
 #include <algorithm>
@@ -131,17 +131,6 @@ __device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void ld2(const T* p, T (&v)[2]) {
-  if constexpr (sizeof(T) == 4) {
-    const float2 f = *reinterpret_cast<const float2*>(p);
-    v[0] = f.x; v[1] = f.y;
-  } else {
-    const double2 f = *reinterpret_cast<const double2*>(p);
-    v[0] = f.x; v[1] = f.y;
-  }
-}
-
 // Transposed butterfly reduction of NV per-lane values over the 32 lanes of a warp: halving
 // levels (xor 16, 8, ...) each keep half of the values, so that afterwards lane l holds the
 // warp totals of entries xr_index<NV>(l) + k, k < max(NV/32, 1); remaining levels sum fully.
@@ -197,8 +186,6 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(const QrPanelPa
   __shared__ T wpart[4][kQrMaxB];                           // per-row-group partial dot products
   __shared__ int s_timeout, s_stop;
   T* P = reinterpret_cast<T*>(smem);                        // [b][mloc]
-  T* G = P + (size_t)b * mloc;                              // [b][b]: partial, then summed V^T V
-  T* GT = G + (size_t)b * b;                                // [b][b]: its transpose
 
   if (*(volatile int32_t*)p.fail) return;
   if (tid == 0) {
@@ -407,157 +394,107 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(const QrPanelPa
     }
   }
   __syncthreads();
-  // this CTA's V_p^T V_p: warps over TB x TB block pairs (jt <= kt), lanes over 4-row groups
-  if (ok) {
-    constexpr int TB = sizeof(T) == 4 ? 8 : 4;
-    const int nbk = (b + TB - 1) / TB;
-    for (int pq = warp; pq < nbk * nbk; pq += nw) {
-      const int jt = pq / nbk, kt = pq % nbk;
-      if (jt > kt) continue;
-      T acc[TB * TB];
+  cluster.sync();     // no CTA leaves while its peers may still address its shared memory
+}
+
+// V_p T_p^T (trailing update) and V_p T_p (formation of Q) for the rows t0.. of a panel, from
+// V and G = V_p^T V_p (b x b, row-major), one row per thread across the grid.  With
+// S = T_p^{-1} = diag(G)/2 + strictly_upper(G) (upper triangular):
+//   (V T^T)(i, :) S^T = V(i, :):  z_j = (V_j - sum_{k>j} S(j, k) z_k) / S(j, j), j descending;
+//   (V T)(i, :)   S   = V(i, :):  z_j = (V_j - sum_{k<j} z_k S(k, j)) / S(j, j), j ascending;
+// in chunks of 16 columns held in registers, a solved chunk removed from the row in place.
+constexpr int kWyRows = 128;
+
+template <typename T>
+size_t qr_wy_smem(int b) {
+  return sizeof(T) * (2 * (size_t)b * b + kQrMaxB + 2 * (size_t)kWyRows * (b + 1));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kWyRows) qr_wy_kernel(const T* V, int64_t ldv, int64_t m, int t0, int b,
+                                                        const T* Gin, T* VT, T* VTN) {
+  extern __shared__ __align__(16) unsigned char wsm[];
+  constexpr int CH = 16;
+  T* G = reinterpret_cast<T*>(wsm);                 // [b][b], upper triangle used
+  T* GT = G + (size_t)b * b;                        // [b][b], GT[j][k] = G(k, j) for k <= j
+  T* dinv = GT + (size_t)b * b;                     // [b]: 1 / S(j, j)
+  T* rowA = dinv + kQrMaxB;                         // [kWyRows][b + 1]
+  T* rowB = rowA + (size_t)kWyRows * (b + 1);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < b * b; e += kWyRows) {
+    const int r = e / b, j = e % b;
+    const T g = j >= r ? Gin[e] : T(0);
+    G[e] = g;
+    GT[j * b + r] = g;
+  }
+  for (int j = tid; j < b; j += kWyRows) dinv[j] = T(2) / Gin[j * b + j];
+  const int64_t i0 = t0 + (int64_t)blockIdx.x * kWyRows;
+  for (int k = 0; k < b; ++k) {
+    const int64_t i = i0 + tid;
+    const T v = i < m ? V[i + (int64_t)(t0 + k) * ldv] : T(0);
+    rowA[tid * (b + 1) + k] = v;
+    rowB[tid * (b + 1) + k] = v;
+  }
+  __syncthreads();
+  const int64_t i = i0 + tid;
+  if (i >= m) return;
+  const bool al = b % (16 / (int)sizeof(T)) == 0;  // 16-byte aligned rows of G and GT
+  T* ra = rowA + tid * (b + 1);
+  for (int h = (b - 1) / CH * CH; h >= 0; h -= CH) {
+    const int nh = b - h < CH ? b - h : CH;
+    T z[CH];
 #pragma unroll
-      for (int e = 0; e < TB * TB; ++e) acc[e] = T(0);
-      for (int ib = 2 * lane; ib < mloc; ib += 64) {   // two rows per lane per pass
-        T x[TB][2], y[TB][2];
+    for (int k = 0; k < CH; ++k) z[k] = k < nh ? ra[h + k] : T(0);
 #pragma unroll
-        for (int a = 0; a < TB; ++a) {
-          const int ja = TB * jt + a, ka = TB * kt + a;
-          x[a][0] = x[a][1] = y[a][0] = y[a][1] = T(0);
-          if (ja < b) ld2(P + ja * mloc + ib, x[a]);
-          if (ka < b) ld2(P + ka * mloc + ib, y[a]);
-        }
+    for (int j = CH - 1; j >= 0; --j) {
+      if (j < nh) {
+        T col[16];                                   // S(h+k, h+j) = G(h+k, h+j), k < j
+        load16(GT + (size_t)(h + j) * b + h, al, nh, col);
+        z[j] *= dinv[h + j];
 #pragma unroll
-        for (int a = 0; a < TB; ++a)
-#pragma unroll
-          for (int q = 0; q < TB; ++q)
-#pragma unroll
-            for (int u = 0; u < 2; ++u) acc[a * TB + q] = fma(x[a][u], y[q][u], acc[a * TB + q]);
+        for (int k = 0; k < j; ++k) z[k] = fma(-col[k], z[j], z[k]);
       }
-      xreduce<TB * TB>(acc, lane);
-      constexpr int per = TB * TB / 32 > 0 ? TB * TB / 32 : 1;
-      const int base = xr_index<TB * TB>(lane);
-      if (TB * TB >= 32 || (lane & (32 / (TB * TB) - 1)) == 0)
+    }
 #pragma unroll
-        for (int k = 0; k < per; ++k) {
-          const int e = base + k, a = e / TB, q = e % TB;
-          if (TB * jt + a < b && TB * kt + q < b) G[(TB * jt + a) * b + TB * kt + q] = acc[k];
-        }
+    for (int k = 0; k < CH; ++k)
+      if (k < nh) VT[i + (int64_t)(h + k) * m] = z[k];
+    for (int j = 0; j < h; ++j) {
+      T row[16];                                     // S(j, h+k) = G(j, h+k)
+      load16(G + (size_t)j * b + h, al, nh, row);
+      T y = ra[j];
+#pragma unroll
+      for (int k = 0; k < CH; ++k)
+        if (k < nh) y = fma(-row[k], z[k], y);
+      ra[j] = y;
     }
   }
-  cluster.sync();     // partial Grams complete in every CTA
-  // rows r = crank + CL*q of G: sum the CL partials in CTA order (upper triangle)
-  T gsum[kQrMaxB / 8] = {};
-  if (ok && tid < b)
+  T* rb = rowB + tid * (b + 1);
+  for (int h = 0; h < b; h += CH) {
+    const int nh = b - h < CH ? b - h : CH;
+    T z[CH];
 #pragma unroll
-    for (int q = 0; q < kQrMaxB / 8; ++q) {
-      const int r = crank + CL * q;
-      if (r < b && tid >= r) {
-        T v[16];
+    for (int k = 0; k < CH; ++k) z[k] = k < nh ? rb[h + k] : T(0);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] = k < CL ? cluster.map_shared_rank(G, k)[r * b + tid] : T(0);
-        T a = T(0);
+    for (int j = 0; j < CH; ++j) {
+      if (j < nh) {
+        T row[16];                                   // S(h+j, h+k) = G(h+j, h+k), k > j
+        load16(G + (size_t)(h + j) * b + h, al, nh, row);
+        z[j] *= dinv[h + j];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) a += v[k];
-        gsum[q] = a;
+        for (int k = j + 1; k < CH; ++k)
+          if (k < nh) z[k] = fma(-row[k], z[j], z[k]);
       }
     }
-  cluster.sync();     // every CTA has read the partials
-  if (ok && tid < b)
 #pragma unroll
-    for (int q = 0; q < kQrMaxB / 8; ++q) {
-      const int r = crank + CL * q;
-      if (r < b && tid >= r) G[r * b + tid] = gsum[q];
-    }
-  cluster.sync();     // summed rows in place
-  if (ok) {
-    T g[8];
+    for (int k = 0; k < CH; ++k)
+      if (k < nh) VTN[i + (int64_t)(t0 + h + k) * m] = z[k];
+    for (int j = h + CH; j < b; ++j) {
+      T col[16];                                     // S(h+k, j) = GT(j, h+k)
+      load16(GT + (size_t)j * b + h, al, CH, col);
+      T y = rb[j];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = tid + bd * u;
-      const int r = e / b, j = e % b;
-      g[u] = e < b * b && j >= r ? cluster.map_shared_rank(G, r % CL)[e] : T(0);
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = tid + bd * u;
-      if (e < b * b) {
-        const int r = e / b, j = e % b;
-        if (j >= r && r % CL != crank) G[e] = g[u];
-        GT[j * b + r] = g[u];
-      }
-    }
-  }
-  cluster.sync();     // G = V_p^T V_p (upper triangle) and its transpose everywhere
-  if (ok) {
-    // (V T^T)(i, :) S^T = V(i, :) with S = diag(G)/2 + strictly_upper(G) upper triangular:
-    //   (V T^T)(i, j) = (V(i, j) - sum_{k>j} S(j, k) (V T^T)(i, k)) / S(j, j),
-    // back substitution in chunks of 16 columns from the last; a solved chunk is removed from
-    // the earlier columns in place
-    constexpr int CH = 16;
-    const bool al = b % (16 / (int)sizeof(T)) == 0;   // 16-byte aligned rows of G and GT
-    for (int i = tid; i < ml; i += bd) {
-      for (int h = (b - 1) / CH * CH; h >= 0; h -= CH) {
-        T z[CH];
-#pragma unroll
-        for (int k = 0; k < CH; ++k) z[k] = h + k < b ? P[(size_t)(h + k) * mloc + i] : T(0);
-#pragma unroll
-        for (int j = CH - 1; j >= 0; --j) {
-          if (h + j < b) {
-            T col[16];                                       // S(h+k, h+j), k < j; G(h+j, h+j)
-            load16(GT + (size_t)(h + j) * b + h, al, b - h < CH ? b - h : CH, col);
-            z[j] = z[j] * (T(2) / col[j]);
-#pragma unroll
-            for (int k = 0; k < j; ++k) z[k] = fma(-col[k], z[j], z[k]);
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < CH; ++k)
-          if (h + k < b) p.VT[r0 + i + (int64_t)(h + k) * p.m] = z[k];
-        for (int j = 0; j < h; ++j) {
-          T row[16];                                         // S(j, h+k)
-          load16(G + (size_t)j * b + h, al, b - h < CH ? b - h : CH, row);
-          T y = P[(size_t)j * mloc + i];
-#pragma unroll
-          for (int k = 0; k < CH; ++k)
-            if (h + k < b) y = fma(-row[k], z[k], y);
-          P[(size_t)j * mloc + i] = y;
-        }
-      }
-    }
-    // V T for the formation of Q: (V T)(i, :) S = V(i, :), forward substitution in chunks of 16
-    // columns from the first, on V reloaded from its global copy (P now holds V T^T's
-    // intermediate values)
-    __syncthreads();
-    for (int k = 0; k < b; ++k)
-      for (int i = tid; i < ml; i += bd) P[(size_t)k * mloc + i] = p.V[r0 + i + (int64_t)(t0 + k) * p.ldv];
-    __syncthreads();
-    for (int i = tid; i < ml; i += bd) {
-      for (int h = 0; h < b; h += CH) {
-        T z[CH];
-#pragma unroll
-        for (int k = 0; k < CH; ++k) z[k] = h + k < b ? P[(size_t)(h + k) * mloc + i] : T(0);
-#pragma unroll
-        for (int j = 0; j < CH; ++j) {
-          if (h + j < b) {
-            T row[16];                                       // S(h+j, h+k), k > j; G(h+j, h+j)
-            load16(G + (size_t)(h + j) * b + h, al, b - h < CH ? b - h : CH, row);
-            z[j] = z[j] * (T(2) / row[j]);
-#pragma unroll
-            for (int k = j + 1; k < CH; ++k) z[k] = fma(-row[k], z[j], z[k]);
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < CH; ++k)
-          if (h + k < b) p.VTN[r0 + i + (int64_t)(t0 + h + k) * p.m] = z[k];
-        for (int j = h + CH; j < b; ++j) {
-          T col[16];                                         // S(h+k, j)
-          load16(GT + (size_t)j * b + h, al, CH, col);
-          T y = P[(size_t)j * mloc + i];
-#pragma unroll
-          for (int k = 0; k < CH; ++k) y = fma(-col[k], z[k], y);
-          P[(size_t)j * mloc + i] = y;
-        }
-      }
+      for (int k = 0; k < CH; ++k) y = fma(-col[k], z[k], y);
+      rb[j] = y;
     }
   }
 }
@@ -569,7 +506,7 @@ struct QrPanelPlan {
 
 template <typename T>
 size_t qr_panel_smem(int b, int mloc) {
-  return sizeof(T) * ((size_t)b * mloc + 2 * (size_t)b * b);
+  return sizeof(T) * (size_t)b * mloc;
 }
 
 template <typename T>
@@ -618,14 +555,15 @@ QrPanelPlan plan_qr_panels(int64_t m, int s) {
   return pl;
 }
 
-// workspace: fail word, Cw (m x s), VTN (m x s), VT (m x kQrMaxB), W (kQrMaxB x s), split-K scratch
+// workspace: fail word, Cw (m x s), VTN (m x s), VT (m x kQrMaxB), W (kQrMaxB x s), G (kQrMaxB^2),
+// split-K scratch
 template <typename T>
 size_t qr_panels_ws(int64_t m, int s) {
   const bool f64 = sizeof(T) == 8;
   size_t kws = 0;                     // split-K scratch of W = V_p^T C(t0:, t0+b:), any width
   for (int ntr = 1; ntr <= s; ++ntr) kws = std::max(kws, gemm_workspace(kQrMaxB, ntr, m, f64));
   return 256 + 2 * align_up(sizeof(T) * (size_t)m * s) + align_up(sizeof(T) * (size_t)m * kQrMaxB) +
-         align_up(sizeof(T) * (size_t)kQrMaxB * s) + kws;
+         align_up(sizeof(T) * (size_t)kQrMaxB * s) + align_up(sizeof(T) * kQrMaxB * kQrMaxB) + kws;
 }
 
 // Q = [I_s; 0] before the panels are applied (m x s, leading dimension ldq)
@@ -652,6 +590,8 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
   base += align_up(sizeof(T) * (size_t)m * kQrMaxB);
   T* Wt = reinterpret_cast<T*>(base);
   base += align_up(sizeof(T) * (size_t)kQrMaxB * s);
+  T* Gp = reinterpret_cast<T*>(base);
+  base += align_up(sizeof(T) * kQrMaxB * kQrMaxB);
   void* kws = base;
   if (cudaMemsetAsync(fail, 0, 4, st) != cudaSuccess) return SKEL_ERR_CUDA;
   if (cudaMemset2DAsync(R, sizeof(double) * ldr, 0, sizeof(double) * s, s, st) != cudaSuccess) return SKEL_ERR_CUDA;
@@ -685,6 +625,25 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
     {
       KernelTimer kt("qr_panel", st);
       if (cudaLaunchKernelEx(&cfg, qr_panel_kernel<T>, p) != cudaSuccess) return SKEL_ERR_CUDA;
+    }
+    // G = V_p^T V_p, then V_p T_p^T and V_p T_p over the rows t0..
+    {
+      GemmArgs g{};
+      g.M = p.b; g.N = p.b; g.K = m - t0;
+      g.L = View{V + t0 + (int64_t)t0 * ldv, ldv, 1}; g.l_dt = dt;
+      g.B = View{V + t0 + (int64_t)t0 * ldv, 1, ldv}; g.b_dt = dt;
+      g.out = Gp; g.out_sr = p.b; g.out_sc = 1; g.out_dt = dt;
+      g.alpha = 1.0;
+      g.splitk_ws = kws;
+      g.timer = "gemm_qr";
+      if (launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, st) != cudaSuccess) return SKEL_ERR_CUDA;
+      const size_t wsm = qr_wy_smem<T>(p.b);
+      if (cudaFuncSetAttribute(qr_wy_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm) != cudaSuccess)
+        return SKEL_ERR_CUDA;
+      KernelTimer kt("qr_wy", st);
+      qr_wy_kernel<T><<<(unsigned)((m - t0 + kWyRows - 1) / kWyRows), kWyRows, wsm, st>>>(V, ldv, m, t0, p.b, Gp, VT,
+                                                                                            VTN);
+      note_launches(1);
     }
     note_launches(1);
     const int ntr = s - t0 - p.b;
