@@ -314,7 +314,9 @@ def run_ours(args, rank, world):
     #   qr_panel    the column steps of three Householder QRs (C twice, R^T once): 2 rows k^2
     #               flop each (the panels' WY factors are formed by other kernels)
     #   trsm        Z = R_C^{-1} W (k^2 n) and four k x k solves (CUR, eta): FP64
-    #   gemm_eta_h  R R^T, 2 k^2 n FP64 flop
+    #   gemm_eta_h  upper triangle of R R^T in float-float: k(k+1)/2 n products, each
+    #               9 FP32 pipe instructions (exact product + two-sum); peak = one FP32
+    #               instruction per lane per clock
     b_pan = 64
     lupp_flops = sum(min(b_pan, k - t0) ** 2 for t0 in range(0, k, b_pan)) * (n + m)
     models = {
@@ -324,7 +326,7 @@ def run_ours(args, rank, world):
         "lupp_panel": ("alu", lupp_flops / 1e12, fp32_alu_peak, "TFLOP/s"),
         "qr_panel": ("alu", 2.0 * (2 * m + n) * k * k / 1e12, fp32_alu_peak, "TFLOP/s"),
         "trsm": ("alu", (1.0 * k * k * n + 4.0 * k ** 3) / 1e12, fp64_alu_peak, "TFLOP/s"),
-        "gemm_eta_h": ("alu", 2.0 * k * k * n / 1e12, fp64_alu_peak, "TFLOP/s"),
+        "gemm_eta_h": ("alu", 9.0 * k * (k + 1) / 2 * n / 1e12, fp32_alu_peak / 2, "TOP/s"),
     }
     kernels = {}
     for nm, (tot, cnt) in ktimes.items():

@@ -390,7 +390,8 @@ skel_status skel_error(int64_t m, int64_t n, skel_dtype dtype, const void* A, in
     double* M1 = Rf ? static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s)) : nullptr;
     double* M2 = Rf ? static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s)) : nullptr;
     double* pscr = Rf ? static_cast<double*>(ar.take(power_scratch_bytes(s))) : nullptr;
-    void* kwsh = Rf ? ar.take(gemm_workspace(s, s, n, true)) : nullptr;
+    const bool ffh = Rf && rf_dtype == SKEL_F32;     // FP32 R: float-float R R^T
+    void* kwsh = Rf ? ar.take(ffh ? syrk_ff_workspace(s, n) : gemm_workspace(s, s, n, true)) : nullptr;
     if (!run) {
       skel_status st;
       if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
@@ -440,7 +441,10 @@ skel_status skel_error(int64_t m, int64_t n, skel_dtype dtype, const void* A, in
       g.out = H; g.out_sr = s; g.out_sc = 1; g.out_dt = SKEL_F64;
       g.alpha = 1.0;
       g.timer = "gemm_eta_h";
-      SK_CUDA(launch_gemm(g, true, LEFT_LOAD, EPI_STORE, stream));
+      if (ffh)
+        SK_CUDA(launch_syrk_ff(s, n, static_cast<const float*>(Rf), ldrf, H, s, kwsh, stream));
+      else
+        SK_CUDA(launch_gemm(g, true, LEFT_LOAD, EPI_STORE, stream));
       SK_CUDA(launch_gather_cols_rowmajor_f64(s, rf_dtype, Rf, ldrf, Js, R1, s, stream));
       SK_CUDA(launch_trsm_upper(s, s, R1, s, 0, SKEL_F64, H, s, M1, s, stream));
       SK_CUDA(launch_transpose_f64(s, M1, s, M2, s, stream));

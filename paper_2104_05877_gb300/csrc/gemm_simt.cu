@@ -237,6 +237,86 @@ cudaError_t dispatch_epi(const GemmArgs& a, int nz, GemmLeft left, GemmEpi epi, 
   return cudaErrorInvalidValue;
 }
 
+// H = R R^T (s x s, FP64) for an FP32 s x n row-major R with float-float accumulation: each
+// product a*b is split exactly into p + e (p = a*b, e = fma(a, b, -p)) and added to a (hi, lo)
+// pair by an error-free two-sum, which keeps ~44 significant bits on the FP32 pipes (FP64
+// arithmetic is scarce on this GPU).  64 x 64 tiles of the upper triangle, the K range split
+// into chunks; the chunk partials are summed in FP64 by syrk_ff_reduce_kernel.
+constexpr int FF_T = 64, FF_BK = 16;
+__device__ __forceinline__ void ff_add_prod(float a, float b, float& hi, float& lo) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);
+  const float t = hi + p;
+  const float z = t - hi;
+  const float err = (hi - (t - z)) + (p - z);
+  hi = t;
+  lo += err + e;
+}
+
+__global__ void __launch_bounds__(256) syrk_ff_kernel(int s, int64_t n, const float* R, int64_t ldr,
+                                                      int64_t kchunk, double* part) {
+  __shared__ float As[FF_BK][FF_T + 4], Bs[FF_BK][FF_T + 4];
+  // blockIdx.x enumerates the tile pairs ti <= tj
+  int ti = 0, rem = blockIdx.x;
+  const int nt = (s + FF_T - 1) / FF_T;
+  while (rem >= nt - ti) { rem -= nt - ti; ++ti; }
+  const int tj = ti + rem;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t k0 = (int64_t)blockIdx.y * kchunk;
+  const int64_t k1 = k0 + kchunk < n ? k0 + kchunk : n;
+  float hi[4][4], lo[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) hi[i][j] = lo[i][j] = 0.f;
+  for (int64_t kb = k0; kb < k1; kb += FF_BK) {
+#pragma unroll
+    for (int q = 0; q < FF_T * FF_BK / 256; ++q) {
+      const int e = q * 256 + tid;
+      const int r = e / FF_BK, k = e % FF_BK;
+      const int64_t gk = kb + k;
+      const int ra = ti * FF_T + r, rb = tj * FF_T + r;
+      As[k][r] = (ra < s && gk < k1) ? R[(int64_t)ra * ldr + gk] : 0.f;
+      Bs[k][r] = (rb < s && gk < k1) ? R[(int64_t)rb * ldr + gk] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < FF_BK; ++k) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ff_add_prod(a[i], b[j], hi[i][j], lo[i][j]);
+    }
+    __syncthreads();
+  }
+  double* out = part + (int64_t)blockIdx.y * s * s;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = ti * FF_T + ty * 4 + i, c = tj * FF_T + tx * 4 + j;
+      if (r < s && c < s && c >= r) out[(int64_t)r * s + c] = (double)hi[i][j] + (double)lo[i][j];
+    }
+}
+
+// H(r, c) = H(c, r) = sum over chunks of part[z][r][c] (upper entries, chunk order)
+__global__ void syrk_ff_reduce_kernel(int s, int P, const double* part, double* H, int64_t ldh) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)s * s;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / s), c = (int)(e % s);
+    if (c < r) continue;
+    double a = 0.0;
+    for (int z = 0; z < P; ++z) a += part[(int64_t)z * s * s + e];
+    H[(int64_t)r * ldh + c] = a;
+    H[(int64_t)c * ldh + r] = a;
+  }
+}
+
 // ------------------------------------------------------------------------------------
 __global__ void reduce_sum_kernel(const double* p, int64_t count, double* out, int take_sqrt) {
   double v = 0.0;
@@ -362,6 +442,34 @@ cudaError_t launch_gemm(const GemmArgs& a0, bool f64, GemmLeft left, GemmEpi epi
     nz = (int)((a.K + a.kchunk - 1) / a.kchunk);
   }
   return f64 ? dispatch_epi<double>(a, nz, left, epi, st) : dispatch_epi<float>(a, nz, left, epi, st);
+}
+
+static int64_t syrk_ff_chunk(int32_t s, int64_t n) {
+  const int64_t nt = (s + FF_T - 1) / FF_T, pairs = nt * (nt + 1) / 2;
+  const int64_t want = 2 * (int64_t)device_sm_count();
+  int64_t P = std::max<int64_t>(1, std::min<int64_t>((want + pairs - 1) / pairs, (n + 255) / 256));
+  return ((n + P - 1) / P + FF_BK - 1) / FF_BK * FF_BK;
+}
+
+size_t syrk_ff_workspace(int32_t s, int64_t n) {
+  const int64_t P = (n + syrk_ff_chunk(s, n) - 1) / syrk_ff_chunk(s, n);
+  return align_up(sizeof(double) * (size_t)P * s * s);
+}
+
+cudaError_t launch_syrk_ff(int32_t s, int64_t n, const float* R, int64_t ldr, double* H, int64_t ldh, void* ws,
+                           cudaStream_t st) {
+  const int64_t nt = (s + FF_T - 1) / FF_T, pairs = nt * (nt + 1) / 2;
+  const int64_t chunk = syrk_ff_chunk(s, n);
+  const int P = (int)((n + chunk - 1) / chunk);
+  double* part = static_cast<double*>(ws);
+  {
+    KernelTimer kt("gemm_eta_h", st);
+    syrk_ff_kernel<<<dim3((unsigned)pairs, (unsigned)P), 256, 0, st>>>(s, n, R, ldr, chunk, part);
+  }
+  syrk_ff_reduce_kernel<<<(unsigned)std::min<int64_t>(((int64_t)s * s + 255) / 256, 1024), 256, 0, st>>>(s, P, part,
+                                                                                                          H, ldh);
+  note_launches(2);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_sum(const double* partials, int64_t count, double* out, int take_sqrt,

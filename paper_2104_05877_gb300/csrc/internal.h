@@ -46,6 +46,11 @@ int64_t gemm_num_blocks(int64_t M, int64_t N);
 size_t gemm_workspace(int64_t M, int64_t N, int64_t K, bool f64);
 cudaError_t launch_gemm(const GemmArgs& a, bool f64, GemmLeft left, GemmEpi epi, cudaStream_t st);
 
+// H = R R^T (s x s FP64, row-major ldh) for an FP32 s x n row-major R, float-float accumulation
+// (~44 bits) on the FP32 pipes; workspace syrk_ff_workspace(s, n) bytes.
+size_t syrk_ff_workspace(int32_t s, int64_t n);
+cudaError_t launch_syrk_ff(int32_t s, int64_t n, const float* R, int64_t ldr, double* H, int64_t ldh, void* ws,
+                           cudaStream_t st);
 // Sum `count` doubles in `partials` (deterministic) into *out (device), optionally sqrt.
 cudaError_t launch_reduce_sum(const double* partials, int64_t count, double* out, int take_sqrt,
                               cudaStream_t st);

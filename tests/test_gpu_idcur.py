@@ -126,3 +126,20 @@ def test_end_to_end_fp64_config1(skel, dev):
     if kk == k:
         assert np.linalg.norm(out["Z"].cpu().numpy() - ref["Z"]) <= 1e-10 * np.linalg.norm(ref["Z"])
         assert e[3] == pytest.approx(ref["eta"], rel=1e-8)
+
+
+def test_eta_from_fp32_rfactor(skel, dev):
+    """Theorem 1's eta from an FP32 R (the mixed-precision path's LUPP factor): the device's
+    float-float R R^T equals the oracle's FP64 eta of the same FP32 numbers within 1e-8.
+    s = 150 spans three 64-row tiles with a ragged tail; n = 3000 splits the K range."""
+    rng = np.random.default_rng(31)
+    m, n, k = 200, 3000, 150
+    X = rng.standard_normal((m, n))
+    piv = pivoting.lupp_columns(X, k)
+    R32 = piv["R"].astype(np.float32)
+    Js = piv["Js"]
+    A = rng.standard_normal((200, n))
+    out, st = skel.error(torch.from_numpy(np.asfortranarray(A)).to(dev).t().contiguous().t(),
+                         torch.from_numpy(Js.astype(np.int32)).to(dev), Rf=torch.from_numpy(R32).to(dev))
+    skel.check_status(st)
+    assert out.cpu().numpy()[3] == pytest.approx(errors.eta(R32.astype(np.float64), Js), rel=1e-8)
