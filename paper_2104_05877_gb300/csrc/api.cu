@@ -104,7 +104,7 @@ skel_status skel_sketch(int64_t m, int64_t n, skel_dtype a_dtype, const void* A,
   }
   const bool tensor = kind == SKEL_SKETCH_GAUSSIAN && (prec == SKEL_PREC_BF16 || prec == SKEL_PREC_TF32);
   if (tensor && a_dtype != SKEL_F32) return SKEL_ERR_UNSUPPORTED;
-  void* tcws = tensor && m > 0 && n > 0 ? ar.take(sketch_tc_workspace(m, n, l)) : nullptr;
+  void* tcws = tensor && m > 0 && n > 0 ? ar.take(sketch_tc_workspace(m, n, l, prec)) : nullptr;
   skel_status st;
   if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
   if (n == 0) return SKEL_OK;

@@ -146,7 +146,7 @@ cudaError_t launch_gauss_sketch_csc(int64_t m, int64_t n, const int64_t* col_ptr
 
 // Tensor-core Gaussian sketch (sketch_tc.cu).  Returns cudaErrorNotSupported when the
 // shape or alignment is outside what the kernel handles.  ws: sketch_tc_workspace bytes.
-size_t sketch_tc_workspace(int64_t m, int64_t n, int32_t l);
+size_t sketch_tc_workspace(int64_t m, int64_t n, int32_t l, skel_prec prec);
 cudaError_t launch_sketch_tc(int64_t m, int64_t n, const float* A, int64_t lda, int32_t l,
                              skel_prec prec, uint64_t seed, float* X, int64_t ldx, void* ws,
                              int32_t* dev_status, cudaStream_t st);

@@ -1,7 +1,8 @@
 // tcgen05 / TMA building blocks shared by the tensor-core kernels (sketch X = Gamma A and the
-// 3xTF32 product W = Q^T A): mbarrier waits bounded in time, 2-D TMA loads, 128-byte-swizzle
-// K-major shared-memory descriptors, TF32 instruction descriptors, MMA issue and commit,
-// TMEM loads, and the driver entry point that encodes tensor maps.
+// 3xTF32 product W = Q^T A): mbarrier waits bounded in time (CTA and cluster scope), remote
+// arrives and loads within a thread-block cluster, 2-D TMA loads, 128- and 64-byte-swizzle
+// K-major shared-memory descriptors, TF32 and BF16 instruction descriptors, MMA issue and
+// commit, TMEM loads, and the driver entry point that encodes tensor maps.
 #pragma once
 
 #include <cuda.h>
@@ -42,6 +43,54 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
   return true;
 }
 
+// Cluster-scope variants: waits that acquire what other CTAs of the cluster released, an
+// arrive on the mbarrier at the same offset in CTA `rank`, and a 16-byte load from the shared
+// memory of another CTA of the cluster.
+__device__ __forceinline__ bool mbar_try_cl(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_cl(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_cl(bar, parity)) {
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t local_bar, int rank) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];"
+               ::"r"(cluster_addr(local_bar, rank)) : "memory");
+}
+// Bulk copy of `bytes` (multiple of 16, 16-byte aligned) from this CTA's shared memory to
+// the same offset in CTA `rank` of the cluster; completes the bytes on that CTA's mbarrier
+// at the offset of `local_bar`.
+__device__ __forceinline__ void bulk_copy_to_peer(uint32_t local_dst_src, uint32_t bytes, uint32_t local_bar, int rank) {
+  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(cluster_addr(local_dst_src, rank)), "r"(local_dst_src), "r"(bytes),
+                 "r"(cluster_addr(local_bar, rank)) : "memory");
+}
+// MMA completion arrives on the mbarrier at the offset of `bar` in every CTA of `mask`.
+__device__ __forceinline__ void mma_commit_multicast(uint32_t bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+               ::"r"(bar), "h"(mask) : "memory");
+}
+__device__ __forceinline__ uint4 ld_cluster_v4(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
@@ -63,6 +112,17 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
+// K-major, 64-byte swizzle (rows of 64 bytes, 8-row groups 512 bytes apart).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(512u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;                   // 64-byte swizzle
+  return d;
+}
+
 // Instruction descriptor: D FP32, A/B TF32, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -71,6 +131,15 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+// Instruction descriptor for kind::f16: D FP32, A/B BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
       ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {

@@ -4,7 +4,7 @@ import pytest
 import scipy.sparse as sp
 import torch
 
-from oracle import embedding, sketch
+from oracle import embedding, pivoting, sketch
 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -113,8 +113,10 @@ def test_gaussian_csc(skel, dev):
     assert np.all(np.abs(X.cpu().numpy() - want) <= _bound(l, 500, 2, Ad, 2.0 ** -22) + 1e-6 * _bound(l, 500, 2, Ad, 1.0) / 500)
 
 
+# column tiles of 512: 2 and 10 (clusters of 2), 3 (no cluster), 4 and 8 (clusters of 4, ragged
+# last tile for n = 4000)
 @pytest.mark.parametrize("m,n,l", [(1000, 777, 61), (2048, 1536, 272), (4096, 600, 130), (300, 5000, 40),
-                                   (129, 513, 128), (8192, 1024, 528)])
+                                   (129, 513, 128), (8192, 1024, 528), (1000, 2048, 100), (600, 4000, 50)])
 def test_sketch_tf32_tensor_cores(skel, dev, m, n, l):
     """tcgen05 kind::tf32 sketch: Gamma is rounded to TF32 in the kernel and A is read by the
     tensor core as TF32 (at most 2^-10 relative per operand); accumulation is FP32.  Bound:
@@ -142,3 +144,48 @@ def test_sketch_tf32_padded_lda(skel, dev):
     G = embedding.gaussian_normals(l, m, 3)
     bound = (2.0 ** -9 + m * 2.0 ** -23) * (np.abs(G) @ np.abs(Ad)) / np.sqrt(l)
     assert np.all(np.abs(X.cpu().numpy() - want) <= bound)
+
+
+@pytest.mark.parametrize("m,n,l", [(1000, 777, 61), (2048, 1536, 272), (129, 513, 128), (1000, 2048, 100),
+                                   (600, 4000, 50), (4100, 2048, 300)])
+def test_sketch_bf16_tensor_cores(skel, dev, m, n, l):
+    """tcgen05 kind::f16 sketch: the kernel rounds Gamma (evaluated in FP32) and A to BF16 to
+    nearest-even; products are exact in FP32 and accumulation is FP32.  Reference: the oracle's
+    BF16-operand sketch (FP64 normals rounded to BF16).  The two Gammas differ by one BF16 ulp
+    (2^-7 relative) where the FP32 normal sits within a few FP32 ulps of a BF16 rounding
+    boundary (about 1 entry in 10^4); at most two such entries per row are allowed for."""
+    A = workloads.dense_config2(m, n, seed=m + l + 1)
+    X, st = skel.sketch(torch.from_numpy(A).to(dev), l, prec="bf16", seed=78)
+    skel.check_status(st)
+    Ad = A.astype(np.float64)
+    want = sketch.gaussian_sketch(Ad, l, 78, operand_rounding="bf16")
+    Gb = embedding.round_bf16(embedding.gaussian_normals(l, m, 78))
+    Ab = embedding.round_bf16(Ad)
+    acc = m * 2.0 ** -23 * (np.abs(Gb) @ np.abs(Ab))
+    flips = 2 * 2.0 ** -7 * np.outer(np.abs(Gb).max(axis=1), np.abs(Ab).max(axis=0))
+    bound = (acc + flips) / np.sqrt(l)
+    err = np.abs(X.cpu().numpy() - want)
+    assert np.all(err <= bound), (err / bound).max()
+    # and the reduced-precision sketch stays within the BF16 operand error of the exact one
+    exact = sketch.gaussian_sketch(Ad, l, 78)
+    G = embedding.gaussian_normals(l, m, 78)
+    assert np.all(np.abs(X.cpu().numpy() - exact) <= (2.0 ** -7 + m * 2.0 ** -23) * (np.abs(G) @ np.abs(Ad)) / np.sqrt(l))
+
+
+def test_sketch_bf16_pivots_well_separated(skel, dev):
+    """Pivots from the BF16 sketch equal the oracle's on columns with geometrically separated
+    norms (every greedy gap far above the BF16 sketch error)."""
+    rng = np.random.default_rng(10)
+    m, n, k = 1500, 2048, 12
+    A = rng.standard_normal((m, n)) * 1e-3
+    cols = rng.choice(n, k, replace=False)
+    for t, c in enumerate(cols):
+        A[:, c] = rng.standard_normal(m) * 4.0 ** (k - t)
+    A = np.asfortranarray(A.astype(np.float32))
+    X, st = skel.sketch(torch.from_numpy(A).to(dev), k + 4, prec="bf16", seed=4)
+    skel.check_status(st)
+    Js, _, _, st2 = skel.pivot_lupp(X, k)
+    skel.check_status(st2)
+    ref = pivoting.lupp_columns(sketch.gaussian_sketch(A.astype(np.float64), k + 4, 4), k)
+    assert ref["gaps"].min() > 0.2          # every step's relative gap far above BF16 rounding
+    assert np.array_equal(Js.cpu().numpy(), ref["Js"])
