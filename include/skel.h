@@ -94,6 +94,22 @@ skel_status skel_sketch(int64_t m, int64_t n, skel_dtype a_dtype, const void* A,
                         int32_t* dev_status, cudaStream_t stream);
 
 /*
+ * skel_sketch_rows -- the partial sketch of a block of rows of a larger A (the row-partitioned
+ * form of Algorithm 2 line 2: X = sum over row blocks of Gamma(:, rows) A(rows, :)).
+ *   row0      : global index of the block's first row; a multiple of 4, row0 + m <= 2^32 - 1.
+ *               Gamma's columns row0 .. row0+m-1 are generated (Gaussian counters (j/4, i, 0, 0)
+ *               and sparse-sign counters (j, 0, 1, c) use the global row j), so the partial
+ *               sketches of a partition of A's rows sum to skel_sketch of the whole A.
+ *   every other argument is skel_sketch's, for the m x n block (A points at its first row).
+ * skel_sketch(...) is skel_sketch_rows(0, ...).  Errors: SKEL_ERR_INVALID_ARG for a negative
+ * or unaligned row0, else as skel_sketch.
+ */
+skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dtype, const void* A,
+                             int64_t lda, int32_t l, skel_sketch_kind kind, int32_t zeta, skel_prec prec,
+                             uint64_t seed, void* X, int64_t ldx, void* ws, size_t* ws_bytes,
+                             int32_t* dev_status, cudaStream_t stream);
+
+/*
  * skel_sketch_csc -- X = Gamma A for a sparse A in compressed sparse column form (Table 1,
  * T_s = O(nnz(A) zeta) for the sparse sign embedding).
  *   col_ptr[n+1] (int64), row_idx[nnz] (int32, any order within a column), val[nnz] (FP32).

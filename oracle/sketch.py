@@ -30,6 +30,33 @@ def gaussian_sketch(A, l, seed, operand_rounding=None):
     return (G @ A) / np.sqrt(l)
 
 
+def gaussian_sketch_rows(A_block, l, seed, row0, operand_rounding=None):
+    """Partial sketch of rows row0 .. row0+m_b-1 of a larger A: Gamma(:, row0:row0+m_b) A_block.
+    Gamma's columns depend only on their global index, so the partial sketches of a row
+    partition sum to the sketch of the whole matrix (the row-partitioned Algorithm 2 line 2)."""
+    A_block = np.asarray(A_block, dtype=np.float64)
+    mb = A_block.shape[0]
+    G = embedding.gaussian_normals(l, row0 + mb, seed)[:, row0:]
+    if operand_rounding == "fp32":
+        G, A_block = embedding.round_fp32(G), embedding.round_fp32(A_block)
+    elif operand_rounding == "bf16":
+        G, A_block = embedding.round_bf16(G), embedding.round_bf16(A_block)
+    elif operand_rounding is not None:
+        raise ValueError(operand_rounding)
+    return (G @ A_block) / np.sqrt(l)
+
+
+def sparse_sign_sketch_rows(A_block, l, zeta, seed, row0):
+    """Partial sparse-sign sketch of rows row0 .. row0+m_b-1 (global column indices of Gamma)."""
+    A_block = np.asarray(A_block, dtype=np.float64)
+    mb = A_block.shape[0]
+    rows, signs = embedding.sparse_sign_pattern(l, row0 + mb, zeta, seed)
+    rows, signs = rows[row0:], signs[row0:]
+    cols = np.repeat(np.arange(mb), zeta)
+    Gam = sp.csr_matrix((signs.ravel() / np.sqrt(zeta), (rows.ravel(), cols)), shape=(l, mb))
+    return np.asarray(Gam @ A_block, dtype=np.float64)
+
+
 def sparse_sign_sketch(A, l, zeta, seed):
     """X = Gamma A with the sparse sign Gamma; A dense (ndarray) or scipy.sparse."""
     m = A.shape[0]

@@ -44,6 +44,7 @@ def lib():
                                    ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t))
     sig = {
         "skel_sketch": [i64, i64, i32, vp, i64, i32, i32, i32, i32, u64, vp, i64, vp, szp, vp, vp],
+        "skel_sketch_rows": [i64, i64, i64, i32, vp, i64, i32, i32, i32, i32, u64, vp, i64, vp, szp, vp, vp],
         "skel_sketch_csc": [i64, i64, i64, vp, vp, vp, i32, i32, i32, u64, vp, i64, vp, szp, vp, vp],
         "skel_pivot_lupp": [i32, vp, i64, i64, i64, i32, vp, vp, i64, vp, i64, vp, szp, vp, vp],
         "skel_pivot_cpqr": [i32, vp, i64, i64, i64, i32, vp, vp, i64, vp, szp, vp, vp],
@@ -136,8 +137,10 @@ def _call(name, build_args, device):
 
 
 # ------------------------------------------------------------------------------------------
-def sketch(A, l, kind="gaussian", prec="f32", seed=0, zeta=8, X=None, status=None):
-    """X = Gamma A (l x n, row-major): FP64 for prec='f64', FP32 otherwise."""
+def sketch(A, l, kind="gaussian", prec="f32", seed=0, zeta=8, X=None, status=None, row0=0):
+    """X = Gamma A (l x n, row-major): FP64 for prec='f64', FP32 otherwise.  With row0 > 0, A
+    is the block of rows row0 .. row0+m-1 of a larger matrix and X its partial sketch (Gamma's
+    columns row0 ..); the partial sketches of a row partition sum to the whole sketch."""
     A, lda = _colmajor(A)
     m, n = A.shape
     if prec in ("tf32", "bf16") and (lda % 4 or A.data_ptr() % 16):
@@ -151,8 +154,8 @@ def sketch(A, l, kind="gaussian", prec="f32", seed=0, zeta=8, X=None, status=Non
         X = torch.empty(l, n, dtype=xdt, device=A.device)
     X, ldx = _rowmajor(X)
     st = status if status is not None else new_status(A.device)
-    _call("skel_sketch", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, l, KIND[kind], zeta, PREC[prec],
-                                        seed, _ptr(X), ldx, w, sz, _ptr(st), _stream()], A.device)
+    _call("skel_sketch_rows", lambda w, sz: [row0, m, n, _dt(A), _ptr(A), lda, l, KIND[kind], zeta, PREC[prec],
+                                             seed, _ptr(X), ldx, w, sz, _ptr(st), _stream()], A.device)
     return X, st
 
 

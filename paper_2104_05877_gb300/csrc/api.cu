@@ -85,6 +85,15 @@ skel_status skel_sketch(int64_t m, int64_t n, skel_dtype a_dtype, const void* A,
                         int32_t l, skel_sketch_kind kind, int32_t zeta, skel_prec prec,
                         uint64_t seed, void* X, int64_t ldx, void* ws, size_t* ws_bytes,
                         int32_t* dev_status, cudaStream_t stream) {
+  return skel_sketch_rows(0, m, n, a_dtype, A, lda, l, kind, zeta, prec, seed, X, ldx, ws, ws_bytes, dev_status,
+                          stream);
+}
+
+skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dtype, const void* A,
+                             int64_t lda, int32_t l, skel_sketch_kind kind, int32_t zeta, skel_prec prec,
+                             uint64_t seed, void* X, int64_t ldx, void* ws, size_t* ws_bytes,
+                             int32_t* dev_status, cudaStream_t stream) {
+  if (row0 < 0 || row0 % 4 != 0 || row0 + m > 0xFFFFFFFFll) return SKEL_ERR_INVALID_ARG;
   if (m < 0 || n < 0 || l < 1 || l > 4096 || !valid_dtype(a_dtype)) return SKEL_ERR_INVALID_ARG;
   if (lda < std::max<int64_t>(1, m) || ldx < std::max<int64_t>(1, n)) return SKEL_ERR_INVALID_ARG;
   if ((m > 0 && n > 0 && A == nullptr) || (n > 0 && X == nullptr)) return SKEL_ERR_INVALID_ARG;
@@ -114,12 +123,12 @@ skel_status skel_sketch(int64_t m, int64_t n, skel_dtype a_dtype, const void* A,
         SK_CUDA(cudaMemsetAsync(static_cast<char*>(X) + esize(x_dt) * r * ldx, 0, esize(x_dt) * n, stream));
       return SKEL_OK;
     }
-    SK_CUDA(launch_sparse_pattern(m, l, zeta, seed, table, stream));
+    SK_CUDA(launch_sparse_pattern(row0, m, l, zeta, seed, table, stream));
     SK_CUDA(launch_sparse_sketch_dense(m, n, a_dtype, A, lda, l, zeta, table, X, ldx, dev_status, stream));
     return SKEL_OK;
   }
   if (tensor && m > 0) {
-    const cudaError_t e = launch_sketch_tc(m, n, static_cast<const float*>(A), lda, l, prec, seed,
+    const cudaError_t e = launch_sketch_tc(row0, m, n, static_cast<const float*>(A), lda, l, prec, seed,
                                            static_cast<float*>(X), ldx, tcws, dev_status, stream);
     if (e == cudaErrorNotSupported) return SKEL_ERR_UNSUPPORTED;
     SK_CUDA(e);
@@ -131,6 +140,7 @@ skel_status skel_sketch(int64_t m, int64_t n, skel_dtype a_dtype, const void* A,
   a.out = X; a.out_sr = ldx; a.out_sc = 1; a.out_dt = x_dt;
   a.alpha = 1.0 / std::sqrt((double)l);
   a.seed = seed;
+  a.gcol0 = row0;
   a.dev_status = dev_status;
   SK_CUDA(launch_gemm(a, prec == SKEL_PREC_F64, LEFT_GAUSSIAN, EPI_SKETCH, stream));
   return SKEL_OK;
@@ -159,7 +169,7 @@ skel_status skel_sketch_csc(int64_t m, int64_t n, int64_t nnz, const int64_t* co
   if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
   if (n == 0) return SKEL_OK;
   if (kind == SKEL_SKETCH_SPARSE_SIGN) {
-    SK_CUDA(launch_sparse_pattern(m, l, zeta, seed, table, stream));
+    SK_CUDA(launch_sparse_pattern(0, m, l, zeta, seed, table, stream));
     SK_CUDA(launch_sparse_sketch_csc(m, n, col_ptr, row_idx, val, l, zeta, table, X, ldx, dev_status, stream));
   } else {
     SK_CUDA(launch_gauss_sketch_csc(m, n, col_ptr, row_idx, val, l, seed, X, ldx, dev_status, stream));

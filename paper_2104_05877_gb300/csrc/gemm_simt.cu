@@ -75,11 +75,11 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmArgs a) {
       if (gr < a.M && gk < a.K) {
         if constexpr (sizeof(T) == 8) {
           double d[4];
-          gaussian4_f64(k0s, k1s, (uint32_t)gr, (uint32_t)(gk >> 2), d);
+          gaussian4_f64(k0s, k1s, (uint32_t)gr, (uint32_t)((a.gcol0 + gk) >> 2), d);
 #pragma unroll
           for (int q = 0; q < 4; ++q) g[q] = (T)d[q];
         } else {
-          const float4 f = gaussian4_f32(k0s, k1s, (uint32_t)gr, (uint32_t)(gk >> 2));
+          const float4 f = gaussian4_f32(k0s, k1s, (uint32_t)gr, (uint32_t)((a.gcol0 + gk) >> 2));
           g[0] = f.x; g[1] = f.y; g[2] = f.z; g[3] = f.w;
         }
       }

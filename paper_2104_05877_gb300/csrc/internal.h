@@ -35,6 +35,7 @@ struct GemmArgs {
   double alpha;
   double* partials;                // EPI_STORE_SQ / EPI_RESID: gemm_num_blocks(M, N) doubles
   uint64_t seed;                   // LEFT_GAUSSIAN
+  int64_t gcol0 = 0;               // LEFT_GAUSSIAN: Gamma column of K index 0 (a multiple of 4)
   int32_t* dev_status;
   void* splitk_ws;                 // optional: gemm_workspace() bytes enable a K-split
   int64_t kchunk;                  // set by launch_gemm
@@ -129,7 +130,7 @@ skel_status run_qr(skel_dtype dt, const void* C, int64_t m, int64_t ldc, int32_t
 
 // Sparse sign / CSC sketches (sparse.cu).
 size_t sparse_pattern_bytes(int64_t m, int32_t zeta);
-cudaError_t launch_sparse_pattern(int64_t m, int32_t l, int32_t zeta, uint64_t seed,
+cudaError_t launch_sparse_pattern(int64_t row0, int64_t m, int32_t l, int32_t zeta, uint64_t seed,
                                   int32_t* table, cudaStream_t st);
 cudaError_t launch_sparse_sketch_dense(int64_t m, int64_t n, skel_dtype dt, const void* A,
                                        int64_t lda, int32_t l, int32_t zeta,
@@ -147,7 +148,7 @@ cudaError_t launch_gauss_sketch_csc(int64_t m, int64_t n, const int64_t* col_ptr
 // Tensor-core Gaussian sketch (sketch_tc.cu).  Returns cudaErrorNotSupported when the
 // shape or alignment is outside what the kernel handles.  ws: sketch_tc_workspace bytes.
 size_t sketch_tc_workspace(int64_t m, int64_t n, int32_t l, skel_prec prec);
-cudaError_t launch_sketch_tc(int64_t m, int64_t n, const float* A, int64_t lda, int32_t l,
+cudaError_t launch_sketch_tc(int64_t row0, int64_t m, int64_t n, const float* A, int64_t lda, int32_t l,
                              skel_prec prec, uint64_t seed, float* X, int64_t ldx, void* ws,
                              int32_t* dev_status, cudaStream_t st);
 

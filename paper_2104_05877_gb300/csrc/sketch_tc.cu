@@ -82,6 +82,7 @@ struct TcParams {
   int l;
   int P;                  // K-split: CTA z takes the K-steps z, z + P, z + 2P, ...
   int64_t ksteps;         // K-steps of TC_BK rows over m
+  int64_t grow0;          // Gamma column of row 0 of A (a multiple of 4)
   uint32_t k0s, k1s;      // Philox key
   float* out;             // X (P == 1) or partial buffers [P][l][n]
   int64_t ldo;
@@ -246,7 +247,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap tmapA, const TcParams p) {
         const int64_t k = kt + 4 * grp;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (row < p.l && k < p.m) {
-          v = gaussian4_f32(p.k0s, p.k1s, (uint32_t)row, (uint32_t)(k >> 2));
+          v = gaussian4_f32(p.k0s, p.k1s, (uint32_t)row, (uint32_t)((p.grow0 + k) >> 2));
           if (k + 1 >= p.m) v.y = 0.f;
           if (k + 2 >= p.m) v.z = 0.f;
           if (k + 3 >= p.m) v.w = 0.f;
@@ -439,7 +440,7 @@ TcPlan plan_tc(int64_t m, int64_t n, int l) {
 }
 
 template <int OP>
-cudaError_t launch_tc_op(int64_t m, int64_t n, const float* A, int64_t lda, int32_t l, uint64_t seed,
+cudaError_t launch_tc_op(int64_t row0, int64_t m, int64_t n, const float* A, int64_t lda, int32_t l, uint64_t seed,
                          float* X, int64_t ldx, void* ws, int32_t* dev_status, cudaStream_t st) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
@@ -457,6 +458,7 @@ cudaError_t launch_tc_op(int64_t m, int64_t n, const float* A, int64_t lda, int3
   p.m = m; p.n = n; p.l = l;
   p.P = pl.P;
   p.ksteps = (m + TC_BK - 1) / TC_BK;
+  p.grow0 = row0;
   p.k0s = (uint32_t)(seed & 0xffffffffu);
   p.k1s = (uint32_t)(seed >> 32);
   p.direct = pl.P == 1;
@@ -499,15 +501,15 @@ size_t sketch_tc_workspace(int64_t m, int64_t n, int32_t l, skel_prec prec) {
   return pl.P > 1 ? align_up(sizeof(float) * (size_t)pl.P * l * n) : 0;
 }
 
-cudaError_t launch_sketch_tc(int64_t m, int64_t n, const float* A, int64_t lda, int32_t l,
+cudaError_t launch_sketch_tc(int64_t row0, int64_t m, int64_t n, const float* A, int64_t lda, int32_t l,
                              skel_prec prec, uint64_t seed, float* X, int64_t ldx, void* ws,
                              int32_t* dev_status, cudaStream_t st) {
   if (prec != SKEL_PREC_TF32 && prec != SKEL_PREC_BF16) return cudaErrorNotSupported;
   if (m < 1 || n < 1) return cudaErrorNotSupported;
   if ((lda % 4) != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
   if (m > (int64_t)INT32_MAX || n > (int64_t)INT32_MAX) return cudaErrorNotSupported;
-  return prec == SKEL_PREC_BF16 ? launch_tc_op<OP_BF16>(m, n, A, lda, l, seed, X, ldx, ws, dev_status, st)
-                                : launch_tc_op<OP_TF32>(m, n, A, lda, l, seed, X, ldx, ws, dev_status, st);
+  return prec == SKEL_PREC_BF16 ? launch_tc_op<OP_BF16>(row0, m, n, A, lda, l, seed, X, ldx, ws, dev_status, st)
+                                : launch_tc_op<OP_TF32>(row0, m, n, A, lda, l, seed, X, ldx, ws, dev_status, st);
 }
 
 }  // namespace skel

@@ -19,14 +19,15 @@ namespace {
 constexpr int CT = 32;       // columns of X per CTA
 constexpr int JCH = 256;     // rows of A per table chunk
 
-__global__ void sparse_pattern_kernel(int64_t m, int32_t l, int32_t zeta, uint32_t k0, uint32_t k1,
+// Pattern of rows row0 .. row0+m-1 of A (counters use the global row index).
+__global__ void sparse_pattern_kernel(int64_t row0, int64_t m, int32_t l, int32_t zeta, uint32_t k0, uint32_t k1,
                                       int32_t* table) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
   uint32_t w[32];
   const int nw = 1 + zeta;
   for (int c = 0; 4 * c < nw; ++c) {
-    const uint4 o = philox4x32_10(make_uint4((uint32_t)j, 0u, kTagSparse, (uint32_t)c), k0, k1);
+    const uint4 o = philox4x32_10(make_uint4((uint32_t)(row0 + j), 0u, kTagSparse, (uint32_t)c), k0, k1);
     w[4 * c] = o.x;
     if (4 * c + 1 < 32) w[4 * c + 1] = o.y;
     if (4 * c + 2 < 32) w[4 * c + 2] = o.z;
@@ -158,11 +159,11 @@ __global__ void __launch_bounds__(256) gauss_csc_kernel(int64_t n, const int64_t
 
 size_t sparse_pattern_bytes(int64_t m, int32_t zeta) { return align_up(sizeof(int32_t) * (size_t)m * zeta); }
 
-cudaError_t launch_sparse_pattern(int64_t m, int32_t l, int32_t zeta, uint64_t seed, int32_t* table,
+cudaError_t launch_sparse_pattern(int64_t row0, int64_t m, int32_t l, int32_t zeta, uint64_t seed, int32_t* table,
                                   cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
   sparse_pattern_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(
-      m, l, zeta, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), table);
+      row0, m, l, zeta, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), table);
   note_launches(1);
   return cudaGetLastError();
 }

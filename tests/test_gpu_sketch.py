@@ -189,3 +189,36 @@ def test_sketch_bf16_pivots_well_separated(skel, dev):
     ref = pivoting.lupp_columns(sketch.gaussian_sketch(A.astype(np.float64), k + 4, 4), k)
     assert ref["gaps"].min() > 0.2          # every step's relative gap far above BF16 rounding
     assert np.array_equal(Js.cpu().numpy(), ref["Js"])
+
+
+@pytest.mark.parametrize("prec,kind", [("f64", "gaussian"), ("f32", "gaussian"), ("tf32", "gaussian"),
+                                       ("bf16", "gaussian"), ("f32", "sparse_sign"), ("f64", "sparse_sign")])
+def test_sketch_row_blocks_sum_to_the_sketch(skel, dev, prec, kind):
+    """The partial sketches of a row partition (row0 = multiples of 32, as dist.row_partition
+    makes them for three ranks) sum to the sketch of the whole matrix: same Gamma columns,
+    only the accumulation order differs."""
+    from paper_2104_05877_gb300 import dist
+    m, n, l = 1000, 600, 48
+    dt = np.float64 if prec == "f64" else np.float32
+    A = np.asfortranarray(np.random.default_rng(7).standard_normal((m, n)).astype(dt))
+    At = torch.from_numpy(A).to(dev)
+    X, st = skel.sketch(At, l, kind=kind, prec=prec, seed=21, zeta=6)
+    skel.check_status(st)
+    total = torch.zeros_like(X)
+    for row0, rows in dist.row_partition(m, 3, 32):
+        Xp, stp = skel.sketch(At[row0:row0 + rows], l, kind=kind, prec=prec, seed=21, zeta=6, row0=row0)
+        skel.check_status(stp)
+        total += Xp
+    Ad = A.astype(np.float64)
+    if kind == "gaussian":
+        want = sketch.gaussian_sketch(Ad, l, 21)
+        mag = (np.abs(embedding.gaussian_normals(l, m, 21)) @ np.abs(Ad)) / np.sqrt(l)
+    else:
+        want = sketch.sparse_sign_sketch(Ad, l, 6, 21)
+        mag = np.abs(embedding.sparse_sign_embedding(l, m, 6, 21)) @ np.abs(Ad)
+    u = 2.0 ** -52 if prec == "f64" else 2.0 ** -23
+    got = total.cpu().numpy()
+    assert np.all(np.abs(got - X.cpu().numpy()) <= 4 * m * u * mag)
+    # and the summed partial sketch still meets the whole sketch's parity bound
+    op = {"f64": 0.0, "f32": 0.0, "tf32": 2.0 ** -9, "bf16": 2.0 ** -7}[prec]
+    assert np.all(np.abs(got - want) <= (op + 4 * m * u) * mag)
