@@ -46,8 +46,10 @@ def parse():
     ap.add_argument("--prec", default="tf32", choices=["tf32", "bf16", "f32"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-GPU comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
-    ap.add_argument("--only", default=None, choices=["sketch", "lupp", "rows", "id", "cur", "eta"],
-                    help="run only this call (warm-up + steps, no extras): a small command for profilers")
+    ap.add_argument("--only", default=None, choices=["sketch", "lupp", "rows", "id", "cur", "eta", "batch"],
+                    help="run only this call (warm-up + steps, no extras): a small command for profilers; "
+                         "'batch' runs the batched configuration (4096 Gaussian-kernel blocks, k_max 128, "
+                         "tol 1e-6) instead of the dense workload")
     return ap.parse_args()
 
 
@@ -199,6 +201,9 @@ def run_ours(args, rank, world):
         __graft_entry__.build()
     k, p = args.k, args.p
     l = k + p
+    if args.only == "batch":
+        run_batch(args, rank, dev, skel, workloads)
+        return
     seed_A, seed_G = workloads.seed_for(2) + rank, workloads.seed_for(2, "gamma")
     A = make_A(dev, seed_A)
     torch.cuda.synchronize()
@@ -431,6 +436,39 @@ def run_ours(args, rank, world):
         "gpu_launches": launches, "clocks": clk.summary(),
     }
     print(json.dumps(res), flush=True)
+
+
+def run_batch(args, rank, dev, skel, workloads):
+    """Batched configuration: 4096 uneven Gaussian-kernel blocks (m_b ~ U[64, 1024], n_b ~
+    U[64, 512], FP32, ~2.6 GB), k_max = 128, p = 16, tol = 1e-6: one skel_batch_run per step."""
+    import torch
+    nblocks, kmax, p, tol = 4096, 128, 16, 1e-6
+    blocks = workloads.torch_kernel_blocks(nblocks, workloads.seed_for(4) + rank, dev)
+    a_bytes = sum(4 * B.shape[0] * B.shape[1] for B in blocks)
+    plan = skel.BatchPlan(blocks, kmax, p=p, tol=tol, seed=workloads.seed_for(4, "gamma"))
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        Js, ranks, Z, st = plan.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        Js, ranks, Z, st = plan.run()
+    e1.record()
+    torch.cuda.synchronize()
+    skel.check_status(st, "batch")
+    ms = e0.elapsed_time(e1) / args.steps
+    skel.kernel_timing(True)
+    plan.run()
+    torch.cuda.synchronize()
+    kern = {nm: skel.kernel_time(nm)[0] for nm in ("batch_sketch", "batch_lupp")}
+    skel.kernel_timing(False)
+    r = ranks.float()
+    if rank == 0:
+        print(json.dumps({"only": "batch", "ms": ms, "a_bytes": a_bytes, "a_streaming_gbs": a_bytes / (ms * 1e-3) / 1e9,
+                          "kernel_ms": kern, "rank_mean": float(r.mean()), "rank_max": int(r.max()),
+                          "config": {"workload": f"{nblocks} Gaussian-kernel blocks m_b~U[64,1024] n_b~U[64,512] fp32, "
+                                                 f"k_max={kmax}, p={p}, tol={tol}", "steps": args.steps}}), flush=True)
 
 
 def main():

@@ -233,6 +233,42 @@ skel_status skel_error(int64_t m, int64_t n, skel_dtype dtype, const void* A, in
                        int32_t* dev_status, cudaStream_t stream);
 
 /*
+ * Batched skeletonization of many independent blocks (hierarchical-matrix compression; the
+ * tolerance-driven rank is a reading: the paper fixes k).  Per block A_b (m_b x n_b, FP32,
+ * column-major, device): the Gaussian sketch X_b = Gamma A_b with l = kmax + p rows (one Gamma
+ * for every block, Gamma(:, 0:m_b)), computed to FP32 accuracy on the tensor cores; column LUPP
+ * on X_b (Sec. 2.5.2) stopped at the smallest t <= kmax with
+ *     ||S_t||_F^2 l/(l - t) <= tol^2 ||X_b||_F^2     (S_t: Schur complement after t steps)
+ * (or at kmax, or at a zero pivot); and the column ID coefficients from the sketch alone,
+ *     Z_b = X_b(0:r, J)^{-1} X_b(0:r, :)       (C^+ A ~ X_1^+ X, Sec. 4, no second pass over A).
+ * A is read once.
+ *
+ * skel_batch_plan_create -- m, n, A, lda: host arrays of nblocks block descriptors (A[b] a
+ *   device pointer, 16-byte aligned, lda[b] >= m[b] and a multiple of 4); 1 <= kmax <= 128,
+ *   p >= 1, kmax + p <= 256, tol >= 0; seed as for skel_sketch.  The plan keeps the pointers
+ *   (the blocks must stay allocated while it is used) and owns its device memory: tensor
+ *   maps, work lists, the Gamma halves (2 (kmax+p) max(m_b) floats) and the sketches
+ *   (sum_b (kmax+p) n_b floats).  Allocates and copies synchronously; no other call does.
+ *   SKEL_ERR_UNSUPPORTED when a block is wider than four CTAs' shared memory hold
+ *   ((kmax+p) n_b / 4 floats per CTA plus kmax^2) or is not TMA-addressable.
+ * skel_batch_z_offsets -- host: offsets[0..nblocks] (in doubles) of the blocks' Z in Z_all,
+ *   offsets[b+1] - offsets[b] = kmax n_b.
+ * skel_batch_run -- on `stream`, no host synchronisation: Js[b*kmax + q] (int32, q < rank_b,
+ *   -1 after), ranks[b], Z_all + offsets[b]: kmax x n_b row-major FP64, rows 0 .. rank_b-1
+ *   written (Z_b(:, Js) = I), rows from rank_b on left as they were.  dev_status: SKEL_ERR_NONFINITE (step = block) for a non-finite sketch,
+ *   SKEL_ERR_TIMEOUT if a pipeline wait of the sketch kernel gave up.
+ * skel_batch_plan_destroy -- frees the plan (after the work using it has finished).
+ */
+typedef struct skel_batch_plan skel_batch_plan;
+skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int64_t* n, const float* const* A,
+                                   const int64_t* lda, int32_t kmax, int32_t p, double tol, uint64_t seed,
+                                   skel_batch_plan** plan);
+skel_status skel_batch_z_offsets(const skel_batch_plan* plan, int64_t* offsets);
+skel_status skel_batch_run(skel_batch_plan* plan, int32_t* Js, int32_t* ranks, double* Z, int32_t* dev_status,
+                           cudaStream_t stream);
+void skel_batch_plan_destroy(skel_batch_plan* plan);
+
+/*
  * skel_debug_gaussian -- writes the standard normals G (l x m, row-major, ld = m) that the
  * Gaussian sketch kernels generate, in FP32 (as_fp64 = 0) or FP64 (as_fp64 = 1).  For tests
  * of the generator; the sketch kernels themselves never store G.
@@ -273,7 +309,7 @@ skel_status skel_debug_grid_timeout(int grid, uint64_t wait_ns, void* ws, size_t
  * of one kernel since the last skel_debug_kernel_timing call; waits for those launches.
  * Names: "sketch_tc", "gemm_tc" (W = Q^T A), "lupp_panel", "lupp_trail", "qr_panel", "qr_wy", "trsm",
  * "gemm_qr" (QR trailing updates and Q formation), "gemm_cur" (W Q_R), "gemm_eta_h" (R R^T),
- * "gemm_eta_sq" (eta's squarings), "gemm_simt" (other SIMT GEMMs).
+ * "gemm_eta_sq" (eta's squarings), "gemm_simt" (other SIMT GEMMs), "batch_sketch", "batch_lupp".
  * Host-side state, process-wide; not for concurrent use from several threads.
  */
 skel_status skel_debug_kernel_timing(int enable);

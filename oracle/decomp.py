@@ -1,4 +1,5 @@
-"""Interpolative and CUR decompositions from chosen skeletons (Sec. 2.2).
+"""Interpolative and CUR decompositions from chosen skeletons (Sec. 2.2), and the column ID
+formed from the sketch alone (Sec. 4).
 
 Column ID (Eq. (2.1)):   CID(A; J_s) = C C^+ A,  C = A(:, J_s),  so Z = C^+ A.
 CUR (Eq. (2.4)):         CUR(A; I_s, J_s) = C (C^+ A R^+) R,  R = A(I_s, :),  U = C^+ A R^+.
@@ -31,3 +32,17 @@ def cur(A, Js, Is):
     U = solve_triangular(Rc, M, lower=False)                # R_C^{-1} M
     U = solve_triangular(Rr, U.T, lower=False).T            # (R_R^{-1} U^T)^T = U R_R^{-T}
     return U
+
+
+def sketch_id(X, Js):
+    """Z (r x n) of the column ID estimated from the row sketch without a second pass over A
+    (Sec. 4: C^+ A ~ X_1^+ X with X_1 = X(:, J_s)), taken on the first r = |J_s| rows of X, whose
+    greedy pivots are J_s (rows r.. never influence them):
+        Z = X(0:r, J_s)^{-1} X(0:r, :).
+    A library LU solve serves as the step."""
+    X = np.asarray(X, dtype=np.float64)
+    Js = np.asarray(Js, dtype=np.int64)
+    r = Js.size
+    if r == 0:
+        return np.zeros((0, X.shape[1]))
+    return np.linalg.solve(X[:r, Js], X[:r, :])

@@ -17,25 +17,35 @@ import numpy as np
 def lupp_tolerance_rank(X, kmax, tol):
     """LUPP (same steps as ``pivoting.lupp_columns``) that stops at the tolerance rank.
 
-    returns dict(rank, Js (rank,), estimates (list of the t-th estimate ratio))
+    returns dict(rank, Js (rank,), estimates (list of the t-th estimate ratio),
+                 gaps (relative gap |best| - |second| over |best| of each step taken),
+                 mags (|best| of each step taken))
+    The steps also stop when no column is left or the best remaining magnitude is 0.
     """
     S = np.array(X, dtype=np.float64, copy=True)
     l, n = S.shape
-    if not (1 <= kmax < l and kmax <= n):
-        raise ValueError("need 1 <= kmax < l and kmax <= n")
+    if not (1 <= kmax < l):
+        raise ValueError("need 1 <= kmax < l")
     normX2 = float(np.sum(S ** 2))
     avail = np.ones(n, dtype=bool)
     Js = []
     ratios = []
+    gaps = []
+    mags = []
+    done = lambda t: dict(rank=t, Js=np.array(Js, dtype=np.int64), estimates=ratios,
+                          gaps=np.array(gaps, dtype=np.float64), mags=np.array(mags, dtype=np.float64))
     for t in range(kmax + 1):
         est = float(np.sum(S[t:] ** 2)) * l / (l - t)
         ratios.append(est / normX2 if normX2 > 0 else 0.0)
         if est <= tol * tol * normX2 or t == kmax:
-            return dict(rank=t, Js=np.array(Js, dtype=np.int64), estimates=ratios)
+            return done(t)
         mag = np.where(avail, np.abs(S[t]), -1.0)
         j = int(np.argmax(mag))
-        if mag[j] == 0.0:
-            return dict(rank=t, Js=np.array(Js, dtype=np.int64), estimates=ratios)
+        if mag[j] <= 0.0:
+            return done(t)
+        srt = np.sort(mag)
+        gaps.append((srt[-1] - max(srt[-2], 0.0)) / srt[-1] if n > 1 else 1.0)
+        mags.append(srt[-1])
         Js.append(j)
         r = S[t] / S[t, j]
         S[t + 1:] -= np.outer(S[t + 1:, j], r)

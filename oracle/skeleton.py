@@ -10,7 +10,7 @@ do enter CPQR's norms.  Row skeletons I_s come from row-wise LUPP on C = A(:, J_
 
 import numpy as np
 
-from . import sketch, pivoting, decomp, errors
+from . import sketch, pivoting, decomp, errors, rank
 
 
 def skeletonize(A, k, p, seed, kind="gaussian", pivot="lupp", zeta=8,
@@ -41,4 +41,18 @@ def skeletonize(A, k, p, seed, kind="gaussian", pivot="lupp", zeta=8,
         Is = rp["Js"]
         U = decomp.cur(A, Js, Is)
         out.update(Is=Is, row_pivot=rp, U=U, err_cur=errors.rel_cur_error(A, Js, U, Is))
+    return out
+
+
+def batch_skeletonize(blocks, kmax, p, tol, seed):
+    """Batched blocks (the tolerance-rank reading, see rank.py): per block the Gaussian sketch
+    with l = kmax + p rows (one Gamma for every block: columns 0..m_b-1 of the same embedding),
+    LUPP stopped at the tolerance rank, and the sketch-only column ID (decomp.sketch_id)."""
+    out = []
+    for A in blocks:
+        A = np.asarray(A, dtype=np.float64)
+        X = sketch.gaussian_sketch(A, kmax + p, seed)
+        rt = rank.lupp_tolerance_rank(X, kmax, tol)
+        out.append(dict(rank=rt["rank"], Js=rt["Js"], Z=decomp.sketch_id(X, rt["Js"]), X=X,
+                        gaps=rt["gaps"], mags=rt["mags"], estimates=rt["estimates"]))
     return out

@@ -71,6 +71,16 @@ def lib():
     L.skel_debug_kernel_time.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int64)]
     L.skel_debug_kernel_time.restype = ctypes.c_int
+    L.skel_batch_plan_create.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(vp),
+                                         ctypes.POINTER(i64), i32, i32, ctypes.c_double, u64,
+                                         ctypes.POINTER(vp)]
+    L.skel_batch_plan_create.restype = ctypes.c_int
+    L.skel_batch_z_offsets.argtypes = [vp, ctypes.POINTER(i64)]
+    L.skel_batch_z_offsets.restype = ctypes.c_int
+    L.skel_batch_run.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.skel_batch_run.restype = ctypes.c_int
+    L.skel_batch_plan_destroy.argtypes = [vp]
+    L.skel_batch_plan_destroy.restype = None
     _lib = L
     return L
 
@@ -342,3 +352,59 @@ def skeletonize(A, k, p=10, seed=0, prec="f32", pivot="lupp", kind="gaussian", z
         e, _ = error(A, Js, Z, out.get("Is"), out.get("U"), Rf, status=st)
         out["errors"] = e
     return out
+
+
+class BatchPlan:
+    """Batched skeletonization of independent FP32 blocks (skel_batch_*): per block the sketch
+    with l = kmax + p rows, LUPP stopped at the tolerance-driven rank, and the column ID
+    coefficients Z_b = X_b(0:r, J)^{-1} X_b(0:r, :).  `blocks`: CUDA float32 tensors (m_b x n_b,
+    column-major views, kept alive by the plan)."""
+
+    def __init__(self, blocks, kmax, p=16, tol=1e-6, seed=0):
+        self.blocks = []
+        for B in blocks:
+            if B.dtype != torch.float32 or not B.is_cuda:
+                raise ValueError("batch blocks must be float32 CUDA tensors")
+            B, ldb = _colmajor(B)
+            if ldb % 4 or B.data_ptr() % 16:       # TMA: 16-byte aligned columns
+                ld4 = (B.shape[0] + 3) // 4 * 4
+                Bp = torch.empty(B.shape[1], ld4, dtype=B.dtype, device=B.device).t()
+                Bp[:B.shape[0]].copy_(B)
+                B, ldb = Bp[:B.shape[0]], ld4
+            self.blocks.append((B, ldb))
+        nb = len(self.blocks)
+        arr = lambda T, v: (T * nb)(*v)
+        m = arr(ctypes.c_int64, [B.shape[0] for B, _ in self.blocks])
+        n = arr(ctypes.c_int64, [B.shape[1] for B, _ in self.blocks])
+        a = arr(ctypes.c_void_p, [B.data_ptr() for B, _ in self.blocks])
+        ld = arr(ctypes.c_int64, [ldb for _, ldb in self.blocks])
+        self.kmax, self.nb, self.device = kmax, nb, self.blocks[0][0].device
+        self._plan = ctypes.c_void_p()
+        rc = lib().skel_batch_plan_create(nb, m, n, a, ld, kmax, p, float(tol), seed, ctypes.byref(self._plan))
+        if rc != 0:
+            raise SkelError(rc, "skel_batch_plan_create")
+        off = (ctypes.c_int64 * (nb + 1))()
+        lib().skel_batch_z_offsets(self._plan, off)
+        self.z_offsets = list(off)
+
+    def run(self, status=None):
+        """Returns (Js (nb x kmax int32), ranks (nb,), Z_all (float64), status) on the device."""
+        Js = torch.empty(self.nb, self.kmax, dtype=torch.int32, device=self.device)
+        ranks = torch.empty(self.nb, dtype=torch.int32, device=self.device)
+        Z = torch.zeros(max(self.z_offsets[-1], 1), dtype=torch.float64, device=self.device)
+        st = status if status is not None else new_status(self.device)
+        rc = lib().skel_batch_run(self._plan, _ptr(Js), _ptr(ranks), _ptr(Z), _ptr(st), _stream())
+        if rc != 0:
+            raise SkelError(rc, "skel_batch_run")
+        return Js, ranks, Z, st
+
+    def z_block(self, Z, b, rank=None):
+        """Z_b (rank x n_b) as a view of Z_all."""
+        n_b = self.blocks[b][0].shape[1]
+        zb = Z[self.z_offsets[b]:self.z_offsets[b + 1]].view(self.kmax, n_b)
+        return zb if rank is None else zb[:rank]
+
+    def __del__(self):
+        if getattr(self, "_plan", None) and self._plan.value and _lib is not None:
+            _lib.skel_batch_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p()

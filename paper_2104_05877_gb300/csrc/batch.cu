@@ -1,0 +1,702 @@
+// Batched skeletonization of many independent blocks (hierarchical-matrix compression): per
+// block A_b (m_b x n_b, FP32, column-major) the Gaussian sketch X_b = Gamma A_b (Algorithm 2
+// line 2), column LUPP on X_b (Sec. 2.5.2, Algorithm 2 line 3) stopped at the tolerance-driven
+// rank, and the column ID coefficients formed from the sketch alone: with r pivots,
+//   Z_b = X_b(0:r, J)^{-1} X_b(0:r, :) = R_1^{-1} R      (C^+ A ~ X_1^+ X, Sec. 4, ID without a
+// second pass over A), where R is the LUPP factor (r x n_b) and R_1 = R(:, J) is unit upper
+// triangular.  A is read once.
+//
+// Kernels, all launched by skel_batch_run on the caller's stream:
+//   batch_gamma_kernel   the standard normals G (l x m_max, one Gamma for every block: the
+//                        blocks are independent problems and each sees a Gaussian sketch),
+//                        split into TF32 halves G = Ghi + Glo; 2 l m_max floats that stay in L2.
+//   batch_sketch_kernel  one CTA per 128-column tile of a block: tcgen05 kind::tf32 with
+//                        M = 128 columns of A_b (A operand, K-major as A is stored) and
+//                        N = l_pad rows of Gamma (B operand); both operands split into TF32
+//                        halves (A in shared memory as it arrives) and X = Ahi Ghi +
+//                        (Ahi Glo + Alo Ghi) in two TMEM accumulators, so X carries FP32
+//                        accuracy (the interpolation Z inherits the sketch's precision).
+//   batch_lupp_kernel    one cluster of CL in {1, 2, 4} CTAs per block, each CTA holding the
+//                        block's X for n_b/CL columns in shared memory: per step every CTA
+//                        sends its best candidate (with the candidate's full column) and the
+//                        sum of squares of its rows below the step to every CTA through
+//                        distributed shared memory, one cluster barrier, then every CTA
+//                        takes the same decision (stop at the tolerance rank, or the pivot)
+//                        and updates its columns.  R_1 is collected from the winners' columns
+//                        and Z is formed by back substitution in place.
+// The tolerance rule (the paper fixes k): the rank is the smallest t <= k_max with
+//   ||S_t||_F^2 l/(l - t) <= tol^2 ||X||_F^2,
+// S_t the Schur complement (rows t..l-1) after t steps, an unbiased estimate of
+// ||A (I - P_t)||_F^2 >= ||A - C C^+ A||_F^2 (proof of Theorem 1), or k_max.
+#include <cooperative_groups.h>
+#include <cuda.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tcgen05.cuh"
+
+namespace cg = cooperative_groups;
+
+struct skel_batch_plan;
+
+namespace skel {
+
+namespace {
+
+using namespace tc;
+
+struct BatchBlock {
+  const float* A;
+  int64_t lda;
+  int32_t m, n;
+  int64_t xoff;     // X_b at X + xoff (l x n_b row-major)
+  int64_t zoff;     // Z_b at Z + zoff (k_max x n_b row-major)
+};
+struct SketchItem {
+  int32_t b, tile;
+};
+
+// ---------------------------------------------------------------------------------------
+// Gamma halves
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__global__ void batch_gamma_kernel(int l, int lp, int64_t mg, uint32_t k0, uint32_t k1, float* Ghi, float* Glo) {
+  const int64_t m4 = mg / 4;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)lp * m4;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / m4);
+    const int64_t j4 = e % m4;
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < l) g = gaussian4_f32(k0, k1, (uint32_t)i, (uint32_t)j4);
+    const float v[4] = {g.x, g.y, g.z, g.w};
+    float4 h, lo;
+    float* hp = &h.x;
+    float* lp_ = &lo.x;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      hp[q] = tf32_rna(v[q]);
+      lp_[q] = tf32_rna(v[q] - hp[q]);
+    }
+    reinterpret_cast<float4*>(Ghi + (int64_t)i * mg)[j4] = h;
+    reinterpret_cast<float4*>(Glo + (int64_t)i * mg)[j4] = lo;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Sketch: X_b(:, tile) = Gamma A_b(:, tile), 3xTF32
+// ---------------------------------------------------------------------------------------
+constexpr int BS_THREADS = 256;       // warp 0 TMA, 1 MMA, 2 TMEM, 4..7 converters + epilogue
+constexpr int BS_CONV_WARP0 = 4;
+constexpr int BS_BK = 32;
+constexpr uint32_t BS_ATILE = 128 * 128;          // 128 columns x 32 rows of A, FP32
+constexpr uint32_t BS_CORR_COL = 256;             // TMEM column of the correction accumulator
+constexpr uint64_t BS_WAIT_NS = 2000000000ull;
+
+struct BatchSketchParams {
+  const BatchBlock* blocks;
+  const CUtensorMap* tmaps;   // one per block, in global memory (64-byte aligned)
+  const SketchItem* items;
+  float* X;
+  int l, lp, stages;
+  float scale;
+  int32_t* dev_status;
+};
+
+__global__ void __launch_bounds__(BS_THREADS, 1)
+batch_sketch_kernel(const __grid_constant__ CUtensorMap tmGhi, const __grid_constant__ CUtensorMap tmGlo,
+                    const BatchSketchParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int AS = p.stages;
+  const uint32_t g_bytes = (uint32_t)p.lp * 128;
+  const uint32_t stage_bytes = 2 * BS_ATILE + 2 * g_bytes;   // [Ahi][Alo][Ghi][Glo]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + AS * stage_bytes);   // full, conv, empty [AS]; done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * AS + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const SketchItem item = p.items[blockIdx.x];
+  const BatchBlock blk = p.blocks[item.b];
+  const CUtensorMap* tmA = p.tmaps + item.b;
+  const int nk = (blk.m + BS_BK - 1) / BS_BK;
+  auto a_buf = [&](int s) { return smem + s * stage_bytes; };
+  auto alo_buf = [&](int s) { return smem + s * stage_bytes + BS_ATILE; };
+  auto ghi_buf = [&](int s) { return smem + s * stage_bytes + 2 * BS_ATILE; };
+  auto glo_buf = [&](int s) { return smem + s * stage_bytes + 2 * BS_ATILE + g_bytes; };
+  auto full = [&](int s) { return smem_u32(&bars[s]); };
+  auto conv = [&](int s) { return smem_u32(&bars[AS + s]); };
+  auto empty = [&](int s) { return smem_u32(&bars[2 * AS + s]); };
+  const uint32_t done = smem_u32(&bars[3 * AS]);
+
+  if (tid == 0) {
+    for (int s = 0; s < AS; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(conv(s), 4);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(tmem_slot)), "r"(512u) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  auto fail = [&]() {
+    if (atomicExch(abort_flag, 1) == 0) record_error(p.dev_status, SKEL_ERR_TIMEOUT, -2);
+  };
+  auto aborted = [&]() { return *(volatile int*)abort_flag != 0; };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % AS;
+        const uint32_t ph = (uint32_t)(it / AS) & 1u;
+        if (aborted()) break;
+        if (it >= AS && !mbar_wait(empty(s), ph ^ 1u, BS_WAIT_NS)) { fail(); break; }
+        mbar_expect_tx(full(s), BS_ATILE + 2 * g_bytes);
+        const int x = it * BS_BK;
+        tma_load_2d(smem_u32(a_buf(s)), tmA, x, item.tile * 128, full(s));
+        tma_load_2d(smem_u32(ghi_buf(s)), &tmGhi, x, 0, full(s));
+        tma_load_2d(smem_u32(glo_buf(s)), &tmGlo, x, 0, full(s));
+        ++issued;
+      }
+      for (int it = std::max(0, issued - AS); it < issued; ++it)
+        if (!mbar_wait(full(it % AS), (uint32_t)(it / AS) & 1u, BS_WAIT_NS)) fail();
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(128, p.lp);
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % AS;
+        const uint32_t ph = (uint32_t)(it / AS) & 1u;
+        if (aborted()) break;
+        if (!mbar_wait(conv(s), ph, BS_WAIT_NS)) { fail(); break; }
+        tc_fence_after();
+        const uint32_t ahi = smem_u32(a_buf(s)), alo = smem_u32(alo_buf(s));
+        const uint32_t ghi = smem_u32(ghi_buf(s)), glo = smem_u32(glo_buf(s));
+#pragma unroll
+        for (int kk = 0; kk < BS_BK / 8; ++kk) {
+          const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+          mma_tf32(tmem, sw128_desc(ahi + kk * 32), sw128_desc(ghi + kk * 32), idesc, acc);
+          mma_tf32(tmem + BS_CORR_COL, sw128_desc(ahi + kk * 32), sw128_desc(glo + kk * 32), idesc, acc);
+          mma_tf32(tmem + BS_CORR_COL, sw128_desc(alo + kk * 32), sw128_desc(ghi + kk * 32), idesc, 1u);
+        }
+        mma_commit(empty(s));
+      }
+      mma_commit(done);
+    }
+  } else if (warp >= BS_CONV_WARP0) {
+    // converters: A tile -> Ahi in place, Alo beside it (same positions: swizzle-agnostic)
+    const int ct = tid - BS_CONV_WARP0 * 32;          // 0..127
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % AS;
+      const uint32_t ph = (uint32_t)(it / AS) & 1u;
+      if (aborted()) break;
+      if (!mbar_wait(full(s), ph, BS_WAIT_NS)) { fail(); break; }
+      float4* a = reinterpret_cast<float4*>(a_buf(s));
+      float4* lo = reinterpret_cast<float4*>(alo_buf(s));
+#pragma unroll
+      for (int q = 0; q < (int)(BS_ATILE / 16) / 128; ++q) {
+        const int e = ct + 128 * q;
+        const float4 v = a[e];
+        float4 h, w;
+        h.x = tf32_rna(v.x); w.x = tf32_rna(v.x - h.x);
+        h.y = tf32_rna(v.y); w.y = tf32_rna(v.y - h.y);
+        h.z = tf32_rna(v.z); w.z = tf32_rna(v.z - h.z);
+        h.w = tf32_rna(v.w); w.w = tf32_rna(v.w - h.w);
+        a[e] = h;
+        lo[e] = w;
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(conv(s));
+    }
+    // epilogue: lane = column of the tile, TMEM columns = rows of X
+    const bool ok = mbar_wait(done, 0, BS_WAIT_NS);
+    if (!ok) fail();
+    tc_fence_after();
+    if (ok && !aborted()) {
+      const int qd = warp & 3;
+      const int64_t j = (int64_t)item.tile * 128 + qd * 32 + lane;
+      float* xb = p.X + blk.xoff;
+      bool bad = false;
+      for (int c0 = 0; c0 < p.lp; c0 += 32) {
+        uint32_t rm[32], rc[32];
+        TMEM_LD32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)c0, rm);
+        TMEM_LD32(tmem + ((uint32_t)(qd * 32) << 16) + BS_CORR_COL + (uint32_t)c0, rc);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (j < blk.n) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const int i = c0 + q;
+            if (i < p.l) {
+              const float v = (__uint_as_float(rm[q]) + __uint_as_float(rc[q])) * p.scale;
+              bad |= !isfinite(v);
+              xb[(int64_t)i * blk.n + j] = v;
+            }
+          }
+        }
+      }
+      if (bad) record_error(p.dev_status, SKEL_ERR_NONFINITE, -1);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Tolerance-rank LUPP on X_b and Z_b = R_1^{-1} R
+// ---------------------------------------------------------------------------------------
+constexpr int BL_THREADS = 512;
+constexpr int BL_MAXCL = 4;
+constexpr int BL_MAXL = 256;
+constexpr int BL_MAXK = 128;
+
+struct __align__(16) BlSlot {
+  float col[BL_MAXL];     // the candidate's column, rows 0 .. l-1
+  double nu;              // sender's sum of squares of the rows below the step
+  float key;              // |S(t, j)|, -1 when the sender has no candidate
+  int idx;                // global column index, INT_MAX when none
+};
+
+struct BatchLuppParams {
+  const BatchBlock* blocks;
+  const int32_t* order;   // block handled by each cluster
+  const float* X;
+  int l, kmax;
+  double tol2;
+  int32_t* Js;            // nblocks x kmax
+  int32_t* ranks;
+  double* Z;
+  int32_t* dev_status;
+};
+
+__device__ __forceinline__ int bl_ldp(int ncl) { return (ncl & 1) ? ncl : ncl + 1; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLuppParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ BlSlot slot[2][BL_MAXCL];
+  __shared__ int s_J[BL_MAXK];
+  __shared__ float s_piv[BL_MAXK];
+  __shared__ float wkey[BL_THREADS / 32];
+  __shared__ int widx[BL_THREADS / 32];
+  __shared__ double wnu[BL_THREADS / 32];
+  __shared__ double s_nu;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks(), crank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = p.order[blockIdx.x / CL];
+  const BatchBlock blk = p.blocks[b];
+  const int n = blk.n, l = p.l, kmax = p.kmax;
+  const int ncl = (n + CL - 1) / CL;
+  const int c0 = crank * ncl;
+  const int nl = max(0, min(ncl, n - c0));
+  const int ldp = bl_ldp(ncl);
+  float* S = reinterpret_cast<float*>(smem);                 // [l][ldp]
+  float* R1 = S + (size_t)l * ldp;                            // [kmax][kmax], R1[q][t] = R(q, j_t)
+  unsigned char* sel = reinterpret_cast<unsigned char*>(R1 + (size_t)kmax * kmax);   // [ncl]
+  const float* xb = p.X + blk.xoff;
+
+  auto block_sum = [&](double v) {           // in fixed order; result in s_nu
+    v = warp_sum(v);
+    if (lane == 0) wnu[warp] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0;
+      for (int w = 0; w < BL_THREADS / 32; ++w) a += wnu[w];
+      s_nu = a;
+    }
+    __syncthreads();
+  };
+
+  // sums of squares: FP32 per thread (a few hundred terms), FP64 across threads (FP64
+  // arithmetic is scarce on this GPU and these run once per element per step)
+  float nu = 0.f;
+  for (int e = tid; e < l * nl; e += BL_THREADS) {
+    const int r = e / nl, jl = e % nl;
+    const float v = xb[(int64_t)r * n + c0 + jl];
+    S[r * ldp + jl] = v;
+    nu = fmaf(v, v, nu);
+  }
+  for (int jl = tid; jl < nl; jl += BL_THREADS) sel[jl] = 0;
+  block_sum((double)nu);
+
+  double normX2 = 0.0;
+  int rank = 0, code = 0;
+  for (int t = 0;; ++t) {
+    // this CTA's candidate on row t: largest magnitude, ties to the lower column index
+    float key = -1.f;
+    int idx = INT_MAX;
+    for (int jl = tid; jl < nl; jl += BL_THREADS) {
+      if (sel[jl]) continue;
+      const float a = fabsf(S[t * ldp + jl]);
+      const float k = a == a ? a : INFINITY;     // NaN is flagged as non-finite below
+      if (k > key) { key = k; idx = c0 + jl; }
+    }
+    {
+      const unsigned kb = key >= 0.f ? __float_as_uint(key) : 0u;
+      const unsigned m = __reduce_max_sync(0xffffffffu, kb);
+      const unsigned im = __reduce_min_sync(0xffffffffu, kb == m && key >= 0.f ? (unsigned)idx : 0x7fffffffu);
+      if (lane == 0) { wkey[warp] = im == 0x7fffffffu ? -1.f : __uint_as_float(m); widx[warp] = (int)im; }
+      __syncthreads();
+      float k2 = lane < BL_THREADS / 32 ? wkey[lane] : -1.f;
+      int i2 = lane < BL_THREADS / 32 ? widx[lane] : 0x7fffffff;
+      const unsigned kb2 = k2 >= 0.f ? __float_as_uint(k2) : 0u;
+      const unsigned m2 = __reduce_max_sync(0xffffffffu, kb2);
+      const unsigned im2 = __reduce_min_sync(0xffffffffu, kb2 == m2 && k2 >= 0.f ? (unsigned)i2 : 0x7fffffffu);
+      key = im2 == 0x7fffffffu ? -1.f : __uint_as_float(m2);
+      idx = im2 == 0x7fffffffu ? INT_MAX : (int)im2;
+    }
+    // send it (with its whole column and this CTA's sum of squares) to every CTA
+    const int par = t & 1;
+    const bool have = idx != INT_MAX;
+    for (int d = 0; d < CL; ++d) {
+      BlSlot* dst = cluster.map_shared_rank(&slot[par][crank], d);
+      for (int r = tid; r < l; r += BL_THREADS) dst->col[r] = have ? S[r * ldp + (idx - c0)] : 0.f;
+      if (tid == 0) {
+        dst->nu = s_nu;
+        dst->key = key;
+        dst->idx = idx;
+      }
+    }
+    cluster.sync();
+    // the same decision everywhere
+    double nut = 0.0;
+    for (int d = 0; d < CL; ++d) nut += slot[par][d].nu;
+    if (t == 0) normX2 = nut;
+    const double est = nut * (double)l / (double)(l - t);
+    float bk = -1.f;
+    int bi = INT_MAX, o = 0;
+    for (int d = 0; d < CL; ++d) {
+      const float k = slot[par][d].key;
+      const int i = slot[par][d].idx;
+      if (i != INT_MAX && (k > bk || (k == bk && i < bi))) { bk = k; bi = i; o = d; }
+    }
+    if (est <= p.tol2 * normX2 || t >= kmax || bi == INT_MAX || !(bk > 0.f) || !isfinite(bk)) {
+      rank = t;
+      if (bi != INT_MAX && !isfinite(bk)) code = SKEL_ERR_NONFINITE;
+      break;
+    }
+    const float* pc = slot[par][o].col;
+    const float piv = pc[t];
+    if (tid == 0) { s_J[t] = bi; s_piv[t] = piv; }
+    for (int q = tid; q < t; q += BL_THREADS) R1[q * kmax + t] = pc[q] / s_piv[q];
+    // rows t+1 .. l-1 of the local columns: S(r, j) -= S(r, j_t) S(t, j) / pivot
+    float nuloc = 0.f;
+    if (nl > 0) {
+      const int nph = max(1, BL_THREADS / nl);           // threads per column (rows split)
+      for (int e = tid; e < nph * nl; e += BL_THREADS) {
+        const int jl = e % nl, ph = e / nl;
+        if (sel[jl]) continue;
+        const float rv = S[t * ldp + jl] / piv;
+        for (int r = t + 1 + ph; r < l; r += nph) {
+          const float x = __fsub_rn(S[r * ldp + jl], __fmul_rn(pc[r], rv));
+          S[r * ldp + jl] = x;
+          nuloc = fmaf(x, x, nuloc);
+        }
+      }
+    }
+    block_sum((double)nuloc);
+    if (o == crank && tid == 0) sel[bi - c0] = 1;
+    __syncthreads();
+  }
+  // R rows, then Z = R_1^{-1} R by back substitution, in place (local columns)
+  for (int jl = tid; jl < nl; jl += BL_THREADS) {
+    if (sel[jl]) continue;
+    for (int q = 0; q < rank; ++q) S[q * ldp + jl] = S[q * ldp + jl] / s_piv[q];
+    for (int q = rank - 1; q >= 0; --q) {
+      float z = S[q * ldp + jl];
+      for (int q2 = q + 1; q2 < rank; ++q2) z = __fsub_rn(z, __fmul_rn(R1[q * kmax + q2], S[q2 * ldp + jl]));
+      S[q * ldp + jl] = z;
+    }
+  }
+  __syncthreads();
+  for (int q = 0; q < rank; ++q) {                    // selected columns: unit vectors
+    const int j = s_J[q];
+    if (j >= c0 && j < c0 + nl)
+      for (int q2 = tid; q2 < rank; q2 += BL_THREADS) S[q2 * ldp + (j - c0)] = q2 == q ? 1.f : 0.f;
+  }
+  __syncthreads();
+  double* zb = p.Z + blk.zoff;                       // rows >= rank are left untouched
+  for (int e = tid; e < rank * nl; e += BL_THREADS) {
+    const int q = e / nl, jl = e % nl;
+    zb[(int64_t)q * n + c0 + jl] = (double)S[q * ldp + jl];
+  }
+  if (crank == 0) {
+    for (int q = tid; q < kmax; q += BL_THREADS) p.Js[(int64_t)b * kmax + q] = q < rank ? s_J[q] : -1;
+    if (tid == 0) {
+      p.ranks[b] = rank;
+      if (code) record_error(p.dev_status, code, b);
+    }
+  }
+}
+
+size_t lupp_smem(int l, int kmax, int ncl) {
+  const int ldp = (ncl & 1) ? ncl : ncl + 1;
+  return sizeof(float) * ((size_t)l * ldp + (size_t)kmax * kmax) + (size_t)ncl;
+}
+
+}  // namespace
+}  // namespace skel
+
+using namespace skel;
+
+struct skel_batch_plan {
+  int nb = 0, kmax = 0, l = 0, lp = 0, stages = 0;
+  double tol = 0.0;
+  uint64_t seed = 0;
+  int64_t mg = 0;                 // Gamma columns (max m_b rounded up to 32)
+  BatchBlock* d_blocks = nullptr;
+  CUtensorMap* d_tmaps = nullptr;
+  SketchItem* d_items = nullptr;
+  int n_items = 0;
+  int32_t* d_order = nullptr;     // blocks grouped by cluster size
+  int cls_count[3] = {0, 0, 0}, cls_off[3] = {0, 0, 0};
+  size_t cls_smem[3] = {0, 0, 0};
+  float* d_ghi = nullptr;
+  float* d_glo = nullptr;
+  CUtensorMap tm_ghi, tm_glo;
+  float* d_X = nullptr;
+  std::vector<int64_t> zoff;      // nb + 1 prefix offsets of Z (doubles)
+  size_t sketch_smem = 0;
+};
+
+namespace {
+
+void plan_free(skel_batch_plan* pl) {
+  if (!pl) return;
+  cudaFree(pl->d_blocks);
+  cudaFree(pl->d_tmaps);
+  cudaFree(pl->d_items);
+  cudaFree(pl->d_order);
+  cudaFree(pl->d_ghi);
+  cudaFree(pl->d_glo);
+  cudaFree(pl->d_X);
+  delete pl;
+}
+
+size_t lupp_budget() {
+  static size_t budget = 0;
+  if (!budget) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, batch_lupp_kernel) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    budget = 227 * 1024 - fa.sharedSizeBytes - 256;
+  }
+  return budget;
+}
+
+}  // namespace
+
+extern "C" {
+
+skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int64_t* n, const float* const* A,
+                                   const int64_t* lda, int32_t kmax, int32_t p, double tol, uint64_t seed,
+                                   skel_batch_plan** plan) {
+  if (plan == nullptr) return SKEL_ERR_INVALID_ARG;
+  *plan = nullptr;
+  if (nblocks < 1 || m == nullptr || n == nullptr || A == nullptr || lda == nullptr) return SKEL_ERR_INVALID_ARG;
+  if (kmax < 1 || kmax > BL_MAXK || p < 1 || kmax + p > BL_MAXL || !(tol >= 0.0) || !std::isfinite(tol))
+    return SKEL_ERR_INVALID_ARG;
+  const int l = kmax + p, lp = (l + 15) / 16 * 16;
+  const size_t budget = lupp_budget();
+  if (budget == 0) return SKEL_ERR_CUDA;
+  int64_t mmax = 0;
+  std::vector<int> cls(nblocks);
+  for (int b = 0; b < nblocks; ++b) {
+    if (m[b] < 1 || n[b] < 1 || m[b] > INT32_MAX || n[b] > INT32_MAX || lda[b] < m[b] || A[b] == nullptr)
+      return SKEL_ERR_INVALID_ARG;
+    if (lda[b] % 4 != 0 || (reinterpret_cast<uintptr_t>(A[b]) & 15) != 0) return SKEL_ERR_UNSUPPORTED;
+    mmax = std::max(mmax, m[b]);
+    int c = 0;
+    while (c < 3 && lupp_smem(l, kmax, (int)((n[b] + (1 << c) - 1) >> c)) > budget) ++c;
+    if (c == 3) return SKEL_ERR_UNSUPPORTED;       // wider than four CTAs' shared memory
+    cls[b] = c;
+  }
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return SKEL_ERR_UNSUPPORTED;
+  skel_batch_plan* pl = new (std::nothrow) skel_batch_plan();
+  if (!pl) return SKEL_ERR_WORKSPACE;
+  pl->nb = nblocks;
+  pl->kmax = kmax;
+  pl->l = l;
+  pl->lp = lp;
+  pl->tol = tol;
+  pl->seed = seed;
+  pl->mg = (mmax + 31) / 32 * 32;
+  // shared memory of the sketch: 3 stages when they fit, else 2
+  const size_t stage = 2 * (size_t)BS_ATILE + 2 * (size_t)lp * 128;
+  pl->stages = 1024 + 3 * stage + 256 <= 227 * 1024 ? 3 : 2;
+  pl->sketch_smem = 1024 + pl->stages * stage + 256;
+
+  std::vector<BatchBlock> hb(nblocks);
+  std::vector<CUtensorMap> ht(nblocks);
+  std::vector<SketchItem> items;
+  pl->zoff.assign(nblocks + 1, 0);
+  int64_t xo = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    hb[b] = BatchBlock{A[b], lda[b], (int32_t)m[b], (int32_t)n[b], xo, pl->zoff[b]};
+    xo += (int64_t)l * n[b];
+    pl->zoff[b + 1] = pl->zoff[b] + (int64_t)kmax * n[b];
+    const cuuint64_t gdim[2] = {(cuuint64_t)m[b], (cuuint64_t)n[b]};
+    const cuuint64_t gstride[1] = {(cuuint64_t)lda[b] * sizeof(float)};
+    const cuuint32_t box[2] = {BS_BK, 128};
+    const cuuint32_t es[2] = {1, 1};
+    if (enc(&ht[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A[b]), gdim, gstride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+      plan_free(pl);
+      return SKEL_ERR_UNSUPPORTED;
+    }
+    for (int t = 0; t < (int)((n[b] + 127) / 128); ++t) items.push_back(SketchItem{b, t});
+  }
+  // longest work first
+  std::stable_sort(items.begin(), items.end(), [&](const SketchItem& a, const SketchItem& c) { return m[a.b] > m[c.b]; });
+  pl->n_items = (int)items.size();
+  std::vector<int32_t> order;
+  for (int c = 0; c < 3; ++c) {
+    pl->cls_off[c] = (int)order.size();
+    std::vector<int32_t> v;
+    for (int b = 0; b < nblocks; ++b)
+      if (cls[b] == c) v.push_back(b);
+    std::stable_sort(v.begin(), v.end(), [&](int a, int d) { return n[a] > n[d]; });
+    for (int b : v) {
+      order.push_back(b);
+      pl->cls_smem[c] = std::max(pl->cls_smem[c], lupp_smem(l, kmax, (int)((n[b] + (1 << c) - 1) >> c)));
+    }
+    pl->cls_count[c] = (int)v.size();
+  }
+  bool ok = cudaMalloc(&pl->d_blocks, sizeof(BatchBlock) * nblocks) == cudaSuccess &&
+            cudaMalloc(&pl->d_tmaps, sizeof(CUtensorMap) * nblocks) == cudaSuccess &&
+            cudaMalloc(&pl->d_items, sizeof(SketchItem) * items.size()) == cudaSuccess &&
+            cudaMalloc(&pl->d_order, sizeof(int32_t) * order.size()) == cudaSuccess &&
+            cudaMalloc(&pl->d_ghi, sizeof(float) * (size_t)lp * pl->mg) == cudaSuccess &&
+            cudaMalloc(&pl->d_glo, sizeof(float) * (size_t)lp * pl->mg) == cudaSuccess &&
+            cudaMalloc(&pl->d_X, sizeof(float) * (size_t)std::max<int64_t>(xo, 1)) == cudaSuccess;
+  ok = ok && cudaMemcpy(pl->d_blocks, hb.data(), sizeof(BatchBlock) * nblocks, cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(pl->d_tmaps, ht.data(), sizeof(CUtensorMap) * nblocks, cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(pl->d_items, items.data(), sizeof(SketchItem) * items.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(pl->d_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (ok) {
+    const cuuint64_t gdim[2] = {(cuuint64_t)pl->mg, (cuuint64_t)lp};
+    const cuuint64_t gstride[1] = {(cuuint64_t)pl->mg * sizeof(float)};
+    const cuuint32_t box[2] = {BS_BK, (cuuint32_t)lp};
+    const cuuint32_t es[2] = {1, 1};
+    ok = enc(&pl->tm_ghi, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pl->d_ghi, gdim, gstride, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
+         enc(&pl->tm_glo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pl->d_glo, gdim, gstride, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  }
+  ok = ok && cudaFuncSetAttribute(batch_sketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)pl->sketch_smem) == cudaSuccess &&
+       cudaFuncSetAttribute(batch_lupp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    plan_free(pl);
+    return SKEL_ERR_CUDA;
+  }
+  *plan = pl;
+  return SKEL_OK;
+}
+
+skel_status skel_batch_z_offsets(const skel_batch_plan* plan, int64_t* offsets) {
+  if (plan == nullptr || offsets == nullptr) return SKEL_ERR_INVALID_ARG;
+  std::copy(plan->zoff.begin(), plan->zoff.end(), offsets);
+  return SKEL_OK;
+}
+
+skel_status skel_batch_run(skel_batch_plan* plan, int32_t* Js, int32_t* ranks, double* Z, int32_t* dev_status,
+                           cudaStream_t stream) {
+  if (plan == nullptr || Js == nullptr || ranks == nullptr || Z == nullptr) return SKEL_ERR_INVALID_ARG;
+  skel_batch_plan* pl = plan;
+  batch_gamma_kernel<<<std::min<int64_t>(((int64_t)pl->lp * pl->mg / 4 + 255) / 256, 1024), 256, 0, stream>>>(
+      pl->l, pl->lp, pl->mg, (uint32_t)(pl->seed & 0xffffffffu), (uint32_t)(pl->seed >> 32), pl->d_ghi, pl->d_glo);
+  note_launches(1);
+  BatchSketchParams sp{};
+  sp.blocks = pl->d_blocks;
+  sp.tmaps = pl->d_tmaps;
+  sp.items = pl->d_items;
+  sp.X = pl->d_X;
+  sp.l = pl->l;
+  sp.lp = pl->lp;
+  sp.stages = pl->stages;
+  sp.scale = (float)(1.0 / std::sqrt((double)pl->l));
+  sp.dev_status = dev_status;
+  {
+    KernelTimer kt("batch_sketch", stream);
+    batch_sketch_kernel<<<pl->n_items, BS_THREADS, pl->sketch_smem, stream>>>(pl->tm_ghi, pl->tm_glo, sp);
+  }
+  note_launches(1);
+  if (cudaGetLastError() != cudaSuccess) return SKEL_ERR_CUDA;
+  BatchLuppParams lp{};
+  lp.blocks = pl->d_blocks;
+  lp.X = pl->d_X;
+  lp.l = pl->l;
+  lp.kmax = pl->kmax;
+  lp.tol2 = pl->tol * pl->tol;
+  lp.Js = Js;
+  lp.ranks = ranks;
+  lp.Z = Z;
+  lp.dev_status = dev_status;
+  for (int c = 0; c < 3; ++c) {
+    if (pl->cls_count[c] == 0) continue;
+    const int CL = 1 << c;
+    lp.order = pl->d_order + pl->cls_off[c];
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(pl->cls_count[c] * CL));
+    cfg.blockDim = dim3(BL_THREADS);
+    cfg.dynamicSmemBytes = pl->cls_smem[c];
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    {
+      KernelTimer kt("batch_lupp", stream);
+      e = cudaLaunchKernelEx(&cfg, batch_lupp_kernel, lp);
+    }
+    note_launches(1);
+    if (e != cudaSuccess) return SKEL_ERR_CUDA;
+  }
+  return SKEL_OK;
+}
+
+void skel_batch_plan_destroy(skel_batch_plan* plan) { plan_free(plan); }
+
+}  // extern "C"

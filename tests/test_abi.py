@@ -16,7 +16,7 @@ def _declared():
     for f in os.listdir(os.path.join(ROOT, "include")):
         if f.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", f)).read()
-            names |= set(re.findall(r"^\s*(?:skel_status|const char\*|int)\s+(skel_\w+)\s*\(", txt, re.M))
+            names |= set(re.findall(r"^\s*(?:skel_status|const char\*|int|void|uint64_t)\s+(skel_\w+)\s*\(", txt, re.M))
     return names
 
 

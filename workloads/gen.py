@@ -6,7 +6,7 @@ __all__ = [
     "sigma_config2", "sigma_config5", "config1", "dense_config2", "snn_csc",
     "kahan_type", "separated_columns", "exact_rank", "kernel_blocks",
     "torch_dense_spectrum",
-]
+ "torch_kernel_blocks"]
 
 SEED_BASE = 2104_05877
 
@@ -153,3 +153,26 @@ def torch_dense_spectrum(m, n, sigma, noise_std, seed, device, dtype):
     if noise_std:
         At += noise_std * torch.randn(n, m, generator=g, device=device, dtype=torch.float64)
     return At.to(dtype).t()                  # m x n view, column-major storage
+
+
+def torch_kernel_blocks(nblocks, seed, device, mrange=(64, 1024), nrange=(64, 512), h=0.5, sep=4.0):
+    """Same recipe as kernel_blocks, built with torch on `device` (for the full-size batch).
+    Sizes and cluster directions come from the host generator; each block is FP32, column-major,
+    with a leading dimension rounded up to a multiple of 4 (16-byte aligned columns)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    out = []
+    for _ in range(nblocks):
+        mb = int(rng.integers(mrange[0], mrange[1] + 1))
+        nb = int(rng.integers(nrange[0], nrange[1] + 1))
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        x = torch.rand(mb, 3, generator=g, device=device, dtype=torch.float64)
+        y = torch.rand(nb, 3, generator=g, device=device, dtype=torch.float64) + torch.as_tensor(sep * d, device=device)
+        ld = (mb + 3) // 4 * 4
+        At = torch.zeros(nb, ld, dtype=torch.float32, device=device)
+        At[:, :mb] = torch.exp(-torch.cdist(y, x) ** 2 / (h * h)).to(torch.float32)
+        out.append(At.t()[:mb])
+    return out
