@@ -133,7 +133,7 @@ TIMED_KERNELS = ("sketch_tc", "gemm_tc", "lupp_panel", "lupp_trail", "qr_panel",
                  "gemm_cur", "gemm_eta_h", "gemm_eta_sq", "gemm_simt")
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel at this
 # workload (None where no capture of the current code exists)
-TRAFFIC_PER_LAUNCH = {"sketch_tc": 271.9e6, "gemm_tc": 332.4e6, "lupp_panel": 3.09e6}
+TRAFFIC_PER_LAUNCH = {"sketch_tc": 271.9e6, "gemm_tc": 332.4e6, "lupp_panel": 3.09e6, "qr_panel": 2.15e6}
 
 
 def load_peaks():
