@@ -39,22 +39,28 @@ def _unit_open(x):
 
 def gaussian_normals(l, m, seed):
     """Standard normal matrix G (l x m, FP64) with Gamma = G / sqrt(l)."""
+    return gaussian_normals_rows(np.arange(l), m, seed)
+
+
+def gaussian_normals_rows(rows, m, seed):
+    """Rows `rows` of G (len(rows) x m): the same counters as gaussian_normals, for sampling
+    entries of a large sketch one by one."""
+    rows = np.asarray(rows, dtype=np.uint64)
     m4 = (m + 3) // 4
-    i_idx, j4_idx = np.meshgrid(np.arange(l, dtype=np.uint64),
-                                np.arange(m4, dtype=np.uint64), indexing="ij")
-    ctr = np.zeros((l * m4, 4), dtype=np.uint64)
+    i_idx, j4_idx = np.meshgrid(rows, np.arange(m4, dtype=np.uint64), indexing="ij")
+    ctr = np.zeros((rows.size * m4, 4), dtype=np.uint64)
     ctr[:, 0] = j4_idx.ravel()
     ctr[:, 1] = i_idx.ravel()
     ctr[:, 2] = TAG_GAUSSIAN
-    words = philox4x32(ctr, seed_key(seed)).reshape(l, m4, 4)
-    G = np.empty((l, m4, 4), dtype=np.float64)
+    words = philox4x32(ctr, seed_key(seed)).reshape(rows.size, m4, 4)
+    G = np.empty((rows.size, m4, 4), dtype=np.float64)
     for a in (0, 2):
         u1 = _unit_open(words[:, :, a])
         u2 = _unit_open(words[:, :, a + 1])
         r = np.sqrt(-2.0 * np.log(u1))
         G[:, :, a] = r * np.cos(2.0 * np.pi * u2)
         G[:, :, a + 1] = r * np.sin(2.0 * np.pi * u2)
-    return G.reshape(l, 4 * m4)[:, :m]
+    return G.reshape(rows.size, 4 * m4)[:, :m]
 
 
 def gaussian_embedding(l, m, seed):

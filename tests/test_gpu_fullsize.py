@@ -1,0 +1,139 @@
+"""GPU parity at full size, in the precision and launch configuration bench.py times.
+
+Config 2 (8192 x 8192 FP32, k = 256, l = 272, TF32 sketch): the oracle runs the whole path in
+FP64 on the same A (a few seconds on the host): the device's sketch against the oracle's
+elementwise on samples (TF32 bound), the device's pivots against the oracle's LUPP of the
+device's sketch before the first near-tie at FP32 level, and the ID error within 1.05x of
+the FP64 oracle's.
+
+Config 5 (65536 x 32768 FP32, k = 1024, l = 1100): too large for the oracle end to end, so the
+checks are ones that hold at any size: sampled sketch entries computed one by one by the
+oracle, the LUPP factor's structure (|R| <= 1, R(t, j_t) = 1, X(0:s, J) = L R(:, J)), the first
+two greedy pivots recomputed on the host from the device's sketch, Theorem 1's bound with the
+device's eta and an independently computed rangefinder error, and the ID error against the
+closed-form best rank-k error of the constructed spectrum.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import embedding, pivoting
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel_id(sq):
+    sq = sq.cpu().numpy()
+    return float(np.sqrt(max(sq[0] - sq[1], 0.0) / sq[0]))
+
+
+def test_config2_full_size_against_oracle(skel, dev):
+    m = n = 8192
+    k, p = 256, 16
+    l = k + p
+    seed_A, seed_G = workloads.seed_for(2), workloads.seed_for(2, "gamma")
+    A = workloads.torch_dense_spectrum(m, n, workloads.sigma_config2(n), 1e-6 / np.sqrt(m), seed_A, dev,
+                                       torch.float32)
+    st = skel.new_status(dev)
+    X, _ = skel.sketch(A, l, prec="tf32", seed=seed_G, status=st)
+    Js, _, _, _ = skel.pivot_lupp(X, k, factors=False, status=st)
+    _, sq, _ = skel.column_id(A, Js, status=st)
+    torch.cuda.synchronize()
+    skel.check_status(st)
+    Ah = A.cpu().double().numpy()
+    G = embedding.gaussian_normals(l, m, seed_G)
+    Xo = (G @ Ah) / np.sqrt(l)
+    Xg = X.cpu().double().numpy()
+    # sketch: the TF32 bound on 4096 sampled entries
+    rng = np.random.default_rng(0)
+    ii, jj = rng.integers(0, l, 4096), rng.integers(0, n, 4096)
+    mag = np.einsum("sk,ks->s", np.abs(G[ii]), np.abs(Ah[:, jj])) / np.sqrt(l)
+    assert np.all(np.abs(Xg[ii, jj] - Xo[ii, jj]) <= (2.0 ** -9 + m * 2.0 ** -23) * mag)
+    # pivots: the oracle's LUPP on the device's own sketch (FP64), equal before the first
+    # relative gap below 1e3 FP32 roundings (the TF32 sketch itself moves X by ~1e-3, which
+    # the ID-error comparison below covers)
+    ref = pivoting.lupp_columns(Xg, k)
+    small = np.flatnonzero(ref["gaps"] < 1e3 * 2.0 ** -23)
+    pre = int(small[0]) if small.size else k
+    assert pre >= 16
+    assert np.array_equal(Js.cpu().numpy()[:pre], ref["Js"][:pre])
+    # ID error within 1.05x of the FP64 oracle's (its own sketch and pivots, FP64 QR)
+    C = Ah[:, pivoting.lupp_columns(Xo, k)["Js"]]
+    Q, _ = np.linalg.qr(C)
+    e_or = float(np.sqrt(max(np.sum(Ah ** 2) - np.sum((Q.T @ Ah) ** 2), 0.0) / np.sum(Ah ** 2)))
+    assert _rel_id(sq) <= 1.05 * e_or
+
+
+def test_config5_full_size_properties(skel, dev):
+    m, n = 65536, 32768
+    k, p = 1024, 76
+    l = k + p
+    r_eff = 3300                       # exp(-3300/200) < 1e-7: the spectrum below is the floor
+    seed_A, seed_G = workloads.seed_for(5), workloads.seed_for(5, "gamma")
+    sig = workloads.sigma_config5(r_eff)
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed_A)
+    with torch.no_grad():
+        U, _ = torch.linalg.qr(torch.randn(m, r_eff, generator=g, device=dev))
+        V, _ = torch.linalg.qr(torch.randn(n, r_eff, generator=g, device=dev))
+        At = V @ (U * torch.as_tensor(sig, device=dev, dtype=torch.float32)[None, :]).T   # n x m
+        del U, V
+        At += (1e-7 / np.sqrt(m)) * torch.randn(n, m, generator=g, device=dev)
+        A = At.t()                      # m x n column-major, FP32 (built in FP32 on the device)
+    st = skel.new_status(dev)
+    X, _ = skel.sketch(A, l, prec="tf32", seed=seed_G, status=st)
+    Js, L, R, _ = skel.pivot_lupp(X, k, factors=True, status=st)
+    _, sq, _ = skel.column_id(A, Js, status=st)
+    torch.cuda.synchronize()
+    skel.check_status(st)
+    # sketch entries, one by one
+    rng = np.random.default_rng(1)
+    ii = np.sort(rng.choice(l, 6, replace=False))
+    Gi = embedding.gaussian_normals_rows(ii, m, seed_G)
+    Xc = X.cpu()
+    for j in rng.integers(0, n, 24):
+        a = A[:, j].double().cpu().numpy()
+        want = Gi @ a / np.sqrt(l)
+        mag = np.abs(Gi) @ np.abs(a) / np.sqrt(l)
+        got = Xc[ii, j].double().numpy()
+        assert np.all(np.abs(got - want) <= (2.0 ** -9 + m * 2.0 ** -23) * mag)
+    # LUPP factor structure
+    J = Js.cpu().numpy()
+    assert len(set(J.tolist())) == k and J.min() >= 0 and J.max() < n
+    Rh = R.cpu().double().numpy()
+    assert np.abs(Rh).max() <= 1.0 + 1e-6
+    assert np.all(Rh[np.arange(k), J] == 1.0)
+    Xs = Xc[:k].double().numpy()
+    Lh = L.cpu().double().numpy()
+    assert np.linalg.norm(Xs[:, J] - Lh @ Rh[:, J]) <= 1e-4 * np.linalg.norm(Xs[:, J])
+    # the first two greedy pivots, recomputed from the device's sketch
+    x0 = Xc[0].double().numpy()
+    assert J[0] == int(np.argmax(np.abs(x0)))
+    s1 = Xc[1].double().numpy() - (Xc[1, J[0]].item() / x0[J[0]]) * x0
+    s1[J[0]] = 0.0
+    top = np.sort(np.abs(s1))[-2:]
+    if (top[1] - top[0]) / top[1] > 1e-4:
+        assert J[1] == int(np.argmax(np.abs(s1)))
+    # Theorem 1: ||A - C C^+ A||_F <= eta ||A - A Xt^+ Xt||_F with Xt = R (the same row space
+    # as X(0:k, :)); eta from the device (skel_error), the rangefinder error from an
+    # orthonormal basis of R's rows (torch QR in FP64, A Q in FP32 without TF32)
+    e, st2 = skel.error(A, Js, Rf=R)
+    skel.check_status(st2)
+    eta = float(e[3])
+    tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        Q, _ = torch.linalg.qr(R.t().double())
+        AQ = A @ Q.float()
+        nA2 = float(e[0]) ** 2
+        e_rf = np.sqrt(max(nA2 - float((AQ.double() ** 2).sum()), 0.0))
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+    e_abs = _rel_id(sq) * np.sqrt(float(sq[0]))
+    assert e_abs <= 1.05 * eta * e_rf, (e_abs, eta, e_rf)
+    # and the ID error is within a small factor of the best rank-k error (closed form)
+    tail = np.sum(sig[k:] ** 2) + (1e-7) ** 2 * n
+    best = np.sqrt(tail / (np.sum(sig ** 2) + (1e-7) ** 2 * n))
+    assert _rel_id(sq) <= 5.0 * best

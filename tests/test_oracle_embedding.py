@@ -116,3 +116,10 @@ def test_sketch_scale_preserves_norms_in_expectation():
     nA = np.sum(A ** 2)
     assert abs(np.mean(vals_g) / nA - 1) < 0.05
     assert abs(np.mean(vals_s) / nA - 1) < 0.05
+
+
+def test_gaussian_rows_subset_matches_full():
+    """The row-sampling generator reproduces the full generator's rows bit for bit."""
+    G = embedding.gaussian_normals(40, 301, 9)
+    rows = [0, 7, 39, 12]
+    assert np.array_equal(embedding.gaussian_normals_rows(rows, 301, 9), G[rows])
