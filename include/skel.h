@@ -110,6 +110,23 @@ skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dt
                              int32_t* dev_status, cudaStream_t stream);
 
 /*
+ * skel_sketch_power -- row space approximator with q plain power iterations (Sec. 3,
+ * Eq. (def_power_iter); Rand-LUPP-1piter of Sec. 5 is q = 1):
+ *     X = Omega (A^T A)^q,   Omega l x n Gaussian with N(0, 1/l) entries,
+ * formed as X = (Omega A^T) A, then q - 1 times X <- (X A^T) A, without orthogonalisation
+ * (the plain form the paper times; it loses accuracy for ill-conditioned A when q > 1).
+ * Omega's counters are those of the Gaussian embedding with n in place of m (column j of
+ * Omega pairs with column j of A).  1 <= q <= 8.
+ *   prec: SKEL_PREC_F64 (a_dtype F64, FP64 throughout), SKEL_PREC_F32 or SKEL_PREC_TF32
+ *   (a_dtype F32; Omega A^T on the FP32 SIMT path, (.) A on the tensor cores with FP32
+ *   accuracy (3xTF32) when A is TMA-addressable, else FP32 SIMT).  X: l x n row-major.
+ * Two passes over A per iteration; workspace l m words plus GEMM scratch (handshake).
+ */
+skel_status skel_sketch_power(int64_t m, int64_t n, skel_dtype a_dtype, const void* A, int64_t lda, int32_t l,
+                              int32_t q, skel_prec prec, uint64_t seed, void* X, int64_t ldx, void* ws,
+                              size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream);
+
+/*
  * skel_sketch_csc -- X = Gamma A for a sparse A in compressed sparse column form (Table 1,
  * T_s = O(nnz(A) zeta) for the sparse sign embedding).
  *   col_ptr[n+1] (int64), row_idx[nnz] (int32, any order within a column), val[nnz] (FP32).
@@ -231,6 +248,19 @@ skel_status skel_error(int64_t m, int64_t n, skel_dtype dtype, const void* A, in
                        const int32_t* Is, const double* U, int64_t ldu, skel_dtype rf_dtype,
                        const void* Rf, int64_t ldrf, double* out, void* ws, size_t* ws_bytes,
                        int32_t* dev_status, cudaStream_t stream);
+
+/*
+ * skel_id_sketch -- column ID coefficients from the sketch alone, without a second pass over
+ * A (Sec. 4: C^+ A ~ X_1^+ X with X_1 = X(:, J_s)), taken on the first s rows of X, whose
+ * greedy pivots are J_s: Z = X(0:s, J)^{-1} X(0:s, :) = R_1^{-1} R with R the s x n LUPP factor
+ * of skel_pivot_lupp (row-major, ldr >= n, dtype FP32 or FP64) and R_1 = R(:, J) its unit upper
+ * triangular pivot columns.  Z: s x n row-major FP64 (ldz >= n), Z(:, J) = I.  Workspace
+ * 8 s^2 bytes (handshake as elsewhere).  Less accurate than skel_id (the sketch's precision
+ * and conditioning enter Z); A is not read.
+ */
+skel_status skel_id_sketch(skel_dtype dtype, int32_t s, int64_t n, const void* R, int64_t ldr,
+                           const int32_t* Js, double* Z, int64_t ldz, void* ws, size_t* ws_bytes,
+                           int32_t* dev_status, cudaStream_t stream);
 
 /*
  * Batched skeletonization of many independent blocks (hierarchical-matrix compression; the

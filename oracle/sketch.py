@@ -65,3 +65,15 @@ def sparse_sign_sketch(A, l, zeta, seed):
     Gam = sp.csr_matrix((signs.ravel() / np.sqrt(zeta), (rows.ravel(), cols)), shape=(l, m))
     X = Gam @ A
     return np.asarray(X.todense() if sp.issparse(X) else X, dtype=np.float64)
+
+
+def gaussian_sketch_power(A, l, seed, q=1):
+    """Row space approximator with q plain power iterations (Sec. 3, Eq. (def_power_iter)):
+    X = Omega (A^T A)^q with Omega (l x n) Gaussian N(0, 1/l), the counters of the Gaussian
+    embedding over n columns; evaluated as (Omega A^T) A, then (X A^T) A."""
+    A = np.asarray(A, dtype=np.float64)
+    Om = embedding.gaussian_normals(l, A.shape[1], seed) / np.sqrt(l)
+    X = Om
+    for _ in range(q):
+        X = (X @ A.T) @ A
+    return X

@@ -53,6 +53,8 @@ def lib():
         "skel_pivot_rows": [i64, i64, i32, vp, i64, i32, vp, vp, vp, szp, vp, vp],
         "skel_error": [i64, i64, i32, vp, i64, i32, vp, vp, i64, vp, vp, i64, i32, vp, i64, vp, vp,
                        szp, vp, vp],
+        "skel_id_sketch": [i32, i32, i64, vp, i64, vp, vp, i64, vp, szp, vp, vp],
+        "skel_sketch_power": [i64, i64, i32, vp, i64, i32, i32, i32, u64, vp, i64, vp, szp, vp, vp],
         "skel_debug_gaussian": [i32, i64, u64, ctypes.c_int, vp, vp],
         "skel_debug_philox": [vp, i64, u32, u32, vp, vp],
         "skel_debug_curand_philox": [u64, i64, ctypes.c_int, vp, vp],
@@ -169,6 +171,23 @@ def sketch(A, l, kind="gaussian", prec="f32", seed=0, zeta=8, X=None, status=Non
     return X, st
 
 
+def sketch_power(A, l, q=1, prec="tf32", seed=0, status=None):
+    """X = Omega (A^T A)^q (l x n row-major), Omega l x n Gaussian: the power-iterated row space
+    approximator (q = 1: Rand-LUPP-1piter)."""
+    A, lda = _colmajor(A)
+    m, n = A.shape
+    if prec in ("tf32", "f32") and (lda % 4 or A.data_ptr() % 16):
+        ld4 = (m + 3) // 4 * 4
+        Ap = torch.empty(n, ld4, dtype=A.dtype, device=A.device).t()
+        Ap[:m].copy_(A)
+        A, lda = Ap[:m], ld4
+    X = torch.empty(l, n, dtype=torch.float64 if prec == "f64" else torch.float32, device=A.device)
+    st = status if status is not None else new_status(A.device)
+    _call("skel_sketch_power", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, l, q, PREC[prec], seed, _ptr(X), n, w,
+                                              sz, _ptr(st), _stream()], A.device)
+    return X, st
+
+
 def sketch_csc(col_ptr, row_idx, val, m, n, l, kind="sparse_sign", seed=0, zeta=8, status=None):
     X = torch.empty(l, n, dtype=torch.float32, device=val.device)
     st = status if status is not None else new_status(val.device)
@@ -225,6 +244,18 @@ def column_id(A, Js, status=None):
     _call("skel_id", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, s, _ptr(Js), _ptr(Z), n, _ptr(sq), w,
                                     sz, _ptr(st), _stream()], A.device)
     return Z, sq, st
+
+
+def column_id_sketch(R, Js, status=None):
+    """Z = R(:, Js)^{-1} R (s x n FP64) from the LUPP factor R of the sketch: the column ID
+    formed from the sketch alone (no pass over A)."""
+    R, ldr = _rowmajor(R)
+    s, n = R.shape
+    Z = torch.empty(s, n, dtype=torch.float64, device=R.device)
+    st = status if status is not None else new_status(R.device)
+    _call("skel_id_sketch", lambda w, sz: [_dt(R), s, n, _ptr(R), ldr, _ptr(Js), _ptr(Z), n, w, sz, _ptr(st),
+                                           _stream()], R.device)
+    return Z, st
 
 
 def pivot_rows(A, Js, status=None):

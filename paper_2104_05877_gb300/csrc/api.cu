@@ -146,6 +146,59 @@ skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dt
   return SKEL_OK;
 }
 
+skel_status skel_sketch_power(int64_t m, int64_t n, skel_dtype a_dtype, const void* A, int64_t lda, int32_t l,
+                              int32_t q, skel_prec prec, uint64_t seed, void* X, int64_t ldx, void* ws,
+                              size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  if (m < 1 || n < 1 || l < 1 || l > 4096 || q < 1 || q > 8 || !valid_dtype(a_dtype) || A == nullptr ||
+      X == nullptr || lda < m || ldx < n || n > 0xFFFFFFFFll)
+    return SKEL_ERR_INVALID_ARG;
+  if (prec != SKEL_PREC_F64 && prec != SKEL_PREC_F32 && prec != SKEL_PREC_TF32) return SKEL_ERR_UNSUPPORTED;
+  if ((prec == SKEL_PREC_F64) != (a_dtype == SKEL_F64)) return SKEL_ERR_INVALID_ARG;
+  const bool f64 = prec == SKEL_PREC_F64;
+  const skel_dtype dt = f64 ? SKEL_F64 : SKEL_F32;
+  const bool tcw = !f64 && gemm_tc_usable(m, n, l, nullptr, m, A, lda);
+  Arena ar(ws);
+  void* Yt = ar.take(esize(dt) * (size_t)l * m);                  // Y^T = X_prev A^T, l x m row-major
+  void* kws1 = ar.take(gemm_workspace(l, m, n, f64));
+  void* kws2 = ar.take(tcw ? gemm_tc_workspace(m, n, l) : gemm_workspace(l, n, m, f64));
+  skel_status st;
+  if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+  for (int it = 0; it < q; ++it) {
+    // Y^T = Omega A^T (it = 0, Omega generated in the kernel, N(0, 1/l)) or X A^T
+    GemmArgs a{};
+    a.M = l; a.N = m; a.K = n;
+    a.B = View{A, lda, 1}; a.b_dt = a_dtype;          // B(k, c) = A^T(k, c) = A(c, k)
+    a.out = Yt; a.out_sr = m; a.out_sc = 1; a.out_dt = dt;
+    a.dev_status = dev_status;
+    a.splitk_ws = kws1;
+    if (it == 0) {
+      a.alpha = 1.0 / std::sqrt((double)l);
+      a.seed = seed;
+      SK_CUDA(launch_gemm(a, f64, LEFT_GAUSSIAN, EPI_SKETCH, stream));
+    } else {
+      a.L = View{X, ldx, 1}; a.l_dt = dt;
+      a.alpha = 1.0;
+      SK_CUDA(launch_gemm(a, f64, LEFT_LOAD, EPI_STORE, stream));
+    }
+    // X = Y^T A
+    if (tcw) {
+      SK_CUDA(launch_gemm_tc_tn(m, n, l, static_cast<const float*>(Yt), m, static_cast<const float*>(A), lda,
+                                static_cast<float*>(X), ldx, nullptr, kws2, dev_status, stream));
+    } else {
+      GemmArgs b{};
+      b.M = l; b.N = n; b.K = m;
+      b.L = View{Yt, m, 1}; b.l_dt = dt;
+      b.B = View{A, 1, lda}; b.b_dt = a_dtype;
+      b.out = X; b.out_sr = ldx; b.out_sc = 1; b.out_dt = dt;
+      b.alpha = 1.0;
+      b.dev_status = dev_status;
+      b.splitk_ws = kws2;
+      SK_CUDA(launch_gemm(b, f64, LEFT_LOAD, EPI_STORE, stream));
+    }
+  }
+  return SKEL_OK;
+}
+
 skel_status skel_sketch_csc(int64_t m, int64_t n, int64_t nnz, const int64_t* col_ptr,
                             const int32_t* row_idx, const float* val, int32_t l,
                             skel_sketch_kind kind, int32_t zeta, uint64_t seed, float* X,
@@ -370,6 +423,23 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
     SK_CUDA(launch_trsm_upper(s, s, Rr, s, 0, SKEL_F64, T2, s, T1, s, stream));
     SK_CUDA(launch_transpose_f64(s, T1, s, U, ldu, stream));
   }
+  return SKEL_OK;
+}
+
+skel_status skel_id_sketch(skel_dtype dtype, int32_t s, int64_t n, const void* R, int64_t ldr,
+                           const int32_t* Js, double* Z, int64_t ldz, void* ws, size_t* ws_bytes,
+                           int32_t* dev_status, cudaStream_t stream) {
+  (void)dev_status;
+  if (!valid_dtype(dtype) || s < 1 || s > kMaxS || n < s || R == nullptr || Js == nullptr || Z == nullptr ||
+      ldr < n || ldz < n)
+    return SKEL_ERR_INVALID_ARG;
+  Arena ar(ws);
+  double* R1 = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
+  skel_status st;
+  if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+  SK_CUDA(launch_gather_cols_rowmajor_f64(s, dtype, R, ldr, Js, R1, s, stream));   // R1(r, t) = R(r, j_t)
+  SK_CUDA(launch_trsm_upper(s, n, R1, s, 1, dtype, R, ldr, Z, ldz, stream));        // Z = R1^{-1} R
+  SK_CUDA(launch_unit_columns(s, Js, Z, ldz, stream));                              // Z(:, J) = I exactly
   return SKEL_OK;
 }
 

@@ -317,6 +317,15 @@ __global__ void syrk_ff_reduce_kernel(int s, int P, const double* part, double* 
   }
 }
 
+// Z(r, Js[t]) = (r == t) for an s x ? row-major FP64 Z: the interpolation's identity columns.
+__global__ void unit_columns_kernel(int32_t s, const int32_t* Js, double* Z, int64_t ldz) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)s * s;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / s), t = (int)(e % s);
+    Z[(int64_t)r * ldz + Js[t]] = r == t ? 1.0 : 0.0;
+  }
+}
+
 // ------------------------------------------------------------------------------------
 __global__ void reduce_sum_kernel(const double* p, int64_t count, double* out, int take_sqrt) {
   double v = 0.0;
@@ -469,6 +478,12 @@ cudaError_t launch_syrk_ff(int32_t s, int64_t n, const float* R, int64_t ldr, do
   syrk_ff_reduce_kernel<<<(unsigned)std::min<int64_t>(((int64_t)s * s + 255) / 256, 1024), 256, 0, st>>>(s, P, part,
                                                                                                           H, ldh);
   note_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unit_columns(int32_t s, const int32_t* Js, double* Z, int64_t ldz, cudaStream_t st) {
+  unit_columns_kernel<<<(unsigned)std::min<int64_t>(((int64_t)s * s + 255) / 256, 1024), 256, 0, st>>>(s, Js, Z, ldz);
+  note_launches(1);
   return cudaGetLastError();
 }
 

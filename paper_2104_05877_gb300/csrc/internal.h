@@ -52,6 +52,8 @@ cudaError_t launch_gemm(const GemmArgs& a, bool f64, GemmLeft left, GemmEpi epi,
 size_t syrk_ff_workspace(int32_t s, int64_t n);
 cudaError_t launch_syrk_ff(int32_t s, int64_t n, const float* R, int64_t ldr, double* H, int64_t ldh, void* ws,
                            cudaStream_t st);
+// Z(r, Js[t]) = delta(r, t) for an s x ? row-major FP64 Z.
+cudaError_t launch_unit_columns(int32_t s, const int32_t* Js, double* Z, int64_t ldz, cudaStream_t st);
 // Sum `count` doubles in `partials` (deterministic) into *out (device), optionally sqrt.
 cudaError_t launch_reduce_sum(const double* partials, int64_t count, double* out, int take_sqrt,
                               cudaStream_t st);

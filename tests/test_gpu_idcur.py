@@ -143,3 +143,26 @@ def test_eta_from_fp32_rfactor(skel, dev):
                          torch.from_numpy(Js.astype(np.int32)).to(dev), Rf=torch.from_numpy(R32).to(dev))
     skel.check_status(st)
     assert out.cpu().numpy()[3] == pytest.approx(errors.eta(R32.astype(np.float64), Js), rel=1e-8)
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_column_id_from_sketch(skel, dev, dt):
+    """Z = X(0:s, J)^{-1} X(0:s, :) from the device's LUPP factor (skel_id_sketch) against the
+    oracle's definition on the same sketch: Z(:, J) = I exactly, the rest within the
+    precision of R; and the ID from the sketch is never better than C^+ A."""
+    A = workloads.dense_config2(600, 400, seed=12, dtype=np.float64)
+    k, l = 30, 40
+    X = sketch.gaussian_sketch(A, l, 5).astype(dt)
+    Xt = torch.from_numpy(X).to(dev)
+    Js, _, Rf, st = skel.pivot_lupp(Xt, k)
+    skel.check_status(st)
+    Z, st = skel.column_id_sketch(Rf, Js)
+    skel.check_status(st)
+    J = Js.cpu().numpy()
+    want = decomp.sketch_id(X.astype(np.float64), J)
+    got = Z.cpu().numpy()
+    assert np.array_equal(got[:, J], np.eye(k))
+    tol = 1e-9 if dt == np.float64 else 2e-3
+    assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want)
+    e_sk = np.linalg.norm(A - A[:, J] @ got)
+    assert e_sk >= np.linalg.norm(A - A[:, J] @ decomp.column_id(A, J)) * (1 - 1e-9)

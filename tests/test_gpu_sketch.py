@@ -222,3 +222,17 @@ def test_sketch_row_blocks_sum_to_the_sketch(skel, dev, prec, kind):
     # and the summed partial sketch still meets the whole sketch's parity bound
     op = {"f64": 0.0, "f32": 0.0, "tf32": 2.0 ** -9, "bf16": 2.0 ** -7}[prec]
     assert np.all(np.abs(got - want) <= (op + 4 * m * u) * mag)
+
+
+@pytest.mark.parametrize("prec,q", [("f64", 1), ("f64", 2), ("f32", 1), ("tf32", 1), ("tf32", 2)])
+def test_sketch_power_iteration(skel, dev, prec, q):
+    """X = Omega (A^T A)^q (Rand-LUPP-1piter for q = 1) against the oracle's definition: FP64
+    to rounding, FP32 paths (SIMT Omega A^T, 3xTF32 or SIMT (.) A) to FP32 accuracy."""
+    m, n, l = 700, 500, 40
+    dt = np.float64 if prec == "f64" else np.float32
+    A = workloads.dense_config2(m, n, seed=31, dtype=dt)
+    X, st = skel.sketch_power(torch.from_numpy(A).to(dev), l, q=q, prec=prec, seed=17)
+    skel.check_status(st)
+    want = sketch.gaussian_sketch_power(A.astype(np.float64), l, 17, q)
+    rel = np.linalg.norm(X.cpu().numpy() - want) / np.linalg.norm(want)
+    assert rel <= (1e-12 if prec == "f64" else 2e-5 * q), rel

@@ -123,3 +123,29 @@ def test_gaussian_rows_subset_matches_full():
     G = embedding.gaussian_normals(40, 301, 9)
     rows = [0, 7, 39, 12]
     assert np.array_equal(embedding.gaussian_normals_rows(rows, 301, 9), G[rows])
+
+
+def test_power_sketch_through_the_svd():
+    """X = Omega (A^T A)^q equals Omega V diag(sigma^(2q)) V^T for A = U diag(sigma) V^T (the
+    plain power iteration of Sec. 3 written through the SVD factors), q = 1, 2."""
+    rng = np.random.default_rng(3)
+    m, n, r = 120, 80, 30
+    U, _ = np.linalg.qr(rng.standard_normal((m, r)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    sig = 0.9 ** np.arange(r)
+    A = (U * sig) @ V.T
+    Om = embedding.gaussian_normals(12, n, 4) / np.sqrt(12)
+    for q in (1, 2):
+        want = (Om @ V) * sig ** (2 * q) @ V.T
+        assert np.allclose(sketch.gaussian_sketch_power(A, 12, 4, q), want, rtol=0, atol=1e-12)
+
+
+def test_power_sketch_improves_the_rangefinder_on_a_flat_spectrum():
+    """One plain power iteration lowers the rangefinder error ||A - A X^+ X|| on a slowly
+    decaying spectrum (the paper's observation for Rand-LUPP-1piter), on average over seeds."""
+    from oracle import errors
+    import workloads
+    A = workloads.dense_spectrum(300, 200, 1.0 / np.sqrt(np.arange(1, 201)), 0.0, seed=9)
+    plain = np.mean([errors.rangefinder_error(A, sketch.gaussian_sketch(A, 20, s)) for s in range(8)])
+    power = np.mean([errors.rangefinder_error(A, sketch.gaussian_sketch_power(A, 20, s, 1)) for s in range(8)])
+    assert power < 0.9 * plain
