@@ -357,7 +357,9 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
     const T lnext = more && !blk_end ? lcol[q + 1] : T(0);
     T key = T(-1);
     int idx = INT_MAX;
-    // R(t, :) replaces row q of P (row q is final at step q); row q+1 is updated and scanned
+    // R(t, :) replaces row q of P (row q is final at step q) and goes to global memory; row q+1
+    // is updated and scanned
+    T* Rg = p.R + (int64_t)t * p.ldr + c0;
     for (int jj = tid; jj < nl; jj += bd) {
       T* pq = &P[q * ldp + jj];
       T rv;
@@ -384,6 +386,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
         }
       }
       *pq = rv;
+      Rg[jj] = rv;
     }
     int jb = -1;                          // the sent column: warp 0 updates it
     if (more) {
@@ -422,9 +425,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
     done = q + 1;
   }
   __syncthreads();
-  // write out what the completed steps produced: R rows, selected flags, pivots
-  for (int q = 0; q < done; ++q)
-    for (int jj = tid; jj < nl; jj += bd) p.R[(int64_t)(p.t0 + q) * p.ldr + c0 + jj] = P[q * ldp + jj];
+  // write out the selected flags and pivots (the R rows went out at their steps)
   for (int jj = tid; jj < nl; jj += bd) p.sel[c0 + jj] = sl[jj];
   if (crank == 0)
     for (int q = tid; q < done; q += bd) p.Js[p.t0 + q] = s_J[q];
@@ -434,12 +435,22 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
   // step-by-step elimination.  R(panel, J_panel) is read from the owners' shared memory.
   cluster.sync();     // every CTA's R rows are final in its shared memory
   const bool trail = !stopped && done == b && p.s - p.t0 - b > 0;
-  if (trail) {
-    for (int e = tid; e < b * b; e += bd) {
-      const int qq = e / b, q = e % b;
-      const int j = s_J[q];
-      const int o = j / ncl;
-      RJ[e] = cluster.map_shared_rank(P, o)[qq * ldp + (j - o * ncl)];
+  if (trail) {                         // eight distributed-shared-memory loads in flight per thread
+    for (int e0 = tid; e0 < b * b; e0 += 8 * bd) {
+      T v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * bd;
+        if (e < b * b) {
+          const int qq = e / b, q = e % b;
+          const int j = s_J[q];
+          const int o = j / ncl;
+          v[u] = cluster.map_shared_rank(P, o)[qq * ldp + (j - o * ncl)];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (e0 + u * bd < b * b) RJ[e0 + u * bd] = v[u];
     }
   }
   cluster.sync();     // no CTA leaves or reuses its shared memory while others read it
