@@ -276,7 +276,7 @@ constexpr int BL_MAXK = 128;
 
 struct __align__(16) BlSlot {
   float col[BL_MAXL];     // the candidate's column, rows 0 .. l-1
-  double nu;              // sender's sum of squares of the rows below the step
+  float nu;               // sender's sum of squares of the rows below the step
   float key;              // |S(t, j)|, -1 when the sender has no candidate
   int idx;                // global column index, INT_MAX when none
 };
@@ -286,7 +286,7 @@ struct BatchLuppParams {
   const int32_t* order;   // block handled by each cluster
   const float* X;
   int l, kmax;
-  double tol2;
+  float tol2;
   int32_t* Js;            // nblocks x kmax
   int32_t* ranks;
   double* Z;
@@ -295,11 +295,19 @@ struct BatchLuppParams {
 
 __device__ __forceinline__ int bl_ldp(int ncl) { return (ncl & 1) ? ncl : ncl + 1; }
 
-__device__ __forceinline__ double warp_sum(double v) {
+__device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
+
+// The per-step decision, taken by one thread and read by all after a CTA barrier.  Sums of
+// squares have no cancellation, so FP32 carries them; the rule is tested without a division:
+//   nu_t l <= tol^2 ||X||^2 (l - t).
+struct BlDecision {
+  float normX2;
+  int stop, bi, o, code;
+};
 
 __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLuppParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -308,8 +316,9 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
   __shared__ float s_piv[BL_MAXK];
   __shared__ float wkey[BL_THREADS / 32];
   __shared__ int widx[BL_THREADS / 32];
-  __shared__ double wnu[BL_THREADS / 32];
-  __shared__ double s_nu;
+  __shared__ float wnu[BL_THREADS / 32];
+  __shared__ float s_nu;
+  __shared__ BlDecision s_dec;
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks(), crank = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -325,12 +334,12 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
   unsigned char* sel = reinterpret_cast<unsigned char*>(R1 + (size_t)kmax * kmax);   // [ncl]
   const float* xb = p.X + blk.xoff;
 
-  auto block_sum = [&](double v) {           // in fixed order; result in s_nu
+  auto block_sum = [&](float v) {            // in fixed order; result in s_nu
     v = warp_sum(v);
     if (lane == 0) wnu[warp] = v;
     __syncthreads();
     if (tid == 0) {
-      double a = 0.0;
+      float a = 0.f;
       for (int w = 0; w < BL_THREADS / 32; ++w) a += wnu[w];
       s_nu = a;
     }
@@ -347,9 +356,8 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
     nu = fmaf(v, v, nu);
   }
   for (int jl = tid; jl < nl; jl += BL_THREADS) sel[jl] = 0;
-  block_sum((double)nu);
+  block_sum(nu);
 
-  double normX2 = 0.0;
   int rank = 0, code = 0;
   for (int t = 0;; ++t) {
     // this CTA's candidate on row t: largest magnitude, ties to the lower column index
@@ -388,21 +396,29 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
       }
     }
     cluster.sync();
-    // the same decision everywhere
-    double nut = 0.0;
-    for (int d = 0; d < CL; ++d) nut += slot[par][d].nu;
-    if (t == 0) normX2 = nut;
-    const double est = nut * (double)l / (double)(l - t);
-    float bk = -1.f;
-    int bi = INT_MAX, o = 0;
-    for (int d = 0; d < CL; ++d) {
-      const float k = slot[par][d].key;
-      const int i = slot[par][d].idx;
-      if (i != INT_MAX && (k > bk || (k == bk && i < bi))) { bk = k; bi = i; o = d; }
+    // the same decision in every CTA (the same inputs, summed in CTA order)
+    if (tid == 0) {
+      float nut = 0.f;
+      for (int d = 0; d < CL; ++d) nut += slot[par][d].nu;
+      if (t == 0) s_dec.normX2 = nut;
+      float bk = -1.f;
+      int bi = INT_MAX, o = 0;
+      for (int d = 0; d < CL; ++d) {
+        const float k = slot[par][d].key;
+        const int i = slot[par][d].idx;
+        if (i != INT_MAX && (k > bk || (k == bk && i < bi))) { bk = k; bi = i; o = d; }
+      }
+      s_dec.stop = nut * (float)l <= p.tol2 * s_dec.normX2 * (float)(l - t) || t >= kmax || bi == INT_MAX ||
+                   !(bk > 0.f) || !isfinite(bk);
+      s_dec.code = bi != INT_MAX && !isfinite(bk) ? SKEL_ERR_NONFINITE : 0;
+      s_dec.bi = bi;
+      s_dec.o = o;
     }
-    if (est <= p.tol2 * normX2 || t >= kmax || bi == INT_MAX || !(bk > 0.f) || !isfinite(bk)) {
+    __syncthreads();
+    const int bi = s_dec.bi, o = s_dec.o;
+    if (s_dec.stop) {
       rank = t;
-      if (bi != INT_MAX && !isfinite(bk)) code = SKEL_ERR_NONFINITE;
+      code = s_dec.code;
       break;
     }
     const float* pc = slot[par][o].col;
@@ -417,14 +433,27 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
         const int jl = e % nl, ph = e / nl;
         if (sel[jl]) continue;
         const float rv = S[t * ldp + jl] / piv;
-        for (int r = t + 1 + ph; r < l; r += nph) {
-          const float x = __fsub_rn(S[r * ldp + jl], __fmul_rn(pc[r], rv));
-          S[r * ldp + jl] = x;
+        float* col = S + jl;
+        int r = t + 1 + ph;
+        for (; r + 3 * nph < l; r += 4 * nph) {         // four rows' loads in flight
+          float x[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) x[u] = col[(r + u * nph) * ldp];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            x[u] = __fsub_rn(x[u], __fmul_rn(pc[r + u * nph], rv));
+            col[(r + u * nph) * ldp] = x[u];
+            nuloc = fmaf(x[u], x[u], nuloc);
+          }
+        }
+        for (; r < l; r += nph) {
+          const float x = __fsub_rn(col[r * ldp], __fmul_rn(pc[r], rv));
+          col[r * ldp] = x;
           nuloc = fmaf(x, x, nuloc);
         }
       }
     }
-    block_sum((double)nuloc);
+    block_sum(nuloc);
     if (o == crank && tid == 0) sel[bi - c0] = 1;
     __syncthreads();
   }
@@ -665,7 +694,7 @@ skel_status skel_batch_run(skel_batch_plan* plan, int32_t* Js, int32_t* ranks, d
   lp.X = pl->d_X;
   lp.l = pl->l;
   lp.kmax = pl->kmax;
-  lp.tol2 = pl->tol * pl->tol;
+  lp.tol2 = (float)(pl->tol * pl->tol);
   lp.Js = Js;
   lp.ranks = ranks;
   lp.Z = Z;
