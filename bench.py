@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--k", type=int, default=256)
     ap.add_argument("--p", type=int, default=16)
-    ap.add_argument("--prec", default="tf32", choices=["tf32", "bf16", "f32"])
+    ap.add_argument("--prec", default="tf32", choices=["tf32", "bf16", "fp8", "f32"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-GPU comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     ap.add_argument("--only", default=None, choices=["sketch", "lupp", "rows", "id", "cur", "eta", "batch"],
@@ -129,7 +129,7 @@ class ClockSampler:
 
 
 # kernels timed with CUDA events during the timed region
-TIMED_KERNELS = ("sketch_tc", "gemm_tc", "lupp_panel", "lupp_trail", "qr_panel", "qr_wy", "trsm", "gemm_qr",
+TIMED_KERNELS = ("sketch_tc", "sketch_fp8", "fp8_quantize", "gemm_tc", "lupp_panel", "lupp_trail", "qr_panel", "qr_wy", "trsm", "gemm_qr",
                  "gemm_cur", "gemm_eta_h", "gemm_eta_sq", "gemm_simt")
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel at this
 # workload (None where no capture of the current code exists)
@@ -313,6 +313,8 @@ def run_ours(args, rank, world):
     fp64_alu_peak = 1.25                                  # TFLOP/s, nominal FP64
     # Algorithmic work of each timed kernel over one step (bound, work, peak, unit):
     #   sketch_tc   X = Gamma A: 2 l m n TF32 flop (or 4 m n bytes of A if HBM-bound)
+    #   sketch_fp8  X = Gamma8 A8 from the e4m3 copy of A: m n bytes; fp8_quantize reads A and
+    #               writes A8: 5 m n bytes
     #   gemm_tc     W = Q^T A in the ID and the CUR: 2 x 3 (2 k m n) TF32 flop (3 products)
     #   lupp_panel  s greedy steps over n (LUPP on X) and over m (row LUPP on C): the panel
     #               rank-1 updates, sum over panels of b^2 cols (mul + sub)
@@ -327,6 +329,8 @@ def run_ours(args, rank, world):
     models = {
         "sketch_tc": ("tensor", 2.0 * l * m * n / 1e12, tf32_peak, "TFLOP/s")
         if 2.0 * l * m * n / (tf32_peak * 1e12) > a_bytes / (hbm * 1e9) else ("hbm", a_bytes / 1e9, hbm, "GB/s"),
+        "sketch_fp8": ("hbm", m * n / 1e9, hbm, "GB/s"),           # A8: one byte per element
+        "fp8_quantize": ("hbm", 5.0 * m * n / 1e9, hbm, "GB/s"),   # A read (4 B), A8 written (1 B)
         "gemm_tc": ("tensor", 2 * 3 * 2.0 * k * m * n / 1e12, tf32_peak, "TFLOP/s"),
         "lupp_panel": ("alu", lupp_flops / 1e12, fp32_alu_peak, "TFLOP/s"),
         "qr_panel": ("alu", 2.0 * (2 * m + n) * k * k / 1e12, fp32_alu_peak, "TFLOP/s"),

@@ -56,7 +56,9 @@ typedef enum {
   SKEL_PREC_F64 = 0,  /* plain: FP64 operands and accumulation (SIMT DFMA)                */
   SKEL_PREC_F32 = 1,  /* FP32 operands and accumulation (SIMT FFMA)                       */
   SKEL_PREC_TF32 = 2, /* tensor cores (tcgen05 kind::tf32), FP32 accumulate in TMEM       */
-  SKEL_PREC_BF16 = 3  /* tensor cores (tcgen05 kind::f16, bf16 operands), FP32 accumulate */
+  SKEL_PREC_BF16 = 3, /* tensor cores (tcgen05 kind::f16, bf16 operands), FP32 accumulate */
+  SKEL_PREC_FP8 = 4   /* tensor cores (tcgen05 kind::f8f6f4, e4m3 operands; A with a power-of-two
+                         scale per 128 rows of a column), FP32 accumulate                       */
 } skel_prec;
 
 /* embedding Gamma (Sec. 2.3) */
@@ -81,7 +83,7 @@ uint64_t skel_launch_count(void);
  *   prec      : arithmetic of the product (skel_prec).  SKEL_PREC_F64 requires
  *               a_dtype = SKEL_F64 and writes X as FP64; every other precision reads A as
  *               stored and writes X as FP32.  Sparse sign supports F64 and F32 only.  The
- *               tensor-core precisions (TF32, BF16) need a_dtype = SKEL_F32, a 16-byte
+ *               tensor-core precisions (TF32, BF16, FP8) need a_dtype = SKEL_F32, a 16-byte
  *               aligned A and lda a multiple of 4 (A is streamed by TMA); otherwise they
  *               return SKEL_ERR_UNSUPPORTED.
  *   X, ldx    : output, l x n row-major (ldx >= n).
@@ -337,7 +339,7 @@ skel_status skel_debug_grid_timeout(int grid, uint64_t wait_ns, void* ws, size_t
  * records.  Costs one branch per launch while disabled (the default).
  * skel_debug_kernel_time -- total device time (ms) and launch count of the recorded launches
  * of one kernel since the last skel_debug_kernel_timing call; waits for those launches.
- * Names: "sketch_tc", "gemm_tc" (W = Q^T A), "lupp_panel", "lupp_trail", "qr_panel", "qr_wy", "trsm",
+ * Names: "sketch_tc", "sketch_fp8", "fp8_quantize", "gemm_tc" (W = Q^T A), "lupp_panel", "lupp_trail", "qr_panel", "qr_wy", "trsm",
  * "gemm_qr" (QR trailing updates and Q formation), "gemm_cur" (W Q_R), "gemm_eta_h" (R R^T),
  * "gemm_eta_sq" (eta's squarings), "gemm_simt" (other SIMT GEMMs), "batch_sketch", "batch_lupp".
  * Host-side state, process-wide; not for concurrent use from several threads.

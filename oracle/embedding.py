@@ -116,6 +116,40 @@ def round_fp32(x):
     return np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
 
 
+def round_e4m3(x):
+    """Round to the nearest FP8 e4m3 value (ties to even; 1 sign, 4 exponent bits with bias 7,
+    3 mantissa bits; normals from 2^-6, subnormals in steps of 2^-9, largest finite 448),
+    saturating at +-448, returned as FP64."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    e = np.floor(np.log2(np.maximum(a, 2.0 ** -10)))
+    q = 2.0 ** (np.maximum(e, -6.0) - 3.0)              # spacing of the binade (or of subnormals)
+    r = np.minimum(np.round(a / q) * q, 448.0)          # numpy rounds halves to even
+    return np.copysign(r, x)
+
+
+def fp8_block_scales(A, block=128):
+    """Per-block power-of-two scales of FP8 quantisation: for every `block` consecutive rows of
+    each column, s = 2^ceil(log2(amax / 448)) (s = 1 for an all-zero block), the smallest power
+    of two that brings the block into e4m3's range.  Returns (ceil(m / block) x n)."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    nb = (m + block - 1) // block
+    S = np.ones((nb, n))
+    for b in range(nb):
+        amax = np.abs(A[b * block:(b + 1) * block]).max(axis=0)
+        pos = amax > 0
+        S[b, pos] = 2.0 ** np.ceil(np.log2(amax[pos] / 448.0))
+    return S
+
+
+def round_fp8_blocks(A, block=128):
+    """A rounded to FP8 e4m3 with the per-block power-of-two scales: s * round_e4m3(A / s)."""
+    A = np.asarray(A, dtype=np.float64)
+    S = np.repeat(fp8_block_scales(A, block), block, axis=0)[:A.shape[0]]
+    return S * round_e4m3(A / S)
+
+
 def round_bf16(x):
     """Round to the nearest bfloat16 value (ties to even) via FP32, returned as FP64.
 

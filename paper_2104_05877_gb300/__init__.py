@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libskel.so")
 
 F64, F32 = 0, 1
-PREC = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3}
+PREC = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3, "fp8": 4}
 KIND = {"gaussian": 0, "sparse_sign": 1}
 STATUS = {0: "ok", 1: "invalid argument", 2: "workspace", 3: "non-finite", 4: "rank deficient",
           5: "timeout", 6: "cuda error", 7: "unsupported"}
@@ -155,7 +155,7 @@ def sketch(A, l, kind="gaussian", prec="f32", seed=0, zeta=8, X=None, status=Non
     columns row0 ..); the partial sketches of a row partition sum to the whole sketch."""
     A, lda = _colmajor(A)
     m, n = A.shape
-    if prec in ("tf32", "bf16") and (lda % 4 or A.data_ptr() % 16):
+    if prec in ("tf32", "bf16", "fp8") and (lda % 4 or A.data_ptr() % 16):
         # the tensor-core path streams A with TMA: 16-byte aligned columns required
         ld4 = (m + 3) // 4 * 4
         Ap = torch.empty(n, ld4, dtype=A.dtype, device=A.device).t()

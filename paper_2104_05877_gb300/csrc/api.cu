@@ -98,7 +98,7 @@ skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dt
   if (lda < std::max<int64_t>(1, m) || ldx < std::max<int64_t>(1, n)) return SKEL_ERR_INVALID_ARG;
   if ((m > 0 && n > 0 && A == nullptr) || (n > 0 && X == nullptr)) return SKEL_ERR_INVALID_ARG;
   if (m > 0xFFFFFFFFll || n > 0xFFFFFFFFll) return SKEL_ERR_INVALID_ARG;
-  if (prec < SKEL_PREC_F64 || prec > SKEL_PREC_BF16) return SKEL_ERR_INVALID_ARG;
+  if (prec < SKEL_PREC_F64 || prec > SKEL_PREC_FP8) return SKEL_ERR_INVALID_ARG;
   if (prec == SKEL_PREC_F64 && a_dtype != SKEL_F64) return SKEL_ERR_INVALID_ARG;
   if (kind != SKEL_SKETCH_GAUSSIAN && kind != SKEL_SKETCH_SPARSE_SIGN) return SKEL_ERR_INVALID_ARG;
   const skel_dtype x_dt = prec == SKEL_PREC_F64 ? SKEL_F64 : SKEL_F32;
@@ -106,14 +106,18 @@ skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dt
   int32_t* table = nullptr;
   if (kind == SKEL_SKETCH_SPARSE_SIGN) {
     if (zeta < 1 || zeta > 31 || zeta > l) return SKEL_ERR_INVALID_ARG;
-    if (prec == SKEL_PREC_TF32 || prec == SKEL_PREC_BF16) return SKEL_ERR_UNSUPPORTED;
+    if (prec == SKEL_PREC_TF32 || prec == SKEL_PREC_BF16 || prec == SKEL_PREC_FP8) return SKEL_ERR_UNSUPPORTED;
     if (esize(x_dt) * (size_t)l * 32 + 4 * 256 * (size_t)zeta > 220 * 1024) return SKEL_ERR_UNSUPPORTED;
     if (prec == SKEL_PREC_F32 && a_dtype != SKEL_F32) return SKEL_ERR_UNSUPPORTED;
     table = static_cast<int32_t*>(ar.take(sparse_pattern_bytes(m, zeta)));
   }
-  const bool tensor = kind == SKEL_SKETCH_GAUSSIAN && (prec == SKEL_PREC_BF16 || prec == SKEL_PREC_TF32);
+  const bool fp8 = kind == SKEL_SKETCH_GAUSSIAN && prec == SKEL_PREC_FP8;
+  const bool tensor = kind == SKEL_SKETCH_GAUSSIAN && (prec == SKEL_PREC_BF16 || prec == SKEL_PREC_TF32 || fp8);
   if (tensor && a_dtype != SKEL_F32) return SKEL_ERR_UNSUPPORTED;
-  void* tcws = tensor && m > 0 && n > 0 ? ar.take(sketch_tc_workspace(m, n, l, prec)) : nullptr;
+  if (fp8 && row0 != 0) return SKEL_ERR_UNSUPPORTED;
+  void* tcws = tensor && m > 0 && n > 0
+                   ? ar.take(fp8 ? sketch_fp8_workspace(m, n, l) : sketch_tc_workspace(m, n, l, prec))
+                   : nullptr;
   skel_status st;
   if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
   if (n == 0) return SKEL_OK;
@@ -128,8 +132,11 @@ skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dt
     return SKEL_OK;
   }
   if (tensor && m > 0) {
-    const cudaError_t e = launch_sketch_tc(row0, m, n, static_cast<const float*>(A), lda, l, prec, seed,
-                                           static_cast<float*>(X), ldx, tcws, dev_status, stream);
+    const cudaError_t e =
+        fp8 ? launch_sketch_fp8(row0, m, n, static_cast<const float*>(A), lda, l, seed, static_cast<float*>(X), ldx,
+                                tcws, dev_status, stream)
+            : launch_sketch_tc(row0, m, n, static_cast<const float*>(A), lda, l, prec, seed,
+                               static_cast<float*>(X), ldx, tcws, dev_status, stream);
     if (e == cudaErrorNotSupported) return SKEL_ERR_UNSUPPORTED;
     SK_CUDA(e);
     return SKEL_OK;

@@ -150,6 +150,11 @@ cudaError_t launch_gauss_sketch_csc(int64_t m, int64_t n, const int64_t* col_ptr
 // Tensor-core Gaussian sketch (sketch_tc.cu).  Returns cudaErrorNotSupported when the
 // shape or alignment is outside what the kernel handles.  ws: sketch_tc_workspace bytes.
 size_t sketch_tc_workspace(int64_t m, int64_t n, int32_t l, skel_prec prec);
+// FP8 (e4m3, per-128-row power-of-two scales) sketch (sketch_fp8.cu): quantisation pre-pass,
+// e4m3 Gamma, tcgen05 kind::f8f6f4.  ws: sketch_fp8_workspace bytes.
+size_t sketch_fp8_workspace(int64_t m, int64_t n, int32_t l);
+cudaError_t launch_sketch_fp8(int64_t row0, int64_t m, int64_t n, const float* A, int64_t lda, int32_t l,
+                              uint64_t seed, float* X, int64_t ldx, void* ws, int32_t* dev_status, cudaStream_t st);
 cudaError_t launch_sketch_tc(int64_t row0, int64_t m, int64_t n, const float* A, int64_t lda, int32_t l,
                              skel_prec prec, uint64_t seed, float* X, int64_t ldx, void* ws,
                              int32_t* dev_status, cudaStream_t st);

@@ -236,3 +236,45 @@ def test_sketch_power_iteration(skel, dev, prec, q):
     want = sketch.gaussian_sketch_power(A.astype(np.float64), l, 17, q)
     rel = np.linalg.norm(X.cpu().numpy() - want) / np.linalg.norm(want)
     assert rel <= (1e-12 if prec == "f64" else 2e-5 * q), rel
+
+
+@pytest.mark.parametrize("m,n,l", [(1000, 777, 61), (2048, 1536, 272), (300, 129, 40), (4100, 600, 130),
+                                   (129, 2048, 128)])
+def test_sketch_fp8_tensor_cores(skel, dev, m, n, l):
+    """tcgen05 kind::f8f6f4 sketch: e4m3 normals, A in e4m3 with a power-of-two scale per 128
+    rows of each column, exact products, FP32 accumulation.  Reference: the oracle's FP8
+    sketch (FP64 normals rounded to e4m3, the same scales).  An FP32 normal near an e4m3
+    rounding boundary can round one e4m3 step (2^-3 relative) away from the FP64 one; two
+    such entries per row are allowed for."""
+    A = workloads.dense_config2(m, n, seed=m + 2 * l, dtype=np.float32)
+    X, st = skel.sketch(torch.from_numpy(A).to(dev), l, prec="fp8", seed=79)
+    skel.check_status(st)
+    Ad = A.astype(np.float64)
+    want = sketch.gaussian_sketch(Ad, l, 79, operand_rounding="fp8")
+    G8 = embedding.round_e4m3(embedding.gaussian_normals(l, m, 79))
+    A8 = embedding.round_fp8_blocks(Ad)
+    acc = 2 * m * 2.0 ** -23 * (np.abs(G8) @ np.abs(A8))
+    flips = 2 * 2.0 ** -3 * np.outer(np.abs(G8).max(axis=1), np.abs(A8).max(axis=0))
+    err = np.abs(X.cpu().numpy() - want)
+    assert np.all(err <= (acc + flips) / np.sqrt(l)), (err / ((acc + flips) / np.sqrt(l))).max()
+
+
+def test_sketch_fp8_pivots_well_separated(skel, dev):
+    """Pivots from the FP8 sketch equal the oracle's on its FP8 sketch (and on the exact one) for
+    columns with geometrically separated norms: every greedy gap (>= 0.35 here) is far above
+    the e4m3 rounding of the sketch."""
+    rng = np.random.default_rng(12)
+    m, n, k = 1500, 2048, 12
+    A = rng.standard_normal((m, n)) * 1e-3
+    cols = rng.choice(n, k, replace=False)
+    for t, c in enumerate(cols):
+        A[:, c] = rng.standard_normal(m) * 4.0 ** (k - t)
+    A = np.asfortranarray(A.astype(np.float32))
+    X, st = skel.sketch(torch.from_numpy(A).to(dev), k + 4, prec="fp8", seed=4)
+    skel.check_status(st)
+    Js, _, _, st2 = skel.pivot_lupp(X, k, factors=False)
+    skel.check_status(st2)
+    ref = pivoting.lupp_columns(sketch.gaussian_sketch(A.astype(np.float64), k + 4, 4, operand_rounding="fp8"), k)
+    assert ref["gaps"].min() > 0.35
+    assert np.array_equal(Js.cpu().numpy(), ref["Js"])
+    assert np.array_equal(ref["Js"], pivoting.lupp_columns(sketch.gaussian_sketch(A.astype(np.float64), k + 4, 4), k)["Js"])

@@ -149,3 +149,34 @@ def test_power_sketch_improves_the_rangefinder_on_a_flat_spectrum():
     plain = np.mean([errors.rangefinder_error(A, sketch.gaussian_sketch(A, 20, s)) for s in range(8)])
     power = np.mean([errors.rangefinder_error(A, sketch.gaussian_sketch_power(A, 20, s, 1)) for s in range(8)])
     assert power < 0.9 * plain
+
+
+def test_round_e4m3_matches_torch():
+    """e4m3 rounding (ties to even, subnormals) against torch's float8_e4m3fn conversion on
+    in-range values, including exact halfway cases; saturation at 448."""
+    import torch
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.uniform(-3, 2.4, 20000),
+                        [0.0, 1.0625, 1.1875, 2.0 ** -7, 3 * 2.0 ** -10, 448.0, -448.0, 15.5, 17.0]])
+    x = x[np.abs(x) <= 448.0]
+    want = torch.from_numpy(x).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(embedding.round_e4m3(x), want)
+    assert embedding.round_e4m3(np.array([500.0, -1e6]))[0] == 448.0
+    assert embedding.round_e4m3(np.array([-1e6]))[0] == -448.0
+
+
+def test_fp8_block_scales_are_minimal_powers_of_two():
+    """s = 2^ceil(log2(amax/448)): |A/s| <= 448 on every block, and s/2 would overflow."""
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((300, 20)) * 10.0 ** rng.uniform(-5, 5, (1, 20))
+    A[:, 3] = 0.0
+    S = embedding.fp8_block_scales(A)
+    assert S.shape == (3, 20) and np.all(S[:, 3] == 1.0)
+    for b in range(3):
+        amax = np.abs(A[b * 128:(b + 1) * 128]).max(axis=0)
+        nz = amax > 0
+        assert np.all(np.log2(S[b]) == np.round(np.log2(S[b])))
+        assert np.all(amax[nz] / S[b, nz] <= 448.0)
+        assert np.all(amax[nz] / (S[b, nz] / 2) > 448.0)
+    R = embedding.round_fp8_blocks(A)
+    assert np.all(np.abs(R - A) <= 2.0 ** -4 * np.abs(A) + 2.0 ** -9 * np.repeat(S, 128, axis=0)[:300])
