@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--k", type=int, default=256)
     ap.add_argument("--p", type=int, default=16)
     ap.add_argument("--prec", default="tf32", choices=["tf32", "bf16", "fp8", "f32"])
+    ap.add_argument("--blocks", type=int, default=4096, help="blocks of the batched run (--only batch)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-GPU comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     ap.add_argument("--only", default=None, choices=["sketch", "lupp", "rows", "id", "cur", "eta", "batch"],
@@ -443,10 +444,11 @@ def run_ours(args, rank, world):
 
 
 def run_batch(args, rank, dev, skel, workloads):
-    """Batched configuration: 4096 uneven Gaussian-kernel blocks (m_b ~ U[64, 1024], n_b ~
-    U[64, 512], FP32, ~2.6 GB), k_max = 128, p = 16, tol = 1e-6: one skel_batch_run per step."""
+    """Batched configuration: uneven Gaussian-kernel blocks (4096 by default: m_b ~ U[64, 1024],
+    n_b ~ U[64, 512], FP32, ~2.6 GB), k_max = 128, p = 16, tol = 1e-6: one skel_batch_run per
+    step."""
     import torch
-    nblocks, kmax, p, tol = 4096, 128, 16, 1e-6
+    nblocks, kmax, p, tol = args.blocks, 128, 16, 1e-6
     blocks = workloads.torch_kernel_blocks(nblocks, workloads.seed_for(4) + rank, dev)
     a_bytes = sum(4 * B.shape[0] * B.shape[1] for B in blocks)
     plan = skel.BatchPlan(blocks, kmax, p=p, tol=tol, seed=workloads.seed_for(4, "gamma"))
