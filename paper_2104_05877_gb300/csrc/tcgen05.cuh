@@ -1,6 +1,6 @@
 // tcgen05 / TMA building blocks shared by the tensor-core kernels (sketch X = Gamma A and the
-// 3xTF32 product W = Q^T A): mbarrier waits bounded in time (CTA and cluster scope), remote
-// arrives and loads within a thread-block cluster, 2-D TMA loads, 128- and 64-byte-swizzle
+// 3xTF32 product W = Q^T A): mbarrier waits bounded in time (CTA and cluster scope), bulk
+// copies and multicast MMA commits within a thread-block cluster, 2-D TMA loads, 128- and 64-byte-swizzle
 // K-major shared-memory descriptors, TF32 and BF16 instruction descriptors, MMA issue and
 // commit, TMEM loads, and the driver entry point that encodes tensor maps.
 #pragma once
@@ -43,9 +43,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
   return true;
 }
 
-// Cluster-scope variants: waits that acquire what other CTAs of the cluster released, an
-// arrive on the mbarrier at the same offset in CTA `rank`, and a 16-byte load from the shared
-// memory of another CTA of the cluster.
+// Cluster-scope waits (acquire what other CTAs of the cluster released) and the address of
+// the same shared-memory offset in CTA `rank` of the cluster.
 __device__ __forceinline__ bool mbar_try_cl(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -67,10 +66,6 @@ __device__ __forceinline__ uint32_t cluster_addr(uint32_t local, int rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
   return r;
 }
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t local_bar, int rank) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];"
-               ::"r"(cluster_addr(local_bar, rank)) : "memory");
-}
 // Bulk copy of `bytes` (multiple of 16, 16-byte aligned) from this CTA's shared memory to
 // the same offset in CTA `rank` of the cluster; completes the bytes on that CTA's mbarrier
 // at the offset of `local_bar`.
@@ -83,12 +78,6 @@ __device__ __forceinline__ void bulk_copy_to_peer(uint32_t local_dst_src, uint32
 __device__ __forceinline__ void mma_commit_multicast(uint32_t bar, uint16_t mask) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
                ::"r"(bar), "h"(mask) : "memory");
-}
-__device__ __forceinline__ uint4 ld_cluster_v4(uint32_t addr) {
-  uint4 v;
-  asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr) : "memory");
-  return v;
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
