@@ -166,3 +166,20 @@ def test_column_id_from_sketch(skel, dev, dt):
     assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want)
     e_sk = np.linalg.norm(A - A[:, J] @ got)
     assert e_sk >= np.linalg.norm(A - A[:, J] @ decomp.column_id(A, J)) * (1 - 1e-9)
+
+
+def test_mixed_path_z_accuracy(skel, dev):
+    """The mixed path's Z (FP32 Householder QR, 3xTF32 W, FP64 solve) against the FP64 oracle's
+    Z on the same skeleton: within a small multiple of cond(C) u_32 (stated per result; no
+    FP64 refinement step)."""
+    A = workloads.dense_config2(2048, 1500, seed=11, dtype=np.float32)
+    Ad = A.astype(np.float64)
+    At = torch.from_numpy(np.asfortranarray(A)).to(dev)
+    X, _ = skel.sketch(At, 80, prec="tf32", seed=3)
+    Js, _, _, _ = skel.pivot_lupp(X, 64, factors=False)
+    Z, _, st = skel.column_id(At, Js)
+    skel.check_status(st)
+    J = Js.cpu().numpy()
+    Zo = decomp.column_id(Ad, J)
+    rel = np.linalg.norm(Z.cpu().numpy() - Zo) / np.linalg.norm(Zo)
+    assert rel <= 10 * np.linalg.cond(Ad[:, J]) * 2.0 ** -24, rel
