@@ -112,6 +112,20 @@ skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dt
                              int32_t* dev_status, cudaStream_t stream);
 
 /*
+ * skel_sketch_cols -- the column sketch of the streaming skeleton selection (Algorithm 3 line 2):
+ *     Y = A Omega^T (m x l),  Omega l x n Gaussian with N(0, 1/l) entries,
+ * returned transposed, Yt = Omega A^T (l x m row-major, ldy >= m), so that the row skeletons
+ * I_s are the column pivots of skel_pivot_lupp on Yt (Algorithm 3 line 4).  Omega's counters
+ * are those of the Gaussian embedding over n columns (column j of Omega pairs with column j of
+ * A); use a seed different from Gamma's for an independent Omega.  prec: SKEL_PREC_F64
+ * (a_dtype F64) or SKEL_PREC_F32 (a_dtype F32), on the SIMT path with Omega generated in the
+ * kernel.  Workspace: GEMM split-K scratch (handshake).
+ */
+skel_status skel_sketch_cols(int64_t m, int64_t n, skel_dtype a_dtype, const void* A, int64_t lda, int32_t l,
+                             skel_prec prec, uint64_t seed, void* Yt, int64_t ldy, void* ws, size_t* ws_bytes,
+                             int32_t* dev_status, cudaStream_t stream);
+
+/*
  * skel_sketch_power -- row space approximator with q plain power iterations (Sec. 3,
  * Eq. (def_power_iter); Rand-LUPP-1piter of Sec. 5 is q = 1):
  *     X = Omega (A^T A)^q,   Omega l x n Gaussian with N(0, 1/l) entries,

@@ -56,3 +56,18 @@ def batch_skeletonize(blocks, kmax, p, tol, seed):
         out.append(dict(rank=rt["rank"], Js=rt["Js"], Z=decomp.sketch_id(X, rt["Js"]), X=X,
                         gaps=rt["gaps"], mags=rt["mags"], estimates=rt["estimates"]))
     return out
+
+
+def streaming_skeletonize(A, k, p, seed_gamma, seed_omega):
+    """Algorithm 3 (streaming skeleton selection): X = Gamma A and Y = A Omega^T from the same
+    pass over A, J_s by column LUPP on X, I_s by row LUPP on Y (column LUPP on Y^T); then the
+    CUR with those skeletons (the stable form of Remark 3, which needs A again)."""
+    A = np.asarray(A, dtype=np.float64)
+    l = k + p
+    X = sketch.gaussian_sketch(A, l, seed_gamma)
+    Yt = sketch.gaussian_col_sketch(A, l, seed_omega)
+    px, py = pivoting.lupp_columns(X, k), pivoting.lupp_columns(Yt, k)
+    Js, Is = px["Js"], py["Js"]
+    U = decomp.cur(A, Js, Is)
+    return dict(X=X, Yt=Yt, Js=Js, Is=Is, Rx=px["R"], Ry=py["R"], gaps_x=px["gaps"], gaps_y=py["gaps"], U=U,
+                err_cur=errors.rel_cur_error(A, Js, U, Is))

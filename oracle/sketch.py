@@ -81,3 +81,12 @@ def gaussian_sketch_power(A, l, seed, q=1):
     for _ in range(q):
         X = (X @ A.T) @ A
     return X
+
+
+def gaussian_col_sketch(A, l, seed):
+    """Transposed column sketch of the streaming selection (Algorithm 3 line 2): Yt = Omega A^T
+    (l x m), i.e. Y = A Omega^T, with Omega (l x n) Gaussian N(0, 1/l) over the counters of the
+    Gaussian embedding on n columns."""
+    A = np.asarray(A, dtype=np.float64)
+    Om = embedding.gaussian_normals(l, A.shape[1], seed) / np.sqrt(l)
+    return Om @ A.T

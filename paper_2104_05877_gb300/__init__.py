@@ -55,6 +55,7 @@ def lib():
                        szp, vp, vp],
         "skel_id_sketch": [i32, i32, i64, vp, i64, vp, vp, i64, vp, szp, vp, vp],
         "skel_sketch_power": [i64, i64, i32, vp, i64, i32, i32, i32, u64, vp, i64, vp, szp, vp, vp],
+        "skel_sketch_cols": [i64, i64, i32, vp, i64, i32, i32, u64, vp, i64, vp, szp, vp, vp],
         "skel_debug_gaussian": [i32, i64, u64, ctypes.c_int, vp, vp],
         "skel_debug_philox": [vp, i64, u32, u32, vp, vp],
         "skel_debug_curand_philox": [u64, i64, ctypes.c_int, vp, vp],
@@ -186,6 +187,32 @@ def sketch_power(A, l, q=1, prec="tf32", seed=0, status=None):
     _call("skel_sketch_power", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, l, q, PREC[prec], seed, _ptr(X), n, w,
                                               sz, _ptr(st), _stream()], A.device)
     return X, st
+
+
+def sketch_cols(A, l, prec="f32", seed=1, status=None):
+    """Yt = Omega A^T (l x m row-major): the transposed column sketch Y = A Omega^T of the
+    streaming skeleton selection (Algorithm 3); LUPP on Yt gives the row skeletons."""
+    A, lda = _colmajor(A)
+    m, n = A.shape
+    Yt = torch.empty(l, m, dtype=torch.float64 if prec == "f64" else torch.float32, device=A.device)
+    st = status if status is not None else new_status(A.device)
+    _call("skel_sketch_cols", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, l, PREC[prec], seed, _ptr(Yt), m, w, sz,
+                                             _ptr(st), _stream()], A.device)
+    return Yt, st
+
+
+def skeletonize_streaming(A, k, p=10, seed=0, seed_omega=None, prec="f32", status=None):
+    """Algorithm 3: row sketch X = Gamma A and column sketch Y = A Omega^T, J_s from LUPP on X
+    and I_s from LUPP on Y^T (no skeleton C is gathered for the row pivots)."""
+    A, _ = _colmajor(A)
+    st = status if status is not None else new_status(A.device)
+    l = k + p
+    X, _ = sketch(A, l, prec=prec, seed=seed, status=st)
+    Yt, _ = sketch_cols(A, l, prec="f64" if prec == "f64" else "f32",
+                        seed=seed + 1 if seed_omega is None else seed_omega, status=st)
+    Js, _, _, _ = pivot_lupp(X, k, factors=False, status=st)
+    Is, _, _, _ = pivot_lupp(Yt, k, factors=False, status=st)
+    return Js, Is, st
 
 
 def sketch_csc(col_ptr, row_idx, val, m, n, l, kind="sparse_sign", seed=0, zeta=8, status=None):

@@ -153,6 +153,31 @@ skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dt
   return SKEL_OK;
 }
 
+skel_status skel_sketch_cols(int64_t m, int64_t n, skel_dtype a_dtype, const void* A, int64_t lda, int32_t l,
+                             skel_prec prec, uint64_t seed, void* Yt, int64_t ldy, void* ws, size_t* ws_bytes,
+                             int32_t* dev_status, cudaStream_t stream) {
+  if (m < 1 || n < 1 || l < 1 || l > 4096 || !valid_dtype(a_dtype) || A == nullptr || Yt == nullptr || lda < m ||
+      ldy < m || n > 0xFFFFFFFFll)
+    return SKEL_ERR_INVALID_ARG;
+  if (prec != SKEL_PREC_F64 && prec != SKEL_PREC_F32) return SKEL_ERR_UNSUPPORTED;
+  if ((prec == SKEL_PREC_F64) != (a_dtype == SKEL_F64)) return SKEL_ERR_INVALID_ARG;
+  const bool f64 = prec == SKEL_PREC_F64;
+  Arena ar(ws);
+  void* kws = ar.take(gemm_workspace(l, m, n, f64));
+  skel_status st;
+  if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+  GemmArgs a{};
+  a.M = l; a.N = m; a.K = n;
+  a.B = View{A, lda, 1}; a.b_dt = a_dtype;            // B(k, c) = A^T(k, c) = A(c, k)
+  a.out = Yt; a.out_sr = ldy; a.out_sc = 1; a.out_dt = f64 ? SKEL_F64 : SKEL_F32;
+  a.alpha = 1.0 / std::sqrt((double)l);
+  a.seed = seed;
+  a.dev_status = dev_status;
+  a.splitk_ws = kws;
+  SK_CUDA(launch_gemm(a, f64, LEFT_GAUSSIAN, EPI_SKETCH, stream));
+  return SKEL_OK;
+}
+
 skel_status skel_sketch_power(int64_t m, int64_t n, skel_dtype a_dtype, const void* A, int64_t lda, int32_t l,
                               int32_t q, skel_prec prec, uint64_t seed, void* X, int64_t ldx, void* ws,
                               size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream) {

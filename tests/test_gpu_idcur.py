@@ -183,3 +183,36 @@ def test_mixed_path_z_accuracy(skel, dev):
     Zo = decomp.column_id(Ad, J)
     rel = np.linalg.norm(Z.cpu().numpy() - Zo) / np.linalg.norm(Zo)
     assert rel <= 10 * np.linalg.cond(Ad[:, J]) * 2.0 ** -24, rel
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_column_sketch(skel, dev, prec):
+    """Yt = Omega A^T (the column sketch of Algorithm 3) against the oracle's."""
+    dt = np.float64 if prec == "f64" else np.float32
+    A = workloads.dense_config2(700, 450, seed=4, dtype=dt)
+    Yt, st = skel.sketch_cols(torch.from_numpy(A).to(dev), 37, prec=prec, seed=9)
+    skel.check_status(st)
+    want = sketch.gaussian_col_sketch(A.astype(np.float64), 37, 9)
+    Om = np.abs(oracle.embedding.gaussian_normals(37, 450, 9)) / np.sqrt(37)
+    mag = Om @ np.abs(A.astype(np.float64)).T
+    u = 2.0 ** -52 if prec == "f64" else 2.0 ** -23
+    assert np.all(np.abs(Yt.cpu().numpy() - want) <= 4 * 450 * u * mag)
+
+
+def test_streaming_skeleton_selection(skel, dev):
+    """Algorithm 3 on the device (X = Gamma A, Y = A Omega^T, LUPP on X and on Y^T) against
+    the oracle's: the same row and column skeletons in FP64 before the first near-tie, and a
+    CUR error within 1.05x of the oracle's."""
+    A = workloads.dense_config2(600, 500, seed=5, dtype=np.float64)
+    k, p = 30, 10
+    Js, Is, st = skel.skeletonize_streaming(torch.from_numpy(A).to(dev), k, p, seed=7, seed_omega=8, prec="f64")
+    torch.cuda.synchronize()
+    skel.check_status(st)
+    ref = oracle.skeleton.streaming_skeletonize(A, k, p, 7, 8)
+    for got, want, gaps in ((Js, ref["Js"], ref["gaps_x"]), (Is, ref["Is"], ref["gaps_y"])):
+        small = np.flatnonzero(gaps < 1e-9)
+        pre = int(small[0]) if small.size else k
+        assert np.array_equal(got.cpu().numpy()[:pre], want[:pre])
+    J, I = Js.cpu().numpy(), Is.cpu().numpy()
+    e_gpu = errors.rel_cur_error(A, J, decomp.cur(A, J, I), I)
+    assert e_gpu <= 1.05 * ref["err_cur"]

@@ -127,3 +127,26 @@ def test_sparse_sign_skeleton_runs_and_is_close_to_optimal():
     out = skeleton.skeletonize(A, k=20, p=20, seed=4, kind="sparse_sign", zeta=8)
     opt = errors.best_rank_k_error(A, 20) / errors.fro(A)
     assert opt <= out["err_id"] < 3 * opt
+
+
+def test_streaming_selection_exact_on_exactly_low_rank():
+    """Algorithm 3 on an exactly rank-r input with k = r: the CUR from the row sketch's column
+    pivots and the column sketch's row pivots reconstructs A (Lemma 1)."""
+    A = workloads.exact_rank(250, 180, 12, seed=7)
+    out = skeleton.streaming_skeletonize(A, 12, 8, 3, 4)
+    C, R = A[:, out["Js"]], A[out["Is"], :]
+    assert np.linalg.norm(A - C @ out["U"] @ R) <= 1e-9 * np.linalg.norm(A)
+
+
+def test_streaming_selection_two_sided_bound():
+    """The bound after Algorithm 3 (Sec. 4): ||A - CUR||_F <= eta_X ||A - A Xt^+ Xt||_F +
+    eta_Y ||A - Yt^T (Yt^T)^+ A||_F, with Xt, Yt the LU factors of the row and the transposed
+    column sketch and eta from each factor."""
+    for seed in range(4):
+        A = workloads.dense_config2(200, 160, seed=seed, dtype=np.float64)
+        k = 15
+        out = skeleton.streaming_skeletonize(A, k, 10, 10 + seed, 20 + seed)
+        err = np.linalg.norm(A - A[:, out["Js"]] @ out["U"] @ A[out["Is"], :])
+        ex = errors.eta(out["Rx"], out["Js"]) * errors.rangefinder_error(A, out["Rx"])
+        ey = errors.eta(out["Ry"], out["Is"]) * errors.rangefinder_error(A.T, out["Ry"])
+        assert err <= (ex + ey) * (1 + 1e-10)
