@@ -266,6 +266,17 @@ skel_status skel_error(int64_t m, int64_t n, skel_dtype dtype, const void* A, in
                        int32_t* dev_status, cudaStream_t stream);
 
 /*
+ * skel_cur_sketch -- the CUR estimated without a second pass over A (Sec. 4: with the skeletons
+ * S = A(I_s, J_s), C = A(:, J_s) and R = A(I_s, :), A ~ C S^{-1} R): U = S^{-1} (s x s row-major
+ * FP64, ldu >= s), formed stably from a Householder QR of S^T (S^T = Q R_S, S^{-1} = Q R_S^{-T}).
+ * Reads only C's rows I_s.  Less accurate than skel_cur's U = C^+ A R^+ (the paper notes the
+ * compromise); S singular gives a non-finite U.  Arguments as skel_cur; workspace (handshake).
+ */
+skel_status skel_cur_sketch(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda, int32_t s,
+                            const int32_t* Js, const int32_t* Is, double* U, int64_t ldu, void* ws,
+                            size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream);
+
+/*
  * skel_id_sketch -- column ID coefficients from the sketch alone, without a second pass over
  * A (Sec. 4: C^+ A ~ X_1^+ X with X_1 = X(:, J_s)), taken on the first s rows of X, whose
  * greedy pivots are J_s: Z = X(0:s, J)^{-1} X(0:s, :) = R_1^{-1} R with R the s x n LUPP factor

@@ -46,3 +46,10 @@ def sketch_id(X, Js):
     if r == 0:
         return np.zeros((0, X.shape[1]))
     return np.linalg.solve(X[:r, Js], X[:r, :])
+
+
+def cur_sketch(A, Js, Is):
+    """U of the CUR estimated without a second pass over A (Sec. 4): with S = A(I_s, J_s),
+    A ~ C S^{-1} R, so U = S^{-1} (a library inverse serves as the step)."""
+    A = np.asarray(A, dtype=np.float64)
+    return np.linalg.inv(A[np.ix_(np.asarray(Is), np.asarray(Js))])

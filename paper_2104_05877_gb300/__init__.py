@@ -54,6 +54,7 @@ def lib():
         "skel_error": [i64, i64, i32, vp, i64, i32, vp, vp, i64, vp, vp, i64, i32, vp, i64, vp, vp,
                        szp, vp, vp],
         "skel_id_sketch": [i32, i32, i64, vp, i64, vp, vp, i64, vp, szp, vp, vp],
+        "skel_cur_sketch": [i64, i64, i32, vp, i64, i32, vp, vp, vp, i64, vp, szp, vp, vp],
         "skel_sketch_power": [i64, i64, i32, vp, i64, i32, i32, i32, u64, vp, i64, vp, szp, vp, vp],
         "skel_sketch_cols": [i64, i64, i32, vp, i64, i32, i32, u64, vp, i64, vp, szp, vp, vp],
         "skel_debug_gaussian": [i32, i64, u64, ctypes.c_int, vp, vp],
@@ -283,6 +284,18 @@ def column_id_sketch(R, Js, status=None):
     _call("skel_id_sketch", lambda w, sz: [_dt(R), s, n, _ptr(R), ldr, _ptr(Js), _ptr(Z), n, w, sz, _ptr(st),
                                            _stream()], R.device)
     return Z, st
+
+
+def cur_sketch(A, Js, Is, status=None):
+    """U = A(Is, Js)^{-1} (s x s FP64): the CUR A ~ C U R without a second pass over A."""
+    A, lda = _colmajor(A)
+    m, n = A.shape
+    s = Js.numel()
+    U = torch.empty(s, s, dtype=torch.float64, device=A.device)
+    st = status if status is not None else new_status(A.device)
+    _call("skel_cur_sketch", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, s, _ptr(Js), _ptr(Is), _ptr(U), s, w, sz,
+                                            _ptr(st), _stream()], A.device)
+    return U, st
 
 
 def pivot_rows(A, Js, status=None):

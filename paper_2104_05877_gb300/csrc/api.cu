@@ -458,6 +458,34 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
   return SKEL_OK;
 }
 
+skel_status skel_cur_sketch(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda, int32_t s,
+                            const int32_t* Js, const int32_t* Is, double* U, int64_t ldu, void* ws,
+                            size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  if (!id_args_ok(m, n, dtype, A, lda, s, Js) || Is == nullptr || U == nullptr || ldu < s) return SKEL_ERR_INVALID_ARG;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool run = pass == 1;
+    Arena ar(run ? ws : nullptr);
+    void* C = ar.take(esize(dtype) * (size_t)m * s);
+    void* St = ar.take(esize(dtype) * (size_t)s * s);          // S^T, column-major
+    void* Q = ar.take(esize(dtype) * (size_t)s * s);
+    double* R = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
+    double* V = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
+    const size_t qn = qr_workspace(dtype, s, s);
+    void* qws = ar.take(qn);
+    if (!run) {
+      skel_status st;
+      if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+      continue;
+    }
+    SK_CUDA(launch_gather_cols(m, s, dtype, A, lda, Js, C, m, stream));           // C = A(:, J)
+    SK_CUDA(launch_gather_rows_t(s, s, dtype, C, m, Is, St, s, stream));          // S^T(c, r) = C(I_r, c)
+    SK_TRY(run_qr(dtype, St, s, s, s, Q, s, R, s, qws, qn, dev_status, stream));   // S^T = Q R
+    SK_CUDA(launch_trsm_upper(s, s, R, s, 0, dtype, Q, s, V, s, stream));          // V = R^{-1} Q^T
+    SK_CUDA(launch_transpose_f64(s, V, s, U, ldu, stream));                       // U = V^T = S^{-1}
+  }
+  return SKEL_OK;
+}
+
 skel_status skel_id_sketch(skel_dtype dtype, int32_t s, int64_t n, const void* R, int64_t ldr,
                            const int32_t* Js, double* Z, int64_t ldz, void* ws, size_t* ws_bytes,
                            int32_t* dev_status, cudaStream_t stream) {

@@ -216,3 +216,27 @@ def test_streaming_skeleton_selection(skel, dev):
     J, I = Js.cpu().numpy(), Is.cpu().numpy()
     e_gpu = errors.rel_cur_error(A, J, decomp.cur(A, J, I), I)
     assert e_gpu <= 1.05 * ref["err_cur"]
+
+
+@pytest.mark.parametrize("dt,m,n,k", [(np.float64, 600, 500, 37), (np.float32, 600, 500, 37),
+                                      (np.float64, 1500, 1300, 200), (np.float64, 50, 40, 1)])
+def test_cur_sketch_core(skel, dev, dt, m, n, k):
+    """The sketch-only CUR core U = A(Is, Js)^{-1} (Sec. 4) against the oracle's inverse, on
+    the oracle's skeletons: within a condition-number multiple of the storage precision, and
+    C U R reproducing A's skeleton rows and columns."""
+    A = workloads.dense_config2(m, n, seed=3, dtype=np.float64).astype(dt)
+    Ad = A.astype(np.float64)
+    ref = oracle.skeleton.skeletonize(Ad, k=k, p=8, seed=4)
+    Js, Is = ref["Js"], ref["Is"]
+    Ur = decomp.cur_sketch(Ad, Js, Is)
+    U, st = skel.cur_sketch(torch.from_numpy(np.asfortranarray(A)).to(dev),
+                            torch.from_numpy(Js.astype(np.int32)).to(dev),
+                            torch.from_numpy(Is.astype(np.int32)).to(dev))
+    torch.cuda.synchronize()
+    skel.check_status(st)
+    Ug = U.cpu().numpy()
+    kappa = np.linalg.cond(Ad[np.ix_(Is, Js)])
+    u = 2.0 ** -52 if dt == np.float64 else 2.0 ** -23
+    assert np.linalg.norm(Ug - Ur) <= 50 * k * kappa * u * np.linalg.norm(Ur)
+    M = Ad[:, Js] @ Ug @ Ad[Is, :]
+    assert np.linalg.norm(M[Is, :] - Ad[Is, :]) <= 50 * k * kappa * u * np.linalg.norm(Ad[Is, :])

@@ -150,3 +150,52 @@ def test_streaming_selection_two_sided_bound():
         ex = errors.eta(out["Rx"], out["Js"]) * errors.rangefinder_error(A, out["Rx"])
         ey = errors.eta(out["Ry"], out["Is"]) * errors.rangefinder_error(A.T, out["Ry"])
         assert err <= (ex + ey) * (1 + 1e-10)
+
+
+def test_cur_sketch_interpolates_skeletons():
+    """C S^{-1} R with S = A(Is, Js) reproduces A's skeleton rows and columns exactly
+    (Sec. 4): rows Is give S S^{-1} R = R, columns Js give C S^{-1} S = C.  A transposed or
+    permuted S^{-1} fails both (S is neither symmetric nor diagonal here)."""
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((90, 70))
+    Js = rng.choice(70, 9, replace=False)
+    Is = rng.choice(90, 9, replace=False)
+    U = decomp.cur_sketch(A, Js, Is)
+    M = A[:, Js] @ U @ A[Is, :]
+    assert np.allclose(M[Is, :], A[Is, :], atol=1e-9)
+    assert np.allclose(M[:, Js], A[:, Js], atol=1e-9)
+
+
+def test_cur_sketch_exact_on_exactly_low_rank():
+    """An exactly rank-r input with nonsingular S = A(Is, Js) is reproduced exactly by
+    C S^{-1} R (the skeleton decomposition of a rank-r matrix), with the skeletons chosen by
+    the sketch path (Algorithm 2)."""
+    A = workloads.exact_rank(300, 200, 15, seed=7)
+    out = skeleton.skeletonize(A, k=15, p=0, seed=11)
+    U = decomp.cur_sketch(A, out["Js"], out["Is"])
+    M = A[:, out["Js"]] @ U @ A[out["Is"], :]
+    assert np.linalg.norm(A - M) <= 1e-9 * np.linalg.norm(A)
+
+
+def test_cur_sketch_never_beats_the_optimal_core():
+    """U = C^+ A R^+ minimises ||A - C U R||_F over all U (Eq. (2.4)), so the sketch-only
+    core S^{-1} is never better; on a decaying spectrum it stays within a modest factor."""
+    A = workloads.config1(160, 120, seed=5)
+    out = skeleton.skeletonize(A, k=20, p=8, seed=2)
+    Js, Is = out["Js"], out["Is"]
+    C, Rm = A[:, Js], A[Is, :]
+    e_opt = np.linalg.norm(A - C @ decomp.cur(A, Js, Is) @ Rm)
+    e_sk = np.linalg.norm(A - C @ decomp.cur_sketch(A, Js, Is) @ Rm)
+    assert e_opt <= e_sk * (1 + 1e-12)
+    assert e_sk <= 1e3 * e_opt
+
+
+def test_cur_sketch_2x2_closed_form():
+    """On a 2 x 2 skeleton the core is the adjugate over the determinant."""
+    A = np.array([[1.0, 7.0, 2.0], [3.0, 5.0, 4.0], [6.0, 2.0, 9.0]])
+    Js, Is = np.array([2, 0]), np.array([1, 2])
+    S = np.array([[4.0, 3.0], [9.0, 6.0]])          # A(Is, Js), written out
+    det = 4.0 * 6.0 - 3.0 * 9.0
+    want = np.array([[6.0, -3.0], [-9.0, 4.0]]) / det
+    assert np.allclose(decomp.cur_sketch(A, Js, Is), want, atol=1e-14)
+    assert np.allclose(A[np.ix_(Is, Js)], S)
