@@ -30,6 +30,9 @@ from .philox import philox4x32, seed_key
 
 TAG_GAUSSIAN = 0
 TAG_SPARSE = 1
+TAG_SRTT_PERM = 2
+TAG_SRTT_SELECT = 3
+TAG_SRTT_SIGN = 4
 
 
 def _unit_open(x):
@@ -105,6 +108,109 @@ def sparse_sign_embedding(l, m, zeta, seed):
     cols = np.repeat(np.arange(m), zeta)
     Gam[rows.ravel(), cols] = signs.ravel() / np.sqrt(zeta)
     return Gam
+
+
+# ---------------------------------------------------------------------------------------
+# Subsampled randomized trigonometric transform (Sec. 2.3, item 2):
+#     Gamma = sqrt(m/l) Pi_{m->l} T Phi Pi_{m->m}
+# with T the unitary discrete Hartley transform of order m (the real trigonometric transform
+# the paper names), Phi = diag(phi) Rademacher signs, Pi_{m->m} a random permutation and
+# Pi_{m->l} a uniformly random choice of l of the m rows.
+#
+# Readings.  Conventions: (Pi_{m->m} a)_r = a_{pi(r)} and (Pi_{m->l} d)_i = d_{sel(i)}.
+# The random permutation is drawn as a keyed pseudo-random permutation: a balanced 4-round
+# Feistel network on 2h bits (Luby & Rackoff, SIAM J. Comput. 1988), 4^h >= m, whose round
+# function is Philox word x of the counter (R, round, tag, 0) masked to h bits, mapped onto
+# 0..m-1 by cycle walking (Black & Rogaway, CT-RSA 2002: re-apply the network until the value
+# falls below m).  The l selected rows are sel(i) = the same construction with another tag,
+# i = 0..l-1 (distinct because it is a bijection).  Signs: phi_r = -1 when bit 0 of Philox
+# word x of the counter (r, 0, TAG_SRTT_SIGN, 0) is set.  The scale sqrt(m/l) is the
+# printed one: with T unitary it makes E[Gamma^T Gamma] = I.
+# ---------------------------------------------------------------------------------------
+def _feistel_half_bits(m):
+    h = 1
+    while 4 ** h < m:
+        h += 1
+    return h
+
+
+def feistel_permutation(m, seed, tag, x=None):
+    """pi(x) for x in 0..m-1 (all of them when x is None): the keyed permutation above."""
+    if m < 1 or m > 2 ** 31:
+        raise ValueError("1 <= m <= 2^31")
+    h = _feistel_half_bits(m)
+    mask = np.uint64((1 << h) - 1)
+    key = seed_key(seed)
+    y = np.arange(m, dtype=np.uint64) if x is None else np.asarray(x, dtype=np.uint64).copy()
+    todo = np.ones(y.shape, dtype=bool)
+    for _ in range(4 ** h + 1):               # a cycle of the network returns within 4^h steps
+        if not todo.any():
+            break
+        L, R = y[todo] >> np.uint64(h), y[todo] & mask
+        for rnd in range(4):
+            ctr = np.zeros((R.size, 4), dtype=np.uint64)
+            ctr[:, 0] = R
+            ctr[:, 1] = rnd
+            ctr[:, 2] = tag
+            f = philox4x32(ctr, key)[:, 0].astype(np.uint64) & mask
+            L, R = R, L ^ f
+        y[todo] = (L << np.uint64(h)) | R
+        todo = y >= np.uint64(m)
+    return y.astype(np.int64)
+
+
+def srtt_signs(m, seed):
+    """phi_r, r = 0..m-1 (+-1.0)."""
+    ctr = np.zeros((m, 4), dtype=np.uint64)
+    ctr[:, 0] = np.arange(m, dtype=np.uint64)
+    ctr[:, 2] = TAG_SRTT_SIGN
+    w = philox4x32(ctr, seed_key(seed))[:, 0].astype(np.uint64)
+    return np.where(w & np.uint64(1), -1.0, 1.0)
+
+
+def srtt_parts(m, l, seed):
+    """(pi, phi, sel) of the SRTT: the permutation, the signs and the l selected rows."""
+    if not 1 <= l <= m:
+        raise ValueError("the SRTT selects 1 <= l <= m rows")
+    return (feistel_permutation(m, seed, TAG_SRTT_PERM), srtt_signs(m, seed),
+            feistel_permutation(m, seed, TAG_SRTT_SELECT, np.arange(l)))
+
+
+def hartley(B):
+    """Unitary discrete Hartley transform along axis 0: (T B)_k = m^{-1/2} sum_r
+    cas(2 pi k r / m) B_r with cas = cos + sin, taken from the FFT (Re F - Im F, F the
+    DFT with kernel exp(-2 pi i k r / m))."""
+    B = np.asarray(B, dtype=np.float64)
+    F = np.fft.fft(B, axis=0)
+    return (F.real - F.imag) / np.sqrt(B.shape[0])
+
+
+def srtt_apply(A, l, seed):
+    """Gamma A for the SRTT, applied in the printed order: permute the rows of A, flip their
+    signs, transform, keep the selected rows, scale by sqrt(m/l)."""
+    A = np.asarray(A, dtype=np.float64)
+    m = A.shape[0]
+    pi, phi, sel = srtt_parts(m, l, seed)
+    B = A[pi] * (phi[:, None] if A.ndim == 2 else phi)
+    return np.sqrt(m / l) * hartley(B)[sel]
+
+
+def srtt_embedding_rows(rows, m, l, seed):
+    """Rows `rows` of Gamma (len(rows) x m): row i of T is the transform of e_{sel(i)} (T is
+    symmetric), then Gamma(i, pi(r)) = sqrt(m/l) T(sel(i), r) phi_r."""
+    pi, phi, sel = srtt_parts(m, l, seed)
+    rows = np.asarray(rows, dtype=np.int64)
+    E = np.zeros((m, rows.size))
+    E[sel[rows], np.arange(rows.size)] = 1.0
+    Trows = hartley(E).T                          # len(rows) x m
+    G = np.empty_like(Trows)
+    G[:, pi] = np.sqrt(m / l) * Trows * phi[None, :]
+    return G
+
+
+def srtt_embedding(l, m, seed):
+    """Dense Gamma (l x m) of the SRTT; small sizes only."""
+    return srtt_embedding_rows(np.arange(l), m, l, seed)
 
 
 # ---------------------------------------------------------------------------------------

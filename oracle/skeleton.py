@@ -21,6 +21,8 @@ def skeletonize(A, k, p, seed, kind="gaussian", pivot="lupp", zeta=8,
         X = sketch.gaussian_sketch(A, l, seed, operand_rounding)
     elif kind == "sparse_sign":
         X = sketch.sparse_sign_sketch(A, l, zeta, seed)
+    elif kind == "srtt":
+        X = sketch.srtt_sketch(A, l, seed)
     else:
         raise ValueError(kind)
     if pivot == "lupp":

@@ -90,3 +90,9 @@ def gaussian_col_sketch(A, l, seed):
     A = np.asarray(A, dtype=np.float64)
     Om = embedding.gaussian_normals(l, A.shape[1], seed) / np.sqrt(l)
     return Om @ A.T
+
+
+def srtt_sketch(A, l, seed):
+    """X = Gamma A for the SRTT embedding (Sec. 2.3, item 2), FP64, by the transform applied
+    to A's columns (not through a dense Gamma)."""
+    return embedding.srtt_apply(A, l, seed)

@@ -180,3 +180,86 @@ def test_fp8_block_scales_are_minimal_powers_of_two():
         assert np.all(amax[nz] / (S[b, nz] / 2) > 448.0)
     R = embedding.round_fp8_blocks(A)
     assert np.all(np.abs(R - A) <= 2.0 ** -4 * np.abs(A) + 2.0 ** -9 * np.repeat(S, 128, axis=0)[:300])
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 5, 16, 17, 1000, 4096, 4097])
+def test_feistel_permutation_is_a_bijection(m):
+    """The keyed permutation (Feistel network + cycle walking) hits every index once, for
+    domains that are and are not powers of 4."""
+    for tag in (embedding.TAG_SRTT_PERM, embedding.TAG_SRTT_SELECT):
+        pi = embedding.feistel_permutation(m, 7, tag)
+        assert np.array_equal(np.sort(pi), np.arange(m))
+    sub = embedding.feistel_permutation(m, 7, embedding.TAG_SRTT_PERM, np.arange(m)[::-1])
+    assert np.array_equal(sub, embedding.feistel_permutation(m, 7, embedding.TAG_SRTT_PERM)[::-1])
+
+
+def test_feistel_permutation_depends_on_seed_and_tag():
+    a = embedding.feistel_permutation(4096, 1, embedding.TAG_SRTT_PERM)
+    b = embedding.feistel_permutation(4096, 2, embedding.TAG_SRTT_PERM)
+    c = embedding.feistel_permutation(4096, 1, embedding.TAG_SRTT_SELECT)
+    assert np.mean(a == b) < 0.01 and np.mean(a == c) < 0.01
+    # a random permutation has ~1 fixed point and its positions are uncorrelated with values
+    assert np.sum(a == np.arange(4096)) < 10
+    assert abs(np.corrcoef(a, np.arange(4096))[0, 1]) < 0.1
+
+
+def test_hartley_transform_closed_forms():
+    """The unitary DHT is its own inverse, and on e_1 at k = m/4 it gives cas(pi/2)/sqrt(m) =
+    +1/sqrt(m) (a flipped sine, cas(-theta) = cos - sin, would give -1/sqrt(m)); the
+    transform of a constant vector is sqrt(m) e_0 times that constant."""
+    rng = np.random.default_rng(3)
+    for m in (1, 2, 7, 64, 1000):
+        x = rng.standard_normal((m, 3))
+        assert np.allclose(embedding.hartley(embedding.hartley(x)), x, atol=1e-12)
+        assert np.isclose(np.linalg.norm(embedding.hartley(x)), np.linalg.norm(x))
+    m = 64
+    e1 = np.zeros(m)
+    e1[1] = 1.0
+    t = embedding.hartley(e1)
+    assert np.isclose(t[m // 4], 1.0 / np.sqrt(m)) and np.isclose(t[3 * m // 4], -1.0 / np.sqrt(m))
+    assert np.isclose(t[0], 1.0 / np.sqrt(m)) and np.isclose(t[m // 8], np.sqrt(2.0) / np.sqrt(m))
+    c = embedding.hartley(np.full(m, 2.0))
+    assert np.isclose(c[0], 2.0 * np.sqrt(m)) and np.allclose(c[1:], 0.0, atol=1e-12)
+
+
+def test_srtt_full_selection_is_orthogonal():
+    """With l = m the SRTT is sqrt(1) T Phi Pi (all rows kept, permuted): an orthogonal
+    matrix, so Gamma^T Gamma = I to rounding."""
+    for m in (5, 64, 300):
+        G = embedding.srtt_embedding(m, m, 11)
+        assert np.allclose(G.T @ G, np.eye(m), atol=1e-12)
+
+
+def test_srtt_dense_rows_agree_with_the_transform():
+    """The dense Gamma (rows of T scattered through the permutation) applied to A equals the
+    transform applied to A's columns in the printed order; any row subset agrees too."""
+    rng = np.random.default_rng(5)
+    m, l = 300, 40
+    A = rng.standard_normal((m, 25))
+    G = embedding.srtt_embedding(l, m, 9)
+    assert np.allclose(G @ A, sketch.srtt_sketch(A, l, 9), atol=1e-12)
+    rows = np.array([3, 0, 39, 17])
+    assert np.allclose(embedding.srtt_embedding_rows(rows, m, l, 9), G[rows], atol=1e-14)
+    # entries have modulus <= sqrt(2/l) (|cas| <= sqrt 2), and row norms are sqrt(m/l)
+    assert np.abs(G).max() <= np.sqrt(2.0 / l) * (1 + 1e-12)
+    assert np.allclose(np.linalg.norm(G, axis=1), np.sqrt(m / l))
+
+
+def test_srtt_is_isometric_in_expectation():
+    """E ||Gamma x||^2 = ||x||^2 over the random choices (T unitary, l of m rows, scale m/l)."""
+    rng = np.random.default_rng(6)
+    m, l = 256, 32
+    x = rng.standard_normal(m)
+    vals = [np.sum(sketch.srtt_sketch(x[:, None], l, s) ** 2) for s in range(400)]
+    assert abs(np.mean(vals) / np.sum(x ** 2) - 1.0) < 0.05
+    phi = embedding.srtt_signs(4096, 3)
+    assert set(np.unique(phi)) == {-1.0, 1.0} and abs(np.mean(phi)) < 0.05
+
+
+def test_srtt_skeleton_exact_on_exactly_low_rank():
+    """Algorithm 2 with the SRTT sketch reconstructs an exactly rank-r input (l >= r)."""
+    import workloads
+    from oracle import skeleton
+    A = workloads.exact_rank(300, 200, 15, seed=7)
+    out = skeleton.skeletonize(A, k=15, p=5, seed=11, kind="srtt")
+    assert out["err_id"] < 1e-12
