@@ -47,10 +47,13 @@ def parse():
     ap.add_argument("--blocks", type=int, default=4096, help="blocks of the batched run (--only batch)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-GPU comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
-    ap.add_argument("--only", default=None, choices=["sketch", "lupp", "rows", "id", "cur", "eta", "batch"],
+    ap.add_argument("--only", default=None, choices=["sketch", "lupp", "rows", "id", "cur", "eta", "batch", "next",
+                                                     "srtt", "power", "cols"],
                     help="run only this call (warm-up + steps, no extras): a small command for profilers; "
                          "'batch' runs the batched configuration (4096 Gaussian-kernel blocks, k_max 128, "
-                         "tol 1e-6) instead of the dense workload")
+                         "tol 1e-6) instead of the dense workload; 'next' times the rows beyond the hot "
+                         "path (SRTT sketch, power sketch, column sketch, streaming selection, ID and CUR "
+                         "from the sketch) on the same workload, one JSON line")
     return ap.parse_args()
 
 
@@ -228,6 +231,9 @@ def run_ours(args, rank, world):
         evs[6].record()
         return Js, Is, sq_id, sq_cur, e
 
+    if args.only == "next":
+        run_next(args, rank, A, skel, st, seed_G)
+        return
     if args.only:
         X, _ = skel.sketch(A, l, prec=args.prec, seed=seed_G, status=st)
         Js, _, Rf, _ = skel.pivot_lupp(X, k, status=st)
@@ -237,7 +243,10 @@ def run_ours(args, rank, world):
                 "rows": lambda: skel.pivot_rows(A, Js, status=st),
                 "id": lambda: skel.column_id(A, Js, status=st),
                 "cur": lambda: skel.cur(A, Js, Is, status=st),
-                "eta": lambda: skel.error(A, Js, Rf=Rf, status=st)}[args.only]
+                "eta": lambda: skel.error(A, Js, Rf=Rf, status=st),
+                "srtt": lambda: skel.sketch(A, l, kind="srtt", prec=args.prec, seed=seed_G, X=X, status=st),
+                "power": lambda: skel.sketch_power(A, l, q=1, prec=args.prec, seed=seed_G, status=st),
+                "cols": lambda: skel.sketch_cols(A, l, prec=args.prec, seed=seed_G + 1, status=st)}[args.only]
         for _ in range(args.warmup):
             call()
         torch.cuda.synchronize()
@@ -441,6 +450,56 @@ def run_ours(args, rank, world):
         "gpu_launches": launches, "clocks": clk.summary(),
     }
     print(json.dumps(res), flush=True)
+
+
+def run_next(args, rank, A, skel, st, seed_G):
+    """The rows beyond the hot path on the dense workload, each timed alone (CUDA events over
+    --steps calls after --warmup): the SRTT sketch (tensor cores), the power-iterated sketch
+    X = Omega (A^T A) (a transposed copy of A, then one pass over each), the column sketch
+    Y^T = Omega A^T (tensor cores on the transposed copy),
+    streaming selection (row and column sketches + two LUPPs), the column ID from the sketch
+    (Z = R_1^{-1} R) and the CUR core from the skeletons (U = A(Is, Js)^{-1})."""
+    import torch
+    k, p = args.k, args.p
+    l = k + p
+    m, n = A.shape
+    X, _ = skel.sketch(A, l, prec=args.prec, seed=seed_G, status=st)
+    Js, _, Rf, _ = skel.pivot_lupp(X, k, status=st)
+    Is, _ = skel.pivot_rows(A, Js, status=st)
+    calls = {
+        "srtt_sketch": (lambda: skel.sketch(A, l, kind="srtt", prec=args.prec, seed=seed_G, X=X, status=st), 1),
+        "power_sketch_q1": (lambda: skel.sketch_power(A, l, q=1, prec=args.prec, seed=seed_G, status=st), 2),
+        "col_sketch": (lambda: skel.sketch_cols(A, l, prec=args.prec, seed=seed_G + 1, status=st), 1),
+        "streaming_selection": (lambda: skel.skeletonize_streaming(A, k, p, seed=seed_G, seed_omega=seed_G + 1,
+                                                                   prec=args.prec, status=st), 2),
+        "id_from_sketch": (lambda: skel.column_id_sketch(Rf, Js, status=st), 0),
+        "cur_core_from_skeletons": (lambda: skel.cur_sketch(A, Js, Is, status=st), 0),
+    }
+    out = {}
+    for nm, (fn, passes) in calls.items():
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        skel.check_status(st, nm)
+        ms = e0.elapsed_time(e1) / args.steps
+        ent = {"ms": ms}
+        if passes:
+            ent["a_passes"] = passes
+            ent["a_gbs"] = passes * 4.0 * m * n / (ms * 1e-3) / 1e9
+        out[nm] = ent
+    hbm, _, src = load_peaks()
+    for ent in out.values():
+        if "a_gbs" in ent:
+            ent["frac_of_hbm"] = ent["a_gbs"] / hbm
+    if rank == 0:
+        print(json.dumps({"only": "next", "rows": out, "hbm_peak_gbs": hbm, "peak_source": src,
+                          "config": workload_config(k, p, args.prec)}), flush=True)
 
 
 def run_batch(args, rank, dev, skel, workloads):

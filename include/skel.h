@@ -63,8 +63,10 @@ typedef enum {
 
 /* embedding Gamma (Sec. 2.3) */
 typedef enum {
-  SKEL_SKETCH_GAUSSIAN = 0,   /* i.i.d. N(0, 1/l) (Sec. 2.3, item 1)                        */
-  SKEL_SKETCH_SPARSE_SIGN = 1 /* zeta +-1/sqrt(zeta) per column at distinct rows (item 3)   */
+  SKEL_SKETCH_GAUSSIAN = 0,    /* i.i.d. N(0, 1/l) (Sec. 2.3, item 1)                        */
+  SKEL_SKETCH_SPARSE_SIGN = 1, /* zeta +-1/sqrt(zeta) per column at distinct rows (item 3)   */
+  SKEL_SKETCH_SRTT = 2         /* sqrt(m/l) Pi_{m->l} T Phi Pi_{m->m}, T the unitary discrete
+                                  Hartley transform (item 2)                                  */
 } skel_sketch_kind;
 
 const char* skel_status_string(int status);
@@ -79,7 +81,15 @@ uint64_t skel_launch_count(void);
  *   l         : number of sketch rows (l = k + p, Sec. 2.3), 1 <= l <= 4096.
  *   kind      : Gaussian (Gamma(i,j) = G(i,j)/sqrt(l), G from Philox + Box-Muller with
  *               counter (j/4, i, 0, 0)) or sparse sign (zeta nonzeros per column, Floyd's
- *               sampling from counters (j, 0, 1, c)); zeta is ignored for Gaussian.
+ *               sampling from counters (j, 0, 1, c)) or SRTT; zeta is ignored for Gaussian
+ *               and SRTT.  SRTT: Gamma(i, q) = phi_r cas(2 pi sel(i) r / m) / sqrt(l) with
+ *               r = pi^{-1}(q); pi and sel are keyed Feistel permutations of 0..m-1 (4 rounds
+ *               on 2h bits, 4^h >= m, round function Philox word x of counter (R, round, tag,
+ *               0) masked to h bits, tags 2 and 3, cycle walking onto 0..m-1), sel(i) for
+ *               i < l, and phi_r = -1 when bit 0 of Philox word x of counter (r, 0, 4, 0) is
+ *               set.  SRTT needs 1 <= l <= m < 2^31 (SKEL_ERR_INVALID_ARG otherwise),
+ *               supports F64, F32, TF32 and BF16, and no row offset (skel_sketch_rows with
+ *               row0 > 0 returns SKEL_ERR_UNSUPPORTED).
  *   prec      : arithmetic of the product (skel_prec).  SKEL_PREC_F64 requires
  *               a_dtype = SKEL_F64 and writes X as FP64; every other precision reads A as
  *               stored and writes X as FP32.  Sparse sign supports F64 and F32 only.  The
@@ -87,7 +97,9 @@ uint64_t skel_launch_count(void);
  *               aligned A and lda a multiple of 4 (A is streamed by TMA); otherwise they
  *               return SKEL_ERR_UNSUPPORTED.
  *   X, ldx    : output, l x n row-major (ldx >= n).
- * The Gaussian entries are generated inside the kernel and never stored.  Non-finite
+ * The Gaussian entries (and the SRTT's, on the tensor-core path) are generated inside the
+ * kernel and never stored; the SRTT's F64 / F32 path stores the l x m Gamma in the
+ * workspace.  Non-finite
  * entries of X set SKEL_ERR_NONFINITE in dev_status.
  */
 skel_status skel_sketch(int64_t m, int64_t n, skel_dtype a_dtype, const void* A, int64_t lda,
@@ -366,7 +378,8 @@ skel_status skel_debug_grid_timeout(int grid, uint64_t wait_ns, void* ws, size_t
  * of one kernel since the last skel_debug_kernel_timing call; waits for those launches.
  * Names: "sketch_tc", "sketch_fp8", "fp8_quantize", "gemm_tc" (W = Q^T A), "lupp_panel", "lupp_trail", "qr_panel", "qr_wy", "trsm",
  * "gemm_qr" (QR trailing updates and Q formation), "gemm_cur" (W Q_R), "gemm_eta_h" (R R^T),
- * "gemm_eta_sq" (eta's squarings), "gemm_simt" (other SIMT GEMMs), "batch_sketch", "batch_lupp".
+ * "gemm_eta_sq" (eta's squarings), "gemm_simt" (other SIMT GEMMs), "batch_sketch", "batch_lupp",
+ * "transpose" (A^T for the column and power sketches on the tensor cores).
  * Host-side state, process-wide; not for concurrent use from several threads.
  */
 skel_status skel_debug_kernel_timing(int enable);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libskel.so")
 
 F64, F32 = 0, 1
 PREC = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3, "fp8": 4}
-KIND = {"gaussian": 0, "sparse_sign": 1}
+KIND = {"gaussian": 0, "sparse_sign": 1, "srtt": 2}
 STATUS = {0: "ok", 1: "invalid argument", 2: "workspace", 3: "non-finite", 4: "rank deficient",
           5: "timeout", 6: "cuda error", 7: "unsupported"}
 
@@ -116,6 +116,16 @@ def _colmajor(A):
     return At, max(At.shape[0], 1)
 
 
+def _pad16(A):
+    """A copy of a column-major A whose columns start on 16-byte boundaries (the tensor-core
+    paths stream A with TMA)."""
+    m, n = A.shape
+    ld4 = (m + 3) // 4 * 4
+    Ap = torch.empty(n, ld4, dtype=A.dtype, device=A.device).t()
+    Ap[:m].copy_(A)
+    return Ap[:m], ld4
+
+
 def _rowmajor(X):
     if X.dim() != 2:
         raise ValueError("expected a matrix")
@@ -158,11 +168,7 @@ def sketch(A, l, kind="gaussian", prec="f32", seed=0, zeta=8, X=None, status=Non
     A, lda = _colmajor(A)
     m, n = A.shape
     if prec in ("tf32", "bf16", "fp8") and (lda % 4 or A.data_ptr() % 16):
-        # the tensor-core path streams A with TMA: 16-byte aligned columns required
-        ld4 = (m + 3) // 4 * 4
-        Ap = torch.empty(n, ld4, dtype=A.dtype, device=A.device).t()
-        Ap[:m].copy_(A)
-        A, lda = Ap[:m], ld4
+        A, lda = _pad16(A)
     xdt = torch.float64 if prec == "f64" else torch.float32
     if X is None:
         X = torch.empty(l, n, dtype=xdt, device=A.device)
@@ -195,6 +201,8 @@ def sketch_cols(A, l, prec="f32", seed=1, status=None):
     streaming skeleton selection (Algorithm 3); LUPP on Yt gives the row skeletons."""
     A, lda = _colmajor(A)
     m, n = A.shape
+    if prec in ("tf32", "bf16") and (lda % 4 or A.data_ptr() % 16):
+        A, lda = _pad16(A)
     Yt = torch.empty(l, m, dtype=torch.float64 if prec == "f64" else torch.float32, device=A.device)
     st = status if status is not None else new_status(A.device)
     _call("skel_sketch_cols", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, l, PREC[prec], seed, _ptr(Yt), m, w, sz,
@@ -209,8 +217,7 @@ def skeletonize_streaming(A, k, p=10, seed=0, seed_omega=None, prec="f32", statu
     st = status if status is not None else new_status(A.device)
     l = k + p
     X, _ = sketch(A, l, prec=prec, seed=seed, status=st)
-    Yt, _ = sketch_cols(A, l, prec="f64" if prec == "f64" else "f32",
-                        seed=seed + 1 if seed_omega is None else seed_omega, status=st)
+    Yt, _ = sketch_cols(A, l, prec=prec, seed=seed + 1 if seed_omega is None else seed_omega, status=st)
     Js, _, _, _ = pivot_lupp(X, k, factors=False, status=st)
     Is, _, _, _ = pivot_lupp(Yt, k, factors=False, status=st)
     return Js, Is, st

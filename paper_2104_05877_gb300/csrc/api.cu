@@ -89,6 +89,46 @@ skel_status skel_sketch(int64_t m, int64_t n, skel_dtype a_dtype, const void* A,
                           stream);
 }
 
+namespace {
+
+// X = Gamma A for the SRTT (Sec. 2.3, item 2): the permutation / sign / selection tables,
+// then the tensor-core kernel generating Gamma's tiles from them (TF32, BF16) or a dense
+// Gamma and the SIMT GEMM (FP64, FP32).
+skel_status sketch_srtt(int64_t m, int64_t n, skel_dtype a_dtype, const void* A, int64_t lda, int32_t l,
+                        skel_prec prec, uint64_t seed, void* X, int64_t ldx, void* ws, size_t* ws_bytes,
+                        int32_t* dev_status, cudaStream_t stream) {
+  const bool tensor = prec == SKEL_PREC_TF32 || prec == SKEL_PREC_BF16;
+  const skel_dtype x_dt = prec == SKEL_PREC_F64 ? SKEL_F64 : SKEL_F32;
+  Arena ar(ws);
+  int32_t* tab = static_cast<int32_t*>(ar.take(sizeof(int32_t) * srtt_table_words(m)));
+  int32_t* sel = static_cast<int32_t*>(ar.take(sizeof(int32_t) * (size_t)l));
+  void* G = !tensor ? ar.take(esize(x_dt) * (size_t)l * m) : nullptr;
+  void* tcws = tensor && n > 0 ? ar.take(sketch_tc_workspace(m, n, l, prec, true)) : nullptr;
+  skel_status st;
+  if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+  if (n == 0) return SKEL_OK;
+  SK_CUDA(launch_srtt_tables(m, l, seed, tab, sel, stream));
+  if (tensor) {
+    const cudaError_t e = launch_sketch_tc(0, m, n, static_cast<const float*>(A), lda, l, prec, seed,
+                                           static_cast<float*>(X), ldx, tcws, dev_status, stream, tab, sel);
+    if (e == cudaErrorNotSupported) return SKEL_ERR_UNSUPPORTED;
+    SK_CUDA(e);
+    return SKEL_OK;
+  }
+  SK_CUDA(launch_srtt_dense(m, l, tab, sel, x_dt, G, m, stream));
+  GemmArgs a{};
+  a.M = l; a.N = n; a.K = m;
+  a.L = View{G, m, 1}; a.l_dt = x_dt;
+  a.B = View{A, 1, lda}; a.b_dt = a_dtype;
+  a.out = X; a.out_sr = ldx; a.out_sc = 1; a.out_dt = x_dt;
+  a.alpha = 1.0 / std::sqrt((double)l);
+  a.dev_status = dev_status;
+  SK_CUDA(launch_gemm(a, prec == SKEL_PREC_F64, LEFT_LOAD, EPI_SKETCH, stream));
+  return SKEL_OK;
+}
+
+}  // namespace
+
 skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dtype, const void* A,
                              int64_t lda, int32_t l, skel_sketch_kind kind, int32_t zeta, skel_prec prec,
                              uint64_t seed, void* X, int64_t ldx, void* ws, size_t* ws_bytes,
@@ -100,8 +140,15 @@ skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dt
   if (m > 0xFFFFFFFFll || n > 0xFFFFFFFFll) return SKEL_ERR_INVALID_ARG;
   if (prec < SKEL_PREC_F64 || prec > SKEL_PREC_FP8) return SKEL_ERR_INVALID_ARG;
   if (prec == SKEL_PREC_F64 && a_dtype != SKEL_F64) return SKEL_ERR_INVALID_ARG;
-  if (kind != SKEL_SKETCH_GAUSSIAN && kind != SKEL_SKETCH_SPARSE_SIGN) return SKEL_ERR_INVALID_ARG;
+  if (kind != SKEL_SKETCH_GAUSSIAN && kind != SKEL_SKETCH_SPARSE_SIGN && kind != SKEL_SKETCH_SRTT)
+    return SKEL_ERR_INVALID_ARG;
   const skel_dtype x_dt = prec == SKEL_PREC_F64 ? SKEL_F64 : SKEL_F32;
+  if (kind == SKEL_SKETCH_SRTT) {
+    if (l > m || m > (int64_t)INT32_MAX) return SKEL_ERR_INVALID_ARG;
+    if (row0 != 0 || prec == SKEL_PREC_FP8) return SKEL_ERR_UNSUPPORTED;
+    if (prec != SKEL_PREC_F64 && a_dtype != SKEL_F32) return SKEL_ERR_UNSUPPORTED;
+    return sketch_srtt(m, n, a_dtype, A, lda, l, prec, seed, X, ldx, ws, ws_bytes, dev_status, stream);
+  }
   Arena ar(ws);
   int32_t* table = nullptr;
   if (kind == SKEL_SKETCH_SPARSE_SIGN) {
@@ -159,8 +206,25 @@ skel_status skel_sketch_cols(int64_t m, int64_t n, skel_dtype a_dtype, const voi
   if (m < 1 || n < 1 || l < 1 || l > 4096 || !valid_dtype(a_dtype) || A == nullptr || Yt == nullptr || lda < m ||
       ldy < m || n > 0xFFFFFFFFll)
     return SKEL_ERR_INVALID_ARG;
-  if (prec != SKEL_PREC_F64 && prec != SKEL_PREC_F32) return SKEL_ERR_UNSUPPORTED;
+  if (prec == SKEL_PREC_FP8) return SKEL_ERR_UNSUPPORTED;
   if ((prec == SKEL_PREC_F64) != (a_dtype == SKEL_F64)) return SKEL_ERR_INVALID_ARG;
+  if (prec == SKEL_PREC_TF32 || prec == SKEL_PREC_BF16) {
+    // the tensor-core sketch on a transposed copy (A^T, n x m column-major): its K dimension
+    // (A's columns) must be contiguous, and Omega's counters are those of the SIMT path
+    if (m > (int64_t)INT32_MAX) return SKEL_ERR_UNSUPPORTED;
+    const int64_t n4 = (n + 3) / 4 * 4;
+    Arena ar(ws);
+    float* At = static_cast<float*>(ar.take(sizeof(float) * (size_t)n4 * m));
+    void* tcws = ar.take(sketch_tc_workspace(n, m, l, prec));
+    skel_status st;
+    if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+    SK_CUDA(launch_transpose_f32(m, n, static_cast<const float*>(A), lda, At, n4, stream));
+    const cudaError_t e = launch_sketch_tc(0, n, m, At, n4, l, prec, seed, static_cast<float*>(Yt), ldy, tcws,
+                                           dev_status, stream);
+    if (e == cudaErrorNotSupported) return SKEL_ERR_UNSUPPORTED;
+    SK_CUDA(e);
+    return SKEL_OK;
+  }
   const bool f64 = prec == SKEL_PREC_F64;
   Arena ar(ws);
   void* kws = ar.take(gemm_workspace(l, m, n, f64));
@@ -189,6 +253,34 @@ skel_status skel_sketch_power(int64_t m, int64_t n, skel_dtype a_dtype, const vo
   const bool f64 = prec == SKEL_PREC_F64;
   const skel_dtype dt = f64 ? SKEL_F64 : SKEL_F32;
   const bool tcw = !f64 && gemm_tc_usable(m, n, l, nullptr, m, A, lda);
+  if (prec == SKEL_PREC_TF32 && tcw && m <= (int64_t)INT32_MAX) {
+    // tensor cores throughout, on A and a transposed copy A^T (n x m column-major):
+    // Y^T = Omega A^T by the TF32 sketch kernel (Omega generated), then X = Y^T A and, for
+    // further iterations, Y^T = X A^T by the 3xTF32 GEMM
+    const int64_t n4 = (n + 3) / 4 * 4;
+    Arena ar(ws);
+    float* At = static_cast<float*>(ar.take(sizeof(float) * (size_t)n4 * m));
+    float* Ytf = static_cast<float*>(ar.take(sizeof(float) * (size_t)l * m));
+    void* tcws = ar.take(sketch_tc_workspace(n, m, l, prec));
+    void* kx = ar.take(gemm_tc_workspace(m, n, l));
+    void* ky = ar.take(q > 1 ? gemm_tc_workspace(n, m, l) : 0);
+    skel_status st;
+    if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+    float* Xf = static_cast<float*>(X);
+    SK_CUDA(launch_transpose_f32(m, n, static_cast<const float*>(A), lda, At, n4, stream));
+    for (int it = 0; it < q; ++it) {
+      if (it == 0) {
+        const cudaError_t e = launch_sketch_tc(0, n, m, At, n4, l, prec, seed, Ytf, m, tcws, dev_status, stream);
+        if (e == cudaErrorNotSupported) return SKEL_ERR_UNSUPPORTED;
+        SK_CUDA(e);
+      } else {
+        SK_CUDA(launch_gemm_tc_tn(n, m, l, Xf, ldx, At, n4, Ytf, m, nullptr, ky, dev_status, stream));
+      }
+      SK_CUDA(launch_gemm_tc_tn(m, n, l, Ytf, m, static_cast<const float*>(A), lda, Xf, ldx, nullptr, kx,
+                                dev_status, stream));
+    }
+    return SKEL_OK;
+  }
   Arena ar(ws);
   void* Yt = ar.take(esize(dt) * (size_t)l * m);                  // Y^T = X_prev A^T, l x m row-major
   void* kws1 = ar.take(gemm_workspace(l, m, n, f64));

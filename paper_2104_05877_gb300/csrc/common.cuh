@@ -39,6 +39,70 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, ui
 
 constexpr uint32_t kTagGaussian = 0;
 constexpr uint32_t kTagSparse = 1;
+constexpr uint32_t kTagSrttPerm = 2;
+constexpr uint32_t kTagSrttSelect = 3;
+constexpr uint32_t kTagSrttSign = 4;
+
+// ------------------------------------------------------------------------------------
+// SRTT randomness (Sec. 2.3, item 2).  A keyed pseudo-random permutation of 0..m-1: a
+// balanced 4-round Feistel network on 2h bits (Luby-Rackoff), 4^h >= m, round function =
+// Philox word x of the counter (R, round, tag, 0) masked to h bits, mapped onto 0..m-1 by
+// cycle walking (Black-Rogaway: re-apply the network until the value is below m; the cycle
+// through x returns to x within 4^h applications, so the loop is bounded).
+// ------------------------------------------------------------------------------------
+__host__ __device__ inline int feistel_half_bits(int64_t m) {
+  int h = 1;
+  while ((int64_t)1 << (2 * h) < m) ++h;
+  return h;
+}
+
+__host__ __device__ __forceinline__ uint32_t feistel_perm(uint32_t x, uint32_t m, int h, uint32_t k0, uint32_t k1,
+                                                 uint32_t tag) {
+  const uint32_t mask = (1u << h) - 1u;
+  const uint64_t walks = (uint64_t)1 << (2 * h);
+  uint32_t y = x;
+  for (uint64_t w = 0; w <= walks; ++w) {
+    uint32_t L = y >> h, R = y & mask;
+#pragma unroll
+    for (uint32_t rnd = 0; rnd < 4; ++rnd) {
+      const uint32_t f = philox4x32_10(make_uint4(R, rnd, tag, 0u), k0, k1).x & mask;
+      const uint32_t t = L ^ f;
+      L = R;
+      R = t;
+    }
+    y = (L << h) | R;
+    if (y < m) break;
+  }
+  return y;
+}
+
+// (a * b) mod m for a, b < m < 2^31 by Barrett reduction with minv = floor((2^64 - 1) / m):
+// the quotient estimate is low by at most one, so one correction suffices.
+__device__ __forceinline__ uint32_t mulmod_barrett(uint32_t a, uint32_t b, uint32_t m, uint64_t minv) {
+  const uint64_t prod = (uint64_t)a * b;
+  const uint64_t q = __umul64hi(prod, minv);
+  uint64_t r = prod - q * m;
+  if (r >= m) r -= m;
+  return (uint32_t)r;
+}
+
+// One SRTT entry without the 1/sqrt(l) scale: phi * cas(2 pi (sel * r mod m) / m), where the
+// table word t = r | (phi < 0) << 31 holds r = pi^{-1}(q) for column q of Gamma.
+__device__ __forceinline__ float srtt_entry_f32(uint32_t sel, int32_t t, uint32_t m, uint64_t minv,
+                                                float two_over_m) {
+  const uint32_t x = mulmod_barrett(sel, (uint32_t)t & 0x7fffffffu, m, minv);
+  float sn, cs;
+  sincospif((float)x * two_over_m, &sn, &cs);
+  const float v = cs + sn;
+  return t < 0 ? -v : v;
+}
+__device__ __forceinline__ double srtt_entry_f64(uint32_t sel, int32_t t, uint32_t m, uint64_t minv) {
+  const uint32_t x = mulmod_barrett(sel, (uint32_t)t & 0x7fffffffu, m, minv);
+  double sn, cs;
+  sincospi(2.0 * (double)x / (double)m, &sn, &cs);
+  const double v = cs + sn;
+  return t < 0 ? -v : v;
+}
 
 // u = (2*(x >> 9) + 1) * 2^-24: exact in FP32, in [2^-24, 1 - 2^-24].
 __device__ __forceinline__ float unit_open_f32(uint32_t x) {

@@ -411,6 +411,26 @@ __global__ void transpose_kernel(int32_t s, const double* in, int64_t ldi, doubl
   for (int c = threadIdx.x; c < s; c += blockDim.x) out[(int64_t)c * ldo + r] = in[(int64_t)r * ldi + c];
 }
 
+// At(j, i) = A(i, j) through a 32 x 32 shared-memory tile (padded against bank conflicts):
+// reads along A's columns and writes along At's columns are both 128-byte coalesced.
+__global__ void transpose_f32_kernel(int64_t m, int64_t n, const float* A, int64_t lda, float* At, int64_t ldt) {
+  __shared__ float tile[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  for (int64_t j0 = (int64_t)blockIdx.y * 32; j0 < n; j0 += (int64_t)gridDim.y * 32) {
+    for (int c = ty; c < 32; c += 8) {
+      const int64_t i = i0 + tx, j = j0 + c;
+      if (i < m && j < n) tile[c][tx] = A[j * lda + i];
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int64_t i = i0 + r, j = j0 + tx;
+      if (i < m && j < n) At[i * ldt + j] = tile[tx][r];
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void fill_kernel(double* d, int64_t count, double v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -540,6 +560,20 @@ cudaError_t launch_gather_cols_rowmajor_f64(int32_t s, skel_dtype dt, const void
 cudaError_t launch_transpose_f64(int32_t s, const double* in, int64_t ldi, double* out,
                                  int64_t ldo, cudaStream_t st) {
   transpose_kernel<<<s, 256, 0, st>>>(s, in, ldi, out, ldo);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_f32(int64_t m, int64_t n, const float* A, int64_t lda, float* At, int64_t ldt,
+                                 cudaStream_t st) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  const int64_t gx = (m + 31) / 32;
+  if (gx > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)gx, (unsigned)std::min<int64_t>((n + 31) / 32, 65535));
+  {
+    KernelTimer kt("transpose", st);
+    transpose_f32_kernel<<<grid, dim3(32, 8), 0, st>>>(m, n, A, lda, At, ldt);
+  }
   note_launches(1);
   return cudaGetLastError();
 }

@@ -75,6 +75,9 @@ cudaError_t launch_gather_cols_rowmajor_f64(int32_t s, skel_dtype dt, const void
 // out = in^T for an s x s row-major FP64 matrix.
 cudaError_t launch_transpose_f64(int32_t s, const double* in, int64_t ldi, double* out,
                                  int64_t ldo, cudaStream_t st);
+// At = A^T for an m x n column-major FP32 A: At is n x m column-major (ld = ldt >= n).
+cudaError_t launch_transpose_f32(int64_t m, int64_t n, const float* A, int64_t lda, float* At, int64_t ldt,
+                                 cudaStream_t st);
 // Set d[0..count) = value.
 cudaError_t launch_fill_f64(double* d, int64_t count, double value, cudaStream_t st);
 
@@ -149,15 +152,27 @@ cudaError_t launch_gauss_sketch_csc(int64_t m, int64_t n, const int64_t* col_ptr
 
 // Tensor-core Gaussian sketch (sketch_tc.cu).  Returns cudaErrorNotSupported when the
 // shape or alignment is outside what the kernel handles.  ws: sketch_tc_workspace bytes.
-size_t sketch_tc_workspace(int64_t m, int64_t n, int32_t l, skel_prec prec);
+size_t sketch_tc_workspace(int64_t m, int64_t n, int32_t l, skel_prec prec, bool srtt = false);
 // FP8 (e4m3, per-128-row power-of-two scales) sketch (sketch_fp8.cu): quantisation pre-pass,
 // e4m3 Gamma, tcgen05 kind::f8f6f4.  ws: sketch_fp8_workspace bytes.
 size_t sketch_fp8_workspace(int64_t m, int64_t n, int32_t l);
 cudaError_t launch_sketch_fp8(int64_t row0, int64_t m, int64_t n, const float* A, int64_t lda, int32_t l,
                               uint64_t seed, float* X, int64_t ldx, void* ws, int32_t* dev_status, cudaStream_t st);
+// With srtt_tab / srtt_sel non-null (row0 = 0), Gamma is the SRTT's (srtt.cu tables) instead
+// of the Gaussian's.
 cudaError_t launch_sketch_tc(int64_t row0, int64_t m, int64_t n, const float* A, int64_t lda, int32_t l,
                              skel_prec prec, uint64_t seed, float* X, int64_t ldx, void* ws,
-                             int32_t* dev_status, cudaStream_t st);
+                             int32_t* dev_status, cudaStream_t st, const int32_t* srtt_tab = nullptr,
+                             const int32_t* srtt_sel = nullptr);
+
+// SRTT embedding (srtt.cu): tab (srtt_table_words(m) int32, 16-byte aligned) holds
+// pi^{-1}(q) | (phi < 0) << 31 per column q of Gamma, sel the l selected rows; the dense
+// Gamma * sqrt(l) (l x m row-major, ldg) for the SIMT GEMM.
+uint64_t srtt_minv(int64_t m);
+size_t srtt_table_words(int64_t m);
+cudaError_t launch_srtt_tables(int64_t m, int32_t l, uint64_t seed, int32_t* tab, int32_t* sel, cudaStream_t st);
+cudaError_t launch_srtt_dense(int64_t m, int32_t l, const int32_t* tab, const int32_t* sel, skel_dtype dt, void* G,
+                              int64_t ldg, cudaStream_t st);
 
 int device_sm_count();
 // Number of kernels this library has launched in the process (diagnostics).

@@ -49,6 +49,7 @@ namespace cg = cooperative_groups;
 using namespace tc;
 
 constexpr int OP_TF32 = 0, OP_BF16 = 1;
+constexpr int GEN_GAUSS = 0, GEN_SRTT = 1;
 
 constexpr int TC_M = 128;
 constexpr int TC_BK = 32;              // K elements per stage (one 128-byte FP32 row of A)
@@ -90,6 +91,10 @@ struct TcParams {
   float scale;            // applied when P == 1
   int direct;             // P == 1
   int32_t* dev_status;
+  const int32_t* srtt_tab;   // GEN_SRTT: pi^{-1}(q) | (phi < 0) << 31, padded to a multiple of 4
+  const int32_t* srtt_sel;   // GEN_SRTT: the l selected rows
+  uint64_t srtt_minv;        // floor((2^64 - 1) / m)
+  float srtt_two_over_m;
 };
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -97,7 +102,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-template <int OP>
+template <int OP, int GEN>
 __global__ void __launch_bounds__(SkCfg<OP>::THREADS, 1)
 sketch_tc_kernel(const __grid_constant__ CUtensorMap tmapA, const TcParams p) {
   using C = SkCfg<OP>;
@@ -247,7 +252,17 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap tmapA, const TcParams p) {
         const int64_t k = kt + 4 * grp;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (row < p.l && k < p.m) {
-          v = gaussian4_f32(p.k0s, p.k1s, (uint32_t)row, (uint32_t)((p.grow0 + k) >> 2));
+          if constexpr (GEN == GEN_SRTT) {
+            // the table is padded to a multiple of 4 words: k .. k+3 are in bounds
+            const int4 t = __ldg(reinterpret_cast<const int4*>(p.srtt_tab + k));
+            const uint32_t s = (uint32_t)__ldg(p.srtt_sel + row), mm = (uint32_t)p.m;
+            v = make_float4(srtt_entry_f32(s, t.x, mm, p.srtt_minv, p.srtt_two_over_m),
+                            srtt_entry_f32(s, t.y, mm, p.srtt_minv, p.srtt_two_over_m),
+                            srtt_entry_f32(s, t.z, mm, p.srtt_minv, p.srtt_two_over_m),
+                            srtt_entry_f32(s, t.w, mm, p.srtt_minv, p.srtt_two_over_m));
+          } else {
+            v = gaussian4_f32(p.k0s, p.k1s, (uint32_t)row, (uint32_t)((p.grow0 + k) >> 2));
+          }
           if (k + 1 >= p.m) v.y = 0.f;
           if (k + 2 >= p.m) v.z = 0.f;
           if (k + 3 >= p.m) v.w = 0.f;
@@ -387,12 +402,12 @@ struct TcPlan {
 };
 
 // Resident clusters of CJ CTAs of the kernel (0 if that cluster shape cannot be launched).
-template <int OP>
+template <int OP, int GEN>
 int active_clusters(int CJ) {
   static int cache[5] = {-1, -1, -1, -1, -1};
   if (cache[CJ] >= 0) return cache[CJ];
   int nc = 0;
-  if (cudaFuncSetAttribute(sketch_tc_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(sketch_tc_kernel<OP, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)SkCfg<OP>::SMEM) == cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(1, CJ, 1);
@@ -405,14 +420,14 @@ int active_clusters(int CJ) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&nc, sketch_tc_kernel<OP>, &cfg) != cudaSuccess) nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, sketch_tc_kernel<OP, GEN>, &cfg) != cudaSuccess) nc = 0;
   }
   cudaGetLastError();
   cache[CJ] = nc;
   return nc;
 }
 
-template <int OP>
+template <int OP, int GEN>
 TcPlan plan_tc(int64_t m, int64_t n, int l) {
   TcPlan pl{};
   pl.lblocks = (l + TC_M - 1) / TC_M;
@@ -421,7 +436,7 @@ TcPlan plan_tc(int64_t m, int64_t n, int l) {
   int slots = device_sm_count();
   for (int cj : {4, 2}) {
     if (pl.jtiles % cj != 0) continue;
-    const int nc = active_clusters<OP>(cj);
+    const int nc = active_clusters<OP, GEN>(cj);
     if (nc > 0) {
       pl.CJ = cj;
       slots = nc * cj;
@@ -429,7 +444,7 @@ TcPlan plan_tc(int64_t m, int64_t n, int l) {
     }
   }
   if (pl.CJ == 1) {
-    const int nc = active_clusters<OP>(1);
+    const int nc = active_clusters<OP, GEN>(1);
     if (nc > 0) slots = nc;
   }
   const int64_t ksteps = (m + TC_BK - 1) / TC_BK;
@@ -439,9 +454,10 @@ TcPlan plan_tc(int64_t m, int64_t n, int l) {
   return pl;
 }
 
-template <int OP>
+template <int OP, int GEN>
 cudaError_t launch_tc_op(int64_t row0, int64_t m, int64_t n, const float* A, int64_t lda, int32_t l, uint64_t seed,
-                         float* X, int64_t ldx, void* ws, int32_t* dev_status, cudaStream_t st) {
+                         float* X, int64_t ldx, void* ws, int32_t* dev_status, cudaStream_t st,
+                         const int32_t* srtt_tab, const int32_t* srtt_sel) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap tmap;
@@ -453,7 +469,7 @@ cudaError_t launch_tc_op(int64_t row0, int64_t m, int64_t n, const float* A, int
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorNotSupported;
-  const TcPlan pl = plan_tc<OP>(m, n, l);
+  const TcPlan pl = plan_tc<OP, GEN>(m, n, l);
   TcParams p{};
   p.m = m; p.n = n; p.l = l;
   p.P = pl.P;
@@ -467,7 +483,11 @@ cudaError_t launch_tc_op(int64_t row0, int64_t m, int64_t n, const float* A, int
   p.ldo = p.direct ? ldx : n;
   p.part_stride = (int64_t)l * n;
   p.dev_status = dev_status;
-  cudaError_t e = cudaFuncSetAttribute(sketch_tc_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  p.srtt_tab = srtt_tab;
+  p.srtt_sel = srtt_sel;
+  p.srtt_minv = srtt_minv(m);
+  p.srtt_two_over_m = (float)(2.0 / (double)m);
+  cudaError_t e = cudaFuncSetAttribute(sketch_tc_kernel<OP, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)SkCfg<OP>::SMEM);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -484,7 +504,7 @@ cudaError_t launch_tc_op(int64_t row0, int64_t m, int64_t n, const float* A, int
   cfg.numAttrs = 1;
   {
     KernelTimer kt("sketch_tc", st);
-    e = cudaLaunchKernelEx(&cfg, sketch_tc_kernel<OP>, tmap, p);
+    e = cudaLaunchKernelEx(&cfg, sketch_tc_kernel<OP, GEN>, tmap, p);
   }
   note_launches(1);
   if (e != cudaSuccess || p.direct) return e;
@@ -496,20 +516,31 @@ cudaError_t launch_tc_op(int64_t row0, int64_t m, int64_t n, const float* A, int
 
 }  // namespace
 
-size_t sketch_tc_workspace(int64_t m, int64_t n, int32_t l, skel_prec prec) {
-  const TcPlan pl = prec == SKEL_PREC_BF16 ? plan_tc<OP_BF16>(m, n, l) : plan_tc<OP_TF32>(m, n, l);
+size_t sketch_tc_workspace(int64_t m, int64_t n, int32_t l, skel_prec prec, bool srtt) {
+  const bool bf = prec == SKEL_PREC_BF16;
+  const TcPlan pl = srtt ? (bf ? plan_tc<OP_BF16, GEN_SRTT>(m, n, l) : plan_tc<OP_TF32, GEN_SRTT>(m, n, l))
+                         : (bf ? plan_tc<OP_BF16, GEN_GAUSS>(m, n, l) : plan_tc<OP_TF32, GEN_GAUSS>(m, n, l));
   return pl.P > 1 ? align_up(sizeof(float) * (size_t)pl.P * l * n) : 0;
 }
 
 cudaError_t launch_sketch_tc(int64_t row0, int64_t m, int64_t n, const float* A, int64_t lda, int32_t l,
                              skel_prec prec, uint64_t seed, float* X, int64_t ldx, void* ws,
-                             int32_t* dev_status, cudaStream_t st) {
+                             int32_t* dev_status, cudaStream_t st, const int32_t* srtt_tab,
+                             const int32_t* srtt_sel) {
   if (prec != SKEL_PREC_TF32 && prec != SKEL_PREC_BF16) return cudaErrorNotSupported;
+  const bool srtt = srtt_tab != nullptr;
+  if (srtt && (srtt_sel == nullptr || row0 != 0 || (reinterpret_cast<uintptr_t>(srtt_tab) & 15) != 0))
+    return cudaErrorNotSupported;
   if (m < 1 || n < 1) return cudaErrorNotSupported;
   if ((lda % 4) != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
   if (m > (int64_t)INT32_MAX || n > (int64_t)INT32_MAX) return cudaErrorNotSupported;
-  return prec == SKEL_PREC_BF16 ? launch_tc_op<OP_BF16>(row0, m, n, A, lda, l, seed, X, ldx, ws, dev_status, st)
-                                : launch_tc_op<OP_TF32>(row0, m, n, A, lda, l, seed, X, ldx, ws, dev_status, st);
+  if (srtt)
+    return prec == SKEL_PREC_BF16
+               ? launch_tc_op<OP_BF16, GEN_SRTT>(0, m, n, A, lda, l, seed, X, ldx, ws, dev_status, st, srtt_tab, srtt_sel)
+               : launch_tc_op<OP_TF32, GEN_SRTT>(0, m, n, A, lda, l, seed, X, ldx, ws, dev_status, st, srtt_tab, srtt_sel);
+  return prec == SKEL_PREC_BF16
+             ? launch_tc_op<OP_BF16, GEN_GAUSS>(row0, m, n, A, lda, l, seed, X, ldx, ws, dev_status, st, nullptr, nullptr)
+             : launch_tc_op<OP_TF32, GEN_GAUSS>(row0, m, n, A, lda, l, seed, X, ldx, ws, dev_status, st, nullptr, nullptr);
 }
 
 }  // namespace skel

@@ -61,6 +61,13 @@ def test_invalid_arguments_rejected_on_host(L):
     # sparse sign zeta > l
     assert L.skel_sketch(10, 10, 0, ctypes.c_void_p(16), 10, 4, 1, 8, 0, 1, ctypes.c_void_p(16), 10,
                          None, ctypes.byref(sz), None, None) == 1
+    # SRTT: l > m is invalid; a row offset and FP8 are not supported
+    assert L.skel_sketch(10, 10, 0, ctypes.c_void_p(16), 10, 11, 2, 8, 0, 1, ctypes.c_void_p(16), 10,
+                         None, ctypes.byref(sz), None, None) == 1
+    assert L.skel_sketch_rows(4, 10, 10, 0, ctypes.c_void_p(16), 10, 4, 2, 8, 0, 1, ctypes.c_void_p(16),
+                              10, None, ctypes.byref(sz), None, None) == 7
+    assert L.skel_sketch(10, 10, 1, ctypes.c_void_p(16), 12, 4, 2, 8, 4, 1, ctypes.c_void_p(16), 10,
+                         None, ctypes.byref(sz), None, None) == 7
     # row-partitioned sketch: row0 not a multiple of 4, negative
     for row0 in (2, -4):
         assert L.skel_sketch_rows(row0, 10, 10, 0, ctypes.c_void_p(16), 10, 4, 0, 8, 0, 1, ctypes.c_void_p(16),

@@ -185,18 +185,22 @@ def test_mixed_path_z_accuracy(skel, dev):
     assert rel <= 10 * np.linalg.cond(Ad[:, J]) * 2.0 ** -24, rel
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_column_sketch(skel, dev, prec):
-    """Yt = Omega A^T (the column sketch of Algorithm 3) against the oracle's."""
+@pytest.mark.parametrize("prec,m,n", [("f64", 700, 450), ("f32", 700, 450), ("tf32", 700, 450), ("bf16", 700, 450),
+                                       ("tf32", 701, 449), ("tf32", 3000, 2500)])
+def test_column_sketch(skel, dev, prec, m, n):
+    """Yt = Omega A^T (the column sketch of Algorithm 3) against the oracle's: SIMT FP64 / FP32
+    to rounding; TF32 / BF16 by the tensor-core sketch on a transposed copy of A, within the
+    operand rounding (2^-9 / 2^-7 relative per product) plus FP32 accumulation."""
     dt = np.float64 if prec == "f64" else np.float32
-    A = workloads.dense_config2(700, 450, seed=4, dtype=dt)
+    A = workloads.dense_config2(m, n, seed=4, dtype=dt)
     Yt, st = skel.sketch_cols(torch.from_numpy(A).to(dev), 37, prec=prec, seed=9)
     skel.check_status(st)
     want = sketch.gaussian_col_sketch(A.astype(np.float64), 37, 9)
-    Om = np.abs(oracle.embedding.gaussian_normals(37, 450, 9)) / np.sqrt(37)
+    Om = np.abs(oracle.embedding.gaussian_normals(37, n, 9)) / np.sqrt(37)
     mag = Om @ np.abs(A.astype(np.float64)).T
     u = 2.0 ** -52 if prec == "f64" else 2.0 ** -23
-    assert np.all(np.abs(Yt.cpu().numpy() - want) <= 4 * 450 * u * mag)
+    op = {"f64": 0.0, "f32": 0.0, "tf32": 2.0 ** -9, "bf16": 2.0 ** -7}[prec]
+    assert np.all(np.abs(Yt.cpu().numpy() - want) <= (op + 4 * n * u) * mag)
 
 
 def test_streaming_skeleton_selection(skel, dev):
@@ -240,3 +244,19 @@ def test_cur_sketch_core(skel, dev, dt, m, n, k):
     assert np.linalg.norm(Ug - Ur) <= 50 * k * kappa * u * np.linalg.norm(Ur)
     M = Ad[:, Js] @ Ug @ Ad[Is, :]
     assert np.linalg.norm(M[Is, :] - Ad[Is, :]) <= 50 * k * kappa * u * np.linalg.norm(Ad[Is, :])
+
+
+def test_streaming_selection_tensor_cores(skel, dev):
+    """Algorithm 3 with both sketches on the tensor cores (TF32): the CUR error of the
+    device's skeletons within 1.05x of the FP64 oracle's."""
+    A = workloads.dense_config2(1200, 1000, seed=5, dtype=np.float32)
+    k, p = 40, 10
+    Js, Is, st = skel.skeletonize_streaming(torch.from_numpy(A).to(dev), k, p, seed=7, seed_omega=8, prec="tf32")
+    torch.cuda.synchronize()
+    skel.check_status(st)
+    Ad = A.astype(np.float64)
+    ref = oracle.skeleton.streaming_skeletonize(Ad, k, p, 7, 8)
+    J, I = Js.cpu().numpy(), Is.cpu().numpy()
+    assert len(set(J.tolist())) == k and len(set(I.tolist())) == k
+    e_gpu = errors.rel_cur_error(Ad, J, decomp.cur(Ad, J, I), I)
+    assert e_gpu <= 1.05 * ref["err_cur"]

@@ -224,18 +224,23 @@ def test_sketch_row_blocks_sum_to_the_sketch(skel, dev, prec, kind):
     assert np.all(np.abs(got - want) <= (op + 4 * m * u) * mag)
 
 
-@pytest.mark.parametrize("prec,q", [("f64", 1), ("f64", 2), ("f32", 1), ("tf32", 1), ("tf32", 2)])
-def test_sketch_power_iteration(skel, dev, prec, q):
+@pytest.mark.parametrize("prec,q,m,n", [("f64", 1, 700, 500), ("f64", 2, 700, 500), ("f32", 1, 700, 500),
+                                         ("tf32", 1, 700, 500), ("tf32", 2, 700, 500), ("tf32", 1, 701, 499),
+                                         ("tf32", 2, 4100, 2050)])
+def test_sketch_power_iteration(skel, dev, prec, q, m, n):
     """X = Omega (A^T A)^q (Rand-LUPP-1piter for q = 1) against the oracle's definition: FP64
-    to rounding, FP32 paths (SIMT Omega A^T, 3xTF32 or SIMT (.) A) to FP32 accuracy."""
-    m, n, l = 700, 500, 40
+    to rounding; FP32 (SIMT) to FP32 accuracy; TF32 takes Omega A^T from the TF32 sketch kernel
+    on a transposed copy of A (TF32 operands, 2^-10 relative each, errors of random sign:
+    about 2^-11 of the norm) and the later products by 3xTF32, so it is held to 4e-3 per
+    iteration -- the sketch's own precision, which is all pivot selection uses."""
+    l = 40
     dt = np.float64 if prec == "f64" else np.float32
     A = workloads.dense_config2(m, n, seed=31, dtype=dt)
     X, st = skel.sketch_power(torch.from_numpy(A).to(dev), l, q=q, prec=prec, seed=17)
     skel.check_status(st)
     want = sketch.gaussian_sketch_power(A.astype(np.float64), l, 17, q)
     rel = np.linalg.norm(X.cpu().numpy() - want) / np.linalg.norm(want)
-    assert rel <= (1e-12 if prec == "f64" else 2e-5 * q), rel
+    assert rel <= {"f64": 1e-12, "f32": 2e-5 * q, "tf32": 4e-3 * q}[prec], rel
 
 
 @pytest.mark.parametrize("m,n,l", [(1000, 777, 61), (2048, 1536, 272), (300, 129, 40), (4100, 600, 130),

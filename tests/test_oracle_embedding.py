@@ -263,3 +263,16 @@ def test_srtt_skeleton_exact_on_exactly_low_rank():
     A = workloads.exact_rank(300, 200, 15, seed=7)
     out = skeleton.skeletonize(A, k=15, p=5, seed=11, kind="srtt")
     assert out["err_id"] < 1e-12
+
+
+def test_srtt_entries_closed_form():
+    """Multiplying out sqrt(m/l) Pi_{m->l} T Phi Pi_{m->m} gives, entry by entry,
+    Gamma(i, q) = phi_r cas(2 pi sel(i) r / m) / sqrt(l) with r = pi^{-1}(q); the oracle's
+    FFT route agrees with it (m not a power of two included)."""
+    for m, l in ((300, 40), (256, 256), (97, 13)):
+        pi, phi, sel = embedding.srtt_parts(m, l, 21)
+        rinv = np.empty(m, dtype=np.int64)
+        rinv[pi] = np.arange(m)
+        ang = 2.0 * np.pi * ((sel[:, None] * rinv[None, :]) % m) / m
+        want = phi[rinv][None, :] * (np.cos(ang) + np.sin(ang)) / np.sqrt(l)
+        assert np.allclose(embedding.srtt_embedding(l, m, 21), want, atol=1e-13)
