@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--blocks", type=int, default=4096, help="blocks of the batched run (--only batch)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-GPU comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
-    ap.add_argument("--only", default=None, choices=["sketch", "lupp", "rows", "id", "cur", "eta", "batch", "next",
+    ap.add_argument("--only", default=None, choices=["sketch", "lupp", "rows", "pivots", "id", "cur", "eta", "batch", "next",
                                                      "srtt", "power", "cols"],
                     help="run only this call (warm-up + steps, no extras): a small command for profilers; "
                          "'batch' runs the batched configuration (4096 Gaussian-kernel blocks, k_max 128, "
@@ -213,22 +213,21 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     st = skel.new_status(dev)
 
-    names = ["sketch", "lupp", "rows", "id", "cur", "eta"]
+    names = ["sketch", "pivots", "id", "cur", "eta"]
 
     def step(evs):
         evs[0].record()
         X, _ = skel.sketch(A, l, prec=args.prec, seed=seed_G, status=st)
         evs[1].record()
-        Js, _, Rf, _ = skel.pivot_lupp(X, k, status=st)
+        # column LUPP on X and row LUPP on C = A(:, Js), the latter pipelined behind the former
+        Js, Is, _, Rf, _ = skel.pivot_skeleton(X, A, k, status=st)
         evs[2].record()
-        Is, _ = skel.pivot_rows(A, Js, status=st)
-        evs[3].record()
         Z, sq_id, _ = skel.column_id(A, Js, status=st)
-        evs[4].record()
+        evs[3].record()
         _, U, sq_cur, _ = skel.cur(A, Js, Is, status=st)
-        evs[5].record()
+        evs[4].record()
         e, _ = skel.error(A, Js, Rf=Rf, status=st)
-        evs[6].record()
+        evs[5].record()
         return Js, Is, sq_id, sq_cur, e
 
     if args.only == "next":
@@ -241,6 +240,7 @@ def run_ours(args, rank, world):
         call = {"sketch": lambda: skel.sketch(A, l, prec=args.prec, seed=seed_G, X=X, status=st),
                 "lupp": lambda: skel.pivot_lupp(X, k, status=st),
                 "rows": lambda: skel.pivot_rows(A, Js, status=st),
+                "pivots": lambda: skel.pivot_skeleton(X, A, k, status=st),
                 "id": lambda: skel.column_id(A, Js, status=st),
                 "cur": lambda: skel.cur(A, Js, Is, status=st),
                 "eta": lambda: skel.error(A, Js, Rf=Rf, status=st),
@@ -262,7 +262,7 @@ def run_ours(args, rank, world):
                               "config": workload_config(k, p, args.prec)}), flush=True)
         return
 
-    mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+    mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
     for _ in range(args.warmup):
         step(mk())
     torch.cuda.synchronize()
@@ -299,9 +299,9 @@ def run_ours(args, rank, world):
     skel.check_status(st, "timed steps")
     total_ms = t_begin.elapsed_time(t_end)
     per = {nm: statistics.mean(ev[i].elapsed_time(ev[i + 1]) for ev in all_evs) for i, nm in enumerate(names)}
-    tts = statistics.mean(ev[0].elapsed_time(ev[3]) for ev in all_evs)
-    tid = per["sketch"] + per["lupp"] + per["id"]
-    tcur = statistics.mean(ev[0].elapsed_time(ev[5]) for ev in all_evs)
+    tts = statistics.mean(ev[0].elapsed_time(ev[2]) for ev in all_evs)
+    tid = per["sketch"] + per["pivots"] + per["id"]
+    tcur = statistics.mean(ev[0].elapsed_time(ev[4]) for ev in all_evs)
     if world > 1:
         t = torch.tensor([tts, total_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -373,22 +373,20 @@ def run_ours(args, rank, world):
     fp64 = None
     if not args.no_fp64:
         A64 = A.double().t().contiguous().t()
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         for rep in range(2):
             evs[0].record()
             X64, _ = skel.sketch(A64, l, prec="f64", seed=seed_G, status=st)
             evs[1].record()
-            J64, _, _, _ = skel.pivot_lupp(X64, k, factors=False, status=st)
+            J64, I64, _, _, _ = skel.pivot_skeleton(X64, A64, k, factors=False, status=st)
             evs[2].record()
-            I64, _ = skel.pivot_rows(A64, J64, status=st)
-            evs[3].record()
         torch.cuda.synchronize()
         _, sq64, _ = skel.column_id(A64, J64, status=st)
         torch.cuda.synchronize()
         skel.check_status(st, "fp64")
         sq64 = sq64.cpu().numpy()
-        fp64 = {"time_to_skeleton_ms": evs[0].elapsed_time(evs[3]), "sketch_ms": evs[0].elapsed_time(evs[1]),
-                "lupp_ms": evs[1].elapsed_time(evs[2]),
+        fp64 = {"time_to_skeleton_ms": evs[0].elapsed_time(evs[2]), "sketch_ms": evs[0].elapsed_time(evs[1]),
+                "pivots_ms": evs[1].elapsed_time(evs[2]),
                 "rel_id_error": float(np.sqrt(max(sq64[0] - sq64[1], 0.0) / sq64[0])),
                 "same_skeleton": bool(torch.equal(J64.cpu(), Js.cpu()))}
         del A64, X64
@@ -404,8 +402,7 @@ def run_ours(args, rank, world):
         A_dev.copy_(A_host, non_blocking=True)
         Ad = A_dev.t()
         X, _ = skel.sketch(Ad, l, prec=args.prec, seed=seed_G, status=st)
-        J, _, _, _ = skel.pivot_lupp(X, k, factors=False, status=st)
-        I, _ = skel.pivot_rows(Ad, J, status=st)
+        J, I, _, _, _ = skel.pivot_skeleton(X, Ad, k, factors=False, status=st)
         Js_h.copy_(J, non_blocking=True)
         Is_h.copy_(I, non_blocking=True)
 

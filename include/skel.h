@@ -246,6 +246,27 @@ skel_status skel_pivot_rows(int64_t m, int64_t n, skel_dtype dtype, const void* 
                             size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream);
 
 /*
+ * skel_pivot_skeleton -- both skeletons of Algorithm 2 (lines 3 and 4) in one call: the
+ * column LUPP of skel_pivot_lupp on X (Js, optional L and R), then the row LUPP of
+ * skel_pivot_rows on C = A(:, Js) (Is), with results identical to those two calls.  The row
+ * LUPP runs behind the column LUPP panel by panel: its panel of steps [t0, t0+b) needs only
+ * Js[0 .. t0+b), so it is factored on an auxiliary stream as soon as the column panel that
+ * ends those pivots is done; the caller's stream waits for both chains at the end.
+ *   dtype     : of X and of A (the same for both).
+ *   X, l, n, ldx : the sketch, l x n row-major;  A, m, lda : m x n column-major.
+ *   s         : skeletons, 1 <= s <= min(l, m, n, 1024).
+ *   Js, Is    : out int32[s];  L, R : optional, as skel_pivot_lupp.
+ * The auxiliary stream and its events are created once per device and shared by every call
+ * (calls are enqueued one at a time under a lock).  When a panel of either LUPP does not fit
+ * a thread-block cluster the two LUPPs run one after the other on the caller's stream.  A
+ * column LUPP that stops early (rank-deficient X) leaves Is at -1.
+ */
+skel_status skel_pivot_skeleton(skel_dtype dtype, const void* X, int64_t l, int64_t n, int64_t ldx, int32_t s,
+                                const void* A, int64_t m, int64_t lda, int32_t* Js, int32_t* Is, void* L,
+                                int64_t ldl, void* R, int64_t ldr, void* ws, size_t* ws_bytes, int32_t* dev_status,
+                                cudaStream_t stream);
+
+/*
  * skel_cur -- CUR A ~ C U R (Eq. (2.4)) with C = A(:, Js), R = A(Is, :) and U from the
  * stable form of Remark 3: U = R_C^{-1} (Q_C^T A Q_R) R_R^{-T}, where C = Q_C R_C and
  * R^T = Q_R R_R (Householder QR, FP64 for dtype F64, FP32 for F32; FP64 solves).

@@ -55,6 +55,8 @@ def lib():
                        szp, vp, vp],
         "skel_id_sketch": [i32, i32, i64, vp, i64, vp, vp, i64, vp, szp, vp, vp],
         "skel_cur_sketch": [i64, i64, i32, vp, i64, i32, vp, vp, vp, i64, vp, szp, vp, vp],
+        "skel_pivot_skeleton": [i32, vp, i64, i64, i64, i32, vp, i64, i64, vp, vp, vp, i64, vp, i64, vp, szp, vp,
+                                vp],
         "skel_sketch_power": [i64, i64, i32, vp, i64, i32, i32, i32, u64, vp, i64, vp, szp, vp, vp],
         "skel_sketch_cols": [i64, i64, i32, vp, i64, i32, i32, u64, vp, i64, vp, szp, vp, vp],
         "skel_debug_gaussian": [i32, i64, u64, ctypes.c_int, vp, vp],
@@ -244,6 +246,26 @@ def pivot_lupp(X, s, factors=True, status=None):
     _call("skel_pivot_lupp", lambda w, sz: [_dt(X), _ptr(X), l, n, ldx, s, _ptr(Js), _ptr(Lf), s,
                                             _ptr(Rf), n, w, sz, _ptr(st), _stream()], X.device)
     return Js, Lf, Rf, st
+
+
+def pivot_skeleton(X, A, s, factors=True, status=None):
+    """Js (LUPP on the sketch X) and Is (LUPP on C^T, C = A(:, Js)) in one call, the row LUPP
+    pipelined behind the column LUPP; returns (Js, Is, L, R, status), L and R as pivot_lupp."""
+    X, ldx = _rowmajor(X)
+    A, lda = _colmajor(A)
+    l, n = X.shape
+    m = A.shape[0]
+    if A.dtype != X.dtype:
+        raise ValueError("X and A must have the same dtype")
+    Js = torch.empty(s, dtype=torch.int32, device=X.device)
+    Is = torch.empty(s, dtype=torch.int32, device=X.device)
+    L = torch.empty(s, s, dtype=X.dtype, device=X.device) if factors else None
+    R = torch.empty(s, n, dtype=X.dtype, device=X.device) if factors else None
+    st = status if status is not None else new_status(X.device)
+    _call("skel_pivot_skeleton", lambda w, sz: [_dt(X), _ptr(X), l, n, ldx, s, _ptr(A), m, lda, _ptr(Js), _ptr(Is),
+                                                _ptr(L), s if factors else 0, _ptr(R), n if factors else 0, w, sz,
+                                                _ptr(st), _stream()], X.device)
+    return Js, Is, L, R, st
 
 
 def pivot_lupp_rows(C, s, status=None):

@@ -368,6 +368,33 @@ skel_status skel_pivot_lupp(skel_dtype dtype, const void* X, int64_t l, int64_t 
   return run_lupp_auto(dtype, X, n, ldx, s, Js, L, ldl, R, ldr, ws, *ws_bytes, dev_status, stream);
 }
 
+skel_status skel_pivot_skeleton(skel_dtype dtype, const void* X, int64_t l, int64_t n, int64_t ldx, int32_t s,
+                                const void* A, int64_t m, int64_t lda, int32_t* Js, int32_t* Is, void* L,
+                                int64_t ldl, void* R, int64_t ldr, void* ws, size_t* ws_bytes, int32_t* dev_status,
+                                cudaStream_t stream) {
+  if (!valid_dtype(dtype) || X == nullptr || Js == nullptr || Is == nullptr || A == nullptr)
+    return SKEL_ERR_INVALID_ARG;
+  if (s < 1 || s > kMaxS || s > l || s > n || s > m || n > 0x7FFFFFFFll || m > 0x7FFFFFFFll) return SKEL_ERR_INVALID_ARG;
+  if (ldx < n || lda < m || (L && ldl < s) || (R && ldr < n)) return SKEL_ERR_INVALID_ARG;
+  if (skeleton_pivot_pipelined(dtype, n, m, s)) {
+    const size_t need = skeleton_pivot_workspace(dtype, n, m, s);
+    skel_status st;
+    if (ws_handshake(need, ws, ws_bytes, &st)) return st;
+    return run_skeleton_pivot(dtype, X, n, ldx, s, A, m, lda, Js, Is, L, ldl, R, ldr, ws, *ws_bytes, dev_status,
+                              stream);
+  }
+  // one after the other: LUPP on X, then on C^T with C = A(:, Js)
+  const size_t lc = lupp_auto_workspace(dtype, n, s), lr = lupp_auto_workspace(dtype, m, s);
+  const size_t cbytes = align_up(esize(dtype) * (size_t)m * s);
+  skel_status st;
+  if (ws_handshake(std::max(lc, cbytes + lr), ws, ws_bytes, &st)) return st;
+  SK_TRY(run_lupp_auto(dtype, X, n, ldx, s, Js, L, ldl, R, ldr, ws, *ws_bytes, dev_status, stream));
+  void* C = ws;
+  SK_CUDA(launch_gather_cols(m, s, dtype, A, lda, Js, C, m, stream));
+  return run_lupp_auto(dtype, C, m, m, s, Is, nullptr, 0, nullptr, 0, static_cast<char*>(ws) + cbytes, lr, dev_status,
+                       stream);
+}
+
 skel_status skel_pivot_cpqr(skel_dtype dtype, const void* X, int64_t l, int64_t n, int64_t ldx,
                             int32_t s, int32_t* Js, void* R, int64_t ldr, void* ws,
                             size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream) {

@@ -101,6 +101,13 @@ skel_status run_lupp(skel_dtype dt, const void* X, int64_t n, int64_t ldx, int32
 // LUPP through the panel-blocked cluster kernels when a panel fits one cluster's shared
 // memory (lupp_panel.cu), else through the grid-barrier kernel above.
 size_t lupp_auto_workspace(skel_dtype dt, int64_t n, int32_t s);
+// Column LUPP on X and row LUPP on C^T (C = A(:, Js)) with the row chain pipelined behind the
+// column chain on an auxiliary stream (lupp_panel.cu); usable when both fit the panel kernel.
+bool skeleton_pivot_pipelined(skel_dtype dt, int64_t n, int64_t m, int32_t s);
+size_t skeleton_pivot_workspace(skel_dtype dt, int64_t n, int64_t m, int32_t s);
+skel_status run_skeleton_pivot(skel_dtype dt, const void* X, int64_t n, int64_t ldx, int32_t s, const void* A,
+                               int64_t m, int64_t lda, int32_t* Js, int32_t* Is, void* L, int64_t ldl, void* R,
+                               int64_t ldr, void* ws, size_t ws_bytes, int32_t* dev_status, cudaStream_t st);
 skel_status run_lupp_auto(skel_dtype dt, const void* X, int64_t n, int64_t ldx, int32_t s,
                           int32_t* Js, void* L, int64_t ldl, void* R, int64_t ldr, void* ws,
                           size_t ws_bytes, int32_t* dev_status, cudaStream_t st);

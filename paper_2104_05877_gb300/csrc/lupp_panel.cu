@@ -16,6 +16,7 @@
 // restatement exactly).  Kernel boundaries order the phases; the working copy of X(0:s, :)
 // lives in the workspace.
 #include <algorithm>
+#include <mutex>
 
 #include <cooperative_groups.h>
 
@@ -44,7 +45,12 @@ struct PanelParams {
   T* L; int64_t ldl;   // optional s x s
   int32_t* dev_status;
   int32_t* fail;       // device word: set when a panel stopped early (zero / non-finite pivot)
-  T* M;                // (s - t0 - b) x b multipliers of the trailing rows (row-major)
+  T* M;                // trailing-row multipliers M(r, q) at M[(r - trow0) * ldm + q]
+  int64_t ldm;         // row stride of M (b when the panel kernel writes it)
+  int64_t trow0;       // first trailing row the trailing update covers (t0 + b by default)
+  int trows;           // trailing rows it covers (s - t0 - b by default)
+  unsigned char sel_tag;    // sel value of columns this panel selects: panel index + 1
+  unsigned char sel_limit;  // trailing update skips columns with 0 < sel <= sel_limit
 };
 
 // Per-step exchange.  Every CTA sends every CTA of the cluster (itself included) its step-q
@@ -365,7 +371,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
       T rv;
       if (jj == mine_w) {
         rv = T(1);
-        sl[jj] = 1;
+        sl[jj] = p.sel_tag;
       } else if (sl[jj]) {
         rv = T(0);
       } else {
@@ -466,7 +472,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
         if (q0 > qq && q0 < b) a0 = dsub(a0, dmul(mq, RJ[qq * b + q0]));
         if (q1 > qq && q1 < b) a1 = dsub(a1, dmul(mq, RJ[qq * b + q1]));
       }
-      T* Mr = p.M + (int64_t)ri * b;
+      T* Mr = p.M + (int64_t)ri * p.ldm;
       if (q0 < b) Mr[q0] = a0;
       if (q1 < b) Mr[q1] = a1;
       if (p.L) {
@@ -490,18 +496,20 @@ __global__ void __launch_bounds__(kTrailThreads) lupp_trail_kernel(const PanelPa
   __shared__ __align__(16) T Mt[kMaxPanel][kTrailRows];   // Mt[q][u] = M(r0 + u, q)
   const int b = p.b;
   const int r0 = blockIdx.y * kTrailRows;                // index among the trailing rows
-  const int rows = p.s - p.t0 - b;
+  const int rows = p.trows;
   const int nrows = rows - r0 < kTrailRows ? rows - r0 : kTrailRows;
   if (nrows <= 0) return;
   if (*(volatile int32_t*)p.fail) return;
   for (int e = threadIdx.x; e < b * kTrailRows; e += blockDim.x) {
     const int q = e / kTrailRows, u = e % kTrailRows;
-    Mt[q][u] = u < nrows ? p.M[(int64_t)(r0 + u) * b + q] : T(0);
+    Mt[q][u] = u < nrows ? p.M[(int64_t)(r0 + u) * p.ldm + q] : T(0);
   }
   __syncthreads();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= p.n || p.sel[j]) return;
-  T* x = p.Xg + (int64_t)(p.t0 + b + r0) * p.n + j;
+  if (j >= p.n) return;
+  const unsigned char sj = p.sel[j];
+  if (sj != 0 && sj <= p.sel_limit) return;              // selected by this panel or an earlier one
+  T* x = p.Xg + (p.trow0 + r0) * p.n + j;
   T v[kTrailRows];
 #pragma unroll
   for (int u = 0; u < kTrailRows; ++u) v[u] = u < nrows ? x[(int64_t)u * p.n] : T(0);
@@ -529,6 +537,131 @@ __global__ void lupp_panel_init_kernel(const T* X, int64_t ldx, int s, int64_t n
       for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s; c += gridDim.x * blockDim.x)
         L[(int64_t)r * ldl + c] = T(0);
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *fail = 0;
+}
+
+// ---------------------------------------------------------------------------------------
+// Row chain of the pipelined skeleton pivoting (row LUPP on C^T, C = A(:, Js), run panel by
+// panel behind the column LUPP that produces Js).  The row panel [t0, t0+b) is factored as
+// soon as its rows exist; the trailing updates that the earlier row panels would have
+// applied to these rows are applied then, entry by entry in the same order (panel by panel,
+// step by step), and the multipliers are formed by the same forward substitutions as the
+// panel kernel's epilogue, so the pivots equal those of the unpipelined factorisation bit
+// for bit.
+// ---------------------------------------------------------------------------------------
+
+// Rows t0 .. t0+b-1 of the working copy: row r is column Js[r] of A.  A missing pivot (the
+// column chain stopped) sets the row chain's fail word instead.
+template <typename T>
+__global__ void lupp_gather_panel_kernel(const T* A, int64_t lda, int64_t m, int64_t ncols, const int32_t* Js,
+                                         int t0, int b, T* Xg, int32_t* fail) {
+  for (int r = blockIdx.y; r < b; r += gridDim.y) {
+    const int32_t j = Js[t0 + r];
+    if (j < 0 || (int64_t)j >= ncols) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(fail, 1);
+      continue;
+    }
+    const T* a = A + (int64_t)j * lda;
+    T* x = Xg + (int64_t)(t0 + r) * m;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+      x[i] = a[i];
+  }
+}
+
+// Multipliers M(r, t), t < t0, of the rows r = t0 .. t0+b-1 (earlier panels of height B):
+// for each earlier panel q, the entries X(r, J_q) after the updates of the panels before q,
+// then forward substitution with R(panel q, J_q).  One warp per row; lane i holds the steps
+// i and i + 32 of panel q.  M(r, t) goes to Lw[r * ldw + t].
+template <typename T>
+__global__ void lupp_defer_m_kernel(const PanelParams<T> p, int B, T* Lw, int64_t ldw) {
+  const int lane = threadIdx.x & 31;
+  const int ri = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (ri >= p.b) return;
+  if (*(volatile int32_t*)p.fail) return;
+  const int64_t r = p.t0 + ri;
+  T* Mr = Lw + r * ldw;
+  const T* xr = p.Xg + r * p.n;
+  for (int tq = 0; tq < p.t0; tq += B) {
+    const int q0 = lane, q1 = lane + 32;
+    const bool h0 = q0 < B, h1 = q1 < B;
+    const int j0 = h0 ? p.Js[tq + q0] : 0, j1 = h1 ? p.Js[tq + q1] : 0;
+    T a0 = h0 ? xr[j0] : T(0);
+    T a1 = h1 ? xr[j1] : T(0);
+    for (int t = 0; t < tq; t += 8) {      // the updates of the panels before q, in order
+      T r0[8], r1[8], mt[8];               // (B need not be a multiple of 8: steps >= tq are skipped)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const bool ok = t + u < tq;
+        const int64_t row = (int64_t)(t + u) * p.ldr;
+        mt[u] = ok ? Mr[t + u] : T(0);
+        r0[u] = ok && h0 ? p.R[row + j0] : T(0);
+        r1[u] = ok && h1 ? p.R[row + j1] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (t + u < tq) {
+          a0 = dsub(a0, dmul(mt[u], r0[u]));
+          a1 = dsub(a1, dmul(mt[u], r1[u]));
+        }
+    }
+    for (int qq = 0; qq < B; ++qq) {        // forward substitution with R(panel q, J_q)
+      const T mq = __shfl_sync(0xffffffffu, qq < 32 ? a0 : a1, qq & 31);
+      const int64_t row = (int64_t)(tq + qq) * p.ldr;
+      if (q0 > qq && h0) a0 = dsub(a0, dmul(mq, p.R[row + j0]));
+      if (q1 > qq && h1) a1 = dsub(a1, dmul(mq, p.R[row + j1]));
+    }
+    if (h0) Mr[tq + q0] = a0;
+    if (h1) Mr[tq + q1] = a1;
+    __syncwarp();
+  }
+}
+
+// The earlier panels' trailing updates of rows t0 .. t0+b-1: panel q (steps tq .. tq+B-1)
+// subtracts M(r, tq+qq) R(tq+qq, j) for qq in order, skipping the columns selected by panel q
+// or earlier (sel tag <= q + 1), exactly as the trailing update after panel q would have.
+template <typename T>
+__global__ void __launch_bounds__(kTrailThreads) lupp_defer_trail_kernel(const PanelParams<T> p, int B,
+                                                                         const T* Lw, int64_t ldw) {
+  __shared__ __align__(16) T Mt[kMaxPanel][kTrailRows];
+  const int r0 = blockIdx.y * kTrailRows;
+  const int nrows = p.b - r0 < kTrailRows ? p.b - r0 : kTrailRows;
+  if (nrows <= 0) return;
+  if (*(volatile int32_t*)p.fail) return;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = j < p.n;
+  const int sj = live ? p.sel[j] : 0;
+  const int npan = p.t0 / B;
+  const int napply = sj == 0 ? npan : (sj - 1 < npan ? sj - 1 : npan);   // panels q < sel tag - 1
+  T* x = p.Xg + (int64_t)(p.t0 + r0) * p.n + j;
+  T v[kTrailRows];
+#pragma unroll
+  for (int u = 0; u < kTrailRows; ++u) v[u] = live && u < nrows ? x[(int64_t)u * p.n] : T(0);
+  for (int q = 0; q < npan; ++q) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < B * kTrailRows; e += blockDim.x) {
+      const int qq = e / kTrailRows, u = e % kTrailRows;
+      Mt[qq][u] = u < nrows ? Lw[(int64_t)(p.t0 + r0 + u) * ldw + (int64_t)q * B + qq] : T(0);
+    }
+    __syncthreads();
+    if (!live || q >= napply) continue;
+    const T* Rj = p.R + (int64_t)q * B * p.ldr + j;
+    for (int qq = 0; qq < B; ++qq) {
+      const T rq = Rj[(int64_t)qq * p.ldr];
+#pragma unroll
+      for (int u = 0; u < kTrailRows; ++u) v[u] = dsub(v[u], dmul(Mt[qq][u], rq));
+    }
+  }
+  if (live)
+#pragma unroll
+    for (int u = 0; u < kTrailRows; ++u)
+      if (u < nrows) x[(int64_t)u * p.n] = v[u];
+}
+
+template <typename T>
+__global__ void lupp_row_init_kernel(int64_t n, int s, unsigned char* sel, int32_t* fail, int32_t* Is) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    sel[j] = 0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < s; t += gridDim.x * blockDim.x) Is[t] = -1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *fail = 0;
 }
 
 struct PanelPlan {
@@ -626,9 +759,14 @@ skel_status run_panel_t(const PanelPlan& pl, const T* X, int64_t n, int64_t ldx,
   if (pl.CL > 8 &&
       cudaFuncSetAttribute(lupp_panel_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
     return SKEL_ERR_CUDA;
+  p.sel_limit = 255;
   for (int t0 = 0; t0 < s; t0 += pl.b) {
     p.t0 = t0;
     p.b = std::min(pl.b, s - t0);
+    p.sel_tag = (unsigned char)(t0 / pl.b + 1);
+    p.ldm = p.b;
+    p.trow0 = t0 + p.b;
+    p.trows = s - t0 - p.b;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(pl.CL);
     cfg.blockDim = dim3(kPanelThreads);
@@ -659,7 +797,197 @@ skel_status run_panel_t(const PanelPlan& pl, const T* X, int64_t n, int64_t ldx,
   return cudaGetLastError() == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
 }
 
+// Auxiliary stream and events of the pipelined skeleton pivoting, one set per device,
+// created on first use; the enqueue is serialised so that concurrent callers never
+// interleave their records and waits on the shared events.
+constexpr int kMaxPanels = kMaxS / 8 + 2;
+struct AuxSet {
+  cudaStream_t st = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t col[kMaxPanels] = {};
+};
+std::mutex g_aux_mu;
+
+AuxSet* aux_set() {
+  static AuxSet sets[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  AuxSet& a = sets[dev];
+  if (a.st) return &a;
+  if (cudaStreamCreateWithFlags(&a.st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+  bool ok = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; ok && k < kMaxPanels; ++k) ok = cudaEventCreateWithFlags(&a.col[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return &a;
+}
+
+template <typename T>
+cudaError_t launch_panel(const PanelParams<T>& p, const PanelPlan& pl, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(pl.CL);
+  cfg.blockDim = dim3(kPanelThreads);
+  cfg.dynamicSmemBytes = panel_smem<T>(p.b, pl.ncl);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = pl.CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e;
+  {
+    KernelTimer kt("lupp_panel", st);
+    e = cudaLaunchKernelEx(&cfg, lupp_panel_kernel<T>, p);
+  }
+  note_launches(1);
+  return e;
+}
+
+// Column LUPP on X (Js, optional L, R) and row LUPP on C^T (Is), the row chain on an
+// auxiliary stream: row panel [t0, t0+b) starts when the column panel holding step t0+b-1
+// has finished (an event) and the previous row panel is done (stream order).  wsc: the
+// column chain's panel workspace; wsr: the row chain's (working copy of C^T, sel, fail, R);
+// Lw: s x s multipliers of the row chain.
+template <typename T>
+skel_status run_skeleton_t(const PanelPlan& pc, const PanelPlan& pr, const T* X, int64_t n, int64_t ldx, int s,
+                           const T* A, int64_t m, int64_t lda, int32_t* Js, int32_t* Is, T* L, int64_t ldl, T* R,
+                           int64_t ldr, void* wsc, void* wsr, T* Lw, int32_t* dev_status, cudaStream_t st) {
+  AuxSet* aux = aux_set();
+  if (aux == nullptr) return SKEL_ERR_CUDA;
+  // column chain parameters (as run_panel_t)
+  char* base = static_cast<char*>(wsc);
+  PanelParams<T> c{};
+  c.Xg = reinterpret_cast<T*>(base);
+  base += align_up(sizeof(T) * (size_t)s * n);
+  c.sel = reinterpret_cast<unsigned char*>(base);
+  base += align_up(n);
+  c.fail = reinterpret_cast<int32_t*>(base);
+  base += 256;
+  c.M = reinterpret_cast<T*>(base);
+  base += align_up(sizeof(T) * (size_t)s * 64);
+  if (R == nullptr) {
+    R = reinterpret_cast<T*>(base);
+    ldr = n;
+  }
+  c.n = n; c.s = s; c.ncl = pc.ncl; c.Js = Js; c.R = R; c.ldr = ldr; c.L = L; c.ldl = ldl;
+  c.dev_status = dev_status;
+  c.sel_limit = 255;
+  // row chain parameters
+  base = static_cast<char*>(wsr);
+  PanelParams<T> r{};
+  r.Xg = reinterpret_cast<T*>(base);
+  base += align_up(sizeof(T) * (size_t)s * m);
+  r.sel = reinterpret_cast<unsigned char*>(base);
+  base += align_up(m);
+  r.fail = reinterpret_cast<int32_t*>(base);
+  base += 256;
+  r.R = reinterpret_cast<T*>(base);
+  r.ldr = m;
+  r.n = m; r.ncl = pr.ncl; r.Js = Is; r.L = nullptr; r.ldl = 0; r.M = nullptr;
+  r.dev_status = dev_status;
+  r.sel_limit = 255;
+
+  const size_t smem = std::max(pc.smem, pr.smem);
+  if (cudaFuncSetAttribute(lupp_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return SKEL_ERR_CUDA;
+  if (std::max(pc.CL, pr.CL) > 8 &&
+      cudaFuncSetAttribute(lupp_panel_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return SKEL_ERR_CUDA;
+
+  std::lock_guard<std::mutex> lock(g_aux_mu);
+  lupp_panel_init_kernel<T><<<dim3((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)std::min(s, 64)), 256, 0, st>>>(
+      X, ldx, s, n, c.Xg, c.sel, c.fail, L, ldl);
+  lupp_row_init_kernel<T><<<(unsigned)std::min<int64_t>((m + 255) / 256, 64), 256, 0, st>>>(m, s, r.sel, r.fail, Is);
+  note_launches(2);
+  if (cudaEventRecord(aux->fork, st) != cudaSuccess) return SKEL_ERR_CUDA;
+  // column chain on the caller's stream
+  int k = 0;
+  for (int t0 = 0; t0 < s; t0 += pc.b, ++k) {
+    c.t0 = t0;
+    c.b = std::min(pc.b, s - t0);
+    c.sel_tag = (unsigned char)(k + 1);
+    c.ldm = c.b;
+    c.trow0 = t0 + c.b;
+    c.trows = s - t0 - c.b;
+    if (launch_panel<T>(c, pc, st) != cudaSuccess) return SKEL_ERR_CUDA;
+    if (cudaEventRecord(aux->col[k], st) != cudaSuccess) return SKEL_ERR_CUDA;
+    if (c.trows > 0) {
+      dim3 grid((unsigned)((n + kTrailThreads - 1) / kTrailThreads), (unsigned)((c.trows + kTrailRows - 1) / kTrailRows));
+      {
+        KernelTimer kt("lupp_trail", st);
+        lupp_trail_kernel<T><<<grid, kTrailThreads, 0, st>>>(c);
+      }
+      note_launches(1);
+    }
+  }
+  // row chain on the auxiliary stream
+  if (cudaStreamWaitEvent(aux->st, aux->fork, 0) != cudaSuccess) return SKEL_ERR_CUDA;
+  k = 0;
+  for (int t0 = 0; t0 < s; t0 += pr.b, ++k) {
+    r.t0 = t0;
+    r.b = std::min(pr.b, s - t0);
+    r.s = t0 + r.b;                       // no rows below: the epilogue forms no multipliers
+    r.sel_tag = (unsigned char)(k + 1);
+    if (cudaStreamWaitEvent(aux->st, aux->col[(t0 + r.b - 1) / pc.b], 0) != cudaSuccess) return SKEL_ERR_CUDA;
+    lupp_gather_panel_kernel<T><<<dim3((unsigned)std::min<int64_t>((m + 255) / 256, 32), (unsigned)r.b), 256, 0, aux->st>>>(
+        A, lda, m, n, Js, t0, r.b, r.Xg, r.fail);
+    note_launches(1);
+    if (t0 > 0) {
+      lupp_defer_m_kernel<T><<<(unsigned)((r.b + 7) / 8), 256, 0, aux->st>>>(r, pr.b, Lw, s);
+      dim3 grid((unsigned)((m + kTrailThreads - 1) / kTrailThreads), (unsigned)((r.b + kTrailRows - 1) / kTrailRows));
+      {
+        KernelTimer kt("lupp_trail", aux->st);
+        lupp_defer_trail_kernel<T><<<grid, kTrailThreads, 0, aux->st>>>(r, pr.b, Lw, s);
+      }
+      note_launches(2);
+    }
+    if (launch_panel<T>(r, pr, aux->st) != cudaSuccess) return SKEL_ERR_CUDA;
+  }
+  if (cudaEventRecord(aux->join, aux->st) != cudaSuccess) return SKEL_ERR_CUDA;
+  if (cudaStreamWaitEvent(st, aux->join, 0) != cudaSuccess) return SKEL_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
+}
+
 }  // namespace
+
+size_t skeleton_pivot_workspace(skel_dtype dt, int64_t n, int64_t m, int32_t s) {
+  const size_t es = dt == SKEL_F64 ? 8 : 4;
+  const size_t col = dt == SKEL_F64 ? panel_ws<double>(n, s, true) : panel_ws<float>(n, s, true);
+  const size_t row = align_up(es * (size_t)s * m) + align_up(m) + 256 + align_up(es * (size_t)s * m);
+  return col + row + align_up(es * (size_t)s * s);
+}
+
+bool skeleton_pivot_pipelined(skel_dtype dt, int64_t n, int64_t m, int32_t s) {
+  if (dt == SKEL_F64) {
+    const PanelPlan pc = plan_panel<double>(n, s), pr = plan_panel<double>(m, s);
+    return pc.b > 0 && pr.b > 0 && (s + std::min(pc.b, pr.b) - 1) / std::min(pc.b, pr.b) <= kMaxPanels;
+  }
+  const PanelPlan pc = plan_panel<float>(n, s), pr = plan_panel<float>(m, s);
+  return pc.b > 0 && pr.b > 0 && (s + std::min(pc.b, pr.b) - 1) / std::min(pc.b, pr.b) <= kMaxPanels;
+}
+
+skel_status run_skeleton_pivot(skel_dtype dt, const void* X, int64_t n, int64_t ldx, int32_t s, const void* A,
+                               int64_t m, int64_t lda, int32_t* Js, int32_t* Is, void* L, int64_t ldl, void* R,
+                               int64_t ldr, void* ws, size_t ws_bytes, int32_t* dev_status, cudaStream_t st) {
+  if (!skeleton_pivot_pipelined(dt, n, m, s)) return SKEL_ERR_UNSUPPORTED;
+  if (ws_bytes < skeleton_pivot_workspace(dt, n, m, s)) return SKEL_ERR_WORKSPACE;
+  const size_t es = dt == SKEL_F64 ? 8 : 4;
+  char* wsc = static_cast<char*>(ws);
+  char* wsr = wsc + (dt == SKEL_F64 ? panel_ws<double>(n, s, true) : panel_ws<float>(n, s, true));
+  char* lw = wsr + align_up(es * (size_t)s * m) + align_up(m) + 256 + align_up(es * (size_t)s * m);
+  if (dt == SKEL_F64)
+    return run_skeleton_t<double>(plan_panel<double>(n, s), plan_panel<double>(m, s), (const double*)X, n, ldx, s,
+                                  (const double*)A, m, lda, Js, Is, (double*)L, ldl, (double*)R, ldr, wsc, wsr,
+                                  (double*)lw, dev_status, st);
+  return run_skeleton_t<float>(plan_panel<float>(n, s), plan_panel<float>(m, s), (const float*)X, n, ldx, s,
+                               (const float*)A, m, lda, Js, Is, (float*)L, ldl, (float*)R, ldr, wsc, wsr, (float*)lw,
+                               dev_status, st);
+}
 
 static bool panel_usable(skel_dtype dt, int64_t n, int32_t s) {
   return (dt == SKEL_F64 ? plan_panel<double>(n, s).b : plan_panel<float>(n, s).b) > 0;

@@ -162,3 +162,58 @@ def test_lupp_very_wide_uses_grid_kernel(skel, dev):
     ref = pivoting.lupp_columns(X, s)
     assert np.array_equal(Js.cpu().numpy(), ref["Js"])
     assert np.array_equal(Rf.cpu().numpy(), ref["R"])
+
+
+@pytest.mark.parametrize("l,n,m,s", [(20, 100, 120, 20), (140, 3001, 2500, 130), (60, 800, 20000, 50),
+                                     (70, 500, 70, 64), (8, 300, 300, 8)])
+def test_pivot_skeleton_fp64_bit_exact(skel, dev, l, n, m, s):
+    """Algorithm 2 lines 3-4 in one call, the row LUPP pipelined behind the column LUPP (row
+    panels of a different height when C^T's panel is smaller): in FP64 the pivots and the
+    column LUPP's factors equal the oracle's bit for bit."""
+    rng = np.random.default_rng(l + n + m + s)
+    X = rng.standard_normal((l, n))
+    A = np.asfortranarray(rng.standard_normal((m, n)))
+    Js, Is, Lf, Rf, st = skel.pivot_skeleton(torch.from_numpy(X).to(dev), torch.from_numpy(A).to(dev), s)
+    torch.cuda.synchronize()
+    skel.check_status(st)
+    ref = pivoting.lupp_columns(X, s)
+    assert np.array_equal(Js.cpu().numpy(), ref["Js"])
+    assert np.array_equal(Rf.cpu().numpy(), ref["R"])
+    assert np.array_equal(Lf.cpu().numpy(), ref["L"][:s, :s])
+    assert np.array_equal(Is.cpu().numpy(), pivoting.lupp_rows(A[:, ref["Js"]], s)["Js"])
+
+
+@pytest.mark.parametrize("prec", ["tf32", "f32"])
+def test_pivot_skeleton_fp32_equals_separate_calls(skel, dev, prec):
+    """FP32 at the measured size (8192 x 8192, k = 256, l = 272): the one-call pipelined form
+    returns exactly the pivots and factors of skel_pivot_lupp followed by skel_pivot_rows."""
+    m = n = 8192
+    k, l = 256, 272
+    A = workloads.torch_dense_spectrum(m, n, workloads.sigma_config2(n), 1e-6 / np.sqrt(m), workloads.seed_for(2),
+                                       dev, torch.float32)
+    X, st = skel.sketch(A, l, prec=prec, seed=5)
+    Js1, L1, R1, _ = skel.pivot_lupp(X, k, status=st)
+    Is1, _ = skel.pivot_rows(A, Js1, status=st)
+    Js2, Is2, L2, R2, _ = skel.pivot_skeleton(X, A, k, status=st)
+    torch.cuda.synchronize()
+    skel.check_status(st)
+    assert torch.equal(Js1, Js2) and torch.equal(Is1, Is2)
+    assert torch.equal(L1, L2) and torch.equal(R1, R2)
+
+
+def test_pivot_skeleton_rank_deficient(skel, dev):
+    """A sketch with two nonzero columns and s = 30: the column LUPP stops at step 2 with
+    SKEL_ERR_RANK_DEFICIENT; the row chain sees the missing pivots and leaves Is at -1 (its
+    first panel needs Js[0 .. 29])."""
+    X = np.zeros((40, 300))
+    X[0, 7] = 2.0
+    X[1, 9] = -1.0
+    A = np.asfortranarray(np.random.default_rng(3).standard_normal((200, 300)))
+    Js, Is, _, _, st = skel.pivot_skeleton(torch.from_numpy(X).to(dev), torch.from_numpy(A).to(dev), 30)
+    torch.cuda.synchronize()
+    with pytest.raises(skel.SkelError) as e:
+        skel.check_status(st)
+    assert e.value.code == 4
+    J, I = Js.cpu().numpy(), Is.cpu().numpy()
+    assert list(J[:2]) == [7, 9] and np.all(J[2:] == -1)
+    assert np.all(I == -1)
