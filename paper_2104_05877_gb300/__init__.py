@@ -438,14 +438,18 @@ def skeletonize(A, k, p=10, seed=0, prec="f32", pivot="lupp", kind="gaussian", z
     st = new_status(A.device)
     l = k + p
     X, _ = sketch(A, l, kind=kind, prec=prec, seed=seed, zeta=zeta, status=st)
-    if pivot == "lupp":
+    Is = None
+    if pivot == "lupp" and want_cur and X.dtype == A.dtype:
+        Js, Is, _, Rf, _ = pivot_skeleton(X, A, k, status=st)     # row LUPP pipelined behind
+    elif pivot == "lupp":
         Js, _, Rf, _ = pivot_lupp(X, k, status=st)
     else:
         Js, Rf, _ = pivot_cpqr(X, k, status=st)
     Z, sq, _ = column_id(A, Js, status=st)
     out = dict(X=X, Js=Js, Rf=Rf, Z=Z, sq_norms=sq, status=st)
     if want_cur:
-        Is, _ = pivot_rows(A, Js, status=st)
+        if Is is None:
+            Is, _ = pivot_rows(A, Js, status=st)
         _, U, sq_cur, _ = cur(A, Js, Is, status=st)
         out.update(Is=Is, U=U, sq_norms_cur=sq_cur)
     if want_error:
