@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--blocks", type=int, default=4096, help="blocks of the batched run (--only batch)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-GPU comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
-    ap.add_argument("--only", default=None, choices=["sketch", "lupp", "rows", "pivots", "id", "cur", "eta", "batch", "next",
+    ap.add_argument("--only", default=None, choices=["sketch", "lupp", "rows", "pivots", "id", "cur", "id_cur", "eta", "batch", "next",
                                                      "srtt", "power", "cols"],
                     help="run only this call (warm-up + steps, no extras): a small command for profilers; "
                          "'batch' runs the batched configuration (4096 Gaussian-kernel blocks, k_max 128, "
@@ -213,7 +213,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     st = skel.new_status(dev)
 
-    names = ["sketch", "pivots", "id", "cur", "eta"]
+    names = ["sketch", "pivots", "id_cur", "eta"]
 
     def step(evs):
         evs[0].record()
@@ -222,12 +222,11 @@ def run_ours(args, rank, world):
         # column LUPP on X and row LUPP on C = A(:, Js), the latter pipelined behind the former
         Js, Is, _, Rf, _ = skel.pivot_skeleton(X, A, k, status=st)
         evs[2].record()
-        Z, sq_id, _ = skel.column_id(A, Js, status=st)
+        # column ID and stable CUR sharing one QR of C (the QR of R^T runs concurrently)
+        Z, U, sq_id, sq_cur, _ = skel.id_cur(A, Js, Is, status=st)
         evs[3].record()
-        _, U, sq_cur, _ = skel.cur(A, Js, Is, status=st)
-        evs[4].record()
         e, _ = skel.error(A, Js, Rf=Rf, status=st)
-        evs[5].record()
+        evs[4].record()
         return Js, Is, sq_id, sq_cur, e
 
     if args.only == "next":
@@ -243,6 +242,7 @@ def run_ours(args, rank, world):
                 "pivots": lambda: skel.pivot_skeleton(X, A, k, status=st),
                 "id": lambda: skel.column_id(A, Js, status=st),
                 "cur": lambda: skel.cur(A, Js, Is, status=st),
+                "id_cur": lambda: skel.id_cur(A, Js, Is, status=st),
                 "eta": lambda: skel.error(A, Js, Rf=Rf, status=st),
                 "srtt": lambda: skel.sketch(A, l, kind="srtt", prec=args.prec, seed=seed_G, X=X, status=st),
                 "power": lambda: skel.sketch_power(A, l, q=1, prec=args.prec, seed=seed_G, status=st),
@@ -300,8 +300,7 @@ def run_ours(args, rank, world):
     total_ms = t_begin.elapsed_time(t_end)
     per = {nm: statistics.mean(ev[i].elapsed_time(ev[i + 1]) for ev in all_evs) for i, nm in enumerate(names)}
     tts = statistics.mean(ev[0].elapsed_time(ev[2]) for ev in all_evs)
-    tid = per["sketch"] + per["pivots"] + per["id"]
-    tcur = statistics.mean(ev[0].elapsed_time(ev[4]) for ev in all_evs)
+    tcur = statistics.mean(ev[0].elapsed_time(ev[3]) for ev in all_evs)
     if world > 1:
         t = torch.tensor([tts, total_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -325,10 +324,10 @@ def run_ours(args, rank, world):
     #   sketch_tc   X = Gamma A: 2 l m n TF32 flop (or 4 m n bytes of A if HBM-bound)
     #   sketch_fp8  X = Gamma8 A8 from the e4m3 copy of A: m n bytes; fp8_quantize reads A and
     #               writes A8: 5 m n bytes
-    #   gemm_tc     W = Q^T A in the ID and the CUR: 2 x 3 (2 k m n) TF32 flop (3 products)
+    #   gemm_tc     W = Q^T A, shared by the ID and the CUR: 3 (2 k m n) TF32 flop (3 products)
     #   lupp_panel  s greedy steps over n (LUPP on X) and over m (row LUPP on C): the panel
     #               rank-1 updates, sum over panels of b^2 cols (mul + sub)
-    #   qr_panel    the column steps of three Householder QRs (C twice, R^T once): 2 rows k^2
+    #   qr_panel    the column steps of the two Householder QRs (C and R^T): 2 rows k^2
     #               flop each (the panels' WY factors are formed by other kernels)
     #   trsm        Z = R_C^{-1} W (k^2 n) and four k x k solves (CUR, eta): FP64
     #   gemm_eta_h  upper triangle of R R^T in float-float: k(k+1)/2 n products, each
@@ -341,9 +340,9 @@ def run_ours(args, rank, world):
         if 2.0 * l * m * n / (tf32_peak * 1e12) > a_bytes / (hbm * 1e9) else ("hbm", a_bytes / 1e9, hbm, "GB/s"),
         "sketch_fp8": ("hbm", m * n / 1e9, hbm, "GB/s"),           # A8: one byte per element
         "fp8_quantize": ("hbm", 5.0 * m * n / 1e9, hbm, "GB/s"),   # A read (4 B), A8 written (1 B)
-        "gemm_tc": ("tensor", 2 * 3 * 2.0 * k * m * n / 1e12, tf32_peak, "TFLOP/s"),
+        "gemm_tc": ("tensor", 3 * 2.0 * k * m * n / 1e12, tf32_peak, "TFLOP/s"),
         "lupp_panel": ("alu", lupp_flops / 1e12, fp32_alu_peak, "TFLOP/s"),
-        "qr_panel": ("alu", 2.0 * (2 * m + n) * k * k / 1e12, fp32_alu_peak, "TFLOP/s"),
+        "qr_panel": ("alu", 2.0 * (m + n) * k * k / 1e12, fp32_alu_peak, "TFLOP/s"),
         "trsm": ("alu", (1.0 * k * k * n + 4.0 * k ** 3) / 1e12, fp64_alu_peak, "TFLOP/s"),
         "gemm_eta_h": ("alu", 9.0 * k * (k + 1) / 2 * n / 1e12, fp32_alu_peak / 2, "TOP/s"),
     }
@@ -435,7 +434,7 @@ def run_ours(args, rank, world):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
         "config": workload_config(k, p, args.prec),
-        "time_to_id_ms": tid, "time_to_cur_ms": tcur, "a_streaming_gbs": sketch_gbs,
+        "time_to_id_and_cur_ms": tcur, "a_streaming_gbs": sketch_gbs,
         "sketch_tflops": sketch_tflops, "calls_ms": per,
         "rel_id_error": rel_id, "rel_cur_error": rel_cur, "eta": float(e[3]),
         "oracle_rel_id_error": oracle_err,

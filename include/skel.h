@@ -299,6 +299,20 @@ skel_status skel_error(int64_t m, int64_t n, skel_dtype dtype, const void* A, in
                        int32_t* dev_status, cudaStream_t stream);
 
 /*
+ * skel_id_cur -- the column ID of skel_id and the stable CUR of skel_cur (Eq. (2.1),
+ * Eq. (2.4), Remark 3) in one call, for given skeletons Js and Is (e.g. from
+ * skel_pivot_skeleton).  The QR of C = A(:, Js) and W = Q_C^T A are formed once and serve
+ * both (Z = R_C^{-1} W, U = R_C^{-1} (W Q_R) R_R^{-T}); the QR of R^T = A(Is, :)^T runs on the
+ * auxiliary stream concurrently with them.  Outputs and their layouts are those of skel_id
+ * (Z, ldz, sq_id) and skel_cur (U, ldu, sq_cur), and equal them.  sq_id / sq_cur may be NULL.
+ * Workspace (handshake).  The auxiliary stream is shared as in skel_pivot_skeleton.
+ */
+skel_status skel_id_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda, int32_t s,
+                        const int32_t* Js, const int32_t* Is, double* Z, int64_t ldz, double* U, int64_t ldu,
+                        double* sq_id, double* sq_cur, void* ws, size_t* ws_bytes, int32_t* dev_status,
+                        cudaStream_t stream);
+
+/*
  * skel_cur_sketch -- the CUR estimated without a second pass over A (Sec. 4: with the skeletons
  * S = A(I_s, J_s), C = A(:, J_s) and R = A(I_s, :), A ~ C S^{-1} R): U = S^{-1} (s x s row-major
  * FP64, ldu >= s), formed stably from a Householder QR of S^T (S^T = Q R_S, S^{-1} = Q R_S^{-T}).

@@ -55,6 +55,7 @@ def lib():
                        szp, vp, vp],
         "skel_id_sketch": [i32, i32, i64, vp, i64, vp, vp, i64, vp, szp, vp, vp],
         "skel_cur_sketch": [i64, i64, i32, vp, i64, i32, vp, vp, vp, i64, vp, szp, vp, vp],
+        "skel_id_cur": [i64, i64, i32, vp, i64, i32, vp, vp, vp, i64, vp, i64, vp, vp, vp, szp, vp, vp],
         "skel_pivot_skeleton": [i32, vp, i64, i64, i64, i32, vp, i64, i64, vp, vp, vp, i64, vp, i64, vp, szp, vp,
                                 vp],
         "skel_sketch_power": [i64, i64, i32, vp, i64, i32, i32, i32, u64, vp, i64, vp, szp, vp, vp],
@@ -313,6 +314,22 @@ def column_id_sketch(R, Js, status=None):
     _call("skel_id_sketch", lambda w, sz: [_dt(R), s, n, _ptr(R), ldr, _ptr(Js), _ptr(Z), n, w, sz, _ptr(st),
                                            _stream()], R.device)
     return Z, st
+
+
+def id_cur(A, Js, Is, status=None):
+    """Column ID and stable CUR in one call (one QR of C and one W = Q_C^T A for both):
+    returns (Z, U, sq_id, sq_cur, status) with the meanings of column_id and cur."""
+    A, lda = _colmajor(A)
+    m, n = A.shape
+    s = Js.numel()
+    Z = torch.empty(s, n, dtype=torch.float64, device=A.device)
+    U = torch.empty(s, s, dtype=torch.float64, device=A.device)
+    sq_id = torch.empty(2, dtype=torch.float64, device=A.device)
+    sq_cur = torch.empty(2, dtype=torch.float64, device=A.device)
+    st = status if status is not None else new_status(A.device)
+    _call("skel_id_cur", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, s, _ptr(Js), _ptr(Is), _ptr(Z), n, _ptr(U), s,
+                                        _ptr(sq_id), _ptr(sq_cur), w, sz, _ptr(st), _stream()], A.device)
+    return Z, U, sq_id, sq_cur, st
 
 
 def cur_sketch(A, Js, Is, status=None):

@@ -577,6 +577,96 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
   return SKEL_OK;
 }
 
+skel_status skel_id_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda, int32_t s,
+                        const int32_t* Js, const int32_t* Is, double* Z, int64_t ldz, double* U, int64_t ldu,
+                        double* sq_id, double* sq_cur, void* ws, size_t* ws_bytes, int32_t* dev_status,
+                        cudaStream_t stream) {
+  if (!id_args_ok(m, n, dtype, A, lda, s, Js) || Is == nullptr || Z == nullptr || ldz < n || U == nullptr ||
+      ldu < s)
+    return SKEL_ERR_INVALID_ARG;
+  const bool f64 = dtype == SKEL_F64;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool run = pass == 1;
+    Arena ar(run ? ws : nullptr);
+    void *C, *Qc;
+    double* Rc;
+    SK_TRY(skeleton_qr(ar, run, m, dtype, A, lda, s, Js, &C, &Qc, &Rc, dev_status, stream));
+    void* Rt = ar.take(esize(dtype) * (size_t)n * s);
+    void* Qr = ar.take(esize(dtype) * (size_t)n * s);
+    double* Rr = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
+    const size_t qn = qr_workspace(dtype, n, s);
+    void* qws = ar.take(qn);
+    void* W = ar.take(esize(dtype) * (size_t)s * n);
+    double* M = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
+    double* T1 = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
+    double* T2 = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
+    const bool tcw = !f64 && gemm_tc_usable(m, n, s, nullptr, m, A, lda);   // tensor-core W
+    const int64_t nbw = tcw ? gemm_tc_num_partials(m, n, s) : gemm_num_blocks(s, n);
+    double* pw = static_cast<double*>(ar.take(sizeof(double) * nbw));
+    const int64_t nbm = gemm_num_blocks(s, s);
+    double* pm = static_cast<double*>(ar.take(sizeof(double) * nbm));
+    const int64_t nba = sqnorm_num_blocks(m, n);
+    double* pa = static_cast<double*>(ar.take(sizeof(double) * nba));
+    void* kws1 = ar.take(tcw ? gemm_tc_workspace(m, n, s) : gemm_workspace(s, n, m, f64));
+    void* kws2 = ar.take(gemm_workspace(s, s, n, f64));
+    if (!run) {
+      skel_status st;
+      if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+      continue;
+    }
+    std::lock_guard<std::mutex> lock(aux_mutex());
+    AuxSet* aux = aux_set();
+    if (aux == nullptr) return SKEL_ERR_CUDA;
+    // R = A(Is, :) and its QR on the auxiliary stream, concurrent with everything on C
+    SK_CUDA(cudaEventRecord(aux->fork, stream));
+    SK_CUDA(cudaStreamWaitEvent(aux->st, aux->fork, 0));
+    SK_CUDA(launch_gather_rows_t(n, s, dtype, A, lda, Is, Rt, n, aux->st));
+    SK_TRY(run_qr(dtype, Rt, n, n, s, Qr, n, Rr, s, qws, qn, dev_status, aux->st));
+    SK_CUDA(cudaEventRecord(aux->join, aux->st));
+    // W = Q_C^T A (with ||W||_F^2) and Z = R_C^{-1} W, as skel_id
+    GemmArgs g{};
+    g.splitk_ws = kws1;
+    g.M = s; g.N = n; g.K = m;
+    g.L = View{Qc, m, 1}; g.l_dt = dtype;
+    g.B = View{A, 1, lda}; g.b_dt = dtype;
+    g.out = W; g.out_sr = n; g.out_sc = 1; g.out_dt = dtype;
+    g.alpha = 1.0;
+    g.partials = pw;
+    if (tcw)
+      SK_CUDA(launch_gemm_tc_tn(m, n, s, static_cast<const float*>(Qc), m, static_cast<const float*>(A), lda,
+                                static_cast<float*>(W), n, pw, kws1, dev_status, stream));
+    else
+      SK_CUDA(launch_gemm(g, f64, LEFT_LOAD, EPI_STORE_SQ, stream));
+    SK_CUDA(launch_trsm_upper(s, n, Rc, s, 0, dtype, W, n, Z, ldz, stream));
+    if (sq_id || sq_cur) SK_CUDA(launch_sqnorm(m, n, dtype, A, lda, pa, stream));
+    if (sq_id) {
+      SK_CUDA(launch_reduce_sum(pa, nba, sq_id, 0, stream));
+      SK_CUDA(launch_reduce_sum(pw, nbw, sq_id + 1, 0, stream));
+    }
+    // M = W Q_R = Q_C^T A Q_R and U = R_C^{-1} M R_R^{-T}, as skel_cur
+    SK_CUDA(cudaStreamWaitEvent(stream, aux->join, 0));
+    GemmArgs h{};
+    h.splitk_ws = kws2;
+    h.M = s; h.N = s; h.K = n;
+    h.L = View{W, n, 1}; h.l_dt = dtype;
+    h.B = View{Qr, 1, n}; h.b_dt = dtype;
+    h.out = M; h.out_sr = s; h.out_sc = 1; h.out_dt = SKEL_F64;
+    h.alpha = 1.0;
+    h.partials = pm;
+    h.timer = "gemm_cur";
+    SK_CUDA(launch_gemm(h, f64, LEFT_LOAD, EPI_STORE_SQ, stream));
+    if (sq_cur) {
+      SK_CUDA(launch_reduce_sum(pa, nba, sq_cur, 0, stream));
+      SK_CUDA(launch_reduce_sum(pm, nbm, sq_cur + 1, 0, stream));
+    }
+    SK_CUDA(launch_trsm_upper(s, s, Rc, s, 0, SKEL_F64, M, s, T1, s, stream));
+    SK_CUDA(launch_transpose_f64(s, T1, s, T2, s, stream));
+    SK_CUDA(launch_trsm_upper(s, s, Rr, s, 0, SKEL_F64, T2, s, T1, s, stream));
+    SK_CUDA(launch_transpose_f64(s, T1, s, U, ldu, stream));
+  }
+  return SKEL_OK;
+}
+
 skel_status skel_cur_sketch(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda, int32_t s,
                             const int32_t* Js, const int32_t* Is, double* U, int64_t ldu, void* ws,
                             size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream) {

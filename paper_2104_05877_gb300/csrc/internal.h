@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "../../include/skel.h"
@@ -101,6 +102,18 @@ skel_status run_lupp(skel_dtype dt, const void* X, int64_t n, int64_t ldx, int32
 // LUPP through the panel-blocked cluster kernels when a panel fits one cluster's shared
 // memory (lupp_panel.cu), else through the grid-barrier kernel above.
 size_t lupp_auto_workspace(skel_dtype dt, int64_t n, int32_t s);
+// Auxiliary stream and events for fork/join concurrency inside one call, one set per device,
+// created on first use.  Hold aux_mutex() for the whole enqueue that uses them, so that
+// concurrent callers never interleave records and waits on the shared events.
+constexpr int kAuxEvents = 130;      // one per panel of >= 8 steps of up to 1024, and spares
+struct AuxSet {
+  cudaStream_t st = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t col[kAuxEvents] = {};
+};
+std::mutex& aux_mutex();
+AuxSet* aux_set();
+
 // Column LUPP on X and row LUPP on C^T (C = A(:, Js)) with the row chain pipelined behind the
 // column chain on an auxiliary stream (lupp_panel.cu); usable when both fit the panel kernel.
 bool skeleton_pivot_pipelined(skel_dtype dt, int64_t n, int64_t m, int32_t s);

@@ -797,33 +797,6 @@ skel_status run_panel_t(const PanelPlan& pl, const T* X, int64_t n, int64_t ldx,
   return cudaGetLastError() == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
 }
 
-// Auxiliary stream and events of the pipelined skeleton pivoting, one set per device,
-// created on first use; the enqueue is serialised so that concurrent callers never
-// interleave their records and waits on the shared events.
-constexpr int kMaxPanels = kMaxS / 8 + 2;
-struct AuxSet {
-  cudaStream_t st = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
-  cudaEvent_t col[kMaxPanels] = {};
-};
-std::mutex g_aux_mu;
-
-AuxSet* aux_set() {
-  static AuxSet sets[64];
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  AuxSet& a = sets[dev];
-  if (a.st) return &a;
-  if (cudaStreamCreateWithFlags(&a.st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
-  bool ok = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) == cudaSuccess;
-  for (int k = 0; ok && k < kMaxPanels; ++k) ok = cudaEventCreateWithFlags(&a.col[k], cudaEventDisableTiming) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  return &a;
-}
 
 template <typename T>
 cudaError_t launch_panel(const PanelParams<T>& p, const PanelPlan& pl, cudaStream_t st) {
@@ -857,6 +830,7 @@ template <typename T>
 skel_status run_skeleton_t(const PanelPlan& pc, const PanelPlan& pr, const T* X, int64_t n, int64_t ldx, int s,
                            const T* A, int64_t m, int64_t lda, int32_t* Js, int32_t* Is, T* L, int64_t ldl, T* R,
                            int64_t ldr, void* wsc, void* wsr, T* Lw, int32_t* dev_status, cudaStream_t st) {
+  std::lock_guard<std::mutex> lock(aux_mutex());
   AuxSet* aux = aux_set();
   if (aux == nullptr) return SKEL_ERR_CUDA;
   // column chain parameters (as run_panel_t)
@@ -899,7 +873,6 @@ skel_status run_skeleton_t(const PanelPlan& pc, const PanelPlan& pr, const T* X,
       cudaFuncSetAttribute(lupp_panel_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
     return SKEL_ERR_CUDA;
 
-  std::lock_guard<std::mutex> lock(g_aux_mu);
   lupp_panel_init_kernel<T><<<dim3((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)std::min(s, 64)), 256, 0, st>>>(
       X, ldx, s, n, c.Xg, c.sel, c.fail, L, ldl);
   lupp_row_init_kernel<T><<<(unsigned)std::min<int64_t>((m + 255) / 256, 64), 256, 0, st>>>(m, s, r.sel, r.fail, Is);
@@ -962,13 +935,36 @@ size_t skeleton_pivot_workspace(skel_dtype dt, int64_t n, int64_t m, int32_t s) 
   return col + row + align_up(es * (size_t)s * s);
 }
 
+std::mutex& aux_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+
+AuxSet* aux_set() {
+  static AuxSet sets[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  AuxSet& a = sets[dev];
+  if (a.st) return &a;
+  if (cudaStreamCreateWithFlags(&a.st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+  bool ok = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; ok && k < kAuxEvents; ++k) ok = cudaEventCreateWithFlags(&a.col[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    a.st = nullptr;
+    return nullptr;
+  }
+  return &a;
+}
+
 bool skeleton_pivot_pipelined(skel_dtype dt, int64_t n, int64_t m, int32_t s) {
   if (dt == SKEL_F64) {
     const PanelPlan pc = plan_panel<double>(n, s), pr = plan_panel<double>(m, s);
-    return pc.b > 0 && pr.b > 0 && (s + std::min(pc.b, pr.b) - 1) / std::min(pc.b, pr.b) <= kMaxPanels;
+    return pc.b > 0 && pr.b > 0 && (s + std::min(pc.b, pr.b) - 1) / std::min(pc.b, pr.b) <= kAuxEvents;
   }
   const PanelPlan pc = plan_panel<float>(n, s), pr = plan_panel<float>(m, s);
-  return pc.b > 0 && pr.b > 0 && (s + std::min(pc.b, pr.b) - 1) / std::min(pc.b, pr.b) <= kMaxPanels;
+  return pc.b > 0 && pr.b > 0 && (s + std::min(pc.b, pr.b) - 1) / std::min(pc.b, pr.b) <= kAuxEvents;
 }
 
 skel_status run_skeleton_pivot(skel_dtype dt, const void* X, int64_t n, int64_t ldx, int32_t s, const void* A,

@@ -260,3 +260,31 @@ def test_streaming_selection_tensor_cores(skel, dev):
     assert len(set(J.tolist())) == k and len(set(I.tolist())) == k
     e_gpu = errors.rel_cur_error(Ad, J, decomp.cur(Ad, J, I), I)
     assert e_gpu <= 1.05 * ref["err_cur"]
+
+
+@pytest.mark.parametrize("dt,m,n,k", [(np.float64, 600, 500, 30), (np.float32, 1000, 900, 64),
+                                      (np.float32, 8192, 8192, 256)])
+def test_id_cur_equals_separate_calls(skel, dev, dt, m, n, k):
+    """skel_id_cur (one QR of C and one W for both, the QR of R^T on the auxiliary stream)
+    returns exactly what skel_id and skel_cur return separately, and the ID matches the
+    oracle's."""
+    if m == 8192:
+        A = workloads.torch_dense_spectrum(m, n, workloads.sigma_config2(n), 1e-6 / np.sqrt(m),
+                                           workloads.seed_for(2), dev, torch.float32)
+        X, st = skel.sketch(A, k + 16, prec="tf32", seed=3)
+    else:
+        A = torch.from_numpy(np.asfortranarray(workloads.dense_config2(m, n, seed=2, dtype=dt))).to(dev)
+        X, st = skel.sketch(A, k + 10, prec="f64" if dt == np.float64 else "f32", seed=3)
+    Js, Is, _, _, _ = skel.pivot_skeleton(X, A, k, status=st)
+    Z1, sq1, _ = skel.column_id(A, Js, status=st)
+    _, U1, sqc1, _ = skel.cur(A, Js, Is, status=st)
+    Z2, U2, sq2, sqc2, _ = skel.id_cur(A, Js, Is, status=st)
+    torch.cuda.synchronize()
+    skel.check_status(st)
+    assert torch.equal(Z1, Z2) and torch.equal(U1, U2)
+    assert torch.equal(sq1, sq2) and torch.equal(sqc1, sqc2)
+    if m < 8192:
+        Ad = A.cpu().double().numpy()
+        Zr = decomp.column_id(Ad, Js.cpu().numpy())
+        tol = 1e-9 if dt == np.float64 else 1e-3
+        assert np.linalg.norm(Z2.cpu().numpy() - Zr) <= tol * np.linalg.norm(Zr)
