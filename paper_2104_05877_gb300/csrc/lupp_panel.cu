@@ -603,11 +603,24 @@ __global__ void lupp_defer_m_kernel(const PanelParams<T> p, int B, T* Lw, int64_
           a1 = dsub(a1, dmul(mt[u], r1[u]));
         }
     }
-    for (int qq = 0; qq < B; ++qq) {        // forward substitution with R(panel q, J_q)
-      const T mq = __shfl_sync(0xffffffffu, qq < 32 ? a0 : a1, qq & 31);
-      const int64_t row = (int64_t)(tq + qq) * p.ldr;
-      if (q0 > qq && h0) a0 = dsub(a0, dmul(mq, p.R[row + j0]));
-      if (q1 > qq && h1) a1 = dsub(a1, dmul(mq, p.R[row + j1]));
+    for (int c0 = 0; c0 < B; c0 += 8) {    // forward substitution with R(panel q, J_q)
+      T r0[8], r1[8];                       // this lane's R entries of 8 steps, loaded together
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int qq = c0 + u;
+        const int64_t row = (int64_t)(tq + qq) * p.ldr;
+        r0[u] = qq < B && q0 > qq && h0 ? p.R[row + j0] : T(0);
+        r1[u] = qq < B && q1 > qq && h1 ? p.R[row + j1] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int qq = c0 + u;
+        if (qq < B) {                       // uniform over the warp
+          const T mq = __shfl_sync(0xffffffffu, qq < 32 ? a0 : a1, qq & 31);
+          if (q0 > qq && h0) a0 = dsub(a0, dmul(mq, r0[u]));
+          if (q1 > qq && h1) a1 = dsub(a1, dmul(mq, r1[u]));
+        }
+      }
     }
     if (h0) Mr[tq + q0] = a0;
     if (h1) Mr[tq + q1] = a1;
