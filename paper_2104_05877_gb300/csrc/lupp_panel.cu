@@ -514,10 +514,15 @@ __global__ void __launch_bounds__(kTrailThreads) lupp_trail_kernel(const PanelPa
 #pragma unroll
   for (int u = 0; u < kTrailRows; ++u) v[u] = u < nrows ? x[(int64_t)u * p.n] : T(0);
   const T* Rj = p.R + (int64_t)p.t0 * p.ldr + j;
-  for (int q = 0; q < b; ++q) {
-    const T rq = Rj[(int64_t)q * p.ldr];
+  for (int q0 = 0; q0 < b; q0 += 8) {          // R entries of 8 steps loaded together
+    T rq[8];
 #pragma unroll
-    for (int u = 0; u < kTrailRows; ++u) v[u] = dsub(v[u], dmul(Mt[q][u], rq));
+    for (int e = 0; e < 8; ++e) rq[e] = q0 + e < b ? Rj[(int64_t)(q0 + e) * p.ldr] : T(0);
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if (q0 + e < b)
+#pragma unroll
+        for (int u = 0; u < kTrailRows; ++u) v[u] = dsub(v[u], dmul(Mt[q0 + e][u], rq[e]));
   }
 #pragma unroll
   for (int u = 0; u < kTrailRows; ++u)
@@ -657,10 +662,15 @@ __global__ void __launch_bounds__(kTrailThreads) lupp_defer_trail_kernel(const P
     __syncthreads();
     if (!live || q >= napply) continue;
     const T* Rj = p.R + (int64_t)q * B * p.ldr + j;
-    for (int qq = 0; qq < B; ++qq) {
-      const T rq = Rj[(int64_t)qq * p.ldr];
+    for (int q0 = 0; q0 < B; q0 += 8) {        // R entries of 8 steps loaded together
+      T rq[8];
 #pragma unroll
-      for (int u = 0; u < kTrailRows; ++u) v[u] = dsub(v[u], dmul(Mt[qq][u], rq));
+      for (int e = 0; e < 8; ++e) rq[e] = q0 + e < B ? Rj[(int64_t)(q0 + e) * p.ldr] : T(0);
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (q0 + e < B)
+#pragma unroll
+          for (int u = 0; u < kTrailRows; ++u) v[u] = dsub(v[u], dmul(Mt[q0 + e][u], rq[e]));
     }
   }
   if (live)
