@@ -501,12 +501,12 @@ def run_next(args, rank, A, skel, st, seed_G):
 def run_batch(args, rank, dev, skel, workloads):
     """Batched configuration: uneven Gaussian-kernel blocks (4096 by default: m_b ~ U[64, 1024],
     n_b ~ U[64, 512], FP32, ~2.6 GB), k_max = 128, p = 16, tol = 1e-6: one skel_batch_run per
-    step."""
+    step (an autotuned plan replaying its captured CUDA graph)."""
     import torch
     nblocks, kmax, p, tol = args.blocks, 128, 16, 1e-6
     blocks = workloads.torch_kernel_blocks(nblocks, workloads.seed_for(4) + rank, dev)
     a_bytes = sum(4 * B.shape[0] * B.shape[1] for B in blocks)
-    plan = skel.BatchPlan(blocks, kmax, p=p, tol=tol, seed=workloads.seed_for(4, "gamma"))
+    plan = skel.BatchPlan(blocks, kmax, p=p, tol=tol, seed=workloads.seed_for(4, "gamma"), graph=True, autotune=True)
     torch.cuda.synchronize()
     for _ in range(args.warmup):
         Js, ranks, Z, st = plan.run()
@@ -528,6 +528,7 @@ def run_batch(args, rank, dev, skel, workloads):
     if rank == 0:
         print(json.dumps({"only": "batch", "ms": ms, "a_bytes": a_bytes, "a_streaming_gbs": a_bytes / (ms * 1e-3) / 1e9,
                           "kernel_ms": kern, "rank_mean": float(r.mean()), "rank_max": int(r.max()),
+                          "plan": plan.info,
                           "config": {"workload": f"{nblocks} Gaussian-kernel blocks m_b~U[64,1024] n_b~U[64,512] fp32, "
                                                  f"k_max={kmax}, p={p}, tol={tol}", "steps": args.steps}}), flush=True)
 

@@ -355,18 +355,30 @@ skel_status skel_id_sketch(skel_dtype dtype, int32_t s, int64_t n, const void* R
  *   (sum_b (kmax+p) n_b floats).  Allocates and copies synchronously; no other call does.
  *   SKEL_ERR_UNSUPPORTED when a block is wider than four CTAs' shared memory hold
  *   ((kmax+p) n_b / 4 floats per CTA plus kmax^2) or is not TMA-addressable.
+ *   flags: SKEL_BATCH_AUTOTUNE times, on the plan's own blocks, every sketch pipeline depth
+ *   that fits and the LUPP cluster classes run one after another or concurrently (one
+ *   warm-up and two timed runs each, synchronously, inside this call) and keeps the fastest;
+ *   no choice changes any result.  SKEL_BATCH_GRAPH makes skel_batch_run replay a CUDA
+ *   graph of the run, captured on its first call and again whenever the output pointers
+ *   change.  Other bits: SKEL_ERR_INVALID_ARG.
+ * skel_batch_plan_info -- host: info[0] sketch pipeline depth, info[1] 1 if the LUPP classes
+ *   run concurrently, info[2] the flags, info[3] sketch work items (128-column tiles).
  * skel_batch_z_offsets -- host: offsets[0..nblocks] (in doubles) of the blocks' Z in Z_all,
  *   offsets[b+1] - offsets[b] = kmax n_b.
  * skel_batch_run -- on `stream`, no host synchronisation: Js[b*kmax + q] (int32, q < rank_b,
  *   -1 after), ranks[b], Z_all + offsets[b]: kmax x n_b row-major FP64, rows 0 .. rank_b-1
  *   written (Z_b(:, Js) = I), rows from rank_b on left as they were.  dev_status: SKEL_ERR_NONFINITE (step = block) for a non-finite sketch,
- *   SKEL_ERR_TIMEOUT if a pipeline wait of the sketch kernel gave up.
+ *   SKEL_ERR_TIMEOUT if a pipeline wait of the sketch kernel gave up.  With SKEL_BATCH_GRAPH
+ *   (and per-kernel timing off) the run is one graph launch; the plan's side streams and
+ *   events make the graph, so one plan serves one run at a time.
  * skel_batch_plan_destroy -- frees the plan (after the work using it has finished).
  */
 typedef struct skel_batch_plan skel_batch_plan;
+enum { SKEL_BATCH_GRAPH = 1, SKEL_BATCH_AUTOTUNE = 2 };
 skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int64_t* n, const float* const* A,
                                    const int64_t* lda, int32_t kmax, int32_t p, double tol, uint64_t seed,
-                                   skel_batch_plan** plan);
+                                   int32_t flags, skel_batch_plan** plan);
+skel_status skel_batch_plan_info(const skel_batch_plan* plan, int32_t* info);
 skel_status skel_batch_z_offsets(const skel_batch_plan* plan, int64_t* offsets);
 skel_status skel_batch_run(skel_batch_plan* plan, int32_t* Js, int32_t* ranks, double* Z, int32_t* dev_status,
                            cudaStream_t stream);

@@ -79,9 +79,11 @@ def lib():
                                          ctypes.POINTER(ctypes.c_int64)]
     L.skel_debug_kernel_time.restype = ctypes.c_int
     L.skel_batch_plan_create.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(vp),
-                                         ctypes.POINTER(i64), i32, i32, ctypes.c_double, u64,
+                                         ctypes.POINTER(i64), i32, i32, ctypes.c_double, u64, i32,
                                          ctypes.POINTER(vp)]
     L.skel_batch_plan_create.restype = ctypes.c_int
+    L.skel_batch_plan_info.argtypes = [vp, ctypes.POINTER(i32)]
+    L.skel_batch_plan_info.restype = ctypes.c_int
     L.skel_batch_z_offsets.argtypes = [vp, ctypes.POINTER(i64)]
     L.skel_batch_z_offsets.restype = ctypes.c_int
     L.skel_batch_run.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -481,7 +483,7 @@ class BatchPlan:
     coefficients Z_b = X_b(0:r, J)^{-1} X_b(0:r, :).  `blocks`: CUDA float32 tensors (m_b x n_b,
     column-major views, kept alive by the plan)."""
 
-    def __init__(self, blocks, kmax, p=16, tol=1e-6, seed=0):
+    def __init__(self, blocks, kmax, p=16, tol=1e-6, seed=0, graph=False, autotune=False):
         self.blocks = []
         for B in blocks:
             if B.dtype != torch.float32 or not B.is_cuda:
@@ -501,19 +503,33 @@ class BatchPlan:
         ld = arr(ctypes.c_int64, [ldb for _, ldb in self.blocks])
         self.kmax, self.nb, self.device = kmax, nb, self.blocks[0][0].device
         self._plan = ctypes.c_void_p()
-        rc = lib().skel_batch_plan_create(nb, m, n, a, ld, kmax, p, float(tol), seed, ctypes.byref(self._plan))
+        flags = (1 if graph else 0) | (2 if autotune else 0)
+        rc = lib().skel_batch_plan_create(nb, m, n, a, ld, kmax, p, float(tol), seed, flags, ctypes.byref(self._plan))
         if rc != 0:
             raise SkelError(rc, "skel_batch_plan_create")
         off = (ctypes.c_int64 * (nb + 1))()
         lib().skel_batch_z_offsets(self._plan, off)
         self.z_offsets = list(off)
+        info = (ctypes.c_int32 * 4)()
+        lib().skel_batch_plan_info(self._plan, info)
+        self.info = {"sketch_stages": info[0], "concurrent_classes": bool(info[1]), "flags": info[2],
+                     "sketch_items": info[3]}
+        self._graph = graph
+        self._out = None
 
     def run(self, status=None):
-        """Returns (Js (nb x kmax int32), ranks (nb,), Z_all (float64), status) on the device."""
-        Js = torch.empty(self.nb, self.kmax, dtype=torch.int32, device=self.device)
-        ranks = torch.empty(self.nb, dtype=torch.int32, device=self.device)
-        Z = torch.zeros(max(self.z_offsets[-1], 1), dtype=torch.float64, device=self.device)
-        st = status if status is not None else new_status(self.device)
+        """Returns (Js (nb x kmax int32), ranks (nb,), Z_all (float64), status) on the device.
+        With graph=True the same output tensors are reused (the captured graph is bound to
+        them) and overwritten by the next run."""
+        if self._graph and self._out is not None and status is None:
+            Js, ranks, Z, st = self._out
+        else:
+            Js = torch.empty(self.nb, self.kmax, dtype=torch.int32, device=self.device)
+            ranks = torch.empty(self.nb, dtype=torch.int32, device=self.device)
+            Z = torch.zeros(max(self.z_offsets[-1], 1), dtype=torch.float64, device=self.device)
+            st = status if status is not None else new_status(self.device)
+            if self._graph and status is None:
+                self._out = (Js, ranks, Z, st)
         rc = lib().skel_batch_run(self._plan, _ptr(Js), _ptr(ranks), _ptr(Z), _ptr(st), _stream())
         if rc != 0:
             raise SkelError(rc, "skel_batch_run")

@@ -516,12 +516,28 @@ struct skel_batch_plan {
   float* d_X = nullptr;
   std::vector<int64_t> zoff;      // nb + 1 prefix offsets of Z (doubles)
   size_t sketch_smem = 0;
+  int max_stages = 2;             // sketch pipeline depths that fit: 2 .. max_stages
+  int concurrent = 0;             // LUPP cluster classes on parallel streams
+  int32_t flags = 0;
+  cudaStream_t cap = nullptr;     // capture / autotuning stream
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec = nullptr; // the captured run, bound to the outputs below
+  const void* bound[4] = {nullptr, nullptr, nullptr, nullptr};
+  int graph_launches = 0;
 };
 
 namespace {
 
 void plan_free(skel_batch_plan* pl) {
   if (!pl) return;
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  for (int i = 0; i < 2; ++i) {
+    if (pl->side[i]) cudaStreamDestroy(pl->side[i]);
+    if (pl->ev_join[i]) cudaEventDestroy(pl->ev_join[i]);
+  }
+  if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+  if (pl->cap) cudaStreamDestroy(pl->cap);
   cudaFree(pl->d_blocks);
   cudaFree(pl->d_tmaps);
   cudaFree(pl->d_items);
@@ -545,18 +561,148 @@ size_t lupp_budget() {
   return budget;
 }
 
+size_t sketch_smem_for(int lp, int stages) {
+  return 1024 + (size_t)stages * (2 * (size_t)BS_ATILE + 2 * (size_t)lp * 128) + 256;
+}
+
+// One run's launches on `st`: Gamma, the sketch, then the LUPP cluster classes, either one
+// after the other on `st` or (plan->concurrent) class 0 on `st` and classes 1, 2 on the plan's
+// side streams, forked from and joined back to `st`.  *launches: kernels enqueued.
+skel_status enqueue_run(skel_batch_plan* pl, int32_t* Js, int32_t* ranks, double* Z, int32_t* dev_status,
+                        cudaStream_t st, bool timers, int* launches) {
+  int nl = 0;
+  batch_gamma_kernel<<<std::min<int64_t>(((int64_t)pl->lp * pl->mg / 4 + 255) / 256, 1024), 256, 0, st>>>(
+      pl->l, pl->lp, pl->mg, (uint32_t)(pl->seed & 0xffffffffu), (uint32_t)(pl->seed >> 32), pl->d_ghi, pl->d_glo);
+  ++nl;
+  BatchSketchParams sp{};
+  sp.blocks = pl->d_blocks;
+  sp.tmaps = pl->d_tmaps;
+  sp.items = pl->d_items;
+  sp.X = pl->d_X;
+  sp.l = pl->l;
+  sp.lp = pl->lp;
+  sp.stages = pl->stages;
+  sp.scale = (float)(1.0 / std::sqrt((double)pl->l));
+  sp.dev_status = dev_status;
+  {
+    KernelTimer kt(timers ? "batch_sketch" : nullptr, st);
+    batch_sketch_kernel<<<pl->n_items, BS_THREADS, pl->sketch_smem, st>>>(pl->tm_ghi, pl->tm_glo, sp);
+  }
+  ++nl;
+  if (cudaGetLastError() != cudaSuccess) return SKEL_ERR_CUDA;
+  BatchLuppParams lp{};
+  lp.blocks = pl->d_blocks;
+  lp.X = pl->d_X;
+  lp.l = pl->l;
+  lp.kmax = pl->kmax;
+  lp.tol2 = (float)(pl->tol * pl->tol);
+  lp.Js = Js;
+  lp.ranks = ranks;
+  lp.Z = Z;
+  lp.dev_status = dev_status;
+  const bool fork = pl->concurrent && (pl->cls_count[1] > 0 || pl->cls_count[2] > 0);
+  if (fork) {
+    if (cudaEventRecord(pl->ev_fork, st) != cudaSuccess) return SKEL_ERR_CUDA;
+    for (int i = 0; i < 2; ++i)
+      if (cudaStreamWaitEvent(pl->side[i], pl->ev_fork, 0) != cudaSuccess) return SKEL_ERR_CUDA;
+  }
+  for (int c = 0; c < 3; ++c) {
+    if (pl->cls_count[c] == 0) continue;
+    const int CL = 1 << c;
+    cudaStream_t cs = fork && c > 0 ? pl->side[c - 1] : st;
+    lp.order = pl->d_order + pl->cls_off[c];
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(pl->cls_count[c] * CL));
+    cfg.blockDim = dim3(BL_THREADS);
+    cfg.dynamicSmemBytes = pl->cls_smem[c];
+    cfg.stream = cs;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    {
+      KernelTimer kt(timers ? "batch_lupp" : nullptr, cs);
+      e = cudaLaunchKernelEx(&cfg, batch_lupp_kernel, lp);
+    }
+    ++nl;
+    if (e != cudaSuccess) return SKEL_ERR_CUDA;
+  }
+  if (fork)
+    for (int i = 0; i < 2; ++i)
+      if (cudaEventRecord(pl->ev_join[i], pl->side[i]) != cudaSuccess ||
+          cudaStreamWaitEvent(st, pl->ev_join[i], 0) != cudaSuccess)
+        return SKEL_ERR_CUDA;
+  if (launches) *launches = nl;
+  return SKEL_OK;
+}
+
+// Autotuning at plan creation: every pipeline depth of the sketch that fits and both
+// schedules of the LUPP classes are run on the plan's own blocks (one warm-up, two timed runs
+// each, CUDA events) and the fastest is kept.  Neither choice changes any result.
+skel_status autotune(skel_batch_plan* pl) {
+  int32_t *Js = nullptr, *ranks = nullptr, *st = nullptr;
+  double* Z = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool ok = cudaMalloc(&Js, sizeof(int32_t) * (size_t)pl->nb * pl->kmax) == cudaSuccess &&
+            cudaMalloc(&ranks, sizeof(int32_t) * (size_t)pl->nb) == cudaSuccess &&
+            cudaMalloc(&st, 2 * sizeof(int32_t)) == cudaSuccess &&
+            cudaMalloc(&Z, sizeof(double) * (size_t)std::max<int64_t>(pl->zoff[pl->nb], 1)) == cudaSuccess &&
+            cudaMemset(st, 0, 2 * sizeof(int32_t)) == cudaSuccess &&
+            cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  float best = 1e30f;
+  int best_stages = pl->stages, best_conc = 0;
+  for (int stages = 2; ok && stages <= pl->max_stages; ++stages)
+    for (int conc = 0; ok && conc < 2; ++conc) {
+      pl->stages = stages;
+      pl->sketch_smem = sketch_smem_for(pl->lp, stages);
+      pl->concurrent = conc;
+      ok = enqueue_run(pl, Js, ranks, Z, st, pl->cap, false, nullptr) == SKEL_OK &&
+           cudaEventRecord(e0, pl->cap) == cudaSuccess;
+      for (int r = 0; ok && r < 2; ++r) ok = enqueue_run(pl, Js, ranks, Z, st, pl->cap, false, nullptr) == SKEL_OK;
+      ok = ok && cudaEventRecord(e1, pl->cap) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+      float ms = 0.f;
+      ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+      if (ok && ms < best) {
+        best = ms;
+        best_stages = stages;
+        best_conc = conc;
+      }
+    }
+  int32_t hst[2] = {0, 0};
+  if (ok) ok = cudaMemcpy(hst, st, sizeof(hst), cudaMemcpyDeviceToHost) == cudaSuccess;
+  pl->stages = best_stages;
+  pl->sketch_smem = sketch_smem_for(pl->lp, best_stages);
+  pl->concurrent = best_conc;
+  cudaFree(Js);
+  cudaFree(ranks);
+  cudaFree(st);
+  cudaFree(Z);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (!ok) {
+    cudaGetLastError();
+    return SKEL_ERR_CUDA;
+  }
+  return hst[0] == 0 ? SKEL_OK : (skel_status)hst[0];
+}
+
 }  // namespace
 
 extern "C" {
 
 skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int64_t* n, const float* const* A,
                                    const int64_t* lda, int32_t kmax, int32_t p, double tol, uint64_t seed,
-                                   skel_batch_plan** plan) {
+                                   int32_t flags, skel_batch_plan** plan) {
   if (plan == nullptr) return SKEL_ERR_INVALID_ARG;
   *plan = nullptr;
   if (nblocks < 1 || m == nullptr || n == nullptr || A == nullptr || lda == nullptr) return SKEL_ERR_INVALID_ARG;
   if (kmax < 1 || kmax > BL_MAXK || p < 1 || kmax + p > BL_MAXL || !(tol >= 0.0) || !std::isfinite(tol))
     return SKEL_ERR_INVALID_ARG;
+  if (flags & ~(SKEL_BATCH_GRAPH | SKEL_BATCH_AUTOTUNE)) return SKEL_ERR_INVALID_ARG;
   const int l = kmax + p, lp = (l + 15) / 16 * 16;
   const size_t budget = lupp_budget();
   if (budget == 0) return SKEL_ERR_CUDA;
@@ -583,10 +729,11 @@ skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int6
   pl->tol = tol;
   pl->seed = seed;
   pl->mg = (mmax + 31) / 32 * 32;
-  // shared memory of the sketch: 3 stages when they fit, else 2
-  const size_t stage = 2 * (size_t)BS_ATILE + 2 * (size_t)lp * 128;
-  pl->stages = 1024 + 3 * stage + 256 <= 227 * 1024 ? 3 : 2;
-  pl->sketch_smem = 1024 + pl->stages * stage + 256;
+  pl->flags = flags;
+  // shared memory of the sketch: 3 stages when they fit, else 2 (the autotuner may pick 2)
+  pl->max_stages = sketch_smem_for(lp, 3) <= 227 * 1024 ? 3 : 2;
+  pl->stages = pl->max_stages;
+  pl->sketch_smem = sketch_smem_for(lp, pl->stages);
 
   std::vector<BatchBlock> hb(nblocks);
   std::vector<CUtensorMap> ht(nblocks);
@@ -649,12 +796,24 @@ skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int6
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   }
   ok = ok && cudaFuncSetAttribute(batch_sketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)pl->sketch_smem) == cudaSuccess &&
+                                  (int)sketch_smem_for(lp, pl->max_stages)) == cudaSuccess &&
        cudaFuncSetAttribute(batch_lupp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; ok && i < 2; ++i)
+    ok = cudaStreamCreateWithFlags(&pl->side[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&pl->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     plan_free(pl);
     return SKEL_ERR_CUDA;
+  }
+  if (flags & SKEL_BATCH_AUTOTUNE) {
+    const skel_status st = autotune(pl);
+    if (st != SKEL_OK) {
+      plan_free(pl);
+      return st;
+    }
   }
   *plan = pl;
   return SKEL_OK;
@@ -670,59 +829,50 @@ skel_status skel_batch_run(skel_batch_plan* plan, int32_t* Js, int32_t* ranks, d
                            cudaStream_t stream) {
   if (plan == nullptr || Js == nullptr || ranks == nullptr || Z == nullptr) return SKEL_ERR_INVALID_ARG;
   skel_batch_plan* pl = plan;
-  batch_gamma_kernel<<<std::min<int64_t>(((int64_t)pl->lp * pl->mg / 4 + 255) / 256, 1024), 256, 0, stream>>>(
-      pl->l, pl->lp, pl->mg, (uint32_t)(pl->seed & 0xffffffffu), (uint32_t)(pl->seed >> 32), pl->d_ghi, pl->d_glo);
-  note_launches(1);
-  BatchSketchParams sp{};
-  sp.blocks = pl->d_blocks;
-  sp.tmaps = pl->d_tmaps;
-  sp.items = pl->d_items;
-  sp.X = pl->d_X;
-  sp.l = pl->l;
-  sp.lp = pl->lp;
-  sp.stages = pl->stages;
-  sp.scale = (float)(1.0 / std::sqrt((double)pl->l));
-  sp.dev_status = dev_status;
-  {
-    KernelTimer kt("batch_sketch", stream);
-    batch_sketch_kernel<<<pl->n_items, BS_THREADS, pl->sketch_smem, stream>>>(pl->tm_ghi, pl->tm_glo, sp);
+  if (!(pl->flags & SKEL_BATCH_GRAPH) || kernel_timing_enabled()) {
+    int nl = 0;
+    const skel_status st = enqueue_run(pl, Js, ranks, Z, dev_status, stream, true, &nl);
+    note_launches(nl);
+    return st;
   }
-  note_launches(1);
-  if (cudaGetLastError() != cudaSuccess) return SKEL_ERR_CUDA;
-  BatchLuppParams lp{};
-  lp.blocks = pl->d_blocks;
-  lp.X = pl->d_X;
-  lp.l = pl->l;
-  lp.kmax = pl->kmax;
-  lp.tol2 = (float)(pl->tol * pl->tol);
-  lp.Js = Js;
-  lp.ranks = ranks;
-  lp.Z = Z;
-  lp.dev_status = dev_status;
-  for (int c = 0; c < 3; ++c) {
-    if (pl->cls_count[c] == 0) continue;
-    const int CL = 1 << c;
-    lp.order = pl->d_order + pl->cls_off[c];
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(pl->cls_count[c] * CL));
-    cfg.blockDim = dim3(BL_THREADS);
-    cfg.dynamicSmemBytes = pl->cls_smem[c];
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e;
-    {
-      KernelTimer kt("batch_lupp", stream);
-      e = cudaLaunchKernelEx(&cfg, batch_lupp_kernel, lp);
+  const void* want[4] = {Js, ranks, Z, dev_status};
+  if (pl->exec == nullptr || !std::equal(want, want + 4, pl->bound)) {
+    // (re)capture the run bound to these outputs on the plan's stream
+    if (pl->exec) {
+      cudaGraphExecDestroy(pl->exec);
+      pl->exec = nullptr;
     }
-    note_launches(1);
-    if (e != cudaSuccess) return SKEL_ERR_CUDA;
+    if (cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SKEL_ERR_CUDA;
+    int nl = 0;
+    const skel_status st = enqueue_run(pl, Js, ranks, Z, dev_status, pl->cap, false, &nl);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(pl->cap, &g);
+    if (st != SKEL_OK || ee != cudaSuccess || g == nullptr) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return st != SKEL_OK ? st : SKEL_ERR_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&pl->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      pl->exec = nullptr;
+      cudaGetLastError();
+      return SKEL_ERR_CUDA;
+    }
+    std::copy(want, want + 4, pl->bound);
+    pl->graph_launches = nl;
   }
+  if (cudaGraphLaunch(pl->exec, stream) != cudaSuccess) return SKEL_ERR_CUDA;
+  note_launches(pl->graph_launches);
+  return SKEL_OK;
+}
+
+skel_status skel_batch_plan_info(const skel_batch_plan* plan, int32_t* info) {
+  if (plan == nullptr || info == nullptr) return SKEL_ERR_INVALID_ARG;
+  info[0] = plan->stages;
+  info[1] = plan->concurrent;
+  info[2] = plan->flags;
+  info[3] = plan->n_items;
   return SKEL_OK;
 }
 

@@ -200,6 +200,7 @@ void note_launches(int n);
 
 // CUDA events around one kernel launch (scope), recorded only while skel_debug_kernel_timing
 // is enabled: construct immediately before the launch, destroy immediately after it.
+bool kernel_timing_enabled();
 class KernelTimer {
  public:
   KernelTimer(const char* name, cudaStream_t st);

@@ -68,6 +68,12 @@ def test_invalid_arguments_rejected_on_host(L):
                               10, None, ctypes.byref(sz), None, None) == 7
     assert L.skel_sketch(10, 10, 1, ctypes.c_void_p(16), 12, 4, 2, 8, 4, 1, ctypes.c_void_p(16), 10,
                          None, ctypes.byref(sz), None, None) == 7
+    # batch plan: unknown flag bits
+    one = (ctypes.c_int64 * 1)(64)
+    ptr = (ctypes.c_void_p * 1)(16)
+    plan = ctypes.c_void_p()
+    assert L.skel_batch_plan_create(1, one, one, ptr, one, 8, 4, ctypes.c_double(1e-6), 1, 4,
+                                    ctypes.byref(plan)) == 1
     # row-partitioned sketch: row0 not a multiple of 4, negative
     for row0 in (2, -4):
         assert L.skel_sketch_rows(row0, 10, 10, 0, ctypes.c_void_p(16), 10, 4, 0, 8, 0, 1, ctypes.c_void_p(16),

@@ -102,3 +102,28 @@ def test_batch_rank_capped_and_narrow_blocks(skel, dev):
     plan, Js, ranks, Z = _run(skel, dev, blocks, kmax, 8, 1e-6, 1)
     assert ranks[0] == kmax and ranks[1] == 12
     assert sorted(Js[1, :12]) == list(range(12)) and np.all(Js[1, 12:] == -1)
+
+
+def test_batch_graph_and_autotune_change_no_result(skel, dev):
+    """A plan with the autotuner (sketch pipeline depth, LUPP classes serial or concurrent) and
+    a captured CUDA graph returns exactly what a plain plan returns, on every replay, and
+    re-captures when its outputs change; blocks of all three cluster classes are present."""
+    blocks = workloads.torch_kernel_blocks(96, workloads.seed_for(4) + 7, dev)
+    blocks[0] = torch.randn(900, 2000, device=dev).t().contiguous().t()[:, :1900]    # a 4-CTA block
+    blocks[1] = torch.randn(800, 1000, device=dev).t().contiguous().t()               # a 2-CTA block
+    kw = dict(p=16, tol=1e-6, seed=11)
+    plain = skel.BatchPlan(blocks, 64, **kw)
+    Js0, r0, Z0, st0 = plain.run()
+    tuned = skel.BatchPlan(blocks, 64, graph=True, autotune=True, **kw)
+    assert tuned.info["flags"] == 3 and tuned.info["sketch_stages"] in (2, 3)
+    for _ in range(3):
+        Js1, r1, Z1, st1 = tuned.run()
+        torch.cuda.synchronize()
+        skel.check_status(st1)
+        assert torch.equal(Js0, Js1) and torch.equal(r0, r1) and torch.equal(Z0, Z1)
+    st2 = skel.new_status(dev)
+    Js2, r2, Z2, _ = tuned.run(status=st2)     # new outputs: captured again
+    torch.cuda.synchronize()
+    skel.check_status(st0)
+    skel.check_status(st2)
+    assert torch.equal(Js0, Js2) and torch.equal(r0, r2) and torch.equal(Z0, Z2)
