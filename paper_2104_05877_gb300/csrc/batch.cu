@@ -672,6 +672,7 @@ skel_status autotune(skel_batch_plan* pl) {
         best_conc = conc;
       }
     }
+  cudaStreamSynchronize(pl->cap);           // nothing of the trials is in flight past here
   int32_t hst[2] = {0, 0};
   if (ok) ok = cudaMemcpy(hst, st, sizeof(hst), cudaMemcpyDeviceToHost) == cudaSuccess;
   pl->stages = best_stages;
