@@ -213,7 +213,9 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     st = skel.new_status(dev)
 
-    names = ["sketch", "pivots", "id_cur", "eta"]
+    names = ["sketch", "pivots", "id_cur", "eta_after_id_cur"]
+    main = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
 
     def step(evs):
         evs[0].record()
@@ -222,10 +224,14 @@ def run_ours(args, rank, world):
         # column LUPP on X and row LUPP on C = A(:, Js), the latter pipelined behind the former
         Js, Is, _, Rf, _ = skel.pivot_skeleton(X, A, k, status=st)
         evs[2].record()
-        # column ID and stable CUR sharing one QR of C (the QR of R^T runs concurrently)
+        # eta needs only the pivot factor: it runs on a second stream while the column ID and
+        # the stable CUR (one QR of C for both) run on this one
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            e, _ = skel.error(A, Js, Rf=Rf, status=st)
         Z, U, sq_id, sq_cur, _ = skel.id_cur(A, Js, Is, status=st)
         evs[3].record()
-        e, _ = skel.error(A, Js, Rf=Rf, status=st)
+        main.wait_stream(side)
         evs[4].record()
         return Js, Is, sq_id, sq_cur, e
 
