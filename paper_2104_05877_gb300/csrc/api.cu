@@ -620,6 +620,7 @@ skel_status skel_id_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, i
     // R = A(Is, :) and its QR on the auxiliary stream, concurrent with everything on C
     SK_CUDA(cudaEventRecord(aux->fork, stream));
     SK_CUDA(cudaStreamWaitEvent(aux->st, aux->fork, 0));
+    AuxJoin joiner{stream, aux};          // joins on every return path below
     SK_CUDA(launch_gather_rows_t(n, s, dtype, A, lda, Is, Rt, n, aux->st));
     SK_TRY(run_qr(dtype, Rt, n, n, s, Qr, n, Rr, s, qws, qn, dev_status, aux->st));
     SK_CUDA(cudaEventRecord(aux->join, aux->st));

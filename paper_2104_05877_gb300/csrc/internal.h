@@ -113,6 +113,16 @@ struct AuxSet {
 };
 std::mutex& aux_mutex();
 AuxSet* aux_set();
+// Joins the auxiliary stream back into `st` when it goes out of scope, so that no return
+// path (errors included) leaves work of the call running on the auxiliary stream unordered
+// with the caller's stream.
+struct AuxJoin {
+  cudaStream_t st;
+  AuxSet* aux;
+  ~AuxJoin() {
+    if (aux && cudaEventRecord(aux->join, aux->st) == cudaSuccess) cudaStreamWaitEvent(st, aux->join, 0);
+  }
+};
 
 // Column LUPP on X and row LUPP on C^T (C = A(:, Js)) with the row chain pipelined behind the
 // column chain on an auxiliary stream (lupp_panel.cu); usable when both fit the panel kernel.

@@ -923,6 +923,7 @@ skel_status run_skeleton_t(const PanelPlan& pc, const PanelPlan& pr, const T* X,
   }
   // row chain on the auxiliary stream
   if (cudaStreamWaitEvent(aux->st, aux->fork, 0) != cudaSuccess) return SKEL_ERR_CUDA;
+  AuxJoin joiner{st, aux};              // joins on every return path below
   k = 0;
   for (int t0 = 0; t0 < s; t0 += pr.b, ++k) {
     r.t0 = t0;
@@ -944,8 +945,6 @@ skel_status run_skeleton_t(const PanelPlan& pc, const PanelPlan& pr, const T* X,
     }
     if (launch_panel<T>(r, pr, aux->st) != cudaSuccess) return SKEL_ERR_CUDA;
   }
-  if (cudaEventRecord(aux->join, aux->st) != cudaSuccess) return SKEL_ERR_CUDA;
-  if (cudaStreamWaitEvent(st, aux->join, 0) != cudaSuccess) return SKEL_ERR_CUDA;
   return cudaGetLastError() == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
 }
 
