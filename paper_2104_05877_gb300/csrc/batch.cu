@@ -606,6 +606,15 @@ skel_status enqueue_run(skel_batch_plan* pl, int32_t* Js, int32_t* ranks, double
     for (int i = 0; i < 2; ++i)
       if (cudaStreamWaitEvent(pl->side[i], pl->ev_fork, 0) != cudaSuccess) return SKEL_ERR_CUDA;
   }
+  // the side streams join `st` on every path out of here once they have been forked
+  auto join = [&]() -> bool {
+    bool ok = true;
+    if (fork)
+      for (int i = 0; i < 2; ++i)
+        ok = cudaEventRecord(pl->ev_join[i], pl->side[i]) == cudaSuccess &&
+             cudaStreamWaitEvent(st, pl->ev_join[i], 0) == cudaSuccess && ok;
+    return ok;
+  };
   for (int c = 0; c < 3; ++c) {
     if (pl->cls_count[c] == 0) continue;
     const int CL = 1 << c;
@@ -629,13 +638,12 @@ skel_status enqueue_run(skel_batch_plan* pl, int32_t* Js, int32_t* ranks, double
       e = cudaLaunchKernelEx(&cfg, batch_lupp_kernel, lp);
     }
     ++nl;
-    if (e != cudaSuccess) return SKEL_ERR_CUDA;
+    if (e != cudaSuccess) {
+      join();
+      return SKEL_ERR_CUDA;
+    }
   }
-  if (fork)
-    for (int i = 0; i < 2; ++i)
-      if (cudaEventRecord(pl->ev_join[i], pl->side[i]) != cudaSuccess ||
-          cudaStreamWaitEvent(st, pl->ev_join[i], 0) != cudaSuccess)
-        return SKEL_ERR_CUDA;
+  if (!join()) return SKEL_ERR_CUDA;
   if (launches) *launches = nl;
   return SKEL_OK;
 }
