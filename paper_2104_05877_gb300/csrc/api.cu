@@ -588,6 +588,19 @@ skel_status skel_id_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, i
   for (int pass = 0; pass < 2; ++pass) {
     const bool run = pass == 1;
     Arena ar(run ? ws : nullptr);
+    // Two chains.  Caller's stream: QR of C, W = Q_C^T A, Z = R_C^{-1} W, the ID's norms.
+    // Auxiliary stream: R^T = A(Is, :)^T and its QR (from the start), then, once W exists,
+    // M = W Q_R and U = R_C^{-1} M R_R^{-T}.  The fork comes before the QR of C is enqueued.
+    std::unique_lock<std::mutex> lock(aux_mutex(), std::defer_lock);
+    AuxSet* aux = nullptr;
+    if (run) {
+      lock.lock();
+      aux = aux_set();
+      if (aux == nullptr) return SKEL_ERR_CUDA;
+      SK_CUDA(cudaEventRecord(aux->fork, stream));
+      SK_CUDA(cudaStreamWaitEvent(aux->st, aux->fork, 0));
+    }
+    AuxJoin joiner{stream, aux};          // joins on every return path below
     void *C, *Qc;
     double* Rc;
     SK_TRY(skeleton_qr(ar, run, m, dtype, A, lda, s, Js, &C, &Qc, &Rc, dev_status, stream));
@@ -614,17 +627,11 @@ skel_status skel_id_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, i
       if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
       continue;
     }
-    std::lock_guard<std::mutex> lock(aux_mutex());
-    AuxSet* aux = aux_set();
-    if (aux == nullptr) return SKEL_ERR_CUDA;
-    // R = A(Is, :) and its QR on the auxiliary stream, concurrent with everything on C
-    SK_CUDA(cudaEventRecord(aux->fork, stream));
-    SK_CUDA(cudaStreamWaitEvent(aux->st, aux->fork, 0));
-    AuxJoin joiner{stream, aux};          // joins on every return path below
+    cudaEvent_t w_ready = aux->col[0];
+    // auxiliary chain, part 1: R^T and its QR, concurrent with the QR of C
     SK_CUDA(launch_gather_rows_t(n, s, dtype, A, lda, Is, Rt, n, aux->st));
     SK_TRY(run_qr(dtype, Rt, n, n, s, Qr, n, Rr, s, qws, qn, dev_status, aux->st));
-    SK_CUDA(cudaEventRecord(aux->join, aux->st));
-    // W = Q_C^T A (with ||W||_F^2) and Z = R_C^{-1} W, as skel_id
+    // caller's chain: W = Q_C^T A (with ||W||_F^2), as skel_id
     GemmArgs g{};
     g.splitk_ws = kws1;
     g.M = s; g.N = n; g.K = m;
@@ -638,14 +645,10 @@ skel_status skel_id_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, i
                                 static_cast<float*>(W), n, pw, kws1, dev_status, stream));
     else
       SK_CUDA(launch_gemm(g, f64, LEFT_LOAD, EPI_STORE_SQ, stream));
-    SK_CUDA(launch_trsm_upper(s, n, Rc, s, 0, dtype, W, n, Z, ldz, stream));
-    if (sq_id || sq_cur) SK_CUDA(launch_sqnorm(m, n, dtype, A, lda, pa, stream));
-    if (sq_id) {
-      SK_CUDA(launch_reduce_sum(pa, nba, sq_id, 0, stream));
-      SK_CUDA(launch_reduce_sum(pw, nbw, sq_id + 1, 0, stream));
-    }
-    // M = W Q_R = Q_C^T A Q_R and U = R_C^{-1} M R_R^{-T}, as skel_cur
-    SK_CUDA(cudaStreamWaitEvent(stream, aux->join, 0));
+    SK_CUDA(cudaEventRecord(w_ready, stream));
+    // auxiliary chain, part 2: M = W Q_R = Q_C^T A Q_R and U = R_C^{-1} M R_R^{-T}, as skel_cur,
+    // concurrent with the solve for Z
+    SK_CUDA(cudaStreamWaitEvent(aux->st, w_ready, 0));
     GemmArgs h{};
     h.splitk_ws = kws2;
     h.M = s; h.N = s; h.K = n;
@@ -655,15 +658,24 @@ skel_status skel_id_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, i
     h.alpha = 1.0;
     h.partials = pm;
     h.timer = "gemm_cur";
-    SK_CUDA(launch_gemm(h, f64, LEFT_LOAD, EPI_STORE_SQ, stream));
+    SK_CUDA(launch_gemm(h, f64, LEFT_LOAD, EPI_STORE_SQ, aux->st));
+    SK_CUDA(launch_trsm_upper(s, s, Rc, s, 0, SKEL_F64, M, s, T1, s, aux->st));
+    SK_CUDA(launch_transpose_f64(s, T1, s, T2, s, aux->st));
+    SK_CUDA(launch_trsm_upper(s, s, Rr, s, 0, SKEL_F64, T2, s, T1, s, aux->st));
+    SK_CUDA(launch_transpose_f64(s, T1, s, U, ldu, aux->st));
+    // caller's chain: Z = R_C^{-1} W and the norms
+    SK_CUDA(launch_trsm_upper(s, n, Rc, s, 0, dtype, W, n, Z, ldz, stream));
+    if (sq_id || sq_cur) SK_CUDA(launch_sqnorm(m, n, dtype, A, lda, pa, stream));
+    if (sq_id) {
+      SK_CUDA(launch_reduce_sum(pa, nba, sq_id, 0, stream));
+      SK_CUDA(launch_reduce_sum(pw, nbw, sq_id + 1, 0, stream));
+    }
+    SK_CUDA(cudaEventRecord(aux->join, aux->st));
+    SK_CUDA(cudaStreamWaitEvent(stream, aux->join, 0));
     if (sq_cur) {
       SK_CUDA(launch_reduce_sum(pa, nba, sq_cur, 0, stream));
       SK_CUDA(launch_reduce_sum(pm, nbm, sq_cur + 1, 0, stream));
     }
-    SK_CUDA(launch_trsm_upper(s, s, Rc, s, 0, SKEL_F64, M, s, T1, s, stream));
-    SK_CUDA(launch_transpose_f64(s, T1, s, T2, s, stream));
-    SK_CUDA(launch_trsm_upper(s, s, Rr, s, 0, SKEL_F64, T2, s, T1, s, stream));
-    SK_CUDA(launch_transpose_f64(s, T1, s, U, ldu, stream));
   }
   return SKEL_OK;
 }
