@@ -17,7 +17,6 @@
 // lives in the workspace.
 #include <algorithm>
 #include <mutex>
-#include <vector>
 
 #include <cooperative_groups.h>
 
@@ -573,20 +572,12 @@ __global__ void lupp_gather_panel_kernel(const T* A, int64_t lda, int64_t m, int
   }
 }
 
-// Starts of the row panels before the current one: panel q covers steps start[q] ..
-// start[q+1]-1, and start[np] is the current panel's first step.
-struct PanelStarts {
-  int np;
-  int start[kAuxEvents + 1];
-};
-
-// Multipliers M(r, t), t < t0, of the rows r = t0 .. t0+b-1 (earlier panels as in ps):
+// Multipliers M(r, t), t < t0, of the rows r = t0 .. t0+b-1 (earlier panels of height B):
 // for each earlier panel q, the entries X(r, J_q) after the updates of the panels before q,
 // then forward substitution with R(panel q, J_q).  One warp per row; lane i holds the steps
 // i and i + 32 of panel q.  M(r, t) goes to Lw[r * ldw + t].
 template <typename T>
-__global__ void lupp_defer_m_kernel(const PanelParams<T> p, const __grid_constant__ PanelStarts ps, T* Lw,
-                                    int64_t ldw) {
+__global__ void lupp_defer_m_kernel(const PanelParams<T> p, int B, T* Lw, int64_t ldw) {
   const int lane = threadIdx.x & 31;
   const int ri = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (ri >= p.b) return;
@@ -594,8 +585,7 @@ __global__ void lupp_defer_m_kernel(const PanelParams<T> p, const __grid_constan
   const int64_t r = p.t0 + ri;
   T* Mr = Lw + r * ldw;
   const T* xr = p.Xg + r * p.n;
-  for (int q = 0; q < ps.np; ++q) {
-    const int tq = ps.start[q], B = ps.start[q + 1] - tq;
+  for (int tq = 0; tq < p.t0; tq += B) {
     const int q0 = lane, q1 = lane + 32;
     const bool h0 = q0 < B, h1 = q1 < B;
     const int j0 = h0 ? p.Js[tq + q0] : 0, j1 = h1 ? p.Js[tq + q1] : 0;
@@ -647,8 +637,7 @@ __global__ void lupp_defer_m_kernel(const PanelParams<T> p, const __grid_constan
 // subtracts M(r, tq+qq) R(tq+qq, j) for qq in order, skipping the columns selected by panel q
 // or earlier (sel tag <= q + 1), exactly as the trailing update after panel q would have.
 template <typename T>
-__global__ void __launch_bounds__(kTrailThreads) lupp_defer_trail_kernel(const PanelParams<T> p,
-                                                                         const __grid_constant__ PanelStarts ps,
+__global__ void __launch_bounds__(kTrailThreads) lupp_defer_trail_kernel(const PanelParams<T> p, int B,
                                                                          const T* Lw, int64_t ldw) {
   __shared__ __align__(16) T Mt[kMaxPanel][kTrailRows];
   const int r0 = blockIdx.y * kTrailRows;
@@ -658,22 +647,21 @@ __global__ void __launch_bounds__(kTrailThreads) lupp_defer_trail_kernel(const P
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = j < p.n;
   const int sj = live ? p.sel[j] : 0;
-  const int npan = ps.np;
+  const int npan = p.t0 / B;
   const int napply = sj == 0 ? npan : (sj - 1 < npan ? sj - 1 : npan);   // panels q < sel tag - 1
   T* x = p.Xg + (int64_t)(p.t0 + r0) * p.n + j;
   T v[kTrailRows];
 #pragma unroll
   for (int u = 0; u < kTrailRows; ++u) v[u] = live && u < nrows ? x[(int64_t)u * p.n] : T(0);
   for (int q = 0; q < npan; ++q) {
-    const int tq = ps.start[q], B = ps.start[q + 1] - tq;
     __syncthreads();
     for (int e = threadIdx.x; e < B * kTrailRows; e += blockDim.x) {
       const int qq = e / kTrailRows, u = e % kTrailRows;
-      Mt[qq][u] = u < nrows ? Lw[(int64_t)(p.t0 + r0 + u) * ldw + tq + qq] : T(0);
+      Mt[qq][u] = u < nrows ? Lw[(int64_t)(p.t0 + r0 + u) * ldw + (int64_t)q * B + qq] : T(0);
     }
     __syncthreads();
     if (!live || q >= napply) continue;
-    const T* Rj = p.R + (int64_t)tq * p.ldr + j;
+    const T* Rj = p.R + (int64_t)q * B * p.ldr + j;
     for (int q0 = 0; q0 < B; q0 += 8) {        // R entries of 8 steps loaded together
       T rq[8];
 #pragma unroll
@@ -833,25 +821,6 @@ skel_status run_panel_t(const PanelPlan& pl, const T* X, int64_t n, int64_t ldx,
 }
 
 
-// Panel boundaries of a pipelined chain: panels of bmax steps, then halving panels (multiples
-// of 8, at least 16 steps until the last) once at most 1.5 bmax steps remain, so that the row
-// chain's last panel, which can only start when the column chain has ended, is short.  Any
-// panel heights give the same factors (every entry sees the textbook operations in order).
-std::vector<int> panel_schedule(int s, int bmax) {
-  std::vector<int> st{0};
-  int t = 0;
-  while (t < s) {
-    const int rem = s - t;
-    int b;
-    if (rem <= 16) b = std::min(rem, bmax);
-    else if (2 * rem > 3 * bmax) b = bmax;
-    else b = std::min(bmax, std::max(16, (rem / 2 + 7) / 8 * 8));
-    t += b;
-    st.push_back(t);
-  }
-  return st;
-}
-
 template <typename T>
 cudaError_t launch_panel(const PanelParams<T>& p, const PanelPlan& pl, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
@@ -933,12 +902,10 @@ skel_status run_skeleton_t(const PanelPlan& pc, const PanelPlan& pr, const T* X,
   note_launches(2);
   if (cudaEventRecord(aux->fork, st) != cudaSuccess) return SKEL_ERR_CUDA;
   // column chain on the caller's stream
-  const std::vector<int> cs = panel_schedule(s, pc.b), rs = panel_schedule(s, pr.b);
-  if ((int)cs.size() - 1 > kAuxEvents || (int)rs.size() - 1 > kAuxEvents) return SKEL_ERR_UNSUPPORTED;
-  for (int k = 0; k + 1 < (int)cs.size(); ++k) {
-    const int t0 = cs[k];
+  int k = 0;
+  for (int t0 = 0; t0 < s; t0 += pc.b, ++k) {
     c.t0 = t0;
-    c.b = cs[k + 1] - t0;
+    c.b = std::min(pc.b, s - t0);
     c.sel_tag = (unsigned char)(k + 1);
     c.ldm = c.b;
     c.trow0 = t0 + c.b;
@@ -957,27 +924,22 @@ skel_status run_skeleton_t(const PanelPlan& pc, const PanelPlan& pr, const T* X,
   // row chain on the auxiliary stream
   if (cudaStreamWaitEvent(aux->st, aux->fork, 0) != cudaSuccess) return SKEL_ERR_CUDA;
   AuxJoin joiner{st, aux};              // joins on every return path below
-  PanelStarts ps{};
-  int kc = 0;
-  for (int k = 0; k + 1 < (int)rs.size(); ++k) {
-    const int t0 = rs[k];
+  k = 0;
+  for (int t0 = 0; t0 < s; t0 += pr.b, ++k) {
     r.t0 = t0;
-    r.b = rs[k + 1] - t0;
+    r.b = std::min(pr.b, s - t0);
     r.s = t0 + r.b;                       // no rows below: the epilogue forms no multipliers
     r.sel_tag = (unsigned char)(k + 1);
-    while (cs[kc + 1] < t0 + r.b) ++kc;   // the column panel that ends step t0+b-1
-    if (cudaStreamWaitEvent(aux->st, aux->col[kc], 0) != cudaSuccess) return SKEL_ERR_CUDA;
+    if (cudaStreamWaitEvent(aux->st, aux->col[(t0 + r.b - 1) / pc.b], 0) != cudaSuccess) return SKEL_ERR_CUDA;
     lupp_gather_panel_kernel<T><<<dim3((unsigned)std::min<int64_t>((m + 255) / 256, 32), (unsigned)r.b), 256, 0, aux->st>>>(
         A, lda, m, n, Js, t0, r.b, r.Xg, r.fail);
     note_launches(1);
     if (t0 > 0) {
-      ps.np = k;
-      for (int q = 0; q <= k; ++q) ps.start[q] = rs[q];
-      lupp_defer_m_kernel<T><<<(unsigned)((r.b + 7) / 8), 256, 0, aux->st>>>(r, ps, Lw, s);
+      lupp_defer_m_kernel<T><<<(unsigned)((r.b + 7) / 8), 256, 0, aux->st>>>(r, pr.b, Lw, s);
       dim3 grid((unsigned)((m + kTrailThreads - 1) / kTrailThreads), (unsigned)((r.b + kTrailRows - 1) / kTrailRows));
       {
         KernelTimer kt("lupp_trail", aux->st);
-        lupp_defer_trail_kernel<T><<<grid, kTrailThreads, 0, aux->st>>>(r, ps, Lw, s);
+        lupp_defer_trail_kernel<T><<<grid, kTrailThreads, 0, aux->st>>>(r, pr.b, Lw, s);
       }
       note_launches(2);
     }
@@ -1021,12 +983,10 @@ AuxSet* aux_set() {
 bool skeleton_pivot_pipelined(skel_dtype dt, int64_t n, int64_t m, int32_t s) {
   if (dt == SKEL_F64) {
     const PanelPlan pc = plan_panel<double>(n, s), pr = plan_panel<double>(m, s);
-    return pc.b > 0 && pr.b > 0 && (int)panel_schedule(s, pc.b).size() - 1 <= kAuxEvents &&
-           (int)panel_schedule(s, pr.b).size() - 1 <= kAuxEvents;
+    return pc.b > 0 && pr.b > 0 && (s + std::min(pc.b, pr.b) - 1) / std::min(pc.b, pr.b) <= kAuxEvents;
   }
   const PanelPlan pc = plan_panel<float>(n, s), pr = plan_panel<float>(m, s);
-  return pc.b > 0 && pr.b > 0 && (int)panel_schedule(s, pc.b).size() - 1 <= kAuxEvents &&
-         (int)panel_schedule(s, pr.b).size() - 1 <= kAuxEvents;
+  return pc.b > 0 && pr.b > 0 && (s + std::min(pc.b, pr.b) - 1) / std::min(pc.b, pr.b) <= kAuxEvents;
 }
 
 skel_status run_skeleton_pivot(skel_dtype dt, const void* X, int64_t n, int64_t ldx, int32_t s, const void* A,
