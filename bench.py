@@ -4,18 +4,20 @@
 Workload (one "step" = the whole hot path on one synthetic matrix resident in HBM):
   A: 8192 x 8192 FP32, A = U diag(sigma) V^T + 1e-6 floor, sigma_j = 1/j, Haar U, V;
   k = 256, oversampling p = 16 (l = 272), Gaussian embedding.
-  step = TF32 tensor-core sketch X = Gamma A  ->  LUPP on X (J_s, R^LU)  ->  gather C + row
-         LUPP on C (I_s)  [time-to-skeleton]  ->  column ID Z  [time-to-ID]  ->  stable CUR U
-         [time-to-CUR]  ->  Theorem 1's eta from R^LU; ID/CUR errors from the Gram identities.
-Reported: time-to-skeleton (ms, the metric), time-to-ID/CUR, A-streaming GB/s of the sketch,
+  step = TF32 tensor-core sketch X = Gamma A  ->  LUPP on X (J_s, R^LU) with the row LUPP on
+         C = A(:, J_s) (I_s) pipelined behind it  [time-to-skeleton]  ->  column ID Z and stable
+         CUR U from one QR of C  [time to ID and CUR]  ->  Theorem 1's eta from R^LU (on a
+         second stream, concurrent with the ID and CUR); errors from the Gram identities.
+Reported: time-to-skeleton (ms, the metric), time to ID and CUR, A-streaming GB/s of the sketch,
 per-call times, the FP64 plain-GPU form of the skeleton stage on the same A, relative ID
 error against the FP64 oracle, a roofline entry for the dominant call, the oracle timed on
 the host cores, and an end-to-end number through host buffers.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--k 256]
 
-Multi-GPU: the path does not shard in this build; N ranks run N independent replicas (one
-matrix each, weak scaling) with no collective on the data path.  --impl reference times the
+Multi-GPU: N ranks run N independent replicas (one matrix each, weak scaling) with no
+collective on the data path (the row-partitioned sketch with its one all-reduce is the
+library's `dist` module, exercised by the multi-process tests).  --impl reference times the
 FP64 CPU oracle (the only reference this paper has) on rank 0.
 """
 

@@ -44,7 +44,7 @@ typedef enum {
   SKEL_ERR_RANK_DEFICIENT = 4, /* device: an exactly zero pivot; dev_status[1] = its step  */
   SKEL_ERR_TIMEOUT = 5,        /* device: a grid-wide wait exceeded its limit              */
   SKEL_ERR_CUDA = 6,           /* a CUDA runtime call failed (launch, attribute, memset)   */
-  SKEL_ERR_UNSUPPORTED = 7     /* valid request this build does not implement              */
+  SKEL_ERR_UNSUPPORTED = 7     /* valid request the library does not implement              */
 } skel_status;
 
 /* storage type of a matrix */

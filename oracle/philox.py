@@ -9,8 +9,8 @@ two W-bit words through R rounds.  One round:
 
 and between rounds the key is bumped by the Weyl constants (k0 += W0, k1 += W1).
 
-The paper draws its embeddings from unspecified generators (Sec. 2.3); this build fixes
-Philox-4x32-10 as the counter-based source of every random number the method draws, so
+The paper draws its embeddings from unspecified generators (Sec. 2.3); this implementation
+fixes Philox-4x32-10 as the counter-based source of every random number the method draws, so
 that the GPU can regenerate any entry of Gamma from (seed, row, column) without storing it.
 """
 
