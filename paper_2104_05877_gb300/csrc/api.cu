@@ -390,7 +390,7 @@ skel_status skel_pivot_skeleton(skel_dtype dtype, const void* X, int64_t l, int6
   if (ws_handshake(std::max(lc, cbytes + lr), ws, ws_bytes, &st)) return st;
   SK_TRY(run_lupp_auto(dtype, X, n, ldx, s, Js, L, ldl, R, ldr, ws, *ws_bytes, dev_status, stream));
   void* C = ws;
-  SK_CUDA(launch_gather_cols(m, s, dtype, A, lda, Js, C, m, stream));
+  SK_CUDA(launch_gather_cols(m, s, dtype, A, lda, n, Js, C, m, stream));
   return run_lupp_auto(dtype, C, m, m, s, Is, nullptr, 0, nullptr, 0, static_cast<char*>(ws) + cbytes, lr, dev_status,
                        stream);
 }
@@ -416,8 +416,8 @@ bool id_args_ok(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t l
          s <= n && lda >= m;
 }
 
-// C = A(:, Js); C = Q R.  Returns device pointers through the arena.
-skel_status skeleton_qr(Arena& ar, bool run, int64_t m, skel_dtype dt, const void* A, int64_t lda,
+// C = A(:, Js) (A: m x n); C = Q R.  Returns device pointers through the arena.
+skel_status skeleton_qr(Arena& ar, bool run, int64_t m, int64_t n, skel_dtype dt, const void* A, int64_t lda,
                         int32_t s, const int32_t* idx, void** C, void** Q, double** R,
                         int32_t* dev_status, cudaStream_t st) {
   *C = ar.take(esize(dt) * (size_t)m * s);
@@ -426,7 +426,7 @@ skel_status skeleton_qr(Arena& ar, bool run, int64_t m, skel_dtype dt, const voi
   const size_t qn = qr_workspace(dt, m, s);
   void* qws = ar.take(qn);
   if (!run) return SKEL_OK;
-  SK_CUDA(launch_gather_cols(m, s, dt, A, lda, idx, *C, m, st));
+  SK_CUDA(launch_gather_cols(m, s, dt, A, lda, n, idx, *C, m, st));
   return run_qr(dt, *C, m, m, s, *Q, m, *R, s, qws, qn, dev_status, st);
 }
 
@@ -442,7 +442,7 @@ skel_status skel_id(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64
     Arena ar(run ? ws : nullptr);
     void *C, *Q;
     double* R;
-    SK_TRY(skeleton_qr(ar, run, m, dtype, A, lda, s, Js, &C, &Q, &R, dev_status, stream));
+    SK_TRY(skeleton_qr(ar, run, m, n, dtype, A, lda, s, Js, &C, &Q, &R, dev_status, stream));
     void* W = ar.take(esize(dtype) * (size_t)s * n);
     const bool tcw = !f64 && gemm_tc_usable(m, n, s, nullptr, m, A, lda);   // tensor-core W
     const int64_t nbw = tcw ? gemm_tc_num_partials(m, n, s) : gemm_num_blocks(s, n);
@@ -493,7 +493,7 @@ skel_status skel_pivot_rows(int64_t m, int64_t n, skel_dtype dtype, const void* 
       if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
       continue;
     }
-    SK_CUDA(launch_gather_cols(m, s, dtype, A, lda, Js, C, m, stream));
+    SK_CUDA(launch_gather_cols(m, s, dtype, A, lda, n, Js, C, m, stream));
     // C column-major m x s is C^T row-major s x m: row pivots of C = column pivots of C^T
     SK_TRY(run_lupp_auto(dtype, C, m, m, s, Is, nullptr, 0, nullptr, 0, lws, lw, dev_status, stream));
   }
@@ -512,7 +512,7 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
     Arena ar(run ? ws : nullptr);
     void *C, *Qc, *Rt, *Qr;
     double *Rc, *Rr;
-    SK_TRY(skeleton_qr(ar, run, m, dtype, A, lda, s, Js, &C, &Qc, &Rc, dev_status, stream));
+    SK_TRY(skeleton_qr(ar, run, m, n, dtype, A, lda, s, Js, &C, &Qc, &Rc, dev_status, stream));
     const size_t lw = rows_given ? 0 : lupp_auto_workspace(dtype, m, s);
     void* lws = rows_given ? nullptr : ar.take(lw);
     Rt = ar.take(esize(dtype) * (size_t)n * s);
@@ -539,7 +539,7 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
     // rows by LUPP on C (Algorithm 2 line 4): C column-major m x s is C^T row-major s x m
     if (!rows_given)
       SK_TRY(run_lupp_auto(dtype, C, m, m, s, Is, nullptr, 0, nullptr, 0, lws, lw, dev_status, stream));
-    SK_CUDA(launch_gather_rows_t(n, s, dtype, A, lda, Is, Rt, n, stream));
+    SK_CUDA(launch_gather_rows_t(n, s, dtype, A, lda, m, Is, Rt, n, stream));
     SK_TRY(run_qr(dtype, Rt, n, n, s, Qr, n, Rr, s, qws, qn, dev_status, stream));
     GemmArgs g{};
     g.splitk_ws = kws1;
@@ -603,7 +603,7 @@ skel_status skel_id_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, i
     AuxJoin joiner{stream, aux};          // joins on every return path below
     void *C, *Qc;
     double* Rc;
-    SK_TRY(skeleton_qr(ar, run, m, dtype, A, lda, s, Js, &C, &Qc, &Rc, dev_status, stream));
+    SK_TRY(skeleton_qr(ar, run, m, n, dtype, A, lda, s, Js, &C, &Qc, &Rc, dev_status, stream));
     void* Rt = ar.take(esize(dtype) * (size_t)n * s);
     void* Qr = ar.take(esize(dtype) * (size_t)n * s);
     double* Rr = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
@@ -629,7 +629,7 @@ skel_status skel_id_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, i
     }
     cudaEvent_t w_ready = aux->col[0];
     // auxiliary chain, part 1: R^T and its QR, concurrent with the QR of C
-    SK_CUDA(launch_gather_rows_t(n, s, dtype, A, lda, Is, Rt, n, aux->st));
+    SK_CUDA(launch_gather_rows_t(n, s, dtype, A, lda, m, Is, Rt, n, aux->st));
     SK_TRY(run_qr(dtype, Rt, n, n, s, Qr, n, Rr, s, qws, qn, dev_status, aux->st));
     // caller's chain: W = Q_C^T A (with ||W||_F^2), as skel_id
     GemmArgs g{};
@@ -699,8 +699,8 @@ skel_status skel_cur_sketch(int64_t m, int64_t n, skel_dtype dtype, const void* 
       if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
       continue;
     }
-    SK_CUDA(launch_gather_cols(m, s, dtype, A, lda, Js, C, m, stream));           // C = A(:, J)
-    SK_CUDA(launch_gather_rows_t(s, s, dtype, C, m, Is, St, s, stream));          // S^T(c, r) = C(I_r, c)
+    SK_CUDA(launch_gather_cols(m, s, dtype, A, lda, n, Js, C, m, stream));           // C = A(:, J)
+    SK_CUDA(launch_gather_rows_t(s, s, dtype, C, m, m, Is, St, s, stream));          // S^T(c, r) = C(I_r, c)
     SK_TRY(run_qr(dtype, St, s, s, s, Q, s, R, s, qws, qn, dev_status, stream));   // S^T = Q R
     SK_CUDA(launch_trsm_upper(s, s, R, s, 0, dtype, Q, s, V, s, stream));          // V = R^{-1} Q^T
     SK_CUDA(launch_transpose_f64(s, V, s, U, ldu, stream));                       // U = V^T = S^{-1}
@@ -719,7 +719,7 @@ skel_status skel_id_sketch(skel_dtype dtype, int32_t s, int64_t n, const void* R
   double* R1 = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
   skel_status st;
   if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
-  SK_CUDA(launch_gather_cols_rowmajor_f64(s, dtype, R, ldr, Js, R1, s, stream));   // R1(r, t) = R(r, j_t)
+  SK_CUDA(launch_gather_cols_rowmajor_f64(s, dtype, R, ldr, n, Js, R1, s, stream));   // R1(r, t) = R(r, j_t)
   SK_CUDA(launch_trsm_upper(s, n, R1, s, 1, dtype, R, ldr, Z, ldz, stream));        // Z = R1^{-1} R
   SK_CUDA(launch_unit_columns(s, Js, Z, ldz, stream));                              // Z(:, J) = I exactly
   return SKEL_OK;
@@ -762,7 +762,7 @@ skel_status skel_error(int64_t m, int64_t n, skel_dtype dtype, const void* A, in
     SK_CUDA(launch_fill_f64(out, 4, NAN, stream));
     SK_CUDA(launch_sqnorm(m, n, dtype, A, lda, pa, stream));
     SK_CUDA(launch_reduce_sum(pa, nba, out + 0, 1, stream));
-    if (need_js) SK_CUDA(launch_gather_cols(m, s, dtype, A, lda, Js, C, m, stream));
+    if (need_js) SK_CUDA(launch_gather_cols(m, s, dtype, A, lda, n, Js, C, m, stream));
     if (Z) {
       GemmArgs g{};
       g.M = m; g.N = n; g.K = s;
@@ -782,7 +782,7 @@ skel_status skel_error(int64_t m, int64_t n, skel_dtype dtype, const void* A, in
       g.out = P; g.out_sr = 1; g.out_sc = m; g.out_dt = dtype;
       g.alpha = 1.0;
       SK_CUDA(launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, stream));
-      SK_CUDA(launch_gather_rows_t(n, s, dtype, A, lda, Is, Rt, n, stream));
+      SK_CUDA(launch_gather_rows_t(n, s, dtype, A, lda, m, Is, Rt, n, stream));
       GemmArgs h{};
       h.M = m; h.N = n; h.K = s;
       h.L = View{P, 1, m}; h.l_dt = dtype;
@@ -807,7 +807,7 @@ skel_status skel_error(int64_t m, int64_t n, skel_dtype dtype, const void* A, in
         SK_CUDA(launch_syrk_ff(s, n, static_cast<const float*>(Rf), ldrf, H, s, kwsh, stream));
       else
         SK_CUDA(launch_gemm(g, true, LEFT_LOAD, EPI_STORE, stream));
-      SK_CUDA(launch_gather_cols_rowmajor_f64(s, rf_dtype, Rf, ldrf, Js, R1, s, stream));
+      SK_CUDA(launch_gather_cols_rowmajor_f64(s, rf_dtype, Rf, ldrf, n, Js, R1, s, stream));
       SK_CUDA(launch_trsm_upper(s, s, R1, s, 0, SKEL_F64, H, s, M1, s, stream));
       SK_CUDA(launch_transpose_f64(s, M1, s, M2, s, stream));
       SK_CUDA(launch_trsm_upper(s, s, R1, s, 0, SKEL_F64, M2, s, M1, s, stream));

@@ -379,31 +379,42 @@ __global__ void __launch_bounds__(256) sqnorm_kernel(int64_t m, int64_t n, const
   if (threadIdx.x == 0) partials[blockIdx.x] = v;
 }
 
+// Quiet NaN of the element type: what a gather writes for an index outside the matrix (never
+// reading it), so that the non-finite checks downstream report the bad index.
+template <typename T> __device__ __forceinline__ T gather_nan();
+template <> __device__ __forceinline__ float gather_nan<float>() { return __int_as_float(0x7fc00000); }
+template <> __device__ __forceinline__ double gather_nan<double>() { return __longlong_as_double(0x7ff8000000000000ll); }
+
 template <typename T>
-__global__ void gather_cols_kernel(int64_t m, const T* A, int64_t lda, const int32_t* idx,
+__global__ void gather_cols_kernel(int64_t m, const T* A, int64_t lda, int64_t ncols, const int32_t* idx,
                                    T* C, int64_t ldc) {
   const int r = blockIdx.y;
   const int64_t src = (int64_t)idx[r];
+  const bool ok = src >= 0 && src < ncols;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x)
-    C[i + r * ldc] = A[i + src * lda];
+    C[i + r * ldc] = ok ? A[i + src * lda] : gather_nan<T>();
 }
 
 template <typename T>
-__global__ void gather_rows_t_kernel(int64_t n, int32_t s, const T* A, int64_t lda,
+__global__ void gather_rows_t_kernel(int64_t n, int32_t s, const T* A, int64_t lda, int64_t nrows,
                                      const int32_t* idx, T* Rt, int64_t ldr) {
   const int r = blockIdx.y;
   const int64_t row = (int64_t)idx[r];
+  const bool ok = row >= 0 && row < nrows;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x)
-    Rt[c + r * ldr] = A[row + c * lda];
+    Rt[c + r * ldr] = ok ? A[row + c * lda] : gather_nan<T>();
 }
 
-__global__ void gather_cols_rm_kernel(int32_t s, skel_dtype dt, const void* F, int64_t ldf,
+__global__ void gather_cols_rm_kernel(int32_t s, skel_dtype dt, const void* F, int64_t ldf, int64_t ncols,
                                       const int32_t* idx, double* out, int64_t ldo) {
   const int r = blockIdx.x;
-  for (int t = threadIdx.x; t < s; t += blockDim.x)
-    out[(int64_t)r * ldo + t] = load_as<double>(F, (int64_t)r * ldf + idx[t], dt);
+  for (int t = threadIdx.x; t < s; t += blockDim.x) {
+    const int64_t j = idx[t];
+    out[(int64_t)r * ldo + t] = j >= 0 && j < ncols ? load_as<double>(F, (int64_t)r * ldf + j, dt)
+                                                    : gather_nan<double>();
+  }
 }
 
 __global__ void transpose_kernel(int32_t s, const double* in, int64_t ldi, double* out, int64_t ldo) {
@@ -527,32 +538,32 @@ cudaError_t launch_sqnorm(int64_t m, int64_t n, skel_dtype dt, const void* A, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_cols(int64_t m, int32_t s, skel_dtype dt, const void* A, int64_t lda,
+cudaError_t launch_gather_cols(int64_t m, int32_t s, skel_dtype dt, const void* A, int64_t lda, int64_t ncols,
                                const int32_t* idx, void* C, int64_t ldc, cudaStream_t st) {
   dim3 grid((unsigned)std::min<int64_t>((m + 255) / 256, 64), (unsigned)s);
   if (dt == SKEL_F64)
-    gather_cols_kernel<double><<<grid, 256, 0, st>>>(m, (const double*)A, lda, idx, (double*)C, ldc);
+    gather_cols_kernel<double><<<grid, 256, 0, st>>>(m, (const double*)A, lda, ncols, idx, (double*)C, ldc);
   else
-    gather_cols_kernel<float><<<grid, 256, 0, st>>>(m, (const float*)A, lda, idx, (float*)C, ldc);
+    gather_cols_kernel<float><<<grid, 256, 0, st>>>(m, (const float*)A, lda, ncols, idx, (float*)C, ldc);
   note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_rows_t(int64_t n, int32_t s, skel_dtype dt, const void* A, int64_t lda,
+cudaError_t launch_gather_rows_t(int64_t n, int32_t s, skel_dtype dt, const void* A, int64_t lda, int64_t nrows,
                                  const int32_t* idx, void* Rt, int64_t ldr, cudaStream_t st) {
   dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)s);
   if (dt == SKEL_F64)
-    gather_rows_t_kernel<double><<<grid, 256, 0, st>>>(n, s, (const double*)A, lda, idx, (double*)Rt, ldr);
+    gather_rows_t_kernel<double><<<grid, 256, 0, st>>>(n, s, (const double*)A, lda, nrows, idx, (double*)Rt, ldr);
   else
-    gather_rows_t_kernel<float><<<grid, 256, 0, st>>>(n, s, (const float*)A, lda, idx, (float*)Rt, ldr);
+    gather_rows_t_kernel<float><<<grid, 256, 0, st>>>(n, s, (const float*)A, lda, nrows, idx, (float*)Rt, ldr);
   note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_cols_rowmajor_f64(int32_t s, skel_dtype dt, const void* F, int64_t ldf,
+cudaError_t launch_gather_cols_rowmajor_f64(int32_t s, skel_dtype dt, const void* F, int64_t ldf, int64_t ncols,
                                             const int32_t* idx, double* out, int64_t ldo,
                                             cudaStream_t st) {
-  gather_cols_rm_kernel<<<s, 256, 0, st>>>(s, dt, F, ldf, idx, out, ldo);
+  gather_cols_rm_kernel<<<s, 256, 0, st>>>(s, dt, F, ldf, ncols, idx, out, ldo);
   note_launches(1);
   return cudaGetLastError();
 }

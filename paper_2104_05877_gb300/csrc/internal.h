@@ -63,14 +63,16 @@ int64_t sqnorm_num_blocks(int64_t m, int64_t n);
 cudaError_t launch_sqnorm(int64_t m, int64_t n, skel_dtype dt, const void* A, int64_t lda,
                           double* partials, cudaStream_t st);
 
-// C(:, r) = A(:, idx[r]) (m x s column-major out, ld = ldc), dtype preserved.
-cudaError_t launch_gather_cols(int64_t m, int32_t s, skel_dtype dt, const void* A, int64_t lda,
+// The gathers write NaN for an index outside [0, ncols) (or [0, nrows)) and never read A there.
+// C(:, r) = A(:, idx[r]) (m x s column-major out, ld = ldc) for A with ncols columns, dtype preserved.
+cudaError_t launch_gather_cols(int64_t m, int32_t s, skel_dtype dt, const void* A, int64_t lda, int64_t ncols,
                                const int32_t* idx, void* C, int64_t ldc, cudaStream_t st);
-// Rt(c, r) = A(idx[r], c): the transpose of the row gather, n x s column-major (ld = ldr).
-cudaError_t launch_gather_rows_t(int64_t n, int32_t s, skel_dtype dt, const void* A, int64_t lda,
+// Rt(c, r) = A(idx[r], c) for A with nrows rows: the transpose of the row gather, n x s
+// column-major (ld = ldr).
+cudaError_t launch_gather_rows_t(int64_t n, int32_t s, skel_dtype dt, const void* A, int64_t lda, int64_t nrows,
                                  const int32_t* idx, void* Rt, int64_t ldr, cudaStream_t st);
-// out(r, t) = F(r, idx[t]) for an s x ? row-major F: s x s row-major FP64 out.
-cudaError_t launch_gather_cols_rowmajor_f64(int32_t s, skel_dtype dt, const void* F, int64_t ldf,
+// out(r, t) = F(r, idx[t]) for an s x ncols row-major F: s x s row-major FP64 out.
+cudaError_t launch_gather_cols_rowmajor_f64(int32_t s, skel_dtype dt, const void* F, int64_t ldf, int64_t ncols,
                                             const int32_t* idx, double* out, int64_t ldo,
                                             cudaStream_t st);
 // out = in^T for an s x s row-major FP64 matrix.
