@@ -96,7 +96,13 @@ def lib():
 
 # ------------------------------------------------------------------------------------------
 def _ptr(t):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+    """Device address of a CUDA tensor (None for None).  Host tensors are refused here: the
+    kernels dereference every pointer they get on the device."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libskel takes CUDA tensors; got a tensor on " + str(t.device))
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _stream():

@@ -94,3 +94,13 @@ def test_oracle_not_imported_by_product():
         for f in fs:
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 assert "oracle" not in open(os.path.join(dp, f)).read(), f
+
+
+def test_binding_refuses_host_tensors():
+    """The binding never hands a host address to the library (the kernels would dereference
+    it on the device): a CPU tensor is refused before any call."""
+    import torch
+    import paper_2104_05877_gb300 as skel
+    with pytest.raises(ValueError):
+        skel._ptr(torch.zeros(4))
+    assert skel._ptr(None) is None
