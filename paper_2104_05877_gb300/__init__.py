@@ -470,13 +470,14 @@ def skeletonize(A, k, p=10, seed=0, prec="f32", pivot="lupp", kind="gaussian", z
         Js, _, Rf, _ = pivot_lupp(X, k, status=st)
     else:
         Js, Rf, _ = pivot_cpqr(X, k, status=st)
-    Z, sq, _ = column_id(A, Js, status=st)
-    out = dict(X=X, Js=Js, Rf=Rf, Z=Z, sq_norms=sq, status=st)
     if want_cur:
         if Is is None:
             Is, _ = pivot_rows(A, Js, status=st)
-        _, U, sq_cur, _ = cur(A, Js, Is, status=st)
-        out.update(Is=Is, U=U, sq_norms_cur=sq_cur)
+        Z, U, sq, sq_cur, _ = id_cur(A, Js, Is, status=st)      # one QR of C for both
+        out = dict(X=X, Js=Js, Rf=Rf, Z=Z, sq_norms=sq, status=st, Is=Is, U=U, sq_norms_cur=sq_cur)
+    else:
+        Z, sq, _ = column_id(A, Js, status=st)
+        out = dict(X=X, Js=Js, Rf=Rf, Z=Z, sq_norms=sq, status=st)
     if want_error:
         e, _ = error(A, Js, Z, out.get("Is"), out.get("U"), Rf, status=st)
         out["errors"] = e
