@@ -276,3 +276,18 @@ def test_srtt_entries_closed_form():
         ang = 2.0 * np.pi * ((sel[:, None] * rinv[None, :]) % m) / m
         want = phi[rinv][None, :] * (np.cos(ang) + np.sin(ang)) / np.sqrt(l)
         assert np.allclose(embedding.srtt_embedding(l, m, 21), want, atol=1e-13)
+
+
+def test_column_sketch_definition_and_range():
+    """Y = A Omega^T (Algorithm 3's column sketch) is the row sketch of A^T with the same
+    Omega, and on an exactly rank-r input with l >= r its columns span the range of A."""
+    import workloads
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((60, 45))
+    Yt = sketch.gaussian_col_sketch(A, 12, 5)
+    assert Yt.shape == (12, 60)
+    assert np.allclose(Yt, sketch.gaussian_sketch(A.T, 12, 5), atol=1e-13)
+    B = workloads.exact_rank(120, 90, 7, seed=2)
+    Y = sketch.gaussian_col_sketch(B, 10, 3).T                     # 120 x 10
+    Q, _ = np.linalg.qr(Y)
+    assert np.linalg.norm(B - Q @ (Q.T @ B)) <= 1e-10 * np.linalg.norm(B)
