@@ -1,19 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of randomized-pivoting skeletonization (Algorithm 2) on GB300.
 
-Workload (one "step" = the whole hot path on one synthetic matrix resident in HBM):
-  A: 8192 x 8192 FP32, A = U diag(sigma) V^T + 1e-6 floor, sigma_j = 1/j, Haar U, V;
-  k = 256, oversampling p = 16 (l = 272), Gaussian embedding.
-  step = TF32 tensor-core sketch X = Gamma A  ->  LUPP on X (J_s, R^LU) with the row LUPP on
-         C = A(:, J_s) (I_s) pipelined behind it  [time-to-skeleton]  ->  column ID Z and stable
-         CUR U from one QR of C  [time to ID and CUR]  ->  Theorem 1's eta from R^LU (on a
-         second stream, concurrent with the ID and CUR); errors from the Gram identities.
-Reported: time-to-skeleton (ms, the metric), time to ID and CUR, A-streaming GB/s of the sketch,
-per-call times, the FP64 plain-GPU form of the skeleton stage on the same A, relative ID
-error against the FP64 oracle, a roofline entry for the dominant call, the oracle timed on
-the host cores, and an end-to-end number through host buffers.
+Headline workload (the largest single-GPU configuration; one "step" = the whole hot path on
+one synthetic matrix resident in HBM):
+  A: 65536 x 32768 FP32 (8.6 GB), A = U diag(sigma) V^T + 1e-7 floor, sigma_j = exp(-j/200),
+     Haar U, V; k = 1024, oversampling p = 76 (l = 1100), Gaussian embedding.
+  step = tensor-core sketch X = Gamma A (--prec, BF16 by default)  ->  LUPP on X (J_s, R^LU)
+         [time-to-skeleton, the metric]  ->  column ID Z = C^+ A (Householder QR of C = A(:, J_s),
+         W = Q_C^T A, FP64 solve)  [time to ID]  ->  Theorem 1's eta from R^LU.
+Reported beside it: time-to-skeleton in every sketch precision (TF32, BF16, FP8) and in the
+plain FP64 GPU form on the same A, each with its relative ID error ||A - C Z||_F / ||A||_F formed
+directly on the device (the FP64 skeleton's error is the reference: the equal-error gate is
+1.05x), the sketch's tensor-core roofline, per-kernel times from a serialised pass, the oracle
+timed on the host cores on a bounded sample, an end-to-end number through host buffers, and
+the 8192 x 8192 (k = 256) step with the row skeletons and the CUR as extra keys.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--k 256]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--prec bf16]
+                  [--workload c5|c2] [--only ...]
 
 Multi-GPU: N ranks run N independent replicas (one matrix each, weak scaling) with no
 collective on the data path (the row-partitioned sketch with its one all-reduce is the
@@ -24,6 +27,7 @@ FP64 CPU oracle (the only reference this paper has) on rank 0.
 import argparse
 import json
 import os
+import resource
 import statistics
 import subprocess
 import sys
@@ -34,21 +38,34 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time-to-skeleton (ms) and A-streaming GB/s at rank k, mixed vs FP64 GPU, equal ID error"
-M_DIM = N_DIM = 8192
+
+# workloads: (m, n, k, p, floor, description)
+WORKLOADS = {
+    "c5": dict(m=65536, n=32768, k=1024, p=76,
+               text="dense 65536x32768 fp32 (8.6 GB), sigma_j=exp(-j/200) (j<=3300) + 1e-7 floor, Haar U/V"),
+    "c2": dict(m=8192, n=8192, k=256, p=16,
+               text="dense 8192x8192 fp32, sigma_j=1/j + 1e-6 floor, Haar U/V"),
+}
+ORACLE_SAMPLE_COLS = 1024       # bounded oracle sample: this many columns of A
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--k", type=int, default=256)
-    ap.add_argument("--p", type=int, default=16)
-    ap.add_argument("--prec", default="tf32", choices=["tf32", "bf16", "fp8", "f32"])
+    ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS))
+    ap.add_argument("--k", type=int, default=None, help="rank (default: the workload's)")
+    ap.add_argument("--p", type=int, default=None, help="oversampling (default: the workload's)")
+    ap.add_argument("--prec", default="bf16", choices=["tf32", "bf16", "fp8", "f32"])
     ap.add_argument("--blocks", type=int, default=4096, help="blocks of the batched run (--only batch)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-GPU comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 8192^2 extra keys")
+    ap.add_argument("--cols", type=int, default=None,
+                    help="with --only: this many columns of the workload's A instead of all of them (a smaller "
+                         "case of the same kernels for profilers)")
     ap.add_argument("--only", default=None, choices=["sketch", "lupp", "rows", "pivots", "id", "cur", "id_cur", "eta", "batch", "next",
                                                      "srtt", "power", "cols"],
                     help="run only this call (warm-up + steps, no extras): a small command for profilers; "
@@ -56,24 +73,37 @@ def parse():
                          "tol 1e-6) instead of the dense workload; 'next' times the rows beyond the hot "
                          "path (SRTT sketch, power sketch, column sketch, streaming selection, ID and CUR "
                          "from the sketch) on the same workload, one JSON line")
-    return ap.parse_args()
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    args.k = w["k"] if args.k is None else args.k
+    args.p = w["p"] if args.p is None else args.p
+    return args
 
 
-def workload_config(k, p, prec):
-    return {"workload": f"dense {M_DIM}x{N_DIM} fp32, sigma_j=1/j + 1e-6 floor, Haar U/V; "
-                        f"rank k={k}, oversampling p={p} (l={k + p}); Gaussian sketch ({prec}), "
-                        "LUPP on X, row LUPP on C, column ID + stable CUR",
-            "m": M_DIM, "n": N_DIM, "k": k, "l": k + p, "sketch_prec": prec,
-            "l2": "inputs larger than L2 (A is 268 MB; L2 129 MB)"}
+def workload_config(workload, k, p, prec):
+    w = WORKLOADS[workload]
+    steps = ("LUPP on X, column ID" if workload == "c5" else "LUPP on X, row LUPP on C, column ID + stable CUR")
+    return {"workload": f"{w['text']}; rank k={k}, oversampling p={p} (l={k + p}); Gaussian sketch ({prec}), {steps}",
+            "m": w["m"], "n": w["n"], "k": k, "l": k + p, "sketch_prec": prec,
+            "l2": f"inputs larger than L2 (A is {4 * w['m'] * w['n'] / 1e6:.0f} MB; L2 129 MB)"}
 
 
-def make_A(device, seed):
+def make_A(workload, device, seed, cols=None):
     import numpy as np
     import torch
     import workloads
-    sig = workloads.sigma_config2(min(M_DIM, N_DIM))
-    return workloads.torch_dense_spectrum(M_DIM, N_DIM, sig, 1e-6 / np.sqrt(M_DIM), seed, device,
-                                          torch.float32)
+    w = WORKLOADS[workload]
+    n = min(cols, w["n"]) if cols else w["n"]
+    if workload == "c5":
+        return workloads.torch_config5(device, w["m"], n, seed=seed)
+    sig = workloads.sigma_config2(min(w["m"], n))
+    return workloads.torch_dense_spectrum(w["m"], n, sig, 1e-6 / np.sqrt(w["m"]), seed, device, torch.float32)
+
+
+def seeds(workload, rank=0):
+    import workloads
+    cid = 5 if workload == "c5" else 2
+    return workloads.seed_for(cid) + rank, workloads.seed_for(cid, "gamma")
 
 
 # ------------------------------------------------------------------------------------------
@@ -134,70 +164,187 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# kernels timed with CUDA events during the timed region
-TIMED_KERNELS = ("sketch_tc", "sketch_fp8", "fp8_quantize", "gemm_tc", "lupp_panel", "lupp_trail", "qr_panel", "qr_wy", "trsm", "gemm_qr",
-                 "gemm_cur", "gemm_eta_h", "gemm_eta_sq", "gemm_simt")
+# kernels timed with CUDA events in the serialised pass
+TIMED_KERNELS = ("sketch_tc", "sketch_fp8", "fp8_quantize", "gemm_tc", "lupp_panel", "lupp_trail", "qr_panel", "qr_wy",
+                 "trsm", "gemm_qr", "gemm_cur", "gemm_eta_h", "gemm_eta_sq", "gemm_simt")
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel at this
-# workload (None where no capture of the current code exists)
-TRAFFIC_PER_LAUNCH = {"sketch_tc": 271.9e6, "gemm_tc": 332.4e6, "lupp_panel": 3.09e6, "qr_panel": 2.15e6}
+# workload, scaled from a smaller capture where noted in the profiles (None where no capture of
+# the current code exists)
+TRAFFIC_PER_LAUNCH = {"c5": {}, "c2": {"sketch_tc": 271.9e6, "gemm_tc": 332.4e6, "lupp_panel": 3.09e6,
+                                        "qr_panel": 2.15e6}}
+FP64_NOMINAL_TFLOPS = 1.25
+TENSOR_RATIO = {"bf16": 1.0, "tf32": 1.1 / 2.25, "fp8": 2.0}     # nominal dense ratios to BF16
 
 
 def load_peaks():
+    """(hbm GB/s, bf16 TFLOP/s burst, source); the full record via load_peaks_full()."""
+    d = load_peaks_full()
+    return d["hbm_gbs"], d["bf16_tflops"], d["source"]
+
+
+def load_peaks_full():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
             d = json.load(f)
-        return d["hbm_gbs"], d["bf16_tflops"], "measured"
-    return 6800.0, 1900.0, "fallback"
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def tensor_peak(prec, peaks, sustained):
+    base = peaks["bf16_tflops_sustained"] if sustained else peaks["bf16_tflops"]
+    return base * TENSOR_RATIO[prec]
 
 
 # ------------------------------------------------------------------------------------------
-def oracle_skeleton(A_np, k, p, seed):
-    """The FP64 CPU oracle's time-to-skeleton: sketch, LUPP on X, row LUPP on C."""
-    from oracle import sketch, pivoting
-    t0 = time.perf_counter()
-    X = sketch.gaussian_sketch(A_np, k + p, seed)
-    Js = pivoting.lupp_columns(X, k)["Js"]
-    Is = pivoting.lupp_rows(A_np[:, Js], k)["Js"]
-    return time.perf_counter() - t0, Js, Is
+def cpu_sample_baseline(A_host_cols, m, n, k, p, seed_G):
+    """The FP64 oracle's time-to-skeleton (sketch + LUPP on X) on a bounded sample: the first
+    n' columns of A.  Gamma's generation does not depend on n and is timed on its own; the
+    oracle's product and its LUPP (which updates every column at every step) scale linearly
+    with n, so the full-size estimate is t_Gamma + (t_sketch - t_Gamma + t_lupp) n / n'.
+    Threads: CPU time over wall time of the timed calls (numpy's BLAS threads the product)."""
+    from oracle import embedding, pivoting, sketch
+    ncols = A_host_cols.shape[1]
+    l = k + p
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    w0 = time.perf_counter()
+    t = time.perf_counter()
+    embedding.gaussian_normals(l, m, seed_G)
+    t_g = time.perf_counter() - t
+    t = time.perf_counter()
+    X = sketch.gaussian_sketch(A_host_cols, l, seed_G)
+    t_sk = time.perf_counter() - t
+    t = time.perf_counter()
+    pivoting.lupp_columns(X, min(k, ncols))
+    t_lu = time.perf_counter() - t
+    wall = time.perf_counter() - w0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    est = t_g + (max(t_sk - t_g, 0.0) + t_lu) * n / ncols
+    return {"value": est * 1e3, "unit": "ms", "cores": round(cpu / wall, 1), "kind": "oracle",
+            "sample": (f"FP64 oracle sketch + LUPP on the first {ncols} of {n} columns of the same A "
+                       f"(Gamma generation {t_g:.2f} s, sketch {t_sk:.2f} s, LUPP {t_lu:.2f} s measured; value = "
+                       f"Gamma + (sketch - Gamma + LUPP) x {n}/{ncols}); cores = CPU time / wall time"),
+            "host_cpus": os.cpu_count(), "measured_s": wall}
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
     import numpy as np
-    import workloads
-    seed_A, seed_G = workloads.seed_for(2), workloads.seed_for(2, "gamma")
-    try:
-        import torch
-        dev = "cuda" if torch.cuda.is_available() else "cpu"
-        A_np = np.asfortranarray(make_A(dev, seed_A).double().cpu().numpy())
-    except Exception:
-        A_np = workloads.dense_config2(M_DIM, N_DIM, seed=seed_A, dtype=np.float32).astype(np.float64)
-    times = []
+    import torch
+    w = WORKLOADS[args.workload]
+    seed_A, seed_G = seeds(args.workload)
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    A = make_A(args.workload, dev, seed_A)
+    ncols = min(ORACLE_SAMPLE_COLS, w["n"])
+    A_np = np.asfortranarray(A[:, :ncols].double().cpu().numpy())
+    del A
+    if dev == "cuda":
+        torch.cuda.empty_cache()
+    vals, last = [], None
     for i in range(args.warmup + args.steps):
-        dt, _, _ = oracle_skeleton(A_np, args.k, args.p, seed_G)
+        last = cpu_sample_baseline(A_np, w["m"], w["n"], args.k, args.p, seed_G)
         if i >= args.warmup:
-            times.append(dt * 1e3)
-    v = statistics.mean(times)
-    cores = os.cpu_count()
+            vals.append(last["value"])
+    v = statistics.mean(vals)
+    cb = dict(last, value=v)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args.k, args.p, "f64 oracle"),
-        "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle",
-                         "sample": "full workload per step (sketch + LUPP on X + row LUPP on C)"},
+        "config": workload_config(args.workload, args.k, args.p, "f64 oracle"),
+        "cpu_baseline": cb,
         "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
 # ------------------------------------------------------------------------------------------
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def direct_rel_error(skel, A, Js, st):
+    """||A - C Z||_F / ||A||_F with Z = C^+ A from skel_id, the residual formed on the device."""
+    Z, sq, _ = skel.column_id(A, Js, status=st)
+    e, _ = skel.error(A, Js, Z=Z, status=st)
+    e, sq = e.cpu().numpy(), sq.cpu().numpy()
+    gram = float(max(sq[0] - sq[1], 0.0) / sq[0]) ** 0.5
+    del Z
+    return float(e[1] / e[0]), gram
+
+
+def time_skeleton(skel, A, l, k, prec, seed_G, st, reps=3):
+    """Sketch + LUPP on X, timed alone with CUDA events (mean over reps after one warm-up)."""
+    import torch
+    X = torch.empty(l, A.shape[1], dtype=torch.float64 if prec == "f64" else torch.float32, device=A.device)
+
+    def once():
+        skel.sketch(A, l, prec=prec, seed=seed_G, X=X, status=st)
+        return skel.pivot_lupp(X, k, factors=False, status=st)[0]
+
+    Js = once()
+    torch.cuda.synchronize()
+    ev = _events(3 * reps)
+    for r in range(reps):
+        ev[3 * r].record()
+        skel.sketch(A, l, prec=prec, seed=seed_G, X=X, status=st)
+        ev[3 * r + 1].record()
+        Js = skel.pivot_lupp(X, k, factors=False, status=st)[0]
+        ev[3 * r + 2].record()
+    torch.cuda.synchronize()
+    skel.check_status(st, f"skeleton {prec}")
+    sk = statistics.mean(ev[3 * r].elapsed_time(ev[3 * r + 1]) for r in range(reps))
+    lu = statistics.mean(ev[3 * r + 1].elapsed_time(ev[3 * r + 2]) for r in range(reps))
+    del X
+    return Js, {"time_to_skeleton_ms": sk + lu, "sketch_ms": sk, "lupp_ms": lu, "reps": reps}
+
+
+def kernel_models(workload, m, n, k, l, prec, peaks, sustained):
+    """Algorithmic work of each timed kernel over one step: (bound, work, peak, unit)."""
+    hbm = peaks["hbm_gbs"]
+    a_bytes = 4.0 * m * n
+    fp32_alu = 152 * 128 * 2 * 2.07e9 / 1e12          # TFLOP/s, FFMA
+    b_pan = 24 if workload == "c5" else 64
+    # LUPP trailing updates: every panel reads and writes the rows below it once (4 B each way)
+    trail_bytes = sum(8.0 * max(k - t0 - b_pan, 0) * n for t0 in range(0, k, b_pan))
+    mod = {
+        "sketch_fp8": ("tensor", 2.0 * l * m * n / 1e12, tensor_peak("fp8", peaks, sustained), "TFLOP/s"),
+        "fp8_quantize": ("hbm", 5.0 * m * n / 1e9, hbm, "GB/s"),   # A read (4 B), A8 written (1 B)
+        "gemm_tc": ("tensor", 3 * 2.0 * k * m * n / 1e12, tensor_peak("tf32", peaks, sustained), "TFLOP/s"),
+        "lupp_trail": ("hbm", trail_bytes / 1e9, hbm, "GB/s"),
+        "trsm": ("alu", (1.0 * k * k * n) / 1e12, FP64_NOMINAL_TFLOPS, "TFLOP/s"),
+        "gemm_qr": ("alu", 4.0 * m * k * k / 1e12, fp32_alu, "TFLOP/s"),
+    }
+    if prec in ("tf32", "bf16"):
+        mod["sketch_tc"] = ("tensor", 2.0 * l * m * n / 1e12, tensor_peak(prec, peaks, sustained), "TFLOP/s")
+    if workload == "c2":
+        mod["trsm"] = ("alu", (1.0 * k * k * n + 4.0 * k ** 3) / 1e12, FP64_NOMINAL_TFLOPS, "TFLOP/s")
+    return mod
+
+
+def kernel_table(skel, nsteps, total_ms, models):
+    out = {}
+    for nm in TIMED_KERNELS:
+        tot, cnt = skel.kernel_time(nm)
+        if cnt == 0:
+            continue
+        ent = {"ms_per_step": tot / nsteps, "launches_per_step": cnt / nsteps, "avg_us": 1e3 * tot / cnt,
+               "share_of_step": tot / total_ms}
+        if nm in models:
+            b, w, pk, u = models[nm]
+            a = w / (tot / nsteps * 1e-3)
+            ent.update({"bound": b, "achieved": a, "peak": pk, "unit": u, "frac": a / pk})
+        out[nm] = ent
+    return out
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
     import paper_2104_05877_gb300 as skel
-    import workloads
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dev = torch.device(f"cuda:{local}")
@@ -205,72 +352,66 @@ def run_ours(args, rank, world):
     if not os.path.exists(skel.LIB_PATH):
         import __graft_entry__
         __graft_entry__.build()
-    k, p = args.k, args.p
-    l = k + p
     if args.only == "batch":
+        import workloads
         run_batch(args, rank, dev, skel, workloads)
         return
-    seed_A, seed_G = workloads.seed_for(2) + rank, workloads.seed_for(2, "gamma")
-    A = make_A(dev, seed_A)
+    k, p = args.k, args.p
+    l = k + p
+    seed_A, seed_G = seeds(args.workload, rank)
+    if args.cols and not args.only:
+        raise SystemExit("--cols is a profiling aid for --only runs")
+    A = make_A(args.workload, dev, seed_A, cols=args.cols)
     torch.cuda.synchronize()
     st = skel.new_status(dev)
-
-    names = ["sketch", "pivots", "id_cur", "eta_after_id_cur"]
-    main = torch.cuda.current_stream()
-    side = torch.cuda.Stream()
-
-    def step(evs):
-        evs[0].record()
-        X, _ = skel.sketch(A, l, prec=args.prec, seed=seed_G, status=st)
-        evs[1].record()
-        # column LUPP on X and row LUPP on C = A(:, Js), the latter pipelined behind the former
-        Js, Is, _, Rf, _ = skel.pivot_skeleton(X, A, k, status=st)
-        evs[2].record()
-        # eta needs only the pivot factor: it runs on a second stream while the column ID and
-        # the stable CUR (one QR of C for both) run on this one
-        side.wait_stream(main)
-        with torch.cuda.stream(side):
-            e, _ = skel.error(A, Js, Rf=Rf, status=st)
-        Z, U, sq_id, sq_cur, _ = skel.id_cur(A, Js, Is, status=st)
-        evs[3].record()
-        main.wait_stream(side)
-        evs[4].record()
-        return Js, Is, sq_id, sq_cur, e
-
     if args.only == "next":
         run_next(args, rank, A, skel, st, seed_G)
         return
     if args.only:
-        X, _ = skel.sketch(A, l, prec=args.prec, seed=seed_G, status=st)
-        Js, _, Rf, _ = skel.pivot_lupp(X, k, status=st)
-        Is, _ = skel.pivot_rows(A, Js, status=st)
-        call = {"sketch": lambda: skel.sketch(A, l, prec=args.prec, seed=seed_G, X=X, status=st),
-                "lupp": lambda: skel.pivot_lupp(X, k, status=st),
-                "rows": lambda: skel.pivot_rows(A, Js, status=st),
-                "pivots": lambda: skel.pivot_skeleton(X, A, k, status=st),
-                "id": lambda: skel.column_id(A, Js, status=st),
-                "cur": lambda: skel.cur(A, Js, Is, status=st),
-                "id_cur": lambda: skel.id_cur(A, Js, Is, status=st),
-                "eta": lambda: skel.error(A, Js, Rf=Rf, status=st),
-                "srtt": lambda: skel.sketch(A, l, kind="srtt", prec=args.prec, seed=seed_G, X=X, status=st),
-                "power": lambda: skel.sketch_power(A, l, q=1, prec=args.prec, seed=seed_G, status=st),
-                "cols": lambda: skel.sketch_cols(A, l, prec=args.prec, seed=seed_G + 1, status=st)}[args.only]
-        for _ in range(args.warmup):
-            call()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            call()
-        e1.record()
-        torch.cuda.synchronize()
-        skel.check_status(st, args.only)
-        if rank == 0:
-            print(json.dumps({"only": args.only, "ms": e0.elapsed_time(e1) / args.steps,
-                              "config": workload_config(k, p, args.prec)}), flush=True)
+        run_only(args, rank, A, skel, st, seed_G)
         return
+    if args.workload == "c2":
+        res = run_c2_step(args, rank, world, dev, A, skel, st, seed_G, headline=True)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return
+    run_c5(args, rank, world, dev, A, skel, st, seed_G, local)
 
-    mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+
+def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
+    import numpy as np
+    import torch
+    k, p = args.k, args.p
+    l = k + p
+    m, n = A.shape
+    prec = args.prec
+    main = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    X = torch.empty(l, n, device=dev)
+    names = ["sketch", "lupp", "id", "eta_after_id"]
+
+    def step(evs, serial=False):
+        evs[0].record()
+        skel.sketch(A, l, prec=prec, seed=seed_G, X=X, status=st)
+        evs[1].record()
+        Js, _, Rf, _ = skel.pivot_lupp(X, k, status=st)
+        evs[2].record()
+        # eta needs only the pivot factor: it runs on a second stream while the column ID runs
+        # on this one (on this stream too in the serialised per-kernel pass)
+        if serial:
+            e, _ = skel.error(A, Js, Rf=Rf, status=st)
+        else:
+            side.wait_stream(main)
+            with torch.cuda.stream(side):
+                e, _ = skel.error(A, Js, Rf=Rf, status=st)
+        Z, sq, _ = skel.column_id(A, Js, status=st)
+        evs[3].record()
+        if not serial:
+            main.wait_stream(side)
+        evs[4].record()
+        return Js, Z, sq, e
+
+    mk = lambda: _events(len(names) + 1)
     for _ in range(args.warmup):
         step(mk())
     torch.cuda.synchronize()
@@ -280,107 +421,251 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     launches0 = skel.launch_count()
     all_evs = [mk() for _ in range(args.steps)]
-    t_begin = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
+    t_begin, t_end = _events(2)
     with ClockSampler(local) as clk:
         t_begin.record()
         for i in range(args.steps):
             out = step(all_evs[i])
         t_end.record()
         torch.cuda.synchronize()
-    # second timed region, same steps, with CUDA events around the hot kernels' launches (kept
-    # apart so that the recorded events do not touch the headline numbers)
-    skel.kernel_timing(True)
-    kev = [mk() for _ in range(args.steps)]
-    k_begin, k_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    k_begin.record()
-    for i in range(args.steps):
-        step(kev[i])
-    k_end.record()
-    torch.cuda.synchronize()
-    ktimes = {nm: skel.kernel_time(nm) for nm in TIMED_KERNELS}
-    skel.kernel_timing(False)
-    k_total_ms = k_begin.elapsed_time(k_end)
+    launches = skel.launch_count() - launches0
     if world > 1:
         torch.distributed.barrier()
+    skel.check_status(st, "timed steps")
+    total_ms = t_begin.elapsed_time(t_end)
+    per = {nm: statistics.mean(ev[i].elapsed_time(ev[i + 1]) for ev in all_evs) for i, nm in enumerate(names)}
+    tts = statistics.mean(ev[0].elapsed_time(ev[2]) for ev in all_evs)
+    tid = statistics.mean(ev[0].elapsed_time(ev[3]) for ev in all_evs)
+    if world > 1:
+        t = torch.tensor([tts, total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tts, total_ms = float(t[0]), float(t[1])
+    Js, Z, sq, e = out
+    del Z
+    if rank != 0:
+        return
+
+    # serialised pass: the same steps on one stream, CUDA events around every hot launch
+    peaks = load_peaks_full()
+    nser = max(2, min(args.steps, 5))
+    skel.kernel_timing(True)
+    s0, s1 = _events(2)
+    s0.record()
+    for _ in range(nser):
+        step(mk(), serial=True)
+    s1.record()
+    torch.cuda.synchronize()
+    ser_ms = s0.elapsed_time(s1)
+    models = kernel_models("c5", m, n, k, l, prec, peaks, sustained=True)
+    kernels = kernel_table(skel, nser, ser_ms, models)
+    skel.kernel_timing(False)
+    skel.check_status(st, "serialised pass")
+
+    # the sketch kernel's roofline (the dominant kernel of time-to-skeleton)
+    sk_name = "sketch_fp8" if prec == "fp8" else "sketch_tc"
+    kd = kernels.get(sk_name, {})
+    roofline = None
+    if "bound" in kd:
+        work = 2.0 * l * m * n
+        achieved = work / (kd["avg_us"] * 1e-6) / 1e12
+        pk = tensor_peak(prec, peaks, sustained=True)
+        roofline = {"kernel": sk_name, "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                    "frac": achieved / pk, "traffic": TRAFFIC_PER_LAUNCH["c5"].get(f"{sk_name}_{prec}"),
+                    "peak_source": (f"{peaks['source']} MEASURED_PEAKS.json bf16_tflops_sustained x {TENSOR_RATIO[prec]:.3f} "
+                                    f"(nominal {prec}:bf16 dense ratio)"),
+                    "frac_of_burst_peak": achieved / tensor_peak(prec, peaks, sustained=False),
+                    "work_per_launch": f"2 l m n = {work:.3e} flop", "avg_launch_us": kd["avg_us"],
+                    "timing": "CUDA events on the launching stream around every launch, serialised pass of the same steps"}
+
+    # every sketch precision: time-to-skeleton alone, and the ID error of its skeleton formed directly
+    per_prec = {}
+    for pr in ("tf32", "bf16", "fp8"):
+        J, tm = time_skeleton(skel, A, l, k, pr, seed_G, st)
+        rel, gram = direct_rel_error(skel, A, J, st)
+        tm.update({"rel_id_error": rel, "rel_id_error_gram": gram, "a_streaming_gbs": 4.0 * m * n / (tm["sketch_ms"] * 1e-3) / 1e9,
+                   "sketch_tflops": 2.0 * l * m * n / (tm["sketch_ms"] * 1e-3) / 1e12})
+        per_prec[pr] = tm
+    torch.cuda.synchronize()
+    skel.check_status(st, "per precision")
+
+    # the plain FP64 GPU form of the skeleton stage on the same A
+    fp64 = None
+    if not args.no_fp64:
+        A64 = A.double().t().contiguous().t()
+        J64, tm = time_skeleton(skel, A64, l, k, "f64", seed_G, st, reps=1)
+        del A64
+        torch.cuda.empty_cache()
+        rel, gram = direct_rel_error(skel, A, J64, st)
+        tm.update({"rel_id_error": rel, "rel_id_error_gram": gram,
+                   "a_streaming_gbs": 8.0 * m * n / (tm["sketch_ms"] * 1e-3) / 1e9,
+                   "id_error_note": "ID of the FP64 skeleton formed by skel_id on the FP32 A, residual on the device"})
+        fp64 = tm
+        for pr, ent in per_prec.items():
+            ent["id_error_ratio_vs_fp64"] = ent["rel_id_error"] / rel
+            ent["speedup_vs_fp64"] = tm["time_to_skeleton_ms"] / ent["time_to_skeleton_ms"]
+    rel_id, rel_gram = direct_rel_error(skel, A, Js, st)
+
+    # end to end through host buffers: pinned A -> device, sketch + LUPP, J_s back
+    A_host = torch.empty(n, m, dtype=torch.float32, pin_memory=True)
+    A_host.copy_(A.t())
+    Js_h = torch.empty(k, dtype=torch.int32, pin_memory=True)
+    A_dev = A.t()           # reuse A's storage: the copy overwrites it with the same values
+
+    def e2e_step():
+        A_dev.copy_(A_host, non_blocking=True)
+        Ad = A_dev.t()
+        skel.sketch(Ad, l, prec=prec, seed=seed_G, X=X, status=st)
+        J, _, _, _ = skel.pivot_lupp(X, k, factors=False, status=st)
+        Js_h.copy_(J, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e_steps = max(3, min(args.steps, 10))
+    e0, e1 = _events(2)
+    e0.record()
+    for _ in range(e_steps):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    skel.check_status(st, "e2e")
+    e2e_ms = e0.elapsed_time(e1) / e_steps
+    del A_host
+
+    cpu = None
+    if not args.no_cpu:
+        ncols = min(ORACLE_SAMPLE_COLS, n)
+        A_np = np.asfortranarray(A[:, :ncols].double().cpu().numpy())
+        cpu = cpu_sample_baseline(A_np, m, n, k, p, seed_G)
+
+    extra = None
+    if not args.no_extra:
+        del X
+        torch.cuda.empty_cache()
+        A2 = make_A("c2", dev, seeds("c2", rank)[0])
+        a2 = argparse.Namespace(**vars(args))
+        a2.workload, a2.k, a2.p, a2.prec, a2.no_cpu = "c2", 256, 16, "tf32", True
+        extra = run_c2_step(a2, rank, world, dev, A2, skel, skel.new_status(dev), seeds("c2")[1], headline=False)
+        del A2
+
+    res = {
+        "metric": METRIC, "value": tts, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+        "config": workload_config("c5", k, p, prec),
+        "time_to_id_ms": tid, "calls_ms": per,
+        "a_streaming_gbs": 4.0 * m * n / (per["sketch"] * 1e-3) / 1e9,
+        "sketch_tflops": 2.0 * l * m * n / (per["sketch"] * 1e-3) / 1e12,
+        "rel_id_error": rel_id, "rel_id_error_gram": rel_gram, "eta": float(e[3]),
+        "id_error_ratio_vs_fp64": (rel_id / fp64["rel_id_error"]) if fp64 else None,
+        "precisions": per_prec, "fp64_gpu": fp64,
+        "roofline": roofline, "kernels": kernels, "serialised_ms_per_step": ser_ms / nser,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(4 * m * n), "d2h_bytes_per_step": int(4 * k),
+                "steps": e_steps, "what": "pinned host A copied to the device, sketch + LUPP, J_s copied back"},
+        "gpu_launches": launches, "clocks": clk.summary(),
+        "extra_8192": extra,
+    }
+    print(json.dumps(res), flush=True)
+
+
+def run_c2_step(args, rank, world, dev, A, skel, st, seed_G, headline):
+    """The 8192 x 8192 step: TF32 sketch -> both LUPPs pipelined (time-to-skeleton) -> column ID
+    and stable CUR from one QR of C -> eta on a second stream."""
+    import numpy as np
+    import torch
+    k, p = args.k, args.p
+    l = k + p
+    m, n = A.shape
+    names = ["sketch", "pivots", "id_cur", "eta_after_id_cur"]
+    main = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+
+    def step(evs, serial=False):
+        evs[0].record()
+        X, _ = skel.sketch(A, l, prec=args.prec, seed=seed_G, status=st)
+        evs[1].record()
+        Js, Is, _, Rf, _ = skel.pivot_skeleton(X, A, k, status=st)
+        evs[2].record()
+        if serial:
+            e, _ = skel.error(A, Js, Rf=Rf, status=st)
+        else:
+            side.wait_stream(main)
+            with torch.cuda.stream(side):
+                e, _ = skel.error(A, Js, Rf=Rf, status=st)
+        Z, U, sq_id, sq_cur, _ = skel.id_cur(A, Js, Is, status=st)
+        evs[3].record()
+        if not serial:
+            main.wait_stream(side)
+        evs[4].record()
+        return Js, Is, Z, U, sq_id, sq_cur, e
+
+    mk = lambda: _events(len(names) + 1)
+    for _ in range(args.warmup):
+        step(mk())
+    torch.cuda.synchronize()
+    skel.check_status(st, "warmup")
+    if world > 1 and headline:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = skel.launch_count()
+    all_evs = [mk() for _ in range(args.steps)]
+    t_begin, t_end = _events(2)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    with ClockSampler(local) as clk:
+        t_begin.record()
+        for i in range(args.steps):
+            out = step(all_evs[i])
+        t_end.record()
+        torch.cuda.synchronize()
     launches = skel.launch_count() - launches0
     skel.check_status(st, "timed steps")
     total_ms = t_begin.elapsed_time(t_end)
     per = {nm: statistics.mean(ev[i].elapsed_time(ev[i + 1]) for ev in all_evs) for i, nm in enumerate(names)}
     tts = statistics.mean(ev[0].elapsed_time(ev[2]) for ev in all_evs)
     tcur = statistics.mean(ev[0].elapsed_time(ev[3]) for ev in all_evs)
-    if world > 1:
+    if world > 1 and headline:
         t = torch.tensor([tts, total_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         tts, total_ms = float(t[0]), float(t[1])
-    Js, Is, sq_id, sq_cur, e = out
-    sq_id, sq_cur, e = sq_id.cpu().numpy(), sq_cur.cpu().numpy(), e.cpu().numpy()
-    rel_id = float(np.sqrt(max(sq_id[0] - sq_id[1], 0.0) / sq_id[0]))
-    rel_cur = float(np.sqrt(max(sq_cur[0] - sq_cur[1], 0.0) / sq_cur[0]))
+    Js, Is, Z, U, sq_id, sq_cur, e = out
+    # errors formed directly from the residuals on the device
+    er, _ = skel.error(A, Js, Z=Z, Is=Is, U=U, status=st)
+    er = er.cpu().numpy()
+    sq_id, sq_cur = sq_id.cpu().numpy(), sq_cur.cpu().numpy()
+    rel_id, rel_cur = float(er[1] / er[0]), float(er[2] / er[0])
+    rel_id_gram = float(np.sqrt(max(sq_id[0] - sq_id[1], 0.0) / sq_id[0]))
+    rel_cur_gram = float(np.sqrt(max(sq_cur[0] - sq_cur[1], 0.0) / sq_cur[0]))
     if rank != 0:
-        return
+        return None
 
-    hbm, bf16, peak_src = load_peaks()
-    tf32_peak = bf16 * (1.1 / 2.25)          # nominal TF32 : BF16 dense ratio
-    m, n = M_DIM, N_DIM
-    a_bytes = 4.0 * m * n
-    sketch_gbs = a_bytes / (per["sketch"] * 1e-3) / 1e9
-    sketch_tflops = 2.0 * l * m * n / (per["sketch"] * 1e-3) / 1e12
-    fp32_alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12        # TFLOP/s, FFMA
-    fp64_alu_peak = 1.25                                  # TFLOP/s, nominal FP64
-    # Algorithmic work of each timed kernel over one step (bound, work, peak, unit):
-    #   sketch_tc   X = Gamma A: 2 l m n TF32 flop (or 4 m n bytes of A if HBM-bound)
-    #   sketch_fp8  X = Gamma8 A8 from the e4m3 copy of A: m n bytes; fp8_quantize reads A and
-    #               writes A8: 5 m n bytes
-    #   gemm_tc     W = Q^T A, shared by the ID and the CUR: 3 (2 k m n) TF32 flop (3 products)
-    #   lupp_panel  s greedy steps over n (LUPP on X) and over m (row LUPP on C): the panel
-    #               rank-1 updates, sum over panels of b^2 cols (mul + sub)
-    #   qr_panel    the column steps of the two Householder QRs (C and R^T): 2 rows k^2
-    #               flop each (the panels' WY factors are formed by other kernels)
-    #   trsm        Z = R_C^{-1} W (k^2 n) and four k x k solves (CUR, eta): FP64
-    #   gemm_eta_h  upper triangle of R R^T in float-float: k(k+1)/2 n products, each
-    #               9 FP32 pipe instructions (exact product + two-sum); peak = one FP32
-    #               instruction per lane per clock
-    b_pan = 64
-    lupp_flops = sum(min(b_pan, k - t0) ** 2 for t0 in range(0, k, b_pan)) * (n + m)
-    models = {
-        "sketch_tc": ("tensor", 2.0 * l * m * n / 1e12, tf32_peak, "TFLOP/s")
-        if 2.0 * l * m * n / (tf32_peak * 1e12) > a_bytes / (hbm * 1e9) else ("hbm", a_bytes / 1e9, hbm, "GB/s"),
-        "sketch_fp8": ("hbm", m * n / 1e9, hbm, "GB/s"),           # A8: one byte per element
-        "fp8_quantize": ("hbm", 5.0 * m * n / 1e9, hbm, "GB/s"),   # A read (4 B), A8 written (1 B)
-        "gemm_tc": ("tensor", 3 * 2.0 * k * m * n / 1e12, tf32_peak, "TFLOP/s"),
-        "lupp_panel": ("alu", lupp_flops / 1e12, fp32_alu_peak, "TFLOP/s"),
-        "qr_panel": ("alu", 2.0 * (m + n) * k * k / 1e12, fp32_alu_peak, "TFLOP/s"),
-        "trsm": ("alu", (1.0 * k * k * n + 4.0 * k ** 3) / 1e12, fp64_alu_peak, "TFLOP/s"),
-        "gemm_eta_h": ("alu", 9.0 * k * (k + 1) / 2 * n / 1e12, fp32_alu_peak / 2, "TOP/s"),
-    }
-    kernels = {}
-    for nm, (tot, cnt) in ktimes.items():
-        if cnt == 0:
-            continue
-        ent = {"ms_per_step": tot / args.steps, "launches_per_step": cnt / args.steps,
-               "avg_us": 1e3 * tot / cnt, "share_of_step": tot / k_total_ms}
-        if nm in models:
-            b, w, pk, u = models[nm]
-            a = w / (tot / args.steps * 1e-3)          # work per step / device time per step
-            ent.update({"bound": b, "achieved": a, "peak": pk, "unit": u, "frac": a / pk})
-        kernels[nm] = ent
+    peaks = load_peaks_full()
+    nser = max(2, min(args.steps, 10))
+    skel.kernel_timing(True)
+    s0, s1 = _events(2)
+    s0.record()
+    for _ in range(nser):
+        step(mk(), serial=True)
+    s1.record()
+    torch.cuda.synchronize()
+    ser_ms = s0.elapsed_time(s1)
+    kernels = kernel_table(skel, nser, ser_ms, kernel_models("c2", m, n, k, l, args.prec, peaks, sustained=False))
+    skel.kernel_timing(False)
     modeled = [nm for nm in kernels if "bound" in kernels[nm]]
-    dom = max(modeled, key=lambda nm: kernels[nm]["ms_per_step"])
-    kd = kernels[dom]
-    roofline = {"kernel": dom, "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
-                "unit": kd["unit"], "frac": kd["frac"], "traffic": TRAFFIC_PER_LAUNCH.get(dom),
-                "peak_source": f"{peak_src} MEASURED_PEAKS.json" if peak_src == "measured" else "fallback",
-                "launches_per_step": kd["launches_per_step"], "avg_launch_us": kd["avg_us"],
-                "timing": "CUDA events on the launching stream around every launch, in a second timed "
-                          "region of the same steps"}
-    calls = {nm: {"ms": per[nm], "share": per[nm] / sum(per.values())} for nm in names}
+    roofline = None
+    if modeled:
+        dom = max(modeled, key=lambda nm: kernels[nm]["ms_per_step"])
+        kd = kernels[dom]
+        roofline = {"kernel": dom, "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
+                    "unit": kd["unit"], "frac": kd["frac"], "traffic": TRAFFIC_PER_LAUNCH["c2"].get(dom),
+                    "peak_source": f"{peaks['source']} MEASURED_PEAKS.json (burst)",
+                    "avg_launch_us": kd["avg_us"],
+                    "timing": "CUDA events around every launch, serialised pass of the same steps"}
 
     # FP64 plain-GPU form of the skeleton stage on the same matrix
     fp64 = None
     if not args.no_fp64:
         A64 = A.double().t().contiguous().t()
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        evs = _events(3)
         for rep in range(2):
             evs[0].record()
             X64, _ = skel.sketch(A64, l, prec="f64", seed=seed_G, status=st)
@@ -388,13 +673,10 @@ def run_ours(args, rank, world):
             J64, I64, _, _, _ = skel.pivot_skeleton(X64, A64, k, factors=False, status=st)
             evs[2].record()
         torch.cuda.synchronize()
-        _, sq64, _ = skel.column_id(A64, J64, status=st)
-        torch.cuda.synchronize()
         skel.check_status(st, "fp64")
-        sq64 = sq64.cpu().numpy()
+        rel64, _ = direct_rel_error(skel, A, J64, st)
         fp64 = {"time_to_skeleton_ms": evs[0].elapsed_time(evs[2]), "sketch_ms": evs[0].elapsed_time(evs[1]),
-                "pivots_ms": evs[1].elapsed_time(evs[2]),
-                "rel_id_error": float(np.sqrt(max(sq64[0] - sq64[1], 0.0) / sq64[0])),
+                "pivots_ms": evs[1].elapsed_time(evs[2]), "rel_id_error": rel64,
                 "same_skeleton": bool(torch.equal(J64.cpu(), Js.cpu()))}
         del A64, X64
 
@@ -416,7 +698,7 @@ def run_ours(args, rank, world):
     for _ in range(2):
         e2e_step()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = _events(2)
     e0.record()
     for _ in range(args.steps):
         e2e_step()
@@ -425,35 +707,62 @@ def run_ours(args, rank, world):
     skel.check_status(st, "e2e")
     e2e_ms = e0.elapsed_time(e1) / args.steps
 
-    # the FP64 CPU oracle on the host: one bounded sample of the same workload + its ID error
     cpu = None
-    oracle_err = None
     if not args.no_cpu:
-        from oracle import decomp, errors
-        A_np = np.asfortranarray(A.double().cpu().numpy())
-        dt, Jo, Io = oracle_skeleton(A_np, k, p, seed_G)
-        cpu = {"value": dt * 1e3, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "one full time-to-skeleton run (FP64 sketch + LUPP on X + row LUPP on C) on the same A"}
-        Zo = decomp.column_id(A_np, Jo)
-        oracle_err = errors.rel_id_error(A_np, Jo, Zo)
-
+        A_np = np.asfortranarray(A[:, :min(ORACLE_SAMPLE_COLS, n)].double().cpu().numpy())
+        cpu = cpu_sample_baseline(A_np, m, n, k, p, seed_G)
     res = {
         "metric": METRIC, "value": tts, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-        "config": workload_config(k, p, args.prec),
-        "time_to_id_and_cur_ms": tcur, "a_streaming_gbs": sketch_gbs,
-        "sketch_tflops": sketch_tflops, "calls_ms": per,
-        "rel_id_error": rel_id, "rel_cur_error": rel_cur, "eta": float(e[3]),
-        "oracle_rel_id_error": oracle_err,
-        "id_error_ratio_vs_oracle": (rel_id / oracle_err) if oracle_err else None,
-        "fp64_gpu": fp64,
-        "roofline": roofline, "kernels": kernels, "calls": calls, "cpu_baseline": cpu,
+        "config": workload_config("c2", k, p, args.prec),
+        "time_to_id_and_cur_ms": tcur, "a_streaming_gbs": 4.0 * m * n / (per["sketch"] * 1e-3) / 1e9,
+        "sketch_tflops": 2.0 * l * m * n / (per["sketch"] * 1e-3) / 1e12, "calls_ms": per,
+        "rel_id_error": rel_id, "rel_cur_error": rel_cur, "rel_id_error_gram": rel_id_gram,
+        "rel_cur_error_gram": rel_cur_gram, "eta": float(e[3]),
+        "fp64_gpu": fp64, "id_error_ratio_vs_fp64": (rel_id / fp64["rel_id_error"]) if fp64 else None,
+        "roofline": roofline, "kernels": kernels, "serialised_ms_per_step": ser_ms / nser, "cpu_baseline": cpu,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(4 * m * n),
                 "d2h_bytes_per_step": int(8 * k)},
         "gpu_launches": launches, "clocks": clk.summary(),
     }
-    print(json.dumps(res), flush=True)
+    return res
+
+
+def run_only(args, rank, A, skel, st, seed_G):
+    """One call, --warmup + --steps times, timed with CUDA events: a small command for profilers."""
+    import torch
+    k, p = args.k, args.p
+    l = k + p
+    X, _ = skel.sketch(A, l, prec=args.prec, seed=seed_G, status=st)
+    Js, _, Rf, _ = skel.pivot_lupp(X, k, status=st)
+    Is = None
+    if args.only in ("rows", "cur", "id_cur"):
+        Is, _ = skel.pivot_rows(A, Js, status=st)
+    call = {"sketch": lambda: skel.sketch(A, l, prec=args.prec, seed=seed_G, X=X, status=st),
+            "lupp": lambda: skel.pivot_lupp(X, k, status=st),
+            "rows": lambda: skel.pivot_rows(A, Js, status=st),
+            "pivots": lambda: skel.pivot_skeleton(X, A, k, status=st),
+            "id": lambda: skel.column_id(A, Js, status=st),
+            "cur": lambda: skel.cur(A, Js, Is, status=st),
+            "id_cur": lambda: skel.id_cur(A, Js, Is, status=st),
+            "eta": lambda: skel.error(A, Js, Rf=Rf, status=st),
+            "srtt": lambda: skel.sketch(A, l, kind="srtt", prec=args.prec, seed=seed_G, X=X, status=st),
+            "power": lambda: skel.sketch_power(A, l, q=1, prec=args.prec, seed=seed_G, status=st),
+            "cols": lambda: skel.sketch_cols(A, l, prec=args.prec, seed=seed_G + 1, status=st)}[args.only]
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = _events(2)
+    e0.record()
+    for _ in range(args.steps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    skel.check_status(st, args.only)
+    if rank == 0:
+        print(json.dumps({"only": args.only, "ms": e0.elapsed_time(e1) / args.steps,
+                          "config": workload_config(args.workload, k, p, args.prec)}), flush=True)
 
 
 def run_next(args, rank, A, skel, st, seed_G):
@@ -462,21 +771,22 @@ def run_next(args, rank, A, skel, st, seed_G):
     X = Omega (A^T A) (a transposed copy of A, then one pass over each), the column sketch
     Y^T = Omega A^T (tensor cores on the transposed copy),
     streaming selection (row and column sketches + two LUPPs), the column ID from the sketch
-    (Z = R_1^{-1} R) and the CUR core from the skeletons (U = A(Is, Js)^{-1})."""
+    (Z = X(:, J)^+ X) and the CUR core from the skeletons (U = A(Is, Js)^{-1})."""
     import torch
     k, p = args.k, args.p
     l = k + p
     m, n = A.shape
-    X, _ = skel.sketch(A, l, prec=args.prec, seed=seed_G, status=st)
+    prec = "tf32" if args.prec not in ("tf32", "bf16") else args.prec
+    X, _ = skel.sketch(A, l, prec=prec, seed=seed_G, status=st)
     Js, _, Rf, _ = skel.pivot_lupp(X, k, status=st)
     Is, _ = skel.pivot_rows(A, Js, status=st)
     calls = {
-        "srtt_sketch": (lambda: skel.sketch(A, l, kind="srtt", prec=args.prec, seed=seed_G, X=X, status=st), 1),
-        "power_sketch_q1": (lambda: skel.sketch_power(A, l, q=1, prec=args.prec, seed=seed_G, status=st), 2),
-        "col_sketch": (lambda: skel.sketch_cols(A, l, prec=args.prec, seed=seed_G + 1, status=st), 1),
+        "srtt_sketch": (lambda: skel.sketch(A, l, kind="srtt", prec=prec, seed=seed_G, X=X, status=st), 1),
+        "power_sketch_q1": (lambda: skel.sketch_power(A, l, q=1, prec=prec, seed=seed_G, status=st), 2),
+        "col_sketch": (lambda: skel.sketch_cols(A, l, prec=prec, seed=seed_G + 1, status=st), 1),
         "streaming_selection": (lambda: skel.skeletonize_streaming(A, k, p, seed=seed_G, seed_omega=seed_G + 1,
-                                                                   prec=args.prec, status=st), 2),
-        "id_from_sketch": (lambda: skel.column_id_sketch(Rf, Js, status=st), 0),
+                                                                   prec=prec, status=st), 2),
+        "id_from_sketch": (lambda: skel.column_id_sketch(X, Js, status=st), 0),
         "cur_core_from_skeletons": (lambda: skel.cur_sketch(A, Js, Is, status=st), 0),
     }
     out = {}
@@ -484,7 +794,7 @@ def run_next(args, rank, A, skel, st, seed_G):
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = _events(2)
         e0.record()
         for _ in range(args.steps):
             fn()
@@ -503,7 +813,7 @@ def run_next(args, rank, A, skel, st, seed_G):
             ent["frac_of_hbm"] = ent["a_gbs"] / hbm
     if rank == 0:
         print(json.dumps({"only": "next", "rows": out, "hbm_peak_gbs": hbm, "peak_source": src,
-                          "config": workload_config(k, p, args.prec)}), flush=True)
+                          "config": workload_config(args.workload, k, p, prec)}), flush=True)
 
 
 def run_batch(args, rank, dev, skel, workloads):
@@ -519,7 +829,7 @@ def run_batch(args, rank, dev, skel, workloads):
     for _ in range(args.warmup):
         Js, ranks, Z, st = plan.run()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = _events(2)
     e0.record()
     for _ in range(args.steps):
         Js, ranks, Z, st = plan.run()
@@ -530,11 +840,13 @@ def run_batch(args, rank, dev, skel, workloads):
     skel.kernel_timing(True)
     plan.run()
     torch.cuda.synchronize()
-    kern = {nm: skel.kernel_time(nm)[0] for nm in ("batch_sketch", "batch_lupp")}
+    kern = {nm: skel.kernel_time(nm)[0] for nm in ("batch_sketch", "batch_lupp", "batch_z")}
     skel.kernel_timing(False)
     r = ranks.float()
+    hbm, _, src = load_peaks()
     if rank == 0:
         print(json.dumps({"only": "batch", "ms": ms, "a_bytes": a_bytes, "a_streaming_gbs": a_bytes / (ms * 1e-3) / 1e9,
+                          "frac_of_hbm": a_bytes / (ms * 1e-3) / 1e9 / hbm,
                           "kernel_ms": kern, "rank_mean": float(r.mean()), "rank_max": int(r.max()),
                           "plan": plan.info,
                           "config": {"workload": f"{nblocks} Gaussian-kernel blocks m_b~U[64,1024] n_b~U[64,512] fp32, "

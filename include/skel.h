@@ -7,8 +7,10 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  *  - Every matrix pointer is a DEVICE pointer owned by the caller; the library never frees
- *    or retains it.  The library never allocates memory: each call that needs scratch memory
- *    takes a caller-provided device workspace `ws` of `*ws_bytes` bytes.  Calling with
+ *    or retains it.  Only skel_batch_plan_create allocates device memory (the plan's own, freed
+ *    by skel_batch_plan_destroy); every other call that needs scratch memory takes a
+ *    caller-provided device workspace `ws` of `*ws_bytes` bytes (skel_pivot_lupp_static uses a
+ *    fixed array inside the library instead).  Calling with
  *    ws == NULL writes the required size to *ws_bytes and returns SKEL_OK without launching
  *    anything.  A workspace smaller than required returns SKEL_ERR_WORKSPACE.  Workspace
  *    must be 256-byte aligned.
@@ -188,19 +190,27 @@ skel_status skel_pivot_lupp(skel_dtype dtype, const void* X, int64_t l, int64_t 
                             cudaStream_t stream);
 
 /*
- * skel_pivot_lupp_static -- the same computation and outputs as skel_pivot_lupp, for callers
- * that cannot allocate device memory.  Some programs must not allocate: a host that hands out
- * all device memory from its own fixed pool and forbids allocations after start-up, or a loop
- * with a hard latency budget where cudaMalloc's implicit synchronisation of the whole device
- * is not acceptable.  Such a caller passes only X and the outputs; this entry point allocates
- * nothing.  (The paper has no counterpart; this is an interface choice of this library.)
+ * skel_pivot_lupp_static -- the LUPP of skel_pivot_lupp (same arguments, same outputs) for
+ * callers that cannot allocate device memory.  Some programs must not allocate: a host that
+ * hands out all device memory from its own fixed pool and forbids allocations after start-up,
+ * or a loop with a hard latency budget where cudaMalloc's implicit synchronisation of the
+ * whole device is not acceptable.  Such a caller passes only X and the outputs; this entry
+ * point allocates nothing.  (The paper has no counterpart; this is an interface choice of
+ * this library.)
+ *   Kernel: always the persistent grid-barrier LUPP kernel (skel_pivot_lupp picks the
+ *   cluster panel kernel when a panel fits a thread-block cluster).  Both kernels apply, to
+ *   every entry, the textbook operations of the LUPP step in the textbook order with
+ *   separately rounded divide, multiply and subtract, so Js, L and R are bitwise equal to
+ *   skel_pivot_lupp's; the two differ in speed only.
  *   Scratch: a fixed 8 MiB array in the library's device image, held by every device that
- *   loads the library until the process exits.  A problem whose scratch need (the workspace
- *   skel_pivot_lupp would ask for) exceeds 8 MiB returns SKEL_ERR_WORKSPACE with nothing
+ *   loads the library until the process exits.  A problem whose scratch need exceeds 8 MiB
+ *   (e.g. FP64 with l = s = n = 996; 992 still fits) returns SKEL_ERR_WORKSPACE with nothing
  *   launched.
- *   Set-up: the first call on a device, with that device current, looks up the array's device
- *   address (cudaGetSymbolAddress) and caches it; make that first call before any stream
- *   capture.  Later calls do no set-up.
+ *   Set-up: the first call in a CUDA context, with that context current, looks up the array's
+ *   device address (cudaGetSymbolAddress) and caches it under the context's unique id; make
+ *   that first call before any stream capture.  Later calls in the same context do no set-up.
+ *   After cudaDeviceReset (the array may move when the library's module is loaded again) or
+ *   from another context, the next call finds no cached address and looks it up again.
  *   Sharing: every call on a device uses the same array and each call leaves its contents
  *   behind; a call clears what must start at zero itself.  Calls that overlap on the GPU
  *   (different streams, or host threads, without ordering between them) race on the array
@@ -325,14 +335,20 @@ skel_status skel_cur_sketch(int64_t m, int64_t n, skel_dtype dtype, const void* 
 
 /*
  * skel_id_sketch -- column ID coefficients from the sketch alone, without a second pass over
- * A (Sec. 4: C^+ A ~ X_1^+ X with X_1 = X(:, J_s)), taken on the first s rows of X, whose
- * greedy pivots are J_s: Z = X(0:s, J)^{-1} X(0:s, :) = R_1^{-1} R with R the s x n LUPP factor
- * of skel_pivot_lupp (row-major, ldr >= n, dtype FP32 or FP64) and R_1 = R(:, J) its unit upper
- * triangular pivot columns.  Z: s x n row-major FP64 (ldz >= n), Z(:, J) = I.  Workspace
- * 8 s^2 bytes (handshake as elsewhere).  Less accurate than skel_id (the sketch's precision
- * and conditioning enter Z); A is not read.
+ * A (Sec. 4: C^+ A ~ X_1^+ X with X_1 = X(:, J_s)), the pseudo-inverse taken over all l rows of
+ * the sketch:
+ *     Z = X(:, J)^+ X = argmin_Z ||X(:, J) Z - X||_F = argmin_Z ||Gamma (C Z - A)||_F,
+ * the sketched least-squares problem for C^+ A (with l = s it is X(:, J)^{-1} X).  Formed as
+ * X(:, J) = Q R_1 (Householder QR, the dtype's precision), W = Q^T X, Z = R_1^{-1} W (FP64
+ * solve), then Z(:, J) = I exactly.
+ *   X, l, n, ldx : the sketch, l x n row-major (ldx >= n), dtype FP32 or FP64.
+ *   s, Js        : int32[s] distinct column indices (device), s <= l, s <= min(n, 1024).
+ *   Z, ldz       : out, s x n row-major FP64 (ldz >= n).
+ * Workspace (handshake).  Less accurate than skel_id (the sketch's precision and the
+ * embedding's distortion enter Z); A is not read.  A rank-deficient X(:, J) gives a non-finite
+ * Z (SKEL_ERR_NONFINITE from the solve's checks).
  */
-skel_status skel_id_sketch(skel_dtype dtype, int32_t s, int64_t n, const void* R, int64_t ldr,
+skel_status skel_id_sketch(skel_dtype dtype, const void* X, int64_t l, int64_t n, int64_t ldx, int32_t s,
                            const int32_t* Js, double* Z, int64_t ldz, void* ws, size_t* ws_bytes,
                            int32_t* dev_status, cudaStream_t stream);
 
@@ -344,7 +360,8 @@ skel_status skel_id_sketch(skel_dtype dtype, int32_t s, int64_t n, const void* R
  * on X_b (Sec. 2.5.2) stopped at the smallest t <= kmax with
  *     ||S_t||_F^2 l/(l - t) <= tol^2 ||X_b||_F^2     (S_t: Schur complement after t steps)
  * (or at kmax, or at a zero pivot); and the column ID coefficients from the sketch alone,
- *     Z_b = X_b(0:r, J)^{-1} X_b(0:r, :)       (C^+ A ~ X_1^+ X, Sec. 4, no second pass over A).
+ *     Z_b = X_b(:, J)^+ X_b = argmin_Z ||X_b(:, J) Z - X_b||_F   (C^+ A ~ X_1^+ X, Sec. 4, no second
+ * pass over A; the pseudo-inverse over all l rows, by an FP32 Householder QR of X_b(:, J)).
  * A is read once.
  *
  * skel_batch_plan_create -- m, n, A, lda: host arrays of nblocks block descriptors (A[b] a
@@ -354,7 +371,7 @@ skel_status skel_id_sketch(skel_dtype dtype, int32_t s, int64_t n, const void* R
  *   maps, work lists, the Gamma halves (2 (kmax+p) max(m_b) floats) and the sketches
  *   (sum_b (kmax+p) n_b floats).  Allocates and copies synchronously; no other call does.
  *   SKEL_ERR_UNSUPPORTED when a block is wider than four CTAs' shared memory hold
- *   ((kmax+p) n_b / 4 floats per CTA plus kmax^2) or is not TMA-addressable.
+ *   ((kmax+p) n_b / 4 floats per CTA) or is not TMA-addressable.
  *   flags: SKEL_BATCH_AUTOTUNE times, on the plan's own blocks, every sketch pipeline depth
  *   that fits and the LUPP cluster classes run one after another or concurrently (one
  *   warm-up and two timed runs each, synchronously, inside this call) and keeps the fastest;
@@ -425,7 +442,7 @@ skel_status skel_debug_grid_timeout(int grid, uint64_t wait_ns, void* ws, size_t
  * of one kernel since the last skel_debug_kernel_timing call; waits for those launches.
  * Names: "sketch_tc", "sketch_fp8", "fp8_quantize", "gemm_tc" (W = Q^T A), "lupp_panel", "lupp_trail", "qr_panel", "qr_wy", "trsm",
  * "gemm_qr" (QR trailing updates and Q formation), "gemm_cur" (W Q_R), "gemm_eta_h" (R R^T),
- * "gemm_eta_sq" (eta's squarings), "gemm_simt" (other SIMT GEMMs), "batch_sketch", "batch_lupp",
+ * "gemm_eta_sq" (eta's squarings), "gemm_simt" (other SIMT GEMMs), "batch_sketch", "batch_lupp", "batch_z",
  * "transpose" (A^T for the column and power sketches on the tensor cores).
  * Host-side state, process-wide; not for concurrent use from several threads.
  */

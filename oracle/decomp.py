@@ -35,17 +35,17 @@ def cur(A, Js, Is):
 
 
 def sketch_id(X, Js):
-    """Z (r x n) of the column ID estimated from the row sketch without a second pass over A
-    (Sec. 4: C^+ A ~ X_1^+ X with X_1 = X(:, J_s)), taken on the first r = |J_s| rows of X, whose
-    greedy pivots are J_s (rows r.. never influence them):
-        Z = X(0:r, J_s)^{-1} X(0:r, :).
-    A library LU solve serves as the step."""
+    """Z (s x n) of the column ID estimated from the row sketch without a second pass over A
+    (Sec. 4: C^+ A ~ X_1^+ X with X_1 = X(:, J_s)), the pseudo-inverse taken over all l rows of
+    the sketch (l >= s = |J_s|):
+        Z = X(:, J_s)^+ X = argmin_Z ||X(:, J_s) Z - X||_F = argmin_Z ||Gamma (C Z - A)||_F,
+    the sketched least-squares problem for C^+ A.  With l = s it is the paper's X_1^{-1} X.
+    A library least-squares solve serves as the step."""
     X = np.asarray(X, dtype=np.float64)
     Js = np.asarray(Js, dtype=np.int64)
-    r = Js.size
-    if r == 0:
+    if Js.size == 0:
         return np.zeros((0, X.shape[1]))
-    return np.linalg.solve(X[:r, Js], X[:r, :])
+    return np.linalg.lstsq(X[:, Js], X, rcond=None)[0]
 
 
 def cur_sketch(A, Js, Is):

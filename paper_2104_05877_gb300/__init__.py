@@ -53,7 +53,7 @@ def lib():
         "skel_pivot_rows": [i64, i64, i32, vp, i64, i32, vp, vp, vp, szp, vp, vp],
         "skel_error": [i64, i64, i32, vp, i64, i32, vp, vp, i64, vp, vp, i64, i32, vp, i64, vp, vp,
                        szp, vp, vp],
-        "skel_id_sketch": [i32, i32, i64, vp, i64, vp, vp, i64, vp, szp, vp, vp],
+        "skel_id_sketch": [i32, vp, i64, i64, i64, i32, vp, vp, i64, vp, szp, vp, vp],
         "skel_cur_sketch": [i64, i64, i32, vp, i64, i32, vp, vp, vp, i64, vp, szp, vp, vp],
         "skel_id_cur": [i64, i64, i32, vp, i64, i32, vp, vp, vp, i64, vp, i64, vp, vp, vp, szp, vp, vp],
         "skel_pivot_skeleton": [i32, vp, i64, i64, i64, i32, vp, i64, i64, vp, vp, vp, i64, vp, i64, vp, szp, vp,
@@ -312,15 +312,16 @@ def column_id(A, Js, status=None):
     return Z, sq, st
 
 
-def column_id_sketch(R, Js, status=None):
-    """Z = R(:, Js)^{-1} R (s x n FP64) from the LUPP factor R of the sketch: the column ID
-    formed from the sketch alone (no pass over A)."""
-    R, ldr = _rowmajor(R)
-    s, n = R.shape
-    Z = torch.empty(s, n, dtype=torch.float64, device=R.device)
-    st = status if status is not None else new_status(R.device)
-    _call("skel_id_sketch", lambda w, sz: [_dt(R), s, n, _ptr(R), ldr, _ptr(Js), _ptr(Z), n, w, sz, _ptr(st),
-                                           _stream()], R.device)
+def column_id_sketch(X, Js, status=None):
+    """Z = X(:, Js)^+ X (s x n FP64): the column ID from the sketch alone (no pass over A), the
+    least-squares solution over all l rows of the sketch X (l x n row-major)."""
+    X, ldx = _rowmajor(X)
+    l, n = X.shape
+    s = Js.numel()
+    Z = torch.empty(s, n, dtype=torch.float64, device=X.device)
+    st = status if status is not None else new_status(X.device)
+    _call("skel_id_sketch", lambda w, sz: [_dt(X), _ptr(X), l, n, ldx, s, _ptr(Js), _ptr(Z), n, w, sz, _ptr(st),
+                                           _stream()], X.device)
     return Z, st
 
 
@@ -487,7 +488,7 @@ def skeletonize(A, k, p=10, seed=0, prec="f32", pivot="lupp", kind="gaussian", z
 class BatchPlan:
     """Batched skeletonization of independent FP32 blocks (skel_batch_*): per block the sketch
     with l = kmax + p rows, LUPP stopped at the tolerance-driven rank, and the column ID
-    coefficients Z_b = X_b(0:r, J)^{-1} X_b(0:r, :).  `blocks`: CUDA float32 tensors (m_b x n_b,
+    coefficients Z_b = X_b(:, J)^+ X_b (least squares over all l rows of the sketch).  `blocks`: CUDA float32 tensors (m_b x n_b,
     column-major views, kept alive by the plan)."""
 
     def __init__(self, blocks, kmax, p=16, tol=1e-6, seed=0, graph=False, autotune=False):

@@ -708,20 +708,43 @@ skel_status skel_cur_sketch(int64_t m, int64_t n, skel_dtype dtype, const void* 
   return SKEL_OK;
 }
 
-skel_status skel_id_sketch(skel_dtype dtype, int32_t s, int64_t n, const void* R, int64_t ldr,
+skel_status skel_id_sketch(skel_dtype dtype, const void* X, int64_t l, int64_t n, int64_t ldx, int32_t s,
                            const int32_t* Js, double* Z, int64_t ldz, void* ws, size_t* ws_bytes,
                            int32_t* dev_status, cudaStream_t stream) {
-  (void)dev_status;
-  if (!valid_dtype(dtype) || s < 1 || s > kMaxS || n < s || R == nullptr || Js == nullptr || Z == nullptr ||
-      ldr < n || ldz < n)
+  if (!valid_dtype(dtype) || X == nullptr || Js == nullptr || Z == nullptr || s < 1 || s > kMaxS || l < s ||
+      l > 4096 || n < s || n > (int64_t)INT32_MAX || ldx < n || ldz < n)
     return SKEL_ERR_INVALID_ARG;
-  Arena ar(ws);
-  double* R1 = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
-  skel_status st;
-  if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
-  SK_CUDA(launch_gather_cols_rowmajor_f64(s, dtype, R, ldr, n, Js, R1, s, stream));   // R1(r, t) = R(r, j_t)
-  SK_CUDA(launch_trsm_upper(s, n, R1, s, 1, dtype, R, ldr, Z, ldz, stream));        // Z = R1^{-1} R
-  SK_CUDA(launch_unit_columns(s, Js, Z, ldz, stream));                              // Z(:, J) = I exactly
+  const bool f64 = dtype == SKEL_F64;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool run = pass == 1;
+    Arena ar(run ? ws : nullptr);
+    void* X1 = ar.take(esize(dtype) * (size_t)l * s);
+    void* Q = ar.take(esize(dtype) * (size_t)l * s);
+    double* R1 = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));
+    const size_t qn = qr_workspace(dtype, l, s);
+    void* qws = ar.take(qn);
+    void* W = ar.take(esize(dtype) * (size_t)s * n);
+    void* kws = ar.take(gemm_workspace(s, n, l, f64));
+    if (!run) {
+      skel_status st;
+      if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+      continue;
+    }
+    // X1 = X(:, J) as an l x s column-major matrix: the row gather of X^T (n x l column-major)
+    SK_CUDA(launch_gather_rows_t(l, s, dtype, X, ldx, n, Js, X1, l, stream));
+    SK_TRY(run_qr(dtype, X1, l, l, s, Q, l, R1, s, qws, qn, dev_status, stream));     // X1 = Q R1
+    GemmArgs g{};
+    g.splitk_ws = kws;
+    g.M = s; g.N = n; g.K = l;
+    g.L = View{Q, l, 1}; g.l_dt = dtype;          // Q^T(t, r) = Q(r, t)
+    g.B = View{X, ldx, 1}; g.b_dt = dtype;        // X(r, j), row-major
+    g.out = W; g.out_sr = n; g.out_sc = 1; g.out_dt = dtype;
+    g.alpha = 1.0;
+    g.dev_status = dev_status;
+    SK_CUDA(launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, stream));                        // W = Q^T X
+    SK_CUDA(launch_trsm_upper(s, n, R1, s, 0, dtype, W, n, Z, ldz, stream));           // Z = R1^{-1} W
+    SK_CUDA(launch_unit_columns(s, Js, Z, ldz, stream));                               // Z(:, J) = I exactly
+  }
   return SKEL_OK;
 }
 

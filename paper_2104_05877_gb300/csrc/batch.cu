@@ -1,10 +1,10 @@
 // Batched skeletonization of many independent blocks (hierarchical-matrix compression): per
 // block A_b (m_b x n_b, FP32, column-major) the Gaussian sketch X_b = Gamma A_b (Algorithm 2
 // line 2), column LUPP on X_b (Sec. 2.5.2, Algorithm 2 line 3) stopped at the tolerance-driven
-// rank, and the column ID coefficients formed from the sketch alone: with r pivots,
-//   Z_b = X_b(0:r, J)^{-1} X_b(0:r, :) = R_1^{-1} R      (C^+ A ~ X_1^+ X, Sec. 4, ID without a
-// second pass over A), where R is the LUPP factor (r x n_b) and R_1 = R(:, J) is unit upper
-// triangular.  A is read once.
+// rank r, and the column ID coefficients formed from the sketch alone (C^+ A ~ X_1^+ X, Sec. 4,
+// ID without a second pass over A), the pseudo-inverse over all l rows of the sketch:
+//   Z_b = X_b(:, J)^+ X_b = argmin_Z ||X_b(:, J) Z - X_b||_F.
+// A is read once.
 //
 // Kernels, all launched by skel_batch_run on the caller's stream:
 //   batch_gamma_kernel   the standard normals G (l x m_max, one Gamma for every block: the
@@ -22,8 +22,10 @@
 //                        sum of squares of its rows below the step to every CTA through
 //                        distributed shared memory, one cluster barrier, then every CTA
 //                        takes the same decision (stop at the tolerance rank, or the pivot)
-//                        and updates its columns.  R_1 is collected from the winners' columns
-//                        and Z is formed by back substitution in place.
+//                        and updates its columns.  Writes J and the rank.
+//   batch_lsq_kernel     one CTA per block: Householder QR of X_b(:, J) (l x r) in shared
+//                        memory, Q^T applied to X_b in chunks of columns, back substitution
+//                        with R; Z_b(:, J) = I exactly.
 // The tolerance rule (the paper fixes k): the rank is the smallest t <= k_max with
 //   ||S_t||_F^2 l/(l - t) <= tol^2 ||X||_F^2,
 // S_t the Schur complement (rows t..l-1) after t steps, an unbiased estimate of
@@ -289,7 +291,6 @@ struct BatchLuppParams {
   float tol2;
   int32_t* Js;            // nblocks x kmax
   int32_t* ranks;
-  double* Z;
   int32_t* dev_status;
 };
 
@@ -313,7 +314,6 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ BlSlot slot[2][BL_MAXCL];
   __shared__ int s_J[BL_MAXK];
-  __shared__ float s_piv[BL_MAXK];
   __shared__ float wkey[BL_THREADS / 32];
   __shared__ int widx[BL_THREADS / 32];
   __shared__ float wnu[BL_THREADS / 32];
@@ -330,8 +330,7 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
   const int nl = max(0, min(ncl, n - c0));
   const int ldp = bl_ldp(ncl);
   float* S = reinterpret_cast<float*>(smem);                 // [l][ldp]
-  float* R1 = S + (size_t)l * ldp;                            // [kmax][kmax], R1[q][t] = R(q, j_t)
-  unsigned char* sel = reinterpret_cast<unsigned char*>(R1 + (size_t)kmax * kmax);   // [ncl]
+  unsigned char* sel = reinterpret_cast<unsigned char*>(S + (size_t)l * ldp);        // [ncl]
   const float* xb = p.X + blk.xoff;
 
   auto block_sum = [&](float v) {            // in fixed order; result in s_nu
@@ -423,8 +422,7 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
     }
     const float* pc = slot[par][o].col;
     const float piv = pc[t];
-    if (tid == 0) { s_J[t] = bi; s_piv[t] = piv; }
-    for (int q = tid; q < t; q += BL_THREADS) R1[q * kmax + t] = pc[q] / s_piv[q];
+    if (tid == 0) s_J[t] = bi;
     // rows t+1 .. l-1 of the local columns: S(r, j) -= S(r, j_t) S(t, j) / pivot
     float nuloc = 0.f;
     if (nl > 0) {
@@ -457,28 +455,6 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
     if (o == crank && tid == 0) sel[bi - c0] = 1;
     __syncthreads();
   }
-  // R rows, then Z = R_1^{-1} R by back substitution, in place (local columns)
-  for (int jl = tid; jl < nl; jl += BL_THREADS) {
-    if (sel[jl]) continue;
-    for (int q = 0; q < rank; ++q) S[q * ldp + jl] = S[q * ldp + jl] / s_piv[q];
-    for (int q = rank - 1; q >= 0; --q) {
-      float z = S[q * ldp + jl];
-      for (int q2 = q + 1; q2 < rank; ++q2) z = __fsub_rn(z, __fmul_rn(R1[q * kmax + q2], S[q2 * ldp + jl]));
-      S[q * ldp + jl] = z;
-    }
-  }
-  __syncthreads();
-  for (int q = 0; q < rank; ++q) {                    // selected columns: unit vectors
-    const int j = s_J[q];
-    if (j >= c0 && j < c0 + nl)
-      for (int q2 = tid; q2 < rank; q2 += BL_THREADS) S[q2 * ldp + (j - c0)] = q2 == q ? 1.f : 0.f;
-  }
-  __syncthreads();
-  double* zb = p.Z + blk.zoff;                       // rows >= rank are left untouched
-  for (int e = tid; e < rank * nl; e += BL_THREADS) {
-    const int q = e / nl, jl = e % nl;
-    zb[(int64_t)q * n + c0 + jl] = (double)S[q * ldp + jl];
-  }
   if (crank == 0) {
     for (int q = tid; q < kmax; q += BL_THREADS) p.Js[(int64_t)b * kmax + q] = q < rank ? s_J[q] : -1;
     if (tid == 0) {
@@ -489,8 +465,165 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
 }
 
 size_t lupp_smem(int l, int kmax, int ncl) {
+  (void)kmax;
   const int ldp = (ncl & 1) ? ncl : ncl + 1;
-  return sizeof(float) * ((size_t)l * ldp + (size_t)kmax * kmax) + (size_t)ncl;
+  return sizeof(float) * (size_t)l * ldp + (size_t)ncl;
+}
+
+// ---------------------------------------------------------------------------------------
+// Z_b = X_b(:, J)^+ X_b (l x n_b sketch, r = rank_b pivots): FP32 Householder QR of the l x r
+// X_b(:, J) in shared memory (column-major, odd leading dimension), then for each chunk of
+// LS_NC columns of X_b: Q^T applied (LS_TPC threads per column, rows split by residue), and the
+// back substitution with R by one thread per column.  Z(:, J) = I is written exactly.
+constexpr int LS_THREADS = 256;
+constexpr int LS_NC = 32;                          // columns per chunk
+constexpr int LS_TPC = LS_THREADS / LS_NC;         // threads per column (a power of two <= 32)
+
+struct BatchLsqParams {
+  const BatchBlock* blocks;
+  const float* X;
+  int l, kmax;
+  const int32_t* Js;
+  const int32_t* ranks;
+  double* Z;
+  int32_t* dev_status;
+};
+
+__host__ __device__ __forceinline__ int ls_ld(int l) { return (l & 1) ? l : l + 1; }
+
+size_t lsq_smem(int l, int kmax) { return sizeof(float) * (size_t)ls_ld(l) * (kmax + LS_NC); }
+
+__global__ void __launch_bounds__(LS_THREADS) batch_lsq_kernel(const BatchLsqParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ float tau[BL_MAXK];
+  __shared__ float red[LS_THREADS / 32];
+  __shared__ float s_nrm2;
+  const int b = blockIdx.x;
+  const BatchBlock blk = p.blocks[b];
+  const int r = p.ranks[b];
+  if (r <= 0) return;
+  const int n = blk.n, l = p.l, ldv = ls_ld(l);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int32_t* J = p.Js + (int64_t)b * p.kmax;
+  const float* xb = p.X + blk.xoff;
+  double* zb = p.Z + blk.zoff;
+  float* V = reinterpret_cast<float*>(smem);             // [kmax][ldv]: column t of X(:, J), then v_t / R
+  float* Cc = V + (size_t)p.kmax * ldv;                  // [LS_NC][ldv]: a chunk of X's columns
+
+  float amax = 0.f;
+  for (int e = tid; e < l * r; e += LS_THREADS) {
+    const int t = e / l, i = e % l;
+    const int j = J[t];
+    const float x = j >= 0 && j < n ? xb[(int64_t)i * n + j] : __int_as_float(0x7fc00000);
+    V[t * ldv + i] = x;
+    amax = fmaxf(amax, fabsf(x));
+  }
+  // Z = X(:, J)^+ X does not change when X is scaled, so X is scaled by the power of two that
+  // brings max |X(:, J)| into [0.5, 1) (exact): blocks far apart in a kernel matrix have
+  // entries near 1e-28, whose squares in the reflectors' norms would underflow FP32.
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if (lane == 0) red[warp] = amax;
+  __syncthreads();
+  if (tid == 0) {
+    float a = 0.f;
+    for (int w = 0; w < LS_THREADS / 32; ++w) a = fmaxf(a, red[w]);
+    s_nrm2 = a;
+  }
+  __syncthreads();
+  int sh = 0;
+  if (s_nrm2 > 0.f && isfinite(s_nrm2)) {
+    frexpf(s_nrm2, &sh);
+    sh = -sh;
+  }
+  for (int e = tid; e < l * r; e += LS_THREADS) {
+    const int t = e / l, i = e % l;
+    V[t * ldv + i] = ldexpf(V[t * ldv + i], sh);
+  }
+  __syncthreads();
+  // Householder QR: H_t = I - tau_t v v^T with v(t) = 1, R(t, t) = beta = -sign(alpha) ||x||
+  for (int t = 0; t < r; ++t) {
+    float* v = V + t * ldv;
+    float part = 0.f;
+    for (int i = t + tid; i < l; i += LS_THREADS) part = fmaf(v[i], v[i], part);
+    part = warp_sum(part);
+    if (lane == 0) red[warp] = part;
+    __syncthreads();
+    if (tid == 0) {
+      float a = 0.f;
+      for (int w = 0; w < LS_THREADS / 32; ++w) a += red[w];
+      s_nrm2 = a;
+    }
+    __syncthreads();
+    const float nrm2 = s_nrm2, alpha = v[t];
+    const float beta = alpha >= 0.f ? -sqrtf(nrm2) : sqrtf(nrm2);
+    const bool refl = nrm2 > 0.f;
+    __syncthreads();                                     // every thread has read v[t]
+    if (refl)
+      for (int i = t + 1 + tid; i < l; i += LS_THREADS) v[i] = v[i] / (alpha - beta);
+    if (tid == 0) {
+      tau[t] = refl ? (beta - alpha) / beta : 0.f;
+      v[t] = beta;
+    }
+    __syncthreads();
+    const float tt = tau[t];
+    for (int c = t + 1 + warp; c < r; c += LS_THREADS / 32) {   // one warp per later column
+      float* x = V + c * ldv;
+      float d = lane == 0 ? x[t] : 0.f;
+      for (int i = t + 1 + lane; i < l; i += 32) d = fmaf(v[i], x[i], d);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      d *= tt;
+      if (lane == 0) x[t] -= d;
+      for (int i = t + 1 + lane; i < l; i += 32) x[i] = fmaf(-d, v[i], x[i]);
+    }
+    __syncthreads();
+  }
+  bool bad = false;
+  const int jj = tid / LS_TPC, h = tid % LS_TPC;
+  for (int c0 = 0; c0 < n; c0 += LS_NC) {
+    const int ncw = min(LS_NC, n - c0);
+    for (int e = tid; e < l * ncw; e += LS_THREADS) {
+      const int i = e / ncw, q = e % ncw;
+      Cc[q * ldv + i] = ldexpf(xb[(int64_t)i * n + c0 + q], sh);
+    }
+    __syncthreads();
+    const bool act = jj < ncw;
+    float* x = Cc + jj * ldv;
+    for (int t = 0; t < r; ++t) {                         // x <- H_t x, t = 0 .. r-1 (Q^T x)
+      const float* v = V + t * ldv;
+      const int i0 = t + ((h - t % LS_TPC) + LS_TPC) % LS_TPC;
+      float d = 0.f;
+      if (act)
+        for (int i = i0; i < l; i += LS_TPC) d = fmaf(i == t ? 1.f : v[i], x[i], d);
+#pragma unroll
+      for (int o = LS_TPC / 2; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      d *= tau[t];
+      if (act)
+        for (int i = i0; i < l; i += LS_TPC) x[i] = fmaf(-d, i == t ? 1.f : v[i], x[i]);
+    }
+    if (act && h == 0) {                                  // z = R^{-1} (Q^T x)(0:r)
+      for (int q = r - 1; q >= 0; --q) {
+        float z = x[q];
+        for (int q2 = q + 1; q2 < r; ++q2) z = fmaf(-V[q2 * ldv + q], x[q2], z);
+        z = z / V[q * ldv + q];
+        x[q] = z;
+        bad |= !isfinite(z);
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < r * ncw; e += LS_THREADS) {
+      const int q = e / ncw, c = e % ncw;
+      zb[(int64_t)q * n + c0 + c] = (double)Cc[c * ldv + q];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < r * r; e += LS_THREADS) {         // the skeleton columns: unit vectors
+    const int q = e / r, t = e % r;
+    const int j = J[t];
+    if (j >= 0 && j < n) zb[(int64_t)q * n + j] = q == t ? 1.0 : 0.0;
+  }
+  if (bad) record_error(p.dev_status, SKEL_ERR_NONFINITE, b);
 }
 
 }  // namespace
@@ -598,7 +731,6 @@ skel_status enqueue_run(skel_batch_plan* pl, int32_t* Js, int32_t* ranks, double
   lp.tol2 = (float)(pl->tol * pl->tol);
   lp.Js = Js;
   lp.ranks = ranks;
-  lp.Z = Z;
   lp.dev_status = dev_status;
   const bool fork = pl->concurrent && (pl->cls_count[1] > 0 || pl->cls_count[2] > 0);
   if (fork) {
@@ -644,6 +776,21 @@ skel_status enqueue_run(skel_batch_plan* pl, int32_t* Js, int32_t* ranks, double
     }
   }
   if (!join()) return SKEL_ERR_CUDA;
+  BatchLsqParams zp{};
+  zp.blocks = pl->d_blocks;
+  zp.X = pl->d_X;
+  zp.l = pl->l;
+  zp.kmax = pl->kmax;
+  zp.Js = Js;
+  zp.ranks = ranks;
+  zp.Z = Z;
+  zp.dev_status = dev_status;
+  {
+    KernelTimer kt(timers ? "batch_z" : nullptr, st);
+    batch_lsq_kernel<<<pl->nb, LS_THREADS, lsq_smem(pl->l, pl->kmax), st>>>(zp);
+  }
+  ++nl;
+  if (cudaGetLastError() != cudaSuccess) return SKEL_ERR_CUDA;
   if (launches) *launches = nl;
   return SKEL_OK;
 }
@@ -806,7 +953,9 @@ skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int6
   }
   ok = ok && cudaFuncSetAttribute(batch_sketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sketch_smem_for(lp, pl->max_stages)) == cudaSuccess &&
-       cudaFuncSetAttribute(batch_lupp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget) == cudaSuccess;
+       cudaFuncSetAttribute(batch_lupp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget) == cudaSuccess &&
+       cudaFuncSetAttribute(batch_lsq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsq_smem(l, kmax)) ==
+           cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking) == cudaSuccess &&
        cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) == cudaSuccess;
   for (int i = 0; ok && i < 2; ++i)

@@ -339,6 +339,11 @@ size_t gemm_tc_workspace(int64_t m, int64_t n, int32_t s) {
          (pl.P > 1 ? align_up(sizeof(float) * (size_t)pl.P * s * n) : 0);
 }
 
+size_t gemm_tc_workspace_bound(int64_t m, int64_t nmax, int32_t s) {
+  // the K-split never exceeds 64 partial buffers (plan_gt)
+  return 2 * align_up(sizeof(float) * (size_t)split_ld(m) * s) + align_up(sizeof(float) * (size_t)64 * s * nmax);
+}
+
 int64_t gemm_tc_num_partials(int64_t m, int64_t n, int32_t s) {
   const GtPlan pl = plan_gt(m, n, s);
   return pl.P > 1 ? (int64_t)s * ((n + GT_RED_COLS - 1) / GT_RED_COLS) : (int64_t)pl.mblocks * pl.jtiles;
@@ -346,7 +351,7 @@ int64_t gemm_tc_num_partials(int64_t m, int64_t n, int32_t s) {
 
 cudaError_t launch_gemm_tc_tn(int64_t m, int64_t n, int32_t s, const float* Q, int64_t ldq, const float* A,
                               int64_t lda, float* W, int64_t ldw, double* sq_partials, void* ws,
-                              int32_t* dev_status, cudaStream_t st) {
+                              int32_t* dev_status, cudaStream_t st, const char* timer) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   const GtPlan pl = plan_gt(m, n, s);
@@ -394,7 +399,7 @@ cudaError_t launch_gemm_tc_tn(int64_t m, int64_t n, int32_t s, const float* Q, i
   if (e != cudaSuccess) return e;
   dim3 grid(pl.mblocks, pl.jtiles, pl.P);
   {
-    KernelTimer kt("gemm_tc", st);
+    KernelTimer kt(timer, st);
     gemm_tn_tf32x3_kernel<<<grid, GT_THREADS, GT_SMEM, st>>>(tA, tQh, tQl, p);
   }
   note_launches(1);

@@ -47,6 +47,11 @@ int64_t gemm_num_blocks(int64_t M, int64_t N);
 // STORE_SQ epilogues with a loaded left operand); 0 when no split is used.
 size_t gemm_workspace(int64_t M, int64_t N, int64_t K, bool f64);
 cudaError_t launch_gemm(const GemmArgs& a, bool f64, GemmLeft left, GemmEpi epi, cudaStream_t st);
+// C += alpha A B for FP32 with 1 <= K <= 64: A (M x K) column-major, B (K x N) row-major, C
+// (M x N) column-major (gemm_update.cu); `timer` names the launch for kernel timing.
+cudaError_t launch_rank_update_f32(int64_t M, int64_t N, int K, const float* A, int64_t lda, const float* B,
+                                   int64_t ldb, float* C, int64_t ldc, float alpha, const char* timer,
+                                   cudaStream_t st);
 
 // H = R R^T (s x s FP64, row-major ldh) for an FP32 s x n row-major R, float-float accumulation
 // (~44 bits) on the FP32 pipes; workspace syrk_ff_workspace(s, n) bytes.
@@ -156,10 +161,12 @@ skel_status run_qr_panels(skel_dtype dt, const void* C, int64_t m, int64_t ldc, 
 // partial sums of W^2 in a fixed order.
 bool gemm_tc_usable(int64_t m, int64_t n, int32_t s, const void* Q, int64_t ldq, const void* A, int64_t lda);
 size_t gemm_tc_workspace(int64_t m, int64_t n, int32_t s);
+// An upper bound of gemm_tc_workspace(m', n', s) over every m' <= m and n' <= nmax.
+size_t gemm_tc_workspace_bound(int64_t m, int64_t nmax, int32_t s);
 int64_t gemm_tc_num_partials(int64_t m, int64_t n, int32_t s);
 cudaError_t launch_gemm_tc_tn(int64_t m, int64_t n, int32_t s, const float* Q, int64_t ldq, const float* A,
                               int64_t lda, float* W, int64_t ldw, double* sq_partials, void* ws,
-                              int32_t* dev_status, cudaStream_t st);
+                              int32_t* dev_status, cudaStream_t st, const char* timer = "gemm_tc");
 size_t qr_workspace(skel_dtype dt, int64_t m, int32_t s);
 skel_status run_qr(skel_dtype dt, const void* C, int64_t m, int64_t ldc, int32_t s, void* Q,
                    int64_t ldq, double* R, int64_t ldr, void* ws, size_t ws_bytes,

@@ -557,11 +557,21 @@ QrPanelPlan plan_qr_panels(int64_t m, int s) {
 
 // workspace: fail word, Cw (m x s), VTN (m x s), VT (m x kQrMaxB), W (kQrMaxB x s), G (kQrMaxB^2),
 // split-K scratch
+// Tensor-core scratch of the FP32 panel products V_p^T (.) (3xTF32, gemm_tc.cu): for every
+// panel start and the three widths used (V_p, the trailing columns, Q's s columns).
+size_t qr_tc_ws(int64_t m, int s) { return gemm_tc_workspace_bound(m, std::max(s, kQrMaxB), kQrMaxB); }
+
+// The FP32 panel products run on the tensor cores when every tile is TMA-addressable: Cw and
+// V have leading dimension m, Q has ldq (rows t0.. start 16-byte aligned when these are
+// multiples of 4; panel starts are multiples of 8).
+bool qr_tc_ok(int64_t m, int64_t ldq) { return m % 4 == 0 && ldq % 4 == 0 && gemm_tc_usable(m, 1, 1, nullptr, m, nullptr, m); }
+
 template <typename T>
 size_t qr_panels_ws(int64_t m, int s) {
   const bool f64 = sizeof(T) == 8;
   size_t kws = 0;                     // split-K scratch of W = V_p^T C(t0:, t0+b:), any width
   for (int ntr = 1; ntr <= s; ++ntr) kws = std::max(kws, gemm_workspace(kQrMaxB, ntr, m, f64));
+  if (!f64 && m % 4 == 0) kws = std::max(kws, qr_tc_ws(m, s));
   return 256 + 2 * align_up(sizeof(T) * (size_t)m * s) + align_up(sizeof(T) * (size_t)m * kQrMaxB) +
          align_up(sizeof(T) * (size_t)kQrMaxB * s) + align_up(sizeof(T) * kQrMaxB * kQrMaxB) + kws;
 }
@@ -604,6 +614,8 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
       cudaFuncSetAttribute(qr_panel_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
     return SKEL_ERR_CUDA;
   const skel_dtype dt = f64 ? SKEL_F64 : SKEL_F32;
+  const bool tc = !f64 && qr_tc_ok(m, Q ? ldq : m) && (reinterpret_cast<uintptr_t>(Q) & 15) == 0 &&
+                  (reinterpret_cast<uintptr_t>(V) & 15) == 0 && ldv % 4 == 0;
   QrPanelParams<T> p{};
   p.Cw = Cw; p.m = m; p.ldw = m; p.s = s; p.mloc = pl.mloc;
   p.V = V; p.ldv = ldv; p.VT = VT; p.VTN = VTN; p.R = R; p.ldr = ldr; p.fail = fail; p.dev_status = dev_status;
@@ -628,15 +640,23 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
     }
     // G = V_p^T V_p, then V_p T_p^T and V_p T_p over the rows t0..
     {
-      GemmArgs g{};
-      g.M = p.b; g.N = p.b; g.K = m - t0;
-      g.L = View{V + t0 + (int64_t)t0 * ldv, ldv, 1}; g.l_dt = dt;
-      g.B = View{V + t0 + (int64_t)t0 * ldv, 1, ldv}; g.b_dt = dt;
-      g.out = Gp; g.out_sr = p.b; g.out_sc = 1; g.out_dt = dt;
-      g.alpha = 1.0;
-      g.splitk_ws = kws;
-      g.timer = "gemm_qr";
-      if (launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, st) != cudaSuccess) return SKEL_ERR_CUDA;
+      const T* Vp = V + t0 + (int64_t)t0 * ldv;
+      if (tc) {
+        if (launch_gemm_tc_tn(m - t0, p.b, p.b, reinterpret_cast<const float*>(Vp), ldv,
+                              reinterpret_cast<const float*>(Vp), ldv, reinterpret_cast<float*>(Gp), p.b, nullptr, kws,
+                              dev_status, st, "gemm_qr") != cudaSuccess)
+          return SKEL_ERR_CUDA;
+      } else {
+        GemmArgs g{};
+        g.M = p.b; g.N = p.b; g.K = m - t0;
+        g.L = View{Vp, ldv, 1}; g.l_dt = dt;
+        g.B = View{Vp, 1, ldv}; g.b_dt = dt;
+        g.out = Gp; g.out_sr = p.b; g.out_sc = 1; g.out_dt = dt;
+        g.alpha = 1.0;
+        g.splitk_ws = kws;
+        g.timer = "gemm_qr";
+        if (launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, st) != cudaSuccess) return SKEL_ERR_CUDA;
+      }
       const size_t wsm = qr_wy_smem<T>(p.b);
       if (cudaFuncSetAttribute(qr_wy_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm) != cudaSuccess)
         return SKEL_ERR_CUDA;
@@ -649,10 +669,23 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
     const int ntr = s - t0 - p.b;
     if (ntr <= 0) continue;
     // W = V_p^T C(t0:, t0+b:)  (b x ntr, row-major)
+    T* Crest = Cw + t0 + (int64_t)(t0 + p.b) * m;
+    if (tc) {
+      if (launch_gemm_tc_tn(m - t0, ntr, p.b, reinterpret_cast<const float*>(V + t0 + (int64_t)t0 * ldv), ldv,
+                            reinterpret_cast<const float*>(Crest), m, reinterpret_cast<float*>(Wt), ntr, nullptr, kws,
+                            dev_status, st, "gemm_qr") != cudaSuccess)
+        return SKEL_ERR_CUDA;
+      // C(t0:, t0+b:) -= (V_p T_p^T) W
+      if (launch_rank_update_f32(m - t0, ntr, p.b, reinterpret_cast<const float*>(VT + t0), m,
+                                 reinterpret_cast<const float*>(Wt), ntr, reinterpret_cast<float*>(Crest), m, -1.0f,
+                                 "gemm_qr", st) != cudaSuccess)
+        return SKEL_ERR_CUDA;
+      continue;
+    }
     GemmArgs g{};
     g.M = p.b; g.N = ntr; g.K = m - t0;
     g.L = View{V + t0 + (int64_t)t0 * ldv, ldv, 1}; g.l_dt = dt;      // V_p^T(r, k) = V(t0+k, t0+r)
-    g.B = View{Cw + t0 + (int64_t)(t0 + p.b) * m, 1, m}; g.b_dt = dt;
+    g.B = View{Crest, 1, m}; g.b_dt = dt;
     g.out = Wt; g.out_sr = ntr; g.out_sc = 1; g.out_dt = dt;
     g.alpha = 1.0;
     g.splitk_ws = kws;
@@ -663,7 +696,7 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
     h.M = m - t0; h.N = ntr; h.K = p.b;
     h.L = View{VT + t0, 1, m}; h.l_dt = dt;
     h.B = View{Wt, ntr, 1}; h.b_dt = dt;
-    h.out = Cw + t0 + (int64_t)(t0 + p.b) * m; h.out_sr = 1; h.out_sc = m; h.out_dt = dt;
+    h.out = Crest; h.out_sr = 1; h.out_sc = m; h.out_dt = dt;
     h.alpha = -1.0;
     h.timer = "gemm_qr";
     if (launch_gemm(h, f64, LEFT_LOAD, EPI_ACCUM, st) != cudaSuccess) return SKEL_ERR_CUDA;
@@ -677,6 +710,16 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
   const int np = (s + pl.b - 1) / pl.b;
   for (int pi = np - 1; pi >= 0; --pi) {
     const int t0 = pi * pl.b, b = std::min(pl.b, s - t0);
+    if (tc) {          // Y = V_p^T E(t0:, :) on the tensor cores, E(t0:, :) -= (V_p T_p) Y
+      if (launch_gemm_tc_tn(m - t0, s, b, reinterpret_cast<const float*>(V + t0 + (int64_t)t0 * ldv), ldv,
+                            reinterpret_cast<const float*>(Q + t0), ldq, reinterpret_cast<float*>(Wt), s, nullptr, kws,
+                            dev_status, st, "gemm_qr") != cudaSuccess ||
+          launch_rank_update_f32(m - t0, s, b, reinterpret_cast<const float*>(VTN + t0 + (int64_t)t0 * m), m,
+                                 reinterpret_cast<const float*>(Wt), s, reinterpret_cast<float*>(Q + t0), ldq, -1.0f,
+                                 "gemm_qr", st) != cudaSuccess)
+        return SKEL_ERR_CUDA;
+      continue;
+    }
     GemmArgs g{};
     g.M = b; g.N = s; g.K = m - t0;
     g.L = View{V + t0 + (int64_t)t0 * ldv, ldv, 1}; g.l_dt = dt;       // V_p^T(r, k) = V(t0+k, t0+r)

@@ -65,9 +65,10 @@ def test_cur_single_skeleton(skel, dev):
 def test_id_sketch_one_and_all(skel, dev, s):
     """The sketch-only ID with one pivot and with as many pivots as columns (Z = I)."""
     X = np.random.default_rng(s).standard_normal((70, 60))
-    Js, _, R, st = skel.pivot_lupp(torch.from_numpy(X).to(dev), s)
+    Xd = torch.from_numpy(X).to(dev)
+    Js, _, _, st = skel.pivot_lupp(Xd, s, factors=False)
     skel.check_status(st)
-    Z, st = skel.column_id_sketch(R, Js)
+    Z, st = skel.column_id_sketch(Xd, Js)
     skel.check_status(st)
     J = Js.cpu().numpy()
     assert np.allclose(Z.cpu().numpy(), decomp.sketch_id(X, J), rtol=0, atol=1e-9)

@@ -73,5 +73,9 @@ def test_peaks_fallback_and_workload_config():
     b = _bench()
     hbm, bf16, src = b.load_peaks()
     assert hbm > 1000 and bf16 > 100 and src in ("measured", "fallback")
-    cfg = b.workload_config(256, 16, "tf32")
+    cfg = b.workload_config("c2", 256, 16, "tf32")
     assert cfg["m"] == cfg["n"] == 8192 and cfg["l"] == 272 and "workload" in cfg
+    cfg = b.workload_config("c5", 1024, 76, "bf16")
+    assert (cfg["m"], cfg["n"], cfg["k"], cfg["l"]) == (65536, 32768, 1024, 1100)
+    assert b.tensor_peak("tf32", {"bf16_tflops": 2250.0, "bf16_tflops_sustained": 1800.0}, False) == pytest.approx(1100.0)
+    assert b.tensor_peak("fp8", {"bf16_tflops": 2250.0, "bf16_tflops_sustained": 1800.0}, True) == pytest.approx(3600.0)

@@ -1,5 +1,6 @@
-"""Oracle pins for the batched path: the sketch-only column ID (Sec. 4, C^+ A ~ X_1^+ X on the
-first r rows of the sketch) and the per-block pipeline with the tolerance-driven rank."""
+"""Oracle pins for the batched path: the sketch-only column ID (Sec. 4, C^+ A ~ X_1^+ X with the
+pseudo-inverse over all l rows of the sketch) and the per-block pipeline with the
+tolerance-driven rank."""
 
 import numpy as np
 import pytest
@@ -9,19 +10,66 @@ from oracle import decomp, pivoting, rank, sketch, skeleton
 import workloads
 
 
-def test_sketch_id_interpolates_and_equals_lu_form():
-    """Z(:, Js) = I, and Z equals R_1^{-1} R formed from the LUPP factor (an independent route:
-    X(0:r, :) = L R with R(:, Js) unit upper triangular)."""
+def _lu_correction_form(X, r):
+    """X(:, J)^+ X from the factors of r LUPP steps on all l rows, an independent route:
+    X = L R + [0; S] with L = [L_top; L_2] (L_top r x r lower triangular), R(:, J) = R_1 unit
+    upper triangular and S(:, J) = 0, so X(:, J) = L R_1 and
+        X(:, J)^+ X = R_1^{-1} R + X(0:r, J)^{-1} (I + B^T B)^{-1} B^T S,   B = L_2 L_top^{-1}
+    (the truncated solution R_1^{-1} R plus a correction from the rows below the pivots)."""
+    piv = pivoting.lupp_columns(X, r)
+    Js, L, R = piv["Js"], piv["L"], piv["R"]
+    Lt, L2 = L[:r], L[r:]
+    S = X[r:] - L2 @ R
+    B = solve_triangular(Lt.T, L2.T, lower=False).T          # B L_top = L_2
+    G = np.eye(r) + B.T @ B
+    corr = np.linalg.solve(X[:r][:, Js], np.linalg.solve(G, B.T @ S))
+    return Js, solve_triangular(R[:, Js], R, lower=False, unit_diagonal=True) + corr
+
+
+def test_sketch_id_interpolates_and_equals_lu_correction_form():
     rng = np.random.default_rng(1)
     X = rng.standard_normal((30, 200))
     r = 12
-    piv = pivoting.lupp_columns(X, r)
-    Js = piv["Js"]
+    Js, Z_lu = _lu_correction_form(X, r)
     Z = decomp.sketch_id(X, Js)
     assert np.allclose(Z[:, Js], np.eye(r), atol=1e-12)
-    R = piv["R"]
-    Z_lu = solve_triangular(R[:, Js], R, lower=False, unit_diagonal=True)
     assert np.allclose(Z, Z_lu, rtol=0, atol=1e-10 * np.abs(Z).max())
+    # the normal equations of the sketched least-squares problem hold
+    X1 = X[:, Js]
+    assert np.linalg.norm(X1.T @ (X - X1 @ Z)) <= 1e-10 * np.linalg.norm(X1) * np.linalg.norm(X)
+
+
+def test_sketch_id_square_sketch_is_the_printed_inverse():
+    """With l = |J_s| (the paper's setting) the pseudo-inverse is the inverse: Z = X_1^{-1} X."""
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((16, 90))
+    Js = pivoting.lupp_columns(X, 16)["Js"]
+    Z = decomp.sketch_id(X, Js)
+    assert np.allclose(Z, np.linalg.solve(X[:, Js], X), rtol=0, atol=1e-10 * np.abs(Z).max())
+
+
+def test_sketch_id_uses_the_oversampling_rows():
+    """With s < l the rows below the pivots enter Z: the least-squares solution differs from
+    the one through the first s rows alone, fits the whole sketch strictly better, and gives a
+    smaller ID error on average (sketch-and-solve with oversampling)."""
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((40, 150))
+    Js = pivoting.lupp_columns(X, 25)["Js"]
+    Z_ls = decomp.sketch_id(X, Js)
+    Z_tr = np.linalg.solve(X[:25][:, Js], X[:25])
+    X1 = X[:, Js]
+    assert np.linalg.norm(Z_ls - Z_tr) > 1e-3 * np.linalg.norm(Z_tr)
+    assert np.linalg.norm(X - X1 @ Z_ls) < np.linalg.norm(X - X1 @ Z_tr)
+    r_ls, r_tr = [], []
+    for seed in range(12):
+        A = workloads.dense_config2(300, 200, seed=seed, dtype=np.float64)
+        Xs = sketch.gaussian_sketch(A, 40, 100 + seed)
+        J = pivoting.lupp_columns(Xs, 25)["Js"]
+        C = A[:, J]
+        e_opt = np.linalg.norm(A - C @ decomp.column_id(A, J))
+        r_ls.append(np.linalg.norm(A - C @ decomp.sketch_id(Xs, J)) / e_opt)
+        r_tr.append(np.linalg.norm(A - C @ np.linalg.solve(Xs[:25][:, J], Xs[:25])) / e_opt)
+    assert np.mean(r_ls) < np.mean(r_tr)
 
 
 def test_sketch_id_exact_on_exactly_low_rank_input():

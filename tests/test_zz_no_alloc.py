@@ -38,8 +38,11 @@ def _run_static(skel, fn, X, s):
     return Js, Lf, Rf
 
 
+# (FP64, 992, 992, 992) needs 8,373,760 bytes of scratch, just under the 8 MiB array, with the
+# column slab in the array rather than in shared memory (32 x 992 FP64 entries per CTA exceed
+# the shared-memory budget): the layout where the slab follows the grid's exchange buffers.
 @pytest.mark.parametrize("dtype,l,n,s", [(torch.float32, 300, 4096, 256), (torch.float64, 60, 800, 50),
-                                         (torch.float32, 8, 8, 8)])
+                                         (torch.float32, 8, 8, 8), (torch.float64, 992, 992, 992)])
 def test_static_scratch_matches_workspace_entry_point(skel, dev, dtype, l, n, s):
     fn = _static_fn(skel)
     gen = torch.Generator(device="cpu").manual_seed(l * n + s)
@@ -54,13 +57,22 @@ def test_static_scratch_matches_workspace_entry_point(skel, dev, dtype, l, n, s)
         assert torch.equal(Lf.cpu(), L_ref.cpu()), f"call {call}"
 
 
-def test_static_scratch_rejects_oversized_problem(skel, dev):
-    """FP64 with s = 512 over 8192 columns needs a ~33 MB global slab: beyond the 8 MiB
-    array, the call returns SKEL_ERR_WORKSPACE and launches nothing."""
+@pytest.mark.parametrize("l,n,s", [(512, 8192, 512), (996, 996, 996)])
+def test_static_scratch_rejects_oversized_problem(skel, dev, l, n, s):
+    """FP64 with s = 512 over 8192 columns needs a ~33 MB slab, and l = s = n = 996 the first
+    square size past the 8 MiB array (992 fits, above): the call returns SKEL_ERR_WORKSPACE,
+    launches nothing and leaves no error behind."""
     fn = _static_fn(skel)
-    X = torch.zeros(512, 8192, dtype=torch.float64, device=dev)
-    Js = torch.zeros(512, dtype=torch.int32, device=dev)
+    X = torch.ones(l, n, dtype=torch.float64, device=dev)
+    Js = torch.full((s,), -7, dtype=torch.int32, device=dev)
+    st = skel.new_status(dev)
+    torch.cuda.synchronize()
+    n0 = skel.launch_count()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    rc = fn(0, ctypes.c_void_p(X.data_ptr()), 512, 8192, 8192, 512, ctypes.c_void_p(Js.data_ptr()),
-            None, 0, None, 0, None, stream)
+    rc = fn(0, ctypes.c_void_p(X.data_ptr()), l, n, n, s, ctypes.c_void_p(Js.data_ptr()),
+            None, 0, None, 0, ctypes.c_void_p(st.data_ptr()), stream)
     assert rc == 2
+    torch.cuda.synchronize()
+    assert skel.launch_count() == n0
+    skel.check_status(st, "rejected call")
+    assert bool((Js.cpu() == -7).all())

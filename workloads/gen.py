@@ -5,8 +5,8 @@ __all__ = [
     "SEED_BASE", "seed_for", "haar_orthogonal", "dense_spectrum", "sigma_config1",
     "sigma_config2", "sigma_config5", "config1", "dense_config2", "snn_csc",
     "kahan_type", "separated_columns", "exact_rank", "kernel_blocks",
-    "torch_dense_spectrum",
- "torch_kernel_blocks"]
+    "torch_dense_spectrum", "torch_config5", "CONFIG5_R_EFF",
+    "torch_kernel_blocks"]
 
 SEED_BASE = 2104_05877
 
@@ -153,6 +153,33 @@ def torch_dense_spectrum(m, n, sigma, noise_std, seed, device, dtype):
     if noise_std:
         At += noise_std * torch.randn(n, m, generator=g, device=device, dtype=torch.float64)
     return At.to(dtype).t()                  # m x n view, column-major storage
+
+
+CONFIG5_R_EFF = 3300        # exp(-3300/200) < 1e-7: below this the spectrum is the noise floor
+
+
+def torch_config5(device, m=65536, n=32768, r_eff=CONFIG5_R_EFF, floor=1e-7, seed=None):
+    """Large low-precision case: A = U diag(sigma) V^T + floor * G / sqrt(m), sigma_j =
+    exp(-j/200) for j <= r_eff, U (m x r_eff) and V (n x r_eff) Haar by QR of FP32 Gaussians,
+    built in FP32 on `device` (an FP64 build at 65536 x 32768 would cost ~14 FP64 TFLOP).
+    Returned column-major (the transpose view of a row-major n x m tensor)."""
+    import torch
+    seed = seed_for(5) if seed is None else seed
+    sig = sigma_config5(r_eff)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        with torch.no_grad():
+            U, _ = torch.linalg.qr(torch.randn(m, r_eff, generator=g, device=device))
+            V, _ = torch.linalg.qr(torch.randn(n, r_eff, generator=g, device=device))
+            At = V @ (U * torch.as_tensor(sig, device=device, dtype=torch.float32)[None, :]).T   # n x m
+            del U, V
+            At += (floor / np.sqrt(m)) * torch.randn(n, m, generator=g, device=device)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+    return At.t()
 
 
 def torch_kernel_blocks(nblocks, seed, device, mrange=(64, 1024), nrange=(64, 512), h=0.5, sep=4.0):
