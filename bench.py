@@ -5,7 +5,7 @@ Headline workload (the largest single-GPU configuration; one "step" = the whole 
 one synthetic matrix resident in HBM):
   A: 65536 x 32768 FP32 (8.6 GB), A = U diag(sigma) V^T + 1e-7 floor, sigma_j = exp(-j/200),
      Haar U, V; k = 1024, oversampling p = 76 (l = 1100), Gaussian embedding.
-  step = tensor-core sketch X = Gamma A (--prec, BF16 by default)  ->  LUPP on X (J_s, R^LU)
+  step = tensor-core sketch X = Gamma A (--prec, TF32 by default)  ->  LUPP on X (J_s, R^LU)
          [time-to-skeleton, the metric]  ->  column ID Z = C^+ A (Householder QR of C = A(:, J_s),
          W = Q_C^T A, FP64 solve)  [time to ID]  ->  Theorem 1's eta from R^LU.
 Reported beside it: time-to-skeleton in every sketch precision (TF32, BF16, FP8) and in the
@@ -58,11 +58,14 @@ def parse():
     ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS))
     ap.add_argument("--k", type=int, default=None, help="rank (default: the workload's)")
     ap.add_argument("--p", type=int, default=None, help="oversampling (default: the workload's)")
-    ap.add_argument("--prec", default="bf16", choices=["tf32", "bf16", "fp8", "f32"])
+    ap.add_argument("--prec", default="tf32", choices=["tf32", "bf16", "fp8", "f32"])
     ap.add_argument("--blocks", type=int, default=4096, help="blocks of the batched run (--only batch)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-GPU comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the 8192^2 extra keys")
+    ap.add_argument("--xonly", action="store_true",
+                    help="with --only lupp: pivot on a seeded Gaussian l x n sketch instead of building A (the "
+                         "same shapes with a few hundred MB on the device, for profilers)")
     ap.add_argument("--cols", type=int, default=None,
                     help="with --only: this many columns of the workload's A instead of all of them (a smaller "
                          "case of the same kernels for profilers)")
@@ -165,7 +168,7 @@ class ClockSampler:
 
 
 # kernels timed with CUDA events in the serialised pass
-TIMED_KERNELS = ("sketch_tc", "sketch_fp8", "fp8_quantize", "gemm_tc", "lupp_panel", "lupp_trail", "qr_panel", "qr_wy",
+TIMED_KERNELS = ("sketch_tc", "sketch_fp8", "fp8_quantize", "gemm_tc", "lupp_panel", "lupp_trail", "qr_panel", "qr_wy", "gemm_refine",
                  "trsm", "gemm_qr", "gemm_cur", "gemm_eta_h", "gemm_eta_sq", "gemm_simt")
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel at this
 # workload, scaled from a smaller capture where noted in the profiles (None where no capture of
@@ -302,11 +305,47 @@ def time_skeleton(skel, A, l, k, prec, seed_G, st, reps=3):
     return Js, {"time_to_skeleton_ms": sk + lu, "sketch_ms": sk, "lupp_ms": lu, "reps": reps}
 
 
-def kernel_models(workload, m, n, k, l, prec, peaks, sustained):
+def measure_floors(skel, dev, col_words):
+    """Measured floors for the latency- and ALU-bound kernels: FMA rates of the FP64 and FP32
+    pipes, one grid-wide barrier round over every SM, one cluster candidate exchange (16 CTAs
+    where the device offers them, else 8) with and without a pivot column of `col_words`."""
+    import torch
+    out = {"fp64_tflops": skel.debug_fma_rate(True, iters=1 << 12),
+           "fp32_tflops": skel.debug_fma_rate(False, iters=1 << 14),
+           "grid_barrier_ns": skel.debug_exchange_latency(0, torch.cuda.get_device_properties(dev).multi_processor_count,
+                                                          steps=2000)}
+    for cl in (16, 8):
+        try:
+            out["cluster_exchange_ns"] = skel.debug_exchange_latency(1, cl, steps=4000)
+            out["cluster_exchange_col_ns"] = skel.debug_exchange_latency(1, cl, steps=4000, col_words=col_words)
+            out["cluster_ctas"] = cl
+            out["col_words"] = col_words
+            break
+        except skel.SkelError:
+            continue
+    return out
+
+
+def latency_roofline(kernels, name, steps, floors):
+    """A latency-bound chain of `steps` dependent exchanges: floor = steps x one exchange round
+    (with the pivot column); frac = floor / measured time per step of the whole run."""
+    kd = kernels.get(name)
+    if not kd or "cluster_exchange_col_ns" not in floors:
+        return None
+    floor_ms = steps * floors["cluster_exchange_col_ns"] * 1e-6
+    kd.update({"bound": "latency", "floor_ms": floor_ms, "frac": floor_ms / kd["ms_per_step"],
+               "us_per_step": 1e3 * kd["ms_per_step"] / steps,
+               "floor_what": f"{steps} steps x one {floors['cluster_ctas']}-CTA cluster exchange round "
+                             f"({floors['cluster_exchange_col_ns']:.0f} ns, measured)"})
+    return kd
+
+
+def kernel_models(workload, m, n, k, l, prec, peaks, sustained, floors=None):
     """Algorithmic work of each timed kernel over one step: (bound, work, peak, unit)."""
     hbm = peaks["hbm_gbs"]
     a_bytes = 4.0 * m * n
-    fp32_alu = 152 * 128 * 2 * 2.07e9 / 1e12          # TFLOP/s, FFMA
+    fp32_alu = (floors or {}).get("fp32_tflops") or 152 * 128 * 2 * 2.07e9 / 1e12     # TFLOP/s, FFMA
+    fp64 = (floors or {}).get("fp64_tflops") or FP64_NOMINAL_TFLOPS
     b_pan = 24 if workload == "c5" else 64
     # LUPP trailing updates: every panel reads and writes the rows below it once (4 B each way)
     trail_bytes = sum(8.0 * max(k - t0 - b_pan, 0) * n for t0 in range(0, k, b_pan))
@@ -315,13 +354,12 @@ def kernel_models(workload, m, n, k, l, prec, peaks, sustained):
         "fp8_quantize": ("hbm", 5.0 * m * n / 1e9, hbm, "GB/s"),   # A read (4 B), A8 written (1 B)
         "gemm_tc": ("tensor", 3 * 2.0 * k * m * n / 1e12, tensor_peak("tf32", peaks, sustained), "TFLOP/s"),
         "lupp_trail": ("hbm", trail_bytes / 1e9, hbm, "GB/s"),
-        "trsm": ("alu", (1.0 * k * k * n) / 1e12, FP64_NOMINAL_TFLOPS, "TFLOP/s"),
-        "gemm_qr": ("alu", 4.0 * m * k * k / 1e12, fp32_alu, "TFLOP/s"),
+        "trsm": ("alu", (1.0 * k * k * n) / 1e12, fp64, "TFLOP/s"),
     }
     if prec in ("tf32", "bf16"):
         mod["sketch_tc"] = ("tensor", 2.0 * l * m * n / 1e12, tensor_peak(prec, peaks, sustained), "TFLOP/s")
     if workload == "c2":
-        mod["trsm"] = ("alu", (1.0 * k * k * n + 4.0 * k ** 3) / 1e12, FP64_NOMINAL_TFLOPS, "TFLOP/s")
+        mod["trsm"] = ("alu", (1.0 * k * k * n + 4.0 * k ** 3) / 1e12, fp64, "TFLOP/s")
     return mod
 
 
@@ -361,6 +399,16 @@ def run_ours(args, rank, world):
     seed_A, seed_G = seeds(args.workload, rank)
     if args.cols and not args.only:
         raise SystemExit("--cols is a profiling aid for --only runs")
+    if args.xonly:
+        if args.only != "lupp":
+            raise SystemExit("--xonly is a profiling aid for --only lupp")
+        w = WORKLOADS[args.workload]
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed_G)
+        X = torch.randn(l, args.cols or w["n"], generator=g, device=dev)
+        st = skel.new_status(dev)
+        run_timed(args, rank, lambda: skel.pivot_lupp(X, k, status=st), st, workload_config(args.workload, k, p, "x only"))
+        return
     A = make_A(args.workload, dev, seed_A, cols=args.cols)
     torch.cuda.synchronize()
     st = skel.new_status(dev)
@@ -447,6 +495,7 @@ def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
 
     # serialised pass: the same steps on one stream, CUDA events around every hot launch
     peaks = load_peaks_full()
+    floors = measure_floors(skel, dev, col_words=24)
     nser = max(2, min(args.steps, 5))
     skel.kernel_timing(True)
     s0, s1 = _events(2)
@@ -456,8 +505,9 @@ def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
     s1.record()
     torch.cuda.synchronize()
     ser_ms = s0.elapsed_time(s1)
-    models = kernel_models("c5", m, n, k, l, prec, peaks, sustained=True)
+    models = kernel_models("c5", m, n, k, l, prec, peaks, sustained=True, floors=floors)
     kernels = kernel_table(skel, nser, ser_ms, models)
+    latency_roofline(kernels, "lupp_panel", k, floors)
     skel.kernel_timing(False)
     skel.check_status(st, "serialised pass")
 
@@ -537,10 +587,11 @@ def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
         A_np = np.asfortranarray(A[:, :ncols].double().cpu().numpy())
         cpu = cpu_sample_baseline(A_np, m, n, k, p, seed_G)
 
-    extra = None
+    extra = extra3 = None
     if not args.no_extra:
         del X
         torch.cuda.empty_cache()
+        extra3 = run_c3(skel, dev)
         A2 = make_A("c2", dev, seeds("c2", rank)[0])
         a2 = argparse.Namespace(**vars(args))
         a2.workload, a2.k, a2.p, a2.prec, a2.no_cpu = "c2", 256, 16, "tf32", True
@@ -559,11 +610,13 @@ def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
         "id_error_ratio_vs_fp64": (rel_id / fp64["rel_id_error"]) if fp64 else None,
         "precisions": per_prec, "fp64_gpu": fp64,
         "roofline": roofline, "kernels": kernels, "serialised_ms_per_step": ser_ms / nser,
+        "measured_floors": floors,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(4 * m * n), "d2h_bytes_per_step": int(4 * k),
                 "steps": e_steps, "what": "pinned host A copied to the device, sketch + LUPP, J_s copied back"},
         "gpu_launches": launches, "clocks": clk.summary(),
         "extra_8192": extra,
+        "extra_sparse_262144x4096": extra3,
     }
     print(json.dumps(res), flush=True)
 
@@ -639,6 +692,7 @@ def run_c2_step(args, rank, world, dev, A, skel, st, seed_G, headline):
         return None
 
     peaks = load_peaks_full()
+    floors = measure_floors(skel, dev, col_words=64)
     nser = max(2, min(args.steps, 10))
     skel.kernel_timing(True)
     s0, s1 = _events(2)
@@ -648,18 +702,39 @@ def run_c2_step(args, rank, world, dev, A, skel, st, seed_G, headline):
     s1.record()
     torch.cuda.synchronize()
     ser_ms = s0.elapsed_time(s1)
-    kernels = kernel_table(skel, nser, ser_ms, kernel_models("c2", m, n, k, l, args.prec, peaks, sustained=False))
+    kernels = kernel_table(skel, nser, ser_ms, kernel_models("c2", m, n, k, l, args.prec, peaks, sustained=False,
+                                                             floors=floors))
     skel.kernel_timing(False)
-    modeled = [nm for nm in kernels if "bound" in kernels[nm]]
+    latency_roofline(kernels, "lupp_panel", 2 * k, floors)      # column LUPP on X and row LUPP on C
+    modeled = [nm for nm in kernels if kernels[nm].get("bound") in ("hbm", "tensor", "alu")]
     roofline = None
     if modeled:
         dom = max(modeled, key=lambda nm: kernels[nm]["ms_per_step"])
         kd = kernels[dom]
         roofline = {"kernel": dom, "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
                     "unit": kd["unit"], "frac": kd["frac"], "traffic": TRAFFIC_PER_LAUNCH["c2"].get(dom),
-                    "peak_source": f"{peaks['source']} MEASURED_PEAKS.json (burst)",
+                    "peak_source": (f"{peaks['source']} MEASURED_PEAKS.json (burst)" if kd["bound"] != "alu" else
+                                    "FMA rate measured in this run (skel_debug_fma_rate)"),
                     "avg_launch_us": kd["avg_us"],
                     "timing": "CUDA events around every launch, serialised pass of the same steps"}
+
+    # the FP64 refinement steps of Z and U (skel_id_refine, skel_cur_refine) against the unrefined calls
+    def t_call(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = _events(2)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    refine = {"id_ms": t_call(lambda: skel.column_id(A, Js, status=st)),
+              "id_refined_ms": t_call(lambda: skel.column_id_refined(A, Js, status=st)),
+              "cur_ms": t_call(lambda: skel.cur(A, Js, Is, status=st)),
+              "cur_refined_ms": t_call(lambda: skel.cur(A, Js, Is, status=st, refine=True))}
+    skel.check_status(st, "refinement")
 
     # FP64 plain-GPU form of the skeleton stage on the same matrix
     fp64 = None
@@ -721,12 +796,108 @@ def run_c2_step(args, rank, world, dev, A, skel, st, seed_G, headline):
         "rel_id_error": rel_id, "rel_cur_error": rel_cur, "rel_id_error_gram": rel_id_gram,
         "rel_cur_error_gram": rel_cur_gram, "eta": float(e[3]),
         "fp64_gpu": fp64, "id_error_ratio_vs_fp64": (rel_id / fp64["rel_id_error"]) if fp64 else None,
+        "fp64_refinement": refine,
         "roofline": roofline, "kernels": kernels, "serialised_ms_per_step": ser_ms / nser, "cpu_baseline": cpu,
+        "measured_floors": floors,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(4 * m * n),
                 "d2h_bytes_per_step": int(8 * k)},
         "gpu_launches": launches, "clocks": clk.summary(),
     }
     return res
+
+
+def run_c3(skel, dev, steps=10, warmup=3):
+    """The tall sparse configuration: 262144 x 4096 SNN-style CSC (~1% dense), k = 256, sparse
+    sign embedding with zeta = 8 and l = 2k.  Times the CSC sketch (algorithmic bytes: the CSC
+    arrays read once and X written once), the skeletons (sketch + LUPP on X + row LUPP on
+    C = A(:, J_s)) and the stable CUR with rows given; C, R and the CUR use the densified A
+    (4.3 GB, column-major FP32)."""
+    import numpy as np
+    import torch
+    import workloads
+    m, n, r, k, zeta = 262144, 4096, 300, 256, 8
+    l = 2 * k
+    seed_G = workloads.seed_for(3, "gamma")
+    A = workloads.snn_csc(m, n, r, seed=workloads.seed_for(3))
+    nnz = int(A.nnz)
+    col_ptr = torch.from_numpy(A.indptr.astype(np.int64)).to(dev)
+    row_idx = torch.from_numpy(A.indices.astype(np.int32)).to(dev)
+    val = torch.from_numpy(A.data.astype(np.float32)).to(dev)
+    cols = torch.repeat_interleave(torch.arange(n, device=dev), col_ptr[1:] - col_ptr[:-1])
+    At = torch.zeros(n, m, dtype=torch.float32, device=dev)
+    At[cols, row_idx.long()] = val
+    Ad = At.t()
+    del cols
+    st = skel.new_status(dev)
+    X = torch.empty(l, n, dtype=torch.float32, device=dev)
+    Js = torch.empty(k, dtype=torch.int32, device=dev)
+
+    def sk():
+        skel.sketch_csc(col_ptr, row_idx, val, m, n, l, seed=seed_G, zeta=zeta, status=st, X=X)
+
+    def timed(fn, reps):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = _events(2)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    sketch_ms = timed(sk, steps)
+    skel.kernel_timing(True)
+    sk()
+    torch.cuda.synchronize()
+    kern_ms = skel.kernel_time("sparse_csc")[0]
+    skel.kernel_timing(False)
+
+    out = {}
+
+    def skeleton():
+        sk()
+        J, _, _, _ = skel.pivot_lupp(X, k, factors=False, status=st)
+        I, _ = skel.pivot_rows(Ad, J, status=st)
+        out["J"], out["I"] = J, I
+
+    tts = timed(skeleton, steps)
+    J, I = out["J"], out["I"]
+    cur_ms = timed(lambda: skel.cur(Ad, J, I, status=st), max(2, steps // 2))
+    _, U, _, _ = skel.cur(Ad, J, I, status=st)
+    e, _ = skel.error(Ad, J, Is=I, U=U, status=st)
+    skel.check_status(st, "tall sparse configuration")
+    e = e.cpu().numpy()
+    hbm = load_peaks_full()["hbm_gbs"]
+    a_bytes = 8.0 * nnz + 8.0 * (n + 1) + 4.0 * l * n
+    k_ms = kern_ms if kern_ms > 0 else sketch_ms
+    res = {"workload": f"262144x4096 SNN-style CSC (nnz {nnz}, {nnz / (m * n):.4f} dense), sparse sign zeta={zeta}, "
+                       f"l={l}, k={k}; CUR with rows by LUPP on C",
+           "sketch_ms": sketch_ms, "sketch_kernel_ms": kern_ms, "sketch_bytes": a_bytes,
+           "sketch_gbs": a_bytes / (k_ms * 1e-3) / 1e9, "sketch_frac_of_hbm": a_bytes / (k_ms * 1e-3) / 1e9 / hbm,
+           "time_to_skeleton_ms": tts, "cur_ms": cur_ms, "rel_cur_error": float(e[2] / e[0])}
+    del At, Ad, X
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_timed(args, rank, call, st, config):
+    """--warmup + --steps calls of `call`, timed with CUDA events; one JSON line."""
+    import torch
+    import paper_2104_05877_gb300 as skel
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = _events(2)
+    e0.record()
+    for _ in range(args.steps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    skel.check_status(st, args.only)
+    if rank == 0:
+        print(json.dumps({"only": args.only, "ms": e0.elapsed_time(e1) / args.steps, "config": config}), flush=True)
 
 
 def run_only(args, rank, A, skel, st, seed_G):

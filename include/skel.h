@@ -247,6 +247,24 @@ skel_status skel_id(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64
                     void* ws, size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream);
 
 /*
+ * skel_id_refine -- the column ID of skel_id for an FP32 A, followed by one step of iterative
+ * refinement in FP64 (corrected seminormal equations): with C = Q_C R_C the FP32 Householder
+ * QR of skel_id and Z0 = R_C^{-1} Q_C^T A,
+ *     Z1 = Z0 + R_C^{-1} R_C^{-T} (C^T A - (C^T C) Z0),
+ * where C^T A and C^T C are formed from exact FP32 x FP32 products summed in float-float pairs
+ * (about 44 significant bits, on the FP32 pipes), and the product with Z0 and both triangular
+ * solves are FP64.  The step contracts the error of Z0 (about cond(C) u_32 relative) by about
+ * cond(C)^2 u_32, leaving Z1 within a small multiple of cond(C)^2 u_64 of C^+ A in practice.
+ * Eq. (2.1); the refinement is this library's mixed-precision design, not the paper's.
+ *   Arguments, outputs and workspace handshake as skel_id (Z: s x n row-major FP64, Z(:, Js) = I;
+ *   sq_norms from the unrefined W).  dtype must be SKEL_F32 (SKEL_ERR_UNSUPPORTED otherwise: an
+ *   FP64 skel_id has nothing to refine at this precision).
+ */
+skel_status skel_id_refine(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
+                           int32_t s, const int32_t* Js, double* Z, int64_t ldz, double* sq_norms,
+                           void* ws, size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream);
+
+/*
  * skel_pivot_rows -- row skeletons of Algorithm 2 line 4: gathers C = A(:, Js) (m x s) and
  * runs row-wise LUPP on it (the LUPP of skel_pivot_lupp applied to C^T).
  *   Is        : out int32[s] row skeletons in selection order.
@@ -290,6 +308,22 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
                      int32_t s, const int32_t* Js, int32_t* Is, int rows_given, double* U,
                      int64_t ldu, double* sq_norms, void* ws, size_t* ws_bytes,
                      int32_t* dev_status, cudaStream_t stream);
+
+/*
+ * skel_cur_refine -- the stable CUR of skel_cur for an FP32 A, followed by one step of
+ * iterative refinement of U in FP64 (the two-sided form of skel_id_refine's step): with
+ * C = Q_C R_C and R^T = Q_R R_R the FP32 Householder QRs of skel_cur and U0 its core,
+ *     U1 = U0 + (R_C^T R_C)^{-1} (C^T A R^T - (C^T C) U0 (R R^T)) (R_R^T R_R)^{-1},
+ * where C^T A, C^T C and R R^T are formed from exact FP32 products summed in float-float pairs
+ * and (C^T A) R^T, the s x s products and the four triangular solves are FP64.  Eq. (2.4),
+ * Remark 3; the refinement is this library's mixed-precision design, not the paper's.
+ *   Arguments, outputs and workspace handshake as skel_cur (sq_norms from the unrefined
+ *   W Q_R).  dtype must be SKEL_F32 (SKEL_ERR_UNSUPPORTED otherwise).
+ */
+skel_status skel_cur_refine(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
+                            int32_t s, const int32_t* Js, int32_t* Is, int rows_given, double* U,
+                            int64_t ldu, double* sq_norms, void* ws, size_t* ws_bytes,
+                            int32_t* dev_status, cudaStream_t stream);
 
 /*
  * skel_error -- Frobenius errors formed directly from the residuals, and Theorem 1's
@@ -434,6 +468,32 @@ skel_status skel_debug_grid_timeout(int grid, uint64_t wait_ns, void* ws, size_t
                                     int32_t* dev_status, cudaStream_t stream);
 
 /*
+ * skel_debug_fma_rate -- measurement aid (no counterpart in the paper): launches 8 CTAs per SM
+ * of 256 threads, each thread running 8 independent FMA chains of `iters` steps in FP64
+ * (fp64 != 0) or FP32, and writes the flop count of the launch to *flops (host).  The caller
+ * times the launch with CUDA events on `stream`: flops / time is the FMA rate the pivot
+ * solves and the float-float products are measured against.  sink: device buffer of at least
+ * 8 x SMs elements of the type (never written in practice).
+ */
+skel_status skel_debug_fma_rate(int fp64, int64_t iters, int64_t* flops, void* sink, cudaStream_t stream);
+
+/*
+ * skel_debug_exchange_latency -- measurement aid (no counterpart in the paper): the time of one
+ * round of the exchanges the pivoting kernels are built on, written to *ns_per_step (device
+ * double) as the mean over rounds 1 .. steps-1 (globaltimer of CTA 0).
+ *   kind 0: grid-wide barrier through global memory (the persistent LUPP / CPQR / QR kernels),
+ *           `ctas` co-resident CTAs (2 .. SMs), cooperative launch; workspace (handshake).
+ *   kind 1: candidate exchange in one thread-block cluster of `ctas` CTAs (2, 4, 8 or 16; 16
+ *           needs the non-portable size, else SKEL_ERR_UNSUPPORTED): per round every CTA sends
+ *           a 16-byte header and `col_words` (a multiple of 4, <= 64) 32-bit words to every CTA
+ *           with st.async stores completing on three rotating mbarrier inboxes, as the LUPP
+ *           panel kernel does per pivot step; no workspace (*ws_bytes = 0).
+ * Waits are bounded (1 s, then SKEL_ERR_TIMEOUT in dev_status).  2 <= steps <= 10^6.
+ */
+skel_status skel_debug_exchange_latency(int kind, int ctas, int steps, int col_words, double* ns_per_step, void* ws,
+                                        size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream);
+
+/*
  * skel_debug_kernel_timing -- measurement aid (no counterpart in the paper): enable != 0 makes
  * the launch sites of the hot kernels record a CUDA event on the launching stream before and
  * after each launch, from now on; enable == 0 stops recording.  Either call discards earlier
@@ -442,7 +502,8 @@ skel_status skel_debug_grid_timeout(int grid, uint64_t wait_ns, void* ws, size_t
  * of one kernel since the last skel_debug_kernel_timing call; waits for those launches.
  * Names: "sketch_tc", "sketch_fp8", "fp8_quantize", "gemm_tc" (W = Q^T A), "lupp_panel", "lupp_trail", "qr_panel", "qr_wy", "trsm",
  * "gemm_qr" (QR trailing updates and Q formation), "gemm_cur" (W Q_R), "gemm_eta_h" (R R^T),
- * "gemm_eta_sq" (eta's squarings), "gemm_simt" (other SIMT GEMMs), "batch_sketch", "batch_lupp", "batch_z",
+ * "gemm_eta_sq" (eta's squarings), "gemm_refine" (the products of skel_id_refine), "gemm_simt" (other SIMT
+ * GEMMs), "sparse_csc" (the CSC sparse-sign sketch), "batch_sketch", "batch_lupp", "batch_z",
  * "transpose" (A^T for the column and power sketches on the tensor cores).
  * Host-side state, process-wide; not for concurrent use from several threads.
  */

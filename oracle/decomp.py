@@ -10,6 +10,7 @@ LAPACK Householder QR (numpy.linalg.qr) and triangular solves serve as single st
 """
 
 import numpy as np
+import scipy.sparse as sp
 from scipy.linalg import solve_triangular
 
 
@@ -22,13 +23,20 @@ def column_id(A, Js):
 
 
 def cur(A, Js, Is):
-    """U (s x s, FP64) of the CUR A ~ A(:, Js) U A(Is, :) via the stable form (Remark 3)."""
-    A = np.asarray(A, dtype=np.float64)
-    C = A[:, np.asarray(Js)]
-    Rm = A[np.asarray(Is), :]
+    """U (s x s, FP64) of the CUR A ~ A(:, Js) U A(Is, :) via the stable form (Remark 3).
+    A dense, or scipy.sparse (then Q_C^T A Q_R is formed as Q_C^T (A Q_R) with a sparse
+    product)."""
+    if sp.issparse(A):
+        A = A.astype(np.float64)
+        C = A[:, np.asarray(Js)].toarray()
+        Rm = A.tocsr()[np.asarray(Is), :].toarray()
+    else:
+        A = np.asarray(A, dtype=np.float64)
+        C = A[:, np.asarray(Js)]
+        Rm = A[np.asarray(Is), :]
     Qc, Rc = np.linalg.qr(C, mode="reduced")
     Qr, Rr = np.linalg.qr(Rm.T, mode="reduced")
-    M = Qc.T @ A @ Qr
+    M = Qc.T @ np.asarray(A @ Qr)
     U = solve_triangular(Rc, M, lower=False)                # R_C^{-1} M
     U = solve_triangular(Rr, U.T, lower=False).T            # (R_R^{-1} U^T)^T = U R_R^{-T}
     return U

@@ -10,6 +10,7 @@ X~_1^{-1} X~_2 = R_1^{-1} R_2 (Sec. 4, item 1).
 """
 
 import numpy as np
+import scipy.sparse as sp
 from scipy.linalg import solve_triangular
 
 
@@ -24,7 +25,18 @@ def rel_id_error(A, Js, Z):
 
 
 def rel_cur_error(A, Js, U, Is):
-    """||A - C U R||_F / ||A||_F with C = A(:, Js), R = A(Is, :) (Eq. (2.4))."""
+    """||A - C U R||_F / ||A||_F with C = A(:, Js), R = A(Is, :) (Eq. (2.4)), the residual
+    formed directly.  A dense, or scipy.sparse (the residual then formed 256 columns at a
+    time)."""
+    if sp.issparse(A):
+        A = A.tocsc().astype(np.float64)
+        CU = A[:, np.asarray(Js)].toarray() @ U
+        Rm = A.tocsr()[np.asarray(Is), :].toarray()
+        num = 0.0
+        for c0 in range(0, A.shape[1], 256):
+            blk = A[:, c0:c0 + 256].toarray() - CU @ Rm[:, c0:c0 + 256]
+            num += float(np.sum(blk ** 2))
+        return float(np.sqrt(num) / np.sqrt(A.multiply(A).sum()))
     A = np.asarray(A, dtype=np.float64)
     C = A[:, np.asarray(Js)]
     Rm = A[np.asarray(Is), :]

@@ -49,7 +49,9 @@ def lib():
         "skel_pivot_lupp": [i32, vp, i64, i64, i64, i32, vp, vp, i64, vp, i64, vp, szp, vp, vp],
         "skel_pivot_cpqr": [i32, vp, i64, i64, i64, i32, vp, vp, i64, vp, szp, vp, vp],
         "skel_id": [i64, i64, i32, vp, i64, i32, vp, vp, i64, vp, vp, szp, vp, vp],
+        "skel_id_refine": [i64, i64, i32, vp, i64, i32, vp, vp, i64, vp, vp, szp, vp, vp],
         "skel_cur": [i64, i64, i32, vp, i64, i32, vp, vp, ctypes.c_int, vp, i64, vp, vp, szp, vp, vp],
+        "skel_cur_refine": [i64, i64, i32, vp, i64, i32, vp, vp, ctypes.c_int, vp, i64, vp, vp, szp, vp, vp],
         "skel_pivot_rows": [i64, i64, i32, vp, i64, i32, vp, vp, vp, szp, vp, vp],
         "skel_error": [i64, i64, i32, vp, i64, i32, vp, vp, i64, vp, vp, i64, i32, vp, i64, vp, vp,
                        szp, vp, vp],
@@ -64,6 +66,8 @@ def lib():
         "skel_debug_philox": [vp, i64, u32, u32, vp, vp],
         "skel_debug_curand_philox": [u64, i64, ctypes.c_int, vp, vp],
         "skel_debug_grid_timeout": [ctypes.c_int, u64, vp, szp, vp, vp],
+        "skel_debug_fma_rate": [ctypes.c_int, i64, ctypes.POINTER(i64), vp, vp],
+        "skel_debug_exchange_latency": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, szp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -234,8 +238,13 @@ def skeletonize_streaming(A, k, p=10, seed=0, seed_omega=None, prec="f32", statu
     return Js, Is, st
 
 
-def sketch_csc(col_ptr, row_idx, val, m, n, l, kind="sparse_sign", seed=0, zeta=8, status=None):
-    X = torch.empty(l, n, dtype=torch.float32, device=val.device)
+def sketch_csc(col_ptr, row_idx, val, m, n, l, kind="sparse_sign", seed=0, zeta=8, status=None, X=None):
+    """X = Gamma A (l x n FP32, row-major) for a CSC A: col_ptr int64 (n+1), row_idx int32,
+    val float32 on the device."""
+    if X is None:
+        X = torch.empty(l, n, dtype=torch.float32, device=val.device)
+    if X.shape != (l, n) or X.dtype != torch.float32 or X.stride() != (n, 1):
+        raise ValueError("X must be a contiguous l x n float32 tensor")
     st = status if status is not None else new_status(val.device)
     nnz = val.numel()
     _call("skel_sketch_csc", lambda w, sz: [m, n, nnz, _ptr(col_ptr), _ptr(row_idx), _ptr(val), l,
@@ -312,6 +321,20 @@ def column_id(A, Js, status=None):
     return Z, sq, st
 
 
+def column_id_refined(A, Js, status=None):
+    """column_id for an FP32 A followed by one FP64 refinement step (corrected seminormal
+    equations with exact FP32 products): returns (Z, [||A||^2, ||Q_C^T A||^2], status)."""
+    A, lda = _colmajor(A)
+    m, n = A.shape
+    s = Js.numel()
+    Z = torch.empty(s, n, dtype=torch.float64, device=A.device)
+    sq = torch.empty(2, dtype=torch.float64, device=A.device)
+    st = status if status is not None else new_status(A.device)
+    _call("skel_id_refine", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, s, _ptr(Js), _ptr(Z), n, _ptr(sq), w,
+                                           sz, _ptr(st), _stream()], A.device)
+    return Z, sq, st
+
+
 def column_id_sketch(X, Js, status=None):
     """Z = X(:, Js)^+ X (s x n FP64): the column ID from the sketch alone (no pass over A), the
     least-squares solution over all l rows of the sketch X (l x n row-major)."""
@@ -365,9 +388,10 @@ def pivot_rows(A, Js, status=None):
     return Is, st
 
 
-def cur(A, Js, Is=None, status=None):
+def cur(A, Js, Is=None, status=None, refine=False):
     """U (s x s FP64) with A ~ A(:, Js) U A(Is, :) (Remark 3) and [||A||_F^2, ||Q_C^T A Q_R||_F^2].
-    Is is computed by row-wise LUPP on C when not given.  Returns (Is, U, sq_norms, status)."""
+    Is is computed by row-wise LUPP on C when not given.  refine=True (FP32 A): one FP64
+    refinement step of U (skel_cur_refine).  Returns (Is, U, sq_norms, status)."""
     A, lda = _colmajor(A)
     m, n = A.shape
     s = Js.numel()
@@ -377,8 +401,9 @@ def cur(A, Js, Is=None, status=None):
     U = torch.empty(s, s, dtype=torch.float64, device=A.device)
     sq = torch.empty(2, dtype=torch.float64, device=A.device)
     st = status if status is not None else new_status(A.device)
-    _call("skel_cur", lambda w, sz: [m, n, _dt(A), _ptr(A), lda, s, _ptr(Js), _ptr(Is), int(given),
-                                     _ptr(U), s, _ptr(sq), w, sz, _ptr(st), _stream()], A.device)
+    _call("skel_cur_refine" if refine else "skel_cur",
+          lambda w, sz: [m, n, _dt(A), _ptr(A), lda, s, _ptr(Js), _ptr(Is), int(given), _ptr(U), s, _ptr(sq), w, sz,
+                         _ptr(st), _stream()], A.device)
     return Is, U, sq, st
 
 
@@ -455,6 +480,35 @@ def debug_grid_timeout(grid, wait_ns, device="cuda"):
     st = new_status(device)
     _call("skel_debug_grid_timeout", lambda w, sz: [grid, wait_ns, w, sz, _ptr(st), _stream()], device)
     return st
+
+
+def debug_fma_rate(fp64=True, iters=1 << 14, device="cuda"):
+    """TFLOP/s of the FP64 (or FP32) FMA pipes, timed with CUDA events on the current stream."""
+    sink = torch.empty(8 * torch.cuda.get_device_properties(device).multi_processor_count,
+                       dtype=torch.float64 if fp64 else torch.float32, device=device)
+    flops = ctypes.c_int64(0)
+    fn = lambda: lib().skel_debug_fma_rate(int(fp64), iters, ctypes.byref(flops), _ptr(sink), _stream())
+    rc = fn()                                   # warm-up
+    if rc != 0:
+        raise SkelError(rc, "skel_debug_fma_rate")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    rc = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    if rc != 0:
+        raise SkelError(rc, "skel_debug_fma_rate")
+    return flops.value / (e0.elapsed_time(e1) * 1e-3) / 1e12
+
+
+def debug_exchange_latency(kind, ctas, steps=2000, col_words=0, device="cuda"):
+    """ns per round of the grid barrier (kind 0) or the cluster candidate exchange (kind 1)."""
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device=device)
+    st = new_status(device)
+    _call("skel_debug_exchange_latency", lambda w, sz: [kind, ctas, steps, col_words, _ptr(out), w, sz, _ptr(st),
+                                                        _stream()], device)
+    check_status(st, "skel_debug_exchange_latency")
+    return float(out.cpu()[0])
 
 
 def skeletonize(A, k, p=10, seed=0, prec="f32", pivot="lupp", kind="gaussian", zeta=8,

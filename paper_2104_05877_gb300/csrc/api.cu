@@ -1,5 +1,6 @@
 // C ABI entry points of libskel (include/skel.h): argument checks, workspace planning and
 // stream-ordered launches.  No entry point allocates memory or synchronizes the host.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -478,6 +479,76 @@ skel_status skel_id(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64
   return SKEL_OK;
 }
 
+skel_status skel_id_refine(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
+                           int32_t s, const int32_t* Js, double* Z, int64_t ldz, double* sq_norms,
+                           void* ws, size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  if (!id_args_ok(m, n, dtype, A, lda, s, Js) || Z == nullptr || ldz < n) return SKEL_ERR_INVALID_ARG;
+  if (dtype != SKEL_F32) return SKEL_ERR_UNSUPPORTED;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool run = pass == 1;
+    Arena ar(run ? ws : nullptr);
+    void *C, *Q;
+    double* R;
+    SK_TRY(skeleton_qr(ar, run, m, n, dtype, A, lda, s, Js, &C, &Q, &R, dev_status, stream));
+    void* W = ar.take(sizeof(float) * (size_t)s * n);
+    const bool tcw = gemm_tc_usable(m, n, s, nullptr, m, A, lda);
+    const int64_t nbw = tcw ? gemm_tc_num_partials(m, n, s) : gemm_num_blocks(s, n);
+    double* pw = static_cast<double*>(ar.take(sizeof(double) * nbw));
+    const int64_t nba = sqnorm_num_blocks(m, n);
+    double* pa = static_cast<double*>(ar.take(sizeof(double) * nba));
+    void* kws = ar.take(tcw ? gemm_tc_workspace(m, n, s) : gemm_workspace(s, n, m, false));
+    double* D = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * n));     // C^T A, then the correction
+    double* G = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));     // C^T C
+    double* U = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));     // J R^T J
+    void* fws = ar.take(std::max(gemm_tn_ff_workspace(m, n, s), gemm_tn_ff_workspace(m, s, s)));
+    if (!run) {
+      skel_status st;
+      if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+      continue;
+    }
+    // Z0 = R_C^{-1} Q_C^T A, as skel_id
+    if (tcw) {
+      SK_CUDA(launch_gemm_tc_tn(m, n, s, static_cast<const float*>(Q), m, static_cast<const float*>(A), lda,
+                                static_cast<float*>(W), n, pw, kws, dev_status, stream));
+    } else {
+      GemmArgs g{};
+      g.splitk_ws = kws;
+      g.M = s; g.N = n; g.K = m;
+      g.L = View{Q, m, 1}; g.l_dt = dtype;
+      g.B = View{A, 1, lda}; g.b_dt = dtype;
+      g.out = W; g.out_sr = n; g.out_sc = 1; g.out_dt = dtype;
+      g.alpha = 1.0;
+      g.partials = pw;
+      SK_CUDA(launch_gemm(g, false, LEFT_LOAD, EPI_STORE_SQ, stream));
+    }
+    SK_CUDA(launch_trsm_upper(s, n, R, s, 0, dtype, W, n, Z, ldz, stream));
+    // one corrected-seminormal-equations step: Z1 = Z0 + R^{-1} R^{-T} (C^T A - C^T C Z0), the
+    // products C^T A and C^T C exact with float-float sums, the rest FP64
+    SK_CUDA(launch_gemm_tn_ff(m, n, s, static_cast<const float*>(C), m, static_cast<const float*>(A), lda, D, n, fws,
+                              "gemm_refine", stream));
+    SK_CUDA(launch_gemm_tn_ff(m, s, s, static_cast<const float*>(C), m, static_cast<const float*>(C), m, G, s, fws,
+                              "gemm_refine", stream));
+    GemmArgs h{};
+    h.M = s; h.N = n; h.K = s;
+    h.L = View{G, s, 1}; h.l_dt = SKEL_F64;
+    h.B = View{Z, ldz, 1}; h.b_dt = SKEL_F64;
+    h.out = D; h.out_sr = n; h.out_sc = 1; h.out_dt = SKEL_F64;
+    h.alpha = -1.0;
+    h.timer = "gemm_refine";
+    SK_CUDA(launch_gemm(h, true, LEFT_LOAD, EPI_ACCUM, stream));                    // D = C^T A - C^T C Z0
+    SK_CUDA(launch_trsm_upper_t(s, n, R, s, U, D, n, stream));                       // D <- R^{-T} D
+    SK_CUDA(launch_trsm_upper(s, n, R, s, 0, SKEL_F64, D, n, D, n, stream));         // D <- R^{-1} D
+    SK_CUDA(launch_axpy_rows_f64(s, n, D, n, Z, ldz, stream));                      // Z1 = Z0 + D
+    SK_CUDA(launch_unit_columns(s, Js, Z, ldz, stream));
+    if (sq_norms) {
+      SK_CUDA(launch_sqnorm(m, n, dtype, A, lda, pa, stream));
+      SK_CUDA(launch_reduce_sum(pa, nba, sq_norms, 0, stream));
+      SK_CUDA(launch_reduce_sum(pw, nbw, sq_norms + 1, 0, stream));
+    }
+  }
+  return SKEL_OK;
+}
+
 skel_status skel_pivot_rows(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
                             int32_t s, const int32_t* Js, int32_t* Is, void* ws,
                             size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream) {
@@ -500,12 +571,13 @@ skel_status skel_pivot_rows(int64_t m, int64_t n, skel_dtype dtype, const void* 
   return SKEL_OK;
 }
 
-skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
-                     int32_t s, const int32_t* Js, int32_t* Is, int rows_given, double* U,
-                     int64_t ldu, double* sq_norms, void* ws, size_t* ws_bytes,
-                     int32_t* dev_status, cudaStream_t stream) {
+// The stable CUR of Remark 3 (skel_cur), and with `refine` one FP64 refinement step of U.
+static skel_status cur_impl(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda, int32_t s,
+                            const int32_t* Js, int32_t* Is, int rows_given, double* U, int64_t ldu, double* sq_norms,
+                            bool refine, void* ws, size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream) {
   if (!id_args_ok(m, n, dtype, A, lda, s, Js) || Is == nullptr || U == nullptr || ldu < s)
     return SKEL_ERR_INVALID_ARG;
+  if (refine && dtype != SKEL_F32) return SKEL_ERR_UNSUPPORTED;
   const bool f64 = dtype == SKEL_F64;
   for (int pass = 0; pass < 2; ++pass) {
     const bool run = pass == 1;
@@ -531,6 +603,16 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
     const bool tcw = !f64 && gemm_tc_usable(m, n, s, nullptr, m, A, lda);   // tensor-core W
     void* kws1 = ar.take(tcw ? gemm_tc_workspace(m, n, s) : gemm_workspace(s, n, m, f64));
     void* kws2 = ar.take(gemm_workspace(s, s, n, f64));
+    // refinement scratch: C^T A (s x n), C^T C, R R^T, the correction and J R^T J (s x s, FP64)
+    double* B1 = refine ? static_cast<double*>(ar.take(sizeof(double) * (size_t)s * n)) : nullptr;
+    double* Gc = refine ? static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s)) : nullptr;
+    double* Gr = refine ? static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s)) : nullptr;
+    double* D = refine ? static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s)) : nullptr;
+    double* Uf = refine ? static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s)) : nullptr;
+    void* fws = refine ? ar.take(std::max({gemm_tn_ff_workspace(m, n, s), gemm_tn_ff_workspace(m, s, s),
+                                           gemm_tn_ff_workspace(n, s, s)}))
+                       : nullptr;
+    void* kws3 = refine ? ar.take(gemm_workspace(s, s, n, true)) : nullptr;
     if (!run) {
       skel_status st;
       if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
@@ -573,8 +655,54 @@ skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int6
     SK_CUDA(launch_transpose_f64(s, T1, s, T2, s, stream));
     SK_CUDA(launch_trsm_upper(s, s, Rr, s, 0, SKEL_F64, T2, s, T1, s, stream));
     SK_CUDA(launch_transpose_f64(s, T1, s, U, ldu, stream));
+    if (!refine) continue;
+    // U1 = U0 + (R_C^T R_C)^{-1} (C^T A R^T - (C^T C) U0 (R R^T)) (R_R^T R_R)^{-1}, with C^T A,
+    // C^T C and R R^T from exact FP32 products in float-float sums and the rest FP64
+    const float* Cf = static_cast<const float*>(C);
+    const float* Rf = static_cast<const float*>(Rt);          // R^T, n x s column-major
+    SK_CUDA(launch_gemm_tn_ff(m, n, s, Cf, m, static_cast<const float*>(A), lda, B1, n, fws, "gemm_refine", stream));
+    SK_CUDA(launch_gemm_tn_ff(m, s, s, Cf, m, Cf, m, Gc, s, fws, "gemm_refine", stream));
+    SK_CUDA(launch_gemm_tn_ff(n, s, s, Rf, n, Rf, n, Gr, s, fws, "gemm_refine", stream));
+    auto gemm64 = [&](int64_t K, View L, skel_dtype ldt, View B, skel_dtype bdt, double* out, double alpha,
+                      GemmEpi epi, void* kws) {
+      GemmArgs q{};
+      q.splitk_ws = kws;
+      q.M = s; q.N = s; q.K = K;
+      q.L = L; q.l_dt = ldt;
+      q.B = B; q.b_dt = bdt;
+      q.out = out; q.out_sr = s; q.out_sc = 1; q.out_dt = SKEL_F64;
+      q.alpha = alpha;
+      q.timer = "gemm_refine";
+      return launch_gemm(q, true, LEFT_LOAD, epi, stream);
+    };
+    SK_CUDA(gemm64(n, View{B1, n, 1}, SKEL_F64, View{Rf, 1, n}, SKEL_F32, D, 1.0, EPI_STORE, kws3));   // C^T A R^T
+    SK_CUDA(gemm64(s, View{Gc, s, 1}, SKEL_F64, View{U, ldu, 1}, SKEL_F64, T1, 1.0, EPI_STORE, nullptr));
+    SK_CUDA(gemm64(s, View{T1, s, 1}, SKEL_F64, View{Gr, s, 1}, SKEL_F64, D, -1.0, EPI_ACCUM, nullptr));
+    SK_CUDA(launch_trsm_upper_t(s, s, Rc, s, Uf, D, s, stream));                  // R_C^{-T} D
+    SK_CUDA(launch_trsm_upper(s, s, Rc, s, 0, SKEL_F64, D, s, D, s, stream));       // R_C^{-1} (.)
+    SK_CUDA(launch_transpose_f64(s, D, s, T2, s, stream));                          // E^T
+    SK_CUDA(launch_trsm_upper_t(s, s, Rr, s, Uf, T2, s, stream));                 // R_R^{-T} E^T
+    SK_CUDA(launch_trsm_upper(s, s, Rr, s, 0, SKEL_F64, T2, s, T2, s, stream));     // R_R^{-1} (.)
+    SK_CUDA(launch_transpose_f64(s, T2, s, T1, s, stream));
+    SK_CUDA(launch_axpy_rows_f64(s, s, T1, s, U, ldu, stream));                     // U1 = U0 + E (R_R^T R_R)^{-1}
   }
   return SKEL_OK;
+}
+
+skel_status skel_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
+                     int32_t s, const int32_t* Js, int32_t* Is, int rows_given, double* U,
+                     int64_t ldu, double* sq_norms, void* ws, size_t* ws_bytes,
+                     int32_t* dev_status, cudaStream_t stream) {
+  return cur_impl(m, n, dtype, A, lda, s, Js, Is, rows_given, U, ldu, sq_norms, false, ws, ws_bytes, dev_status,
+                  stream);
+}
+
+skel_status skel_cur_refine(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda,
+                            int32_t s, const int32_t* Js, int32_t* Is, int rows_given, double* U,
+                            int64_t ldu, double* sq_norms, void* ws, size_t* ws_bytes,
+                            int32_t* dev_status, cudaStream_t stream) {
+  return cur_impl(m, n, dtype, A, lda, s, Js, Is, rows_given, U, ldu, sq_norms, true, ws, ws_bytes, dev_status,
+                  stream);
 }
 
 skel_status skel_id_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64_t lda, int32_t s,

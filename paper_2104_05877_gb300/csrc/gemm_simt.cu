@@ -304,6 +304,70 @@ __global__ void __launch_bounds__(256) syrk_ff_kernel(int s, int64_t n, const fl
     }
 }
 
+// out(r, c) = sum_k C(k, r) B(k, c) (s x n, FP64) for FP32 column-major C (m x s) and B
+// (m x n), every product split exactly into p + e and accumulated in a float-float pair (the
+// error-free transformations above): the products are exact and each sum keeps ~44 bits, on
+// the FP32 pipes.  64 x 64 output tiles; the K range split into chunks whose FP64 partials are
+// summed in chunk order (or, with one chunk, stored directly).
+__global__ void __launch_bounds__(256) gemm_tn_ff_kernel(int s, int64_t n, int64_t m, const float* C, int64_t ldc,
+                                                         const float* B, int64_t ldb, int64_t kchunk, double* out,
+                                                         int64_t ldo, int64_t part_stride) {
+  __shared__ float As[FF_BK][FF_T + 4], Bs[FF_BK][FF_T + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int r0 = blockIdx.y * FF_T;
+  const int64_t c0 = (int64_t)blockIdx.x * FF_T;
+  const int64_t k0 = (int64_t)blockIdx.z * kchunk;
+  const int64_t k1 = k0 + kchunk < m ? k0 + kchunk : m;
+  float hi[4][4], lo[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) hi[i][j] = lo[i][j] = 0.f;
+  for (int64_t kb = k0; kb < k1; kb += FF_BK) {
+#pragma unroll
+    for (int q = 0; q < FF_T * FF_BK / 256; ++q) {
+      const int e = q * 256 + tid;
+      const int r = e / FF_BK, k = e % FF_BK;
+      const int64_t gk = kb + k;
+      As[k][r] = (r0 + r < s && gk < k1) ? __ldg(C + gk + (int64_t)(r0 + r) * ldc) : 0.f;
+      Bs[k][r] = (c0 + r < n && gk < k1) ? __ldg(B + gk + (c0 + r) * ldb) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < FF_BK; ++k) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ff_add_prod(a[i], b[j], hi[i][j], lo[i][j]);
+    }
+    __syncthreads();
+  }
+  double* o = out + (int64_t)blockIdx.z * part_stride;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = r0 + ty * 4 + i;
+      const int64_t c = c0 + tx * 4 + j;
+      if (r < s && c < n) o[(int64_t)r * ldo + c] = (double)hi[i][j] + (double)lo[i][j];
+    }
+}
+
+// out(r, c) = sum_z part[z][r][c] in chunk order (s x n)
+__global__ void ff_reduce_kernel(int s, int64_t n, int P, const double* part, double* out, int64_t ldo) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)s * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double a = 0.0;
+    for (int z = 0; z < P; ++z) a += part[(int64_t)z * s * n + e];
+    out[(e / n) * ldo + e % n] = a;
+  }
+}
+
 // H(r, c) = H(c, r) = sum over chunks of part[z][r][c] (upper entries, chunk order)
 __global__ void syrk_ff_reduce_kernel(int s, int P, const double* part, double* H, int64_t ldh) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)s * s;
@@ -509,6 +573,42 @@ cudaError_t launch_syrk_ff(int32_t s, int64_t n, const float* R, int64_t ldr, do
   syrk_ff_reduce_kernel<<<(unsigned)std::min<int64_t>(((int64_t)s * s + 255) / 256, 1024), 256, 0, st>>>(s, P, part,
                                                                                                           H, ldh);
   note_launches(2);
+  return cudaGetLastError();
+}
+
+static int gemm_tn_ff_chunks(int32_t s, int64_t n, int64_t m) {
+  const int64_t tiles = ((s + FF_T - 1) / FF_T) * ((n + FF_T - 1) / FF_T);
+  const int64_t want = 2 * (int64_t)device_sm_count();
+  int64_t P = tiles >= want ? 1 : (want + tiles - 1) / tiles;
+  P = std::min<int64_t>(P, std::max<int64_t>(1, m / 256));
+  return (int)std::min<int64_t>(P, 64);
+}
+
+size_t gemm_tn_ff_workspace(int64_t m, int64_t n, int32_t s) {
+  const int P = gemm_tn_ff_chunks(s, n, m);
+  return P > 1 ? align_up(sizeof(double) * (size_t)P * s * n) : 0;
+}
+
+cudaError_t launch_gemm_tn_ff(int64_t m, int64_t n, int32_t s, const float* C, int64_t ldc, const float* B,
+                              int64_t ldb, double* out, int64_t ldo, void* ws, const char* timer, cudaStream_t st) {
+  if (s <= 0 || n <= 0) return cudaSuccess;
+  const int P = gemm_tn_ff_chunks(s, n, m);
+  const int64_t chunk = ((m + P - 1) / P + FF_BK - 1) / FF_BK * FF_BK;
+  const int Pz = (int)((m + chunk - 1) / chunk);
+  const int64_t gx = (n + FF_T - 1) / FF_T;
+  if (gx > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)gx, (unsigned)((s + FF_T - 1) / FF_T), (unsigned)std::max(Pz, 1));
+  double* dst = Pz > 1 ? static_cast<double*>(ws) : out;
+  {
+    KernelTimer kt(timer ? timer : "gemm_simt", st);
+    gemm_tn_ff_kernel<<<grid, 256, 0, st>>>(s, n, m, C, ldc, B, ldb, chunk, dst, Pz > 1 ? n : ldo, (int64_t)s * n);
+  }
+  note_launches(1);
+  if (Pz > 1) {
+    ff_reduce_kernel<<<(unsigned)std::min<int64_t>(((int64_t)s * n + 255) / 256, 4096), 256, 0, st>>>(
+        s, n, Pz, static_cast<const double*>(ws), out, ldo);
+    note_launches(1);
+  }
   return cudaGetLastError();
 }
 

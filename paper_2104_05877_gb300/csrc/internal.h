@@ -95,6 +95,19 @@ cudaError_t launch_trsm_upper(int32_t s, int64_t N, const double* R, int64_t ldr
                               skel_dtype b_dt, const void* B, int64_t ldb, double* Y, int64_t ldy,
                               cudaStream_t st);
 
+// Y = R^{-T} D in place (D s x N row-major FP64, ldd) for an s x s upper triangular FP64 R,
+// through U = J R^T J (s x s scratch) and the upper solve on the rows in reverse order.
+cudaError_t launch_trsm_upper_t(int32_t s, int64_t N, const double* R, int64_t ldr, double* U, double* D,
+                                int64_t ldd, cudaStream_t st);
+// Z += X for s x n row-major FP64 matrices.
+cudaError_t launch_axpy_rows_f64(int32_t s, int64_t n, const double* X, int64_t ldx, double* Z, int64_t ldz,
+                                 cudaStream_t st);
+// out = C^T B (s x n row-major FP64, ldo) for FP32 column-major C (m x s) and B (m x n): exact
+// products, float-float sums (~44 bits); workspace gemm_tn_ff_workspace bytes.
+size_t gemm_tn_ff_workspace(int64_t m, int64_t n, int32_t s);
+cudaError_t launch_gemm_tn_ff(int64_t m, int64_t n, int32_t s, const float* C, int64_t ldc, const float* B,
+                              int64_t ldb, double* out, int64_t ldo, void* ws, const char* timer, cudaStream_t st);
+
 // sqrt(lambda_max(G)) for a symmetric positive definite s x s FP64 G (row-major): trace
 // normalisation and repeated squaring, then power iteration in one CTA.  Writes *out.
 size_t power_scratch_bytes(int32_t s);

@@ -529,6 +529,16 @@ __global__ void __launch_bounds__(kTrailThreads) lupp_trail_kernel(const PanelPa
     if (u < nrows) x[(int64_t)u * p.n] = v[u];
 }
 
+// The trailing update of one panel (rows trow0 .. trow0+rows-1 of Xg).
+template <typename T>
+cudaError_t launch_trail(const PanelParams<T>& p, int rows, cudaStream_t st) {
+  dim3 grid((unsigned)((p.n + kTrailThreads - 1) / kTrailThreads), (unsigned)((rows + kTrailRows - 1) / kTrailRows));
+  KernelTimer kt("lupp_trail", st);
+  lupp_trail_kernel<T><<<grid, kTrailThreads, 0, st>>>(p);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void lupp_panel_init_kernel(const T* X, int64_t ldx, int s, int64_t n, T* Xg,
                                        unsigned char* sel, int32_t* fail, T* L, int64_t ldl) {
@@ -808,14 +818,7 @@ skel_status run_panel_t(const PanelPlan& pl, const T* X, int64_t n, int64_t ldx,
     }
     note_launches(1);
     const int rows = s - t0 - p.b;
-    if (rows > 0) {
-      dim3 grid((unsigned)((n + kTrailThreads - 1) / kTrailThreads), (unsigned)((rows + kTrailRows - 1) / kTrailRows));
-      {
-        KernelTimer kt("lupp_trail", st);
-        lupp_trail_kernel<T><<<grid, kTrailThreads, 0, st>>>(p);
-      }
-      note_launches(1);
-    }
+    if (rows > 0 && launch_trail<T>(p, rows, st) != cudaSuccess) return SKEL_ERR_CUDA;
   }
   return cudaGetLastError() == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
 }
@@ -912,14 +915,7 @@ skel_status run_skeleton_t(const PanelPlan& pc, const PanelPlan& pr, const T* X,
     c.trows = s - t0 - c.b;
     if (launch_panel<T>(c, pc, st) != cudaSuccess) return SKEL_ERR_CUDA;
     if (cudaEventRecord(aux->col[k], st) != cudaSuccess) return SKEL_ERR_CUDA;
-    if (c.trows > 0) {
-      dim3 grid((unsigned)((n + kTrailThreads - 1) / kTrailThreads), (unsigned)((c.trows + kTrailRows - 1) / kTrailRows));
-      {
-        KernelTimer kt("lupp_trail", st);
-        lupp_trail_kernel<T><<<grid, kTrailThreads, 0, st>>>(c);
-      }
-      note_launches(1);
-    }
+    if (c.trows > 0 && launch_trail<T>(c, c.trows, st) != cudaSuccess) return SKEL_ERR_CUDA;
   }
   // row chain on the auxiliary stream
   if (cudaStreamWaitEvent(aux->st, aux->fork, 0) != cudaSuccess) return SKEL_ERR_CUDA;

@@ -619,124 +619,121 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
   QrPanelParams<T> p{};
   p.Cw = Cw; p.m = m; p.ldw = m; p.s = s; p.mloc = pl.mloc;
   p.V = V; p.ldv = ldv; p.VT = VT; p.VTN = VTN; p.R = R; p.ldr = ldr; p.fail = fail; p.dev_status = dev_status;
-  for (int t0 = 0; t0 < s; t0 += pl.b) {
-    p.t0 = t0;
-    p.b = std::min(pl.b, s - t0);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(pl.CL);
-    cfg.blockDim = dim3(kQrThreads);
-    cfg.dynamicSmemBytes = qr_panel_smem<T>(p.b, pl.mloc);
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = pl.CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    {
-      KernelTimer kt("qr_panel", st);
-      if (cudaLaunchKernelEx(&cfg, qr_panel_kernel<T>, p) != cudaSuccess) return SKEL_ERR_CUDA;
-    }
-    // G = V_p^T V_p, then V_p T_p^T and V_p T_p over the rows t0..
-    {
-      const T* Vp = V + t0 + (int64_t)t0 * ldv;
-      if (tc) {
-        if (launch_gemm_tc_tn(m - t0, p.b, p.b, reinterpret_cast<const float*>(Vp), ldv,
-                              reinterpret_cast<const float*>(Vp), ldv, reinterpret_cast<float*>(Gp), p.b, nullptr, kws,
-                              dev_status, st, "gemm_qr") != cudaSuccess)
-          return SKEL_ERR_CUDA;
-      } else {
-        GemmArgs g{};
-        g.M = p.b; g.N = p.b; g.K = m - t0;
-        g.L = View{Vp, ldv, 1}; g.l_dt = dt;
-        g.B = View{Vp, 1, ldv}; g.b_dt = dt;
-        g.out = Gp; g.out_sr = p.b; g.out_sc = 1; g.out_dt = dt;
-        g.alpha = 1.0;
-        g.splitk_ws = kws;
-        g.timer = "gemm_qr";
-        if (launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, st) != cudaSuccess) return SKEL_ERR_CUDA;
-      }
-      const size_t wsm = qr_wy_smem<T>(p.b);
-      if (cudaFuncSetAttribute(qr_wy_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm) != cudaSuccess)
-        return SKEL_ERR_CUDA;
-      KernelTimer kt("qr_wy", st);
-      qr_wy_kernel<T><<<(unsigned)((m - t0 + kWyRows - 1) / kWyRows), kWyRows, wsm, st>>>(V, ldv, m, t0, p.b, Gp, VT,
-                                                                                            VTN);
-      note_launches(1);
-    }
-    note_launches(1);
-    const int ntr = s - t0 - p.b;
-    if (ntr <= 0) continue;
-    // W = V_p^T C(t0:, t0+b:)  (b x ntr, row-major)
-    T* Crest = Cw + t0 + (int64_t)(t0 + p.b) * m;
+  // G = V_p^T V_p over rows t0.. for the b reflectors starting at column t0, then (qr_wy_kernel)
+  // V_p T_p^T into VT and V_p T_p into VTN(:, t0 : t0+b).
+  auto wy = [&](int t0, int b) -> skel_status {
+    const T* Vp = V + t0 + (int64_t)t0 * ldv;
     if (tc) {
-      if (launch_gemm_tc_tn(m - t0, ntr, p.b, reinterpret_cast<const float*>(V + t0 + (int64_t)t0 * ldv), ldv,
-                            reinterpret_cast<const float*>(Crest), m, reinterpret_cast<float*>(Wt), ntr, nullptr, kws,
-                            dev_status, st, "gemm_qr") != cudaSuccess)
+      if (launch_gemm_tc_tn(m - t0, b, b, reinterpret_cast<const float*>(Vp), ldv, reinterpret_cast<const float*>(Vp),
+                            ldv, reinterpret_cast<float*>(Gp), b, nullptr, kws, dev_status, st, "gemm_qr") != cudaSuccess)
         return SKEL_ERR_CUDA;
-      // C(t0:, t0+b:) -= (V_p T_p^T) W
-      if (launch_rank_update_f32(m - t0, ntr, p.b, reinterpret_cast<const float*>(VT + t0), m,
-                                 reinterpret_cast<const float*>(Wt), ntr, reinterpret_cast<float*>(Crest), m, -1.0f,
-                                 "gemm_qr", st) != cudaSuccess)
+    } else {
+      GemmArgs g{};
+      g.M = b; g.N = b; g.K = m - t0;
+      g.L = View{Vp, ldv, 1}; g.l_dt = dt;
+      g.B = View{Vp, 1, ldv}; g.b_dt = dt;
+      g.out = Gp; g.out_sr = b; g.out_sc = 1; g.out_dt = dt;
+      g.alpha = 1.0;
+      g.splitk_ws = kws;
+      g.timer = "gemm_qr";
+      if (launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, st) != cudaSuccess) return SKEL_ERR_CUDA;
+    }
+    const size_t wsm = qr_wy_smem<T>(b);
+    if (cudaFuncSetAttribute(qr_wy_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm) != cudaSuccess)
+      return SKEL_ERR_CUDA;
+    KernelTimer kt("qr_wy", st);
+    qr_wy_kernel<T><<<(unsigned)((m - t0 + kWyRows - 1) / kWyRows), kWyRows, wsm, st>>>(V, ldv, m, t0, b, Gp, VT, VTN);
+    note_launches(1);
+    return cudaGetLastError() == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
+  };
+  // Y (b x N, row-major, ld N) = V_p^T E(t0:, 0:N), then E(t0:, 0:N) -= L Y with L = the
+  // (m - t0) x b block at Lm (leading dimension m): applies the block reflector to N columns.
+  auto apply = [&](int t0, int b, const T* Lm, T* E, int64_t lde, int64_t N) -> skel_status {
+    if (N <= 0) return SKEL_OK;
+    const T* Vp = V + t0 + (int64_t)t0 * ldv;
+    if (tc) {
+      if (launch_gemm_tc_tn(m - t0, N, b, reinterpret_cast<const float*>(Vp), ldv, reinterpret_cast<const float*>(E),
+                            lde, reinterpret_cast<float*>(Wt), N, nullptr, kws, dev_status, st, "gemm_qr") != cudaSuccess ||
+          launch_rank_update_f32(m - t0, N, b, reinterpret_cast<const float*>(Lm), m, reinterpret_cast<const float*>(Wt),
+                                 N, reinterpret_cast<float*>(E), lde, -1.0f, "gemm_qr", st) != cudaSuccess)
         return SKEL_ERR_CUDA;
-      continue;
+      return SKEL_OK;
     }
     GemmArgs g{};
-    g.M = p.b; g.N = ntr; g.K = m - t0;
-    g.L = View{V + t0 + (int64_t)t0 * ldv, ldv, 1}; g.l_dt = dt;      // V_p^T(r, k) = V(t0+k, t0+r)
-    g.B = View{Crest, 1, m}; g.b_dt = dt;
-    g.out = Wt; g.out_sr = ntr; g.out_sc = 1; g.out_dt = dt;
+    g.M = b; g.N = N; g.K = m - t0;
+    g.L = View{Vp, ldv, 1}; g.l_dt = dt;                // V_p^T(r, k) = V(t0+k, t0+r)
+    g.B = View{E, 1, lde}; g.b_dt = dt;
+    g.out = Wt; g.out_sr = N; g.out_sc = 1; g.out_dt = dt;
     g.alpha = 1.0;
     g.splitk_ws = kws;
     g.timer = "gemm_qr";
     if (launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, st) != cudaSuccess) return SKEL_ERR_CUDA;
-    // C(t0:, t0+b:) -= (V_p T_p^T) W
     GemmArgs h{};
-    h.M = m - t0; h.N = ntr; h.K = p.b;
-    h.L = View{VT + t0, 1, m}; h.l_dt = dt;
-    h.B = View{Wt, ntr, 1}; h.b_dt = dt;
-    h.out = Crest; h.out_sr = 1; h.out_sc = m; h.out_dt = dt;
+    h.M = m - t0; h.N = N; h.K = b;
+    h.L = View{Lm, 1, m}; h.l_dt = dt;
+    h.B = View{Wt, N, 1}; h.b_dt = dt;
+    h.out = E; h.out_sr = 1; h.out_sc = lde; h.out_dt = dt;
     h.alpha = -1.0;
     h.timer = "gemm_qr";
-    if (launch_gemm(h, f64, LEFT_LOAD, EPI_ACCUM, st) != cudaSuccess) return SKEL_ERR_CUDA;
+    return launch_gemm(h, f64, LEFT_LOAD, EPI_ACCUM, st) == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
+  };
+  // Super-panels of B columns (B a multiple of the cluster panel width b, at most kQrMaxB): a
+  // panel updates only the later columns of its super-panel; at the end of the super-panel
+  // its compact WY form (from V_B^T V_B) is applied once to every column to the right, and
+  // Q_C is formed one super-panel at a time.  Where m is large the cluster's shared memory
+  // limits b (12 columns at m = 65536), and B = 60 cuts the passes over the trailing columns
+  // and over Q five-fold.
+  const int B = pl.b * std::max(1, kQrMaxB / pl.b);
+  for (int T0 = 0; T0 < s; T0 += B) {
+    const int Bw = std::min(B, s - T0);
+    for (int t0 = T0; t0 < T0 + Bw; t0 += pl.b) {
+      p.t0 = t0;
+      p.b = std::min(pl.b, T0 + Bw - t0);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(pl.CL);
+      cfg.blockDim = dim3(kQrThreads);
+      cfg.dynamicSmemBytes = qr_panel_smem<T>(p.b, pl.mloc);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = pl.CL;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      {
+        KernelTimer kt("qr_panel", st);
+        if (cudaLaunchKernelEx(&cfg, qr_panel_kernel<T>, p) != cudaSuccess) return SKEL_ERR_CUDA;
+      }
+      note_launches(1);
+      const int nin = T0 + Bw - t0 - p.b;          // later columns of this super-panel
+      if (nin > 0 || p.b == Bw) {
+        const skel_status e = wy(t0, p.b);
+        if (e != SKEL_OK) return e;
+      }
+      if (nin > 0) {
+        const skel_status e = apply(t0, p.b, VT + t0, Cw + t0 + (int64_t)(t0 + p.b) * m, m, nin);
+        if (e != SKEL_OK) return e;
+      }
+    }
+    if (Bw > pl.b) {
+      const skel_status e = wy(T0, Bw);
+      if (e != SKEL_OK) return e;
+    }
+    const skel_status e = apply(T0, Bw, VT + T0, Cw + T0 + (int64_t)(T0 + Bw) * m, m, s - T0 - Bw);
+    if (e != SKEL_OK) return e;
   }
   if (Q == nullptr) return cudaGetLastError() == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
-  // Q_C = Q_0 Q_1 .. [I; 0] with Q_p = I - V_p T_p V_p^T, applied from the last panel:
-  // Y = V_p^T E(t0:, :), E(t0:, :) -= (V_p T_p) Y
+  // Q_C = Q_0 Q_1 .. [I; 0] with Q_B = I - V_B T_B V_B^T per super-panel, applied from the last:
+  // Y = V_B^T E(T0:, :), E(T0:, :) -= (V_B T_B) Y
   eye_kernel<T><<<dim3((unsigned)std::min<int64_t>((m + 255) / 256, 64), (unsigned)std::min(s, 1024)), 256, 0, st>>>(
       m, s, Q, ldq);
   note_launches(1);
-  const int np = (s + pl.b - 1) / pl.b;
-  for (int pi = np - 1; pi >= 0; --pi) {
-    const int t0 = pi * pl.b, b = std::min(pl.b, s - t0);
-    if (tc) {          // Y = V_p^T E(t0:, :) on the tensor cores, E(t0:, :) -= (V_p T_p) Y
-      if (launch_gemm_tc_tn(m - t0, s, b, reinterpret_cast<const float*>(V + t0 + (int64_t)t0 * ldv), ldv,
-                            reinterpret_cast<const float*>(Q + t0), ldq, reinterpret_cast<float*>(Wt), s, nullptr, kws,
-                            dev_status, st, "gemm_qr") != cudaSuccess ||
-          launch_rank_update_f32(m - t0, s, b, reinterpret_cast<const float*>(VTN + t0 + (int64_t)t0 * m), m,
-                                 reinterpret_cast<const float*>(Wt), s, reinterpret_cast<float*>(Q + t0), ldq, -1.0f,
-                                 "gemm_qr", st) != cudaSuccess)
-        return SKEL_ERR_CUDA;
-      continue;
-    }
-    GemmArgs g{};
-    g.M = b; g.N = s; g.K = m - t0;
-    g.L = View{V + t0 + (int64_t)t0 * ldv, ldv, 1}; g.l_dt = dt;       // V_p^T(r, k) = V(t0+k, t0+r)
-    g.B = View{Q + t0, 1, ldq}; g.b_dt = dt;
-    g.out = Wt; g.out_sr = s; g.out_sc = 1; g.out_dt = dt;
-    g.alpha = 1.0;
-    g.splitk_ws = kws;
-    g.timer = "gemm_qr";
-    if (launch_gemm(g, f64, LEFT_LOAD, EPI_STORE, st) != cudaSuccess) return SKEL_ERR_CUDA;
-    GemmArgs h{};
-    h.M = m - t0; h.N = s; h.K = b;
-    h.L = View{VTN + t0 + (int64_t)t0 * m, 1, m}; h.l_dt = dt;
-    h.B = View{Wt, s, 1}; h.b_dt = dt;
-    h.out = Q + t0; h.out_sr = 1; h.out_sc = ldq; h.out_dt = dt;
-    h.alpha = -1.0;
-    h.timer = "gemm_qr";
-    if (launch_gemm(h, f64, LEFT_LOAD, EPI_ACCUM, st) != cudaSuccess) return SKEL_ERR_CUDA;
+  const int nsp = (s + B - 1) / B;
+  for (int q = nsp - 1; q >= 0; --q) {
+    const int T0 = q * B, Bw = std::min(B, s - T0);
+    const skel_status e = apply(T0, Bw, VTN + T0 + (int64_t)T0 * m, Q + T0, ldq, s);
+    if (e != SKEL_OK) return e;
   }
   return cudaGetLastError() == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
 }

@@ -10,7 +10,7 @@
 //   MMA B operand = A tile (32 rows of A x 512 columns), K-major (A is column-major): for TF32
 //                   the 128-byte-swizzled FP32 tile exactly as TMA lands it; for BF16 a copy
 //                   converted into the 64-byte-swizzled BF16 layout.
-// Generation is shared: the CJ CTAs of a thread-block cluster (1 x CJ x 1, CJ in {1, 2, 4})
+// Generation is shared: the CJ CTAs of a thread-block cluster (1 x CJ x 1, CJ in {1, 2, 4, 8})
 // work on the same 128 Gamma rows and K-steps for CJ different column tiles of A.  Each CTA
 // generates 128/CJ rows of every Gamma tile and pushes them into its peers' shared memory
 // with bulk copies (cp.async.bulk shared::cta -> shared::cluster) that complete their bytes
@@ -282,7 +282,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap tmapA, const TcParams p) {
       } else if (calls == 512) {
 #pragma unroll
         for (int q = 0; q < 2; ++q) gen_call(gt + 256 * q);
-      } else {
+      } else if (gt < calls) {          // CJ = 8: 128 calls, warps 4 .. 7 of the generators idle
         gen_call(gt);
       }
       fence_proxy_async();
@@ -291,6 +291,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap tmapA, const TcParams p) {
         // this warp's rows: r0 + 4 w + 32 q .. + 3 for each q, contiguous per q
         const int w = gt >> 5;
         for (int q = 0; q * 256 < calls; ++q) {
+          if (4 * w + 32 * q >= rows_per) continue;                // rows outside this CTA's slice
           const uint32_t src = smem_u32(g) + (uint32_t)(r0 + 4 * w + 32 * q) * C::G_ROW;
           for (int pr = 0; pr < CJ; ++pr)
             if (pr != crank) bulk_copy_to_peer(src, 4 * C::G_ROW, full_g(s), pr);
@@ -404,7 +405,7 @@ struct TcPlan {
 // Resident clusters of CJ CTAs of the kernel (0 if that cluster shape cannot be launched).
 template <int OP, int GEN>
 int active_clusters(int CJ) {
-  static int cache[5] = {-1, -1, -1, -1, -1};
+  static int cache[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
   if (cache[CJ] >= 0) return cache[CJ];
   int nc = 0;
   if (cudaFuncSetAttribute(sketch_tc_kernel<OP, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -434,6 +435,10 @@ TcPlan plan_tc(int64_t m, int64_t n, int l) {
   pl.jtiles = (int)((n + TC_N - 1) / TC_N);
   pl.CJ = 1;
   int slots = device_sm_count();
+  // Clusters of 4 along the column tiles share each Gamma tile.  Clusters of 8 (supported by
+  // the generator) halve the generation per flop but were measured slower at 65536 x 32768,
+  // l = 1100 (TF32 7.7 -> 11.0 ms, BF16 9.6 -> 12.9 ms): every stage waits for all eight CTAs'
+  // MMAs before it is refilled.
   for (int cj : {4, 2}) {
     if (pl.jtiles % cj != 0) continue;
     const int nc = active_clusters<OP, GEN>(cj);

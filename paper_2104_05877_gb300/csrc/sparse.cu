@@ -16,7 +16,8 @@ namespace skel {
 
 namespace {
 
-constexpr int CT = 32;       // columns of X per CTA
+constexpr int CT = 32;       // columns of X per CTA (dense A)
+constexpr int CT_CSC = 16;   // columns of X per CTA (CSC A)
 constexpr int JCH = 256;     // rows of A per table chunk
 
 // Pattern of rows row0 .. row0+m-1 of A (counters use the global row index).
@@ -97,28 +98,35 @@ __global__ void __launch_bounds__(256) sparse_csc_kernel(int64_t n, const int64_
                                                          int32_t l, int32_t zeta,
                                                          const int32_t* table, float* X, int64_t ldx,
                                                          float scale, int32_t* dev_status) {
+  // acc[cc * lda + r]: a column's l sums are contiguous (odd stride), so the lanes of a warp,
+  // which work on one column, add into banks spread by their random rows
   extern __shared__ __align__(16) unsigned char smem[];
   float* acc = reinterpret_cast<float*>(smem);
+  const int lda = l | 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const int64_t c0 = (int64_t)blockIdx.x * CT;
-  const int nc = (int)std::min<int64_t>(CT, n - c0);
-  for (int e = tid; e < l * CT; e += blockDim.x) acc[e] = 0.f;
+  const int64_t c0 = (int64_t)blockIdx.x * CT_CSC;
+  const int nc = (int)std::min<int64_t>(CT_CSC, n - c0);
+  for (int e = tid; e < lda * CT_CSC; e += blockDim.x) acc[e] = 0.f;
   __syncthreads();
   for (int cc = warp; cc < nc; cc += nwarps) {
     const int64_t b = col_ptr[c0 + cc], e_ = col_ptr[c0 + cc + 1];
+    float* ac = acc + cc * lda;
     for (int64_t k = b + lane; k < e_; k += 32) {
-      const int64_t j = row_idx[k];
-      const float v = val[k];
+      const int64_t j = __ldg(row_idx + k);
+      const float v = __ldg(val + k);
       const int32_t* tj = table + j * zeta;
-      for (int q = 0; q < zeta; ++q) scatter(acc, __ldg(tj + q), cc, v);
+      for (int q = 0; q < zeta; ++q) {
+        const int32_t code = __ldg(tj + q);
+        atomicAdd(&ac[code & 0x7fffffff], code < 0 ? -v : v);
+      }
     }
   }
   __syncthreads();
   bool bad = false;
-  for (int e = tid; e < l * CT; e += blockDim.x) {
-    const int r = e / CT, cc = e % CT;
+  for (int e = tid; e < l * CT_CSC; e += blockDim.x) {
+    const int r = e / CT_CSC, cc = e % CT_CSC;
     if (cc < nc) {
-      const float v = acc[e] * scale;
+      const float v = acc[cc * lda + r] * scale;
       bad |= !isfinite(v);
       X[(int64_t)r * ldx + c0 + cc] = v;
     }
@@ -197,11 +205,14 @@ cudaError_t launch_sparse_sketch_csc(int64_t m, int64_t n, const int64_t* col_pt
                                      int32_t zeta, const int32_t* table, float* X, int64_t ldx,
                                      int32_t* dev_status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  const size_t smem = sizeof(float) * (size_t)l * CT;
+  const size_t smem = sizeof(float) * (size_t)(l | 1) * CT_CSC;
   cudaError_t e = cudaFuncSetAttribute(sparse_csc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  sparse_csc_kernel<<<(unsigned)((n + CT - 1) / CT), 256, smem, st>>>(
-      n, col_ptr, row_idx, val, l, zeta, table, X, ldx, (float)(1.0 / sqrt((double)zeta)), dev_status);
+  {
+    KernelTimer kt("sparse_csc", st);
+    sparse_csc_kernel<<<(unsigned)((n + CT_CSC - 1) / CT_CSC), 256, smem, st>>>(
+        n, col_ptr, row_idx, val, l, zeta, table, X, ldx, (float)(1.0 / sqrt((double)zeta)), dev_status);
+  }
   note_launches(1);
   return cudaGetLastError();
 }

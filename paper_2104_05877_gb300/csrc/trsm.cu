@@ -225,6 +225,45 @@ __global__ void eta_finalize_kernel(const double* logs, int q, double* out) {
 
 }  // namespace
 
+// U(i, j) = R(s-1-j, s-1-i) for j >= i, 0 below: with J the order-reversing permutation,
+// U = J R^T J is upper triangular, and R^T Y = D is U (J Y) = J D.
+__global__ void flip_transpose_kernel(int s, const double* R, int64_t ldr, double* U, int64_t ldu) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)s * s;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / s), j = (int)(e % s);
+    U[(int64_t)i * ldu + j] = j >= i ? R[(int64_t)(s - 1 - j) * ldr + (s - 1 - i)] : 0.0;
+  }
+}
+
+__global__ void axpy_rows_kernel(int s, int64_t n, const double* X, int64_t ldx, double* Z, int64_t ldz) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)s * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / n, c = e % n;
+    Z[r * ldz + c] += X[r * ldx + c];
+  }
+}
+
+cudaError_t launch_trsm_upper_t(int32_t s, int64_t N, const double* R, int64_t ldr, double* U, double* D,
+                                int64_t ldd, cudaStream_t st) {
+  if (N <= 0 || s <= 0) return cudaSuccess;
+  flip_transpose_kernel<<<(unsigned)std::min<int64_t>(((int64_t)s * s + 255) / 256, 1024), 256, 0, st>>>(s, R, ldr,
+                                                                                                        U, s);
+  note_launches(1);
+  if (cudaGetLastError() != cudaSuccess) return cudaErrorLaunchFailure;
+  // rows taken from the last one up (negative leading dimension): J D in, J Y out
+  double* last = D + (int64_t)(s - 1) * ldd;
+  return launch_trsm_upper(s, N, U, s, 0, SKEL_F64, last, -ldd, last, -ldd, st);
+}
+
+cudaError_t launch_axpy_rows_f64(int32_t s, int64_t n, const double* X, int64_t ldx, double* Z, int64_t ldz,
+                                 cudaStream_t st) {
+  if (s <= 0 || n <= 0) return cudaSuccess;
+  axpy_rows_kernel<<<(unsigned)std::min<int64_t>(((int64_t)s * n + 255) / 256, 4096), 256, 0, st>>>(s, n, X, ldx, Z,
+                                                                                                   ldz);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_trsm_upper(int32_t s, int64_t N, const double* R, int64_t ldr, int unit_diag,
                               skel_dtype b_dt, const void* B, int64_t ldb, double* Y, int64_t ldy,
                               cudaStream_t st) {

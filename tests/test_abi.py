@@ -43,6 +43,14 @@ def test_status_strings(L):
 
 def test_invalid_arguments_rejected_on_host(L):
     sz = ctypes.c_size_t(0)
+    # measurement aids: unknown kind, too few rounds, a 3-CTA cluster, an unaligned column
+    ns = ctypes.c_void_p(16)
+    assert L.skel_debug_exchange_latency(2, 8, 100, 0, ns, None, ctypes.byref(sz), None, None) == 1
+    assert L.skel_debug_exchange_latency(1, 8, 1, 0, ns, None, ctypes.byref(sz), None, None) == 1
+    assert L.skel_debug_exchange_latency(1, 3, 100, 0, ns, None, ctypes.byref(sz), None, None) == 1
+    assert L.skel_debug_exchange_latency(1, 8, 100, 6, ns, None, ctypes.byref(sz), None, None) == 1
+    fl = ctypes.c_int64(0)
+    assert L.skel_debug_fma_rate(1, 0, ctypes.byref(fl), ns, None) == 1
     # l = 0
     assert L.skel_sketch(10, 10, 0, ctypes.c_void_p(16), 10, 0, 0, 8, 0, 1, ctypes.c_void_p(16), 10,
                          None, ctypes.byref(sz), None, None) == 1

@@ -6,6 +6,10 @@ elementwise on samples (TF32 bound), the device's pivots against the oracle's LU
 device's sketch before the first near-tie at FP32 level, and the ID error within 1.05x of
 the FP64 oracle's.
 
+Config 3 (262144 x 4096 SNN-style CSC, ~1% dense, k = 256, l = 512, sparse sign with zeta = 8):
+the oracle runs end to end on the same FP32 values with scipy sparse products: the device's
+sketch elementwise, its pivots before the first near-tie, and the CUR error within 1.05x.
+
 Config 5 (65536 x 32768 FP32, k = 1024, l = 1100): too large for the oracle end to end, so the
 checks are ones that hold at any size: sampled sketch entries computed one by one by the
 oracle, the LUPP factor's structure (|R| <= 1, R(t, j_t) = 1, X(0:s, J) = L R(:, J)), the first
@@ -16,9 +20,10 @@ closed-form best rank-k error of the constructed spectrum.
 
 import numpy as np
 import pytest
+import scipy.sparse as sp
 import torch
 
-from oracle import embedding, pivoting
+from oracle import decomp, embedding, errors, pivoting, sketch
 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -137,3 +142,52 @@ def test_config5_full_size_properties(skel, dev):
     tail = np.sum(sig[k:] ** 2) + (1e-7) ** 2 * n
     best = np.sqrt(tail / (np.sum(sig ** 2) + (1e-7) ** 2 * n))
     assert _rel_id(sq) <= 5.0 * best
+
+
+def test_config3_full_size_sparse_sign_and_cur(skel, dev):
+    m, n, r = 262144, 4096, 300
+    k, l, zeta = 256, 512, 8
+    seed_G = workloads.seed_for(3, "gamma")
+    A = workloads.snn_csc(m, n, r, seed=workloads.seed_for(3))          # FP32 CSC, ~1% dense
+    col_ptr = torch.from_numpy(A.indptr.astype(np.int64)).to(dev)
+    row_idx = torch.from_numpy(A.indices.astype(np.int32)).to(dev)
+    val = torch.from_numpy(A.data.astype(np.float32)).to(dev)
+    X, st = skel.sketch_csc(col_ptr, row_idx, val, m, n, l, seed=seed_G, zeta=zeta)
+    Js, _, _, _ = skel.pivot_lupp(X, k, factors=False, status=st)
+    torch.cuda.synchronize()
+    skel.check_status(st)
+    A64 = A.astype(np.float64)
+    # the sketch: A >= 0, so |Gamma| |A| is the sketch with every sign +; FP32 accumulation of
+    # at most nnz(A(:, j)) terms in any order bounds each entry of column j
+    Xo = sketch.sparse_sign_sketch(A64, l, zeta, seed_G)
+    rows, _ = embedding.sparse_sign_pattern(l, m, zeta, seed_G)
+    Gabs = sp.csr_matrix((np.full(m * zeta, 1.0 / np.sqrt(zeta)), (rows.ravel(), np.repeat(np.arange(m), zeta))),
+                         shape=(l, m))
+    mag = np.asarray((Gabs @ A64).todense())
+    Xg = X.cpu().double().numpy()
+    nnz_col = np.diff(A.indptr).astype(np.float64)
+    assert np.all(np.abs(Xg - Xo) <= (nnz_col[None, :] + 1) * 2.0 ** -23 * mag + 1e-30)
+    # pivots: the oracle's LUPP on the device's sketch, equal before the first relative gap
+    # below 1e3 FP32 roundings
+    ref = pivoting.lupp_columns(Xg, k)
+    small = np.flatnonzero(ref["gaps"] < 1e3 * 2.0 ** -23)
+    pre = int(small[0]) if small.size else k
+    assert pre >= 16
+    J = Js.cpu().numpy()
+    assert np.array_equal(J[:pre], ref["Js"][:pre])
+    # CUR on the densified A (column-major FP32 on the device): rows by LUPP on C, stable U
+    cols = torch.repeat_interleave(torch.arange(n, device=dev), col_ptr[1:] - col_ptr[:-1])
+    At = torch.zeros(n, m, dtype=torch.float32, device=dev)
+    At[cols, row_idx.long()] = val
+    Ad = At.t()
+    Is, U, _, st = skel.cur(Ad, Js)
+    e, _ = skel.error(Ad, Js, Is=Is, U=U, status=st)
+    skel.check_status(st)
+    e = e.cpu().numpy()
+    e_gpu = float(e[2] / e[0])
+    # the oracle end to end: its own sketch and pivots, rows by LUPP on C, stable CUR
+    Jo = pivoting.lupp_columns(Xo, k)["Js"]
+    Io = pivoting.lupp_rows(A64[:, Jo].toarray(), k)["Js"]
+    e_or = errors.rel_cur_error(A64, Jo, decomp.cur(A64, Jo, Io), Io)
+    assert e_gpu <= 1.05 * e_or, (e_gpu, e_or)
+

@@ -199,3 +199,21 @@ def test_cur_sketch_2x2_closed_form():
     want = np.array([[6.0, -3.0], [-9.0, 4.0]]) / det
     assert np.allclose(decomp.cur_sketch(A, Js, Is), want, atol=1e-14)
     assert np.allclose(A[np.ix_(Is, Js)], S)
+
+
+def test_cur_and_its_error_agree_for_sparse_and_dense_input():
+    """The sparse form of the stable CUR and of the direct residual (used for the tall sparse
+    configuration) equal the dense forms on the same matrix."""
+    import scipy.sparse as sps
+    A = workloads.snn_csc(700, 300, 12, seed=6, density=0.1).astype(np.float64)
+    Ad = A.toarray()
+    k = 10
+    X = sketch.sparse_sign_sketch(A, 2 * k, 4, 3)
+    Js = pivoting.lupp_columns(X, k)["Js"]
+    Is = pivoting.lupp_rows(Ad[:, Js], k)["Js"]
+    U_s, U_d = decomp.cur(A, Js, Is), decomp.cur(Ad, Js, Is)
+    assert np.allclose(U_s, U_d, rtol=1e-10, atol=1e-12 * np.abs(U_d).max())
+    e_s, e_d = errors.rel_cur_error(A, Js, U_d, Is), errors.rel_cur_error(Ad, Js, U_d, Is)
+    assert abs(e_s - e_d) <= 1e-12 * max(e_d, 1e-300)
+    assert sps.issparse(A)
+
