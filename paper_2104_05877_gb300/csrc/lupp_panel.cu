@@ -529,12 +529,114 @@ __global__ void __launch_bounds__(kTrailThreads) lupp_trail_kernel(const PanelPa
     if (u < nrows) x[(int64_t)u * p.n] = v[u];
 }
 
-// The trailing update of one panel (rows trow0 .. trow0+rows-1 of Xg).
+// The same trailing update as a register-blocked rank-b update: a CTA takes 64 trailing rows
+// x 128 columns, stages M's rows (transposed, [q][row]) and R's panel rows ([q][column]) in
+// shared memory, and each thread keeps an 8 x 4 block of Xg in registers: per step q two
+// 16-byte loads of multipliers (a warp broadcast) and one of R feed 32 multiply-subtract pairs
+// (about two instructions per entry and step, against three).  Every entry still sees
+// x = x - M(r, q) R(t0 + q, j) for q = 0 .. b-1 in order with separately rounded multiply and
+// subtract, so the results equal the column kernel's bit for bit.  Columns selected by this or
+// an earlier panel are updated too: from this panel on their R entries are 0 (earlier pivots)
+// or belong to this panel's pivot columns, and those trailing entries are never read again.
+constexpr int TT_R = 64, TT_C = 128, TT_THREADS = 256;
+
+template <typename T>
+size_t trail_tile_smem() { return sizeof(T) * (size_t)kMaxPanel * (TT_R + TT_C); }
+
+template <typename T>
+__device__ __forceinline__ void load4(const T* p, int64_t c, int64_t n, bool vec, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    if (vec && c + 3 < n) {
+      const float4 q = *reinterpret_cast<const float4*>(p);
+      v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+      return;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) v[u] = c + u < n ? p[u] : T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ void store4(T* p, int64_t c, int64_t n, bool vec, const T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    if (vec && c + 3 < n) {
+      *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+      return;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (c + u < n) p[u] = v[u];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TT_THREADS) lupp_trail_tile_kernel(const PanelParams<T> p) {
+  extern __shared__ __align__(16) unsigned char tsm[];
+  T* Ms = reinterpret_cast<T*>(tsm);                   // [b][TT_R]: Ms[q][rr] = M(r0 + rr, q)
+  T* Rs = Ms + (size_t)kMaxPanel * TT_R;               // [b][TT_C]: Rs[q][cc] = R(t0 + q, c0 + cc)
+  const int b = p.b;
+  const int r0 = blockIdx.y * TT_R;
+  const int64_t c0 = (int64_t)blockIdx.x * TT_C;
+  const int rows = p.trows;
+  if (r0 >= rows) return;
+  if (*(volatile int32_t*)p.fail) return;
+  const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;    // rows ty*8 .. +7, columns tx*4 .. +3
+  // the block of Xg is loaded first: its loads are in flight while M and R are staged
+  const bool vec = (p.n & 3) == 0;
+  const int64_t c = c0 + tx * 4;
+  T v[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = r0 + ty * 8 + i;
+    if (r < rows && c < p.n) load4<T>(p.Xg + (p.trow0 + r) * p.n + c, c, p.n, vec, v[i]);
+    else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[i][u] = T(0);
+    }
+  }
+  for (int e = tid; e < b * TT_R; e += TT_THREADS) {
+    const int rr = e / b, q = e % b;
+    Ms[q * TT_R + rr] = r0 + rr < rows ? p.M[(int64_t)(r0 + rr) * p.ldm + q] : T(0);
+  }
+  for (int e = tid; e < b * TT_C; e += TT_THREADS) {
+    const int q = e / TT_C, cc = e % TT_C;
+    Rs[q * TT_C + cc] = c0 + cc < p.n ? p.R[(int64_t)(p.t0 + q) * p.ldr + c0 + cc] : T(0);
+  }
+  __syncthreads();
+  for (int q = 0; q < b; ++q) {
+    T m[8], rv[4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) m[i] = Ms[q * TT_R + ty * 8 + i];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) rv[u] = Rs[q * TT_C + tx * 4 + u];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[i][u] = dsub(v[i][u], dmul(m[i], rv[u]));
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = r0 + ty * 8 + i;
+    if (r < rows && c < p.n) store4<T>(p.Xg + (p.trow0 + r) * p.n + c, c, p.n, vec, v[i]);
+  }
+}
+
+// The trailing update of one panel (rows trow0 .. trow0+rows-1 of Xg): the tiled kernel.
 template <typename T>
 cudaError_t launch_trail(const PanelParams<T>& p, int rows, cudaStream_t st) {
-  dim3 grid((unsigned)((p.n + kTrailThreads - 1) / kTrailThreads), (unsigned)((rows + kTrailRows - 1) / kTrailRows));
+  const int64_t gx = (p.n + TT_C - 1) / TT_C, gy = (rows + TT_R - 1) / TT_R;
+  if (gx > (int64_t)INT32_MAX || gy > 65535) {       // beyond the tiled grid: the column kernel
+    dim3 grid((unsigned)((p.n + kTrailThreads - 1) / kTrailThreads), (unsigned)((rows + kTrailRows - 1) / kTrailRows));
+    KernelTimer kt("lupp_trail", st);
+    lupp_trail_kernel<T><<<grid, kTrailThreads, 0, st>>>(p);
+    note_launches(1);
+    return cudaGetLastError();
+  }
+  const cudaError_t e = cudaFuncSetAttribute(lupp_trail_tile_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)trail_tile_smem<T>());
+  if (e != cudaSuccess) return e;
   KernelTimer kt("lupp_trail", st);
-  lupp_trail_kernel<T><<<grid, kTrailThreads, 0, st>>>(p);
+  lupp_trail_tile_kernel<T><<<dim3((unsigned)gx, (unsigned)gy), TT_THREADS, trail_tile_smem<T>(), st>>>(p);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -695,6 +797,218 @@ __global__ void lupp_row_init_kernel(int64_t n, int s, unsigned char* sel, int32
     sel[j] = 0;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < s; t += gridDim.x * blockDim.x) Is[t] = -1;
   if (blockIdx.x == 0 && threadIdx.x == 0) *fail = 0;
+}
+
+// ---------------------------------------------------------------------------------------
+// Grid-wide panels, for matrices too wide for a cluster panel (e.g. the row LUPP on a tall
+// C^T with 262144 columns): a persistent grid of G CTAs (all co-resident, cooperative launch),
+// CTA g holding columns [g nloc, (g+1) nloc) of the panel's b rows in shared memory.  Per step
+// every CTA publishes its best candidate (index, value, and its column below the step) to a
+// slot in global memory, arrives at the grid barrier and, after it, all CTAs take the same
+// winner (the largest magnitude, ties to the lower index: an atomicMax on a packed key for
+// FP32, a scan of the slots for FP64); R(t, :) is written and rows q+1 .. b-1 updated, row q+1
+// first so that the next candidate is published before the rest of the update.  The trailing
+// rows then get their multipliers (lupp_gmult_kernel: forward substitution with the panel's
+// R(panel, J_panel), warp per row) and the tiled trailing update; every entry sees the textbook
+// operations in the textbook order, as in the cluster path.
+struct GPanelParams {
+  int64_t n;
+  int s, t0, b, nloc;
+  unsigned char* sel;     // n flags (global): columns selected by earlier panels
+  unsigned char tag;      // flag value of this panel's pivot columns
+  int32_t* Js;
+  int32_t* fail;
+  int32_t* dev_status;
+  GridComm gc;
+};
+
+template <typename T>
+size_t gpanel_smem(int b, int nloc) {
+  auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+  return a16(sizeof(T) * (size_t)b * nloc) + a16(sizeof(T) * kMaxPanel) + a16(sizeof(T) * (size_t)nloc) + a16(nloc);
+}
+
+template <typename T>
+__device__ __forceinline__ KeyIdx<T> gp_best(const T* W, int nloc, int row, int nl, int64_t c0,
+                                             const unsigned char* sl) {
+  T key = T(-1);
+  int64_t idx = INT64_MAX;
+  for (int jj = threadIdx.x; jj < nl; jj += blockDim.x) {
+    if (sl[jj]) continue;
+    const T k = pivot_key(W[(int64_t)row * nloc + jj]);
+    if (better(k, c0 + jj, key, idx)) { key = k; idx = c0 + jj; }
+  }
+  return block_argmax<T>(key, idx);
+}
+
+// Slot layout: int64 index (-1: no candidate), T value, then the column rows 0 .. b-1.
+template <typename T>
+__device__ __forceinline__ void gp_publish(const GridComm& gc, int q, const KeyIdx<T>& c, const T* W, int nloc,
+                                           int64_t c0, int b) {
+  char* sl = gc.slot(q, blockIdx.x);
+  T* col = reinterpret_cast<T*>(sl + 16);
+  const bool have = c.idx != INT64_MAX && c.key >= T(0);
+  const int jb = have ? (int)(c.idx - c0) : 0;
+  if (have)
+    for (int r = q + threadIdx.x; r < b; r += blockDim.x) col[r] = W[(int64_t)r * nloc + jb];
+  if (threadIdx.x == 0) {
+    *reinterpret_cast<long long*>(sl) = have ? (long long)c.idx : -1ll;
+    *reinterpret_cast<T*>(sl + 8) = have ? W[(int64_t)q * nloc + jb] : T(0);
+    if constexpr (sizeof(T) == 4)
+      if (have) atomicMax(gc.keys + q, pack_key((float)c.key, c.idx));
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ int64_t gp_winner(const GridComm& gc, int q) {
+  if constexpr (sizeof(T) == 4) {
+    __shared__ long long s_w;
+    if (threadIdx.x == 0) {
+      const unsigned long long k = __ldcg(gc.keys + q);
+      s_w = k == 0ull ? -1 : key_index(k);
+    }
+    __syncthreads();
+    const long long w = s_w;
+    __syncthreads();
+    return w;
+  } else {
+    T key = T(-1);
+    int64_t idx = INT64_MAX;
+    for (int g = threadIdx.x; g < gc.G; g += blockDim.x) {
+      const char* sl = gc.slot(q, g);
+      const long long ci = __ldcg(reinterpret_cast<const long long*>(sl));
+      if (ci >= 0) {
+        const T kq = pivot_key(__ldcg(reinterpret_cast<const T*>(sl + 8)));
+        if (better(kq, (int64_t)ci, key, idx)) { key = kq; idx = ci; }
+      }
+    }
+    const KeyIdx<T> r = block_argmax<T>(key, idx);
+    return r.idx == INT64_MAX ? -1 : r.idx;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) lupp_gpanel_kernel(const GPanelParams p, T* Xg, T* R, int64_t ldr, T* L,
+                                                          int64_t ldl) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  if (*(volatile const int32_t*)p.fail) return;        // an earlier panel stopped: uniform over the grid
+  const int b = p.b, nloc = p.nloc, tid = threadIdx.x, bd = blockDim.x;
+  const int64_t c0 = (int64_t)blockIdx.x * nloc;
+  const int nl = (int)(p.n - c0 < 0 ? 0 : (p.n - c0 < nloc ? p.n - c0 : nloc));
+  auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+  T* W = reinterpret_cast<T*>(gsm);
+  T* pivcol = reinterpret_cast<T*>(gsm + a16(sizeof(T) * (size_t)b * nloc));
+  T* rowt = pivcol + kMaxPanel;
+  unsigned char* sl = reinterpret_cast<unsigned char*>(rowt) + a16(sizeof(T) * (size_t)nloc);
+  for (int q = 0; q < b; ++q)
+    for (int jj = tid; jj < nl; jj += bd) W[(int64_t)q * nloc + jj] = Xg[(int64_t)(p.t0 + q) * p.n + c0 + jj];
+  for (int jj = tid; jj < nloc; jj += bd) sl[jj] = jj < nl ? p.sel[c0 + jj] : (unsigned char)1;
+  __syncthreads();
+  auto stop = [&](int t, int code) {
+    if (blockIdx.x == 0 && tid == 0) {
+      record_error(p.dev_status, code, t);
+      atomicExch(p.fail, 1);
+    }
+    if (blockIdx.x == 0)
+      for (int r = t + tid; r < p.s; r += bd) p.Js[r] = -1;
+    if (tid == 0) atomicExch(p.gc.abort, 1);
+  };
+  gp_publish<T>(p.gc, 0, gp_best<T>(W, nloc, 0, nl, c0, sl), W, nloc, c0, b);
+  comm_arrive(p.gc, 0);
+  for (int q = 0; q < b; ++q) {
+    const int t = p.t0 + q;
+    if (!comm_wait(p.gc, q, p.dev_status)) {
+      if (blockIdx.x == 0 && tid == 0) atomicExch(p.fail, 1);
+      return;
+    }
+    const int64_t w = gp_winner<T>(p.gc, q);
+    if (w < 0) { stop(t, SKEL_ERR_RANK_DEFICIENT); return; }
+    const char* wsl = p.gc.slot(q, (int)(w / nloc));
+    const T piv = __ldcg(reinterpret_cast<const T*>(wsl + 8));
+    if (!isfinite(piv)) { stop(t, SKEL_ERR_NONFINITE); return; }
+    if (piv == T(0)) { stop(t, SKEL_ERR_RANK_DEFICIENT); return; }
+    const T* wcol = reinterpret_cast<const T*>(wsl + 16);
+    for (int r = q + tid; r < b; r += bd) pivcol[r] = __ldcg(wcol + r);
+    if (blockIdx.x == 0 && tid == 0) p.Js[t] = (int32_t)w;
+    const int jw = (w >= c0 && w < c0 + nl) ? (int)(w - c0) : -1;
+    for (int jj = tid; jj < nl; jj += bd) {          // R(t, :): row q is final at step q
+      T rv;
+      if (jj == jw) rv = T(1);
+      else if (sl[jj]) rv = T(0);
+      else rv = ddiv(W[(int64_t)q * nloc + jj], piv);
+      rowt[jj] = rv;
+      R[(int64_t)t * ldr + c0 + jj] = rv;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && L)
+      for (int r = q + tid; r < b; r += bd) L[(int64_t)(p.t0 + r) * ldl + t] = pivcol[r];
+    if (jw >= 0 && tid == 0) sl[jw] = p.tag;
+    __syncthreads();
+    if (q + 1 == b) break;
+    const int r1 = q + 1;                            // row q+1 first, then the next candidate
+    for (int jj = tid; jj < nl; jj += bd) {
+      if (sl[jj]) continue;
+      T* x = &W[(int64_t)r1 * nloc + jj];
+      *x = dsub(*x, dmul(pivcol[r1], rowt[jj]));
+    }
+    __syncthreads();
+    const KeyIdx<T> c = gp_best<T>(W, nloc, r1, nl, c0, sl);
+    int jb = -1;
+    if (c.idx != INT64_MAX && c.key >= T(0)) {
+      jb = (int)(c.idx - c0);
+      for (int r = q + 2 + tid; r < b; r += bd) {
+        T* x = &W[(int64_t)r * nloc + jb];
+        *x = dsub(*x, dmul(pivcol[r], rowt[jb]));
+      }
+      __syncthreads();
+    }
+    gp_publish<T>(p.gc, r1, c, W, nloc, c0, b);
+    comm_arrive(p.gc, r1);
+    for (int jj = tid; jj < nl; jj += bd) {          // rows q+2 .. b-1, overlapping the barrier
+      if (sl[jj] || jj == jb) continue;
+      const T rv = rowt[jj];
+      for (int r = q + 2; r < b; ++r) {
+        T* x = &W[(int64_t)r * nloc + jj];
+        *x = dsub(*x, dmul(pivcol[r], rv));
+      }
+    }
+    __syncthreads();
+  }
+  for (int jj = tid; jj < nl; jj += bd) p.sel[c0 + jj] = sl[jj];
+}
+
+// Multipliers of the trailing rows r = t0+b .. s-1 for a finished panel, one warp per row:
+// M(r, q) = S^(q)(r, j_q) = X(r, j_q) - sum_{q' < q} M(r, q') R(t0 + q', j_q), the subtractions
+// in q' order (lane i owns q = i and i + 32; M(r, q') is broadcast when final).
+template <typename T>
+__global__ void __launch_bounds__(256) lupp_gmult_kernel(const T* Xg, int64_t n, int s, int t0, int b, const T* R,
+                                                         int64_t ldr, const int32_t* Js, T* M, int64_t ldm, T* L,
+                                                         int64_t ldl, const int32_t* fail) {
+  __shared__ T RJ[kMaxPanel][kMaxPanel + 1];           // RJ[qq][q] = R(t0 + qq, j_q)
+  __shared__ int jq[kMaxPanel];
+  if (*(volatile const int32_t*)fail) return;
+  for (int q = threadIdx.x; q < b; q += blockDim.x) jq[q] = Js[t0 + q];
+  __syncthreads();
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int qq = e / b, q = e % b;
+    RJ[qq][q] = R[(int64_t)(t0 + qq) * ldr + jq[q]];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t r = t0 + b + (int64_t)blockIdx.x * nw + warp; r < s; r += (int64_t)gridDim.x * nw) {
+    const int qa = lane, qb = lane + 32;
+    T xa = qa < b ? Xg[r * n + jq[qa]] : T(0);
+    T xb = qb < b ? Xg[r * n + jq[qb]] : T(0);
+    for (int qq = 0; qq < b; ++qq) {
+      const T m = __shfl_sync(0xffffffffu, qq < 32 ? xa : xb, qq & 31);
+      if (lane == 0) {
+        M[(r - t0 - b) * ldm + qq] = m;
+        if (L) L[r * ldl + t0 + qq] = m;
+      }
+      if (qa > qq && qa < b) xa = dsub(xa, dmul(m, RJ[qq][qa]));
+      if (qb > qq && qb < b) xb = dsub(xb, dmul(m, RJ[qq][qb]));
+    }
+  }
 }
 
 struct PanelPlan {
@@ -1003,6 +1317,125 @@ skel_status run_skeleton_pivot(skel_dtype dt, const void* X, int64_t n, int64_t 
                                dev_status, st);
 }
 
+struct GPanelPlan {
+  int G = 0, nloc = 0, b = 0;
+  size_t smem = 0, slot_bytes = 0, comm = 0;
+};
+
+// Grid panels: every SM holds n/G columns of a panel of b rows (b as large as 200 KB of shared
+// memory allows, at most 64); 0 when not even one row fits or the grid cannot be co-resident.
+template <typename T>
+GPanelPlan plan_gpanel(int64_t n, int s) {
+  GPanelPlan pl;
+  if (n >= (int64_t)1 << 31) return pl;
+  const int sms = device_sm_count();
+  const int G = (int)std::max<int64_t>(1, std::min<int64_t>(sms, (n + 31) / 32));
+  const int nloc = (int)((n + G - 1) / G);
+  int b = std::min(kMaxPanel, s);
+  while (b > 1 && gpanel_smem<T>(b, nloc) > 200 * 1024) --b;
+  if (gpanel_smem<T>(b, nloc) > 200 * 1024) return pl;
+  const size_t smem = gpanel_smem<T>(b, nloc);
+  if (cudaFuncSetAttribute(lupp_gpanel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return pl;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lupp_gpanel_kernel<T>, 256, smem) != cudaSuccess ||
+      per_sm * sms < G) {
+    cudaGetLastError();
+    return pl;
+  }
+  pl.G = G;
+  pl.nloc = nloc;
+  pl.b = b;
+  pl.smem = smem;
+  pl.slot_bytes = align_up(16 + sizeof(T) * (size_t)kMaxPanel, 16);
+  pl.comm = comm_header_bytes(kMaxPanel) + align_up(2 * (size_t)G * pl.slot_bytes);
+  return pl;
+}
+
+template <typename T>
+size_t gpanel_ws(int64_t n, int s, const GPanelPlan& pl) {
+  return panel_ws<T>(n, s, true) + pl.comm;
+}
+
+template <typename T>
+skel_status run_gpanel_t(const GPanelPlan& pl, const T* X, int64_t n, int64_t ldx, int s, int32_t* Js, T* L,
+                         int64_t ldl, T* R, int64_t ldr, void* ws, int32_t* dev_status, cudaStream_t st) {
+  char* base = static_cast<char*>(ws);
+  T* Xg = reinterpret_cast<T*>(base);
+  base += align_up(sizeof(T) * (size_t)s * n);
+  unsigned char* sel = reinterpret_cast<unsigned char*>(base);
+  base += align_up(n);
+  int32_t* fail = reinterpret_cast<int32_t*>(base);
+  base += 256;
+  T* M = reinterpret_cast<T*>(base);
+  base += align_up(sizeof(T) * (size_t)s * 64);
+  T* Rw = reinterpret_cast<T*>(base);
+  base += align_up(sizeof(T) * (size_t)s * n);
+  if (R == nullptr) {
+    R = Rw;
+    ldr = n;
+  }
+  char* comm = base;
+  lupp_panel_init_kernel<T><<<dim3((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)std::min(s, 64)), 256, 0, st>>>(
+      X, ldx, s, n, Xg, sel, fail, L, ldl);
+  note_launches(1);
+  if (cudaFuncSetAttribute(lupp_gpanel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem) != cudaSuccess)
+    return SKEL_ERR_CUDA;
+  int k = 0;
+  for (int t0 = 0; t0 < s; t0 += pl.b, ++k) {
+    const int bb = std::min(pl.b, s - t0);
+    if (cudaMemsetAsync(comm, 0, comm_header_bytes(kMaxPanel), st) != cudaSuccess) return SKEL_ERR_CUDA;
+    GPanelParams gp{};
+    gp.n = n; gp.s = s; gp.t0 = t0; gp.b = bb; gp.nloc = pl.nloc;
+    gp.sel = sel;
+    gp.tag = (unsigned char)std::min(k + 1, 255);
+    gp.Js = Js; gp.fail = fail; gp.dev_status = dev_status;
+    gp.gc.counter = reinterpret_cast<unsigned int*>(comm);
+    gp.gc.abort = reinterpret_cast<int32_t*>(comm + 4);
+    gp.gc.keys = reinterpret_cast<unsigned long long*>(comm + 256);
+    gp.gc.payload = comm + comm_header_bytes(kMaxPanel);
+    gp.gc.slot_bytes = (int64_t)pl.slot_bytes;
+    gp.gc.G = pl.G;
+    gp.gc.wait_ns = kDefaultWaitNs;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(pl.G);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = pl.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    {
+      KernelTimer kt("lupp_panel", st);
+      if (cudaLaunchKernelEx(&cfg, lupp_gpanel_kernel<T>, gp, Xg, R, ldr, L, ldl) != cudaSuccess) return SKEL_ERR_CUDA;
+    }
+    note_launches(1);
+    const int trows = s - t0 - bb;
+    if (trows <= 0) continue;
+    lupp_gmult_kernel<T><<<(unsigned)std::min<int64_t>((trows + 7) / 8, 1024), 256, 0, st>>>(
+        Xg, n, s, t0, bb, R, ldr, Js, M, bb, L, ldl, fail);
+    note_launches(1);
+    PanelParams<T> tp{};
+    tp.Xg = Xg; tp.n = n; tp.s = s; tp.t0 = t0; tp.b = bb; tp.R = R; tp.ldr = ldr; tp.fail = fail;
+    tp.M = M; tp.ldm = bb; tp.trow0 = t0 + bb; tp.trows = trows; tp.sel = sel; tp.sel_limit = 255;
+    if (launch_trail<T>(tp, trows, st) != cudaSuccess) return SKEL_ERR_CUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
+}
+
+static bool gpanel_usable(skel_dtype dt, int64_t n, int32_t s) {
+  return (dt == SKEL_F64 ? plan_gpanel<double>(n, s).b : plan_gpanel<float>(n, s).b) > 0;
+}
+
+static size_t gpanel_workspace(skel_dtype dt, int64_t n, int32_t s) {
+  return dt == SKEL_F64 ? gpanel_ws<double>(n, s, plan_gpanel<double>(n, s))
+                        : gpanel_ws<float>(n, s, plan_gpanel<float>(n, s));
+}
+
 static bool panel_usable(skel_dtype dt, int64_t n, int32_t s) {
   return (dt == SKEL_F64 ? plan_panel<double>(n, s).b : plan_panel<float>(n, s).b) > 0;
 }
@@ -1012,14 +1445,25 @@ static size_t panel_workspace(skel_dtype dt, int64_t n, int32_t s) {
 }
 
 size_t lupp_auto_workspace(skel_dtype dt, int64_t n, int32_t s) {
-  return panel_usable(dt, n, s) ? panel_workspace(dt, n, s) : lupp_workspace(dt, n, s, nullptr);
+  if (panel_usable(dt, n, s)) return panel_workspace(dt, n, s);
+  if (gpanel_usable(dt, n, s)) return gpanel_workspace(dt, n, s);
+  return lupp_workspace(dt, n, s, nullptr);
 }
 
 skel_status run_lupp_auto(skel_dtype dt, const void* X, int64_t n, int64_t ldx, int32_t s,
                           int32_t* Js, void* L, int64_t ldl, void* R, int64_t ldr, void* ws,
                           size_t ws_bytes, int32_t* dev_status, cudaStream_t st) {
-  if (!panel_usable(dt, n, s))
+  if (!panel_usable(dt, n, s)) {
+    if (gpanel_usable(dt, n, s)) {           // wider than a cluster panel: grid-wide panels
+      if (ws_bytes < gpanel_workspace(dt, n, s)) return SKEL_ERR_WORKSPACE;
+      if (dt == SKEL_F64)
+        return run_gpanel_t<double>(plan_gpanel<double>(n, s), (const double*)X, n, ldx, s, Js, (double*)L, ldl,
+                                    (double*)R, ldr, ws, dev_status, st);
+      return run_gpanel_t<float>(plan_gpanel<float>(n, s), (const float*)X, n, ldx, s, Js, (float*)L, ldl, (float*)R,
+                                 ldr, ws, dev_status, st);
+    }
     return run_lupp(dt, X, n, ldx, s, Js, L, ldl, R, ldr, ws, ws_bytes, dev_status, st);
+  }
   if (ws_bytes < panel_workspace(dt, n, s)) return SKEL_ERR_WORKSPACE;
   if (dt == SKEL_F64) {
     const PanelPlan pl = plan_panel<double>(n, s);

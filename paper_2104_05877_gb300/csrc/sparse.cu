@@ -17,7 +17,7 @@ namespace skel {
 namespace {
 
 constexpr int CT = 32;       // columns of X per CTA (dense A)
-constexpr int CT_CSC = 16;   // columns of X per CTA (CSC A)
+constexpr int CT_CSC = 8;    // columns of X per CTA (CSC A): one per warp
 constexpr int JCH = 256;     // rows of A per table chunk
 
 // Pattern of rows row0 .. row0+m-1 of A (counters use the global row index).
@@ -111,13 +111,44 @@ __global__ void __launch_bounds__(256) sparse_csc_kernel(int64_t n, const int64_
   for (int cc = warp; cc < nc; cc += nwarps) {
     const int64_t b = col_ptr[c0 + cc], e_ = col_ptr[c0 + cc + 1];
     float* ac = acc + cc * lda;
-    for (int64_t k = b + lane; k < e_; k += 32) {
-      const int64_t j = __ldg(row_idx + k);
-      const float v = __ldg(val + k);
-      const int32_t* tj = table + j * zeta;
-      for (int q = 0; q < zeta; ++q) {
-        const int32_t code = __ldg(tj + q);
-        atomicAdd(&ac[code & 0x7fffffff], code < 0 ? -v : v);
+    // four nonzeros per lane per round, their indices, values and (for zeta = 8) two 16-byte
+    // table rows loaded before any add, so that each lane has several loads in flight
+    for (int64_t k0 = b; k0 < e_; k0 += 128) {
+      int64_t j[4];
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t k = k0 + lane + 32 * u;
+        j[u] = k < e_ ? (int64_t)__ldg(row_idx + k) : -1;
+        v[u] = k < e_ ? __ldg(val + k) : 0.f;
+      }
+      if (zeta == 8) {
+        int4 t[4][2];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (j[u] >= 0) {
+            const int4* tj = reinterpret_cast<const int4*>(table + j[u] * 8);
+            t[u][0] = __ldg(tj);
+            t[u][1] = __ldg(tj + 1);
+          }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (j[u] >= 0) {
+            const int32_t codes[8] = {t[u][0].x, t[u][0].y, t[u][0].z, t[u][0].w,
+                                      t[u][1].x, t[u][1].y, t[u][1].z, t[u][1].w};
+#pragma unroll
+            for (int q = 0; q < 8; ++q) atomicAdd(&ac[codes[q] & 0x7fffffff], codes[q] < 0 ? -v[u] : v[u]);
+          }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (j[u] >= 0) {
+            const int32_t* tj = table + j[u] * zeta;
+            for (int q = 0; q < zeta; ++q) {
+              const int32_t code = __ldg(tj + q);
+              atomicAdd(&ac[code & 0x7fffffff], code < 0 ? -v[u] : v[u]);
+            }
+          }
       }
     }
   }

@@ -39,6 +39,46 @@ def test_lupp_fp64_global_slab_path(skel, dev):
     assert np.array_equal(Rf.cpu().numpy(), ref["R"])
 
 
+@pytest.mark.parametrize("l,n,s", [(80, 70000, 70), (20, 300000, 20)])
+def test_lupp_fp64_grid_panels_bit_exact(skel, dev, l, n, s):
+    """Too wide for a cluster panel (n / 16 columns per CTA overflow shared memory): grid-wide
+    panels of b rows over every SM, the trailing rows' multipliers by forward substitution and
+    the tiled trailing update.  Textbook operation order, so Js, L and R are bit-identical to
+    the FP64 oracle's (70 steps: panels of 54 and 16 rows)."""
+    X = np.random.default_rng(l * n + s).standard_normal((l, n))
+    Js, Lf, Rf, st = skel.pivot_lupp(torch.from_numpy(X).to(dev), s)
+    skel.check_status(st)
+    ref = pivoting.lupp_columns(X, s)
+    assert np.array_equal(Js.cpu().numpy(), ref["Js"])
+    assert np.array_equal(Rf.cpu().numpy(), ref["R"])
+    assert np.array_equal(Lf.cpu().numpy(), ref["L"][:s, :s])
+
+
+def test_lupp_fp32_grid_panels_tall_rows(skel, dev):
+    """FP32 row LUPP of a tall C (262144 x 96, as for the tall sparse configuration's CUR), on the
+    grid-panel path: C = 0.01 N(0, 1) plus C(i_q, q) = 1 in distinct random rows, so step q
+    picks row i_q with a wide gap; the pivots equal the FP64 oracle's and the planted rows, and
+    the factor has |R| <= 1 with R(t, j_t) = 1."""
+    rng = np.random.default_rng(9)
+    m, s = 262144, 96
+    C = 0.01 * rng.standard_normal((m, s))
+    rows = rng.choice(m, s, replace=False)
+    C[rows, np.arange(s)] = 1.0
+    C = np.asfortranarray(C.astype(np.float32))
+    Is, st = skel.pivot_lupp_rows(torch.from_numpy(C).to(dev), s)
+    skel.check_status(st)
+    ref = pivoting.lupp_rows(C.astype(np.float64), s)
+    assert np.array_equal(ref["Js"], rows)
+    assert np.array_equal(Is.cpu().numpy(), ref["Js"])
+    Xt = torch.from_numpy(np.ascontiguousarray(C.T)).to(dev)
+    Js, _, Rf, st = skel.pivot_lupp(Xt, s)
+    skel.check_status(st)
+    R = Rf.cpu().numpy()
+    J = Js.cpu().numpy()
+    assert np.array_equal(J, rows)
+    assert np.abs(R).max() <= 1.0 and np.all(R[np.arange(s), J] == 1.0)
+
+
 def _separated(l, n, seed, ratio):
     """Gaussian X with geometric column scales in random order: wide pivot gaps."""
     rng = np.random.default_rng(seed)
