@@ -169,7 +169,7 @@ class ClockSampler:
 
 # kernels timed with CUDA events in the serialised pass
 TIMED_KERNELS = ("sketch_tc", "sketch_fp8", "fp8_quantize", "gemm_tc", "lupp_panel", "lupp_trail", "qr_panel", "qr_wy", "gemm_refine",
-                 "trsm", "gemm_qr", "gemm_cur", "gemm_eta_h", "gemm_eta_sq", "gemm_simt")
+                 "trsm", "gemm_qr", "gemm_cur", "gemm_eta_h", "gemm_eta_sq", "gemm_simt", "transpose", "lupp_mult")
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel at this
 # workload, scaled from a smaller capture where noted in the profiles (None where no capture of
 # the current code exists)
@@ -587,11 +587,12 @@ def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
         A_np = np.asfortranarray(A[:, :ncols].double().cpu().numpy())
         cpu = cpu_sample_baseline(A_np, m, n, k, p, seed_G)
 
-    extra = extra3 = None
+    extra = extra3 = extra4 = None
     if not args.no_extra:
         del X
         torch.cuda.empty_cache()
         extra3 = run_c3(skel, dev)
+        extra4 = batch_measure(skel, dev)
         A2 = make_A("c2", dev, seeds("c2", rank)[0])
         a2 = argparse.Namespace(**vars(args))
         a2.workload, a2.k, a2.p, a2.prec, a2.no_cpu = "c2", 256, 16, "tf32", True
@@ -617,6 +618,7 @@ def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
         "gpu_launches": launches, "clocks": clk.summary(),
         "extra_8192": extra,
         "extra_sparse_262144x4096": extra3,
+        "extra_batched_4096_blocks": extra4,
     }
     print(json.dumps(res), flush=True)
 
@@ -865,7 +867,11 @@ def run_c3(skel, dev, steps=10, warmup=3):
     tts = timed(skeleton, steps)
     J, I = out["J"], out["I"]
     cur_ms = timed(lambda: skel.cur(Ad, J, I, status=st), max(2, steps // 2))
+    skel.kernel_timing(True)
     _, U, _, _ = skel.cur(Ad, J, I, status=st)
+    torch.cuda.synchronize()
+    cur_kernels = kernel_table(skel, 1, cur_ms, {})
+    skel.kernel_timing(False)
     e, _ = skel.error(Ad, J, Is=I, U=U, status=st)
     skel.check_status(st, "tall sparse configuration")
     e = e.cpu().numpy()
@@ -876,7 +882,8 @@ def run_c3(skel, dev, steps=10, warmup=3):
                        f"l={l}, k={k}; CUR with rows by LUPP on C",
            "sketch_ms": sketch_ms, "sketch_kernel_ms": kern_ms, "sketch_bytes": a_bytes,
            "sketch_gbs": a_bytes / (k_ms * 1e-3) / 1e9, "sketch_frac_of_hbm": a_bytes / (k_ms * 1e-3) / 1e9 / hbm,
-           "time_to_skeleton_ms": tts, "cur_ms": cur_ms, "rel_cur_error": float(e[2] / e[0])}
+           "time_to_skeleton_ms": tts, "cur_ms": cur_ms, "cur_kernels_serialised": cur_kernels,
+           "rel_cur_error": float(e[2] / e[0])}
     del At, Ad, X
     torch.cuda.empty_cache()
     return res
@@ -987,41 +994,96 @@ def run_next(args, rank, A, skel, st, seed_G):
                           "config": workload_config(args.workload, k, p, prec)}), flush=True)
 
 
-def run_batch(args, rank, dev, skel, workloads):
-    """Batched configuration: uneven Gaussian-kernel blocks (4096 by default: m_b ~ U[64, 1024],
-    n_b ~ U[64, 512], FP32, ~2.6 GB), k_max = 128, p = 16, tol = 1e-6: one skel_batch_run per
-    step (an autotuned plan replaying its captured CUDA graph)."""
+def batch_measure(skel, dev, nblocks=4096, steps=10, warmup=3, seed_offset=0):
+    """Batched configuration: uneven Gaussian-kernel blocks (m_b ~ U[64, 1024], n_b ~ U[64, 512],
+    FP32, ~2.5 GB for 4096 blocks), k_max = 128, p = 16, tol = 1e-6: one skel_batch_run per
+    step (an autotuned plan replaying its captured CUDA graph), A read once per run."""
     import torch
-    nblocks, kmax, p, tol = args.blocks, 128, 16, 1e-6
-    blocks = workloads.torch_kernel_blocks(nblocks, workloads.seed_for(4) + rank, dev)
+    import workloads
+    kmax, p, tol = 128, 16, 1e-6
+    blocks = workloads.torch_kernel_blocks(nblocks, workloads.seed_for(4) + seed_offset, dev)
     a_bytes = sum(4 * B.shape[0] * B.shape[1] for B in blocks)
     plan = skel.BatchPlan(blocks, kmax, p=p, tol=tol, seed=workloads.seed_for(4, "gamma"), graph=True, autotune=True)
     torch.cuda.synchronize()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         Js, ranks, Z, st = plan.run()
     torch.cuda.synchronize()
     e0, e1 = _events(2)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         Js, ranks, Z, st = plan.run()
     e1.record()
     torch.cuda.synchronize()
     skel.check_status(st, "batch")
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     skel.kernel_timing(True)
     plan.run()
     torch.cuda.synchronize()
     kern = {nm: skel.kernel_time(nm)[0] for nm in ("batch_sketch", "batch_lupp", "batch_z")}
     skel.kernel_timing(False)
     r = ranks.float()
-    hbm, _, src = load_peaks()
+    hbm = load_peaks_full()["hbm_gbs"]
+    out = {"ms": ms, "a_bytes": a_bytes, "a_streaming_gbs": a_bytes / (ms * 1e-3) / 1e9,
+           "frac_of_hbm": a_bytes / (ms * 1e-3) / 1e9 / hbm, "kernel_ms": kern,
+           "rank_mean": float(r.mean()), "rank_max": int(r.max()), "plan": plan.info,
+           "workload": f"{nblocks} Gaussian-kernel blocks m_b~U[64,1024] n_b~U[64,512] fp32, k_max={kmax}, p={p}, "
+                       f"tol={tol}; Z = X_b(:, J)^+ X_b", "steps": steps}
+    del plan, blocks
+    torch.cuda.empty_cache()
+    out["points"] = batch_points_measure(skel, dev, nblocks, steps, warmup, seed_offset, a_bytes)
+    return out
+
+
+def batch_points_measure(skel, dev, nblocks, steps, warmup, seed_offset, a_bytes):
+    """The same batched workload given implicitly by its point sets (kernel_points: the draws of
+    the stored blocks, FP32): skel_batch_plan_create_points evaluates every kernel entry inside
+    the sketch kernel (a two-float exponent and expf per entry), so the blocks are never
+    stored; 32 bytes per point are read instead of 4 bytes per entry."""
+    import numpy as np
+    import torch
+    import workloads
+    kmax, p, tol = 128, 16, 1e-6
+    pts = workloads.kernel_points(nblocks, workloads.seed_for(4) + seed_offset)
+    xs = [torch.from_numpy(x).to(dev) for x, _ in pts]
+    ys = [torch.from_numpy(y).to(dev) for _, y in pts]
+    entries = sum(x.shape[0] * y.shape[0] for x, y in pts)
+    plan = skel.BatchPlan.from_points(xs, ys, 0.5, kmax, p=p, tol=tol, seed=workloads.seed_for(4, "gamma"), graph=True,
+                                      autotune=True)
+    torch.cuda.synchronize()
+    for _ in range(warmup):
+        Js, ranks, Z, st = plan.run()
+    torch.cuda.synchronize()
+    e0, e1 = _events(2)
+    e0.record()
+    for _ in range(steps):
+        Js, ranks, Z, st = plan.run()
+    e1.record()
+    torch.cuda.synchronize()
+    skel.check_status(st, "batch points")
+    ms = e0.elapsed_time(e1) / steps
+    skel.kernel_timing(True)
+    plan.run()
+    torch.cuda.synchronize()
+    kern = {nm: skel.kernel_time(nm)[0] for nm in ("batch_sketch", "batch_lupp", "batch_z")}
+    skel.kernel_timing(False)
+    r = ranks.float()
+    out = {"ms": ms, "kernel_ms": kern, "kernel_entries": entries,
+           "entries_per_s": entries / (kern["batch_sketch"] * 1e-3) if kern["batch_sketch"] > 0 else None,
+           "point_bytes": 32 * sum(x.shape[0] + y.shape[0] for x, y in pts), "stored_block_bytes": a_bytes,
+           "rank_mean": float(r.mean()), "rank_max": int(r.max()), "plan": plan.info,
+           "workload": f"the same {nblocks} blocks given by their FP32 point sets (3-D, h = 0.5), entries evaluated "
+                       "inside the sketch kernel"}
+    del plan, xs, ys
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch(args, rank, dev, skel, workloads):
+    """--only batch: the batched configuration alone, one JSON line."""
+    out = batch_measure(skel, dev, args.blocks, args.steps, args.warmup, seed_offset=rank)
     if rank == 0:
-        print(json.dumps({"only": "batch", "ms": ms, "a_bytes": a_bytes, "a_streaming_gbs": a_bytes / (ms * 1e-3) / 1e9,
-                          "frac_of_hbm": a_bytes / (ms * 1e-3) / 1e9 / hbm,
-                          "kernel_ms": kern, "rank_mean": float(r.mean()), "rank_max": int(r.max()),
-                          "plan": plan.info,
-                          "config": {"workload": f"{nblocks} Gaussian-kernel blocks m_b~U[64,1024] n_b~U[64,512] fp32, "
-                                                 f"k_max={kmax}, p={p}, tol={tol}", "steps": args.steps}}), flush=True)
+        out["only"] = "batch"
+        print(json.dumps(out), flush=True)
 
 
 def main():

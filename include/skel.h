@@ -7,7 +7,7 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  *  - Every matrix pointer is a DEVICE pointer owned by the caller; the library never frees
- *    or retains it.  Only skel_batch_plan_create allocates device memory (the plan's own, freed
+ *    or retains it.  Only the two batch plan constructors allocate device memory (the plan's own, freed
  *    by skel_batch_plan_destroy); every other call that needs scratch memory takes a
  *    caller-provided device workspace `ws` of `*ws_bytes` bytes (skel_pivot_lupp_static uses a
  *    fixed array inside the library instead).  Calling with
@@ -412,6 +412,23 @@ skel_status skel_id_sketch(skel_dtype dtype, const void* X, int64_t l, int64_t n
  *   no choice changes any result.  SKEL_BATCH_GRAPH makes skel_batch_run replay a CUDA
  *   graph of the run, captured on its first call and again whenever the output pointers
  *   change.  Other bits: SKEL_ERR_INVALID_ARG.
+ * skel_batch_plan_create_points -- the same batch for blocks given implicitly (Sec. 1: the
+ *   method needs A only through the entries it evaluates and the products it forms; the
+ *   experiments on SNN1e6 in Sec. 5 access A only through products): block b is the
+ *   Gaussian-kernel matrix A_b(i, j) = exp(-||x_i - y_j||^2 / h^2) between point sets
+ *   x[b] (m[b] x dim) and y[b] (n[b] x dim), device pointers, row-major FP32 (point i's
+ *   coordinates at x[b][i*dim .. i*dim + dim)), 1 <= dim <= 3, h > 0.  A_b is never stored:
+ *   the sketch kernel evaluates its entries tile by tile in shared memory from per-point
+ *   records the run forms first ({coordinates, -||p||^2/h^2 as a pair of floats}, 32 bytes
+ *   per point, owned by the plan), the exponent -||x - y||^2/h^2 = c_x + c_y + (2/h^2) x.y
+ *   as a pair of floats and the entry as expf of its leading part times (1 + its trailing
+ *   part), so every entry is within a few FP32 roundings of the exact kernel value.  Z and
+ *   the pivots come from the sketch alone, so no A_b exists anywhere.  The points are read
+ *   at every run (they must stay allocated and may change between runs); all other
+ *   arguments, errors and outputs are those of skel_batch_plan_create / skel_batch_run.
+ * skel_batch_copy_sketch -- enqueues on `stream` a device-to-device copy of block b's sketch
+ *   X_b ((kmax+p) x n_b, row-major FP32, as the last run left it) into X (device, caller's).
+ *   For tests and diagnostics.
  * skel_batch_plan_info -- host: info[0] sketch pipeline depth, info[1] 1 if the LUPP classes
  *   run concurrently, info[2] the flags, info[3] sketch work items (128-column tiles).
  * skel_batch_z_offsets -- host: offsets[0..nblocks] (in doubles) of the blocks' Z in Z_all,
@@ -429,6 +446,11 @@ enum { SKEL_BATCH_GRAPH = 1, SKEL_BATCH_AUTOTUNE = 2 };
 skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int64_t* n, const float* const* A,
                                    const int64_t* lda, int32_t kmax, int32_t p, double tol, uint64_t seed,
                                    int32_t flags, skel_batch_plan** plan);
+skel_status skel_batch_plan_create_points(int32_t nblocks, const int64_t* m, const int64_t* n, int32_t dim,
+                                          const float* const* x, const float* const* y, double h, int32_t kmax,
+                                          int32_t p, double tol, uint64_t seed, int32_t flags,
+                                          skel_batch_plan** plan);
+skel_status skel_batch_copy_sketch(const skel_batch_plan* plan, int32_t b, float* X, cudaStream_t stream);
 skel_status skel_batch_plan_info(const skel_batch_plan* plan, int32_t* info);
 skel_status skel_batch_z_offsets(const skel_batch_plan* plan, int64_t* offsets);
 skel_status skel_batch_run(skel_batch_plan* plan, int32_t* Js, int32_t* ranks, double* Z, int32_t* dev_status,

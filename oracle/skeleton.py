@@ -60,6 +60,23 @@ def batch_skeletonize(blocks, kmax, p, tol, seed):
     return out
 
 
+def gaussian_kernel_block(x, y, h):
+    """A(i, j) = exp(-||x_i - y_j||^2 / h^2) (the Gaussian kernel between point sets x (m x d)
+    and y (n x d)), formed in FP64 from the given coordinates: the implicit matrix of a batch
+    given by points (Sec. 1: A is needed only through the entries the method evaluates)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    D2 = np.zeros((x.shape[0], y.shape[0]))
+    for c in range(x.shape[1]):
+        D2 += (x[:, c][:, None] - y[:, c][None, :]) ** 2
+    return np.exp(-D2 / (h * h))
+
+
+def batch_skeletonize_points(points, h, kmax, p, tol, seed):
+    """batch_skeletonize on the Gaussian-kernel blocks of the point sets [(x_b, y_b)]."""
+    return batch_skeletonize([gaussian_kernel_block(x, y, h) for x, y in points], kmax, p, tol, seed)
+
+
 def streaming_skeletonize(A, k, p, seed_gamma, seed_omega):
     """Algorithm 3 (streaming skeleton selection): X = Gamma A and Y = A Omega^T from the same
     pass over A, J_s by column LUPP on X, I_s by row LUPP on Y (column LUPP on Y^T); then the

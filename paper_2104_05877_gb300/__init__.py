@@ -86,6 +86,12 @@ def lib():
                                          ctypes.POINTER(i64), i32, i32, ctypes.c_double, u64, i32,
                                          ctypes.POINTER(vp)]
     L.skel_batch_plan_create.restype = ctypes.c_int
+    L.skel_batch_plan_create_points.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(i64), i32,
+                                                ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_double, i32, i32,
+                                                ctypes.c_double, ctypes.c_uint64, i32, ctypes.POINTER(vp)]
+    L.skel_batch_plan_create_points.restype = ctypes.c_int
+    L.skel_batch_copy_sketch.argtypes = [vp, i32, vp, vp]
+    L.skel_batch_copy_sketch.restype = ctypes.c_int
     L.skel_batch_plan_info.argtypes = [vp, ctypes.POINTER(i32)]
     L.skel_batch_plan_info.restype = ctypes.c_int
     L.skel_batch_z_offsets.argtypes = [vp, ctypes.POINTER(i64)]
@@ -547,6 +553,9 @@ class BatchPlan:
 
     def __init__(self, blocks, kmax, p=16, tol=1e-6, seed=0, graph=False, autotune=False):
         self.blocks = []
+        self.l = kmax + p
+        if blocks is None:                     # from_points fills the plan in
+            return
         for B in blocks:
             if B.dtype != torch.float32 or not B.is_cuda:
                 raise ValueError("batch blocks must be float32 CUDA tensors")
@@ -569,6 +578,44 @@ class BatchPlan:
         rc = lib().skel_batch_plan_create(nb, m, n, a, ld, kmax, p, float(tol), seed, flags, ctypes.byref(self._plan))
         if rc != 0:
             raise SkelError(rc, "skel_batch_plan_create")
+        self.ncols = [B.shape[1] for B, _ in self.blocks]
+        self._finish(graph)
+
+    @classmethod
+    def from_points(cls, xs, ys, h, kmax, p=16, tol=1e-6, seed=0, graph=False, autotune=False):
+        """The batch for Gaussian-kernel blocks A_b(i, j) = exp(-||x_i - y_j||^2 / h^2) given by
+        point sets (skel_batch_plan_create_points): xs[b] (m_b x dim) and ys[b] (n_b x dim),
+        float32 CUDA tensors, dim <= 3, kept alive by the plan and read at every run.  A_b is
+        evaluated inside the sketch kernel and never stored."""
+        self = cls(None, kmax, p)
+        pts = []
+        for x, y in zip(xs, ys):
+            if x.dtype != torch.float32 or y.dtype != torch.float32 or not (x.is_cuda and y.is_cuda):
+                raise ValueError("points must be float32 CUDA tensors")
+            if x.dim() != 2 or y.dim() != 2 or x.shape[1] != y.shape[1]:
+                raise ValueError("points: (m_b, dim) and (n_b, dim) tensors")
+            pts.append((x.contiguous(), y.contiguous()))
+        self.points = pts
+        nb = len(pts)
+        dim = pts[0][0].shape[1]
+        arr = lambda T, v: (T * nb)(*v)
+        m = arr(ctypes.c_int64, [x.shape[0] for x, _ in pts])
+        n = arr(ctypes.c_int64, [y.shape[0] for _, y in pts])
+        xp = arr(ctypes.c_void_p, [x.data_ptr() for x, _ in pts])
+        yp = arr(ctypes.c_void_p, [y.data_ptr() for _, y in pts])
+        self.kmax, self.nb, self.device = kmax, nb, pts[0][0].device
+        self._plan = ctypes.c_void_p()
+        flags = (1 if graph else 0) | (2 if autotune else 0)
+        rc = lib().skel_batch_plan_create_points(nb, m, n, dim, xp, yp, float(h), kmax, p, float(tol), seed, flags,
+                                                 ctypes.byref(self._plan))
+        if rc != 0:
+            raise SkelError(rc, "skel_batch_plan_create_points")
+        self.ncols = [y.shape[0] for _, y in pts]
+        self._finish(graph)
+        return self
+
+    def _finish(self, graph):
+        nb = self.nb
         off = (ctypes.c_int64 * (nb + 1))()
         lib().skel_batch_z_offsets(self._plan, off)
         self.z_offsets = list(off)
@@ -597,9 +644,17 @@ class BatchPlan:
             raise SkelError(rc, "skel_batch_run")
         return Js, ranks, Z, st
 
+    def sketch_block(self, b):
+        """X_b ((kmax + p) x n_b float32, a copy) as the last run left it."""
+        X = torch.empty(self.l, self.ncols[b], dtype=torch.float32, device=self.device)
+        rc = lib().skel_batch_copy_sketch(self._plan, b, _ptr(X), _stream())
+        if rc != 0:
+            raise SkelError(rc, "skel_batch_copy_sketch")
+        return X
+
     def z_block(self, Z, b, rank=None):
         """Z_b (rank x n_b) as a view of Z_all."""
-        n_b = self.blocks[b][0].shape[1]
+        n_b = self.ncols[b]
         zb = Z[self.z_offsets[b]:self.z_offsets[b + 1]].view(self.kmax, n_b)
         return zb if rank is None else zb[:rank]
 

@@ -54,12 +54,18 @@ namespace {
 using namespace tc;
 
 struct BatchBlock {
-  const float* A;
+  const float* A;   // A_b (column-major, lda); for a point plan the records of x_1 .. x_m
   int64_t lda;
   int32_t m, n;
   int64_t xoff;     // X_b at X + xoff (l x n_b row-major)
   int64_t zoff;     // Z_b at Z + zoff (k_max x n_b row-major)
+  const float* Y;   // point plans: the records of y_1 .. y_n
 };
+
+// A point record (point plans): 8 floats, {p_0, p_1, p_2, 0, c_hi, c_lo, 0, 0} with the
+// coordinates padded by zeros to three and c = -||p||^2 / h^2 as an unevaluated sum of two
+// floats (formed in FP64).
+constexpr int kRec = 8;
 struct SketchItem {
   int32_t b, tile;
 };
@@ -99,6 +105,7 @@ __global__ void batch_gamma_kernel(int l, int lp, int64_t mg, uint32_t k0, uint3
 // Sketch: X_b(:, tile) = Gamma A_b(:, tile), 3xTF32
 // ---------------------------------------------------------------------------------------
 constexpr int BS_THREADS = 256;       // warp 0 TMA, 1 MMA, 2 TMEM, 4..7 converters + epilogue
+constexpr int BS_THREADS_P = 384;     // point plans: warps 4..11 generate A's tiles, 4..7 epilogue
 constexpr int BS_CONV_WARP0 = 4;
 constexpr int BS_BK = 32;
 constexpr uint32_t BS_ATILE = 128 * 128;          // 128 columns x 32 rows of A, FP32
@@ -107,15 +114,84 @@ constexpr uint64_t BS_WAIT_NS = 2000000000ull;
 
 struct BatchSketchParams {
   const BatchBlock* blocks;
-  const CUtensorMap* tmaps;   // one per block, in global memory (64-byte aligned)
+  const CUtensorMap* tmaps;   // one per block, in global memory (64-byte aligned); stored blocks
   const SketchItem* items;
   float* X;
   int l, lp, stages;
   float scale;
+  float w_hi, w_lo;           // point plans: 2 / h^2 as an unevaluated sum of two floats
   int32_t* dev_status;
 };
 
-__global__ void __launch_bounds__(BS_THREADS, 1)
+// Two-sum (Knuth): s + e = a + b exactly, s = fl(a + b).  Explicit round-to-nearest
+// operations, so that no multiply-add contraction alters the error terms.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Gaussian-kernel entry exp(-||x - y||^2 / h^2) from two point records, through
+//   -||x - y||^2 / h^2 = c_x + c_y + (2 / h^2) x.y,   c_p = -||p||^2 / h^2,
+// evaluated as an unevaluated sum of two floats (products split exactly with FMA, sums by
+// two-sum), so the exponent carries ~44 bits: a plain FP32 evaluation would put an absolute
+// error of ~1e-5 into exponents near -100 and a relative error of that size into the entry.
+// The entry is expf(a_hi) (1 + a_lo).
+__device__ __forceinline__ float kernel_entry(const float4 x, const float2 cx, const float4 y, const float2 cy,
+                                              float w_hi, float w_lo) {
+  const float p0 = __fmul_rn(x.x, y.x), p1 = __fmul_rn(x.y, y.y), p2 = __fmul_rn(x.z, y.z);
+  const float e0 = fmaf(x.x, y.x, -p0), e1 = fmaf(x.y, y.y, -p1), e2 = fmaf(x.z, y.z, -p2);
+  float s1, t1, dh, t2;
+  two_sum(p0, p1, s1, t1);
+  two_sum(s1, p2, dh, t2);
+  const float dl = __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, t1)), t2);   // x.y = dh + dl
+  const float ph = __fmul_rn(dh, w_hi);
+  const float pl = fmaf(dh, w_lo, fmaf(dl, w_hi, fmaf(dh, w_hi, -ph)));               // w x.y = ph + pl
+  float u, ue, ah, ae;
+  two_sum(cx.x, cy.x, u, ue);
+  two_sum(u, ph, ah, ae);
+  const float al = __fadd_rn(__fadd_rn(__fadd_rn(ue, ae), __fadd_rn(cx.y, cy.y)), pl);
+  const float ex = expf(ah);
+  return fmaf(ex, al, ex);
+}
+
+// Point records of every block (one grid row per block), formed at the start of each run from
+// the caller's points (m_b x dim and n_b x dim, row-major FP32, dim <= 3).
+struct PointSrc {
+  const float* x;
+  const float* y;
+  int32_t m, n;
+  float* xrec;
+  float* yrec;
+};
+
+__global__ void batch_points_prep_kernel(const PointSrc* src, int dim, double inv_h2) {
+  const PointSrc ps = src[blockIdx.y];
+  const int tot = ps.m + ps.n;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+    const bool isx = e < ps.m;
+    const int i = isx ? e : e - ps.m;
+    const float* q = (isx ? ps.x : ps.y) + (int64_t)i * dim;
+    float c3[3] = {0.f, 0.f, 0.f};
+    double n2 = 0.0;
+    for (int d = 0; d < dim; ++d) {
+      c3[d] = q[d];
+      n2 += (double)c3[d] * (double)c3[d];
+    }
+    const double c = -n2 * inv_h2;
+    const float ch = (float)c;
+    const float cl = (float)(c - (double)ch);
+    float4* r = reinterpret_cast<float4*>((isx ? ps.xrec : ps.yrec) + (int64_t)i * kRec);
+    r[0] = make_float4(c3[0], c3[1], c3[2], 0.f);
+    r[1] = make_float4(ch, cl, 0.f, 0.f);
+  }
+}
+
+// PTS: the block is given by point records and the generator warps form A's tiles in shared
+// memory (in the 128-byte swizzled K-major layout the TMA would have written), so A is never
+// read from (or stored in) device memory.
+template <bool PTS>
+__global__ void __launch_bounds__(PTS ? BS_THREADS_P : BS_THREADS, 1)
 batch_sketch_kernel(const __grid_constant__ CUtensorMap tmGhi, const __grid_constant__ CUtensorMap tmGlo,
                     const BatchSketchParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -130,8 +206,9 @@ batch_sketch_kernel(const __grid_constant__ CUtensorMap tmGhi, const __grid_cons
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const SketchItem item = p.items[blockIdx.x];
   const BatchBlock blk = p.blocks[item.b];
-  const CUtensorMap* tmA = p.tmaps + item.b;
+  const CUtensorMap* tmA = PTS ? nullptr : p.tmaps + item.b;
   const int nk = (blk.m + BS_BK - 1) / BS_BK;
+  constexpr int kConvWarps = PTS ? (BS_THREADS_P / 32 - BS_CONV_WARP0) : 4;
   auto a_buf = [&](int s) { return smem + s * stage_bytes; };
   auto alo_buf = [&](int s) { return smem + s * stage_bytes + BS_ATILE; };
   auto ghi_buf = [&](int s) { return smem + s * stage_bytes + 2 * BS_ATILE; };
@@ -144,7 +221,7 @@ batch_sketch_kernel(const __grid_constant__ CUtensorMap tmGhi, const __grid_cons
   if (tid == 0) {
     for (int s = 0; s < AS; ++s) {
       mbar_init(full(s), 1);
-      mbar_init(conv(s), 4);
+      mbar_init(conv(s), kConvWarps);
       mbar_init(empty(s), 1);
     }
     mbar_init(done, 1);
@@ -173,9 +250,9 @@ batch_sketch_kernel(const __grid_constant__ CUtensorMap tmGhi, const __grid_cons
         const uint32_t ph = (uint32_t)(it / AS) & 1u;
         if (aborted()) break;
         if (it >= AS && !mbar_wait(empty(s), ph ^ 1u, BS_WAIT_NS)) { fail(); break; }
-        mbar_expect_tx(full(s), BS_ATILE + 2 * g_bytes);
+        mbar_expect_tx(full(s), (PTS ? 0u : BS_ATILE) + 2 * g_bytes);
         const int x = it * BS_BK;
-        tma_load_2d(smem_u32(a_buf(s)), tmA, x, item.tile * 128, full(s));
+        if constexpr (!PTS) tma_load_2d(smem_u32(a_buf(s)), tmA, x, item.tile * 128, full(s));
         tma_load_2d(smem_u32(ghi_buf(s)), &tmGhi, x, 0, full(s));
         tma_load_2d(smem_u32(glo_buf(s)), &tmGlo, x, 0, full(s));
         ++issued;
@@ -190,6 +267,7 @@ batch_sketch_kernel(const __grid_constant__ CUtensorMap tmGhi, const __grid_cons
         const int s = it % AS;
         const uint32_t ph = (uint32_t)(it / AS) & 1u;
         if (aborted()) break;
+        if (PTS && !mbar_wait(full(s), ph, BS_WAIT_NS)) { fail(); break; }   // Gamma's tiles
         if (!mbar_wait(conv(s), ph, BS_WAIT_NS)) { fail(); break; }
         tc_fence_after();
         const uint32_t ahi = smem_u32(a_buf(s)), alo = smem_u32(alo_buf(s));
@@ -206,9 +284,62 @@ batch_sketch_kernel(const __grid_constant__ CUtensorMap tmGhi, const __grid_cons
       mma_commit(done);
     }
   } else if (warp >= BS_CONV_WARP0) {
+    if constexpr (PTS) {
+      // generators: thread gt forms column jl of the tile (y_j) for the k-chunks 4hh .. 4hh+3
+      // of every 32-row step: A(i, j) for i = 32 it + 4c + u, split into TF32 halves and
+      // stored as 16-byte chunk c of row jl (swizzled: chunk c ^ (jl mod 8)).  The x records
+      // of a step are the same for the 32 lanes of a warp (broadcast loads).
+      const int gt = tid - BS_CONV_WARP0 * 32;        // 0..255
+      const int jl = gt & 127, hh = gt >> 7;
+      const int64_t j = (int64_t)item.tile * 128 + jl;
+      const bool colv = j < blk.n;
+      float4 yc = make_float4(0.f, 0.f, 0.f, 0.f);
+      float2 cy = make_float2(0.f, 0.f);
+      if (colv) {
+        const float4* yr = reinterpret_cast<const float4*>(blk.Y + j * kRec);
+        yc = __ldg(yr);
+        const float4 t = __ldg(yr + 1);
+        cy = make_float2(t.x, t.y);
+      }
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % AS;
+        const uint32_t ph = (uint32_t)(it / AS) & 1u;
+        if (aborted()) break;
+        if (it >= AS && !mbar_wait(empty(s), ph ^ 1u, BS_WAIT_NS)) { fail(); break; }
+        float4* ahi = reinterpret_cast<float4*>(a_buf(s));
+        float4* alo = reinterpret_cast<float4*>(alo_buf(s));
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const int c = 4 * hh + cc;
+          float v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = it * BS_BK + 4 * c + u;
+            v[u] = 0.f;
+            if (colv && i < blk.m) {
+              const float4* xr = reinterpret_cast<const float4*>(blk.A + (int64_t)i * kRec);
+              const float4 xc = __ldg(xr);
+              const float4 t = __ldg(xr + 1);
+              v[u] = kernel_entry(xc, make_float2(t.x, t.y), yc, cy, p.w_hi, p.w_lo);
+            }
+          }
+          float4 h, w;
+          h.x = tf32_rna(v[0]); w.x = tf32_rna(v[0] - h.x);
+          h.y = tf32_rna(v[1]); w.y = tf32_rna(v[1] - h.y);
+          h.z = tf32_rna(v[2]); w.z = tf32_rna(v[2] - h.z);
+          h.w = tf32_rna(v[3]); w.w = tf32_rna(v[3] - h.w);
+          const int pos = jl * 8 + (c ^ (jl & 7));
+          ahi[pos] = h;
+          alo[pos] = w;
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(conv(s));
+      }
+    }
     // converters: A tile -> Ahi in place, Alo beside it (same positions: swizzle-agnostic)
     const int ct = tid - BS_CONV_WARP0 * 32;          // 0..127
-    for (int it = 0; it < nk; ++it) {
+    for (int it = 0; !PTS && it < nk; ++it) {
       const int s = it % AS;
       const uint32_t ph = (uint32_t)(it / AS) & 1u;
       if (aborted()) break;
@@ -231,9 +362,9 @@ batch_sketch_kernel(const __grid_constant__ CUtensorMap tmGhi, const __grid_cons
       __syncwarp();
       if (lane == 0) mbar_arrive(conv(s));
     }
-    // epilogue: lane = column of the tile, TMEM columns = rows of X
-    const bool ok = mbar_wait(done, 0, BS_WAIT_NS);
-    if (!ok) fail();
+    // epilogue (warps 4..7): lane = column of the tile, TMEM columns = rows of X
+    const bool ok = warp < BS_CONV_WARP0 + 4 && mbar_wait(done, 0, BS_WAIT_NS);
+    if (!ok && warp < BS_CONV_WARP0 + 4) fail();
     tc_fence_after();
     if (ok && !aborted()) {
       const int qd = warp & 3;
@@ -302,6 +433,12 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
 // The per-step decision, taken by one thread and read by all after a CTA barrier.  Sums of
 // squares have no cancellation, so FP32 carries them; the rule is tested without a division:
 //   nu_t l <= tol^2 ||X||^2 (l - t).
@@ -313,6 +450,7 @@ struct BlDecision {
 __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLuppParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ BlSlot slot[2][BL_MAXCL];
+  __shared__ float s_amax[BL_MAXCL];
   __shared__ int s_J[BL_MAXK];
   __shared__ float wkey[BL_THREADS / 32];
   __shared__ int widx[BL_THREADS / 32];
@@ -345,16 +483,50 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
     __syncthreads();
   };
 
+  // The block's X is scaled by the power of two that brings its largest magnitude into
+  // [1, 2): exact in FP32, so pivots and ranks do not change, but the squares of Schur
+  // complement entries near the tolerance stay far above FP32's underflow threshold (kernel
+  // blocks between distant clusters have entries near 1e-13, whose tolerance-level residues
+  // would square to ~1e-38).  The scale is agreed across the cluster.
+  float am = 0.f;
+  for (int e0 = tid; e0 < l * nl; e0 += 8 * BL_THREADS) {   // eight loads in flight per thread
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * BL_THREADS;
+      v[u] = e < l * nl ? xb[(int64_t)(e / nl) * n + c0 + e % nl] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * BL_THREADS;
+      if (e < l * nl) {
+        S[(e / nl) * ldp + e % nl] = v[u];
+        am = fmaxf(am, fabsf(v[u]));    // NaN is ignored here and flagged by the pivot search
+      }
+    }
+  }
+  for (int jl = tid; jl < nl; jl += BL_THREADS) sel[jl] = 0;
+  am = warp_max(am);
+  if (lane == 0) wnu[warp] = am;
+  cluster.sync();                        // every CTA of the cluster is running before DSMEM writes
+  if (tid == 0) {
+    float a = 0.f;
+    for (int w = 0; w < BL_THREADS / 32; ++w) a = fmaxf(a, wnu[w]);
+    for (int d = 0; d < CL; ++d) *cluster.map_shared_rank(&s_amax[crank], d) = a;
+  }
+  cluster.sync();
+  float amax = 0.f;
+  for (int d = 0; d < CL; ++d) amax = fmaxf(amax, s_amax[d]);
+  const float sc = amax > 0.f && amax < INFINITY ? ldexpf(1.f, -ilogbf(amax)) : 1.f;
   // sums of squares: FP32 per thread (a few hundred terms), FP64 across threads (FP64
   // arithmetic is scarce on this GPU and these run once per element per step)
   float nu = 0.f;
   for (int e = tid; e < l * nl; e += BL_THREADS) {
     const int r = e / nl, jl = e % nl;
-    const float v = xb[(int64_t)r * n + c0 + jl];
+    const float v = S[r * ldp + jl] * sc;
     S[r * ldp + jl] = v;
     nu = fmaf(v, v, nu);
   }
-  for (int jl = tid; jl < nl; jl += BL_THREADS) sel[jl] = 0;
   block_sum(nu);
 
   int rank = 0, code = 0;
@@ -511,12 +683,25 @@ __global__ void __launch_bounds__(LS_THREADS) batch_lsq_kernel(const BatchLsqPar
   float* Cc = V + (size_t)p.kmax * ldv;                  // [LS_NC][ldv]: a chunk of X's columns
 
   float amax = 0.f;
-  for (int e = tid; e < l * r; e += LS_THREADS) {
-    const int t = e / l, i = e % l;
-    const int j = J[t];
-    const float x = j >= 0 && j < n ? xb[(int64_t)i * n + j] : __int_as_float(0x7fc00000);
-    V[t * ldv + i] = x;
-    amax = fmaxf(amax, fabsf(x));
+  for (int e0 = tid; e0 < l * r; e0 += 8 * LS_THREADS) {    // eight loads in flight per thread
+    float x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * LS_THREADS;
+      x[u] = 0.f;
+      if (e < l * r) {
+        const int j = J[e / l];
+        x[u] = j >= 0 && j < n ? xb[(int64_t)(e % l) * n + j] : __int_as_float(0x7fc00000);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * LS_THREADS;
+      if (e < l * r) {
+        V[(e / l) * ldv + e % l] = x[u];
+        amax = fmaxf(amax, fabsf(x[u]));
+      }
+    }
   }
   // Z = X(:, J)^+ X does not change when X is scaled, so X is scaled by the power of two that
   // brings max |X(:, J)| into [0.5, 1) (exact): blocks far apart in a kernel matrix have
@@ -583,9 +768,18 @@ __global__ void __launch_bounds__(LS_THREADS) batch_lsq_kernel(const BatchLsqPar
   const int jj = tid / LS_TPC, h = tid % LS_TPC;
   for (int c0 = 0; c0 < n; c0 += LS_NC) {
     const int ncw = min(LS_NC, n - c0);
-    for (int e = tid; e < l * ncw; e += LS_THREADS) {
-      const int i = e / ncw, q = e % ncw;
-      Cc[q * ldv + i] = ldexpf(xb[(int64_t)i * n + c0 + q], sh);
+    for (int e0 = tid; e0 < l * ncw; e0 += 8 * LS_THREADS) {   // eight loads in flight per thread
+      float x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * LS_THREADS;
+        x[u] = e < l * ncw ? xb[(int64_t)(e / ncw) * n + c0 + e % ncw] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * LS_THREADS;
+        if (e < l * ncw) Cc[(e % ncw) * ldv + e / ncw] = ldexpf(x[u], sh);
+      }
     }
     __syncthreads();
     const bool act = jj < ncw;
@@ -658,6 +852,14 @@ struct skel_batch_plan {
   cudaGraphExec_t exec = nullptr; // the captured run, bound to the outputs below
   const void* bound[4] = {nullptr, nullptr, nullptr, nullptr};
   int graph_launches = 0;
+  // point plans (kernel blocks evaluated inside the sketch)
+  bool points = false;
+  int dim = 0;
+  double inv_h2 = 0.0;
+  float w_hi = 0.f, w_lo = 0.f;
+  float* d_rec = nullptr;         // point records of every block
+  PointSrc* d_src = nullptr;
+  std::vector<int64_t> xoff;      // nb + 1 prefix offsets of X (floats)
 };
 
 namespace {
@@ -678,6 +880,8 @@ void plan_free(skel_batch_plan* pl) {
   cudaFree(pl->d_ghi);
   cudaFree(pl->d_glo);
   cudaFree(pl->d_X);
+  cudaFree(pl->d_rec);
+  cudaFree(pl->d_src);
   delete pl;
 }
 
@@ -704,6 +908,10 @@ size_t sketch_smem_for(int lp, int stages) {
 skel_status enqueue_run(skel_batch_plan* pl, int32_t* Js, int32_t* ranks, double* Z, int32_t* dev_status,
                         cudaStream_t st, bool timers, int* launches) {
   int nl = 0;
+  if (pl->points) {
+    batch_points_prep_kernel<<<dim3(4, (unsigned)pl->nb), 256, 0, st>>>(pl->d_src, pl->dim, pl->inv_h2);
+    ++nl;
+  }
   batch_gamma_kernel<<<std::min<int64_t>(((int64_t)pl->lp * pl->mg / 4 + 255) / 256, 1024), 256, 0, st>>>(
       pl->l, pl->lp, pl->mg, (uint32_t)(pl->seed & 0xffffffffu), (uint32_t)(pl->seed >> 32), pl->d_ghi, pl->d_glo);
   ++nl;
@@ -716,10 +924,15 @@ skel_status enqueue_run(skel_batch_plan* pl, int32_t* Js, int32_t* ranks, double
   sp.lp = pl->lp;
   sp.stages = pl->stages;
   sp.scale = (float)(1.0 / std::sqrt((double)pl->l));
+  sp.w_hi = pl->w_hi;
+  sp.w_lo = pl->w_lo;
   sp.dev_status = dev_status;
   {
     KernelTimer kt(timers ? "batch_sketch" : nullptr, st);
-    batch_sketch_kernel<<<pl->n_items, BS_THREADS, pl->sketch_smem, st>>>(pl->tm_ghi, pl->tm_glo, sp);
+    if (pl->points)
+      batch_sketch_kernel<true><<<pl->n_items, BS_THREADS_P, pl->sketch_smem, st>>>(pl->tm_ghi, pl->tm_glo, sp);
+    else
+      batch_sketch_kernel<false><<<pl->n_items, BS_THREADS, pl->sketch_smem, st>>>(pl->tm_ghi, pl->tm_glo, sp);
   }
   ++nl;
   if (cudaGetLastError() != cudaSuccess) return SKEL_ERR_CUDA;
@@ -846,16 +1059,24 @@ skel_status autotune(skel_batch_plan* pl) {
   return hst[0] == 0 ? SKEL_OK : (skel_status)hst[0];
 }
 
-}  // namespace
+struct PointArgs {
+  int dim;
+  const float* const* x;
+  const float* const* y;
+  double h;
+};
 
-extern "C" {
-
-skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int64_t* n, const float* const* A,
-                                   const int64_t* lda, int32_t kmax, int32_t p, double tol, uint64_t seed,
-                                   int32_t flags, skel_batch_plan** plan) {
+// Stored blocks (A, lda) or, with pts, Gaussian-kernel blocks given by point sets.
+static skel_status plan_create(int32_t nblocks, const int64_t* m, const int64_t* n, const float* const* A,
+                               const int64_t* lda, const PointArgs* pts, int32_t kmax, int32_t p, double tol,
+                               uint64_t seed, int32_t flags, skel_batch_plan** plan) {
   if (plan == nullptr) return SKEL_ERR_INVALID_ARG;
   *plan = nullptr;
-  if (nblocks < 1 || m == nullptr || n == nullptr || A == nullptr || lda == nullptr) return SKEL_ERR_INVALID_ARG;
+  if (nblocks < 1 || m == nullptr || n == nullptr) return SKEL_ERR_INVALID_ARG;
+  if (pts == nullptr && (A == nullptr || lda == nullptr)) return SKEL_ERR_INVALID_ARG;
+  if (pts && (pts->x == nullptr || pts->y == nullptr || pts->dim < 1 || pts->dim > 3 || !(pts->h > 0.0) ||
+              !std::isfinite(pts->h) || !std::isfinite(1.0 / (pts->h * pts->h))))
+    return SKEL_ERR_INVALID_ARG;
   if (kmax < 1 || kmax > BL_MAXK || p < 1 || kmax + p > BL_MAXL || !(tol >= 0.0) || !std::isfinite(tol))
     return SKEL_ERR_INVALID_ARG;
   if (flags & ~(SKEL_BATCH_GRAPH | SKEL_BATCH_AUTOTUNE)) return SKEL_ERR_INVALID_ARG;
@@ -865,9 +1086,13 @@ skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int6
   int64_t mmax = 0;
   std::vector<int> cls(nblocks);
   for (int b = 0; b < nblocks; ++b) {
-    if (m[b] < 1 || n[b] < 1 || m[b] > INT32_MAX || n[b] > INT32_MAX || lda[b] < m[b] || A[b] == nullptr)
-      return SKEL_ERR_INVALID_ARG;
-    if (lda[b] % 4 != 0 || (reinterpret_cast<uintptr_t>(A[b]) & 15) != 0) return SKEL_ERR_UNSUPPORTED;
+    if (m[b] < 1 || n[b] < 1 || m[b] > INT32_MAX || n[b] > INT32_MAX) return SKEL_ERR_INVALID_ARG;
+    if (pts) {
+      if (pts->x[b] == nullptr || pts->y[b] == nullptr) return SKEL_ERR_INVALID_ARG;
+    } else {
+      if (lda[b] < m[b] || A[b] == nullptr) return SKEL_ERR_INVALID_ARG;
+      if (lda[b] % 4 != 0 || (reinterpret_cast<uintptr_t>(A[b]) & 15) != 0) return SKEL_ERR_UNSUPPORTED;
+    }
     mmax = std::max(mmax, m[b]);
     int c = 0;
     while (c < 3 && lupp_smem(l, kmax, (int)((n[b] + (1 << c) - 1) >> c)) > budget) ++c;
@@ -876,6 +1101,9 @@ skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int6
   }
   EncodeTiledFn enc = encode_fn();
   if (!enc) return SKEL_ERR_UNSUPPORTED;
+  int64_t npts = 0;
+  if (pts)
+    for (int b = 0; b < nblocks; ++b) npts += m[b] + n[b];
   skel_batch_plan* pl = new (std::nothrow) skel_batch_plan();
   if (!pl) return SKEL_ERR_WORKSPACE;
   pl->nb = nblocks;
@@ -886,20 +1114,46 @@ skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int6
   pl->seed = seed;
   pl->mg = (mmax + 31) / 32 * 32;
   pl->flags = flags;
+  if (pts) {
+    pl->points = true;
+    pl->dim = pts->dim;
+    pl->inv_h2 = 1.0 / (pts->h * pts->h);
+    const double w = 2.0 * pl->inv_h2;
+    pl->w_hi = (float)w;
+    pl->w_lo = (float)(w - (double)pl->w_hi);
+  }
   // shared memory of the sketch: 3 stages when they fit, else 2 (the autotuner may pick 2)
   pl->max_stages = sketch_smem_for(lp, 3) <= 227 * 1024 ? 3 : 2;
   pl->stages = pl->max_stages;
   pl->sketch_smem = sketch_smem_for(lp, pl->stages);
 
   std::vector<BatchBlock> hb(nblocks);
-  std::vector<CUtensorMap> ht(nblocks);
+  std::vector<CUtensorMap> ht(pts ? 0 : nblocks);
   std::vector<SketchItem> items;
+  std::vector<PointSrc> hsrc(pts ? nblocks : 0);
+  if (pts && cudaMalloc(&pl->d_rec, sizeof(float) * kRec * (size_t)npts) != cudaSuccess) {
+    cudaGetLastError();
+    plan_free(pl);
+    return SKEL_ERR_CUDA;
+  }
   pl->zoff.assign(nblocks + 1, 0);
-  int64_t xo = 0;
+  pl->xoff.assign(nblocks + 1, 0);
+  int64_t xo = 0, ro = 0;
   for (int b = 0; b < nblocks; ++b) {
-    hb[b] = BatchBlock{A[b], lda[b], (int32_t)m[b], (int32_t)n[b], xo, pl->zoff[b]};
+    if (pts) {
+      float* xr = pl->d_rec + ro * kRec;
+      float* yr = xr + m[b] * kRec;
+      ro += m[b] + n[b];
+      hsrc[b] = PointSrc{pts->x[b], pts->y[b], (int32_t)m[b], (int32_t)n[b], xr, yr};
+      hb[b] = BatchBlock{xr, 0, (int32_t)m[b], (int32_t)n[b], xo, pl->zoff[b], yr};
+    } else {
+      hb[b] = BatchBlock{A[b], lda[b], (int32_t)m[b], (int32_t)n[b], xo, pl->zoff[b], nullptr};
+    }
     xo += (int64_t)l * n[b];
+    pl->xoff[b + 1] = xo;
     pl->zoff[b + 1] = pl->zoff[b] + (int64_t)kmax * n[b];
+    for (int t = 0; t < (int)((n[b] + 127) / 128); ++t) items.push_back(SketchItem{b, t});
+    if (pts) continue;
     const cuuint64_t gdim[2] = {(cuuint64_t)m[b], (cuuint64_t)n[b]};
     const cuuint64_t gstride[1] = {(cuuint64_t)lda[b] * sizeof(float)};
     const cuuint32_t box[2] = {BS_BK, 128};
@@ -910,7 +1164,6 @@ skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int6
       plan_free(pl);
       return SKEL_ERR_UNSUPPORTED;
     }
-    for (int t = 0; t < (int)((n[b] + 127) / 128); ++t) items.push_back(SketchItem{b, t});
   }
   // longest work first
   std::stable_sort(items.begin(), items.end(), [&](const SketchItem& a, const SketchItem& c) { return m[a.b] > m[c.b]; });
@@ -929,14 +1182,17 @@ skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int6
     pl->cls_count[c] = (int)v.size();
   }
   bool ok = cudaMalloc(&pl->d_blocks, sizeof(BatchBlock) * nblocks) == cudaSuccess &&
-            cudaMalloc(&pl->d_tmaps, sizeof(CUtensorMap) * nblocks) == cudaSuccess &&
+            (pts || cudaMalloc(&pl->d_tmaps, sizeof(CUtensorMap) * nblocks) == cudaSuccess) &&
+            (!pts || cudaMalloc(&pl->d_src, sizeof(PointSrc) * nblocks) == cudaSuccess) &&
             cudaMalloc(&pl->d_items, sizeof(SketchItem) * items.size()) == cudaSuccess &&
             cudaMalloc(&pl->d_order, sizeof(int32_t) * order.size()) == cudaSuccess &&
             cudaMalloc(&pl->d_ghi, sizeof(float) * (size_t)lp * pl->mg) == cudaSuccess &&
             cudaMalloc(&pl->d_glo, sizeof(float) * (size_t)lp * pl->mg) == cudaSuccess &&
             cudaMalloc(&pl->d_X, sizeof(float) * (size_t)std::max<int64_t>(xo, 1)) == cudaSuccess;
   ok = ok && cudaMemcpy(pl->d_blocks, hb.data(), sizeof(BatchBlock) * nblocks, cudaMemcpyHostToDevice) == cudaSuccess &&
-       cudaMemcpy(pl->d_tmaps, ht.data(), sizeof(CUtensorMap) * nblocks, cudaMemcpyHostToDevice) == cudaSuccess &&
+       (pts || cudaMemcpy(pl->d_tmaps, ht.data(), sizeof(CUtensorMap) * nblocks, cudaMemcpyHostToDevice) ==
+                   cudaSuccess) &&
+       (!pts || cudaMemcpy(pl->d_src, hsrc.data(), sizeof(PointSrc) * nblocks, cudaMemcpyHostToDevice) == cudaSuccess) &&
        cudaMemcpy(pl->d_items, items.data(), sizeof(SketchItem) * items.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(pl->d_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice) == cudaSuccess;
   if (ok) {
@@ -951,8 +1207,10 @@ skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int6
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   }
-  ok = ok && cudaFuncSetAttribute(batch_sketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  ok = ok && cudaFuncSetAttribute(batch_sketch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sketch_smem_for(lp, pl->max_stages)) == cudaSuccess &&
+       cudaFuncSetAttribute(batch_sketch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)sketch_smem_for(lp, pl->max_stages)) == cudaSuccess &&
        cudaFuncSetAttribute(batch_lupp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget) == cudaSuccess &&
        cudaFuncSetAttribute(batch_lsq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsq_smem(l, kmax)) ==
            cudaSuccess;
@@ -974,6 +1232,33 @@ skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int6
     }
   }
   *plan = pl;
+  return SKEL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+skel_status skel_batch_plan_create(int32_t nblocks, const int64_t* m, const int64_t* n, const float* const* A,
+                                   const int64_t* lda, int32_t kmax, int32_t p, double tol, uint64_t seed,
+                                   int32_t flags, skel_batch_plan** plan) {
+  return plan_create(nblocks, m, n, A, lda, nullptr, kmax, p, tol, seed, flags, plan);
+}
+
+skel_status skel_batch_plan_create_points(int32_t nblocks, const int64_t* m, const int64_t* n, int32_t dim,
+                                          const float* const* x, const float* const* y, double h, int32_t kmax,
+                                          int32_t p, double tol, uint64_t seed, int32_t flags,
+                                          skel_batch_plan** plan) {
+  const PointArgs pa{dim, x, y, h};
+  return plan_create(nblocks, m, n, nullptr, nullptr, &pa, kmax, p, tol, seed, flags, plan);
+}
+
+skel_status skel_batch_copy_sketch(const skel_batch_plan* plan, int32_t b, float* X, cudaStream_t stream) {
+  if (plan == nullptr || X == nullptr || b < 0 || b >= plan->nb) return SKEL_ERR_INVALID_ARG;
+  const int64_t cnt = plan->xoff[b + 1] - plan->xoff[b];
+  if (cudaMemcpyAsync(X, plan->d_X + plan->xoff[b], sizeof(float) * (size_t)cnt, cudaMemcpyDeviceToDevice, stream) !=
+      cudaSuccess)
+    return SKEL_ERR_CUDA;
   return SKEL_OK;
 }
 

@@ -49,6 +49,7 @@ struct PanelParams {
   int64_t ldm;         // row stride of M (b when the panel kernel writes it)
   int64_t trow0;       // first trailing row the trailing update covers (t0 + b by default)
   int trows;           // trailing rows it covers (s - t0 - b by default)
+  int epi_rows;        // rows t0+b .. whose multipliers the panel kernel's epilogue forms
   unsigned char sel_tag;    // sel value of columns this panel selects: panel index + 1
   unsigned char sel_limit;  // trailing update skips columns with 0 < sel <= sel_limit
 };
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
   // subtracts M(r, qq) R(t0+qq, j_q) -- the same operations in the same order as
   // step-by-step elimination.  R(panel, J_panel) is read from the owners' shared memory.
   cluster.sync();     // every CTA's R rows are final in its shared memory
-  const bool trail = !stopped && done == b && p.s - p.t0 - b > 0;
+  const bool trail = !stopped && done == b && p.epi_rows > 0;
   if (trail) {                         // eight distributed-shared-memory loads in flight per thread
     for (int e0 = tid; e0 < b * b; e0 += 8 * bd) {
       T v[8];
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
   }
   cluster.sync();     // no CTA leaves or reuses its shared memory while others read it
   if (trail) {
-    const int rows = p.s - p.t0 - b;
+    const int rows = p.epi_rows;
     for (int ri = crank * nw + warp; ri < rows; ri += CL * nw) {
       const int64_t r = p.t0 + b + ri;
       const int q0 = lane, q1 = lane + 32;
@@ -977,13 +978,14 @@ __global__ void __launch_bounds__(256) lupp_gpanel_kernel(const GPanelParams p, 
   for (int jj = tid; jj < nl; jj += bd) p.sel[c0 + jj] = sl[jj];
 }
 
-// Multipliers of the trailing rows r = t0+b .. s-1 for a finished panel, one warp per row:
-// M(r, q) = S^(q)(r, j_q) = X(r, j_q) - sum_{q' < q} M(r, q') R(t0 + q', j_q), the subtractions
-// in q' order (lane i owns q = i and i + 32; M(r, q') is broadcast when final).
+// Multipliers of the rows r = r0 .. r1-1 (below a finished panel) for the panel's steps, one
+// warp per row: M(r, q) = S^(q)(r, j_q) = X(r, j_q) - sum_{q' < q} M(r, q') R(t0 + q', j_q),
+// the subtractions in q' order (lane i owns q = i and i + 32; M(r, q') is broadcast when
+// final).  M(r, q) goes to M[(r - r0) * ldm + q] and, when L is given, to L(r, t0 + q).
 template <typename T>
-__global__ void __launch_bounds__(256) lupp_gmult_kernel(const T* Xg, int64_t n, int s, int t0, int b, const T* R,
-                                                         int64_t ldr, const int32_t* Js, T* M, int64_t ldm, T* L,
-                                                         int64_t ldl, const int32_t* fail) {
+__global__ void __launch_bounds__(256) lupp_gmult_kernel(const T* Xg, int64_t n, int64_t r0, int64_t r1, int t0, int b,
+                                                         const T* R, int64_t ldr, const int32_t* Js, T* M,
+                                                         int64_t ldm, T* L, int64_t ldl, const int32_t* fail) {
   __shared__ T RJ[kMaxPanel][kMaxPanel + 1];           // RJ[qq][q] = R(t0 + qq, j_q)
   __shared__ int jq[kMaxPanel];
   if (*(volatile const int32_t*)fail) return;
@@ -995,14 +997,14 @@ __global__ void __launch_bounds__(256) lupp_gmult_kernel(const T* Xg, int64_t n,
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int64_t r = t0 + b + (int64_t)blockIdx.x * nw + warp; r < s; r += (int64_t)gridDim.x * nw) {
+  for (int64_t r = r0 + (int64_t)blockIdx.x * nw + warp; r < r1; r += (int64_t)gridDim.x * nw) {
     const int qa = lane, qb = lane + 32;
     T xa = qa < b ? Xg[r * n + jq[qa]] : T(0);
     T xb = qb < b ? Xg[r * n + jq[qb]] : T(0);
     for (int qq = 0; qq < b; ++qq) {
       const T m = __shfl_sync(0xffffffffu, qq < 32 ? xa : xb, qq & 31);
       if (lane == 0) {
-        M[(r - t0 - b) * ldm + qq] = m;
+        M[(r - r0) * ldm + qq] = m;
         if (L) L[r * ldl + t0 + qq] = m;
       }
       if (qa > qq && qa < b) xa = dsub(xa, dmul(m, RJ[qq][qa]));
@@ -1075,8 +1077,54 @@ PanelPlan plan_panel(int64_t n, int s) {
 template <typename T>
 size_t panel_ws(int64_t n, int s, bool need_r) {
   return align_up(sizeof(T) * (size_t)s * n) + align_up(n) + 256 + align_up(sizeof(T) * (size_t)s * 64) +
-         (need_r ? align_up(sizeof(T) * (size_t)s * n) : 0);
+         align_up(sizeof(T) * (size_t)kMaxPanel * kMaxPanel) + (need_r ? align_up(sizeof(T) * (size_t)s * n) : 0);
 }
+
+// Streams of the look-ahead schedule (one set per device, used under its mutex while a call
+// enqueues): `hi` (highest priority) carries the panels and the updates of the next panel's
+// rows, `lo` (lowest priority) the bulk trailing updates.
+struct LookaheadSet {
+  cudaStream_t hi = nullptr, lo = nullptr;
+  cudaEvent_t fork = nullptr, join_hi = nullptr, join_lo = nullptr, panel_done = nullptr, bulk_done = nullptr;
+};
+
+std::mutex& lookahead_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+
+LookaheadSet* lookahead_set() {
+  static LookaheadSet sets[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  LookaheadSet& a = sets[dev];
+  if (a.hi) return &a;
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return nullptr;
+  bool ok = cudaStreamCreateWithPriority(&a.hi, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+            cudaStreamCreateWithPriority(&a.lo, cudaStreamNonBlocking, least) == cudaSuccess;
+  for (cudaEvent_t* e : {&a.fork, &a.join_hi, &a.join_lo, &a.panel_done, &a.bulk_done})
+    ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    a.hi = nullptr;
+    return nullptr;
+  }
+  return &a;
+}
+
+// Joins both look-ahead streams back into the caller's stream on every return path.
+struct LookaheadJoin {
+  cudaStream_t st;
+  LookaheadSet* la;
+  ~LookaheadJoin() {
+    if (cudaEventRecord(la->join_hi, la->hi) == cudaSuccess) cudaStreamWaitEvent(st, la->join_hi, 0);
+    if (cudaEventRecord(la->join_lo, la->lo) == cudaSuccess) cudaStreamWaitEvent(st, la->join_lo, 0);
+  }
+};
+
+template <typename T>
+cudaError_t launch_panel(const PanelParams<T>& p, const PanelPlan& pl, cudaStream_t st);
 
 template <typename T>
 skel_status run_panel_t(const PanelPlan& pl, const T* X, int64_t n, int64_t ldx, int s, int32_t* Js,
@@ -1092,6 +1140,8 @@ skel_status run_panel_t(const PanelPlan& pl, const T* X, int64_t n, int64_t ldx,
   base += 256;
   p.M = reinterpret_cast<T*>(base);
   base += align_up(sizeof(T) * (size_t)s * 64);
+  T* Mnext = reinterpret_cast<T*>(base);             // multipliers of the next panel's rows
+  base += align_up(sizeof(T) * (size_t)kMaxPanel * kMaxPanel);
   if (R == nullptr) {
     R = reinterpret_cast<T*>(base);
     ldr = n;
@@ -1106,33 +1156,57 @@ skel_status run_panel_t(const PanelPlan& pl, const T* X, int64_t n, int64_t ldx,
   if (pl.CL > 8 &&
       cudaFuncSetAttribute(lupp_panel_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
     return SKEL_ERR_CUDA;
-  p.sel_limit = 255;
-  for (int t0 = 0; t0 < s; t0 += pl.b) {
-    p.t0 = t0;
-    p.b = std::min(pl.b, s - t0);
-    p.sel_tag = (unsigned char)(t0 / pl.b + 1);
-    p.ldm = p.b;
-    p.trow0 = t0 + p.b;
-    p.trows = s - t0 - p.b;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(pl.CL);
-    cfg.blockDim = dim3(kPanelThreads);
-    cfg.dynamicSmemBytes = panel_smem<T>(p.b, pl.ncl);
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = pl.CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+  // Look-ahead schedule.  Panel k (rows [t_k, t_k + b)) needs its rows updated by every
+  // earlier panel.  After panel k: on `hi`, the multipliers and the update of panel k+1's rows
+  // only (then panel k+1 starts); on `lo`, concurrently with panel k+1, the multipliers and
+  // the update of rows t_{k+2} .. s-1 (the bulk).  Panel k+1's look-ahead waits for the bulk
+  // of panel k, which holds panel k's update of panel k+2's rows.  Every entry still receives
+  // the panels' updates in panel order and, within a panel, step by step with separately
+  // rounded multiply and subtract, so the factors equal the sequential schedule's bit for bit.
+  std::lock_guard<std::mutex> lock(lookahead_mutex());
+  LookaheadSet* la = lookahead_set();
+  if (la == nullptr) return SKEL_ERR_CUDA;
+  if (cudaEventRecord(la->fork, st) != cudaSuccess || cudaStreamWaitEvent(la->hi, la->fork, 0) != cudaSuccess ||
+      cudaStreamWaitEvent(la->lo, la->fork, 0) != cudaSuccess)
+    return SKEL_ERR_CUDA;
+  LookaheadJoin joiner{st, la};
+  auto rows_update = [&](const PanelParams<T>& pp, int64_t r0, int64_t r1, T* Mb, cudaStream_t cs) -> cudaError_t {
     {
-      KernelTimer kt("lupp_panel", st);
-      if (cudaLaunchKernelEx(&cfg, lupp_panel_kernel<T>, p) != cudaSuccess) return SKEL_ERR_CUDA;
+      KernelTimer kt("lupp_mult", cs);
+      lupp_gmult_kernel<T><<<(unsigned)std::min<int64_t>((r1 - r0 + 7) / 8, 1024), 256, 0, cs>>>(
+          pp.Xg, pp.n, r0, r1, pp.t0, pp.b, pp.R, pp.ldr, pp.Js, Mb, pp.b, pp.L, pp.ldl, pp.fail);
     }
     note_launches(1);
-    const int rows = s - t0 - p.b;
-    if (rows > 0 && launch_trail<T>(p, rows, st) != cudaSuccess) return SKEL_ERR_CUDA;
+    PanelParams<T> q = pp;
+    q.M = Mb;
+    q.ldm = pp.b;
+    q.trow0 = r0;
+    q.trows = (int)(r1 - r0);
+    return launch_trail<T>(q, q.trows, cs);
+  };
+  for (int t0 = 0, k = 0; t0 < s; t0 += pl.b, ++k) {
+    p.t0 = t0;
+    p.b = std::min(pl.b, s - t0);
+    p.sel_tag = (unsigned char)(k + 1);
+    p.sel_limit = p.sel_tag;               // the bulk runs while the next panel tags its columns
+    p.ldm = p.b;
+    p.trow0 = t0 + p.b;
+    p.trows = 0;
+    p.epi_rows = 0;
+    if (launch_panel<T>(p, pl, la->hi) != cudaSuccess) return SKEL_ERR_CUDA;
+    const int t1 = t0 + p.b;
+    if (t1 >= s) break;
+    const int t2 = t1 + std::min(pl.b, s - t1);
+    if (t2 < s) {                          // the bulk of panel k
+      if (cudaEventRecord(la->panel_done, la->hi) != cudaSuccess ||
+          cudaStreamWaitEvent(la->lo, la->panel_done, 0) != cudaSuccess)
+        return SKEL_ERR_CUDA;
+      if (rows_update(p, t2, s, p.M, la->lo) != cudaSuccess) return SKEL_ERR_CUDA;
+    }
+    // panel k+1's rows: they hold panel k-1's update once the bulk of panel k-1 is done
+    if (k > 0 && cudaStreamWaitEvent(la->hi, la->bulk_done, 0) != cudaSuccess) return SKEL_ERR_CUDA;
+    if (rows_update(p, t1, t2, Mnext, la->hi) != cudaSuccess) return SKEL_ERR_CUDA;
+    if (t2 < s && cudaEventRecord(la->bulk_done, la->lo) != cudaSuccess) return SKEL_ERR_CUDA;
   }
   return cudaGetLastError() == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
 }
@@ -1227,6 +1301,7 @@ skel_status run_skeleton_t(const PanelPlan& pc, const PanelPlan& pr, const T* X,
     c.ldm = c.b;
     c.trow0 = t0 + c.b;
     c.trows = s - t0 - c.b;
+    c.epi_rows = c.trows;
     if (launch_panel<T>(c, pc, st) != cudaSuccess) return SKEL_ERR_CUDA;
     if (cudaEventRecord(aux->col[k], st) != cudaSuccess) return SKEL_ERR_CUDA;
     if (c.trows > 0 && launch_trail<T>(c, c.trows, st) != cudaSuccess) return SKEL_ERR_CUDA;
@@ -1239,6 +1314,7 @@ skel_status run_skeleton_t(const PanelPlan& pc, const PanelPlan& pr, const T* X,
     r.t0 = t0;
     r.b = std::min(pr.b, s - t0);
     r.s = t0 + r.b;                       // no rows below: the epilogue forms no multipliers
+    r.epi_rows = 0;
     r.sel_tag = (unsigned char)(k + 1);
     if (cudaStreamWaitEvent(aux->st, aux->col[(t0 + r.b - 1) / pc.b], 0) != cudaSuccess) return SKEL_ERR_CUDA;
     lupp_gather_panel_kernel<T><<<dim3((unsigned)std::min<int64_t>((m + 255) / 256, 32), (unsigned)r.b), 256, 0, aux->st>>>(
@@ -1416,8 +1492,11 @@ skel_status run_gpanel_t(const GPanelPlan& pl, const T* X, int64_t n, int64_t ld
     note_launches(1);
     const int trows = s - t0 - bb;
     if (trows <= 0) continue;
-    lupp_gmult_kernel<T><<<(unsigned)std::min<int64_t>((trows + 7) / 8, 1024), 256, 0, st>>>(
-        Xg, n, s, t0, bb, R, ldr, Js, M, bb, L, ldl, fail);
+    {
+      KernelTimer kt("lupp_mult", st);
+      lupp_gmult_kernel<T><<<(unsigned)std::min<int64_t>((trows + 7) / 8, 1024), 256, 0, st>>>(
+          Xg, n, t0 + bb, s, t0, bb, R, ldr, Js, M, bb, L, ldl, fail);
+    }
     note_launches(1);
     PanelParams<T> tp{};
     tp.Xg = Xg; tp.n = n; tp.s = s; tp.t0 = t0; tp.b = bb; tp.R = R; tp.ldr = ldr; tp.fail = fail;

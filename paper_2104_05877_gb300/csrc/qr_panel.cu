@@ -52,6 +52,8 @@ struct QrPanelParams {
   double* R; int64_t ldr;      // out: s x s row-major
   int32_t* fail;
   int32_t* dev_status;
+  GridComm gc;                 // grid panels: per-step slots of the CTAs' partial dot products
+  T* growt;                    // grid panels: row t of the panel, [2][kQrMaxB]
 };
 
 __host__ __device__ constexpr int qr_b4(int b) { return (b + 3) / 4 * 4; }
@@ -166,20 +168,27 @@ __device__ __forceinline__ int xr_index(int lane) {
 
 constexpr int kQrMaxChunks = 8;       // rows per CTA <= 8 chunks of 512
 
-template <typename T>
+// GRID: the panel is spread over a cooperative grid instead of one cluster (m too tall for a
+// cluster's shared memory).  Each CTA then publishes its partial dot products (and the owner
+// of row t that row) to a global slot per step, one grid barrier follows, and every CTA sums
+// the G partials of each column itself in the same fixed order (lanes over CTAs, then a
+// butterfly), so the reflector and every update are again identical in every CTA.
+template <typename T, bool GRID>
 __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(const QrPanelParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cluster = cg::this_cluster();
-  const int crank = (int)cluster.block_rank();
-  const int CL = (int)cluster.num_blocks();
+  const int crank = GRID ? (int)blockIdx.x : (int)cluster.block_rank();
+  const int CL = GRID ? (int)gridDim.x : (int)cluster.num_blocks();
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
   const int b = p.b, b4 = qr_b4(b), mloc = p.mloc, t0 = p.t0;
   const int64_t r0 = (int64_t)crank * mloc;
   const int ml = (int)(p.m - r0 < 0 ? 0 : (p.m - r0 < mloc ? p.m - r0 : mloc));
 
-  __shared__ __align__(16) T part[kQrInbox][16][kQrMaxB];   // partial dot products per sender
-  __shared__ __align__(16) T rowt[kQrInbox][kQrMaxB];       // row t of the panel
+  __shared__ __align__(16) T part[GRID ? 1 : kQrInbox][GRID ? 1 : 16][kQrMaxB];   // partials per sender
+  __shared__ __align__(16) T rowt[GRID ? 1 : kQrInbox][kQrMaxB];       // row t of the panel
   __shared__ __align__(8) uint64_t qbar[kQrInbox];
+  __shared__ __align__(16) T dsum[kQrMaxB];                 // this step's summed dot products
+  __shared__ __align__(16) T srow[kQrMaxB];                 // this step's row t
   __shared__ __align__(16) T wloc[kQrMaxB];                 // this CTA's partials for the next step
   __shared__ __align__(16) T rownext[kQrMaxB];              // row t+1 (owner)
   __shared__ T wv[kQrMaxB];                                 // tau * w_j of the current step
@@ -189,11 +198,23 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(const QrPanelPa
 
   if (*(volatile int32_t*)p.fail) return;
   if (tid == 0) {
-    for (int k = 0; k < kQrInbox; ++k) mbar_init(smem_u32(&qbar[k]), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if constexpr (!GRID) {
+      for (int k = 0; k < kQrInbox; ++k) mbar_init(smem_u32(&qbar[k]), 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     s_timeout = 0;
     s_stop = 0;
   }
+  // grid panels: publish this CTA's partials (and row t, by its owner) for step c
+  auto publish = [&](int c, bool owner) {
+    if constexpr (GRID) {
+      T* sl = reinterpret_cast<T*>(p.gc.slot(c, crank));
+      for (int j = tid; j < b4; j += bd) sl[j] = wloc[j];
+      if (owner)
+        for (int j = tid; j < b4; j += bd) p.growt[(c & 1) * kQrMaxB + j] = rownext[j];
+      comm_arrive(p.gc, c);
+    }
+  };
   // load the panel (rows past m are zero); rows above the panel hold final R entries
   for (int j0 = 0; j0 < b; j0 += 8)         // eight independent loads in flight per thread
     for (int i = tid; i < mloc; i += bd) {
@@ -228,35 +249,64 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(const QrPanelPa
   if (crank == owner0)
     for (int j = tid; j < b4; j += bd) rownext[j] = j < b ? P[(size_t)j * mloc + (t0 - r0)] : T(0);
   __syncthreads();
-  if (tid == 0)
-    for (int k = 0; k < kQrInbox && k < b; ++k) mbar_expect_tx(bar_at(k), qr_step_bytes<T>(CL, b, k));
-  cluster.sync();     // barriers initialised and armed everywhere before the first send
-  qr_send<T>(wloc, part_dst(0), bar_at(0), CL, 0, b4, tid, bd / 2);
-  if (crank == owner0) qr_send<T>(rownext, rowt_dst(0), bar_at(0), CL, 0, b4, tid - bd / 2 >= 0 ? tid - bd / 2 : bd, bd / 2);
+  if constexpr (GRID) {
+    publish(0, crank == owner0);
+  } else {
+    if (tid == 0)
+      for (int k = 0; k < kQrInbox && k < b; ++k) mbar_expect_tx(bar_at(k), qr_step_bytes<T>(CL, b, k));
+    cluster.sync();     // barriers initialised and armed everywhere before the first send
+    qr_send<T>(wloc, part_dst(0), bar_at(0), CL, 0, b4, tid, bd / 2);
+    if (crank == owner0) qr_send<T>(rownext, rowt_dst(0), bar_at(0), CL, 0, b4, tid - bd / 2 >= 0 ? tid - bd / 2 : bd, bd / 2);
+  }
 
   bool stopped = false;
   for (int c = 0; c < b; ++c) {
     const int64_t t = t0 + c;
     const int buf = c % kQrInbox;
     const uint32_t par = (uint32_t)((c / kQrInbox) & 1);
-    if (warp == 0) {                     // one warp polls; the others wait at the CTA barrier
-      const bool okw = mbar_wait(bar_at(buf), par, kDefaultWaitNs);
-      if (!__all_sync(0xffffffffu, okw) && lane == 0 && atomicExch(&s_timeout, 1) == 0) {
-        record_error(p.dev_status, SKEL_ERR_TIMEOUT, (int)t);
-        atomicExch(p.fail, 1);
+    if constexpr (GRID) {
+      if (!comm_wait(p.gc, c, p.dev_status)) {       // uniform over the CTA
+        if (tid == 0) atomicExch(p.fail, 1);
+        stopped = true;
+        break;
+      }
+      // dsum[j] = sum over the CTAs of their partials, in a fixed order (lanes over CTAs,
+      // then a butterfly): the same bits in every CTA
+      for (int j = (c & ~3) + warp; j < b4; j += nw) {
+        T d = T(0);
+        for (int k = lane; k < CL; k += 32) d += __ldcg(reinterpret_cast<const T*>(p.gc.slot(c, k)) + j);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) dsum[j] = d;
+      }
+      for (int j = tid; j < b4; j += bd) srow[j] = __ldcg(p.growt + (c & 1) * kQrMaxB + j);   // L2: slots are reused
+    } else {
+      if (warp == 0) {                   // one warp polls; the others wait at the CTA barrier
+        const bool okw = mbar_wait(bar_at(buf), par, kDefaultWaitNs);
+        if (!__all_sync(0xffffffffu, okw) && lane == 0 && atomicExch(&s_timeout, 1) == 0) {
+          record_error(p.dev_status, SKEL_ERR_TIMEOUT, (int)t);
+          atomicExch(p.fail, 1);
+        }
+      }
+      __syncthreads();
+      if (s_timeout) {
+        stopped = true;
+        break;
+      }
+      if (warp != 0) mbar_try_wait(bar_at(buf), par);   // acquire of the completed phase
+      if (tid == bd - 1 && c + kQrInbox < b) mbar_expect_tx(bar_at(buf), qr_step_bytes<T>(CL, b, c + kQrInbox));
+      // the partials of the CL CTAs summed in CTA order
+      for (int j = tid; j < b4; j += bd) {
+        T d = T(0);
+        for (int k = 0; k < CL; ++k) d += part[buf][k][j];
+        dsum[j] = d;
+        srow[j] = rowt[buf][j];
       }
     }
     __syncthreads();
-    if (s_timeout) {
-      stopped = true;
-      break;
-    }
-    if (warp != 0) mbar_try_wait(bar_at(buf), par);   // acquire of the completed phase
-    if (tid == bd - 1 && c + kQrInbox < b) mbar_expect_tx(bar_at(buf), qr_step_bytes<T>(CL, b, c + kQrInbox));
-    // scalars of the reflector (every thread, same order)
-    T sig2 = T(0);
-    for (int k = 0; k < CL; ++k) sig2 += part[buf][k][c];
-    const T alpha = rowt[buf][c];
+    // scalars of the reflector (every thread, same values)
+    const T sig2 = dsum[c];
+    const T alpha = srow[c];
     if (!isfinite(sig2) || sig2 == T(0)) {           // uniform over the cluster
       if (crank == 0 && tid == 0) {
         record_error(p.dev_status, isfinite(sig2) ? SKEL_ERR_RANK_DEFICIENT : SKEL_ERR_NONFINITE, (int)t);
@@ -276,11 +326,9 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(const QrPanelPa
       if (j == c) {
         rv = (double)beta;
       } else if (j > c) {
-        T D = T(0);
-        for (int k = 0; k < CL; ++k) D += part[buf][k][j];
-        const T wj = (D - beta * rowt[buf][j]) / den;
+        const T wj = (dsum[j] - beta * srow[j]) / den;
         wv[j] = tau * wj;
-        rv = (double)(rowt[buf][j] - tau * wj);
+        rv = (double)(srow[j] - tau * wj);
       }
       if (crank == 0) p.R[t * p.ldr + t0 + j] = rv;
     }
@@ -365,10 +413,14 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(const QrPanelPa
     if (crank == (int)((t + 1) / mloc) && tid >= b && tid < b4) rownext[tid] = T(0);
     __syncthreads();
     const int own = (int)((t + 1) / mloc);
-    const int nb = (c + 1) % kQrInbox;
-    const int g0 = (c + 1) / 4;
-    qr_send<T>(wloc, part_dst(nb), bar_at(nb), CL, g0, b4, tid, bd / 2);
-    if (crank == own) qr_send<T>(rownext, rowt_dst(nb), bar_at(nb), CL, g0, b4, tid - bd / 2 >= 0 ? tid - bd / 2 : bd, bd / 2);
+    if constexpr (GRID) {
+      publish(c + 1, crank == own);
+    } else {
+      const int nb = (c + 1) % kQrInbox;
+      const int g0 = (c + 1) / 4;
+      qr_send<T>(wloc, part_dst(nb), bar_at(nb), CL, g0, b4, tid, bd / 2);
+      if (crank == own) qr_send<T>(rownext, rowt_dst(nb), bar_at(nb), CL, g0, b4, tid - bd / 2 >= 0 ? tid - bd / 2 : bd, bd / 2);
+    }
   }
   if (stopped && tid == 0) s_stop = 1;
   __syncthreads();
@@ -394,7 +446,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_panel_kernel(const QrPanelPa
     }
   }
   __syncthreads();
-  cluster.sync();     // no CTA leaves while its peers may still address its shared memory
+  if constexpr (!GRID) cluster.sync();   // no CTA leaves while its peers may still address its shared memory
 }
 
 // V_p T_p^T (trailing update) and V_p T_p (formation of Q) for the rows t0.. of a panel, from
@@ -500,13 +552,60 @@ __global__ void __launch_bounds__(kWyRows) qr_wy_kernel(const T* V, int64_t ldv,
 }
 
 struct QrPanelPlan {
-  int CL = 0, b = 0, mloc = 0;
+  int CL = 0, b = 0, mloc = 0;   // CL: CTAs of the cluster, or of the cooperative grid when grid
   size_t smem = 0;
+  bool grid = false;
 };
 
 template <typename T>
 size_t qr_panel_smem(int b, int mloc) {
   return sizeof(T) * (size_t)b * mloc;
+}
+
+// Panels on one cooperative grid (one CTA per SM): G and the dynamic shared memory budget.
+template <typename T>
+void grid_panel_limits(int* G, size_t* budget) {
+  static int g = -1;
+  static size_t bud = 0;
+  if (g < 0) {
+    g = 0;
+    cudaFuncAttributes fa{};
+    int dev = 0, nsm = 0, per = 0;
+    if (cudaFuncGetAttributes(&fa, qr_panel_kernel<T, true>) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
+      bud = kQrSmemOptin - fa.sharedSizeBytes - 1024;
+      if (cudaFuncSetAttribute(qr_panel_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bud) ==
+              cudaSuccess &&
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, qr_panel_kernel<T, true>, kQrThreads, bud) == cudaSuccess &&
+          per > 0)
+        g = nsm;                          // one CTA per SM: the grid is co-resident
+    }
+    cudaGetLastError();
+  }
+  *G = g;
+  *budget = bud;
+}
+
+// Matrices too tall for a cluster's shared memory: the panel rows spread over the grid, m/G
+// rows per CTA, panels as wide as shared memory allows (32 columns at m = 262144).
+template <typename T>
+QrPanelPlan plan_qr_grid(int64_t m, int s) {
+  QrPanelPlan pl;
+  int G = 0;
+  size_t budget = 0;
+  grid_panel_limits<T>(&G, &budget);
+  if (G < 2 || s < 1 || m < s) return pl;
+  const int64_t mloc = ((m + G - 1) / G + 3) / 4 * 4;
+  if (mloc > kQrMaxChunks * 512) return pl;
+  int b = std::min(kQrMaxB, s);
+  while (b >= 8 && qr_panel_smem<T>(b, (int)mloc) > budget) b -= 4;
+  if (b < std::min(8, s) || qr_panel_smem<T>(b, (int)mloc) > budget) return pl;
+  pl.CL = G;
+  pl.b = b;
+  pl.mloc = (int)mloc;
+  pl.smem = qr_panel_smem<T>(b, (int)mloc);
+  pl.grid = true;
+  return pl;
 }
 
 template <typename T>
@@ -516,14 +615,14 @@ QrPanelPlan plan_qr_panels(int64_t m, int s) {
   static size_t budget = 0;
   if (max_cluster < 0) {
     cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, qr_panel_kernel<T>) != cudaSuccess) {
+    if (cudaFuncGetAttributes(&fa, qr_panel_kernel<T, false>) != cudaSuccess) {
       cudaGetLastError();
       return pl;
     }
     budget = kQrSmemOptin - fa.sharedSizeBytes - 1024;
     max_cluster = 8;
-    if (cudaFuncSetAttribute(qr_panel_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
-        cudaFuncSetAttribute(qr_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget) == cudaSuccess) {
+    if (cudaFuncSetAttribute(qr_panel_kernel<T, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+        cudaFuncSetAttribute(qr_panel_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget) == cudaSuccess) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(16);
       cfg.blockDim = dim3(kQrThreads);
@@ -536,7 +635,7 @@ QrPanelPlan plan_qr_panels(int64_t m, int s) {
       cfg.attrs = attr;
       cfg.numAttrs = 1;
       int nclusters = 0;
-      if (cudaOccupancyMaxActiveClusters(&nclusters, qr_panel_kernel<T>, &cfg) == cudaSuccess && nclusters > 0)
+      if (cudaOccupancyMaxActiveClusters(&nclusters, qr_panel_kernel<T, false>, &cfg) == cudaSuccess && nclusters > 0)
         max_cluster = 16;
     }
     cudaGetLastError();
@@ -544,10 +643,10 @@ QrPanelPlan plan_qr_panels(int64_t m, int s) {
   if (s < 1 || m < s) return pl;
   const int CL = max_cluster;
   const int64_t mloc = ((m + CL - 1) / CL + 3) / 4 * 4;
-  if (mloc > kQrMaxChunks * 512) return pl;                // keep the row loops short
+  if (mloc > kQrMaxChunks * 512) return plan_qr_grid<T>(m, s);   // keep the row loops short
   int b = std::min(kQrMaxB, s);
   while (b >= 8 && qr_panel_smem<T>(b, (int)mloc) > budget) b -= 4;
-  if (b < std::min(8, s) || qr_panel_smem<T>(b, (int)mloc) > budget) return pl;
+  if (b < std::min(8, s) || qr_panel_smem<T>(b, (int)mloc) > budget) return plan_qr_grid<T>(m, s);
   pl.CL = CL;
   pl.b = b;
   pl.mloc = (int)mloc;
@@ -566,14 +665,21 @@ size_t qr_tc_ws(int64_t m, int s) { return gemm_tc_workspace_bound(m, std::max(s
 // multiples of 4; panel starts are multiples of 8).
 bool qr_tc_ok(int64_t m, int64_t ldq) { return m % 4 == 0 && ldq % 4 == 0 && gemm_tc_usable(m, 1, 1, nullptr, m, nullptr, m); }
 
+// grid panels' exchange: barrier header, [2][G][kQrMaxB] partials, [2][kQrMaxB] row t
 template <typename T>
-size_t qr_panels_ws(int64_t m, int s) {
+size_t qr_comm_ws(int G) {
+  return comm_header_bytes(0) + align_up(sizeof(T) * 2 * (size_t)G * kQrMaxB) + align_up(sizeof(T) * 2 * kQrMaxB);
+}
+
+template <typename T>
+size_t qr_panels_ws(int64_t m, int s, const QrPanelPlan& pl) {
   const bool f64 = sizeof(T) == 8;
   size_t kws = 0;                     // split-K scratch of W = V_p^T C(t0:, t0+b:), any width
   for (int ntr = 1; ntr <= s; ++ntr) kws = std::max(kws, gemm_workspace(kQrMaxB, ntr, m, f64));
   if (!f64 && m % 4 == 0) kws = std::max(kws, qr_tc_ws(m, s));
   return 256 + 2 * align_up(sizeof(T) * (size_t)m * s) + align_up(sizeof(T) * (size_t)m * kQrMaxB) +
-         align_up(sizeof(T) * (size_t)kQrMaxB * s) + align_up(sizeof(T) * kQrMaxB * kQrMaxB) + kws;
+         align_up(sizeof(T) * (size_t)kQrMaxB * s) + align_up(sizeof(T) * kQrMaxB * kQrMaxB) +
+         (pl.grid ? qr_comm_ws<T>(pl.CL) : 0) + kws;
 }
 
 // Q = [I_s; 0] before the panels are applied (m x s, leading dimension ldq)
@@ -602,23 +708,42 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
   base += align_up(sizeof(T) * (size_t)kQrMaxB * s);
   T* Gp = reinterpret_cast<T*>(base);
   base += align_up(sizeof(T) * kQrMaxB * kQrMaxB);
+  char* comm = pl.grid ? base : nullptr;
+  if (pl.grid) base += qr_comm_ws<T>(pl.CL);
   void* kws = base;
   if (cudaMemsetAsync(fail, 0, 4, st) != cudaSuccess) return SKEL_ERR_CUDA;
   if (cudaMemset2DAsync(R, sizeof(double) * ldr, 0, sizeof(double) * s, s, st) != cudaSuccess) return SKEL_ERR_CUDA;
   if (cudaMemcpy2DAsync(Cw, sizeof(T) * m, C, sizeof(T) * ldc, sizeof(T) * m, s, cudaMemcpyDeviceToDevice, st) !=
       cudaSuccess)
     return SKEL_ERR_CUDA;
-  if (cudaFuncSetAttribute(qr_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem) != cudaSuccess)
-    return SKEL_ERR_CUDA;
-  if (pl.CL > 8 &&
-      cudaFuncSetAttribute(qr_panel_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-    return SKEL_ERR_CUDA;
+  if (pl.grid) {
+    if (cudaFuncSetAttribute(qr_panel_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem) !=
+        cudaSuccess)
+      return SKEL_ERR_CUDA;
+  } else {
+    if (cudaFuncSetAttribute(qr_panel_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem) !=
+        cudaSuccess)
+      return SKEL_ERR_CUDA;
+    if (pl.CL > 8 &&
+        cudaFuncSetAttribute(qr_panel_kernel<T, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+      return SKEL_ERR_CUDA;
+  }
   const skel_dtype dt = f64 ? SKEL_F64 : SKEL_F32;
   const bool tc = !f64 && qr_tc_ok(m, Q ? ldq : m) && (reinterpret_cast<uintptr_t>(Q) & 15) == 0 &&
                   (reinterpret_cast<uintptr_t>(V) & 15) == 0 && ldv % 4 == 0;
   QrPanelParams<T> p{};
   p.Cw = Cw; p.m = m; p.ldw = m; p.s = s; p.mloc = pl.mloc;
   p.V = V; p.ldv = ldv; p.VT = VT; p.VTN = VTN; p.R = R; p.ldr = ldr; p.fail = fail; p.dev_status = dev_status;
+  if (pl.grid) {
+    p.gc.counter = reinterpret_cast<unsigned int*>(comm);
+    p.gc.abort = reinterpret_cast<int32_t*>(comm + 4);
+    p.gc.keys = nullptr;
+    p.gc.payload = comm + comm_header_bytes(0);
+    p.gc.slot_bytes = (int64_t)sizeof(T) * kQrMaxB;
+    p.gc.G = pl.CL;
+    p.gc.wait_ns = kDefaultWaitNs;
+    p.growt = reinterpret_cast<T*>(comm + comm_header_bytes(0) + align_up(sizeof(T) * 2 * (size_t)pl.CL * kQrMaxB));
+  }
   // G = V_p^T V_p over rows t0.. for the b reflectors starting at column t0, then (qr_wy_kernel)
   // V_p T_p^T into VT and V_p T_p into VTN(:, t0 : t0+b).
   auto wy = [&](int t0, int b) -> skel_status {
@@ -695,15 +820,23 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
       cfg.dynamicSmemBytes = qr_panel_smem<T>(p.b, pl.mloc);
       cfg.stream = st;
       cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = pl.CL;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
+      if (pl.grid) {
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+      } else {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = pl.CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+      }
       cfg.attrs = attr;
       cfg.numAttrs = 1;
+      if (pl.grid && cudaMemsetAsync(comm, 0, 256, st) != cudaSuccess) return SKEL_ERR_CUDA;   // barrier counter, abort
       {
         KernelTimer kt("qr_panel", st);
-        if (cudaLaunchKernelEx(&cfg, qr_panel_kernel<T>, p) != cudaSuccess) return SKEL_ERR_CUDA;
+        const cudaError_t e = pl.grid ? cudaLaunchKernelEx(&cfg, qr_panel_kernel<T, true>, p)
+                                      : cudaLaunchKernelEx(&cfg, qr_panel_kernel<T, false>, p);
+        if (e != cudaSuccess) return SKEL_ERR_CUDA;
       }
       note_launches(1);
       const int nin = T0 + Bw - t0 - p.b;          // later columns of this super-panel
@@ -741,8 +874,12 @@ skel_status run_qr_panels_t(const QrPanelPlan& pl, const T* C, int64_t m, int64_
 }  // namespace
 
 size_t qr_panels_workspace(skel_dtype dt, int64_t m, int32_t s) {
-  if (dt == SKEL_F64) return plan_qr_panels<double>(m, s).b > 0 ? qr_panels_ws<double>(m, s) : 0;
-  return plan_qr_panels<float>(m, s).b > 0 ? qr_panels_ws<float>(m, s) : 0;
+  if (dt == SKEL_F64) {
+    const QrPanelPlan pl = plan_qr_panels<double>(m, s);
+    return pl.b > 0 ? qr_panels_ws<double>(m, s, pl) : 0;
+  }
+  const QrPanelPlan pl = plan_qr_panels<float>(m, s);
+  return pl.b > 0 ? qr_panels_ws<float>(m, s, pl) : 0;
 }
 
 skel_status run_qr_panels(skel_dtype dt, const void* C, int64_t m, int64_t ldc, int32_t s, void* V,
@@ -751,13 +888,13 @@ skel_status run_qr_panels(skel_dtype dt, const void* C, int64_t m, int64_t ldc, 
   if (dt == SKEL_F64) {
     const QrPanelPlan pl = plan_qr_panels<double>(m, s);
     if (pl.b == 0) return SKEL_ERR_UNSUPPORTED;
-    if (ws_bytes < qr_panels_ws<double>(m, s)) return SKEL_ERR_WORKSPACE;
+    if (ws_bytes < qr_panels_ws<double>(m, s, pl)) return SKEL_ERR_WORKSPACE;
     return run_qr_panels_t<double>(pl, (const double*)C, m, ldc, s, (double*)V, ldv, R, ldr, (double*)Q, ldq, ws,
                                    dev_status, st);
   }
   const QrPanelPlan pl = plan_qr_panels<float>(m, s);
   if (pl.b == 0) return SKEL_ERR_UNSUPPORTED;
-  if (ws_bytes < qr_panels_ws<float>(m, s)) return SKEL_ERR_WORKSPACE;
+  if (ws_bytes < qr_panels_ws<float>(m, s, pl)) return SKEL_ERR_WORKSPACE;
   return run_qr_panels_t<float>(pl, (const float*)C, m, ldc, s, (float*)V, ldv, R, ldr, (float*)Q, ldq, ws,
                                  dev_status, st);
 }

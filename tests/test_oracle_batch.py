@@ -116,3 +116,41 @@ def test_kernel_blocks_reach_tolerance():
         assert o["estimates"][o["rank"]] <= 1e-12
         e = np.linalg.norm(A - A[:, o["Js"]] @ o["Z"]) / np.linalg.norm(A)
         assert e < 1e-4
+
+
+def test_gaussian_kernel_block_pins():
+    """The oracle's kernel block of a point batch: equal to scipy's squared-Euclidean cdist
+    route; in 1-D the separable form exp(-x^2/h^2) exp(2xy/h^2) exp(-y^2/h^2); for x = y a
+    symmetric positive semidefinite matrix with unit diagonal (the Gaussian kernel is positive
+    definite); unchanged when both point sets are translated together."""
+    from scipy.spatial.distance import cdist
+    rng = np.random.default_rng(21)
+    x = rng.random((37, 3)).astype(np.float32)
+    y = (rng.random((23, 3)) + np.array([1.5, -0.5, 0.25])).astype(np.float32)
+    h = 0.7
+    A = skeleton.gaussian_kernel_block(x, y, h)
+    ref = np.exp(-cdist(x.astype(np.float64), y.astype(np.float64), "sqeuclidean") / (h * h))
+    assert np.allclose(A, ref, rtol=1e-12, atol=0)
+    a, b = rng.random(9), rng.random(5) + 0.5
+    A1 = skeleton.gaussian_kernel_block(a[:, None], b[:, None], h)
+    sep = np.exp(-a ** 2 / h ** 2)[:, None] * np.exp(2 * np.outer(a, b) / h ** 2) * np.exp(-b ** 2 / h ** 2)[None, :]
+    assert np.allclose(A1, sep, rtol=1e-12, atol=0)
+    K = skeleton.gaussian_kernel_block(x, x, h)
+    assert np.array_equal(K, K.T) and np.all(np.diag(K) == 1.0)
+    assert np.linalg.eigvalsh(K).min() > -1e-12
+    shift = np.array([3.0, -2.0, 0.5])
+    At = skeleton.gaussian_kernel_block(x.astype(np.float64) + shift, y.astype(np.float64) + shift, h)
+    assert np.allclose(At, A, rtol=1e-9, atol=0)
+
+
+def test_kernel_points_follow_kernel_blocks():
+    """kernel_points draws the same point sets as kernel_blocks (same seed, same order), so the
+    oracle's blocks from the FP32 points differ from the FP64-point blocks only by the points'
+    rounding (relative 1e-5 at most for exponents down to -130)."""
+    pts = workloads.kernel_points(4, seed=8)
+    blocks = workloads.kernel_blocks(4, seed=8)
+    for (x, y), B in zip(pts, blocks):
+        A = skeleton.gaussian_kernel_block(x, y, 0.5)
+        assert A.shape == B.shape and x.dtype == np.float32 and x.shape[1] == 3
+        nz = B > 1e-30
+        assert np.max(np.abs(A[nz] / B[nz] - 1)) < 1e-4

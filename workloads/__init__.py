@@ -18,6 +18,7 @@ separated_columns  A = B D with geometric column scales in random order, so that
                    pivots are separated by wide relative gaps.
 kernel_blocks      uneven Gaussian-kernel blocks exp(-|x - y|^2 / h^2) between
                    well-separated 3-D point clusters.
+kernel_points      the same blocks' point sets (FP32), for blocks given implicitly.
 """
 
 from .gen import *  # noqa: F401,F403

@@ -6,7 +6,7 @@ __all__ = [
     "sigma_config2", "sigma_config5", "config1", "dense_config2", "snn_csc",
     "kahan_type", "separated_columns", "exact_rank", "kernel_blocks",
     "torch_dense_spectrum", "torch_config5", "CONFIG5_R_EFF",
-    "torch_kernel_blocks"]
+    "torch_kernel_blocks", "kernel_points"]
 
 SEED_BASE = 2104_05877
 
@@ -128,6 +128,22 @@ def kernel_blocks(nblocks, seed, mrange=(64, 1024), nrange=(64, 512), h=0.5, sep
         y = rng.random((nb, 3)) + sep * d
         D2 = ((x[:, None, :] - y[None, :, :]) ** 2).sum(-1)
         out.append(np.asfortranarray(np.exp(-D2 / (h * h)).astype(dtype)))
+    return out
+
+
+def kernel_points(nblocks, seed, mrange=(64, 1024), nrange=(64, 512), sep=4.0):
+    """The point sets of kernel_blocks (same seeded draws, same order), rounded to FP32: a list
+    of (x (m_b x 3), y (n_b x 3)) float32 arrays, for blocks given implicitly by their points."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(nblocks):
+        mb = int(rng.integers(mrange[0], mrange[1] + 1))
+        nb = int(rng.integers(nrange[0], nrange[1] + 1))
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        x = rng.random((mb, 3))
+        y = rng.random((nb, 3)) + sep * d
+        out.append((x.astype(np.float32), y.astype(np.float32)))
     return out
 
 
