@@ -169,7 +169,8 @@ class ClockSampler:
 
 # kernels timed with CUDA events in the serialised pass
 TIMED_KERNELS = ("sketch_tc", "sketch_fp8", "fp8_quantize", "gemm_tc", "lupp_panel", "lupp_trail", "qr_panel", "qr_wy", "gemm_refine",
-                 "trsm", "gemm_qr", "gemm_cur", "gemm_eta_h", "gemm_eta_sq", "gemm_simt", "transpose", "lupp_mult")
+                 "trsm", "gemm_qr", "gemm_cur", "gemm_eta_h", "gemm_eta_sq", "gemm_simt", "transpose", "lupp_mult",
+                 "trsm_ff")
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel at this
 # workload, scaled from a smaller capture where noted in the profiles (None where no capture of
 # the current code exists)
@@ -354,12 +355,14 @@ def kernel_models(workload, m, n, k, l, prec, peaks, sustained, floors=None):
         "fp8_quantize": ("hbm", 5.0 * m * n / 1e9, hbm, "GB/s"),   # A read (4 B), A8 written (1 B)
         "gemm_tc": ("tensor", 3 * 2.0 * k * m * n / 1e12, tensor_peak("tf32", peaks, sustained), "TFLOP/s"),
         "lupp_trail": ("hbm", trail_bytes / 1e9, hbm, "GB/s"),
-        "trsm": ("alu", (1.0 * k * k * n) / 1e12, fp64, "TFLOP/s"),
+        # Z = R^{-1} W in float-float on the FP32 pipes: k^2 n / 2 multiply-add terms, each at
+        # least 12 FP32 instructions (exact product split, two-sum, carries)
+        "trsm_ff": ("alu", (0.5 * k * k * n) / 1e12, fp32_alu / 2.0 / 12.0, "T terms/s"),
     }
     if prec in ("tf32", "bf16"):
         mod["sketch_tc"] = ("tensor", 2.0 * l * m * n / 1e12, tensor_peak(prec, peaks, sustained), "TFLOP/s")
     if workload == "c2":
-        mod["trsm"] = ("alu", (1.0 * k * k * n + 4.0 * k ** 3) / 1e12, fp64, "TFLOP/s")
+        mod["trsm"] = ("alu", (4.0 * k ** 3) / 1e12, fp64, "TFLOP/s")      # U's and eta's k x k solves
     return mod
 
 

@@ -199,9 +199,11 @@ skel_status skel_pivot_lupp(skel_dtype dtype, const void* X, int64_t l, int64_t 
  * this library.)
  *   Kernel: always the persistent grid-barrier LUPP kernel (skel_pivot_lupp picks the
  *   cluster panel kernel when a panel fits a thread-block cluster).  Both kernels apply, to
- *   every entry, the textbook operations of the LUPP step in the textbook order with
- *   separately rounded divide, multiply and subtract, so Js, L and R are bitwise equal to
- *   skel_pivot_lupp's; the two differ in speed only.
+ *   every entry, the operations of the LUPP step in the textbook order with the same
+ *   arithmetic (FP64: separately rounded divide, multiply and subtract; FP32: a fused
+ *   multiply-subtract per update and a multiply by the correctly rounded reciprocal of the
+ *   pivot), so Js, L and R are bitwise equal to skel_pivot_lupp's; the two differ in speed
+ *   only.
  *   Scratch: a fixed 8 MiB array in the library's device image, held by every device that
  *   loads the library until the process exits.  A problem whose scratch need exceeds 8 MiB
  *   (e.g. FP64 with l = s = n = 996; 992 still fits) returns SKEL_ERR_WORKSPACE with nothing

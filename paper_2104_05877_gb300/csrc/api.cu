@@ -451,6 +451,7 @@ skel_status skel_id(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64
     const int64_t nba = sqnorm_num_blocks(m, n);
     double* pa = static_cast<double*>(ar.take(sizeof(double) * nba));
     void* kws = ar.take(tcw ? gemm_tc_workspace(m, n, s) : gemm_workspace(s, n, m, f64));
+    void* tws = f64 ? nullptr : ar.take(trsm_ff_workspace(s));
     if (!run) {
       skel_status st;
       if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
@@ -469,7 +470,10 @@ skel_status skel_id(int64_t m, int64_t n, skel_dtype dtype, const void* A, int64
                                 static_cast<float*>(W), n, pw, kws, dev_status, stream));
     else
       SK_CUDA(launch_gemm(g, f64, LEFT_LOAD, EPI_STORE_SQ, stream));
-    SK_CUDA(launch_trsm_upper(s, n, R, s, 0, dtype, W, n, Z, ldz, stream));
+    if (f64)
+      SK_CUDA(launch_trsm_upper(s, n, R, s, 0, dtype, W, n, Z, ldz, stream));
+    else    // the FP32 W in float-float arithmetic (FP32 pipes)
+      SK_CUDA(launch_trsm_upper_ff(s, n, R, s, static_cast<const float*>(W), n, Z, ldz, tws, stream));
     if (sq_norms) {
       SK_CUDA(launch_sqnorm(m, n, dtype, A, lda, pa, stream));
       SK_CUDA(launch_reduce_sum(pa, nba, sq_norms, 0, stream));
@@ -501,6 +505,7 @@ skel_status skel_id_refine(int64_t m, int64_t n, skel_dtype dtype, const void* A
     double* G = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));     // C^T C
     double* U = static_cast<double*>(ar.take(sizeof(double) * (size_t)s * s));     // J R^T J
     void* fws = ar.take(std::max(gemm_tn_ff_workspace(m, n, s), gemm_tn_ff_workspace(m, s, s)));
+    void* tws = ar.take(trsm_ff_workspace(s));
     if (!run) {
       skel_status st;
       if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
@@ -521,7 +526,7 @@ skel_status skel_id_refine(int64_t m, int64_t n, skel_dtype dtype, const void* A
       g.partials = pw;
       SK_CUDA(launch_gemm(g, false, LEFT_LOAD, EPI_STORE_SQ, stream));
     }
-    SK_CUDA(launch_trsm_upper(s, n, R, s, 0, dtype, W, n, Z, ldz, stream));
+    SK_CUDA(launch_trsm_upper_ff(s, n, R, s, static_cast<const float*>(W), n, Z, ldz, tws, stream));
     // one corrected-seminormal-equations step: Z1 = Z0 + R^{-1} R^{-T} (C^T A - C^T C Z0), the
     // products C^T A and C^T C exact with float-float sums, the rest FP64
     SK_CUDA(launch_gemm_tn_ff(m, n, s, static_cast<const float*>(C), m, static_cast<const float*>(A), lda, D, n, fws,
@@ -750,6 +755,7 @@ skel_status skel_id_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, i
     double* pa = static_cast<double*>(ar.take(sizeof(double) * nba));
     void* kws1 = ar.take(tcw ? gemm_tc_workspace(m, n, s) : gemm_workspace(s, n, m, f64));
     void* kws2 = ar.take(gemm_workspace(s, s, n, f64));
+    void* tws = f64 ? nullptr : ar.take(trsm_ff_workspace(s));
     if (!run) {
       skel_status st;
       if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
@@ -792,7 +798,10 @@ skel_status skel_id_cur(int64_t m, int64_t n, skel_dtype dtype, const void* A, i
     SK_CUDA(launch_trsm_upper(s, s, Rr, s, 0, SKEL_F64, T2, s, T1, s, aux->st));
     SK_CUDA(launch_transpose_f64(s, T1, s, U, ldu, aux->st));
     // caller's chain: Z = R_C^{-1} W and the norms
-    SK_CUDA(launch_trsm_upper(s, n, Rc, s, 0, dtype, W, n, Z, ldz, stream));
+    if (f64)
+      SK_CUDA(launch_trsm_upper(s, n, Rc, s, 0, dtype, W, n, Z, ldz, stream));
+    else    // the FP32 W in float-float arithmetic (FP32 pipes)
+      SK_CUDA(launch_trsm_upper_ff(s, n, Rc, s, static_cast<const float*>(W), n, Z, ldz, tws, stream));
     if (sq_id || sq_cur) SK_CUDA(launch_sqnorm(m, n, dtype, A, lda, pa, stream));
     if (sq_id) {
       SK_CUDA(launch_reduce_sum(pa, nba, sq_id, 0, stream));

@@ -334,4 +334,17 @@ __device__ __forceinline__ float dsub(float a, float b) { return __fsub_rn(a, b)
 __device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ float ddiv(float a, float b) { return __fdiv_rn(a, b); }
 
+// The LU updates x - a*b: FP64 rounds the product and the difference separately (the textbook
+// sequence, so FP64 factors equal those of a plain FP64 restatement bit for bit); FP32 uses one
+// fused multiply-add (one rounding, half the instructions).  Every FP32 LUPP kernel uses the
+// same form, so the FP32 paths agree with each other bit for bit.
+__device__ __forceinline__ double msub(double x, double a, double b) { return __dsub_rn(x, __dmul_rn(a, b)); }
+__device__ __forceinline__ float msub(float x, float a, float b) { return __fmaf_rn(-a, b, x); }
+// R's row x / p from q = rdiv_prep(p), formed once per step: FP64 divides (correctly rounded
+// quotient), FP32 multiplies by the correctly rounded reciprocal.
+__device__ __forceinline__ double rdiv_prep(double p) { return p; }
+__device__ __forceinline__ float rdiv_prep(float p) { return __frcp_rn(p); }
+__device__ __forceinline__ double rdiv(double x, double q) { return __ddiv_rn(x, q); }
+__device__ __forceinline__ float rdiv(float x, float q) { return __fmul_rn(x, q); }
+
 }  // namespace skel

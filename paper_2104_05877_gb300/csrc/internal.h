@@ -95,6 +95,12 @@ cudaError_t launch_trsm_upper(int32_t s, int64_t N, const double* R, int64_t ldr
                               skel_dtype b_dt, const void* B, int64_t ldb, double* Y, int64_t ldy,
                               cudaStream_t st);
 
+// Z = R^{-1} B for an FP32 right-hand side B (s x N row-major) in float-float arithmetic (R FP64
+// upper triangular, split into float pairs in the workspace of trsm_ff_workspace(s) bytes).
+size_t trsm_ff_workspace(int32_t s);
+cudaError_t launch_trsm_upper_ff(int32_t s, int64_t N, const double* R, int64_t ldr, const float* B, int64_t ldb,
+                                 double* Y, int64_t ldy, void* ws, cudaStream_t st);
+
 // Y = R^{-T} D in place (D s x N row-major FP64, ldd) for an s x s upper triangular FP64 R,
 // through U = J R^T J (s x s scratch) and the upper solve on the rows in reverse order.
 cudaError_t launch_trsm_upper_t(int32_t s, int64_t N, const double* R, int64_t ldr, double* U, double* D,

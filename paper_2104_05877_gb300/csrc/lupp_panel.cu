@@ -11,9 +11,10 @@
 //     M(r, q) = S^{(q)}(r, j_q), by forward substitution with the unit upper triangular
 //     R(panel, J_panel), then the b rank-1 updates S(r, :) -= M(r, q) R(q, :) applied in the
 //     same order as one-step-at-a-time elimination.
-// Every update is a separately rounded multiply then subtract in the textbook order, so the
-// factors equal those of unblocked LUPP bit for bit (FP64 runs reproduce a plain FP64
-// restatement exactly).  Kernel boundaries order the phases; the working copy of X(0:s, :)
+// Every update is msub(x, m, r) in the textbook order (common.cuh: separately rounded
+// multiply then subtract in FP64, one fused multiply-subtract in FP32), and R's rows come from
+// rdiv, so the factors equal those of unblocked LUPP in the same arithmetic bit for bit (FP64
+// runs reproduce a plain FP64 restatement exactly).  Kernel boundaries order the phases; the working copy of X(0:s, :)
 // lives in the workspace.
 #include <algorithm>
 #include <mutex>
@@ -140,7 +141,7 @@ __device__ __forceinline__ void push_candidate(uint32_t col_base, uint32_t hdr_b
       const T rq = P[(qn - 1) * ldp + jb];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if (f0 + u > qn && f0 + u < q1) v[u] = dsub(v[u], dmul(lcol[f0 + u], rq));
+        if (f0 + u > qn && f0 + u < q1) v[u] = msub(v[u], lcol[f0 + u], rq);
     }
   }
   __syncwarp();                          // every lane has read column jb before it is rewritten
@@ -171,7 +172,7 @@ __device__ __forceinline__ void push_candidate(uint32_t col_base, uint32_t hdr_b
     for (int f = q1 + 1 + lane; f < b; f += 32) {
       T x = P[f * ldp + jb];
 #pragma unroll
-      for (int kk = 0; kk < kPanelKB; ++kk) x = dsub(x, dmul(LkT[f][kk], P[(q0 + kk) * ldp + jb]));
+      for (int kk = 0; kk < kPanelKB; ++kk) x = msub(x, LkT[f][kk], P[(q0 + kk) * ldp + jb]);
       P[f * ldp + jb] = x;
     }
 }
@@ -308,6 +309,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
     }
     const T* lc = icol[buf][owner].col;          // pivot column as sent
     const T piv = w != INT_MAX ? lc[q] : T(0);
+    const T pr = rdiv_prep(piv);
     const int code = w == INT_MAX ? SKEL_ERR_INVALID_ARG
                    : !isfinite(piv) ? SKEL_ERR_NONFINITE
                    : piv == T(0) ? SKEL_ERR_RANK_DEFICIENT : 0;
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
       for (int f = q + 1 + tid; f < b; f += bd) {
         T x = lc[f];
 #pragma unroll
-        for (int kk = 0; kk < kPanelKB; ++kk) x = dsub(x, dmul(Lk[sb ^ 1][kk][f], lc[p0 + kk]));
+        for (int kk = 0; kk < kPanelKB; ++kk) x = msub(x, Lk[sb ^ 1][kk][f], lc[p0 + kk]);
         lfix[f] = x;
       }
       __syncthreads();
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
           T x = Lk[sb][kk][tid];
 #pragma unroll
           for (int k2 = 0; k2 < kk; ++k2)
-            x = dsub(x, dmul(xs[k2], kk == kPanelKB - 1 ? lc[q0 + k2] : Rsub[kk][k2]));
+            x = msub(x, xs[k2], kk == kPanelKB - 1 ? lc[q0 + k2] : Rsub[kk][k2]);
           xs[kk] = x;
         }
 #pragma unroll
@@ -376,16 +378,16 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
       } else if (sl[jj]) {
         rv = T(0);
       } else {
-        rv = ddiv(*pq, piv);
+        rv = rdiv(*pq, pr);
         if (more) {
           T x = pq[ldp];
           if (!blk_end) {
-            x = dsub(x, dmul(lnext, rv));
+            x = msub(x, lnext, rv);
           } else {                         // all steps of the sub-block for row q1
             const T* Lq1 = LkT[sb][q1];
 #pragma unroll
-            for (int kk = 0; kk < kPanelKB - 1; ++kk) x = dsub(x, dmul(Lq1[kk], P[(q0 + kk) * ldp + jj]));
-            x = dsub(x, dmul(Lq1[kPanelKB - 1], rv));
+            for (int kk = 0; kk < kPanelKB - 1; ++kk) x = msub(x, Lq1[kk], P[(q0 + kk) * ldp + jj]);
+            x = msub(x, Lq1[kPanelKB - 1], rv);
           }
           pq[ldp] = x;
           const T kx = pivot_key(x);
@@ -411,7 +413,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
         const T rv = P[q * ldp + jj];
         for (int r = q + 2; r < q1; ++r) {
           T* x = &P[r * ldp + jj];
-          *x = dsub(*x, dmul(lcol[r], rv));
+          *x = msub(*x, lcol[r], rv);
         }
       }
     } else if (blk_end) {                  // rows q1+1 .. b-1: steps q0 .. q (a full sub-block)
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
           T* x = &P[r * ldp + jj];
           T xv = *x;
 #pragma unroll
-          for (int kk = 0; kk < kPanelKB; ++kk) xv = dsub(xv, dmul(LkT[sb][r][kk], rk[kk]));
+          for (int kk = 0; kk < kPanelKB; ++kk) xv = msub(xv, LkT[sb][r][kk], rk[kk]);
           *x = xv;
         }
       }
@@ -470,8 +472,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lupp_panel_kernel(const Pane
       T a1 = q1 < b ? p.Xg[r * p.n + s_J[q1]] : T(0);
       for (int qq = 0; qq < b; ++qq) {
         const T mq = __shfl_sync(0xffffffffu, qq < 32 ? a0 : a1, qq & 31);   // final M(r, qq)
-        if (q0 > qq && q0 < b) a0 = dsub(a0, dmul(mq, RJ[qq * b + q0]));
-        if (q1 > qq && q1 < b) a1 = dsub(a1, dmul(mq, RJ[qq * b + q1]));
+        if (q0 > qq && q0 < b) a0 = msub(a0, mq, RJ[qq * b + q0]);
+        if (q1 > qq && q1 < b) a1 = msub(a1, mq, RJ[qq * b + q1]);
       }
       T* Mr = p.M + (int64_t)ri * p.ldm;
       if (q0 < b) Mr[q0] = a0;
@@ -523,7 +525,7 @@ __global__ void __launch_bounds__(kTrailThreads) lupp_trail_kernel(const PanelPa
     for (int e = 0; e < 8; ++e)
       if (q0 + e < b)
 #pragma unroll
-        for (int u = 0; u < kTrailRows; ++u) v[u] = dsub(v[u], dmul(Mt[q0 + e][u], rq[e]));
+        for (int u = 0; u < kTrailRows; ++u) v[u] = msub(v[u], Mt[q0 + e][u], rq[e]);
   }
 #pragma unroll
   for (int u = 0; u < kTrailRows; ++u)
@@ -535,8 +537,8 @@ __global__ void __launch_bounds__(kTrailThreads) lupp_trail_kernel(const PanelPa
 // shared memory, and each thread keeps an 8 x 4 block of Xg in registers: per step q two
 // 16-byte loads of multipliers (a warp broadcast) and one of R feed 32 multiply-subtract pairs
 // (about two instructions per entry and step, against three).  Every entry still sees
-// x = x - M(r, q) R(t0 + q, j) for q = 0 .. b-1 in order with separately rounded multiply and
-// subtract, so the results equal the column kernel's bit for bit.  Columns selected by this or
+// x = msub(x, M(r, q), R(t0 + q, j)) for q = 0 .. b-1 in order, so the results equal the
+// column kernel's bit for bit.  Columns selected by this or
 // an earlier panel are updated too: from this panel on their R entries are 0 (earlier pivots)
 // or belong to this panel's pivot columns, and those trailing entries are never read again.
 constexpr int TT_R = 64, TT_C = 128, TT_THREADS = 256;
@@ -613,7 +615,7 @@ __global__ void __launch_bounds__(TT_THREADS) lupp_trail_tile_kernel(const Panel
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) v[i][u] = dsub(v[i][u], dmul(m[i], rv[u]));
+      for (int u = 0; u < 4; ++u) v[i][u] = msub(v[i][u], m[i], rv[u]);
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -717,8 +719,8 @@ __global__ void lupp_defer_m_kernel(const PanelParams<T> p, int B, T* Lw, int64_
 #pragma unroll
       for (int u = 0; u < 8; ++u)
         if (t + u < tq) {
-          a0 = dsub(a0, dmul(mt[u], r0[u]));
-          a1 = dsub(a1, dmul(mt[u], r1[u]));
+          a0 = msub(a0, mt[u], r0[u]);
+          a1 = msub(a1, mt[u], r1[u]);
         }
     }
     for (int c0 = 0; c0 < B; c0 += 8) {    // forward substitution with R(panel q, J_q)
@@ -735,8 +737,8 @@ __global__ void lupp_defer_m_kernel(const PanelParams<T> p, int B, T* Lw, int64_
         const int qq = c0 + u;
         if (qq < B) {                       // uniform over the warp
           const T mq = __shfl_sync(0xffffffffu, qq < 32 ? a0 : a1, qq & 31);
-          if (q0 > qq && h0) a0 = dsub(a0, dmul(mq, r0[u]));
-          if (q1 > qq && h1) a1 = dsub(a1, dmul(mq, r1[u]));
+          if (q0 > qq && h0) a0 = msub(a0, mq, r0[u]);
+          if (q1 > qq && h1) a1 = msub(a1, mq, r1[u]);
         }
       }
     }
@@ -783,7 +785,7 @@ __global__ void __launch_bounds__(kTrailThreads) lupp_defer_trail_kernel(const P
       for (int e = 0; e < 8; ++e)
         if (q0 + e < B)
 #pragma unroll
-          for (int u = 0; u < kTrailRows; ++u) v[u] = dsub(v[u], dmul(Mt[q0 + e][u], rq[e]));
+          for (int u = 0; u < kTrailRows; ++u) v[u] = msub(v[u], Mt[q0 + e][u], rq[e]);
     }
   }
   if (live)
@@ -928,6 +930,7 @@ __global__ void __launch_bounds__(256) lupp_gpanel_kernel(const GPanelParams p, 
     const T piv = __ldcg(reinterpret_cast<const T*>(wsl + 8));
     if (!isfinite(piv)) { stop(t, SKEL_ERR_NONFINITE); return; }
     if (piv == T(0)) { stop(t, SKEL_ERR_RANK_DEFICIENT); return; }
+    const T pr = rdiv_prep(piv);
     const T* wcol = reinterpret_cast<const T*>(wsl + 16);
     for (int r = q + tid; r < b; r += bd) pivcol[r] = __ldcg(wcol + r);
     if (blockIdx.x == 0 && tid == 0) p.Js[t] = (int32_t)w;
@@ -936,7 +939,7 @@ __global__ void __launch_bounds__(256) lupp_gpanel_kernel(const GPanelParams p, 
       T rv;
       if (jj == jw) rv = T(1);
       else if (sl[jj]) rv = T(0);
-      else rv = ddiv(W[(int64_t)q * nloc + jj], piv);
+      else rv = rdiv(W[(int64_t)q * nloc + jj], pr);
       rowt[jj] = rv;
       R[(int64_t)t * ldr + c0 + jj] = rv;
     }
@@ -950,7 +953,7 @@ __global__ void __launch_bounds__(256) lupp_gpanel_kernel(const GPanelParams p, 
     for (int jj = tid; jj < nl; jj += bd) {
       if (sl[jj]) continue;
       T* x = &W[(int64_t)r1 * nloc + jj];
-      *x = dsub(*x, dmul(pivcol[r1], rowt[jj]));
+      *x = msub(*x, pivcol[r1], rowt[jj]);
     }
     __syncthreads();
     const KeyIdx<T> c = gp_best<T>(W, nloc, r1, nl, c0, sl);
@@ -959,7 +962,7 @@ __global__ void __launch_bounds__(256) lupp_gpanel_kernel(const GPanelParams p, 
       jb = (int)(c.idx - c0);
       for (int r = q + 2 + tid; r < b; r += bd) {
         T* x = &W[(int64_t)r * nloc + jb];
-        *x = dsub(*x, dmul(pivcol[r], rowt[jb]));
+        *x = msub(*x, pivcol[r], rowt[jb]);
       }
       __syncthreads();
     }
@@ -970,7 +973,7 @@ __global__ void __launch_bounds__(256) lupp_gpanel_kernel(const GPanelParams p, 
       const T rv = rowt[jj];
       for (int r = q + 2; r < b; ++r) {
         T* x = &W[(int64_t)r * nloc + jj];
-        *x = dsub(*x, dmul(pivcol[r], rv));
+        *x = msub(*x, pivcol[r], rv);
       }
     }
     __syncthreads();
@@ -1007,8 +1010,8 @@ __global__ void __launch_bounds__(256) lupp_gmult_kernel(const T* Xg, int64_t n,
         M[(r - r0) * ldm + qq] = m;
         if (L) L[r * ldl + t0 + qq] = m;
       }
-      if (qa > qq && qa < b) xa = dsub(xa, dmul(m, RJ[qq][qa]));
-      if (qb > qq && qb < b) xb = dsub(xb, dmul(m, RJ[qq][qb]));
+      if (qa > qq && qa < b) xa = msub(xa, m, RJ[qq][qa]);
+      if (qb > qq && qb < b) xb = msub(xb, m, RJ[qq][qb]);
     }
   }
 }

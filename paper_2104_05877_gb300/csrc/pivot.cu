@@ -14,9 +14,10 @@
 // published copy stays valid.  LUPP looks one step ahead: after the pivot of step t arrives,
 // a CTA first updates row t+1 (and its own next candidate column), publishes its candidate
 // for step t+1, and only then applies the rest of the Schur update while the barrier
-// completes.  The LUPP update uses separately rounded multiply and subtract (no FMA
-// contraction), the operation order of the textbook algorithm, so FP64 runs reproduce a
-// plain FP64 restatement bit for bit.
+// completes.  The LUPP updates follow the textbook order with msub / rdiv (common.cuh): in
+// FP64 separately rounded multiply and subtract and a correctly rounded division, so FP64
+// runs reproduce a plain FP64 restatement bit for bit; in FP32 a fused multiply-subtract and
+// a multiply by the pivot's reciprocal, as in every other FP32 LUPP kernel.
 #include <algorithm>
 
 #include "common.cuh"
@@ -163,6 +164,7 @@ __global__ void __launch_bounds__(kThreads) lupp_kernel(const PivParams<T> p) {
     const T piv = __ldcg(reinterpret_cast<const T*>(wsl + 8));
     if (!isfinite(piv)) { fail_tail(p, t, SKEL_ERR_NONFINITE); return; }
     if (piv == T(0)) { fail_tail(p, t, SKEL_ERR_RANK_DEFICIENT); return; }
+    const T pr = rdiv_prep(piv);
     const T* wcol = reinterpret_cast<const T*>(wsl + kHeader);
     for (int r = t + tid; r < s; r += bd) pivcol[r] = __ldcg(wcol + r);
     if (b == 0 && tid == 0) p.Js[t] = (int32_t)w;
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(kThreads) lupp_kernel(const PivParams<T> p) {
       T rv;
       if (jj == jw) rv = T(1);
       else if (sel[jj]) rv = T(0);
-      else rv = ddiv(W[(int64_t)t * nloc + jj], piv);
+      else rv = rdiv(W[(int64_t)t * nloc + jj], pr);
       rowt[jj] = rv;
       if (p.R) p.R[(int64_t)t * p.ldr + c0 + jj] = rv;
     }
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(kThreads) lupp_kernel(const PivParams<T> p) {
     for (int jj = tid; jj < nl; jj += bd) {
       if (sel[jj]) continue;
       T* x = &W[(int64_t)r1 * nloc + jj];
-      *x = dsub(*x, dmul(pivcol[r1], rowt[jj]));
+      *x = msub(*x, pivcol[r1], rowt[jj]);
     }
     __syncthreads();
     const KeyIdx<T> c = local_best<T>(W, nloc, r1, nl, c0, sel);
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(kThreads) lupp_kernel(const PivParams<T> p) {
       jb = (int)(c.idx - c0);
       for (int r = t + 2 + tid; r < s; r += bd) {
         T* x = &W[(int64_t)r * nloc + jb];
-        *x = dsub(*x, dmul(pivcol[r], rowt[jb]));
+        *x = msub(*x, pivcol[r], rowt[jb]);
       }
       __syncthreads();
       publish<T>(p.gc, r1, c.idx, W[(int64_t)r1 * nloc + jb], c.key, W, nloc, jb, r1, s);
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(kThreads) lupp_kernel(const PivParams<T> p) {
       const T rv = rowt[jj];
       for (int r = t + 2; r < s; ++r) {
         T* x = &W[(int64_t)r * nloc + jj];
-        *x = dsub(*x, dmul(pivcol[r], rv));
+        *x = msub(*x, pivcol[r], rv);
       }
     }
     __syncthreads();

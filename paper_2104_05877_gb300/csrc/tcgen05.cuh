@@ -74,6 +74,12 @@ __device__ __forceinline__ void bulk_copy_to_peer(uint32_t local_dst_src, uint32
                ::"r"(cluster_addr(local_dst_src, rank)), "r"(local_dst_src), "r"(bytes),
                  "r"(cluster_addr(local_bar, rank)) : "memory");
 }
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from global memory to
+// this CTA's shared memory, completing the bytes on the mbarrier `bar`.
+__device__ __forceinline__ void bulk_load_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
 // MMA completion arrives on the mbarrier at the offset of `bar` in every CTA of `mask`.
 __device__ __forceinline__ void mma_commit_multicast(uint32_t bar, uint16_t mask) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"

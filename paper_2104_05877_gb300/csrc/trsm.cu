@@ -54,6 +54,164 @@ __global__ void __launch_bounds__(256) trsm_upper_kernel(int s, int64_t N, int n
   }
 }
 
+// The same back substitution for an FP32 right-hand side (the mixed-precision ID's W) in
+// float-float arithmetic on the FP32 pipes, whose rate on this GPU is ~70x the FP64 rate:
+// every value is an unevaluated sum hi + lo of two floats (~44 significant bits), R is given
+// as such pairs (Rh, Rl, from the FP64 R), products are split exactly by FMA and sums kept by
+// two-sum.  The result is far more accurate than the
+// FP32 W it starts from.
+__device__ __forceinline__ void ff_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (ah + al) += (bh + bl) * (ch + cl), the lo * lo term dropped
+__device__ __forceinline__ void ff_fma(float& ah, float& al, float bh, float bl, float ch, float cl) {
+  const float p = __fmul_rn(bh, ch);
+  float e = fmaf(bh, ch, -p);
+  e = fmaf(bh, cl, e);
+  e = fmaf(bl, ch, e);
+  float sh, se;
+  ff_two_sum(ah, p, sh, se);
+  ah = sh;
+  al = __fadd_rn(al, __fadd_rn(se, e));
+}
+__device__ __forceinline__ void ff_norm(float& h, float& l) {
+  const float s = __fadd_rn(h, l);
+  l = __fsub_rn(l, __fsub_rn(s, h));
+  h = s;
+}
+
+// Rows are solved in blocks of RB = 32 from the bottom: the off-diagonal update from the rows
+// already solved (dot products over q >= hi, four independent float-float accumulators per
+// thread), then the block's rows times the FP64 inverse of the 32 x 32 diagonal block (given
+// as float pairs Dh, Dl: a product, parallel over rows and columns, instead of a sequential
+// substitution).
+__global__ void __launch_bounds__(256) trsm_upper_ff_kernel(int s, int64_t N, int nb, const float* Rh,
+                                                            const float* Rl, const float* Dh, const float* Dl,
+                                                            const float* B, int64_t ldb, double* Y, int64_t ldy) {
+  extern __shared__ float Yff[];      // Yh [s][nb], then Yl [s][nb]
+  float* Yh = Yff;
+  float* Yl = Yff + (size_t)s * nb;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int64_t c0 = (int64_t)blockIdx.x * nb;
+  const int nc = (int)std::min<int64_t>(nb, N - c0);
+  for (int64_t e = tid; e < (int64_t)s * nb; e += bd) {
+    const int r = (int)(e / nb), cc = (int)(e % nb);
+    Yh[e] = cc < nc ? B[(int64_t)r * ldb + c0 + cc] : 0.f;
+    Yl[e] = 0.f;
+  }
+  __syncthreads();
+  for (int kb = (s + RB - 1) / RB - 1; kb >= 0; --kb) {   // row blocks [32 kb, 32 kb + 32), last first
+    const int lo = kb * RB, hi = std::min(s, lo + RB);
+    // y(r) -= sum_{q >= hi} R(r, q) y(q), r in [lo, hi)
+    if (hi < s)
+      for (int e = tid; e < (hi - lo) * nb; e += bd) {
+        const int r = lo + e / nb, cc = e % nb;
+        const float* rh = Rh + (int64_t)r * s;
+        const float* rl = Rl + (int64_t)r * s;
+        float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
+        int q = hi;
+        for (; q + 3 < s; q += 4) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            ff_fma(ah[u], al[u], __ldg(rh + q + u), __ldg(rl + q + u), Yh[(q + u) * nb + cc], Yl[(q + u) * nb + cc]);
+        }
+        for (; q < s; ++q) ff_fma(ah[0], al[0], __ldg(rh + q), __ldg(rl + q), Yh[q * nb + cc], Yl[q * nb + cc]);
+        float h, l, t;
+        ff_two_sum(ah[0], ah[1], h, t);
+        l = __fadd_rn(__fadd_rn(al[0], al[1]), t);
+        float h2, l2;
+        ff_two_sum(ah[2], ah[3], h2, t);
+        l2 = __fadd_rn(__fadd_rn(al[2], al[3]), t);
+        float hs, ts;
+        ff_two_sum(h, h2, hs, ts);
+        const float ls = __fadd_rn(__fadd_rn(l, l2), ts);
+        // Y(r) -= (hs + ls)
+        const int idx = r * nb + cc;
+        float sh, se;
+        ff_two_sum(Yh[idx], -hs, sh, se);
+        float lo2 = __fadd_rn(__fsub_rn(Yl[idx], ls), se);
+        ff_norm(sh, lo2);
+        Yh[idx] = sh;
+        Yl[idx] = lo2;
+      }
+    __syncthreads();
+    // y(lo:hi) = D_kb^{-1} y(lo:hi): D^{-1} upper triangular, rows of the block over threads
+    const float* dh = Dh + (size_t)kb * RB * RB;
+    const float* dl = Dl + (size_t)kb * RB * RB;
+    const int nr = hi - lo;
+    float zh[2], zl[2];
+    for (int k = 0; k < 2; ++k) {
+      const int e = tid + k * bd;
+      zh[k] = 0.f;
+      zl[k] = 0.f;
+      if (e < nr * nb) {
+        const int i = e / nb, cc = e % nb;
+        for (int q = i; q < nr; ++q)
+          ff_fma(zh[k], zl[k], dh[i * RB + q], dl[i * RB + q], Yh[(lo + q) * nb + cc], Yl[(lo + q) * nb + cc]);
+        ff_norm(zh[k], zl[k]);
+      }
+    }
+    __syncthreads();
+    for (int k = 0; k < 2; ++k) {
+      const int e = tid + k * bd;
+      if (e < nr * nb) {
+        Yh[lo * nb + e] = zh[k];
+        Yl[lo * nb + e] = zl[k];
+      }
+    }
+    __syncthreads();
+  }
+  for (int64_t e = tid; e < (int64_t)s * nb; e += bd) {
+    const int r = (int)(e / nb), cc = (int)(e % nb);
+    if (cc < nc) Y[(int64_t)r * ldy + c0 + cc] = (double)Yh[e] + (double)Yl[e];
+  }
+}
+
+// R (FP64, upper triangular) as float pairs, and the FP64 inverses of its RB x RB diagonal
+// blocks as float pairs (block k at D + k RB^2, row-major; rows past s: the identity).
+__global__ void ff_split_kernel(int s, const double* R, int64_t ldr, float* Rh, float* Rl) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)s * s;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / s), q = (int)(e % s);
+    const double v = q >= r ? R[(int64_t)r * ldr + q] : 0.0;
+    const float h = (float)v;
+    Rh[e] = h;
+    Rl[e] = (float)(v - (double)h);
+  }
+}
+
+// One warp per diagonal block: lane j solves D x = e_j by back substitution in FP64.
+__global__ void ff_diag_inverse_kernel(int s, const double* R, int64_t ldr, float* Dh, float* Dl) {
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int nbk = (s + RB - 1) / RB;
+  if (k >= nbk) return;
+  const int b0 = RB * k;
+  double x[RB];
+#pragma unroll
+  for (int i = RB - 1; i >= 0; --i) {
+    double v;
+    if (b0 + i >= s) {
+      v = i == lane ? 1.0 : 0.0;
+    } else {
+      double acc = i == lane ? 1.0 : 0.0;
+#pragma unroll
+      for (int q = i + 1; q < RB; ++q)
+        if (b0 + q < s) acc -= R[(int64_t)(b0 + i) * ldr + b0 + q] * x[q];
+      v = acc / R[(int64_t)(b0 + i) * ldr + b0 + i];
+    }
+    x[i] = v;
+  }
+#pragma unroll
+  for (int i = 0; i < RB; ++i) {
+    const float h = (float)x[i];
+    Dh[(size_t)k * RB * RB + i * RB + lane] = h;
+    Dl[(size_t)k * RB * RB + i * RB + lane] = (float)(x[i] - (double)h);
+  }
+}
+
 // Few right-hand sides (N small against the GPU): a CTA solves nbs = 4 columns.  The 32 x 32
 // diagonal blocks of R are inverted first (warp k inverts block k by back substitution on the
 // identity), so that the back substitution over the s/32 row blocks is, per block, one
@@ -301,6 +459,43 @@ cudaError_t launch_trsm_upper(int32_t s, int64_t N, const double* R, int64_t ldr
     e = cudaFuncSetAttribute(trsm_upper_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     trsm_upper_kernel<float><<<grid, 256, smem, st>>>(s, N, nb, R, ldr, unit_diag, (const float*)B, ldb, Y, ldy);
+  }
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+size_t trsm_ff_workspace(int32_t s) {
+  const size_t nbk = (size_t)(s + RB - 1) / RB;
+  return 2 * align_up(sizeof(float) * (size_t)s * s) + 2 * align_up(sizeof(float) * nbk * RB * RB);
+}
+
+cudaError_t launch_trsm_upper_ff(int32_t s, int64_t N, const double* R, int64_t ldr, const float* B, int64_t ldb,
+                                 double* Y, int64_t ldy, void* ws, cudaStream_t st) {
+  if (N <= 0 || s <= 0) return cudaSuccess;
+  char* base = static_cast<char*>(ws);
+  float* Rh = reinterpret_cast<float*>(base);
+  base += align_up(sizeof(float) * (size_t)s * s);
+  float* Rl = reinterpret_cast<float*>(base);
+  base += align_up(sizeof(float) * (size_t)s * s);
+  const size_t nbk = (size_t)(s + RB - 1) / RB;
+  float* Dh = reinterpret_cast<float*>(base);
+  base += align_up(sizeof(float) * nbk * RB * RB);
+  float* Dl = reinterpret_cast<float*>(base);
+  ff_split_kernel<<<(unsigned)std::min<int64_t>(((int64_t)s * s + 255) / 256, 4096), 256, 0, st>>>(s, R, ldr, Rh, Rl);
+  ff_diag_inverse_kernel<<<(unsigned)((nbk + 3) / 4), 128, 0, st>>>(s, R, ldr, Dh, Dl);
+  note_launches(2);
+  const int sms = device_sm_count();
+  // eight columns per CTA (~64 KB of shared memory at s = 1024: three CTAs per SM) unless
+  // that leaves too few CTAs
+  int nb = 8;
+  while (nb > 2 && (N + nb - 1) / nb < 2 * sms) nb >>= 1;
+  while ((size_t)s * nb * 2 * sizeof(float) > 160 * 1024 && nb > 1) nb >>= 1;
+  const size_t smem = (size_t)s * nb * 2 * sizeof(float);
+  const cudaError_t e = cudaFuncSetAttribute(trsm_upper_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  {
+    KernelTimer kt("trsm_ff", st);
+    trsm_upper_ff_kernel<<<(unsigned)((N + nb - 1) / nb), 256, smem, st>>>(s, N, nb, Rh, Rl, Dh, Dl, B, ldb, Y, ldy);
   }
   note_launches(1);
   return cudaGetLastError();
