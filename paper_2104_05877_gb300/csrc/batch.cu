@@ -110,6 +110,7 @@ constexpr int BS_CONV_WARP0 = 4;
 constexpr int BS_BK = 32;
 constexpr uint32_t BS_ATILE = 128 * 128;          // 128 columns x 32 rows of A, FP32
 constexpr uint32_t BS_CORR_COL = 256;             // TMEM column of the correction accumulator
+constexpr uint32_t BS_XREC = 32 * 32;              // point plans: the 32 x records of a step
 constexpr uint64_t BS_WAIT_NS = 2000000000ull;
 
 struct BatchSketchParams {
@@ -198,7 +199,8 @@ batch_sketch_kernel(const __grid_constant__ CUtensorMap tmGhi, const __grid_cons
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int AS = p.stages;
   const uint32_t g_bytes = (uint32_t)p.lp * 128;
-  const uint32_t stage_bytes = 2 * BS_ATILE + 2 * g_bytes;   // [Ahi][Alo][Ghi][Glo]
+  // [Ahi][Alo][Ghi][Glo] (+ [x records of the step] for point plans; 1 KB keeps 1024-byte alignment)
+  const uint32_t stage_bytes = 2 * BS_ATILE + 2 * g_bytes + (PTS ? BS_XREC : 0u);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + AS * stage_bytes);   // full, conv, empty [AS]; done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * AS + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
@@ -213,6 +215,7 @@ batch_sketch_kernel(const __grid_constant__ CUtensorMap tmGhi, const __grid_cons
   auto alo_buf = [&](int s) { return smem + s * stage_bytes + BS_ATILE; };
   auto ghi_buf = [&](int s) { return smem + s * stage_bytes + 2 * BS_ATILE; };
   auto glo_buf = [&](int s) { return smem + s * stage_bytes + 2 * BS_ATILE + g_bytes; };
+  auto xr_buf = [&](int s) { return smem + s * stage_bytes + 2 * BS_ATILE + 2 * g_bytes; };
   auto full = [&](int s) { return smem_u32(&bars[s]); };
   auto conv = [&](int s) { return smem_u32(&bars[AS + s]); };
   auto empty = [&](int s) { return smem_u32(&bars[2 * AS + s]); };
@@ -250,9 +253,12 @@ batch_sketch_kernel(const __grid_constant__ CUtensorMap tmGhi, const __grid_cons
         const uint32_t ph = (uint32_t)(it / AS) & 1u;
         if (aborted()) break;
         if (it >= AS && !mbar_wait(empty(s), ph ^ 1u, BS_WAIT_NS)) { fail(); break; }
-        mbar_expect_tx(full(s), (PTS ? 0u : BS_ATILE) + 2 * g_bytes);
+        mbar_expect_tx(full(s), (PTS ? BS_XREC : BS_ATILE) + 2 * g_bytes);
         const int x = it * BS_BK;
-        if constexpr (!PTS) tma_load_2d(smem_u32(a_buf(s)), tmA, x, item.tile * 128, full(s));
+        if constexpr (PTS)
+          bulk_load_g2s(smem_u32(xr_buf(s)), blk.A + (int64_t)x * kRec, BS_XREC, full(s));   // the step's x records
+        else
+          tma_load_2d(smem_u32(a_buf(s)), tmA, x, item.tile * 128, full(s));
         tma_load_2d(smem_u32(ghi_buf(s)), &tmGhi, x, 0, full(s));
         tma_load_2d(smem_u32(glo_buf(s)), &tmGlo, x, 0, full(s));
         ++issued;
@@ -306,8 +312,10 @@ batch_sketch_kernel(const __grid_constant__ CUtensorMap tmGhi, const __grid_cons
         const uint32_t ph = (uint32_t)(it / AS) & 1u;
         if (aborted()) break;
         if (it >= AS && !mbar_wait(empty(s), ph ^ 1u, BS_WAIT_NS)) { fail(); break; }
+        if (!mbar_wait(full(s), ph, BS_WAIT_NS)) { fail(); break; }     // the step's x records
         float4* ahi = reinterpret_cast<float4*>(a_buf(s));
         float4* alo = reinterpret_cast<float4*>(alo_buf(s));
+        const float4* xs = reinterpret_cast<const float4*>(xr_buf(s));
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
           const int c = 4 * hh + cc;
@@ -317,9 +325,8 @@ batch_sketch_kernel(const __grid_constant__ CUtensorMap tmGhi, const __grid_cons
             const int i = it * BS_BK + 4 * c + u;
             v[u] = 0.f;
             if (colv && i < blk.m) {
-              const float4* xr = reinterpret_cast<const float4*>(blk.A + (int64_t)i * kRec);
-              const float4 xc = __ldg(xr);
-              const float4 t = __ldg(xr + 1);
+              const float4 xc = xs[2 * (4 * c + u)];
+              const float4 t = xs[2 * (4 * c + u) + 1];
               v[u] = kernel_entry(xc, make_float2(t.x, t.y), yc, cy, p.w_hi, p.w_lo);
             }
           }
@@ -645,8 +652,11 @@ size_t lupp_smem(int l, int kmax, int ncl) {
 // ---------------------------------------------------------------------------------------
 // Z_b = X_b(:, J)^+ X_b (l x n_b sketch, r = rank_b pivots): FP32 Householder QR of the l x r
 // X_b(:, J) in shared memory (column-major, odd leading dimension), then for each chunk of
-// LS_NC columns of X_b: Q^T applied (LS_TPC threads per column, rows split by residue), and the
-// back substitution with R by one thread per column.  Z(:, J) = I is written exactly.
+// LS_NC columns of X_b: Q^T applied four reflectors at a time in compact WY form,
+// (H_t .. H_t+3)^T x = x - V_4 T_4^T V_4^T x with T_4 (4 x 4) formed once per group
+// (LS_TPC threads per column, rows split by residue: one pass for the four dot products, one
+// for the update), then the back substitution with R, column-oriented over the same eight
+// lanes.  Z(:, J) = I is written exactly.
 constexpr int LS_THREADS = 256;
 constexpr int LS_NC = 32;                          // columns per chunk
 constexpr int LS_TPC = LS_THREADS / LS_NC;         // threads per column (a power of two <= 32)
@@ -668,6 +678,8 @@ size_t lsq_smem(int l, int kmax) { return sizeof(float) * (size_t)ls_ld(l) * (km
 __global__ void __launch_bounds__(LS_THREADS) batch_lsq_kernel(const BatchLsqParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float tau[BL_MAXK];
+  __shared__ float rdiag[BL_MAXK];                      // R(t, t); V(t, t) holds the reflector's 1
+  __shared__ float T4[BL_MAXK / 4][16];                 // per group of four: T_4 (row-major)
   __shared__ float red[LS_THREADS / 32];
   __shared__ float s_nrm2;
   const int b = blockIdx.x;
@@ -749,6 +761,7 @@ __global__ void __launch_bounds__(LS_THREADS) batch_lsq_kernel(const BatchLsqPar
     if (tid == 0) {
       tau[t] = refl ? (beta - alpha) / beta : 0.f;
       v[t] = beta;
+      rdiag[t] = beta;
     }
     __syncthreads();
     const float tt = tau[t];
@@ -764,8 +777,49 @@ __global__ void __launch_bounds__(LS_THREADS) batch_lsq_kernel(const BatchLsqPar
     }
     __syncthreads();
   }
+  // the reflectors' unit diagonal in V (R's diagonal is in rdiag), then T_4 per group of four:
+  // T(j, j) = tau_j, T(0:j, j) = -tau_j T(0:j, 0:j) G(0:j, j), G(i, j) = v_i^T v_j
+  for (int t = tid; t < r; t += LS_THREADS) V[t * ldv + t] = 1.f;
+  __syncthreads();
+  const int ng = (r + 3) / 4;
+  for (int g = warp; g < ng; g += LS_THREADS / 32) {
+    const int t0 = 4 * g, nw4 = min(4, r - t0);
+    float G[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float d = 0.f;
+        if (a < c && c < nw4) {        // v_a(i) = 0 for i < t0 + a; v_c(i) = 0 for i < t0 + c
+          const float* va = V + (t0 + a) * ldv;
+          const float* vc = V + (t0 + c) * ldv;
+          for (int i = t0 + c + lane; i < l; i += 32) d = fmaf(va[i], vc[i], d);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        }
+        G[a][c] = d;
+      }
+    if (lane == 0) {
+      float Tm[4][4] = {};
+      for (int j = 0; j < nw4; ++j) {
+        const float tj = tau[t0 + j];
+        Tm[j][j] = tj;
+        for (int i = 0; i < j; ++i) {
+          float a = 0.f;
+          for (int k = i; k < j; ++k) a = fmaf(Tm[i][k], G[k][j], a);
+          Tm[i][j] = -tj * a;
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) T4[g][a * 4 + c] = Tm[a][c];
+    }
+  }
+  __syncthreads();
   bool bad = false;
   const int jj = tid / LS_TPC, h = tid % LS_TPC;
+  const unsigned gmask = 0xffu << (lane & ~(LS_TPC - 1));     // the eight lanes of this column
   for (int c0 = 0; c0 < n; c0 += LS_NC) {
     const int ncw = min(LS_NC, n - c0);
     for (int e0 = tid; e0 < l * ncw; e0 += 8 * LS_THREADS) {   // eight loads in flight per thread
@@ -784,25 +838,53 @@ __global__ void __launch_bounds__(LS_THREADS) batch_lsq_kernel(const BatchLsqPar
     __syncthreads();
     const bool act = jj < ncw;
     float* x = Cc + jj * ldv;
-    for (int t = 0; t < r; ++t) {                         // x <- H_t x, t = 0 .. r-1 (Q^T x)
-      const float* v = V + t * ldv;
-      const int i0 = t + ((h - t % LS_TPC) + LS_TPC) % LS_TPC;
-      float d = 0.f;
+    for (int g = 0; g < ng; ++g) {                        // x <- (H_t0 .. H_t0+3)^T x
+      const int t0 = 4 * g;
+      const float* v0 = V + t0 * ldv;
+      const int i0 = t0 + ((h - t0 % LS_TPC) + LS_TPC) % LS_TPC;
+      float w[4] = {0.f, 0.f, 0.f, 0.f};
       if (act)
-        for (int i = i0; i < l; i += LS_TPC) d = fmaf(i == t ? 1.f : v[i], x[i], d);
+        for (int i = i0; i < l; i += LS_TPC) {
+          const float xi = x[i];
 #pragma unroll
-      for (int o = LS_TPC / 2; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      d *= tau[t];
+          for (int c = 0; c < 4; ++c) {
+            // v_c(i) = 0 above its diagonal (V holds R there); columns past r are absent
+            const float vc = (i < t0 + c || t0 + c >= r) ? 0.f : v0[c * ldv + i];
+            w[c] = fmaf(vc, xi, w[c]);
+          }
+        }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int o = LS_TPC / 2; o > 0; o >>= 1) w[c] += __shfl_xor_sync(0xffffffffu, w[c], o);
+      float u[4];                                         // u = T_4^T w
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float a = 0.f;
+#pragma unroll
+        for (int k = 0; k <= c; ++k) a = fmaf(T4[g][k * 4 + c], w[k], a);
+        u[c] = a;
+      }
       if (act)
-        for (int i = i0; i < l; i += LS_TPC) x[i] = fmaf(-d, i == t ? 1.f : v[i], x[i]);
+        for (int i = i0; i < l; i += LS_TPC) {
+          float xi = x[i];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float vc = (i < t0 + c || t0 + c >= r) ? 0.f : v0[c * ldv + i];
+            xi = fmaf(-u[c], vc, xi);
+          }
+          x[i] = xi;
+        }
     }
-    if (act && h == 0) {                                  // z = R^{-1} (Q^T x)(0:r)
-      for (int q = r - 1; q >= 0; --q) {
-        float z = x[q];
-        for (int q2 = q + 1; q2 < r; ++q2) z = fmaf(-V[q2 * ldv + q], x[q2], z);
-        z = z / V[q * ldv + q];
-        x[q] = z;
-        bad |= !isfinite(z);
+    // z = R^{-1} (Q^T x)(0:r), column-oriented over the eight lanes of the column
+    for (int q = r - 1; q >= 0; --q) {
+      __syncwarp(gmask);                                  // row q of x is final
+      const float z = act ? x[q] / rdiag[q] : 0.f;
+      bad |= act && !isfinite(z);
+      __syncwarp(gmask);                                  // every lane has read x[q]
+      if (act) {
+        if (h == q % LS_TPC) x[q] = z;
+        for (int i = h; i < q; i += LS_TPC) x[i] = fmaf(-V[q * ldv + i], z, x[i]);
       }
     }
     __syncthreads();
@@ -898,8 +980,8 @@ size_t lupp_budget() {
   return budget;
 }
 
-size_t sketch_smem_for(int lp, int stages) {
-  return 1024 + (size_t)stages * (2 * (size_t)BS_ATILE + 2 * (size_t)lp * 128) + 256;
+size_t sketch_smem_for(int lp, int stages, bool pts) {
+  return 1024 + (size_t)stages * (2 * (size_t)BS_ATILE + 2 * (size_t)lp * 128 + (pts ? BS_XREC : 0)) + 256;
 }
 
 // One run's launches on `st`: Gamma, the sketch, then the LUPP cluster classes, either one
@@ -1026,7 +1108,7 @@ skel_status autotune(skel_batch_plan* pl) {
   for (int stages = 2; ok && stages <= pl->max_stages; ++stages)
     for (int conc = 0; ok && conc < 2; ++conc) {
       pl->stages = stages;
-      pl->sketch_smem = sketch_smem_for(pl->lp, stages);
+      pl->sketch_smem = sketch_smem_for(pl->lp, stages, pl->points);
       pl->concurrent = conc;
       ok = enqueue_run(pl, Js, ranks, Z, st, pl->cap, false, nullptr) == SKEL_OK &&
            cudaEventRecord(e0, pl->cap) == cudaSuccess;
@@ -1044,7 +1126,7 @@ skel_status autotune(skel_batch_plan* pl) {
   int32_t hst[2] = {0, 0};
   if (ok) ok = cudaMemcpy(hst, st, sizeof(hst), cudaMemcpyDeviceToHost) == cudaSuccess;
   pl->stages = best_stages;
-  pl->sketch_smem = sketch_smem_for(pl->lp, best_stages);
+  pl->sketch_smem = sketch_smem_for(pl->lp, best_stages, pl->points);
   pl->concurrent = best_conc;
   cudaFree(Js);
   cudaFree(ranks);
@@ -1123,15 +1205,16 @@ static skel_status plan_create(int32_t nblocks, const int64_t* m, const int64_t*
     pl->w_lo = (float)(w - (double)pl->w_hi);
   }
   // shared memory of the sketch: 3 stages when they fit, else 2 (the autotuner may pick 2)
-  pl->max_stages = sketch_smem_for(lp, 3) <= 227 * 1024 ? 3 : 2;
+  pl->max_stages = sketch_smem_for(lp, 3, pts != nullptr) <= 227 * 1024 ? 3 : 2;
   pl->stages = pl->max_stages;
-  pl->sketch_smem = sketch_smem_for(lp, pl->stages);
+  pl->sketch_smem = sketch_smem_for(lp, pl->stages, pts != nullptr);
 
   std::vector<BatchBlock> hb(nblocks);
   std::vector<CUtensorMap> ht(pts ? 0 : nblocks);
   std::vector<SketchItem> items;
   std::vector<PointSrc> hsrc(pts ? nblocks : 0);
-  if (pts && cudaMalloc(&pl->d_rec, sizeof(float) * kRec * (size_t)npts) != cudaSuccess) {
+  // 32 records of padding: the last block's last 32-row step may copy past its x records
+  if (pts && cudaMalloc(&pl->d_rec, sizeof(float) * kRec * (size_t)(npts + 32)) != cudaSuccess) {
     cudaGetLastError();
     plan_free(pl);
     return SKEL_ERR_CUDA;
@@ -1208,9 +1291,9 @@ static skel_status plan_create(int32_t nblocks, const int64_t* m, const int64_t*
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   }
   ok = ok && cudaFuncSetAttribute(batch_sketch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sketch_smem_for(lp, pl->max_stages)) == cudaSuccess &&
+                                  (int)sketch_smem_for(lp, pl->max_stages, false)) == cudaSuccess &&
        cudaFuncSetAttribute(batch_sketch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)sketch_smem_for(lp, pl->max_stages)) == cudaSuccess &&
+                            (int)sketch_smem_for(lp, pl->max_stages, true)) == cudaSuccess &&
        cudaFuncSetAttribute(batch_lupp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget) == cudaSuccess &&
        cudaFuncSetAttribute(batch_lsq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsq_smem(l, kmax)) ==
            cudaSuccess;
