@@ -647,6 +647,12 @@ QrPanelPlan plan_qr_panels(int64_t m, int s) {
   int b = std::min(kQrMaxB, s);
   while (b >= 8 && qr_panel_smem<T>(b, (int)mloc) > budget) b -= 4;
   if (b < std::min(8, s) || qr_panel_smem<T>(b, (int)mloc) > budget) return plan_qr_grid<T>(m, s);
+  // a cluster panel this narrow means many panels, each with its WY factor and trailing
+  // products: the grid's wider panels cost a grid barrier per column instead
+  if (b < 16) {
+    const QrPanelPlan g = plan_qr_grid<T>(m, s);
+    if (g.b >= 2 * b) return g;
+  }
   pl.CL = CL;
   pl.b = b;
   pl.mloc = (int)mloc;
