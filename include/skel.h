@@ -6,8 +6,8 @@
  *
  * Conventions shared by every entry point
  * ---------------------------------------
- *  - Every matrix pointer is a DEVICE pointer owned by the caller; the library never frees
- *    or retains it.  Only the two batch plan constructors allocate device memory (the plan's own, freed
+ *  - Every matrix pointer is a DEVICE pointer owned by the caller (skel_sketch_host's A is a
+ *    host pointer); the library never frees or retains it.  Only the two batch plan constructors allocate device memory (the plan's own, freed
  *    by skel_batch_plan_destroy); every other call that needs scratch memory takes a
  *    caller-provided device workspace `ws` of `*ws_bytes` bytes (skel_pivot_lupp_static uses a
  *    fixed array inside the library instead).  Calling with
@@ -18,7 +18,8 @@
  *    Wide matrices (the sketch X, pivot factors R, the ID matrix Z: l or s rows, n columns)
  *    are ROW-MAJOR: element (r, j) at p[r*ld + j], ld >= n.  (So X^T is column-major n x l.)
  *  - Indices are 0-based int32 (the paper's MATLAB indices are 1-based), in selection order.
- *  - All work is enqueued on `stream` in stream order; no call synchronizes the host.
+ *  - All work is enqueued on `stream` in stream order; no call synchronizes the host (except
+ *    skel_sketch_host with a pageable A, whose copies the driver stages through the host).
  *    Argument errors are detected on the host and returned synchronously with nothing
  *    launched.  Errors found on the device (non-finite data, a zero pivot, a timed-out grid
  *    wait) are written to `dev_status` (device int32[2]: {code, step}; may be NULL), first
@@ -124,6 +125,33 @@ skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dt
                              int64_t lda, int32_t l, skel_sketch_kind kind, int32_t zeta, skel_prec prec,
                              uint64_t seed, void* X, int64_t ldx, void* ws, size_t* ws_bytes,
                              int32_t* dev_status, cudaStream_t stream);
+
+/*
+ * skel_sketch_host -- skel_sketch of an A that lives in host memory, streamed to the device in
+ * column panels.  X = Gamma A reads A once (Algorithm 1 line 2; the single pass over A of
+ * Sec. 2.3), and X's columns j0..j1 depend on A's columns j0..j1 only, so the copy of one panel
+ * overlaps the sketch of the one before: panels go through two device staging buffers in the
+ * workspace, copied on a library-owned stream and sketched on `stream`.  A never has to fit
+ * in device memory.
+ *   A, lda    : m x n column-major in host memory (a device pointer also works).  Page-locked
+ *               (pinned) memory gives asynchronous copies that overlap the sketch; pageable
+ *               memory is accepted, and the driver then stages each panel copy through the
+ *               host, which may block the calling thread.
+ *   panel     : columns per panel; 0 chooses about 512 MiB of A per panel, a multiple of 256
+ *               columns.
+ *   every other argument is skel_sketch's; the tensor-core precisions need no alignment of the
+ *               host A (the staging columns are padded to 16 bytes).
+ * X equals skel_sketch of the same A on the device up to the summation order of the K-split
+ * partial sums, which depends on the panel width.  Workspace: two staging panels of
+ * esize * round_up(m, 4) * panel bytes plus skel_sketch's workspace for one panel.  The call
+ * enqueues its work and returns (pinned A); the caller must keep A unchanged until `stream`
+ * reaches the end of the call's work.  Errors: as skel_sketch; SKEL_ERR_INVALID_ARG for a
+ * negative panel.
+ */
+skel_status skel_sketch_host(int64_t m, int64_t n, skel_dtype a_dtype, const void* A, int64_t lda, int32_t l,
+                             skel_sketch_kind kind, int32_t zeta, skel_prec prec, uint64_t seed, void* X,
+                             int64_t ldx, int64_t panel, void* ws, size_t* ws_bytes, int32_t* dev_status,
+                             cudaStream_t stream);
 
 /*
  * skel_sketch_cols -- the column sketch of the streaming skeleton selection (Algorithm 3 line 2):

@@ -45,6 +45,7 @@ def lib():
     sig = {
         "skel_sketch": [i64, i64, i32, vp, i64, i32, i32, i32, i32, u64, vp, i64, vp, szp, vp, vp],
         "skel_sketch_rows": [i64, i64, i64, i32, vp, i64, i32, i32, i32, i32, u64, vp, i64, vp, szp, vp, vp],
+        "skel_sketch_host": [i64, i64, i32, vp, i64, i32, i32, i32, i32, u64, vp, i64, i64, vp, szp, vp, vp],
         "skel_sketch_csc": [i64, i64, i64, vp, vp, vp, i32, i32, i32, u64, vp, i64, vp, szp, vp, vp],
         "skel_pivot_lupp": [i32, vp, i64, i64, i64, i32, vp, vp, i64, vp, i64, vp, szp, vp, vp],
         "skel_pivot_cpqr": [i32, vp, i64, i64, i64, i32, vp, vp, i64, vp, szp, vp, vp],
@@ -197,6 +198,31 @@ def sketch(A, l, kind="gaussian", prec="f32", seed=0, zeta=8, X=None, status=Non
     st = status if status is not None else new_status(A.device)
     _call("skel_sketch_rows", lambda w, sz: [row0, m, n, _dt(A), _ptr(A), lda, l, KIND[kind], zeta, PREC[prec],
                                              seed, _ptr(X), ldx, w, sz, _ptr(st), _stream()], A.device)
+    return X, st
+
+
+def sketch_host(A, l, kind="gaussian", prec="f32", seed=0, zeta=8, X=None, status=None, panel=0, device=None):
+    """X = Gamma A for a host (CPU) A: the library copies A's column panels to the device (two
+    staging buffers in the workspace) while it sketches the panel before; X lands on `device`.
+    A pinned A (``pin_memory()``) lets the copies run asynchronously; it must then stay alive and
+    unchanged until the current stream has passed this call (synchronize, or an event)."""
+    if A.is_cuda:
+        raise ValueError("sketch_host takes a host tensor; use sketch() for a device A")
+    if A.dim() != 2:
+        raise ValueError("expected a matrix")
+    if not (A.stride(0) == 1 and (A.stride(1) >= max(1, A.shape[0]) or A.shape[1] <= 1)):
+        A = A.t().contiguous().t()
+    lda = max(A.stride(1), A.shape[0], 1)
+    m, n = A.shape
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    xdt = torch.float64 if prec == "f64" else torch.float32
+    if X is None:
+        X = torch.empty(l, n, dtype=xdt, device=dev)
+    X, ldx = _rowmajor(X)
+    st = status if status is not None else new_status(dev)
+    host = ctypes.c_void_p(A.data_ptr())
+    _call("skel_sketch_host", lambda w, sz: [m, n, _dt(A), host, lda, l, KIND[kind], zeta, PREC[prec], seed,
+                                            _ptr(X), ldx, panel, w, sz, _ptr(st), _stream()], dev)
     return X, st
 
 

@@ -8,6 +8,7 @@
 #include "internal.h"
 
 #include <atomic>
+#include <mutex>
 
 using namespace skel;
 
@@ -198,6 +199,113 @@ skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dt
   a.gcol0 = row0;
   a.dev_status = dev_status;
   SK_CUDA(launch_gemm(a, prec == SKEL_PREC_F64, LEFT_GAUSSIAN, EPI_SKETCH, stream));
+  return SKEL_OK;
+}
+
+namespace {
+
+// The copy stream and events of skel_sketch_host, one set per device, created on first use.
+// copied[b] marks staging buffer b filled, consumed[b] the sketch of it finished.
+struct HostStreamSet {
+  cudaStream_t copy = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+};
+
+std::mutex& host_stream_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+
+HostStreamSet* host_stream_set() {
+  static HostStreamSet sets[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  HostStreamSet& h = sets[dev];
+  if (h.copy) return &h;
+  bool ok = cudaStreamCreateWithFlags(&h.copy, cudaStreamNonBlocking) == cudaSuccess;
+  for (cudaEvent_t* e : {&h.fork, &h.join, &h.copied[0], &h.copied[1], &h.consumed[0], &h.consumed[1]})
+    ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    h.copy = nullptr;
+    return nullptr;
+  }
+  return &h;
+}
+
+// Joins the copy stream back into the caller's stream on every return path.
+struct HostStreamJoin {
+  cudaStream_t st;
+  HostStreamSet* h;
+  ~HostStreamJoin() {
+    if (cudaEventRecord(h->join, h->copy) == cudaSuccess) cudaStreamWaitEvent(st, h->join, 0);
+  }
+};
+
+// Columns per panel: the caller's choice, else about 512 MiB of A in multiples of 256 columns.
+int64_t host_panel_cols(int64_t m, int64_t n, skel_dtype dt, int64_t panel) {
+  if (panel > 0) return std::min(panel, n);
+  int64_t w = ((int64_t)512 << 20) / std::max<int64_t>(1, (int64_t)esize(dt) * m);
+  w = std::max<int64_t>(256, w / 256 * 256);
+  return std::min(w, n);
+}
+
+}  // namespace
+
+skel_status skel_sketch_host(int64_t m, int64_t n, skel_dtype a_dtype, const void* A, int64_t lda, int32_t l,
+                             skel_sketch_kind kind, int32_t zeta, skel_prec prec, uint64_t seed, void* X,
+                             int64_t ldx, int64_t panel, void* ws, size_t* ws_bytes, int32_t* dev_status,
+                             cudaStream_t stream) {
+  if (m < 0 || n < 0 || panel < 0 || !valid_dtype(a_dtype)) return SKEL_ERR_INVALID_ARG;
+  if (lda < std::max<int64_t>(1, m) || ldx < std::max<int64_t>(1, n)) return SKEL_ERR_INVALID_ARG;
+  if ((m > 0 && n > 0 && A == nullptr) || (n > 0 && X == nullptr)) return SKEL_ERR_INVALID_ARG;
+  const skel_dtype x_dt = prec == SKEL_PREC_F64 ? SKEL_F64 : SKEL_F32;
+  const int64_t w = n > 0 ? host_panel_cols(m, n, a_dtype, panel) : 0;
+  const int64_t npan = w > 0 ? (n + w - 1) / w : 0;
+  const int64_t wlast = npan > 0 ? n - (npan - 1) * w : 0;
+  const int64_t lds = std::max<int64_t>(4, (m + 3) / 4 * 4);   // staging columns start 16-byte aligned
+  // the sketch workspace of the two panel widths that occur (argument checks happen here too)
+  size_t need_w = 0, need_last = 0;
+  SK_TRY(skel_sketch_rows(0, m, w, a_dtype, A, lds, l, kind, zeta, prec, seed, X, ldx, nullptr, &need_w, dev_status,
+                          stream));
+  if (wlast > 0 && wlast != w)
+    SK_TRY(skel_sketch_rows(0, m, wlast, a_dtype, A, lds, l, kind, zeta, prec, seed, X, ldx, nullptr, &need_last,
+                            dev_status, stream));
+  Arena ar(ws);
+  char* stage[2];
+  stage[0] = static_cast<char*>(m > 0 && n > 0 ? ar.take(esize(a_dtype) * (size_t)lds * w) : nullptr);
+  stage[1] = static_cast<char*>(m > 0 && npan > 1 ? ar.take(esize(a_dtype) * (size_t)lds * w) : nullptr);
+  size_t sws_bytes = std::max(need_w, need_last);
+  void* sws = ar.take(sws_bytes);
+  skel_status st;
+  if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+  if (n == 0) return SKEL_OK;
+  if (m == 0) return skel_sketch_rows(0, 0, n, a_dtype, nullptr, lda, l, kind, zeta, prec, seed, X, ldx, sws, &sws_bytes,
+                                      dev_status, stream);
+  std::lock_guard<std::mutex> lock(host_stream_mutex());
+  HostStreamSet* h = host_stream_set();
+  if (h == nullptr) return SKEL_ERR_CUDA;
+  SK_CUDA(cudaEventRecord(h->fork, stream));
+  SK_CUDA(cudaStreamWaitEvent(h->copy, h->fork, 0));
+  HostStreamJoin joiner{stream, h};
+  const size_t ea = esize(a_dtype);
+  for (int64_t i = 0; i < npan; ++i) {
+    const int b = (int)(i & 1);
+    const int64_t j0 = i * w, wi = std::min(w, n - j0);
+    if (i >= 2) SK_CUDA(cudaStreamWaitEvent(h->copy, h->consumed[b], 0));
+    const char* src = static_cast<const char*>(A) + ea * (size_t)lda * j0;
+    if (lda == lds)   // contiguous columns: one linear copy
+      SK_CUDA(cudaMemcpyAsync(stage[b], src, ea * (size_t)lds * (wi - 1) + ea * m, cudaMemcpyDefault, h->copy));
+    else
+      SK_CUDA(cudaMemcpy2DAsync(stage[b], ea * lds, src, ea * lda, ea * m, wi, cudaMemcpyDefault, h->copy));
+    SK_CUDA(cudaEventRecord(h->copied[b], h->copy));
+    SK_CUDA(cudaStreamWaitEvent(stream, h->copied[b], 0));
+    size_t sz = sws_bytes;
+    SK_TRY(skel_sketch_rows(0, m, wi, a_dtype, stage[b], lds, l, kind, zeta, prec, seed,
+                            static_cast<char*>(X) + esize(x_dt) * j0, ldx, sws, &sz, dev_status, stream));
+    SK_CUDA(cudaEventRecord(h->consumed[b], stream));
+  }
   return SKEL_OK;
 }
 

@@ -353,7 +353,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap tmapA, const TcParams p) {
         const int64_t jc = j0 + c0;
         if (row < p.l && jc < p.n) {
           const float sc = p.direct ? p.scale : 1.0f;
-          if (jc + 32 <= p.n && ((p.ldo & 3) == 0)) {
+          if (jc + 32 <= p.n && ((p.ldo & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 15) == 0)) {
 #pragma unroll
             for (int q = 0; q < 32; q += 4) {
               float4 v = make_float4(__uint_as_float(r[q]) * sc, __uint_as_float(r[q + 1]) * sc,
