@@ -6,8 +6,8 @@
  *
  * Conventions shared by every entry point
  * ---------------------------------------
- *  - Every matrix pointer is a DEVICE pointer owned by the caller (skel_sketch_host's A is a
- *    host pointer); the library never frees or retains it.  Only the two batch plan constructors allocate device memory (the plan's own, freed
+ *  - Every matrix pointer is a DEVICE pointer owned by the caller (the A of skel_sketch_host and
+ *    skel_sketch_host_two_sided is a host pointer); the library never frees or retains it.  Only the two batch plan constructors allocate device memory (the plan's own, freed
  *    by skel_batch_plan_destroy); every other call that needs scratch memory takes a
  *    caller-provided device workspace `ws` of `*ws_bytes` bytes (skel_pivot_lupp_static uses a
  *    fixed array inside the library instead).  Calling with
@@ -19,7 +19,7 @@
  *    are ROW-MAJOR: element (r, j) at p[r*ld + j], ld >= n.  (So X^T is column-major n x l.)
  *  - Indices are 0-based int32 (the paper's MATLAB indices are 1-based), in selection order.
  *  - All work is enqueued on `stream` in stream order; no call synchronizes the host (except
- *    skel_sketch_host with a pageable A, whose copies the driver stages through the host).
+ *    the host-A sketches with a pageable A, whose copies the driver stages through the host).
  *    Argument errors are detected on the host and returned synchronously with nothing
  *    launched.  Errors found on the device (non-finite data, a zero pivot, a timed-out grid
  *    wait) are written to `dev_status` (device int32[2]: {code, step}; may be NULL), first
@@ -152,6 +152,33 @@ skel_status skel_sketch_host(int64_t m, int64_t n, skel_dtype a_dtype, const voi
                              skel_sketch_kind kind, int32_t zeta, skel_prec prec, uint64_t seed, void* X,
                              int64_t ldx, int64_t panel, void* ws, size_t* ws_bytes, int32_t* dev_status,
                              cudaStream_t stream);
+
+/*
+ * skel_sketch_host_two_sided -- both sketches of the streaming skeleton selection (Algorithm 3
+ * line 2) from ONE pass over an A in host memory: X = Gamma A (l x n, as skel_sketch with the
+ * Gaussian embedding and seed_gamma) and Yt = Omega A^T (l x m, as skel_sketch_cols with
+ * seed_omega).  Each column panel A(:, j0:j0+w) is copied to the device once (as in
+ * skel_sketch_host) and gives X(:, j0:j0+w) = Gamma A(:, panel) and the partial sum
+ * Omega(:, j0:j0+w) A(:, panel)^T of Yt, which the library adds up across panels (the first
+ * panel writes Yt, later ones add a partial).  This is the single-pass form Algorithm 3 is
+ * designed for: A is seen once, and neither A nor a transposed copy of it is kept on the device.
+ *   m, n >= 1; l in 1..4096; prec: SKEL_PREC_F64 (a_dtype F64), SKEL_PREC_F32, SKEL_PREC_TF32 or
+ *               SKEL_PREC_BF16 (a_dtype F32).  The tensor-core precisions transpose each panel on
+ *               the device and run the tensor-core sketch with Omega's column offset j0.
+ *   panel     : columns per panel, a multiple of 4 (Omega's counters take columns four at a
+ *               time); 0 chooses about 512 MiB of A per panel.
+ *   X, ldx    : l x n row-major (ldx >= n).   Yt, ldy: l x m row-major (ldy >= m).
+ * X and Yt equal skel_sketch and skel_sketch_cols on the device copy of A up to the order of
+ * their sums.  Workspace: two staging panels, the row sketch's workspace for one panel, the
+ * column sketch's (plus a transposed panel for TF32 / BF16) and one l x m partial.  A must stay
+ * unchanged until `stream` reaches the end of the call's work.  Errors: SKEL_ERR_INVALID_ARG for
+ * bad sizes, a panel that is negative or not a multiple of 4, or a_dtype not matching prec;
+ * SKEL_ERR_UNSUPPORTED for FP8; non-finite entries set SKEL_ERR_NONFINITE in dev_status.
+ */
+skel_status skel_sketch_host_two_sided(int64_t m, int64_t n, skel_dtype a_dtype, const void* A, int64_t lda,
+                                       int32_t l, skel_prec prec, uint64_t seed_gamma, uint64_t seed_omega, void* X,
+                                       int64_t ldx, void* Yt, int64_t ldy, int64_t panel, void* ws, size_t* ws_bytes,
+                                       int32_t* dev_status, cudaStream_t stream);
 
 /*
  * skel_sketch_cols -- the column sketch of the streaming skeleton selection (Algorithm 3 line 2):

@@ -46,6 +46,8 @@ def lib():
         "skel_sketch": [i64, i64, i32, vp, i64, i32, i32, i32, i32, u64, vp, i64, vp, szp, vp, vp],
         "skel_sketch_rows": [i64, i64, i64, i32, vp, i64, i32, i32, i32, i32, u64, vp, i64, vp, szp, vp, vp],
         "skel_sketch_host": [i64, i64, i32, vp, i64, i32, i32, i32, i32, u64, vp, i64, i64, vp, szp, vp, vp],
+        "skel_sketch_host_two_sided": [i64, i64, i32, vp, i64, i32, i32, u64, u64, vp, i64, vp, i64, i64, vp, szp, vp,
+                                       vp],
         "skel_sketch_csc": [i64, i64, i64, vp, vp, vp, i32, i32, i32, u64, vp, i64, vp, szp, vp, vp],
         "skel_pivot_lupp": [i32, vp, i64, i64, i64, i32, vp, vp, i64, vp, i64, vp, szp, vp, vp],
         "skel_pivot_cpqr": [i32, vp, i64, i64, i64, i32, vp, vp, i64, vp, szp, vp, vp],
@@ -206,13 +208,7 @@ def sketch_host(A, l, kind="gaussian", prec="f32", seed=0, zeta=8, X=None, statu
     staging buffers in the workspace) while it sketches the panel before; X lands on `device`.
     A pinned A (``pin_memory()``) lets the copies run asynchronously; it must then stay alive and
     unchanged until the current stream has passed this call (synchronize, or an event)."""
-    if A.is_cuda:
-        raise ValueError("sketch_host takes a host tensor; use sketch() for a device A")
-    if A.dim() != 2:
-        raise ValueError("expected a matrix")
-    if not (A.stride(0) == 1 and (A.stride(1) >= max(1, A.shape[0]) or A.shape[1] <= 1)):
-        A = A.t().contiguous().t()
-    lda = max(A.stride(1), A.shape[0], 1)
+    A, lda = _host_colmajor(A)
     m, n = A.shape
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     xdt = torch.float64 if prec == "f64" else torch.float32
@@ -224,6 +220,44 @@ def sketch_host(A, l, kind="gaussian", prec="f32", seed=0, zeta=8, X=None, statu
     _call("skel_sketch_host", lambda w, sz: [m, n, _dt(A), host, lda, l, KIND[kind], zeta, PREC[prec], seed,
                                             _ptr(X), ldx, panel, w, sz, _ptr(st), _stream()], dev)
     return X, st
+
+
+def _host_colmajor(A):
+    if A.is_cuda:
+        raise ValueError("expected a host tensor; the device forms take a CUDA tensor")
+    if A.dim() != 2:
+        raise ValueError("expected a matrix")
+    if not (A.stride(0) == 1 and (A.stride(1) >= max(1, A.shape[0]) or A.shape[1] <= 1)):
+        A = A.t().contiguous().t()
+    return A, max(A.stride(1), A.shape[0], 1)
+
+
+def sketch_host_two_sided(A, l, prec="f32", seed=0, seed_omega=None, status=None, panel=0, device=None):
+    """X = Gamma A (l x n) and Yt = Omega A^T (l x m) from one pass over a host A, streamed in
+    column panels: the two sketches of Algorithm 3.  A must stay alive and unchanged until the
+    current stream has passed this call."""
+    A, lda = _host_colmajor(A)
+    m, n = A.shape
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    xdt = torch.float64 if prec == "f64" else torch.float32
+    X = torch.empty(l, n, dtype=xdt, device=dev)
+    Yt = torch.empty(l, m, dtype=xdt, device=dev)
+    st = status if status is not None else new_status(dev)
+    so = seed + 1 if seed_omega is None else seed_omega
+    host = ctypes.c_void_p(A.data_ptr())
+    _call("skel_sketch_host_two_sided", lambda w, sz: [m, n, _dt(A), host, lda, l, PREC[prec], seed, so, _ptr(X), n,
+                                                       _ptr(Yt), m, panel, w, sz, _ptr(st), _stream()], dev)
+    return X, Yt, st
+
+
+def skeletonize_streaming_host(A, k, p=10, seed=0, seed_omega=None, prec="f32", status=None, panel=0):
+    """Algorithm 3 on a host A in one pass: both sketches from the same streamed panels, then J_s
+    by LUPP on X and I_s by LUPP on Y^T."""
+    X, Yt, st = sketch_host_two_sided(A, k + p, prec=prec, seed=seed, seed_omega=seed_omega, status=status,
+                                      panel=panel)
+    Js, _, _, _ = pivot_lupp(X, k, factors=False, status=st)
+    Is, _, _, _ = pivot_lupp(Yt, k, factors=False, status=st)
+    return Js, Is, st
 
 
 def sketch_power(A, l, q=1, prec="tf32", seed=0, status=None):

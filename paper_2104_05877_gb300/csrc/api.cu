@@ -202,6 +202,8 @@ skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dt
   return SKEL_OK;
 }
 
+}  // extern "C"
+
 namespace {
 
 // The copy stream and events of skel_sketch_host, one set per device, created on first use.
@@ -251,7 +253,40 @@ int64_t host_panel_cols(int64_t m, int64_t n, skel_dtype dt, int64_t panel) {
   return std::min(w, n);
 }
 
+// Streams the column panels of A (w columns each; host or device memory) through the staging
+// buffers stage[0..1] (leading dimension lds) and calls work(i, stage, j0, wi) on `stream` for
+// panel i once its copy has landed; the copy of panel i + 1 runs meanwhile on the copy stream,
+// and the copy of panel i + 2 waits until the work on panel i has finished with its buffer.
+template <typename Work>
+skel_status stream_panels(int64_t m, int64_t n, size_t ea, const void* A, int64_t lda, int64_t lds, int64_t w,
+                          char* const stage[2], cudaStream_t stream, Work&& work) {
+  std::lock_guard<std::mutex> lock(host_stream_mutex());
+  HostStreamSet* h = host_stream_set();
+  if (h == nullptr) return SKEL_ERR_CUDA;
+  SK_CUDA(cudaEventRecord(h->fork, stream));
+  SK_CUDA(cudaStreamWaitEvent(h->copy, h->fork, 0));
+  HostStreamJoin joiner{stream, h};
+  const int64_t npan = (n + w - 1) / w;
+  for (int64_t i = 0; i < npan; ++i) {
+    const int b = (int)(i & 1);
+    const int64_t j0 = i * w, wi = std::min(w, n - j0);
+    if (i >= 2) SK_CUDA(cudaStreamWaitEvent(h->copy, h->consumed[b], 0));
+    const char* src = static_cast<const char*>(A) + ea * (size_t)lda * j0;
+    if (lda == lds)   // contiguous columns: one linear copy
+      SK_CUDA(cudaMemcpyAsync(stage[b], src, ea * (size_t)lds * (wi - 1) + ea * m, cudaMemcpyDefault, h->copy));
+    else
+      SK_CUDA(cudaMemcpy2DAsync(stage[b], ea * lds, src, ea * lda, ea * m, wi, cudaMemcpyDefault, h->copy));
+    SK_CUDA(cudaEventRecord(h->copied[b], h->copy));
+    SK_CUDA(cudaStreamWaitEvent(stream, h->copied[b], 0));
+    SK_TRY(work(i, stage[b], j0, wi));
+    SK_CUDA(cudaEventRecord(h->consumed[b], stream));
+  }
+  return SKEL_OK;
+}
+
 }  // namespace
+
+extern "C" {
 
 skel_status skel_sketch_host(int64_t m, int64_t n, skel_dtype a_dtype, const void* A, int64_t lda, int32_t l,
                              skel_sketch_kind kind, int32_t zeta, skel_prec prec, uint64_t seed, void* X,
@@ -281,32 +316,94 @@ skel_status skel_sketch_host(int64_t m, int64_t n, skel_dtype a_dtype, const voi
   skel_status st;
   if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
   if (n == 0) return SKEL_OK;
-  if (m == 0) return skel_sketch_rows(0, 0, n, a_dtype, nullptr, lda, l, kind, zeta, prec, seed, X, ldx, sws, &sws_bytes,
-                                      dev_status, stream);
-  std::lock_guard<std::mutex> lock(host_stream_mutex());
-  HostStreamSet* h = host_stream_set();
-  if (h == nullptr) return SKEL_ERR_CUDA;
-  SK_CUDA(cudaEventRecord(h->fork, stream));
-  SK_CUDA(cudaStreamWaitEvent(h->copy, h->fork, 0));
-  HostStreamJoin joiner{stream, h};
-  const size_t ea = esize(a_dtype);
-  for (int64_t i = 0; i < npan; ++i) {
-    const int b = (int)(i & 1);
-    const int64_t j0 = i * w, wi = std::min(w, n - j0);
-    if (i >= 2) SK_CUDA(cudaStreamWaitEvent(h->copy, h->consumed[b], 0));
-    const char* src = static_cast<const char*>(A) + ea * (size_t)lda * j0;
-    if (lda == lds)   // contiguous columns: one linear copy
-      SK_CUDA(cudaMemcpyAsync(stage[b], src, ea * (size_t)lds * (wi - 1) + ea * m, cudaMemcpyDefault, h->copy));
-    else
-      SK_CUDA(cudaMemcpy2DAsync(stage[b], ea * lds, src, ea * lda, ea * m, wi, cudaMemcpyDefault, h->copy));
-    SK_CUDA(cudaEventRecord(h->copied[b], h->copy));
-    SK_CUDA(cudaStreamWaitEvent(stream, h->copied[b], 0));
-    size_t sz = sws_bytes;
-    SK_TRY(skel_sketch_rows(0, m, wi, a_dtype, stage[b], lds, l, kind, zeta, prec, seed,
-                            static_cast<char*>(X) + esize(x_dt) * j0, ldx, sws, &sz, dev_status, stream));
-    SK_CUDA(cudaEventRecord(h->consumed[b], stream));
-  }
-  return SKEL_OK;
+  if (m == 0) return skel_sketch_rows(0, 0, n, a_dtype, nullptr, lda, l, kind, zeta, prec, seed, X, ldx, sws,
+                                      &sws_bytes, dev_status, stream);
+  return stream_panels(m, n, esize(a_dtype), A, lda, lds, w, stage, stream,
+                       [&](int64_t, const char* panel_a, int64_t j0, int64_t wi) -> skel_status {
+                         size_t sz = sws_bytes;
+                         return skel_sketch_rows(0, m, wi, a_dtype, panel_a, lds, l, kind, zeta, prec, seed,
+                                                 static_cast<char*>(X) + esize(x_dt) * j0, ldx, sws, &sz,
+                                                 dev_status, stream);
+                       });
+}
+
+skel_status skel_sketch_host_two_sided(int64_t m, int64_t n, skel_dtype a_dtype, const void* A, int64_t lda,
+                                       int32_t l, skel_prec prec, uint64_t seed_gamma, uint64_t seed_omega, void* X,
+                                       int64_t ldx, void* Yt, int64_t ldy, int64_t panel, void* ws, size_t* ws_bytes,
+                                       int32_t* dev_status, cudaStream_t stream) {
+  if (m < 1 || n < 1 || l < 1 || l > 4096 || !valid_dtype(a_dtype) || A == nullptr || X == nullptr ||
+      Yt == nullptr || lda < m || ldx < n || ldy < m || panel < 0 || panel % 4 != 0 || n > 0xFFFFFFFFll)
+    return SKEL_ERR_INVALID_ARG;
+  if (prec == SKEL_PREC_FP8) return SKEL_ERR_UNSUPPORTED;
+  if ((prec == SKEL_PREC_F64) != (a_dtype == SKEL_F64)) return SKEL_ERR_INVALID_ARG;
+  const bool tc = prec == SKEL_PREC_TF32 || prec == SKEL_PREC_BF16;
+  if (tc && m > (int64_t)INT32_MAX) return SKEL_ERR_UNSUPPORTED;
+  const bool f64 = prec == SKEL_PREC_F64;
+  const skel_dtype x_dt = f64 ? SKEL_F64 : SKEL_F32;
+  const size_t ex = esize(x_dt), ea = esize(a_dtype);
+  // panel offsets stay multiples of 4: Omega's counters take its columns four at a time
+  const int64_t w = std::max<int64_t>(4, host_panel_cols(m, n, a_dtype, panel) / 4 * 4);
+  const int64_t npan = (n + w - 1) / w;
+  const int64_t wlast = n - (npan - 1) * w;
+  const int64_t lds = (m + 3) / 4 * 4;
+  const int64_t w4 = (w + 3) / 4 * 4;
+  size_t need_w = 0, need_last = 0;
+  SK_TRY(skel_sketch_rows(0, m, std::min(w, n), a_dtype, A, lds, l, SKEL_SKETCH_GAUSSIAN, 0, prec, seed_gamma, X,
+                          ldx, nullptr, &need_w, dev_status, stream));
+  if (wlast != w)
+    SK_TRY(skel_sketch_rows(0, m, wlast, a_dtype, A, lds, l, SKEL_SKETCH_GAUSSIAN, 0, prec, seed_gamma, X, ldx,
+                            nullptr, &need_last, dev_status, stream));
+  size_t yws_bytes = tc ? std::max(sketch_tc_workspace(std::min(w, n), m, l, prec), sketch_tc_workspace(wlast, m, l, prec))
+                        : std::max(gemm_workspace(l, m, std::min(w, n), f64), gemm_workspace(l, m, wlast, f64));
+  Arena ar(ws);
+  char* stage[2];
+  stage[0] = static_cast<char*>(ar.take(ea * (size_t)lds * w));
+  stage[1] = static_cast<char*>(npan > 1 ? ar.take(ea * (size_t)lds * w) : nullptr);
+  size_t xws_bytes = std::max(need_w, need_last);
+  void* xws = ar.take(xws_bytes);
+  float* At = tc ? static_cast<float*>(ar.take(sizeof(float) * (size_t)w4 * m)) : nullptr;
+  void* yws = ar.take(yws_bytes);
+  char* part = static_cast<char*>(npan > 1 ? ar.take(ex * (size_t)l * m) : nullptr);
+  skel_status st;
+  if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
+  return stream_panels(m, n, ea, A, lda, lds, w, stage, stream,
+                       [&](int64_t i, const char* panel_a, int64_t j0, int64_t wi) -> skel_status {
+    // X(:, j0 : j0 + wi) = Gamma A(:, panel)   (Algorithm 3 line 2, row sketch)
+    size_t sz = xws_bytes;
+    SK_TRY(skel_sketch_rows(0, m, wi, a_dtype, panel_a, lds, l, SKEL_SKETCH_GAUSSIAN, 0, prec, seed_gamma,
+                            static_cast<char*>(X) + ex * j0, ldx, xws, &sz, dev_status, stream));
+    // Y^T += Omega(:, panel) A(:, panel)^T   (Algorithm 3 line 2, column sketch): the first
+    // panel writes Y^T, later ones a partial that is added to it
+    void* out = i == 0 ? Yt : part;
+    const int64_t ldo = i == 0 ? ldy : m;
+    if (tc) {
+      SK_CUDA(launch_transpose_f32(m, wi, reinterpret_cast<const float*>(panel_a), lds, At, w4, stream));
+      const cudaError_t e = launch_sketch_tc(j0, wi, m, At, w4, l, prec, seed_omega, static_cast<float*>(out), ldo,
+                                             yws, dev_status, stream);
+      if (e == cudaErrorNotSupported) return SKEL_ERR_UNSUPPORTED;
+      SK_CUDA(e);
+    } else {
+      GemmArgs a{};
+      a.M = l; a.N = m; a.K = wi;
+      a.B = View{panel_a, lds, 1}; a.b_dt = a_dtype;      // B(k, c) = A(c, j0 + k)
+      a.out = out; a.out_sr = ldo; a.out_sc = 1; a.out_dt = x_dt;
+      a.alpha = 1.0 / std::sqrt((double)l);
+      a.seed = seed_omega;
+      a.gcol0 = j0;
+      a.dev_status = dev_status;
+      a.splitk_ws = yws;
+      SK_CUDA(launch_gemm(a, f64, LEFT_GAUSSIAN, EPI_SKETCH, stream));
+    }
+    if (i > 0) {
+      if (f64)
+        SK_CUDA(launch_axpy_rows_f64(l, m, reinterpret_cast<const double*>(part), m, static_cast<double*>(Yt), ldy,
+                                     stream));
+      else
+        SK_CUDA(launch_axpy_rows_f32(l, m, reinterpret_cast<const float*>(part), m, static_cast<float*>(Yt), ldy,
+                                     stream));
+    }
+    return SKEL_OK;
+  });
 }
 
 skel_status skel_sketch_cols(int64_t m, int64_t n, skel_dtype a_dtype, const void* A, int64_t lda, int32_t l,

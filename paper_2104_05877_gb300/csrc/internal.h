@@ -105,8 +105,10 @@ cudaError_t launch_trsm_upper_ff(int32_t s, int64_t N, const double* R, int64_t 
 // through U = J R^T J (s x s scratch) and the upper solve on the rows in reverse order.
 cudaError_t launch_trsm_upper_t(int32_t s, int64_t N, const double* R, int64_t ldr, double* U, double* D,
                                 int64_t ldd, cudaStream_t st);
-// Z += X for s x n row-major FP64 matrices.
+// Z += X for s x n row-major FP64 (FP32) matrices.
 cudaError_t launch_axpy_rows_f64(int32_t s, int64_t n, const double* X, int64_t ldx, double* Z, int64_t ldz,
+                                 cudaStream_t st);
+cudaError_t launch_axpy_rows_f32(int32_t s, int64_t n, const float* X, int64_t ldx, float* Z, int64_t ldz,
                                  cudaStream_t st);
 // out = C^T B (s x n row-major FP64, ldo) for FP32 column-major C (m x s) and B (m x n): exact
 // products, float-float sums (~44 bits); workspace gemm_tn_ff_workspace bytes.

@@ -393,12 +393,24 @@ __global__ void flip_transpose_kernel(int s, const double* R, int64_t ldr, doubl
   }
 }
 
-__global__ void axpy_rows_kernel(int s, int64_t n, const double* X, int64_t ldx, double* Z, int64_t ldz) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)s * n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / n, c = e % n;
-    Z[r * ldz + c] += X[r * ldx + c];
+// Z(r, :) += X(r, :) for the rows r = blockIdx.y (+ gridDim.y ...), coalesced along each row.
+template <typename T>
+__global__ void axpy_rows_kernel(int s, int64_t n, const T* X, int64_t ldx, T* Z, int64_t ldz) {
+  for (int64_t r = blockIdx.y; r < s; r += gridDim.y) {
+    const T* x = X + r * ldx;
+    T* z = Z + r * ldz;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+      z[c] += x[c];
   }
+}
+
+template <typename T>
+cudaError_t launch_axpy_rows_t(int32_t s, int64_t n, const T* X, int64_t ldx, T* Z, int64_t ldz, cudaStream_t st) {
+  if (s <= 0 || n <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)std::min<int64_t>((n + 1023) / 1024, 64), (unsigned)std::min<int32_t>(s, 65535));
+  axpy_rows_kernel<T><<<grid, 256, 0, st>>>(s, n, X, ldx, Z, ldz);
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_trsm_upper_t(int32_t s, int64_t N, const double* R, int64_t ldr, double* U, double* D,
@@ -415,11 +427,12 @@ cudaError_t launch_trsm_upper_t(int32_t s, int64_t N, const double* R, int64_t l
 
 cudaError_t launch_axpy_rows_f64(int32_t s, int64_t n, const double* X, int64_t ldx, double* Z, int64_t ldz,
                                  cudaStream_t st) {
-  if (s <= 0 || n <= 0) return cudaSuccess;
-  axpy_rows_kernel<<<(unsigned)std::min<int64_t>(((int64_t)s * n + 255) / 256, 4096), 256, 0, st>>>(s, n, X, ldx, Z,
-                                                                                                   ldz);
-  note_launches(1);
-  return cudaGetLastError();
+  return launch_axpy_rows_t<double>(s, n, X, ldx, Z, ldz, st);
+}
+
+cudaError_t launch_axpy_rows_f32(int32_t s, int64_t n, const float* X, int64_t ldx, float* Z, int64_t ldz,
+                                 cudaStream_t st) {
+  return launch_axpy_rows_t<float>(s, n, X, ldx, Z, ldz, st);
 }
 
 cudaError_t launch_trsm_upper(int32_t s, int64_t N, const double* R, int64_t ldr, int unit_diag,

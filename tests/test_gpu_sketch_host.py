@@ -121,3 +121,62 @@ def test_sketch_host_then_pivots(skel, dev):
     skel.check_status(st)
     skel.check_status(std)
     assert torch.equal(J.cpu(), Jd.cpu())
+
+
+def _col_mag(l, n, seed, Ad):
+    return (np.abs(embedding.gaussian_normals(l, n, seed)) @ np.abs(Ad).T) / np.sqrt(l)
+
+
+@pytest.mark.parametrize("prec,m,n,l,panel", [("f64", 700, 1300, 37, 256), ("f64", 700, 1301, 37, 0),
+                                              ("f32", 777, 900, 40, 300), ("tf32", 1001, 2000, 61, 512),
+                                              ("tf32", 2048, 1536, 130, 4), ("bf16", 1001, 1000, 61, 768)])
+def test_two_sided_single_pass(skel, dev, prec, m, n, l, panel):
+    """Both sketches of Algorithm 3 from one pass over a host A: X against the oracle's row
+    sketch and Yt against its column sketch, each within the precision's bound, and both
+    against the device calls on the same A (only the order of the sums differs; Yt adds one
+    partial per panel)."""
+    dt = np.float64 if prec == "f64" else np.float32
+    A = np.asfortranarray(np.random.default_rng(m + n).standard_normal((m, n)).astype(dt))
+    X, Yt, st = skel.sketch_host_two_sided(torch.from_numpy(A), l, prec=prec, seed=7, seed_omega=8, panel=panel)
+    Ad_dev = torch.from_numpy(A).to(dev)
+    Xd, _ = skel.sketch(Ad_dev, l, prec=prec, seed=7, status=st)
+    Ytd, _ = skel.sketch_cols(Ad_dev, l, prec=prec, seed=8, status=st)
+    skel.check_status(st)
+    Ad = A.astype(np.float64)
+    u = 2.0 ** -52 if prec == "f64" else 2.0 ** -23
+    op = {"f64": 0.0, "f32": 0.0, "tf32": 2.0 ** -9, "bf16": 2.0 ** -7}[prec]
+    mx, my = _mag(l, m, 7, Ad), _col_mag(l, n, 8, Ad)
+    gx, gy = X.cpu().numpy(), Yt.cpu().numpy()
+    assert np.all(np.abs(gx - sketch.gaussian_sketch(Ad, l, 7)) <= (op + 2 * m * u) * mx + 1e-300)
+    assert np.all(np.abs(gy - sketch.gaussian_col_sketch(Ad, l, 8)) <= (op + 2 * n * u) * my + 1e-300)
+    assert np.all(np.abs(gx - Xd.cpu().numpy()) <= 4 * m * u * mx + 1e-300)
+    assert np.all(np.abs(gy - Ytd.cpu().numpy()) <= 4 * n * u * my + 1e-300)
+
+
+def test_streaming_selection_host_one_pass(skel, dev):
+    """Algorithm 3 on a host A in one pass: the same row and column skeletons as the oracle's
+    in FP64 before the first near-tie (the oracle forms both sketches from the whole A)."""
+    from oracle import skeleton
+    A = np.asfortranarray(workloads.dense_config2(600, 500, seed=5, dtype=np.float64))
+    k, p = 30, 10
+    Js, Is, st = skel.skeletonize_streaming_host(torch.from_numpy(A), k, p, seed=7, seed_omega=8, prec="f64",
+                                                 panel=128)
+    skel.check_status(st)
+    ref = skeleton.streaming_skeletonize(A, k, p, 7, 8)
+    for got, want, gaps in ((Js, ref["Js"], ref["gaps_x"]), (Is, ref["Is"], ref["gaps_y"])):
+        small = np.flatnonzero(gaps < 1e-9)
+        pre = int(small[0]) if small.size else k
+        assert np.array_equal(got.cpu().numpy()[:pre], want[:pre])
+
+
+def test_two_sided_argument_errors(skel, dev):
+    A = torch.zeros(64, 64, dtype=torch.float32)
+    for kw, code in (({"panel": 6}, 1), ({"panel": -4}, 1), ({"prec": "fp8"}, 7)):
+        args = {"prec": "tf32", "panel": 0}
+        args.update(kw)
+        with pytest.raises(skel.SkelError) as e:
+            skel.sketch_host_two_sided(A, 8, **args)
+        assert e.value.code == code
+    with pytest.raises(skel.SkelError) as e:     # FP64 arithmetic needs FP64 storage
+        skel.sketch_host_two_sided(A, 8, prec="f64")
+    assert e.value.code == 1
