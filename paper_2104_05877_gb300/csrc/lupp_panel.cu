@@ -52,7 +52,6 @@ struct PanelParams {
   int trows;           // trailing rows it covers (s - t0 - b by default)
   int epi_rows;        // rows t0+b .. whose multipliers the panel kernel's epilogue forms
   unsigned char sel_tag;    // sel value of columns this panel selects: panel index + 1
-  unsigned char sel_limit;  // trailing update skips columns with 0 < sel <= sel_limit
 };
 
 // Per-step exchange.  Every CTA sends every CTA of the cluster (itself included) its step-q
@@ -510,8 +509,8 @@ __global__ void __launch_bounds__(kTrailThreads) lupp_trail_kernel(const PanelPa
   __syncthreads();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= p.n) return;
-  const unsigned char sj = p.sel[j];
-  if (sj != 0 && sj <= p.sel_limit) return;              // selected by this panel or an earlier one
+  // columns selected by this or an earlier panel are updated too, as in the tiled kernel: their
+  // trailing entries are never read again
   T* x = p.Xg + (p.trow0 + r0) * p.n + j;
   T v[kTrailRows];
 #pragma unroll
@@ -1190,8 +1189,7 @@ skel_status run_panel_t(const PanelPlan& pl, const T* X, int64_t n, int64_t ldx,
   for (int t0 = 0, k = 0; t0 < s; t0 += pl.b, ++k) {
     p.t0 = t0;
     p.b = std::min(pl.b, s - t0);
-    p.sel_tag = (unsigned char)(k + 1);
-    p.sel_limit = p.sel_tag;               // the bulk runs while the next panel tags its columns
+    p.sel_tag = (unsigned char)(1 + k % 255);   // never 0: 0 marks an unselected column
     p.ldm = p.b;
     p.trow0 = t0 + p.b;
     p.trows = 0;
@@ -1267,7 +1265,6 @@ skel_status run_skeleton_t(const PanelPlan& pc, const PanelPlan& pr, const T* X,
   }
   c.n = n; c.s = s; c.ncl = pc.ncl; c.Js = Js; c.R = R; c.ldr = ldr; c.L = L; c.ldl = ldl;
   c.dev_status = dev_status;
-  c.sel_limit = 255;
   // row chain parameters
   base = static_cast<char*>(wsr);
   PanelParams<T> r{};
@@ -1281,7 +1278,6 @@ skel_status run_skeleton_t(const PanelPlan& pc, const PanelPlan& pr, const T* X,
   r.ldr = m;
   r.n = m; r.ncl = pr.ncl; r.Js = Is; r.L = nullptr; r.ldl = 0; r.M = nullptr;
   r.dev_status = dev_status;
-  r.sel_limit = 255;
 
   const size_t smem = std::max(pc.smem, pr.smem);
   if (cudaFuncSetAttribute(lupp_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -1300,7 +1296,7 @@ skel_status run_skeleton_t(const PanelPlan& pc, const PanelPlan& pr, const T* X,
   for (int t0 = 0; t0 < s; t0 += pc.b, ++k) {
     c.t0 = t0;
     c.b = std::min(pc.b, s - t0);
-    c.sel_tag = (unsigned char)(k + 1);
+    c.sel_tag = (unsigned char)(1 + k % 255);   // never 0: 0 marks an unselected column
     c.ldm = c.b;
     c.trow0 = t0 + c.b;
     c.trows = s - t0 - c.b;
@@ -1318,7 +1314,7 @@ skel_status run_skeleton_t(const PanelPlan& pc, const PanelPlan& pr, const T* X,
     r.b = std::min(pr.b, s - t0);
     r.s = t0 + r.b;                       // no rows below: the epilogue forms no multipliers
     r.epi_rows = 0;
-    r.sel_tag = (unsigned char)(k + 1);
+    r.sel_tag = (unsigned char)(1 + k % 255);   // never 0: 0 marks an unselected column
     if (cudaStreamWaitEvent(aux->st, aux->col[(t0 + r.b - 1) / pc.b], 0) != cudaSuccess) return SKEL_ERR_CUDA;
     lupp_gather_panel_kernel<T><<<dim3((unsigned)std::min<int64_t>((m + 255) / 256, 32), (unsigned)r.b), 256, 0, aux->st>>>(
         A, lda, m, n, Js, t0, r.b, r.Xg, r.fail);
@@ -1503,7 +1499,7 @@ skel_status run_gpanel_t(const GPanelPlan& pl, const T* X, int64_t n, int64_t ld
     note_launches(1);
     PanelParams<T> tp{};
     tp.Xg = Xg; tp.n = n; tp.s = s; tp.t0 = t0; tp.b = bb; tp.R = R; tp.ldr = ldr; tp.fail = fail;
-    tp.M = M; tp.ldm = bb; tp.trow0 = t0 + bb; tp.trows = trows; tp.sel = sel; tp.sel_limit = 255;
+    tp.M = M; tp.ldm = bb; tp.trow0 = t0 + bb; tp.trows = trows; tp.sel = sel;
     if (launch_trail<T>(tp, trows, st) != cudaSuccess) return SKEL_ERR_CUDA;
   }
   return cudaGetLastError() == cudaSuccess ? SKEL_OK : SKEL_ERR_CUDA;
