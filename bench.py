@@ -658,9 +658,12 @@ def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
         "roofline": roofline, "kernels": kernels, "serialised_ms_per_step": ser_ms / nser,
         "measured_floors": floors,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(4 * m * n), "d2h_bytes_per_step": int(4 * k),
-                "steps": e_steps, "skeleton_overlap_vs_device_sketch": e2e_overlap, "step_ms": e2e_steps_ms, "clock": "host wall",
-                "median_ms": statistics.median(e2e_steps_ms), "h2d_copy_alone_ms": h2d_ms,
+        # the host link is shared with other tenants of the machine: single steps were seen at
+        # 6x the rest, so the value is the median step, with the mean and every step beside it
+        "e2e": {"value": statistics.median(e2e_steps_ms), "unit": "ms", "h2d_bytes_per_step": int(4 * m * n),
+                "d2h_bytes_per_step": int(4 * k), "steps": e_steps, "statistic": "median of the steps",
+                "mean_ms": e2e_ms, "skeleton_overlap_vs_device_sketch": e2e_overlap, "step_ms": e2e_steps_ms,
+                "clock": "host wall", "h2d_copy_alone_ms": h2d_ms,
                 "h2d_gbs": 4.0 * m * n / (h2d_ms * 1e-3) / 1e9,
                 "what": "pinned host A streamed in column panels through skel_sketch_host (copies overlapped "
                         "with the sketch), LUPP, J_s copied back"},
