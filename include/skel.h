@@ -7,13 +7,13 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  *  - Every matrix pointer is a DEVICE pointer owned by the caller (the A of skel_sketch_host and
- *    skel_sketch_host_two_sided is a host pointer); the library never frees or retains it.  Only the two batch plan constructors allocate device memory (the plan's own, freed
- *    by skel_batch_plan_destroy); every other call that needs scratch memory takes a
+ *    skel_sketch_host_two_sided is a host pointer); the library never frees or retains it.
+ *    Only the two batch plan constructors allocate device memory (the plan's own, freed by
+ *    skel_batch_plan_destroy); every other call that needs scratch memory takes a
  *    caller-provided device workspace `ws` of `*ws_bytes` bytes (skel_pivot_lupp_static uses a
- *    fixed array inside the library instead).  Calling with
- *    ws == NULL writes the required size to *ws_bytes and returns SKEL_OK without launching
- *    anything.  A workspace smaller than required returns SKEL_ERR_WORKSPACE.  Workspace
- *    must be 256-byte aligned.
+ *    fixed array inside the library instead).  Calling with ws == NULL writes the required
+ *    size to *ws_bytes and returns SKEL_OK without launching anything.  A workspace smaller
+ *    than required returns SKEL_ERR_WORKSPACE.  Workspace must be 256-byte aligned.
  *  - Tall matrices (A, C, Q: m rows) are COLUMN-MAJOR: element (i, j) at p[i + j*ld], ld >= m.
  *    Wide matrices (the sketch X, pivot factors R, the ID matrix Z: l or s rows, n columns)
  *    are ROW-MAJOR: element (r, j) at p[r*ld + j], ld >= n.  (So X^T is column-major n x l.)

@@ -88,6 +88,36 @@ def test_invalid_arguments_rejected_on_host(L):
                                   10, None, ctypes.byref(sz), None, None) == 1
 
 
+def test_host_sketch_arguments_and_workspace(L):
+    """The host-A sketches check their arguments on the host before any device call, and the
+    streaming sketch's workspace is two staging panels (columns padded to a multiple of 4 rows)
+    plus the per-panel sketch's workspace (none for the FP64 Gaussian sketch)."""
+    sz = ctypes.c_size_t(0)
+    A, X = ctypes.c_void_p(16), ctypes.c_void_p(16)
+    # skel_sketch_host: negative panel, lda < m, an unknown storage type
+    assert L.skel_sketch_host(10, 10, 0, A, 10, 4, 0, 8, 0, 1, X, 10, -1, None, ctypes.byref(sz), None, None) == 1
+    assert L.skel_sketch_host(10, 10, 0, A, 9, 4, 0, 8, 0, 1, X, 10, 0, None, ctypes.byref(sz), None, None) == 1
+    assert L.skel_sketch_host(10, 10, 7, A, 10, 4, 0, 8, 0, 1, X, 10, 0, None, ctypes.byref(sz), None, None) == 1
+    # m = 10, n = 10 in panels of 4 columns: three panels, two staging buffers of 12 x 4 doubles
+    assert L.skel_sketch_host(10, 10, 0, A, 10, 4, 0, 8, 0, 1, X, 10, 4, None, ctypes.byref(sz), None, None) == 0
+    assert sz.value == 2 * 512
+    # one panel: one staging buffer
+    assert L.skel_sketch_host(10, 10, 0, A, 10, 4, 0, 8, 0, 1, X, 10, 0, None, ctypes.byref(sz), None, None) == 0
+    assert sz.value == 1024
+    # skel_sketch_host_two_sided: a panel not a multiple of 4, negative; FP64 arithmetic on FP32
+    # storage; m = 0; FP8
+    Y = ctypes.c_void_p(16)
+    for panel in (6, -4):
+        assert L.skel_sketch_host_two_sided(10, 10, 1, A, 10, 4, 2, 1, 2, X, 10, Y, 10, panel, None,
+                                            ctypes.byref(sz), None, None) == 1
+    assert L.skel_sketch_host_two_sided(10, 10, 1, A, 10, 4, 0, 1, 2, X, 10, Y, 10, 0, None,
+                                        ctypes.byref(sz), None, None) == 1
+    assert L.skel_sketch_host_two_sided(0, 10, 1, A, 10, 4, 2, 1, 2, X, 10, Y, 10, 0, None,
+                                        ctypes.byref(sz), None, None) == 1
+    assert L.skel_sketch_host_two_sided(10, 10, 1, A, 10, 4, 4, 1, 2, X, 10, Y, 10, 0, None,
+                                        ctypes.byref(sz), None, None) == 7
+
+
 def test_workspace_query_gaussian_needs_none(L):
     sz = ctypes.c_size_t(123)
     assert L.skel_sketch(100, 50, 0, ctypes.c_void_p(16), 100, 8, 0, 8, 0, 1, ctypes.c_void_p(16), 50,
