@@ -446,14 +446,8 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-// The per-step decision, taken by one thread and read by all after a CTA barrier.  Sums of
-// squares have no cancellation, so FP32 carries them; the rule is tested without a division:
-//   nu_t l <= tol^2 ||X||^2 (l - t).
-struct BlDecision {
-  float normX2;
-  int stop, bi, o, code;
-};
-
+// The stopping rule is tested without a division: nu_t l <= tol^2 ||X||^2 (l - t).  Sums of
+// squares have no cancellation, so FP32 carries them.
 __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLuppParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ BlSlot slot[2][BL_MAXCL];
@@ -462,8 +456,6 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
   __shared__ float wkey[BL_THREADS / 32];
   __shared__ int widx[BL_THREADS / 32];
   __shared__ float wnu[BL_THREADS / 32];
-  __shared__ float s_nu;
-  __shared__ BlDecision s_dec;
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks(), crank = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -478,17 +470,6 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
   unsigned char* sel = reinterpret_cast<unsigned char*>(S + (size_t)l * ldp);        // [ncl]
   const float* xb = p.X + blk.xoff;
 
-  auto block_sum = [&](float v) {            // in fixed order; result in s_nu
-    v = warp_sum(v);
-    if (lane == 0) wnu[warp] = v;
-    __syncthreads();
-    if (tid == 0) {
-      float a = 0.f;
-      for (int w = 0; w < BL_THREADS / 32; ++w) a += wnu[w];
-      s_nu = a;
-    }
-    __syncthreads();
-  };
 
   // The block's X is scaled by the power of two that brings its largest magnitude into
   // [1, 2): exact in FP32, so pivots and ranks do not change, but the squares of Schur
@@ -525,18 +506,23 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
   float amax = 0.f;
   for (int d = 0; d < CL; ++d) amax = fmaxf(amax, s_amax[d]);
   const float sc = amax > 0.f && amax < INFINITY ? ldexpf(1.f, -ilogbf(amax)) : 1.f;
-  // sums of squares: FP32 per thread (a few hundred terms), FP64 across threads (FP64
-  // arithmetic is scarce on this GPU and these run once per element per step)
-  float nu = 0.f;
+  // Sums of squares: FP32 per thread over its entries, then warp sums and the warps' sum in a
+  // fixed order.  A thread's partial for step t is over the entries it updated at step t-1
+  // (all its entries at t = 0), so ||S_t||^2 rides with step t's candidate reduction.
+  float nuloc = 0.f;
   for (int e = tid; e < l * nl; e += BL_THREADS) {
     const int r = e / nl, jl = e % nl;
     const float v = S[r * ldp + jl] * sc;
     S[r * ldp + jl] = v;
-    nu = fmaf(v, v, nu);
+    nuloc = fmaf(v, v, nuloc);
   }
-  block_sum(nu);
+  __syncthreads();
 
+  // Per step one CTA barrier (the candidates and sums of squares of the warps) and one
+  // cluster barrier (the CTAs' candidates); every thread then takes the same decision from
+  // the same slots in the same order.
   int rank = 0, code = 0;
+  float normX2 = 0.f;
   for (int t = 0;; ++t) {
     // this CTA's candidate on row t: largest magnitude, ties to the lower column index
     float key = -1.f;
@@ -547,11 +533,18 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
       const float k = a == a ? a : INFINITY;     // NaN is flagged as non-finite below
       if (k > key) { key = k; idx = c0 + jl; }
     }
+    const int par = t & 1;
+    float nu_cta;
     {
       const unsigned kb = key >= 0.f ? __float_as_uint(key) : 0u;
       const unsigned m = __reduce_max_sync(0xffffffffu, kb);
       const unsigned im = __reduce_min_sync(0xffffffffu, kb == m && key >= 0.f ? (unsigned)idx : 0x7fffffffu);
-      if (lane == 0) { wkey[warp] = im == 0x7fffffffu ? -1.f : __uint_as_float(m); widx[warp] = (int)im; }
+      const float nw_ = warp_sum(nuloc);
+      if (lane == 0) {
+        wkey[warp] = im == 0x7fffffffu ? -1.f : __uint_as_float(m);
+        widx[warp] = (int)im;
+        wnu[warp] = nw_;
+      }
       __syncthreads();
       float k2 = lane < BL_THREADS / 32 ? wkey[lane] : -1.f;
       int i2 = lane < BL_THREADS / 32 ? widx[lane] : 0x7fffffff;
@@ -560,50 +553,49 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
       const unsigned im2 = __reduce_min_sync(0xffffffffu, kb2 == m2 && k2 >= 0.f ? (unsigned)i2 : 0x7fffffffu);
       key = im2 == 0x7fffffffu ? -1.f : __uint_as_float(m2);
       idx = im2 == 0x7fffffffu ? INT_MAX : (int)im2;
+      float a = 0.f;
+      for (int w = 0; w < BL_THREADS / 32; ++w) a += wnu[w];
+      nu_cta = a;
     }
     // send it (with its whole column and this CTA's sum of squares) to every CTA
-    const int par = t & 1;
     const bool have = idx != INT_MAX;
     for (int d = 0; d < CL; ++d) {
       BlSlot* dst = cluster.map_shared_rank(&slot[par][crank], d);
       for (int r = tid; r < l; r += BL_THREADS) dst->col[r] = have ? S[r * ldp + (idx - c0)] : 0.f;
       if (tid == 0) {
-        dst->nu = s_nu;
+        dst->nu = nu_cta;
         dst->key = key;
         dst->idx = idx;
       }
     }
     cluster.sync();
-    // the same decision in every CTA (the same inputs, summed in CTA order)
-    if (tid == 0) {
-      float nut = 0.f;
-      for (int d = 0; d < CL; ++d) nut += slot[par][d].nu;
-      if (t == 0) s_dec.normX2 = nut;
-      float bk = -1.f;
-      int bi = INT_MAX, o = 0;
-      for (int d = 0; d < CL; ++d) {
-        const float k = slot[par][d].key;
-        const int i = slot[par][d].idx;
-        if (i != INT_MAX && (k > bk || (k == bk && i < bi))) { bk = k; bi = i; o = d; }
-      }
-      s_dec.stop = nut * (float)l <= p.tol2 * s_dec.normX2 * (float)(l - t) || t >= kmax || bi == INT_MAX ||
-                   !(bk > 0.f) || !isfinite(bk);
-      s_dec.code = bi != INT_MAX && !isfinite(bk) ? SKEL_ERR_NONFINITE : 0;
-      s_dec.bi = bi;
-      s_dec.o = o;
+    // the same decision in every thread of every CTA (the same inputs, summed in CTA order)
+    float nut = 0.f;
+    for (int d = 0; d < CL; ++d) nut += slot[par][d].nu;
+    if (t == 0) normX2 = nut;
+    float bk = -1.f;
+    int bi = INT_MAX, o = 0;
+    for (int d = 0; d < CL; ++d) {
+      const float k = slot[par][d].key;
+      const int i = slot[par][d].idx;
+      if (i != INT_MAX && (k > bk || (k == bk && i < bi))) { bk = k; bi = i; o = d; }
     }
-    __syncthreads();
-    const int bi = s_dec.bi, o = s_dec.o;
-    if (s_dec.stop) {
+    const bool stop = nut * (float)l <= p.tol2 * normX2 * (float)(l - t) || t >= kmax || bi == INT_MAX ||
+                      !(bk > 0.f) || !isfinite(bk);
+    if (stop) {
       rank = t;
-      code = s_dec.code;
+      code = bi != INT_MAX && !isfinite(bk) ? SKEL_ERR_NONFINITE : 0;
       break;
     }
     const float* pc = slot[par][o].col;
     const float piv = pc[t];
     if (tid == 0) s_J[t] = bi;
+    // The pivot column leaves the candidates: the thread that scans it marks it (its entries
+    // below row t would become exact zeros and are not read again, so whether an updating
+    // thread still sees it unmarked changes nothing).
+    if (o == crank && (bi - c0) % BL_THREADS == tid) sel[bi - c0] = 1;
     // rows t+1 .. l-1 of the local columns: S(r, j) -= S(r, j_t) S(t, j) / pivot
-    float nuloc = 0.f;
+    nuloc = 0.f;
     if (nl > 0) {
       const int nph = max(1, BL_THREADS / nl);           // threads per column (rows split)
       for (int e = tid; e < nph * nl; e += BL_THREADS) {
@@ -630,9 +622,6 @@ __global__ void __launch_bounds__(BL_THREADS, 1) batch_lupp_kernel(const BatchLu
         }
       }
     }
-    block_sum(nuloc);
-    if (o == crank && tid == 0) sel[bi - c0] = 1;
-    __syncthreads();
   }
   if (crank == 0) {
     for (int q = tid; q < kmax; q += BL_THREADS) p.Js[(int64_t)b * kmax + q] = q < rank ? s_J[q] : -1;
