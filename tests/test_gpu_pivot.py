@@ -259,3 +259,34 @@ def test_pivot_skeleton_rank_deficient(skel, dev):
     J, I = Js.cpu().numpy(), Is.cpu().numpy()
     assert list(J[:2]) == [7, 9] and np.all(J[2:] == -1)
     assert np.all(I == -1)
+
+
+def test_sketch_and_lupp_capture_into_a_cuda_graph(skel, dev):
+    """The sketch and the look-ahead LUPP (two library streams forked from and joined back into
+    the caller's) capture into a CUDA graph; replays give the eager call's pivots and factors."""
+    m, n, l, k = 4096, 8192, 272, 256
+    A = torch.randn(n, m, device=dev, generator=torch.Generator(device=dev).manual_seed(3)).t()
+    X = torch.empty(l, n, device=dev)
+    st = skel.new_status(dev)
+
+    def step():
+        skel.sketch(A, l, prec="tf32", seed=3, X=X, status=st)
+        return skel.pivot_lupp(X, k, factors=True, status=st)
+
+    J0, _, R0, _ = step()
+    J0, R0 = J0.clone(), R0.clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        step()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            out = step()
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    skel.check_status(st)
+    assert torch.equal(out[0], J0)
+    assert torch.equal(out[2], R0)
