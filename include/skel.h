@@ -137,8 +137,8 @@ skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dt
  *               (pinned) memory gives asynchronous copies that overlap the sketch; pageable
  *               memory is accepted, and the driver then stages each panel copy through the
  *               host, which may block the calling thread.
- *   panel     : columns per panel; 0 chooses about 512 MiB of A per panel, a multiple of 256
- *               columns.
+ *   panel     : columns per panel; 0 chooses about 512 MiB of A per panel (a multiple of 256
+ *               columns, of 4 when columns are taller than 2 MiB, at least one column).
  *   every other argument is skel_sketch's; the tensor-core precisions need no alignment of the
  *               host A (the staging columns are padded to 16 bytes).
  * X equals skel_sketch of the same A on the device up to the summation order of the K-split

@@ -245,11 +245,12 @@ struct HostStreamJoin {
   }
 };
 
-// Columns per panel: the caller's choice, else about 512 MiB of A in multiples of 256 columns.
+// Columns per panel: the caller's choice, else about 512 MiB of A: a multiple of 256 columns,
+// of 4 for taller columns, and at least one column.
 int64_t host_panel_cols(int64_t m, int64_t n, skel_dtype dt, int64_t panel) {
   if (panel > 0) return std::min(panel, n);
   int64_t w = ((int64_t)512 << 20) / std::max<int64_t>(1, (int64_t)esize(dt) * m);
-  w = std::max<int64_t>(256, w / 256 * 256);
+  w = w >= 256 ? w / 256 * 256 : w >= 4 ? w / 4 * 4 : std::max<int64_t>(1, w);
   return std::min(w, n);
 }
 
