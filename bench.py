@@ -5,7 +5,8 @@ Headline workload (the largest single-GPU configuration; one "step" = the whole 
 one synthetic matrix resident in HBM):
   A: 65536 x 32768 FP32 (8.6 GB), A = U diag(sigma) V^T + 1e-7 floor, sigma_j = exp(-j/200),
      Haar U, V; k = 1024, oversampling p = 76 (l = 1100), Gaussian embedding.
-  step = tensor-core sketch X = Gamma A (--prec, TF32 by default)  ->  LUPP on X (J_s, R^LU)
+  step = tensor-core sketch X = Gamma A (--prec, FP8 by default: e4m3 operands with one power-
+         of-two scale per column of A, FP32 accumulation)  ->  LUPP on X (J_s, R^LU)
          [time-to-skeleton, the metric]  ->  column ID Z = C^+ A (Householder QR of C = A(:, J_s),
          W = Q_C^T A, FP64 solve)  [time to ID]  ->  Theorem 1's eta from R^LU.
 Reported beside it: time-to-skeleton in every sketch precision (TF32, BF16, FP8) and in the
@@ -58,7 +59,7 @@ def parse():
     ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS))
     ap.add_argument("--k", type=int, default=None, help="rank (default: the workload's)")
     ap.add_argument("--p", type=int, default=None, help="oversampling (default: the workload's)")
-    ap.add_argument("--prec", default="tf32", choices=["tf32", "bf16", "fp8", "f32"])
+    ap.add_argument("--prec", default="fp8", choices=["tf32", "bf16", "fp8", "f32"])
     ap.add_argument("--blocks", type=int, default=4096, help="blocks of the batched run (--only batch)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain-GPU comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
@@ -607,12 +608,13 @@ def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
     h2d_ms = e0.elapsed_time(e1) / 3
 
     # Algorithm 3 on the host A in one pass: both sketches from the same streamed panels, the
-    # two LUPPs, both skeletons read on the host every step
+    # two LUPPs, both skeletons read on the host every step (the one-pass sketches have no FP8 form)
     Is_h = torch.empty(k, dtype=torch.int32, pin_memory=True)
+    stream_prec = prec if prec in ("tf32", "bf16", "f32") else "tf32"
 
     def stream_step():
         Jx, Iy, _ = skel.skeletonize_streaming_host(A_host.t(), k, p, seed=seed_G, seed_omega=seed_G + 1,
-                                                    prec=prec, status=st)
+                                                    prec=stream_prec, status=st)
         Js_h.copy_(Jx, non_blocking=True)
         Is_h.copy_(Iy, non_blocking=True)
         main.synchronize()
@@ -622,7 +624,7 @@ def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
     stream_ms, stream_steps_ms = wall_steps(stream_step, 3)
     skel.check_status(st, "streaming selection")
     streaming = {"ms": stream_ms, "step_ms": stream_steps_ms, "median_ms": statistics.median(stream_steps_ms),
-                 "clock": "host wall", "prec": prec,
+                 "clock": "host wall", "prec": stream_prec,
                  "h2d_bytes_per_step": int(4 * m * n), "passes_over_A": 1,
                  "what": "Algorithm 3 on the pinned host A: X = Gamma A and Y^T = Omega A^T from one streamed "
                          "pass (skel_sketch_host_two_sided), LUPP on X and on Y^T, J_s and I_s read back",

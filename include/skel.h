@@ -60,8 +60,8 @@ typedef enum {
   SKEL_PREC_F32 = 1,  /* FP32 operands and accumulation (SIMT FFMA)                       */
   SKEL_PREC_TF32 = 2, /* tensor cores (tcgen05 kind::tf32), FP32 accumulate in TMEM       */
   SKEL_PREC_BF16 = 3, /* tensor cores (tcgen05 kind::f16, bf16 operands), FP32 accumulate */
-  SKEL_PREC_FP8 = 4   /* tensor cores (tcgen05 kind::f8f6f4, e4m3 operands; A with a power-of-two
-                         scale per 128 rows of a column), FP32 accumulate                       */
+  SKEL_PREC_FP8 = 4   /* tensor cores (tcgen05 kind::f8f6f4, e4m3 operands; A with one
+                         power-of-two scale per column), FP32 accumulate                        */
 } skel_prec;
 
 /* embedding Gamma (Sec. 2.3) */

@@ -14,8 +14,8 @@ from . import embedding
 def gaussian_sketch(A, l, seed, operand_rounding=None):
     """X = Gamma A with the Gaussian Gamma (l x m) of ``embedding.gaussian_embedding``.
 
-    operand_rounding: None (exact FP64), "fp32", "bf16" or "fp8" (e4m3; A with a power-of-two
-    scale per 128 consecutive rows of each column, the normals unscaled).  When given, the standard normals
+    operand_rounding: None (exact FP64), "fp32", "bf16" or "fp8" (e4m3; A with one power-of-two
+    scale per column, the normals unscaled).  When given, the standard normals
     G and A are each rounded to that format, X = (round(G) @ round(A)) / sqrt(l) in FP64 --
     which is what a kernel multiplying such operands with exact products computes, up to
     its own summation order.
@@ -27,8 +27,9 @@ def gaussian_sketch(A, l, seed, operand_rounding=None):
     elif operand_rounding == "bf16":
         G, A = embedding.round_bf16(G), embedding.round_bf16(A)
     elif operand_rounding == "fp8":
-        # e4m3: the normals as they are (x1), A with a power-of-two scale per 128 rows of a column
-        G, A = embedding.round_e4m3(G), embedding.round_fp8_blocks(A, 128)
+        # e4m3: the normals as they are (x1), A with one power-of-two scale per column (a block
+        # of all its rows)
+        G, A = embedding.round_e4m3(G), embedding.round_fp8_blocks(A, A.shape[0])
     elif operand_rounding is not None:
         raise ValueError(operand_rounding)
     return (G @ A) / np.sqrt(l)

@@ -1,23 +1,22 @@
 // FP8 (e4m3) Gaussian sketch X = Gamma A (Algorithm 2 line 2) on sm_103a tensor cores.
 //
-// Quantisation: every 128 consecutive rows of a column of A share one power-of-two scale,
-// s = 2^ceil(log2(amax / 448)) (the smallest that keeps the block inside e4m3's range), and
-// A8 = e4m3(A / s) rounded to nearest even (the division is exact).  The standard normals
-// are rounded to e4m3 unscaled (|g| < 448).  Products of two e4m3 numbers are exact in FP32.
+// Quantisation: every column of A has one power-of-two scale, s = 2^ceil(log2(amax / 448))
+// (the smallest that keeps the column inside e4m3's range), and A8 = e4m3(A / s) rounded to
+// nearest even (the division is exact).  The standard normals are rounded to e4m3 unscaled
+// (|g| < 448).  Products of two e4m3 numbers are exact in FP32.
 //
 // Kernels:
-//   fp8_quantize_kernel  one warp per (128-row block, column): amax by warp reduction, the
-//                        scale, 128 codes written as 32 words; A is read once.
+//   fp8_quantize_kernel  one CTA per column at a time: amax over the column, the scale, then
+//                        the codes (the column's second read is served from L2: few columns
+//                        are in flight at once).
 //   fp8_gamma_kernel     e4m3 normals G8 (l_pad x m_pad bytes, zero padded), 0.35 l m bytes
 //                        that stay in L2.
 //   sketch_fp8_kernel    one CTA per 128 rows of X x 128 columns of A over an interleaved
 //                        K-split of 128-row blocks: TMA brings the A8 and G8 tiles (128-byte
 //                        swizzle, 128 K-elements per row), tcgen05.mma kind::f8f6f4 (M 128,
-//                        N 128, K 32) accumulates one row block into one of two TMEM buffers,
-//                        and four epilogue warps add s(block, column) x that partial to FP32
-//                        register accumulators (one row of X per thread) while the MMA fills
-//                        the other buffer.  The scale varies with the column, so it cannot
-//                        be applied after an accumulation over several row blocks.
+//                        N 128, K 32) accumulates the CTA's whole K range in one TMEM buffer,
+//                        and four epilogue warps multiply each column by its scale once at
+//                        the end (the scale is constant along K).
 // Every mbarrier wait is bounded (SKEL_ERR_TIMEOUT, then drain and free TMEM).
 #include <cuda.h>
 
@@ -49,29 +48,43 @@ __device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
   return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
-// One warp per (block kb, column j): lane covers rows kb*128 + 4 lane .. +3.
+// One CTA per column j (grid-stride): amax by thread, warp and CTA reductions, the scale S[j],
+// then the codes, thread t covering rows 4t .. 4t+3 of every 4 * blockDim.x.
 __global__ void fp8_quantize_kernel(int64_t m, int64_t n, const float* A, int64_t lda, uint8_t* A8, int64_t ld8,
-                                    float* S, int64_t nkb, int32_t* dev_status) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nkb * n; w += warps) {
-    const int64_t j = w / nkb, kb = w % nkb;
-    const int64_t r = kb * F8_BLOCK + 4 * lane;
-    const float* col = A + j * lda;
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
-    if (r + 3 < m) {
+                                    float* S, int32_t* dev_status) {
+  __shared__ uint32_t wmax[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  auto load4 = [&](const float* col, int64_t r, float (&v)[4]) {
+    if (r >= m) {
+      v[0] = v[1] = v[2] = v[3] = 0.f;
+    } else if (r + 3 < m) {
       const float4 q = *reinterpret_cast<const float4*>(col + r);
       v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
     } else {
-      for (int u = 0; u < 4; ++u)
-        if (r + u < m) v[u] = col[r + u];
+      for (int u = 0; u < 4; ++u) v[u] = r + u < m ? col[r + u] : 0.f;
     }
+  };
+  for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+    const float* col = A + j * lda;
     uint32_t bits = 0;
-    for (int u = 0; u < 4; ++u) bits = max(bits, __float_as_uint(fabsf(v[u])));
+    const int64_t step = 4 * (int64_t)blockDim.x;
+    for (int64_t r0 = 4 * (int64_t)threadIdx.x; r0 < m; r0 += 4 * step) {   // four loads in flight
+      float v[4][4];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) load4(col, r0 + g * step, v[g]);
+#pragma unroll
+      for (int g = 0; g < 4; ++g)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) bits = max(bits, __float_as_uint(fabsf(v[g][u])));
+    }
     bits = __reduce_max_sync(0xffffffffu, bits);
+    if (lane == 0) wmax[warp] = bits;
+    __syncthreads();
+    bits = 0;
+    for (int w = 0; w < nw; ++w) bits = max(bits, wmax[w]);
     float scale = 1.f, inv = 1.f;
     if (bits >= 0x7f800000u) {
-      if (lane == 0) record_error(dev_status, SKEL_ERR_NONFINITE, -1);
+      if (threadIdx.x == 0) record_error(dev_status, SKEL_ERR_NONFINITE, -1);
     } else if (bits != 0u) {
       // amax = f 2^E, f in [0.5, 1): the smallest e with 448 2^e >= amax is E - 9, or E - 8
       // when f > 0.875 (448 = 0.875 2^9)
@@ -81,16 +94,25 @@ __global__ void fp8_quantize_kernel(int64_t m, int64_t n, const float* A, int64_
       scale = ldexpf(1.f, e);
       inv = ldexpf(1.f, -e);
     }
-    if (lane == 0) S[kb * n + j] = scale;
-    if (r < m) {
-      const uint32_t word = e4m3x4(v[0] * inv, v[1] * inv, v[2] * inv, v[3] * inv);
-      uint8_t* dst = A8 + j * ld8 + r;
-      if (r + 3 < m) {
-        *reinterpret_cast<uint32_t*>(dst) = word;
-      } else {
-        for (int u = 0; u < 4 && r + u < m; ++u) dst[u] = (uint8_t)(word >> (8 * u));
+    if (threadIdx.x == 0) S[j] = scale;
+    uint8_t* dst = A8 + j * ld8;
+    for (int64_t r0 = 4 * (int64_t)threadIdx.x; r0 < m; r0 += 4 * step) {
+      float v[4][4];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) load4(col, r0 + g * step, v[g]);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const int64_t r = r0 + g * step;
+        if (r >= m) continue;
+        const uint32_t word = e4m3x4(v[g][0] * inv, v[g][1] * inv, v[g][2] * inv, v[g][3] * inv);
+        if (r + 3 < m) {
+          *reinterpret_cast<uint32_t*>(dst + r) = word;
+        } else {
+          for (int u = 0; u < 4 && r + u < m; ++u) dst[r + u] = (uint8_t)(word >> (8 * u));
+        }
       }
     }
+    __syncthreads();                 // wmax is rewritten for the next column
   }
 }
 
@@ -126,7 +148,7 @@ struct F8Params {
   int64_t m, n;
   int l, P;                 // K-split: CTA z takes the row blocks z, z + P, ...
   int64_t nkb;              // 128-row blocks over m
-  const float* S;           // scales [nkb][n]
+  const float* S;           // column scales [n]
   float* out;               // X (P == 1) or partial buffers [P][l][n]
   int64_t ldo, part_stride;
   float scale;              // 1 / sqrt(l), applied when P == 1
@@ -202,10 +224,10 @@ sketch_fp8_kernel(const __grid_constant__ CUtensorMap tmA8, const __grid_constan
     if (lane == 0) {
       const uint32_t idesc = idesc_e4m3(128, F8_N);
       for (int it = 0; it < nk; ++it) {
-        const int s = it % F8_STAGES, b = it & 1;
-        const uint32_t ph = (uint32_t)(it / F8_STAGES) & 1u, pb = (uint32_t)(it >> 1) & 1u;
+        const int s = it % F8_STAGES;
+        const uint32_t ph = (uint32_t)(it / F8_STAGES) & 1u;
         if (aborted()) break;
-        if (!mbar_wait(full(s), ph, F8_WAIT_NS) || (it >= 2 && !mbar_wait(tempty(b), pb ^ 1u, F8_WAIT_NS))) {
+        if (!mbar_wait(full(s), ph, F8_WAIT_NS)) {
           fail();
           break;
         }
@@ -213,61 +235,45 @@ sketch_fp8_kernel(const __grid_constant__ CUtensorMap tmA8, const __grid_constan
         const uint32_t ga = smem_u32(g_buf(s)), aa = smem_u32(a_buf(s));
 #pragma unroll
         for (int kk = 0; kk < F8_BLOCK / 32; ++kk)      // K = 32 per MMA: 32 bytes of each row
-          mma_f8(tmem + (uint32_t)(b * F8_N), sw128_desc(ga + kk * 32), sw128_desc(aa + kk * 32), idesc,
-                 kk > 0 ? 1u : 0u);
+          mma_f8(tmem, sw128_desc(ga + kk * 32), sw128_desc(aa + kk * 32), idesc, (it > 0 || kk > 0) ? 1u : 0u);
         mma_commit(empty(s));
-        mma_commit(tfull(b));
       }
+      mma_commit(tfull(0));      // arrives once every MMA issued above has completed
     }
   } else if (warp >= 4) {
-    // epilogue warps: row i of X per thread, 128 FP32 accumulators in registers
+    // epilogue warps: row i of X per thread, read from TMEM once the whole K range is in
     const int qd = warp & 3;
     const int64_t i = (int64_t)lb * 128 + qd * 32 + lane;
-    float acc[F8_N];
-#pragma unroll
-    for (int c = 0; c < F8_N; ++c) acc[c] = 0.f;
     bool ok = true;
-    for (int it = 0; it < nk && ok; ++it) {
-      const int b = it & 1;
-      const int64_t kb = (int64_t)kz + (int64_t)it * p.P;
-      float sv[4];                                   // scales of columns 4 lane .. 4 lane + 3
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t jc = j0 + 4 * lane + u;
-        sv[u] = jc < p.n ? p.S[kb * p.n + jc] : 0.f;
-      }
-      if (aborted() || !mbar_wait(tfull(b), (uint32_t)(it >> 1) & 1u, F8_WAIT_NS)) {
-        fail();
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-#pragma unroll
-      for (int c0 = 0; c0 < F8_N; c0 += 32) {
-        uint32_t r[32];
-        TMEM_LD32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * F8_N + c0), r);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int c = c0 + q;
-          const float sc = __shfl_sync(0xffffffffu, sv[c & 3], c >> 2);
-          acc[c] = fmaf(__uint_as_float(r[q]), sc, acc[c]);
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty(b));
+    if (nk > 0 && !mbar_wait(tfull(0), 0u, F8_WAIT_NS)) {
+      fail();
+      ok = false;
     }
-    if (ok && !aborted() && i < p.l) {
+    tc_fence_after();
+    if (ok && !aborted()) {
       float* orow = p.out + (p.direct ? 0 : (int64_t)kz * p.part_stride) + i * p.ldo;
       const float scl = p.direct ? p.scale : 1.f;
       bool bad = false;
 #pragma unroll
-      for (int c = 0; c < F8_N; ++c) {
-        if (j0 + c < p.n) {
-          const float v = acc[c] * scl;
-          bad |= !isfinite(v);
-          orow[j0 + c] = v;
+      for (int c0 = 0; c0 < F8_N; c0 += 32) {
+        uint32_t r[32];
+        if (nk > 0) {
+          TMEM_LD32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)c0, r);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) r[q] = 0u;
+        }
+        if (i < p.l) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const int64_t jc = j0 + c0 + q;
+            if (jc < p.n) {
+              const float v = __uint_as_float(r[q]) * __ldg(p.S + jc) * scl;
+              bad |= !isfinite(v);
+              orow[jc] = v;
+            }
+          }
         }
       }
       if (bad && p.direct) record_error(p.dev_status, SKEL_ERR_NONFINITE, -1);
@@ -320,7 +326,7 @@ F8Plan plan_f8(int64_t m, int64_t n, int l) {
 
 size_t sketch_fp8_workspace(int64_t m, int64_t n, int32_t l) {
   const F8Plan pl = plan_f8(m, n, l);
-  return align_up((size_t)pl.ld8 * n) + align_up(sizeof(float) * (size_t)pl.nkb * n) +
+  return align_up((size_t)pl.ld8 * n) + align_up(sizeof(float) * (size_t)n) +
          align_up((size_t)pl.lp * pl.mg) + (pl.P > 1 ? align_up(sizeof(float) * (size_t)pl.P * l * n) : 0);
 }
 
@@ -336,7 +342,7 @@ cudaError_t launch_sketch_fp8(int64_t row0, int64_t m, int64_t n, const float* A
   uint8_t* A8 = base;
   base += align_up((size_t)pl.ld8 * n);
   float* S = reinterpret_cast<float*>(base);
-  base += align_up(sizeof(float) * (size_t)pl.nkb * n);
+  base += align_up(sizeof(float) * (size_t)n);
   uint8_t* G8 = base;
   base += align_up((size_t)pl.lp * pl.mg);
   float* part = reinterpret_cast<float*>(base);
@@ -364,7 +370,9 @@ cudaError_t launch_sketch_fp8(int64_t row0, int64_t m, int64_t n, const float* A
   const int sms = device_sm_count();
   {
     KernelTimer kt("fp8_quantize", st);
-    fp8_quantize_kernel<<<sms * 8, 256, 0, st>>>(m, n, A, lda, A8, pl.ld8, S, pl.nkb, dev_status);
+    // two CTAs per SM: a few hundred columns in flight, so that each column's second read hits L2
+    fp8_quantize_kernel<<<(unsigned)std::min<int64_t>(n, 2 * sms), 512, 0, st>>>(m, n, A, lda, A8, pl.ld8, S,
+                                                                                 dev_status);
   }
   fp8_gamma_kernel<<<(unsigned)std::min<int64_t>((pl.lp * pl.mg / 4 + 255) / 256, 4096), 256, 0, st>>>(
       l, (int)pl.lp, m, pl.mg, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), G8);

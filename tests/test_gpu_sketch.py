@@ -246,8 +246,8 @@ def test_sketch_power_iteration(skel, dev, prec, q, m, n):
 @pytest.mark.parametrize("m,n,l", [(1000, 777, 61), (2048, 1536, 272), (300, 129, 40), (4100, 600, 130),
                                    (129, 2048, 128)])
 def test_sketch_fp8_tensor_cores(skel, dev, m, n, l):
-    """tcgen05 kind::f8f6f4 sketch: e4m3 normals, A in e4m3 with a power-of-two scale per 128
-    rows of each column, exact products, FP32 accumulation.  Reference: the oracle's FP8
+    """tcgen05 kind::f8f6f4 sketch: e4m3 normals, A in e4m3 with one power-of-two scale per
+    column, exact products, FP32 accumulation.  Reference: the oracle's FP8
     sketch (FP64 normals rounded to e4m3, the same scales).  An FP32 normal near an e4m3
     rounding boundary can round one e4m3 step (2^-3 relative) away from the FP64 one; two
     such entries per row are allowed for."""
@@ -257,7 +257,7 @@ def test_sketch_fp8_tensor_cores(skel, dev, m, n, l):
     Ad = A.astype(np.float64)
     want = sketch.gaussian_sketch(Ad, l, 79, operand_rounding="fp8")
     G8 = embedding.round_e4m3(embedding.gaussian_normals(l, m, 79))
-    A8 = embedding.round_fp8_blocks(Ad)
+    A8 = embedding.round_fp8_blocks(Ad, Ad.shape[0])
     acc = 2 * m * 2.0 ** -23 * (np.abs(G8) @ np.abs(A8))
     flips = 2 * 2.0 ** -3 * np.outer(np.abs(G8).max(axis=1), np.abs(A8).max(axis=0))
     err = np.abs(X.cpu().numpy() - want)
