@@ -11,10 +11,11 @@
 //                        are in flight at once).
 //   fp8_gamma_kernel     e4m3 normals G8 (l_pad x m_pad bytes, zero padded), 0.35 l m bytes
 //                        that stay in L2.
-//   sketch_fp8_kernel    one CTA per 128 rows of X x 128 columns of A over an interleaved
+//   sketch_fp8_kernel    one CTA per 128 rows of X x 512 columns of A over an interleaved
 //                        K-split of 128-row blocks: TMA brings the A8 and G8 tiles (128-byte
-//                        swizzle, 128 K-elements per row), tcgen05.mma kind::f8f6f4 (M 128,
-//                        N 128, K 32) accumulates the CTA's whole K range in one TMEM buffer,
+//                        swizzle, 128 K-elements per row; one G8 tile serves four 128-column
+//                        quarters of A8), tcgen05.mma kind::f8f6f4 (M 128, N 256, K 32, two per
+//                        K-step) accumulates the CTA's whole K range in 512 TMEM columns,
 //                        and four epilogue warps multiply each column by its scale once at
 //                        the end (the scale is constant along K).
 // Every mbarrier wait is bounded (SKEL_ERR_TIMEOUT, then drain and free TMEM).
@@ -34,11 +35,13 @@ namespace {
 using namespace tc;
 
 constexpr int F8_BLOCK = 128;                 // rows per scale block = K per stage
-constexpr int F8_N = 128;                     // columns of A per CTA
-constexpr int F8_STAGES = 4;
+constexpr int F8_N = 512;                     // columns of A per CTA: two N = 256 MMAs
+constexpr int F8_STAGES = 2;
 constexpr int F8_THREADS = 256;               // warp 0 TMA, 1 MMA, 2 TMEM, 4..7 epilogue
-constexpr uint32_t F8_TILE = 128 * 128;       // bytes of one A8 or G8 tile
-constexpr size_t F8_SMEM = 1024 + F8_STAGES * 2 * F8_TILE + 256;
+constexpr uint32_t F8_GTILE = 128 * 128;                  // G8 tile: 128 rows of Gamma x 128 K bytes
+constexpr uint32_t F8_ATILE = F8_N * 128;                 // A8 tile: 512 columns of A x 128 K bytes
+constexpr uint32_t F8_STAGE = F8_ATILE + F8_GTILE;        // a multiple of 1024 (128-byte swizzle atoms)
+constexpr size_t F8_SMEM = 1024 + F8_STAGES * (size_t)F8_STAGE + 256;
 constexpr uint64_t F8_WAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
@@ -161,7 +164,7 @@ sketch_fp8_kernel(const __grid_constant__ CUtensorMap tmA8, const __grid_constan
                   const F8Params p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + F8_STAGES * 2 * F8_TILE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + F8_STAGES * F8_STAGE);
   // bars: full[S], empty[S], tfull[2], tempty[2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * F8_STAGES + 4);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
@@ -170,8 +173,8 @@ sketch_fp8_kernel(const __grid_constant__ CUtensorMap tmA8, const __grid_constan
   const int64_t j0 = (int64_t)blockIdx.y * F8_N;
   const int kz = blockIdx.z;
   const int nk = (int)((p.nkb - kz + p.P - 1) / p.P);
-  auto a_buf = [&](int s) { return smem + s * 2 * F8_TILE; };
-  auto g_buf = [&](int s) { return smem + s * 2 * F8_TILE + F8_TILE; };
+  auto a_buf = [&](int s) { return smem + s * F8_STAGE; };
+  auto g_buf = [&](int s) { return smem + s * F8_STAGE + F8_ATILE; };
   auto full = [&](int s) { return smem_u32(&bars[s]); };
   auto empty = [&](int s) { return smem_u32(&bars[F8_STAGES + s]); };
   auto tfull = [&](int b) { return smem_u32(&bars[2 * F8_STAGES + b]); };
@@ -191,7 +194,7 @@ sketch_fp8_kernel(const __grid_constant__ CUtensorMap tmA8, const __grid_constan
   }
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(smem_u32(tmem_slot)), "r"(256u) : "memory");
+                 ::"r"(smem_u32(tmem_slot)), "r"((uint32_t)F8_N) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
@@ -211,9 +214,10 @@ sketch_fp8_kernel(const __grid_constant__ CUtensorMap tmA8, const __grid_constan
         const uint32_t ph = (uint32_t)(it / F8_STAGES) & 1u;
         if (aborted()) break;
         if (it >= F8_STAGES && !mbar_wait(empty(s), ph ^ 1u, F8_WAIT_NS)) { fail(); break; }
-        mbar_expect_tx(full(s), 2 * F8_TILE);
+        mbar_expect_tx(full(s), F8_STAGE);
         const int x = (int)(((int64_t)kz + (int64_t)it * p.P) * F8_BLOCK);
-        tma_load_2d(smem_u32(a_buf(s)), &tmA8, x, (int)j0, full(s));
+        tma_load_2d(smem_u32(a_buf(s)), &tmA8, x, (int)j0, full(s));               // columns j0 .. +255
+        tma_load_2d(smem_u32(a_buf(s)) + 256 * 128, &tmA8, x, (int)j0 + 256, full(s));   // .. +511
         tma_load_2d(smem_u32(g_buf(s)), &tmG8, x, lb * 128, full(s));
         ++issued;
       }
@@ -222,7 +226,7 @@ sketch_fp8_kernel(const __grid_constant__ CUtensorMap tmA8, const __grid_constan
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_e4m3(128, F8_N);
+      const uint32_t idesc = idesc_e4m3(128, 256);
       for (int it = 0; it < nk; ++it) {
         const int s = it % F8_STAGES;
         const uint32_t ph = (uint32_t)(it / F8_STAGES) & 1u;
@@ -234,8 +238,11 @@ sketch_fp8_kernel(const __grid_constant__ CUtensorMap tmA8, const __grid_constan
         tc_fence_after();
         const uint32_t ga = smem_u32(g_buf(s)), aa = smem_u32(a_buf(s));
 #pragma unroll
-        for (int kk = 0; kk < F8_BLOCK / 32; ++kk)      // K = 32 per MMA: 32 bytes of each row
-          mma_f8(tmem, sw128_desc(ga + kk * 32), sw128_desc(aa + kk * 32), idesc, (it > 0 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < F8_BLOCK / 32; ++kk) {    // K = 32 per MMA: 32 bytes of each row
+          const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+          mma_f8(tmem, sw128_desc(ga + kk * 32), sw128_desc(aa + kk * 32), idesc, acc);
+          mma_f8(tmem + 256, sw128_desc(ga + kk * 32), sw128_desc(aa + 256 * 128 + kk * 32), idesc, acc);
+        }
         mma_commit(empty(s));
       }
       mma_commit(tfull(0));      // arrives once every MMA issued above has completed
@@ -253,8 +260,11 @@ sketch_fp8_kernel(const __grid_constant__ CUtensorMap tmA8, const __grid_constan
     if (ok && !aborted()) {
       float* orow = p.out + (p.direct ? 0 : (int64_t)kz * p.part_stride) + i * p.ldo;
       const float scl = p.direct ? p.scale : 1.f;
+      // 16-byte stores when every row of the output starts on a 16-byte boundary (S is
+      // 256-byte aligned in the workspace)
+      const bool vec = (p.ldo & 3) == 0 && (reinterpret_cast<uintptr_t>(p.out) & 15) == 0 &&
+                       (p.part_stride & 3) == 0;
       bool bad = false;
-#pragma unroll
       for (int c0 = 0; c0 < F8_N; c0 += 32) {
         uint32_t r[32];
         if (nk > 0) {
@@ -265,13 +275,25 @@ sketch_fp8_kernel(const __grid_constant__ CUtensorMap tmA8, const __grid_constan
           for (int q = 0; q < 32; ++q) r[q] = 0u;
         }
         if (i < p.l) {
+          const int64_t jb = j0 + c0;
+          if (jb + 32 <= p.n && vec) {
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const int64_t jc = j0 + c0 + q;
-            if (jc < p.n) {
-              const float v = __uint_as_float(r[q]) * __ldg(p.S + jc) * scl;
-              bad |= !isfinite(v);
-              orow[jc] = v;
+            for (int q = 0; q < 32; q += 4) {
+              const float4 sc = __ldg(reinterpret_cast<const float4*>(p.S + jb + q));
+              const float4 v = make_float4(__uint_as_float(r[q]) * sc.x * scl, __uint_as_float(r[q + 1]) * sc.y * scl,
+                                           __uint_as_float(r[q + 2]) * sc.z * scl, __uint_as_float(r[q + 3]) * sc.w * scl);
+              bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+              *reinterpret_cast<float4*>(orow + jb + q) = v;
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+              const int64_t jc = jb + q;
+              if (jc < p.n) {
+                const float v = __uint_as_float(r[q]) * __ldg(p.S + jc) * scl;
+                bad |= !isfinite(v);
+                orow[jc] = v;
+              }
             }
           }
         }
@@ -283,7 +305,7 @@ sketch_fp8_kernel(const __grid_constant__ CUtensorMap tmA8, const __grid_constan
   __syncthreads();
   if (warp == 2) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)F8_N) : "memory");
   }
 }
 
@@ -350,7 +372,7 @@ cudaError_t launch_sketch_fp8(int64_t row0, int64_t m, int64_t n, const float* A
   {
     const cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)n};
     const cuuint64_t gstride[1] = {(cuuint64_t)pl.ld8};
-    const cuuint32_t box[2] = {F8_BLOCK, F8_N};
+    const cuuint32_t box[2] = {F8_BLOCK, 256};           // two boxes per 512-column tile
     const cuuint32_t es[2] = {1, 1};
     if (enc(&tA, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, A8, gdim, gstride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
