@@ -51,6 +51,8 @@ __device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
   return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
+constexpr int kQG = 8;                        // 16-byte loads in flight per quantisation thread
+
 // One CTA per column j (grid-stride): amax by thread, warp and CTA reductions, the scale S[j],
 // then the codes, thread t covering rows 4t .. 4t+3 of every 4 * blockDim.x.
 __global__ void fp8_quantize_kernel(int64_t m, int64_t n, const float* A, int64_t lda, uint8_t* A8, int64_t ld8,
@@ -71,12 +73,12 @@ __global__ void fp8_quantize_kernel(int64_t m, int64_t n, const float* A, int64_
     const float* col = A + j * lda;
     uint32_t bits = 0;
     const int64_t step = 4 * (int64_t)blockDim.x;
-    for (int64_t r0 = 4 * (int64_t)threadIdx.x; r0 < m; r0 += 4 * step) {   // four loads in flight
-      float v[4][4];
+    for (int64_t r0 = 4 * (int64_t)threadIdx.x; r0 < m; r0 += kQG * step) {   // kQG loads in flight
+      float v[kQG][4];
 #pragma unroll
-      for (int g = 0; g < 4; ++g) load4(col, r0 + g * step, v[g]);
+      for (int g = 0; g < kQG; ++g) load4(col, r0 + g * step, v[g]);
 #pragma unroll
-      for (int g = 0; g < 4; ++g)
+      for (int g = 0; g < kQG; ++g)
 #pragma unroll
         for (int u = 0; u < 4; ++u) bits = max(bits, __float_as_uint(fabsf(v[g][u])));
     }
@@ -99,12 +101,12 @@ __global__ void fp8_quantize_kernel(int64_t m, int64_t n, const float* A, int64_
     }
     if (threadIdx.x == 0) S[j] = scale;
     uint8_t* dst = A8 + j * ld8;
-    for (int64_t r0 = 4 * (int64_t)threadIdx.x; r0 < m; r0 += 4 * step) {
-      float v[4][4];
+    for (int64_t r0 = 4 * (int64_t)threadIdx.x; r0 < m; r0 += kQG * step) {
+      float v[kQG][4];
 #pragma unroll
-      for (int g = 0; g < 4; ++g) load4(col, r0 + g * step, v[g]);
+      for (int g = 0; g < kQG; ++g) load4(col, r0 + g * step, v[g]);
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
+      for (int g = 0; g < kQG; ++g) {
         const int64_t r = r0 + g * step;
         if (r >= m) continue;
         const uint32_t word = e4m3x4(v[g][0] * inv, v[g][1] * inv, v[g][2] * inv, v[g][3] * inv);
