@@ -177,8 +177,11 @@ TIMED_KERNELS = ("sketch_tc", "sketch_fp8", "fp8_quantize", "gemm_tc", "lupp_pan
 # the current code exists)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture.  c5: the TF32
 # sketch captured on the 65536 x 8192 slice of the workload (2.164 GB read, 3.5 MB written),
-# scaled by the columns to the full 32768-column launch (the kernel reads each column of A once).
-TRAFFIC_PER_LAUNCH = {"c5": {"sketch_tc_tf32": 4 * (2.164166912e9 + 3.450624e6)},
+# scaled by the columns to the full 32768-column launch (the kernel reads each column of A once);
+# the FP8 GEMM on the same slice (612.5 MB read: the 536.9 MB of A8 and Gamma's 75.5 MB; 0.15 MB
+# written), its A8 part scaled by the columns.
+TRAFFIC_PER_LAUNCH = {"c5": {"sketch_tc_tf32": 4 * (2.164166912e9 + 3.450624e6),
+                             "sketch_fp8_fp8": 4 * (612513024 - 75497472 + 145408) + 75497472},
                       "c2": {"sketch_tc": 271.9e6, "gemm_tc": 332.4e6, "lupp_panel": 3.09e6, "qr_panel": 2.15e6}}
 FP64_NOMINAL_TFLOPS = 1.25
 TENSOR_RATIO = {"bf16": 1.0, "tf32": 1.1 / 2.25, "fp8": 2.0}     # nominal dense ratios to BF16
