@@ -264,6 +264,33 @@ def test_sketch_fp8_tensor_cores(skel, dev, m, n, l):
     assert np.all(err <= (acc + flips) / np.sqrt(l)), (err / ((acc + flips) / np.sqrt(l))).max()
 
 
+@pytest.mark.parametrize("m,n,l", [(16384, 40, 32), (16385, 40, 32), (40000, 37, 61), (131072, 9, 16),
+                                   (140000, 9, 16)])
+def test_sketch_fp8_tall_columns(skel, dev, m, n, l):
+    """Columns taller than one CTA's share of the quantisation (16384 rows): column j is 8 times
+    larger in the 16384-row block j mod b (b blocks), so its amax and scale come from a
+    different block for each j, and a block quantised with its own amax instead of the
+    column's would be off by a factor near 8.  m = 16384 and 16385 straddle one block,
+    131072 is the tallest clustered column (8 blocks), 140000 the two-pass path for taller
+    ones.  Same bound as the FP8 test above."""
+    A = workloads.dense_config2(m, n, seed=m % 1000 + l, dtype=np.float32)
+    b = (m + 16383) // 16384
+    for j in range(n):
+        q = j % b
+        A[q * 16384:(q + 1) * 16384, j] *= 8.0
+    A = np.asfortranarray(A)
+    X, st = skel.sketch(torch.from_numpy(A).to(dev), l, prec="fp8", seed=83)
+    skel.check_status(st)
+    Ad = A.astype(np.float64)
+    want = sketch.gaussian_sketch(Ad, l, 83, operand_rounding="fp8")
+    G8 = embedding.round_e4m3(embedding.gaussian_normals(l, m, 83))
+    A8 = embedding.round_fp8_blocks(Ad, Ad.shape[0])
+    acc = 2 * m * 2.0 ** -23 * (np.abs(G8) @ np.abs(A8))
+    flips = 2 * 2.0 ** -3 * np.outer(np.abs(G8).max(axis=1), np.abs(A8).max(axis=0))
+    err = np.abs(X.cpu().numpy() - want)
+    assert np.all(err <= (acc + flips) / np.sqrt(l)), (err / ((acc + flips) / np.sqrt(l))).max()
+
+
 def test_sketch_fp8_pivots_well_separated(skel, dev):
     """Pivots from the FP8 sketch equal the oracle's on its FP8 sketch (and on the exact one) for
     columns with geometrically separated norms: every greedy gap (>= 0.35 here) is far above
