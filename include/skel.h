@@ -27,6 +27,12 @@
  *  - Random numbers: every entry of an embedding is a function of (seed, row, column) through
  *    Philox-4x32-10 (Salmon et al., SC'11), so the same seed gives the same embedding in any
  *    launch shape.
+ *  - Library-owned streams and events (the look-ahead streams of skel_pivot_lupp, the
+ *    auxiliary stream of skel_pivot_skeleton and skel_id_cur, the copy stream of the host-A
+ *    sketches) are created by the first call that needs them in each CUDA context and device,
+ *    and kept under that context's unique id (cuCtxGetId).  After cudaDeviceReset, or from
+ *    another context, the next call creates new ones; those of a destroyed context are not
+ *    released.  Make the first such call before any stream capture.
  */
 #ifndef SKEL_H
 #define SKEL_H
@@ -341,8 +347,8 @@ skel_status skel_pivot_rows(int64_t m, int64_t n, skel_dtype dtype, const void* 
  *   X, l, n, ldx : the sketch, l x n row-major;  A, m, lda : m x n column-major.
  *   s         : skeletons, 1 <= s <= min(l, m, n, 1024).
  *   Js, Is    : out int32[s];  L, R : optional, as skel_pivot_lupp.
- * The auxiliary stream and its events are created once per device and shared by every call
- * (calls are enqueued one at a time under a lock).  When a panel of either LUPP does not fit
+ * The auxiliary stream and its events are created once per context and device and shared by
+ * every call (calls are enqueued one at a time under a lock).  When a panel of either LUPP does not fit
  * a thread-block cluster the two LUPPs run one after the other on the caller's stream.  A
  * column LUPP that stops early (rank-deficient X) leaves Is at -1.
  */

@@ -206,8 +206,9 @@ skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dt
 
 namespace {
 
-// The copy stream and events of skel_sketch_host, one set per device, created on first use.
-// copied[b] marks staging buffer b filled, consumed[b] the sketch of it finished.
+// The copy stream and events of skel_sketch_host, one set per context and device
+// (context_cache.h), created on first use.  copied[b] marks staging buffer b filled,
+// consumed[b] the sketch of it finished.
 struct HostStreamSet {
   cudaStream_t copy = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
@@ -220,20 +221,16 @@ std::mutex& host_stream_mutex() {
 }
 
 HostStreamSet* host_stream_set() {
-  static HostStreamSet sets[64];
+  static ContextCache<HostStreamSet> sets;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  HostStreamSet& h = sets[dev];
-  if (h.copy) return &h;
-  bool ok = cudaStreamCreateWithFlags(&h.copy, cudaStreamNonBlocking) == cudaSuccess;
-  for (cudaEvent_t* e : {&h.fork, &h.join, &h.copied[0], &h.copied[1], &h.consumed[0], &h.consumed[1]})
-    ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    h.copy = nullptr;
-    return nullptr;
-  }
-  return &h;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  return sets.get(current_context_id(), dev, [](HostStreamSet& h) {
+    bool ok = cudaStreamCreateWithFlags(&h.copy, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t* e : {&h.fork, &h.join, &h.copied[0], &h.copied[1], &h.consumed[0], &h.consumed[1]})
+      ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+    return ok;
+  });
 }
 
 // Joins the copy stream back into the caller's stream on every return path.

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/skel.h"
+#include "context_cache.h"
 
 namespace skel {
 
@@ -130,8 +131,13 @@ skel_status run_lupp(skel_dtype dt, const void* X, int64_t n, int64_t ldx, int32
 // LUPP through the panel-blocked cluster kernels when a panel fits one cluster's shared
 // memory (lupp_panel.cu), else through the grid-barrier kernel above.
 size_t lupp_auto_workspace(skel_dtype dt, int64_t n, int32_t s);
-// Auxiliary stream and events for fork/join concurrency inside one call, one set per device,
-// created on first use.  Hold aux_mutex() for the whole enqueue that uses them, so that
+// Unique id of the calling thread's current CUDA context (cuCtxGetId), after making the
+// current device's primary context current when the thread has none; 0 when the driver
+// offers no context ids (context.cu).
+unsigned long long current_context_id();
+
+// Auxiliary stream and events for fork/join concurrency inside one call, one set per context
+// and device (context_cache.h), created on first use.  Hold aux_mutex() for the whole enqueue that uses them, so that
 // concurrent callers never interleave records and waits on the shared events.
 constexpr int kAuxEvents = 130;      // one per panel of >= 8 steps of up to 1024, and spares
 struct AuxSet {

@@ -1082,8 +1082,8 @@ size_t panel_ws(int64_t n, int s, bool need_r) {
          align_up(sizeof(T) * (size_t)kMaxPanel * kMaxPanel) + (need_r ? align_up(sizeof(T) * (size_t)s * n) : 0);
 }
 
-// Streams of the look-ahead schedule (one set per device, used under its mutex while a call
-// enqueues): `hi` (highest priority) carries the panels and the updates of the next panel's
+// Streams of the look-ahead schedule (one set per context and device, context_cache.h; used
+// under its mutex while a call enqueues): `hi` (highest priority) carries the panels and the updates of the next panel's
 // rows, `lo` (lowest priority) the bulk trailing updates.
 struct LookaheadSet {
   cudaStream_t hi = nullptr, lo = nullptr;
@@ -1096,23 +1096,19 @@ std::mutex& lookahead_mutex() {
 }
 
 LookaheadSet* lookahead_set() {
-  static LookaheadSet sets[64];
+  static ContextCache<LookaheadSet> sets;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  LookaheadSet& a = sets[dev];
-  if (a.hi) return &a;
-  int least = 0, greatest = 0;
-  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return nullptr;
-  bool ok = cudaStreamCreateWithPriority(&a.hi, cudaStreamNonBlocking, greatest) == cudaSuccess &&
-            cudaStreamCreateWithPriority(&a.lo, cudaStreamNonBlocking, least) == cudaSuccess;
-  for (cudaEvent_t* e : {&a.fork, &a.join_hi, &a.join_lo, &a.panel_done, &a.bulk_done})
-    ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    a.hi = nullptr;
-    return nullptr;
-  }
-  return &a;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  return sets.get(current_context_id(), dev, [](LookaheadSet& a) {
+    int least = 0, greatest = 0;
+    bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&a.hi, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&a.lo, cudaStreamNonBlocking, least) == cudaSuccess;
+    for (cudaEvent_t* e : {&a.fork, &a.join_hi, &a.join_lo, &a.panel_done, &a.bulk_done})
+      ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+    return ok;
+  });
 }
 
 // Joins both look-ahead streams back into the caller's stream on every return path.
@@ -1348,21 +1344,18 @@ std::mutex& aux_mutex() {
 }
 
 AuxSet* aux_set() {
-  static AuxSet sets[64];
+  static ContextCache<AuxSet> sets;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  AuxSet& a = sets[dev];
-  if (a.st) return &a;
-  if (cudaStreamCreateWithFlags(&a.st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
-  bool ok = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) == cudaSuccess;
-  for (int k = 0; ok && k < kAuxEvents; ++k) ok = cudaEventCreateWithFlags(&a.col[k], cudaEventDisableTiming) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    a.st = nullptr;
-    return nullptr;
-  }
-  return &a;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  return sets.get(current_context_id(), dev, [](AuxSet& a) {
+    bool ok = cudaStreamCreateWithFlags(&a.st, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < kAuxEvents; ++k)
+      ok = cudaEventCreateWithFlags(&a.col[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+    return ok;
+  });
 }
 
 bool skeleton_pivot_pipelined(skel_dtype dt, int64_t n, int64_t m, int32_t s) {

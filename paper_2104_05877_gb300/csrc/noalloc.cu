@@ -2,8 +2,6 @@
 // allocate device memory.  Its scratch (grid-barrier counter, per-step argmax keys, candidate
 // slots, and the column slab when it does not fit in shared memory) lives in a fixed-size
 // array in this library's device image instead of a caller-provided workspace.
-#include <cuda.h>
-
 #include <mutex>
 
 #include "common.cuh"
@@ -22,19 +20,6 @@ __device__ __align__(256) unsigned char g_lupp_scratch[kStaticScratchBytes];
 // looked up once, with that context current, and cached under the context's unique id: a
 // device reset (which destroys the primary context and reloads the module, so the array may
 // move) or a call from another context on the same device yields a new id and a new lookup.
-using CtxGetCurrentFn = CUresult (*)(CUcontext*);
-using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
-
-template <typename F>
-F driver_fn(const char* name) {
-  void* f = nullptr;
-  cudaDriverEntryPointQueryResult q;
-  if (cudaGetDriverEntryPointByVersion(name, &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-      q != cudaDriverEntryPointSuccess)
-    return nullptr;
-  return reinterpret_cast<F>(f);
-}
-
 constexpr int kCacheEntries = 64;
 struct ScratchEntry {
   unsigned long long ctx_id;
@@ -44,21 +29,9 @@ ScratchEntry g_cache[kCacheEntries] = {};
 int g_cache_next = 0;
 std::mutex g_scratch_mu;
 
-// Unique id of the calling thread's current context, 0 if none is current (or the driver
-// does not offer context ids).
-unsigned long long current_ctx_id() {
-  static const CtxGetCurrentFn get_ctx = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent");
-  static const CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId");
-  CUcontext ctx = nullptr;
-  unsigned long long id = 0;
-  if (!get_ctx || !get_id || get_ctx(&ctx) != CUDA_SUCCESS || ctx == nullptr || get_id(ctx, &id) != CUDA_SUCCESS)
-    return 0;
-  return id;
-}
-
 skel_status static_scratch(void** out) {
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  const unsigned long long id0 = current_ctx_id();
+  const unsigned long long id0 = current_context_id();
   if (id0 != 0)
     for (const ScratchEntry& e : g_cache)
       if (e.ctx_id == id0 && e.ptr != nullptr) {
@@ -72,7 +45,7 @@ skel_status static_scratch(void** out) {
     cudaGetLastError();
     return SKEL_ERR_CUDA;
   }
-  const unsigned long long id = current_ctx_id();
+  const unsigned long long id = current_context_id();
   if (id != 0) {        // without a context id every call looks the address up (no caching)
     g_cache[g_cache_next] = {id, p};
     g_cache_next = (g_cache_next + 1) % kCacheEntries;
