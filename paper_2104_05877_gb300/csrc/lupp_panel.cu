@@ -1083,8 +1083,8 @@ size_t panel_ws(int64_t n, int s, bool need_r) {
 }
 
 // Streams of the look-ahead schedule (one set per context and device, context_cache.h; used
-// under its mutex while a call enqueues): `hi` (highest priority) carries the panels and the updates of the next panel's
-// rows, `lo` (lowest priority) the bulk trailing updates.
+// under its mutex while a call enqueues): `hi` (highest priority) carries the panels and the
+// updates of the next panel's rows, `lo` (lowest priority) the bulk trailing updates.
 struct LookaheadSet {
   cudaStream_t hi = nullptr, lo = nullptr;
   cudaEvent_t fork = nullptr, join_hi = nullptr, join_lo = nullptr, panel_done = nullptr, bulk_done = nullptr;
