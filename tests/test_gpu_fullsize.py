@@ -17,6 +17,8 @@ two greedy pivots recomputed on the host from the device's sketch, Theorem 1's b
 device's eta and an independently computed rangefinder error, and the ID error of the device's Z
 (the residual formed on the device) against the closed-form best rank-k error of the
 constructed spectrum and within 1.05x of the FP64 GPU form's skeleton (the equal-error gate).
+The FP8 sketch, bench.py's default, gets the same sampled-entry check against the oracle's FP8
+sketch and the same equal-error gate.
 """
 
 import numpy as np
@@ -168,6 +170,52 @@ def test_config5_full_size_properties(skel, dev):
     skel.check_status(st)
     e64 = e64.cpu().numpy()
     assert rel_direct <= 1.05 * float(e64[1] / e64[0]), (rel_direct, float(e64[1] / e64[0]))
+
+
+def test_config5_fp8_sketch_full_size(skel, dev):
+    """The FP8 sketch bench.py times by default, at 65536 x 32768 on the bench's A and seeds:
+    sampled entries one by one against the oracle's FP8 sketch (e4m3 normals; each column of A
+    in e4m3 with its power-of-two scale), with the bound of the smaller FP8 tests, and the
+    equal-error gate: the ID error of the FP8 skeleton (residual formed on the device) within
+    1.05x of the FP64 GPU skeleton's."""
+    m, n = 65536, 32768
+    k, p = 1024, 76
+    l = k + p
+    seed_G = workloads.seed_for(5, "gamma")
+    A = workloads.torch_config5(dev, m, n, seed=workloads.seed_for(5))
+    st = skel.new_status(dev)
+    X, _ = skel.sketch(A, l, prec="fp8", seed=seed_G, status=st)
+    Js, _, _, _ = skel.pivot_lupp(X, k, factors=False, status=st)
+    Z, _, _ = skel.column_id(A, Js, status=st)
+    e8, _ = skel.error(A, Js, Z=Z, status=st)
+    del Z
+    torch.cuda.synchronize()
+    skel.check_status(st)
+    rng = np.random.default_rng(2)
+    ii = np.sort(rng.choice(l, 6, replace=False))
+    G8 = embedding.round_e4m3(embedding.gaussian_normals_rows(ii, m, seed_G))
+    Xc = X.cpu()
+    for j in rng.integers(0, n, 24):
+        a = A[:, j].double().cpu().numpy()
+        a8 = embedding.round_fp8_blocks(a[:, None], m)[:, 0]
+        want = G8 @ a8 / np.sqrt(l)
+        acc = 2 * m * 2.0 ** -23 * (np.abs(G8) @ np.abs(a8))
+        flips = 2 * 2.0 ** -3 * np.abs(G8).max(axis=1) * np.abs(a8).max()
+        got = Xc[ii, j].double().numpy()
+        assert np.all(np.abs(got - want) <= (acc + flips) / np.sqrt(l)), j
+    J = Js.cpu().numpy()
+    assert len(set(J.tolist())) == k and J.min() >= 0 and J.max() < n
+    e8 = e8.cpu().numpy()
+    rel8 = float(e8[1] / e8[0])
+    A64 = A.double().t().contiguous().t()
+    X64, _ = skel.sketch(A64, l, prec="f64", seed=seed_G, status=st)
+    J64, _, _, _ = skel.pivot_lupp(X64, k, factors=False, status=st)
+    del A64, X64
+    Z64, _, _ = skel.column_id(A, J64, status=st)
+    e64, _ = skel.error(A, J64, Z=Z64, status=st)
+    skel.check_status(st)
+    e64 = e64.cpu().numpy()
+    assert rel8 <= 1.05 * float(e64[1] / e64[0]), (rel8, float(e64[1] / e64[0]))
 
 
 def test_config3_full_size_sparse_sign_and_cur(skel, dev):
