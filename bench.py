@@ -172,14 +172,12 @@ class ClockSampler:
 TIMED_KERNELS = ("sketch_tc", "sketch_fp8", "fp8_quantize", "gemm_tc", "lupp_panel", "lupp_trail", "qr_panel", "qr_wy", "gemm_refine",
                  "trsm", "gemm_qr", "gemm_cur", "gemm_eta_h", "gemm_eta_sq", "gemm_simt", "transpose", "lupp_mult",
                  "trsm_ff")
-# DRAM bytes (read + write) per launch from one ncu capture of the current kernel at this
-# workload, scaled from a smaller capture where noted in the profiles (None where no capture of
-# the current code exists)
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture.  c5: the TF32
-# sketch captured on the 65536 x 8192 slice of the workload (2.164 GB read, 3.5 MB written),
-# scaled by the columns to the full 32768-column launch (the kernel reads each column of A once);
-# the FP8 GEMM on the same slice (612.5 MB read: the 536.9 MB of A8 and Gamma's 75.5 MB; 0.15 MB
-# written), its A8 part scaled by the columns.
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
+# the current kernel at this workload; None where no capture of the current code exists.  c5 is
+# too large to capture whole: the TF32 sketch was captured on the 65536 x 8192 slice (2.164 GB
+# read, 3.5 MB written) and scaled by the columns to the full 32768-column launch (the kernel
+# reads each column of A once); the FP8 GEMM on the same slice (612.5 MB read: the 536.9 MB of
+# A8 and Gamma's 75.5 MB of e4m3 normals; 0.15 MB written), its A8 part scaled by the columns.
 TRAFFIC_PER_LAUNCH = {"c5": {"sketch_tc_tf32": 4 * (2.164166912e9 + 3.450624e6),
                              "sketch_fp8_fp8": 4 * (612513024 - 75497472 + 145408) + 75497472},
                       "c2": {"sketch_tc": 271.9e6, "gemm_tc": 332.4e6, "lupp_panel": 3.09e6, "qr_panel": 2.15e6}}

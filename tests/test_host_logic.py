@@ -79,3 +79,17 @@ def test_peaks_fallback_and_workload_config():
     assert (cfg["m"], cfg["n"], cfg["k"], cfg["l"]) == (65536, 32768, 1024, 1100)
     assert b.tensor_peak("tf32", {"bf16_tflops": 2250.0, "bf16_tflops_sustained": 1800.0}, False) == pytest.approx(1100.0)
     assert b.tensor_peak("fp8", {"bf16_tflops": 2250.0, "bf16_tflops_sustained": 1800.0}, True) == pytest.approx(3600.0)
+
+
+def test_recorded_traffic_is_the_algorithmic_bytes():
+    """The DRAM traffic the bench line reports for its sketch kernels (ncu captures, scaled from a
+    slice at 65536 x 32768) is within 1% of the algorithmic bytes: A read once by the TF32
+    sketch (4 m n), A8 and Gamma's e4m3 normals read once by the FP8 GEMM (m n + l_pad m),
+    the 8192^2 sketch reading A once."""
+    b = _bench()
+    m, n, l = 65536, 32768, 1100
+    lpad = (l + 127) // 128 * 128
+    t5 = b.TRAFFIC_PER_LAUNCH["c5"]
+    assert t5["sketch_tc_tf32"] == pytest.approx(4.0 * m * n, rel=0.01)
+    assert t5["sketch_fp8_fp8"] == pytest.approx(1.0 * m * n + lpad * m, rel=0.01)
+    assert b.TRAFFIC_PER_LAUNCH["c2"]["sketch_tc"] == pytest.approx(4.0 * 8192 * 8192, rel=0.02)
