@@ -505,6 +505,7 @@ def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
     total_ms = t_begin.elapsed_time(t_end)
     per = {nm: statistics.mean(ev[i].elapsed_time(ev[i + 1]) for ev in all_evs) for i, nm in enumerate(names)}
     tts = statistics.mean(ev[0].elapsed_time(ev[2]) for ev in all_evs)
+    tts_median = statistics.median([ev[0].elapsed_time(ev[2]) for ev in all_evs])
     tid = statistics.mean(ev[0].elapsed_time(ev[3]) for ev in all_evs)
     if world > 1:
         t = torch.tensor([tts, total_ms], device=dev)
@@ -655,6 +656,7 @@ def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
         "config": workload_config("c5", k, p, prec),
+        "time_to_skeleton_median_ms": tts_median,     # rank 0's steps; `value` is the mean (max over ranks)
         "time_to_id_ms": tid, "calls_ms": per,
         "a_streaming_gbs": 4.0 * m * n / (per["sketch"] * 1e-3) / 1e9,
         "sketch_tflops": 2.0 * l * m * n / (per["sketch"] * 1e-3) / 1e12,
