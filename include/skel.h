@@ -84,8 +84,8 @@ int skel_version(void);
 uint64_t skel_launch_count(void);
 
 /*
- * skel_sketch -- row sketch X = Gamma A of a dense A (Algorithm 1 line 2; Algorithm 2
- * line 2; Table 1).
+ * skel_sketch -- row sketch X = Gamma A of a dense A (the sketch step of Algorithms 1 and 2;
+ * Table 1).
  *   m, n      : A is m x n, column-major, leading dimension lda >= m, storage a_dtype.
  *   l         : number of sketch rows (l = k + p, Sec. 2.3), 1 <= l <= 4096.
  *   kind      : Gaussian (Gamma(i,j) = G(i,j)/sqrt(l), G from Philox + Box-Muller with
@@ -118,7 +118,7 @@ skel_status skel_sketch(int64_t m, int64_t n, skel_dtype a_dtype, const void* A,
 
 /*
  * skel_sketch_rows -- the partial sketch of a block of rows of a larger A (the row-partitioned
- * form of Algorithm 2 line 2: X = sum over row blocks of Gamma(:, rows) A(rows, :)).
+ * form of Algorithm 2's sketch step: X = sum over row blocks of Gamma(:, rows) A(rows, :)).
  *   row0      : global index of the block's first row; a multiple of 4, row0 + m <= 2^32 - 1.
  *               Gamma's columns row0 .. row0+m-1 are generated (Gaussian counters (j/4, i, 0, 0)
  *               and sparse-sign counters (j, 0, 1, c) use the global row j), so the partial
@@ -134,7 +134,7 @@ skel_status skel_sketch_rows(int64_t row0, int64_t m, int64_t n, skel_dtype a_dt
 
 /*
  * skel_sketch_host -- skel_sketch of an A that lives in host memory, streamed to the device in
- * column panels.  X = Gamma A reads A once (Algorithm 1 line 2; the single pass over A of
+ * column panels.  X = Gamma A reads A once (Algorithm 1, sketch step; the single pass over A of
  * Sec. 2.3), and X's columns j0..j1 depend on A's columns j0..j1 only, so the copy of one panel
  * overlaps the sketch of the one before: panels go through two device staging buffers in the
  * workspace, copied on a library-owned stream and sketched on `stream`.  A never has to fit
@@ -160,8 +160,8 @@ skel_status skel_sketch_host(int64_t m, int64_t n, skel_dtype a_dtype, const voi
                              cudaStream_t stream);
 
 /*
- * skel_sketch_host_two_sided -- both sketches of the streaming skeleton selection (Algorithm 3
- * line 2) from ONE pass over an A in host memory: X = Gamma A (l x n, as skel_sketch with the
+ * skel_sketch_host_two_sided -- both sketches of the streaming skeleton selection (Algorithm 3)
+ * from ONE pass over an A in host memory: X = Gamma A (l x n, as skel_sketch with the
  * Gaussian embedding and seed_gamma) and Yt = Omega A^T (l x m, as skel_sketch_cols with
  * seed_omega).  Each column panel A(:, j0:j0+w) is copied to the device once (as in
  * skel_sketch_host) and gives X(:, j0:j0+w) = Gamma A(:, panel) and the partial sum
@@ -187,10 +187,10 @@ skel_status skel_sketch_host_two_sided(int64_t m, int64_t n, skel_dtype a_dtype,
                                        int32_t* dev_status, cudaStream_t stream);
 
 /*
- * skel_sketch_cols -- the column sketch of the streaming skeleton selection (Algorithm 3 line 2):
+ * skel_sketch_cols -- the column sketch of the streaming skeleton selection (Algorithm 3):
  *     Y = A Omega^T (m x l),  Omega l x n Gaussian with N(0, 1/l) entries,
  * returned transposed, Yt = Omega A^T (l x m row-major, ldy >= m), so that the row skeletons
- * I_s are the column pivots of skel_pivot_lupp on Yt (Algorithm 3 line 4).  Omega's counters
+ * I_s are the column pivots of skel_pivot_lupp on Yt (Algorithm 3, row pivoting).  Omega's counters
  * are those of the Gaussian embedding over n columns (column j of Omega pairs with column j of
  * A); use a seed different from Gamma's for an independent Omega.  prec: SKEL_PREC_F64
  * (a_dtype F64) or SKEL_PREC_F32 (a_dtype F32), on the SIMT path with Omega generated in the
@@ -232,10 +232,10 @@ skel_status skel_sketch_csc(int64_t m, int64_t n, int64_t nnz, const int64_t* co
 
 /*
  * skel_pivot_lupp -- column-wise LU with partial pivoting on X (Sec. 2.5.2, Eq. (LUPP);
- * Algorithm 2 line 3), first s steps.  Step t picks j_t = argmax over unselected j of
+ * Algorithm 2, column pivoting), first s steps.  Step t picks j_t = argmax over unselected j of
  * |S(t, j)| for the current Schur complement S (ties: lowest column index), then
  * R(t, :) = S(t, :)/S(t, j_t) and S(t+1:, :) -= S(t+1:, j_t) R(t, :).  Only rows 0..s-1 of X
- * are read.  Row pivoting of a tall C (Algorithm 2 line 4) is this call on C^T: pass the
+ * are read.  Row pivoting of a tall C (Algorithm 2) is this call on C^T: pass the
  * column-major m x s C as X with l = s, n = m, ldx = ldc.
  *   dtype     : storage and arithmetic of X and of the factors (F64 or F32).
  *   X, ldx    : l x n row-major input (not modified).  1 <= s <= min(l, n), s <= 1024.
@@ -328,7 +328,7 @@ skel_status skel_id_refine(int64_t m, int64_t n, skel_dtype dtype, const void* A
                            void* ws, size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream);
 
 /*
- * skel_pivot_rows -- row skeletons of Algorithm 2 line 4: gathers C = A(:, Js) (m x s) and
+ * skel_pivot_rows -- row skeletons of Algorithm 2 (row pivoting): gathers C = A(:, Js) (m x s) and
  * runs row-wise LUPP on it (the LUPP of skel_pivot_lupp applied to C^T).
  *   Is        : out int32[s] row skeletons in selection order.
  */
@@ -337,7 +337,7 @@ skel_status skel_pivot_rows(int64_t m, int64_t n, skel_dtype dtype, const void* 
                             size_t* ws_bytes, int32_t* dev_status, cudaStream_t stream);
 
 /*
- * skel_pivot_skeleton -- both skeletons of Algorithm 2 (lines 3 and 4) in one call: the
+ * skel_pivot_skeleton -- both skeletons of Algorithm 2 (column and row pivoting) in one call: the
  * column LUPP of skel_pivot_lupp on X (Js, optional L and R), then the row LUPP of
  * skel_pivot_rows on C = A(:, Js) (Is), with results identical to those two calls.  The row
  * LUPP runs behind the column LUPP panel by panel: its panel of steps [t0, t0+b) needs only
@@ -362,7 +362,7 @@ skel_status skel_pivot_skeleton(skel_dtype dtype, const void* X, int64_t l, int6
  * stable form of Remark 3: U = R_C^{-1} (Q_C^T A Q_R) R_R^{-T}, where C = Q_C R_C and
  * R^T = Q_R R_R (Householder QR, FP64 for dtype F64, FP32 for F32; FP64 solves).
  *   Is        : row skeletons; input when rows_given != 0, otherwise computed here by
- *               row-wise LUPP on C (Algorithm 2 line 4) and written.
+ *               row-wise LUPP on C (Algorithm 2, row pivoting) and written.
  *   U, ldu    : out s x s row-major FP64.
  *   sq_norms  : optional out (may be NULL), device double[2] = {||A||_F^2, ||Q_C^T A Q_R||_F^2};
  *               their difference is ||A - C U R||_F^2 (a two-sided orthogonal projection).

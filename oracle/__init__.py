@@ -16,7 +16,7 @@ Modules
 philox      Philox-4x32-10 / 4x64-10 counter-based generator (Salmon et al., SC'11).
 embedding   Gaussian embedding (Sec. 2.3, item 1) and sparse sign embedding (Sec. 2.3,
             item 3); operand-rounding emulation (FP32, BF16).
-sketch      Row sketch X = Gamma A (Algorithm 1 line 2, Algorithm 2 line 2).
+sketch      Row sketch X = Gamma A (the sketch step of Algorithms 1 and 2).
 pivoting    Column-wise LUPP (Sec. 2.5.2, Eq. (LUPP)) and CPQR (Sec. 2.5.1).
 decomp      Column ID  C C^+ A  (Eq. (2.1)) and stable CUR  Q_C (Q_C^T A Q_R) Q_R^T
             (Remark 3).

@@ -63,7 +63,7 @@ def lupp_columns(X, s):
 
 def lupp_rows(C, s):
     """Row-wise LUPP on C (m x s'): the row pivots of C are the column pivots of C^T
-    (Algorithm 2 line 4)."""
+    (Algorithm 2, row pivoting)."""
     return lupp_columns(np.asarray(C).T, s)
 
 

@@ -5,7 +5,7 @@ Readings: the algorithms return |J_s| = l pivots; with a target rank k and overs
 (l = k + p, Sec. 2.3), the first s = k greedy pivots form the skeleton.  For LUPP the first
 k steps read only rows 0..k-1 of X, so the extra p rows never change LUPP's k pivots; they
 do enter CPQR's norms.  Row skeletons I_s come from row-wise LUPP on C = A(:, J_s)
-(Algorithm 2 line 4).
+(Algorithm 2, row pivoting).
 """
 
 import numpy as np

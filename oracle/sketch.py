@@ -1,4 +1,4 @@
-"""Row sketch X = Gamma A (Algorithm 1 line 2; Algorithm 2 line 2; Table 1).
+"""Row sketch X = Gamma A (the sketch step of Algorithms 1 and 2; Table 1).
 
 The sketch is a plain product; the only choices are the embedding and, when emulating a
 reduced-precision sketch, the rounding applied to each operand before the exact (FP64)
@@ -38,7 +38,7 @@ def gaussian_sketch(A, l, seed, operand_rounding=None):
 def gaussian_sketch_rows(A_block, l, seed, row0, operand_rounding=None):
     """Partial sketch of rows row0 .. row0+m_b-1 of a larger A: Gamma(:, row0:row0+m_b) A_block.
     Gamma's columns depend only on their global index, so the partial sketches of a row
-    partition sum to the sketch of the whole matrix (the row-partitioned Algorithm 2 line 2)."""
+    partition sum to the sketch of the whole matrix (the row-partitioned sketch step of Algorithm 2)."""
     A_block = np.asarray(A_block, dtype=np.float64)
     mb = A_block.shape[0]
     G = embedding.gaussian_normals(l, row0 + mb, seed)[:, row0:]
@@ -85,7 +85,7 @@ def gaussian_sketch_power(A, l, seed, q=1):
 
 
 def gaussian_col_sketch(A, l, seed):
-    """Transposed column sketch of the streaming selection (Algorithm 3 line 2): Yt = Omega A^T
+    """Transposed column sketch of the streaming selection (Algorithm 3): Yt = Omega A^T
     (l x m), i.e. Y = A Omega^T, with Omega (l x n) Gaussian N(0, 1/l) over the counters of the
     Gaussian embedding on n columns."""
     A = np.asarray(A, dtype=np.float64)

@@ -443,7 +443,7 @@ def cur_sketch(A, Js, Is, status=None):
 
 
 def pivot_rows(A, Js, status=None):
-    """Row skeletons Is by row-wise LUPP on C = A(:, Js) (Algorithm 2 line 4)."""
+    """Row skeletons Is by row-wise LUPP on C = A(:, Js) (Algorithm 2, row pivoting)."""
     A, lda = _colmajor(A)
     m, n = A.shape
     s = Js.numel()

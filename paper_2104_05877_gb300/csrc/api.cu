@@ -366,11 +366,11 @@ skel_status skel_sketch_host_two_sided(int64_t m, int64_t n, skel_dtype a_dtype,
   if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
   return stream_panels(m, n, ea, A, lda, lds, w, stage, stream,
                        [&](int64_t i, const char* panel_a, int64_t j0, int64_t wi) -> skel_status {
-    // X(:, j0 : j0 + wi) = Gamma A(:, panel)   (Algorithm 3 line 2, row sketch)
+    // X(:, j0 : j0 + wi) = Gamma A(:, panel)   (Algorithm 3, row sketch)
     size_t sz = xws_bytes;
     SK_TRY(skel_sketch_rows(0, m, wi, a_dtype, panel_a, lds, l, SKEL_SKETCH_GAUSSIAN, 0, prec, seed_gamma,
                             static_cast<char*>(X) + ex * j0, ldx, xws, &sz, dev_status, stream));
-    // Y^T += Omega(:, panel) A(:, panel)^T   (Algorithm 3 line 2, column sketch): the first
+    // Y^T += Omega(:, panel) A(:, panel)^T   (Algorithm 3, column sketch): the first
     // panel writes Y^T, later ones a partial that is added to it
     void* out = i == 0 ? Yt : part;
     const int64_t ldo = i == 0 ? ldy : m;
@@ -826,7 +826,7 @@ static skel_status cur_impl(int64_t m, int64_t n, skel_dtype dtype, const void* 
       if (ws_handshake(ar.off, ws, ws_bytes, &st)) return st;
       continue;
     }
-    // rows by LUPP on C (Algorithm 2 line 4): C column-major m x s is C^T row-major s x m
+    // rows by LUPP on C (Algorithm 2, row pivoting): C column-major m x s is C^T row-major s x m
     if (!rows_given)
       SK_TRY(run_lupp_auto(dtype, C, m, m, s, Is, nullptr, 0, nullptr, 0, lws, lw, dev_status, stream));
     SK_CUDA(launch_gather_rows_t(n, s, dtype, A, lda, m, Is, Rt, n, stream));

@@ -1,8 +1,8 @@
 // Batched skeletonization of many independent blocks (hierarchical-matrix compression): per
-// block A_b (m_b x n_b, FP32, column-major) the Gaussian sketch X_b = Gamma A_b (Algorithm 2
-// line 2), column LUPP on X_b (Sec. 2.5.2, Algorithm 2 line 3) stopped at the tolerance-driven
-// rank r, and the column ID coefficients formed from the sketch alone (C^+ A ~ X_1^+ X, Sec. 4,
-// ID without a second pass over A), the pseudo-inverse over all l rows of the sketch:
+// block A_b (m_b x n_b, FP32, column-major) the Gaussian sketch X_b = Gamma A_b (Algorithm 2),
+// column LUPP on X_b (Sec. 2.5.2, Algorithm 2) stopped at the tolerance-driven rank r, and
+// the column ID coefficients formed from the sketch alone (C^+ A ~ X_1^+ X, Sec. 4, ID
+// without a second pass over A), the pseudo-inverse over all l rows of the sketch:
 //   Z_b = X_b(:, J)^+ X_b = argmin_Z ||X_b(:, J) Z - X_b||_F.
 // A is read once.
 //

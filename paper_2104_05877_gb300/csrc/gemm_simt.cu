@@ -1,7 +1,7 @@
 // SIMT tiled GEMM with pluggable left operand (loaded, or Gaussian generated in-kernel from
 // Philox) and fused epilogues; plus gathers, transposes and deterministic reductions.
 //
-// Used for: the FP64/FP32 Gaussian sketch X = Gamma A (Algorithm 2 line 2) with Gamma never
+// Used for: the FP64/FP32 Gaussian sketch X = Gamma A (Algorithm 2, sketch step) with Gamma never
 // stored; W = Q_C^T A (Eq. (2.1) via Q_C R_C = C); W Q_R (Remark 3); T T^T for Theorem 1's
 // eta; and the residual norms ||A - C Z||_F, ||A - C U R||_F.
 #include <algorithm>

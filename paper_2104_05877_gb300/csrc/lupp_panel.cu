@@ -1,4 +1,4 @@
-// Panel-blocked column-wise LUPP on X (Sec. 2.5.2, Algorithm 2 line 3) for n small enough
+// Panel-blocked column-wise LUPP on X (Sec. 2.5.2, Algorithm 2, column pivoting) for n small enough
 // that a panel of b rows of X fits in the shared memory of one thread-block cluster.
 //
 // The s pivot steps are grouped into panels of b consecutive rows.  For each panel:

@@ -1,6 +1,6 @@
 // Greedy column pivoting on the sketch X (l x n, row-major) -- Sec. 2.5.
 //
-//   LUPP (Sec. 2.5.2, Algorithm 2 line 3): step t picks j_t = argmax |S(t, j)| over the
+//   LUPP (Sec. 2.5.2, Algorithm 2, column pivoting): step t picks j_t = argmax |S(t, j)| over the
 //   unselected columns, R(t,:) = S(t,:)/S(t,j_t), S(t+1:,:) -= S(t+1:,j_t) R(t,:).
 //   CPQR (Sec. 2.5.1): step t picks the largest remaining column norm (downdated, with a
 //   recompute guard), then applies a Householder reflector to the remaining columns.

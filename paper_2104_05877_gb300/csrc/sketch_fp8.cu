@@ -1,4 +1,4 @@
-// FP8 (e4m3) Gaussian sketch X = Gamma A (Algorithm 2 line 2) on sm_103a tensor cores.
+// FP8 (e4m3) Gaussian sketch X = Gamma A (Algorithm 2, sketch step) on sm_103a tensor cores.
 //
 // Quantisation: every column of A has one power-of-two scale, s = 2^ceil(log2(amax / 448))
 // (the smallest that keeps the column inside e4m3's range), and A8 = e4m3(A / s) rounded to

@@ -1,4 +1,4 @@
-// Tensor-core Gaussian sketch X = Gamma A (Algorithm 2 line 2; Table 1, T_s = O(nnz(A) l)) on
+// Tensor-core Gaussian sketch X = Gamma A (Algorithm 2, sketch step; Table 1, T_s = O(nnz(A) l)) on
 // sm_103a: tcgen05.mma with FP32 accumulators in tensor memory, A streamed by TMA, Gamma
 // generated in shared memory by Philox-4x32-10 + Box-Muller and never written to global
 // memory.  Operands are TF32 (kind::tf32: A read as stored, Gamma rounded to TF32) or BF16

@@ -1,6 +1,6 @@
 """Row-partitioned sketch across ranks (one process per GPU).
 
-The sketch X = Gamma A (Algorithm 2 line 2) is a sum over the rows of A: with A's rows split
+The sketch X = Gamma A (Algorithm 2, sketch step) is a sum over the rows of A: with A's rows split
 into blocks, X = sum_r Gamma(:, rows_r) A(rows_r, :).  Gamma is counter-based (its column j
 depends only on the seed and j), so each rank generates exactly the columns of Gamma that
 meet its rows and the partial sketches need one exchange: a sum all-reduce of the l x n

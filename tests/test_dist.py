@@ -1,4 +1,4 @@
-"""Row-partitioned sketch (the multi-GPU form of Algorithm 2 line 2): the partition logic and
+"""Row-partitioned sketch (the multi-GPU form of Algorithm 2's sketch step): the partition logic and
 the single sum all-reduce, run as two gloo ranks on the CPU.  The ranks' partial sketches come
 from the oracle, standing in for the device kernel (which the GPU tests check against the
 same oracle)."""

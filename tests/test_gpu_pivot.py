@@ -135,7 +135,7 @@ def test_lupp_nonfinite(skel, dev):
 
 @pytest.mark.parametrize("m,s", [(500, 20), (8192, 64), (20000, 129)])
 def test_row_lupp_on_tall_C(skel, dev, m, s):
-    """Algorithm 2 line 4: row pivots of C (column-major) via LUPP on C^T."""
+    """Algorithm 2, row pivoting: row pivots of C (column-major) via LUPP on C^T."""
     C = np.asfortranarray(np.random.default_rng(m).standard_normal((m, s)))
     Is, st = skel.pivot_lupp_rows(torch.from_numpy(C).to(dev), s)
     skel.check_status(st)
@@ -209,8 +209,8 @@ def test_lupp_very_wide_uses_grid_kernel(skel, dev):
 @pytest.mark.parametrize("l,n,m,s", [(20, 100, 120, 20), (140, 3001, 2500, 130), (60, 800, 20000, 50),
                                      (70, 500, 70, 64), (8, 300, 300, 8)])
 def test_pivot_skeleton_fp64_bit_exact(skel, dev, l, n, m, s):
-    """Algorithm 2 lines 3-4 in one call, the row LUPP pipelined behind the column LUPP (row
-    panels of a different height when C^T's panel is smaller): in FP64 the pivots and the
+    """Algorithm 2's column and row pivoting in one call, the row LUPP pipelined behind the
+    column LUPP (row panels of a different height when C^T's panel is smaller): in FP64 the pivots and the
     column LUPP's factors equal the oracle's bit for bit."""
     rng = np.random.default_rng(l + n + m + s)
     X = rng.standard_normal((l, n))

@@ -1,4 +1,4 @@
-"""GPU: the sketch X = Gamma A against the oracle (Algorithm 2 line 2)."""
+"""GPU: the sketch X = Gamma A against the oracle (Algorithm 2, sketch step)."""
 import numpy as np
 import pytest
 import scipy.sparse as sp

@@ -1,6 +1,6 @@
 """GPU: the sketch of a host-resident A streamed in column panels (skel_sketch_host) against the
 oracle and against the device sketch of the same A.  X's columns j0..j1 depend only on A's
-columns j0..j1 (Algorithm 1 line 2), so any panel width gives the same sketch up to the
+columns j0..j1 (Algorithm 1, sketch step), so any panel width gives the same sketch up to the
 summation order of the K-split."""
 import numpy as np
 import pytest

@@ -99,6 +99,6 @@ def test_cpqr_factor_reconstructs():
 
 
 def test_lupp_and_cpqr_on_row_pivots():
-    """Row-wise LUPP on C equals column-wise LUPP on C^T (Algorithm 2 line 4)."""
+    """Row-wise LUPP on C equals column-wise LUPP on C^T (Algorithm 2, row pivoting)."""
     C = _tie_free(60, 9, seed=5)
     assert np.array_equal(pivoting.lupp_rows(C, 9)["Js"], pivoting.lupp_columns(C.T, 9)["Js"])
