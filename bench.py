@@ -17,7 +17,7 @@ timed on the host cores on a bounded sample, an end-to-end number through host b
 the 8192 x 8192 (k = 256) step with the row skeletons and the CUR as extra keys.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--prec bf16]
-                  [--workload c5|c2] [--only ...]
+                  [--workload dense_65536x32768|dense_8192x8192] [--only ...]
 
 Multi-GPU: N ranks run N independent replicas (one matrix each, weak scaling) with no
 collective on the data path (the row-partitioned sketch with its one all-reduce is the
@@ -42,9 +42,9 @@ METRIC = "time-to-skeleton (ms) and A-streaming GB/s at rank k, mixed vs FP64 GP
 
 # workloads: (m, n, k, p, floor, description)
 WORKLOADS = {
-    "c5": dict(m=65536, n=32768, k=1024, p=76,
+    "dense_65536x32768": dict(m=65536, n=32768, k=1024, p=76,
                text="dense 65536x32768 fp32 (8.6 GB), sigma_j=exp(-j/200) (j<=3300) + 1e-7 floor, Haar U/V"),
-    "c2": dict(m=8192, n=8192, k=256, p=16,
+    "dense_8192x8192": dict(m=8192, n=8192, k=256, p=16,
                text="dense 8192x8192 fp32, sigma_j=1/j + 1e-6 floor, Haar U/V"),
 }
 ORACLE_SAMPLE_COLS = 1024       # bounded oracle sample: this many columns of A
@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="dense_65536x32768", choices=sorted(WORKLOADS))
     ap.add_argument("--k", type=int, default=None, help="rank (default: the workload's)")
     ap.add_argument("--p", type=int, default=None, help="oversampling (default: the workload's)")
     ap.add_argument("--prec", default="fp8", choices=["tf32", "bf16", "fp8", "f32"])
@@ -86,7 +86,8 @@ def parse():
 
 def workload_config(workload, k, p, prec):
     w = WORKLOADS[workload]
-    steps = ("LUPP on X, column ID" if workload == "c5" else "LUPP on X, row LUPP on C, column ID + stable CUR")
+    steps = ("LUPP on X, column ID" if workload == "dense_65536x32768"
+             else "LUPP on X, row LUPP on C, column ID + stable CUR")
     return {"workload": f"{w['text']}; rank k={k}, oversampling p={p} (l={k + p}); Gaussian sketch ({prec}), {steps}",
             "m": w["m"], "n": w["n"], "k": k, "l": k + p, "sketch_prec": prec,
             "l2": f"inputs larger than L2 (A is {4 * w['m'] * w['n'] / 1e6:.0f} MB; L2 129 MB)"}
@@ -98,16 +99,15 @@ def make_A(workload, device, seed, cols=None):
     import workloads
     w = WORKLOADS[workload]
     n = min(cols, w["n"]) if cols else w["n"]
-    if workload == "c5":
-        return workloads.torch_config5(device, w["m"], n, seed=seed)
-    sig = workloads.sigma_config2(min(w["m"], n))
+    if workload == "dense_65536x32768":
+        return workloads.torch_dense_exp200(device, w["m"], n, seed=seed)
+    sig = workloads.sigma_harmonic(min(w["m"], n))
     return workloads.torch_dense_spectrum(w["m"], n, sig, 1e-6 / np.sqrt(w["m"]), seed, device, torch.float32)
 
 
 def seeds(workload, rank=0):
     import workloads
-    cid = 5 if workload == "c5" else 2
-    return workloads.seed_for(cid) + rank, workloads.seed_for(cid, "gamma")
+    return workloads.seed_for(workload) + rank, workloads.seed_for(workload, "gamma")
 
 
 # ------------------------------------------------------------------------------------------
@@ -173,14 +173,16 @@ TIMED_KERNELS = ("sketch_tc", "sketch_fp8", "fp8_quantize", "gemm_tc", "lupp_pan
                  "trsm", "gemm_qr", "gemm_cur", "gemm_eta_h", "gemm_eta_sq", "gemm_simt", "transpose", "lupp_mult",
                  "trsm_ff")
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
-# the current kernel at this workload; None where no capture of the current code exists.  c5 is
-# too large to capture whole: the TF32 sketch was captured on the 65536 x 8192 slice (2.164 GB
-# read, 3.5 MB written) and scaled by the columns to the full 32768-column launch (the kernel
-# reads each column of A once); the FP8 GEMM on the same slice (612.5 MB read: the 536.9 MB of
-# A8 and Gamma's 75.5 MB of e4m3 normals; 0.15 MB written), its A8 part scaled by the columns.
-TRAFFIC_PER_LAUNCH = {"c5": {"sketch_tc_tf32": 4 * (2.164166912e9 + 3.450624e6),
+# the current kernel at this workload; None where no capture of the current code exists.
+# 65536 x 32768 is too large to capture whole: the TF32 sketch was captured on the 65536 x 8192
+# slice (2.164 GB read, 3.5 MB written) and scaled by the columns to the full 32768-column
+# launch (the kernel reads each column of A once); the FP8 GEMM on the same slice (612.5 MB
+# read: the 536.9 MB of A8 and Gamma's 75.5 MB of e4m3 normals; 0.15 MB written), its A8 part
+# scaled by the columns.
+TRAFFIC_PER_LAUNCH = {"dense_65536x32768": {"sketch_tc_tf32": 4 * (2.164166912e9 + 3.450624e6),
                              "sketch_fp8_fp8": 4 * (612513024 - 75497472 + 145408) + 75497472},
-                      "c2": {"sketch_tc": 271.9e6, "gemm_tc": 332.4e6, "lupp_panel": 3.09e6, "qr_panel": 2.15e6}}
+                      "dense_8192x8192": {"sketch_tc": 271.9e6, "gemm_tc": 332.4e6, "lupp_panel": 3.09e6,
+                                          "qr_panel": 2.15e6}}
 FP64_NOMINAL_TFLOPS = 1.25
 TENSOR_RATIO = {"bf16": 1.0, "tf32": 1.1 / 2.25, "fp8": 2.0}     # nominal dense ratios to BF16
 
@@ -366,7 +368,7 @@ def kernel_models(workload, m, n, k, l, prec, peaks, sustained, floors=None):
     a_bytes = 4.0 * m * n
     fp32_alu = (floors or {}).get("fp32_tflops") or 152 * 128 * 2 * 2.07e9 / 1e12     # TFLOP/s, FFMA
     fp64 = (floors or {}).get("fp64_tflops") or FP64_NOMINAL_TFLOPS
-    b_pan = 24 if workload == "c5" else 64
+    b_pan = 24 if workload == "dense_65536x32768" else 64
     # LUPP trailing updates: every panel reads and writes the rows below it once (4 B each way)
     trail_bytes = sum(8.0 * max(k - t0 - b_pan, 0) * n for t0 in range(0, k, b_pan))
     mod = {
@@ -380,7 +382,7 @@ def kernel_models(workload, m, n, k, l, prec, peaks, sustained, floors=None):
     }
     if prec in ("tf32", "bf16"):
         mod["sketch_tc"] = ("tensor", 2.0 * l * m * n / 1e12, tensor_peak(prec, peaks, sustained), "TFLOP/s")
-    if workload == "c2":
+    if workload == "dense_8192x8192":
         mod["trsm"] = ("alu", (4.0 * k ** 3) / 1e12, fp64, "TFLOP/s")      # U's and eta's k x k solves
     return mod
 
@@ -440,15 +442,15 @@ def run_ours(args, rank, world):
     if args.only:
         run_only(args, rank, A, skel, st, seed_G)
         return
-    if args.workload == "c2":
-        res = run_c2_step(args, rank, world, dev, A, skel, st, seed_G, headline=True)
+    if args.workload == "dense_8192x8192":
+        res = run_dense_8192_step(args, rank, world, dev, A, skel, st, seed_G, headline=True)
         if rank == 0:
             print(json.dumps(res), flush=True)
         return
-    run_c5(args, rank, world, dev, A, skel, st, seed_G, local)
+    run_dense_large(args, rank, world, dev, A, skel, st, seed_G, local)
 
 
-def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
+def run_dense_large(args, rank, world, dev, A, skel, st, seed_G, local):
     import numpy as np
     import torch
     k, p = args.k, args.p
@@ -528,7 +530,7 @@ def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
     s1.record()
     torch.cuda.synchronize()
     ser_ms = s0.elapsed_time(s1)
-    models = kernel_models("c5", m, n, k, l, prec, peaks, sustained=True, floors=floors)
+    models = kernel_models("dense_65536x32768", m, n, k, l, prec, peaks, sustained=True, floors=floors)
     kernels = kernel_table(skel, nser, ser_ms, models)
     latency_roofline(kernels, "lupp_panel", k, floors)
     skel.kernel_timing(False)
@@ -543,7 +545,7 @@ def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
         achieved = work / (kd["avg_us"] * 1e-6) / 1e12
         pk = tensor_peak(prec, peaks, sustained=True)
         roofline = {"kernel": sk_name, "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                    "frac": achieved / pk, "traffic": TRAFFIC_PER_LAUNCH["c5"].get(f"{sk_name}_{prec}"),
+                    "frac": achieved / pk, "traffic": TRAFFIC_PER_LAUNCH["dense_65536x32768"].get(f"{sk_name}_{prec}"),
                     "peak_source": (f"{peaks['source']} MEASURED_PEAKS.json bf16_tflops_sustained x {TENSOR_RATIO[prec]:.3f} "
                                     f"(nominal {prec}:bf16 dense ratio)"),
                     "frac_of_burst_peak": achieved / tensor_peak(prec, peaks, sustained=False),
@@ -645,17 +647,18 @@ def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
         torch.cuda.empty_cache()
         extra3 = run_c3(skel, dev)
         extra4 = batch_measure(skel, dev)
-        A2 = make_A("c2", dev, seeds("c2", rank)[0])
+        A2 = make_A("dense_8192x8192", dev, seeds("dense_8192x8192", rank)[0])
         a2 = argparse.Namespace(**vars(args))
-        a2.workload, a2.k, a2.p, a2.prec, a2.no_cpu = "c2", 256, 16, "tf32", True
-        extra = run_c2_step(a2, rank, world, dev, A2, skel, skel.new_status(dev), seeds("c2")[1], headline=False)
+        a2.workload, a2.k, a2.p, a2.prec, a2.no_cpu = "dense_8192x8192", 256, 16, "tf32", True
+        extra = run_dense_8192_step(a2, rank, world, dev, A2, skel, skel.new_status(dev), seeds("dense_8192x8192")[1],
+                                    headline=False)
         del A2
 
     res = {
         "metric": METRIC, "value": tts, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
-        "config": workload_config("c5", k, p, prec),
+        "config": workload_config("dense_65536x32768", k, p, prec),
         "time_to_skeleton_median_ms": tts_median,     # rank 0's steps; `value` is the mean (max over ranks)
         "time_to_id_ms": tid, "calls_ms": per,
         "a_streaming_gbs": 4.0 * m * n / (per["sketch"] * 1e-3) / 1e9,
@@ -684,7 +687,7 @@ def run_c5(args, rank, world, dev, A, skel, st, seed_G, local):
     print(json.dumps(res), flush=True)
 
 
-def run_c2_step(args, rank, world, dev, A, skel, st, seed_G, headline):
+def run_dense_8192_step(args, rank, world, dev, A, skel, st, seed_G, headline):
     """The 8192 x 8192 step: TF32 sketch -> both LUPPs pipelined (time-to-skeleton) -> column ID
     and stable CUR from one QR of C -> eta on a second stream."""
     import numpy as np
@@ -765,8 +768,8 @@ def run_c2_step(args, rank, world, dev, A, skel, st, seed_G, headline):
     s1.record()
     torch.cuda.synchronize()
     ser_ms = s0.elapsed_time(s1)
-    kernels = kernel_table(skel, nser, ser_ms, kernel_models("c2", m, n, k, l, args.prec, peaks, sustained=False,
-                                                             floors=floors))
+    models = kernel_models("dense_8192x8192", m, n, k, l, args.prec, peaks, sustained=False, floors=floors)
+    kernels = kernel_table(skel, nser, ser_ms, models)
     skel.kernel_timing(False)
     latency_roofline(kernels, "lupp_panel", 2 * k, floors)      # column LUPP on X and row LUPP on C
     modeled = [nm for nm in kernels if kernels[nm].get("bound") in ("hbm", "tensor", "alu")]
@@ -775,7 +778,7 @@ def run_c2_step(args, rank, world, dev, A, skel, st, seed_G, headline):
         dom = max(modeled, key=lambda nm: kernels[nm]["ms_per_step"])
         kd = kernels[dom]
         roofline = {"kernel": dom, "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
-                    "unit": kd["unit"], "frac": kd["frac"], "traffic": TRAFFIC_PER_LAUNCH["c2"].get(dom),
+                    "unit": kd["unit"], "frac": kd["frac"], "traffic": TRAFFIC_PER_LAUNCH["dense_8192x8192"].get(dom),
                     "peak_source": (f"{peaks['source']} MEASURED_PEAKS.json (burst)" if kd["bound"] != "alu" else
                                     "FMA rate measured in this run (skel_debug_fma_rate)"),
                     "avg_launch_us": kd["avg_us"],
@@ -848,7 +851,7 @@ def run_c2_step(args, rank, world, dev, A, skel, st, seed_G, headline):
         "metric": METRIC, "value": tts, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-        "config": workload_config("c2", k, p, args.prec),
+        "config": workload_config("dense_8192x8192", k, p, args.prec),
         "time_to_id_and_cur_ms": tcur, "a_streaming_gbs": 4.0 * m * n / (per["sketch"] * 1e-3) / 1e9,
         "sketch_tflops": 2.0 * l * m * n / (per["sketch"] * 1e-3) / 1e12, "calls_ms": per,
         "rel_id_error": rel_id, "rel_cur_error": rel_cur, "rel_id_error_gram": rel_id_gram,
@@ -875,8 +878,8 @@ def run_c3(skel, dev, steps=10, warmup=3):
     import workloads
     m, n, r, k, zeta = 262144, 4096, 300, 256, 8
     l = 2 * k
-    seed_G = workloads.seed_for(3, "gamma")
-    A = workloads.snn_csc(m, n, r, seed=workloads.seed_for(3))
+    seed_G = workloads.seed_for("snn_262144x4096", "gamma")
+    A = workloads.snn_csc(m, n, r, seed=workloads.seed_for("snn_262144x4096"))
     nnz = int(A.nnz)
     col_ptr = torch.from_numpy(A.indptr.astype(np.int64)).to(dev)
     row_idx = torch.from_numpy(A.indices.astype(np.int32)).to(dev)
@@ -1057,9 +1060,10 @@ def batch_measure(skel, dev, nblocks=4096, steps=10, warmup=3, seed_offset=0):
     import torch
     import workloads
     kmax, p, tol = 128, 16, 1e-6
-    blocks = workloads.torch_kernel_blocks(nblocks, workloads.seed_for(4) + seed_offset, dev)
+    blocks = workloads.torch_kernel_blocks(nblocks, workloads.seed_for("kernel_blocks_4096") + seed_offset, dev)
     a_bytes = sum(4 * B.shape[0] * B.shape[1] for B in blocks)
-    plan = skel.BatchPlan(blocks, kmax, p=p, tol=tol, seed=workloads.seed_for(4, "gamma"), graph=True, autotune=True)
+    plan = skel.BatchPlan(blocks, kmax, p=p, tol=tol, seed=workloads.seed_for("kernel_blocks_4096", "gamma"),
+                          graph=True, autotune=True)
     torch.cuda.synchronize()
     for _ in range(warmup):
         Js, ranks, Z, st = plan.run()
@@ -1099,12 +1103,12 @@ def batch_points_measure(skel, dev, nblocks, steps, warmup, seed_offset, a_bytes
     import torch
     import workloads
     kmax, p, tol = 128, 16, 1e-6
-    pts = workloads.kernel_points(nblocks, workloads.seed_for(4) + seed_offset)
+    pts = workloads.kernel_points(nblocks, workloads.seed_for("kernel_blocks_4096") + seed_offset)
     xs = [torch.from_numpy(x).to(dev) for x, _ in pts]
     ys = [torch.from_numpy(y).to(dev) for _, y in pts]
     entries = sum(x.shape[0] * y.shape[0] for x, y in pts)
-    plan = skel.BatchPlan.from_points(xs, ys, 0.5, kmax, p=p, tol=tol, seed=workloads.seed_for(4, "gamma"), graph=True,
-                                      autotune=True)
+    plan = skel.BatchPlan.from_points(xs, ys, 0.5, kmax, p=p, tol=tol,
+                                      seed=workloads.seed_for("kernel_blocks_4096", "gamma"), graph=True, autotune=True)
     torch.cuda.synchronize()
     for _ in range(warmup):
         Js, ranks, Z, st = plan.run()

@@ -85,8 +85,8 @@ def _check_tolerance_batch(plan, Js, ranks, Z, blocks, ref, tol):
 
 
 @pytest.mark.parametrize("nblocks,seed", [(40, 14), (320, 15)])
-def test_batch_kernel_blocks_config4_style(skel, dev, nblocks, seed):
-    """Gaussian-kernel blocks between separated point clusters (config 4's generator; 40 and 320
+def test_batch_kernel_blocks(skel, dev, nblocks, seed):
+    """Gaussian-kernel blocks between separated point clusters (the 4096-block workload's generator; 40 and 320
     blocks), stored: the checks of _check_tolerance_batch."""
     blocks = workloads.kernel_blocks(nblocks, seed=seed, mrange=(64, 1024), nrange=(64, 700))
     blocks = [B.astype(np.float64) for B in blocks]
@@ -146,8 +146,8 @@ def test_points_sketch_matches_oracle(skel, dev):
 
 
 @pytest.mark.parametrize("nblocks,seed", [(40, 14), (320, 15)])
-def test_points_plan_config4_style(skel, dev, nblocks, seed):
-    """Config 4's blocks given by their point sets (kernel_points, the draws of kernel_blocks in
+def test_points_plan_kernel_blocks(skel, dev, nblocks, seed):
+    """The kernel blocks given by their point sets (kernel_points, the draws of kernel_blocks in
     FP32): the same checks as for the stored blocks, against the oracle's blocks formed from the
     same points; the plan holds 32 bytes per point instead of the blocks."""
     pts = workloads.kernel_points(nblocks, seed=seed, mrange=(64, 1024), nrange=(64, 700))
@@ -201,7 +201,7 @@ def test_batch_graph_and_autotune_change_no_result(skel, dev):
     """A plan with the autotuner (sketch pipeline depth, LUPP classes serial or concurrent) and
     a captured CUDA graph returns exactly what a plain plan returns, on every replay, and
     re-captures when its outputs change; blocks of all three cluster classes are present."""
-    blocks = workloads.torch_kernel_blocks(96, workloads.seed_for(4) + 7, dev)
+    blocks = workloads.torch_kernel_blocks(96, workloads.seed_for("kernel_blocks_4096") + 7, dev)
     blocks[0] = torch.randn(900, 2000, device=dev).t().contiguous().t()[:, :1900]    # a 4-CTA block
     blocks[1] = torch.randn(800, 1000, device=dev).t().contiguous().t()               # a 2-CTA block
     kw = dict(p=16, tol=1e-6, seed=11)

@@ -44,7 +44,7 @@ def test_lupp_all_columns_and_one(skel, dev, dt, l, n, s):
 @pytest.mark.parametrize("m,s", [(48, 48), (300, 1), (64, 64)])
 def test_column_id_square_and_single(skel, dev, m, s):
     """C square (s = m) and a single skeleton column."""
-    A = workloads.dense_config2(m, 120, seed=m + s, dtype=np.float64)
+    A = workloads.dense_harmonic(m, 120, seed=m + s, dtype=np.float64)
     Js = np.random.default_rng(s).choice(120, s, replace=False).astype(np.int32)
     Z, sq, st = skel.column_id(torch.from_numpy(A).to(dev), torch.from_numpy(Js).to(dev))
     skel.check_status(st)
@@ -53,7 +53,7 @@ def test_column_id_square_and_single(skel, dev, m, s):
 
 
 def test_cur_single_skeleton(skel, dev):
-    A = workloads.dense_config2(200, 150, seed=3, dtype=np.float64)
+    A = workloads.dense_harmonic(200, 150, seed=3, dtype=np.float64)
     Js = torch.tensor([17], dtype=torch.int32, device=dev)
     Is, U, sq, st = skel.cur(torch.from_numpy(A).to(dev), Js)
     skel.check_status(st)

@@ -1,16 +1,16 @@
 """GPU parity at full size, in the precision and launch configuration bench.py times.
 
-Config 2 (8192 x 8192 FP32, k = 256, l = 272, TF32 sketch): the oracle runs the whole path in
+8192 x 8192 FP32 (k = 256, l = 272, TF32 sketch): the oracle runs the whole path in
 FP64 on the same A (a few seconds on the host): the device's sketch against the oracle's
 elementwise on samples (TF32 bound), the device's pivots against the oracle's LUPP of the
 device's sketch before the first near-tie at FP32 level, and the residual ||A - C Z_gpu||_F of
 the device's Z formed on the host within 1.05x of the FP64 oracle's.
 
-Config 3 (262144 x 4096 SNN-style CSC, ~1% dense, k = 256, l = 512, sparse sign with zeta = 8):
+262144 x 4096 SNN-style CSC (~1% dense, k = 256, l = 512, sparse sign with zeta = 8):
 the oracle runs end to end on the same FP32 values with scipy sparse products: the device's
 sketch elementwise, its pivots before the first near-tie, and the CUR error within 1.05x.
 
-Config 5 (65536 x 32768 FP32, k = 1024, l = 1100): too large for the oracle end to end, so the
+65536 x 32768 FP32 (k = 1024, l = 1100): too large for the oracle end to end, so the
 checks are ones that hold at any size: sampled sketch entries computed one by one by the
 oracle, the LUPP factor's structure (|R| <= 1, R(t, j_t) = 1, X(0:s, J) = L R(:, J)), the first
 two greedy pivots recomputed on the host from the device's sketch, Theorem 1's bound with the
@@ -37,12 +37,12 @@ def _rel_id(sq):
     return float(np.sqrt(max(sq[0] - sq[1], 0.0) / sq[0]))
 
 
-def test_config2_full_size_against_oracle(skel, dev):
+def test_dense_8192_full_size_against_oracle(skel, dev):
     m = n = 8192
     k, p = 256, 16
     l = k + p
-    seed_A, seed_G = workloads.seed_for(2), workloads.seed_for(2, "gamma")
-    A = workloads.torch_dense_spectrum(m, n, workloads.sigma_config2(n), 1e-6 / np.sqrt(m), seed_A, dev,
+    seed_A, seed_G = workloads.seed_for("dense_8192x8192"), workloads.seed_for("dense_8192x8192", "gamma")
+    A = workloads.torch_dense_spectrum(m, n, workloads.sigma_harmonic(n), 1e-6 / np.sqrt(m), seed_A, dev,
                                        torch.float32)
     st = skel.new_status(dev)
     X, _ = skel.sketch(A, l, prec="tf32", seed=seed_G, status=st)
@@ -80,13 +80,13 @@ def test_config2_full_size_against_oracle(skel, dev):
     assert e_host <= 1.05 * e_or, (e_host, e_or)
 
 
-def test_config5_full_size_properties(skel, dev):
+def test_dense_65536x32768_full_size_properties(skel, dev):
     m, n = 65536, 32768
     k, p = 1024, 76
     l = k + p
     r_eff = 3300                       # exp(-3300/200) < 1e-7: the spectrum below is the floor
-    seed_A, seed_G = workloads.seed_for(5), workloads.seed_for(5, "gamma")
-    sig = workloads.sigma_config5(r_eff)
+    seed_A, seed_G = workloads.seed_for("dense_65536x32768"), workloads.seed_for("dense_65536x32768", "gamma")
+    sig = workloads.sigma_exp200(r_eff)
     g = torch.Generator(device=dev)
     g.manual_seed(seed_A)
     with torch.no_grad():
@@ -172,7 +172,7 @@ def test_config5_full_size_properties(skel, dev):
     assert rel_direct <= 1.05 * float(e64[1] / e64[0]), (rel_direct, float(e64[1] / e64[0]))
 
 
-def test_config5_fp8_sketch_full_size(skel, dev):
+def test_dense_65536x32768_fp8_sketch(skel, dev):
     """The FP8 sketch bench.py times by default, at 65536 x 32768 on the bench's A and seeds:
     sampled entries one by one against the oracle's FP8 sketch (e4m3 normals; each column of A
     in e4m3 with its power-of-two scale), with the bound of the smaller FP8 tests, and the
@@ -181,8 +181,8 @@ def test_config5_fp8_sketch_full_size(skel, dev):
     m, n = 65536, 32768
     k, p = 1024, 76
     l = k + p
-    seed_G = workloads.seed_for(5, "gamma")
-    A = workloads.torch_config5(dev, m, n, seed=workloads.seed_for(5))
+    seed_G = workloads.seed_for("dense_65536x32768", "gamma")
+    A = workloads.torch_dense_exp200(dev, m, n, seed=workloads.seed_for("dense_65536x32768"))
     st = skel.new_status(dev)
     X, _ = skel.sketch(A, l, prec="fp8", seed=seed_G, status=st)
     Js, _, _, _ = skel.pivot_lupp(X, k, factors=False, status=st)
@@ -218,11 +218,11 @@ def test_config5_fp8_sketch_full_size(skel, dev):
     assert rel8 <= 1.05 * float(e64[1] / e64[0]), (rel8, float(e64[1] / e64[0]))
 
 
-def test_config3_full_size_sparse_sign_and_cur(skel, dev):
+def test_snn_262144x4096_sparse_sign_and_cur(skel, dev):
     m, n, r = 262144, 4096, 300
     k, l, zeta = 256, 512, 8
-    seed_G = workloads.seed_for(3, "gamma")
-    A = workloads.snn_csc(m, n, r, seed=workloads.seed_for(3))          # FP32 CSC, ~1% dense
+    seed_G = workloads.seed_for("snn_262144x4096", "gamma")
+    A = workloads.snn_csc(m, n, r, seed=workloads.seed_for("snn_262144x4096"))          # FP32 CSC, ~1% dense
     col_ptr = torch.from_numpy(A.indptr.astype(np.int64)).to(dev)
     row_idx = torch.from_numpy(A.indices.astype(np.int32)).to(dev)
     val = torch.from_numpy(A.data.astype(np.float32)).to(dev)

@@ -18,7 +18,8 @@ def _js(A, k, p, seed):
 @pytest.mark.parametrize("m,n,k", [(1000, 800, 50), (300, 200, 20), (257, 129, 1), (640, 130, 128)])
 def test_id_fp64_matches_oracle(skel, dev, m, n, k):
     """FP64 mode, same J_s: ||Z_gpu - Z_or||_F <= 1e-10 ||Z_or||_F, Z(:, Js) = I."""
-    A = workloads.config1(m, n, seed=m) if k > 1 else np.asfortranarray(np.random.default_rng(0).standard_normal((m, n)))
+    A = (workloads.dense_geometric40(m, n, seed=m) if k > 1
+         else np.asfortranarray(np.random.default_rng(0).standard_normal((m, n))))
     Js = _js(A, k, 10 if k + 10 <= n else 0, 1)["Js"]
     C = A[:, Js]
     kappa = np.linalg.cond(C)
@@ -37,7 +38,7 @@ def test_id_fp64_matches_oracle(skel, dev, m, n, k):
 
 def test_id_fp32_error_within_gate(skel, dev):
     """FP32 QR / FP32 Q^T A / FP64 solve: the ID error stays within 1.05x of the oracle's."""
-    A = workloads.dense_config2(2048, 1536, seed=4)
+    A = workloads.dense_harmonic(2048, 1536, seed=4)
     Ad = A.astype(np.float64)
     Js = _js(Ad, 128, 16, 2)["Js"]
     Z, _, st = skel.column_id(torch.from_numpy(A).to(dev), torch.from_numpy(Js.astype(np.int32)).to(dev))
@@ -65,7 +66,7 @@ def test_exact_rank_reconstruction_fp64(skel, dev):
 
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 def test_cur_matches_oracle(skel, dev, dt):
-    A = workloads.config1(600, 500, seed=8).astype(dt)
+    A = workloads.dense_geometric40(600, 500, seed=8).astype(dt)
     Ad = A.astype(np.float64)
     k = 30
     Js = _js(Ad, k, 10, 3)["Js"]
@@ -86,7 +87,7 @@ def test_cur_matches_oracle(skel, dev, dt):
 
 @pytest.mark.parametrize("pivot", ["lupp", "cpqr"])
 def test_error_and_eta_match_oracle(skel, dev, pivot):
-    A = workloads.dense_config2(700, 500, seed=6, dtype=np.float64)
+    A = workloads.dense_harmonic(700, 500, seed=6, dtype=np.float64)
     k, l = 40, 50
     X = sketch.gaussian_sketch(A, l, 9)
     piv = pivoting.lupp_columns(X, k) if pivot == "lupp" else pivoting.cpqr_columns(X, k)
@@ -107,11 +108,11 @@ def test_error_and_eta_match_oracle(skel, dev, pivot):
     assert e[1] <= e[3] * errors.rangefinder_error(A, piv["R"]) * (1 + 1e-10)
 
 
-def test_end_to_end_fp64_config1(skel, dev):
-    """Config 1 (1000 x 800, k = 50, p = 10): the whole FP64 device pipeline equals the
+def test_end_to_end_fp64_1000x800(skel, dev):
+    """1000 x 800 FP64 (k = 50, p = 10): the whole FP64 device pipeline equals the
     oracle's skeleton, Z within 1e-10, errors within 1.05x."""
-    A = workloads.config1()
-    k, p, seed = 50, 10, workloads.seed_for(1, "gamma")
+    A = workloads.dense_geometric40()
+    k, p, seed = 50, 10, workloads.seed_for("dense_1000x800", "gamma")
     out = skel.skeletonize(torch.from_numpy(A).to(dev), k, p, seed=seed, prec="f64")
     torch.cuda.synchronize()
     skel.check_status(out["status"])
@@ -151,7 +152,7 @@ def test_column_id_from_sketch(skel, dev, dt):
     least-squares solution on the same sketch: Z(:, J) = I exactly, the rest within the
     precision of the Householder QR (FP64; FP32 within 50 cond(X(:, J)) u_32); the ID from the
     sketch is never better than C^+ A."""
-    A = workloads.dense_config2(600, 400, seed=12, dtype=np.float64)
+    A = workloads.dense_harmonic(600, 400, seed=12, dtype=np.float64)
     k, l = 30, 40
     X = sketch.gaussian_sketch(A, l, 5).astype(dt)
     Xt = torch.from_numpy(X).to(dev)
@@ -174,7 +175,7 @@ def test_mixed_path_z_accuracy(skel, dev):
     """The mixed path's Z (FP32 Householder QR, 3xTF32 W, FP64 solve) against the FP64 oracle's
     Z on the same skeleton: within a small multiple of cond(C) u_32 (stated per result; no
     FP64 refinement step)."""
-    A = workloads.dense_config2(2048, 1500, seed=11, dtype=np.float32)
+    A = workloads.dense_harmonic(2048, 1500, seed=11, dtype=np.float32)
     Ad = A.astype(np.float64)
     At = torch.from_numpy(np.asfortranarray(A)).to(dev)
     X, _ = skel.sketch(At, 80, prec="tf32", seed=3)
@@ -194,7 +195,7 @@ def test_column_sketch(skel, dev, prec, m, n):
     to rounding; TF32 / BF16 by the tensor-core sketch on a transposed copy of A, within the
     operand rounding (2^-9 / 2^-7 relative per product) plus FP32 accumulation."""
     dt = np.float64 if prec == "f64" else np.float32
-    A = workloads.dense_config2(m, n, seed=4, dtype=dt)
+    A = workloads.dense_harmonic(m, n, seed=4, dtype=dt)
     Yt, st = skel.sketch_cols(torch.from_numpy(A).to(dev), 37, prec=prec, seed=9)
     skel.check_status(st)
     want = sketch.gaussian_col_sketch(A.astype(np.float64), 37, 9)
@@ -209,7 +210,7 @@ def test_streaming_skeleton_selection(skel, dev):
     """Algorithm 3 on the device (X = Gamma A, Y = A Omega^T, LUPP on X and on Y^T) against
     the oracle's: the same row and column skeletons in FP64 before the first near-tie, and a
     CUR error within 1.05x of the oracle's."""
-    A = workloads.dense_config2(600, 500, seed=5, dtype=np.float64)
+    A = workloads.dense_harmonic(600, 500, seed=5, dtype=np.float64)
     k, p = 30, 10
     Js, Is, st = skel.skeletonize_streaming(torch.from_numpy(A).to(dev), k, p, seed=7, seed_omega=8, prec="f64")
     torch.cuda.synchronize()
@@ -230,7 +231,7 @@ def test_cur_sketch_core(skel, dev, dt, m, n, k):
     """The sketch-only CUR core U = A(Is, Js)^{-1} (Sec. 4) against the oracle's inverse, on
     the oracle's skeletons: within a condition-number multiple of the storage precision, and
     C U R reproducing A's skeleton rows and columns."""
-    A = workloads.dense_config2(m, n, seed=3, dtype=np.float64).astype(dt)
+    A = workloads.dense_harmonic(m, n, seed=3, dtype=np.float64).astype(dt)
     Ad = A.astype(np.float64)
     ref = oracle.skeleton.skeletonize(Ad, k=k, p=8, seed=4)
     Js, Is = ref["Js"], ref["Is"]
@@ -251,7 +252,7 @@ def test_cur_sketch_core(skel, dev, dt, m, n, k):
 def test_streaming_selection_tensor_cores(skel, dev):
     """Algorithm 3 with both sketches on the tensor cores (TF32): the CUR error of the
     device's skeletons within 1.05x of the FP64 oracle's."""
-    A = workloads.dense_config2(1200, 1000, seed=5, dtype=np.float32)
+    A = workloads.dense_harmonic(1200, 1000, seed=5, dtype=np.float32)
     k, p = 40, 10
     Js, Is, st = skel.skeletonize_streaming(torch.from_numpy(A).to(dev), k, p, seed=7, seed_omega=8, prec="tf32")
     torch.cuda.synchronize()
@@ -271,11 +272,11 @@ def test_id_cur_equals_separate_calls(skel, dev, dt, m, n, k):
     returns exactly what skel_id and skel_cur return separately, and the ID matches the
     oracle's."""
     if m == 8192:
-        A = workloads.torch_dense_spectrum(m, n, workloads.sigma_config2(n), 1e-6 / np.sqrt(m),
-                                           workloads.seed_for(2), dev, torch.float32)
+        A = workloads.torch_dense_spectrum(m, n, workloads.sigma_harmonic(n), 1e-6 / np.sqrt(m),
+                                           workloads.seed_for("dense_8192x8192"), dev, torch.float32)
         X, st = skel.sketch(A, k + 16, prec="tf32", seed=3)
     else:
-        A = torch.from_numpy(np.asfortranarray(workloads.dense_config2(m, n, seed=2, dtype=dt))).to(dev)
+        A = torch.from_numpy(np.asfortranarray(workloads.dense_harmonic(m, n, seed=2, dtype=dt))).to(dev)
         X, st = skel.sketch(A, k + 10, prec="f64" if dt == np.float64 else "f32", seed=3)
     Js, Is, _, _, _ = skel.pivot_skeleton(X, A, k, status=st)
     Z1, sq1, _ = skel.column_id(A, Js, status=st)
@@ -300,7 +301,7 @@ def test_refined_z_accuracy(skel, dev, m, n, k):
     Frobenius), at least 100x closer than before; Z(:, J) = I exactly.  Measured: 7.9e-6 ->
     5.6e-9 at 4096^2, s = 256, cond(C) = 337.  (m = 1001 leaves the tensor-core W for the SIMT
     path.)"""
-    A = workloads.dense_config2(m, n, seed=11, dtype=np.float32)
+    A = workloads.dense_harmonic(m, n, seed=11, dtype=np.float32)
     Ad = A.astype(np.float64)
     At = torch.from_numpy(np.asfortranarray(A)).to(dev)
     X, _ = skel.sketch(At, k + 16, prec="tf32" if m % 4 == 0 else "f32", seed=3)
@@ -325,7 +326,7 @@ def test_refined_u_accuracy(skel, dev, m, n, k):
     seminormal equations, C^T A, C^T C and R R^T from exact FP32 products in float-float sums)
     takes U to within u_32 of the FP64 oracle's U on the same skeletons (relative, Frobenius),
     at least 100x closer than the unrefined mixed-path U."""
-    A = workloads.dense_config2(m, n, seed=11, dtype=np.float32)
+    A = workloads.dense_harmonic(m, n, seed=11, dtype=np.float32)
     Ad = A.astype(np.float64)
     At = torch.from_numpy(np.asfortranarray(A)).to(dev)
     X, _ = skel.sketch(At, k + 16, prec="tf32", seed=3)

@@ -231,8 +231,8 @@ def test_pivot_skeleton_fp32_equals_separate_calls(skel, dev, prec):
     returns exactly the pivots and factors of skel_pivot_lupp followed by skel_pivot_rows."""
     m = n = 8192
     k, l = 256, 272
-    A = workloads.torch_dense_spectrum(m, n, workloads.sigma_config2(n), 1e-6 / np.sqrt(m), workloads.seed_for(2),
-                                       dev, torch.float32)
+    A = workloads.torch_dense_spectrum(m, n, workloads.sigma_harmonic(n), 1e-6 / np.sqrt(m),
+                                       workloads.seed_for("dense_8192x8192"), dev, torch.float32)
     X, st = skel.sketch(A, l, prec=prec, seed=5)
     Js1, L1, R1, _ = skel.pivot_lupp(X, k, status=st)
     Is1, _ = skel.pivot_rows(A, Js1, status=st)

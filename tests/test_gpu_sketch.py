@@ -18,7 +18,7 @@ def _bound(l, m, seed, A, u):
 
 @pytest.mark.parametrize("m,n,l", [(300, 200, 30), (1000, 777, 61), (129, 1, 5), (64, 300, 1)])
 def test_sketch_fp64(skel, dev, m, n, l):
-    A = workloads.config1(m, n, seed=m + n) if m >= n else np.random.default_rng(1).standard_normal((m, n))
+    A = workloads.dense_geometric40(m, n, seed=m + n) if m >= n else np.random.default_rng(1).standard_normal((m, n))
     A = np.asfortranarray(A)
     X, st = skel.sketch(torch.from_numpy(A).to(dev), l, prec="f64", seed=42)
     skel.check_status(st)
@@ -28,7 +28,7 @@ def test_sketch_fp64(skel, dev, m, n, l):
 
 @pytest.mark.parametrize("m,n,l", [(512, 300, 40), (1000, 130, 80)])
 def test_sketch_fp32(skel, dev, m, n, l):
-    A = workloads.dense_config2(m, n, seed=3)                 # FP32 storage
+    A = workloads.dense_harmonic(m, n, seed=3)                 # FP32 storage
     X, st = skel.sketch(torch.from_numpy(A).to(dev), l, prec="f32", seed=5)
     skel.check_status(st)
     want = sketch.gaussian_sketch(A.astype(np.float64), l, 5, operand_rounding="fp32")
@@ -121,7 +121,7 @@ def test_sketch_tf32_tensor_cores(skel, dev, m, n, l):
     """tcgen05 kind::tf32 sketch: Gamma is rounded to TF32 in the kernel and A is read by the
     tensor core as TF32 (at most 2^-10 relative per operand); accumulation is FP32.  Bound:
     |dX| <= (2^-9 + m 2^-23) (|G| |A|) / sqrt(l) elementwise against the exact FP64 sketch."""
-    A = workloads.dense_config2(m, n, seed=m + l)
+    A = workloads.dense_harmonic(m, n, seed=m + l)
     X, st = skel.sketch(torch.from_numpy(A).to(dev), l, prec="tf32", seed=77)
     skel.check_status(st)
     Ad = A.astype(np.float64)
@@ -154,7 +154,7 @@ def test_sketch_bf16_tensor_cores(skel, dev, m, n, l):
     BF16-operand sketch (FP64 normals rounded to BF16).  The two Gammas differ by one BF16 ulp
     (2^-7 relative) where the FP32 normal sits within a few FP32 ulps of a BF16 rounding
     boundary (about 1 entry in 10^4); at most two such entries per row are allowed for."""
-    A = workloads.dense_config2(m, n, seed=m + l + 1)
+    A = workloads.dense_harmonic(m, n, seed=m + l + 1)
     X, st = skel.sketch(torch.from_numpy(A).to(dev), l, prec="bf16", seed=78)
     skel.check_status(st)
     Ad = A.astype(np.float64)
@@ -235,7 +235,7 @@ def test_sketch_power_iteration(skel, dev, prec, q, m, n):
     iteration -- the sketch's own precision, which is all pivot selection uses."""
     l = 40
     dt = np.float64 if prec == "f64" else np.float32
-    A = workloads.dense_config2(m, n, seed=31, dtype=dt)
+    A = workloads.dense_harmonic(m, n, seed=31, dtype=dt)
     X, st = skel.sketch_power(torch.from_numpy(A).to(dev), l, q=q, prec=prec, seed=17)
     skel.check_status(st)
     want = sketch.gaussian_sketch_power(A.astype(np.float64), l, 17, q)
@@ -251,7 +251,7 @@ def test_sketch_fp8_tensor_cores(skel, dev, m, n, l):
     sketch (FP64 normals rounded to e4m3, the same scales).  An FP32 normal near an e4m3
     rounding boundary can round one e4m3 step (2^-3 relative) away from the FP64 one; two
     such entries per row are allowed for."""
-    A = workloads.dense_config2(m, n, seed=m + 2 * l, dtype=np.float32)
+    A = workloads.dense_harmonic(m, n, seed=m + 2 * l, dtype=np.float32)
     X, st = skel.sketch(torch.from_numpy(A).to(dev), l, prec="fp8", seed=79)
     skel.check_status(st)
     Ad = A.astype(np.float64)
@@ -273,7 +273,7 @@ def test_sketch_fp8_tall_columns(skel, dev, m, n, l):
     column's would be off by a factor near 8.  m = 16384 and 16385 straddle one block,
     131072 is the tallest clustered column (8 blocks), 140000 the two-pass path for taller
     ones.  Same bound as the FP8 test above."""
-    A = workloads.dense_config2(m, n, seed=m % 1000 + l, dtype=np.float32)
+    A = workloads.dense_harmonic(m, n, seed=m % 1000 + l, dtype=np.float32)
     b = (m + 16383) // 16384
     for j in range(n):
         q = j % b

@@ -36,7 +36,7 @@ def test_sketch_host_fp64_panels(skel, dev, panel):
 def test_sketch_host_single_precision(skel, dev, prec, m, n, l, panel):
     """Pinned host A, m not a multiple of 4 (the staging columns are padded): the oracle's bound
     for the precision, and agreement with skel.sketch on the device copy."""
-    A = torch.from_numpy(workloads.dense_config2(m, n, seed=m + l)).pin_memory()
+    A = torch.from_numpy(workloads.dense_harmonic(m, n, seed=m + l)).pin_memory()
     X, st = skel.sketch_host(A, l, prec=prec, seed=77, panel=panel)
     Xd, std = skel.sketch(A.to(dev), l, prec=prec, seed=77)
     skel.check_status(st)
@@ -55,7 +55,7 @@ def test_sketch_host_fp8(skel, dev):
     """FP8: the scales are per column, so a column panel scales exactly as the whole matrix
     does."""
     m, n, l = 1000, 1200, 61
-    A = torch.from_numpy(workloads.dense_config2(m, n, seed=5, dtype=np.float32)).pin_memory()
+    A = torch.from_numpy(workloads.dense_harmonic(m, n, seed=5, dtype=np.float32)).pin_memory()
     X, st = skel.sketch_host(A, l, prec="fp8", seed=79, panel=256)
     Xd, std = skel.sketch(A.to(dev), l, prec="fp8", seed=79)
     skel.check_status(st)
@@ -113,7 +113,7 @@ def test_sketch_host_then_pivots(skel, dev):
     """The skeleton from the streamed sketch equals the one from the device sketch (FP64: the
     two sketches agree to rounding and the pivots' gaps are far above it)."""
     m, n, l, k = 2000, 1500, 40, 30
-    A = np.asfortranarray(workloads.config1(m, n, seed=11))
+    A = np.asfortranarray(workloads.dense_geometric40(m, n, seed=11))
     X, st = skel.sketch_host(torch.from_numpy(A), l, prec="f64", seed=5, panel=512)
     Xd, std = skel.sketch(torch.from_numpy(A).to(dev), l, prec="f64", seed=5)
     J, _, _, _ = skel.pivot_lupp(X, k, factors=False, status=st)
@@ -157,7 +157,7 @@ def test_streaming_selection_host_one_pass(skel, dev):
     """Algorithm 3 on a host A in one pass: the same row and column skeletons as the oracle's
     in FP64 before the first near-tie (the oracle forms both sketches from the whole A)."""
     from oracle import skeleton
-    A = np.asfortranarray(workloads.dense_config2(600, 500, seed=5, dtype=np.float64))
+    A = np.asfortranarray(workloads.dense_harmonic(600, 500, seed=5, dtype=np.float64))
     k, p = 30, 10
     Js, Is, st = skel.skeletonize_streaming_host(torch.from_numpy(A), k, p, seed=7, seed_omega=8, prec="f64",
                                                  panel=128)

@@ -39,7 +39,7 @@ def test_srtt_fp64(skel, dev, m, n, l):
 
 @pytest.mark.parametrize("m,n,l", [(512, 300, 40), (1000, 130, 80), (333, 50, 333)])
 def test_srtt_fp32(skel, dev, m, n, l):
-    A = workloads.dense_config2(m, n, seed=3)
+    A = workloads.dense_harmonic(m, n, seed=3)
     X, st = skel.sketch(torch.from_numpy(A).to(dev), l, kind="srtt", prec="f32", seed=5)
     skel.check_status(st)
     Ad = A.astype(np.float64)
@@ -56,7 +56,7 @@ def test_srtt_fp32(skel, dev, m, n, l):
 def test_srtt_tensor_cores(skel, dev, prec, m, n, l):
     """The tcgen05 sketch with Gamma's tiles generated from the SRTT tables: TF32 operands
     (2^-10 relative each) or BF16 (2^-8 each), FP32 accumulation."""
-    A = workloads.dense_config2(m, n, seed=m + l)
+    A = workloads.dense_harmonic(m, n, seed=m + l)
     X, st = skel.sketch(torch.from_numpy(A).to(dev), l, kind="srtt", prec=prec, seed=77)
     skel.check_status(st)
     Ad = A.astype(np.float64)
@@ -72,8 +72,8 @@ def test_srtt_full_size_sampled(skel, dev):
     """8192 x 8192 FP32, l = 272, TF32: sampled entries against rows of the oracle's Gamma."""
     m = n = 8192
     l = 272
-    A = workloads.torch_dense_spectrum(m, n, workloads.sigma_config2(n), 1e-6 / np.sqrt(m), workloads.seed_for(2),
-                                       dev, torch.float32)
+    A = workloads.torch_dense_spectrum(m, n, workloads.sigma_harmonic(n), 1e-6 / np.sqrt(m),
+                                       workloads.seed_for("dense_8192x8192"), dev, torch.float32)
     X, st = skel.sketch(A, l, kind="srtt", prec="tf32", seed=9)
     torch.cuda.synchronize()
     skel.check_status(st)
@@ -91,7 +91,7 @@ def test_srtt_full_size_sampled(skel, dev):
 def test_srtt_skeleton_pivots_match_oracle(skel, dev):
     """Algorithm 2 with the SRTT sketch in FP64: the device's pivots equal the oracle's before
     the first near-tie."""
-    A = workloads.config1(600, 500, seed=8)
+    A = workloads.dense_geometric40(600, 500, seed=8)
     k, p = 40, 10
     X, st = skel.sketch(torch.from_numpy(np.asfortranarray(A)).to(dev), k + p, kind="srtt", prec="f64", seed=3)
     Js, _, _, _ = skel.pivot_lupp(X, k, factors=False, status=st)

@@ -73,9 +73,9 @@ def test_peaks_fallback_and_workload_config():
     b = _bench()
     hbm, bf16, src = b.load_peaks()
     assert hbm > 1000 and bf16 > 100 and src in ("measured", "fallback")
-    cfg = b.workload_config("c2", 256, 16, "tf32")
+    cfg = b.workload_config("dense_8192x8192", 256, 16, "tf32")
     assert cfg["m"] == cfg["n"] == 8192 and cfg["l"] == 272 and "workload" in cfg
-    cfg = b.workload_config("c5", 1024, 76, "bf16")
+    cfg = b.workload_config("dense_65536x32768", 1024, 76, "bf16")
     assert (cfg["m"], cfg["n"], cfg["k"], cfg["l"]) == (65536, 32768, 1024, 1100)
     assert b.tensor_peak("tf32", {"bf16_tflops": 2250.0, "bf16_tflops_sustained": 1800.0}, False) == pytest.approx(1100.0)
     assert b.tensor_peak("fp8", {"bf16_tflops": 2250.0, "bf16_tflops_sustained": 1800.0}, True) == pytest.approx(3600.0)
@@ -89,7 +89,7 @@ def test_recorded_traffic_is_the_algorithmic_bytes():
     b = _bench()
     m, n, l = 65536, 32768, 1100
     lpad = (l + 127) // 128 * 128
-    t5 = b.TRAFFIC_PER_LAUNCH["c5"]
+    t5 = b.TRAFFIC_PER_LAUNCH["dense_65536x32768"]
     assert t5["sketch_tc_tf32"] == pytest.approx(4.0 * m * n, rel=0.01)
     assert t5["sketch_fp8_fp8"] == pytest.approx(1.0 * m * n + lpad * m, rel=0.01)
-    assert b.TRAFFIC_PER_LAUNCH["c2"]["sketch_tc"] == pytest.approx(4.0 * 8192 * 8192, rel=0.02)
+    assert b.TRAFFIC_PER_LAUNCH["dense_8192x8192"]["sketch_tc"] == pytest.approx(4.0 * 8192 * 8192, rel=0.02)

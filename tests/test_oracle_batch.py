@@ -62,7 +62,7 @@ def test_sketch_id_uses_the_oversampling_rows():
     assert np.linalg.norm(X - X1 @ Z_ls) < np.linalg.norm(X - X1 @ Z_tr)
     r_ls, r_tr = [], []
     for seed in range(12):
-        A = workloads.dense_config2(300, 200, seed=seed, dtype=np.float64)
+        A = workloads.dense_harmonic(300, 200, seed=seed, dtype=np.float64)
         Xs = sketch.gaussian_sketch(A, 40, 100 + seed)
         J = pivoting.lupp_columns(Xs, 25)["Js"]
         C = A[:, J]
@@ -85,7 +85,7 @@ def test_sketch_id_exact_on_exactly_low_rank_input():
 def test_sketch_id_not_better_than_least_squares():
     """C^+ A minimises ||A - C Z||_F: the sketch-only Z can only do worse (or equal)."""
     rng = np.random.default_rng(2)
-    A = workloads.dense_config2(400, 300, seed=9, dtype=np.float64)
+    A = workloads.dense_harmonic(400, 300, seed=9, dtype=np.float64)
     l, k = 40, 25
     X = sketch.gaussian_sketch(A, l, 4)
     Js = pivoting.lupp_columns(X, k)["Js"]

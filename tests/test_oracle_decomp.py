@@ -10,7 +10,7 @@ import workloads
 
 def test_id_interpolates_skeleton_columns():
     """Z(:, Js) = I for linearly independent skeleton columns (Eq. (2.1))."""
-    A = workloads.config1(200, 150, seed=3)
+    A = workloads.dense_geometric40(200, 150, seed=3)
     Js = np.array([5, 17, 3, 100, 42])
     Z = decomp.column_id(A, Js)
     assert np.allclose(Z[:, Js], np.eye(5), atol=1e-10)
@@ -43,7 +43,7 @@ def test_exact_rank_reconstruction():
 def test_remark1_sandwich():
     """Remark 1: ||A - CC^+A|| <= ||A - CUR|| <= sqrt(||A - CC^+A||^2 + ||A - AR^+R||^2),
     Frobenius and spectral norms."""
-    A = workloads.config1(120, 90, seed=4)
+    A = workloads.dense_geometric40(120, 90, seed=4)
     out = skeleton.skeletonize(A, k=20, p=5, seed=2)
     Js, Is, Z, U = out["Js"], out["Is"], out["Z"], out["U"]
     C, Rm = A[:, Js], A[Is, :]
@@ -70,7 +70,7 @@ def test_theorem1_bound_and_eta_formula():
     """Theorem 1: ||A - CC^+A||_F <= eta ||A - A Xt^+ Xt||_F with Xt = R^LU(0:s, :), and
     eta = ||I - P_X||_2 for the oblique projector P_X = Pi_1 Xt_1^{-1} Xt (brute force)."""
     for seed in range(5):
-        A = workloads.dense_config2(150, 120, seed=seed, dtype=np.float64)
+        A = workloads.dense_harmonic(150, 120, seed=seed, dtype=np.float64)
         X = sketch.gaussian_sketch(A, 26, seed=100 + seed)
         piv = pivoting.lupp_columns(X, 20)
         Js, R = piv["Js"], piv["R"]
@@ -89,7 +89,7 @@ def test_theorem1_bound_and_eta_formula():
 
 def test_theorem1_bound_cpqr():
     """Theorem 1 with CPQR pivots, Xt = R^QR(0:s, :)."""
-    A = workloads.dense_config2(140, 100, seed=9, dtype=np.float64)
+    A = workloads.dense_harmonic(140, 100, seed=9, dtype=np.float64)
     X = sketch.gaussian_sketch(A, 30, seed=1)
     piv = pivoting.cpqr_columns(X, 24)
     Z = decomp.column_id(A, piv["Js"])
@@ -115,7 +115,7 @@ def test_volume_sampling_existence_brute_force():
 def test_rangefinder_expectation_bound():
     """Eq. (2.7): E||A - A X^+ X||_F^2 <= (l-1)/(l-k-1) ||A - A_k||_F^2 for Gaussian
     sketches (mean over 200 seeds, 10% slack for sampling error)."""
-    A = workloads.dense_config2(60, 50, seed=1, dtype=np.float64)
+    A = workloads.dense_harmonic(60, 50, seed=1, dtype=np.float64)
     k, l = 6, 12
     vals = [errors.rangefinder_error(A, sketch.gaussian_sketch(A, l, seed=s)) ** 2 for s in range(200)]
     bound = (l - 1) / (l - k - 1) * errors.best_rank_k_error(A, k) ** 2
@@ -123,7 +123,7 @@ def test_rangefinder_expectation_bound():
 
 
 def test_sparse_sign_skeleton_runs_and_is_close_to_optimal():
-    A = workloads.dense_config2(400, 200, seed=2, dtype=np.float64)
+    A = workloads.dense_harmonic(400, 200, seed=2, dtype=np.float64)
     out = skeleton.skeletonize(A, k=20, p=20, seed=4, kind="sparse_sign", zeta=8)
     opt = errors.best_rank_k_error(A, 20) / errors.fro(A)
     assert opt <= out["err_id"] < 3 * opt
@@ -143,7 +143,7 @@ def test_streaming_selection_two_sided_bound():
     eta_Y ||A - Yt^T (Yt^T)^+ A||_F, with Xt, Yt the LU factors of the row and the transposed
     column sketch and eta from each factor."""
     for seed in range(4):
-        A = workloads.dense_config2(200, 160, seed=seed, dtype=np.float64)
+        A = workloads.dense_harmonic(200, 160, seed=seed, dtype=np.float64)
         k = 15
         out = skeleton.streaming_skeletonize(A, k, 10, 10 + seed, 20 + seed)
         err = np.linalg.norm(A - A[:, out["Js"]] @ out["U"] @ A[out["Is"], :])
@@ -180,7 +180,7 @@ def test_cur_sketch_exact_on_exactly_low_rank():
 def test_cur_sketch_never_beats_the_optimal_core():
     """U = C^+ A R^+ minimises ||A - C U R||_F over all U (Eq. (2.4)), so the sketch-only
     core S^{-1} is never better; on a decaying spectrum it stays within a modest factor."""
-    A = workloads.config1(160, 120, seed=5)
+    A = workloads.dense_geometric40(160, 120, seed=5)
     out = skeleton.skeletonize(A, k=20, p=8, seed=2)
     Js, Is = out["Js"], out["Is"]
     C, Rm = A[:, Js], A[Is, :]

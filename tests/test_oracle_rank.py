@@ -18,7 +18,7 @@ def test_exact_rank_is_found():
 def test_estimate_is_unbiased_for_oblique_residual():
     """E ||S_t||_F^2 l/(l-t) = ||A (I - P_t)||_F^2 with P_t = Pi_1 X_1^{-1} X(0:t, :) (proof
     of Theorem 1): the mean ratio over 150 seeds is 1 within sampling error."""
-    A = workloads.dense_config2(120, 80, seed=3, dtype=np.float64)
+    A = workloads.dense_harmonic(120, 80, seed=3, dtype=np.float64)
     l, t = 20, 8
     ratios = []
     for s in range(150):
@@ -37,7 +37,7 @@ def test_estimate_is_unbiased_for_oblique_residual():
 
 
 def test_tolerance_monotone():
-    A = workloads.dense_config2(200, 150, seed=4, dtype=np.float64)
+    A = workloads.dense_harmonic(200, 150, seed=4, dtype=np.float64)
     X = sketch.gaussian_sketch(A, 60, seed=5)
     ranks = [rank.lupp_tolerance_rank(X, kmax=40, tol=tol)["rank"] for tol in (0.5, 0.2, 0.1, 0.05)]
     assert ranks == sorted(ranks) and ranks[0] < ranks[-1]

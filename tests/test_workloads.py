@@ -6,9 +6,9 @@ import torch
 import workloads
 
 
-def test_config1_spectrum():
+def test_geometric40_spectrum():
     """sigma_j = 10^(-(j-1)/40) plus a 1e-12 Gaussian floor."""
-    A = workloads.config1(200, 150, seed=1)
+    A = workloads.dense_geometric40(200, 150, seed=1)
     s = np.linalg.svd(A, compute_uv=False)
     want = 10.0 ** (-np.arange(150) / 40.0)
     big = want > 1e-9
@@ -16,15 +16,15 @@ def test_config1_spectrum():
     assert A.dtype == np.float64 and A.flags.f_contiguous
 
 
-def test_config2_spectrum_and_floor():
+def test_harmonic_spectrum_and_floor():
     """sigma_j = 1/j above a noise floor of about 1e-6 (FP32 storage)."""
     m, n = 400, 300
-    A = workloads.dense_config2(m, n, seed=2, dtype=np.float64)
+    A = workloads.dense_harmonic(m, n, seed=2, dtype=np.float64)
     s = np.linalg.svd(A, compute_uv=False)
     want = 1.0 / np.arange(1, n + 1)
     assert np.allclose(s[:50], want[:50], rtol=1e-3)
     assert s.min() > 1e-7                       # the floor lifts the tail ...
-    A32 = workloads.dense_config2(m, n, seed=2)
+    A32 = workloads.dense_harmonic(m, n, seed=2)
     assert A32.dtype == np.float32 and A32.flags.f_contiguous
 
 
@@ -37,7 +37,7 @@ def test_exact_rank_and_haar_factors():
 
 
 def test_kernel_blocks_shapes_and_values():
-    """Config 4: block sizes inside their ranges, entries exp(-|x-y|^2/h^2) in (0, 1), and
+    """Kernel blocks: block sizes inside their ranges, entries exp(-|x-y|^2/h^2) in (0, 1), and
     well-separated clusters make the blocks numerically low rank."""
     blocks = workloads.kernel_blocks(12, seed=4)
     for B in blocks:
@@ -50,7 +50,7 @@ def test_kernel_blocks_shapes_and_values():
 def test_torch_builders_match_recipe():
     """The device builders (run here on the CPU) keep the recipe: spectrum of the dense case,
     column-major blocks with 16-byte aligned columns."""
-    A = workloads.torch_dense_spectrum(256, 192, workloads.sigma_config2(192), 0.0, 5, "cpu", torch.float64)
+    A = workloads.torch_dense_spectrum(256, 192, workloads.sigma_harmonic(192), 0.0, 5, "cpu", torch.float64)
     s = torch.linalg.svdvals(A).numpy()
     assert np.allclose(s[:40], 1.0 / np.arange(1, 41), rtol=1e-8)
     blocks = workloads.torch_kernel_blocks(6, 7, "cpu")

@@ -2,18 +2,21 @@ import numpy as np
 import scipy.sparse as sp
 
 __all__ = [
-    "SEED_BASE", "seed_for", "haar_orthogonal", "dense_spectrum", "sigma_config1",
-    "sigma_config2", "sigma_config5", "config1", "dense_config2", "snn_csc",
+    "SEED_BASE", "WORKLOAD_SEED_OFFSETS", "seed_for", "haar_orthogonal", "dense_spectrum",
+    "sigma_geometric40", "sigma_harmonic", "sigma_exp200", "dense_geometric40", "dense_harmonic", "snn_csc",
     "kahan_type", "separated_columns", "exact_rank", "kernel_blocks",
-    "torch_dense_spectrum", "torch_config5", "CONFIG5_R_EFF",
+    "torch_dense_spectrum", "torch_dense_exp200", "EXP200_R_EFF",
     "torch_kernel_blocks", "kernel_points"]
 
 SEED_BASE = 2104_05877
+# Seed offsets of the named workloads: seed_A = SEED_BASE + offset, seed_Gamma = seed_A + 1000.
+WORKLOAD_SEED_OFFSETS = {"dense_1000x800": 1, "dense_8192x8192": 2, "snn_262144x4096": 3,
+                         "kernel_blocks_4096": 4, "dense_65536x32768": 5}
 
 
-def seed_for(config_id, what="A"):
-    """seed_A = 2104_05877 + config id; seed_Gamma = seed_A + 1000."""
-    base = SEED_BASE + int(config_id)
+def seed_for(workload, what="A"):
+    """Seed of a named workload's A (what = "A") or of its embedding (what = "gamma")."""
+    base = SEED_BASE + WORKLOAD_SEED_OFFSETS[workload]
     return base if what == "A" else base + 1000
 
 
@@ -36,31 +39,31 @@ def dense_spectrum(m, n, sigma, noise_std, seed, dtype=np.float64):
     return np.asfortranarray(A.astype(dtype))
 
 
-def sigma_config1(n):
+def sigma_geometric40(n):
     """sigma_j = 10^(-(j-1)/40), j = 1..n."""
     return 10.0 ** (-np.arange(n) / 40.0)
 
 
-def sigma_config2(n):
+def sigma_harmonic(n):
     """sigma_j = 1/j, j = 1..n."""
     return 1.0 / np.arange(1, n + 1)
 
 
-def sigma_config5(r):
+def sigma_exp200(r):
     """sigma_j = exp(-j/200), j = 1..r."""
     return np.exp(-np.arange(1, r + 1) / 200.0)
 
 
-def config1(m=1000, n=800, seed=None):
+def dense_geometric40(m=1000, n=800, seed=None):
     """Plain small case: 1000 x 800 FP64, sigma_j = 10^(-(j-1)/40), + 1e-12 N(0,1)."""
-    seed = seed_for(1) if seed is None else seed
-    return dense_spectrum(m, n, sigma_config1(min(m, n)), 1e-12, seed, np.float64)
+    seed = seed_for("dense_1000x800") if seed is None else seed
+    return dense_spectrum(m, n, sigma_geometric40(min(m, n)), 1e-12, seed, np.float64)
 
 
-def dense_config2(m, n, seed=None, floor=1e-6, dtype=np.float32):
+def dense_harmonic(m, n, seed=None, floor=1e-6, dtype=np.float32):
     """sigma_j = 1/j plus a noise floor: floor * G / sqrt(m) (singular values ~ floor)."""
-    seed = seed_for(2) if seed is None else seed
-    return dense_spectrum(m, n, sigma_config2(min(m, n)), floor / np.sqrt(m), seed, dtype)
+    seed = seed_for("dense_8192x8192") if seed is None else seed
+    return dense_spectrum(m, n, sigma_harmonic(min(m, n)), floor / np.sqrt(m), seed, dtype)
 
 
 def exact_rank(m, n, r, seed, dtype=np.float64, decay=0.8):
@@ -171,17 +174,17 @@ def torch_dense_spectrum(m, n, sigma, noise_std, seed, device, dtype):
     return At.to(dtype).t()                  # m x n view, column-major storage
 
 
-CONFIG5_R_EFF = 3300        # exp(-3300/200) < 1e-7: below this the spectrum is the noise floor
+EXP200_R_EFF = 3300        # exp(-3300/200) < 1e-7: below this the spectrum is the noise floor
 
 
-def torch_config5(device, m=65536, n=32768, r_eff=CONFIG5_R_EFF, floor=1e-7, seed=None):
+def torch_dense_exp200(device, m=65536, n=32768, r_eff=EXP200_R_EFF, floor=1e-7, seed=None):
     """Large low-precision case: A = U diag(sigma) V^T + floor * G / sqrt(m), sigma_j =
     exp(-j/200) for j <= r_eff, U (m x r_eff) and V (n x r_eff) Haar by QR of FP32 Gaussians,
     built in FP32 on `device` (an FP64 build at 65536 x 32768 would cost ~14 FP64 TFLOP).
     Returned column-major (the transpose view of a row-major n x m tensor)."""
     import torch
-    seed = seed_for(5) if seed is None else seed
-    sig = sigma_config5(r_eff)
+    seed = seed_for("dense_65536x32768") if seed is None else seed
+    sig = sigma_exp200(r_eff)
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
     tf32 = torch.backends.cuda.matmul.allow_tf32
